@@ -1,0 +1,353 @@
+#!/usr/bin/env python
+"""Throughput of DNA iterations for KL-NMF on GB300 (one JSON line on stdout).
+
+A step is one DNA iteration (H half-step then W half-step, Algorithm 1 steps 4-29) on
+the workload N=4096 T=16384 R=128 (Gamma(0.3) truth scaled to mean count 2, Poisson
+counts; seeded synthetic data standing in for the paper's dense datasets) in the FP32
+form.  The inputs (V is 268 MB) are larger than L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl dna|reference]
+
+Under torchrun each rank solves its own independent problem (seed = rank) on its own
+GPU: weak scaling with no collective on the data path; the timed region is bracketed by
+barriers and the max over ranks is reported.  ``--impl reference`` times the FP64 CPU
+oracle on the host cores instead (bounded column sample, scaled to the full workload).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "sec to target d_KL & DNA iters/s (BF16 vs FP32 form), % tensor peak"
+UNIT = "DNA iterations/s"
+SMS = 152
+FP32_LANES_PER_SM = 128
+
+WORKLOADS = {
+    "plain_large": dict(fn=workloads.plain_large, N=4096, T=16384, R=128,
+                        desc="N=4096 T=16384 R=128, Gamma(0.3) truth scaled to mean 2, Poisson V"),
+    "plain_small": dict(fn=workloads.plain_small, N=256, T=512, R=16,
+                        desc="N=256 T=512 R=16, Gamma(0.5) truth, Poisson V"),
+}
+
+
+def measured_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1301_3389_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode())
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(phase: str, workload: str):
+    """DRAM bytes per launch from profiles/traffic.txt, if taken on the current sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    want = kernel_source_hash()
+    with open(path) as f:
+        for line in f:
+            parts = line.split("#", 1)[0].split()
+            if len(parts) == 4 and parts[0] == phase and parts[1] == workload and parts[2] == want:
+                return float(parts[3])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, local_rank: int):
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        ident = vis.split(",")[local_rank].strip() if vis else str(local_rank)
+        self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={ident}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.tmp.flush()
+        self.tmp.seek(0)
+        rows = [r.split(",") for r in self.tmp.read().splitlines() if r.strip()]
+        os.unlink(self.tmp.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for name, flag in zip(names, r[5:9]):
+                if flag.strip().lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def sample_columns(prob, cols: int):
+    V = prob.V[:, :cols]
+    H = prob.H[:, :cols]
+    return V, prob.W, H
+
+
+def oracle_rate(prob, cols: int, budget_s: float, min_iters: int = 1, max_iters=None):
+    """FP64 oracle DNA iterations on the first ``cols`` columns; returns (iters, seconds)."""
+    from oracle import dna as o
+    V, W, H = sample_columns(prob, cols)
+    W, H = o.normalize_w_columns(W, H)
+    it, t0 = 0, time.perf_counter()
+    while True:
+        W, H, _, _ = o.dna_iteration(V, W, H)
+        it += 1
+        el = time.perf_counter() - t0
+        if it >= min_iters and (el >= budget_s or (max_iters and it >= max_iters)):
+            return it, el
+
+
+def cpu_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def run_reference(args, spec, prob):
+    """The FP64 CPU oracle as it stands, timed on the host cores (bounded sample)."""
+    from oracle import dna as o
+    cols = args.ref_cols
+    V, W, H = sample_columns(prob, cols)
+    W, H = o.normalize_w_columns(W, H)
+    for _ in range(args.warmup):
+        W, H, _, _ = o.dna_iteration(V, W, H)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        W, H, _, _ = o.dna_iteration(V, W, H)
+    el = time.perf_counter() - t0
+    scale = cols / spec["T"]
+    value = args.steps / el * scale
+    sample = (f"{args.steps} timed DNA iterations of the FP64 NumPy oracle on the first "
+              f"{cols} of {spec['T']} columns; rate scaled by {cols}/{spec['T']}")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3 / scale,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": args.workload, "desc": spec["desc"],
+                                        "sample_columns": cols},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["dna", "reference"], default="dna")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="plain_large")
+    ap.add_argument("--dtype", choices=["f32", "f64"], default="f32")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work")
+    ap.add_argument("--ref-cols", type=int, default=512)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    spec = WORKLOADS[args.workload]
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        prob = spec["fn"](0)
+        run_reference(args, spec, prob)
+        return 0
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_1301_3389_gb300 as dna
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    prob = spec["fn"](rank)                      # independent problem per rank
+    N, T, R = spec["N"], spec["T"], spec["R"]
+    code = dna.DNA_F32 if args.dtype == "f32" else dna.DNA_F64
+    tdt = torch.float32 if args.dtype == "f32" else torch.float64
+    dev = torch.device("cuda", local)
+    V = torch.from_numpy(prob.V).to(dev, tdt)
+    W = torch.from_numpy(prob.W).to(dev, tdt)
+    H = torch.from_numpy(prob.H).to(dev, tdt)
+    stream = torch.cuda.current_stream()
+    ctx = dna.dna_create(N, T, R, dna.make_opts(dtype=code))
+    dna.dna_set_stream(ctx, stream)
+    dna.dna_bind(ctx, V, W, H)
+    dna.dna_normalize(ctx, 1)                    # Algorithm 1 step 1
+    kl_start = dna.dna_kl(ctx)
+    for _ in range(args.warmup):
+        dna.dna_iterate(ctx, 1)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    time.sleep(0.3)
+    dna.dna_profile(ctx, True)
+    dna.dna_phase_times(ctx)                     # reset counters
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        dna.dna_iterate(ctx, 1)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    phases = dna.dna_phase_times(ctx)
+    dna.dna_profile(ctx, False)
+    clk = clocks.stop()
+    kl_end = dna.dna_kl(ctx)
+    dna.dna_destroy(ctx)
+
+    ms_max = ms
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = world * args.steps / (ms_max / 1e3)
+
+    # roofline of the dominant kernel (largest share of the timed region)
+    dom = max(("pass1", "pass2"), key=lambda p: phases[p][0])
+    dom_ms, dom_launches = phases[dom]
+    per_launch_s = dom_ms / max(dom_launches, 1) / 1e3
+    flops = (6 if dom == "pass1" else 4) * R * N * T    # per launch (H or W half-step)
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tflops = SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12 if args.dtype == "f32" \
+        else None
+    achieved = flops / per_launch_s / 1e12
+    traffic = recorded_traffic(dom, args.workload)
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_tflops,
+                "unit": "TFLOP/s", "frac": (achieved / peak_tflops) if peak_tflops else None,
+                "traffic": traffic,
+                "peak_source": (f"derived: {SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x "
+                                f"{sm_max:.0f} MHz (max SM clock of measured)"),
+                "algorithmic_flops_per_launch": flops,
+                "launch_ms": per_launch_s * 1e3,
+                "phase_share": {p: phases[p][0] / ms for p in ("pass1", "candidates", "pass2",
+                                                                "select", "sums")}}
+    launches = sum(v[1] for k, v in phases.items())
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+        "config": {"workload": args.workload, "desc": spec["desc"], "N": N, "T": T, "R": R,
+                   "form": args.dtype.upper(), "engine": "simt",
+                   "l2": "inputs larger than L2 (V is %d MB)" % (N * T * 4 // 2**20),
+                   "parallelism": "independent problem per GPU" if world > 1 else "single GPU",
+                   "zero_fraction": prob.meta.get("zero_fraction")},
+        "gpu_launches": launches,
+        "roofline": roofline,
+        "clocks": clk,
+        "kl_start": kl_start, "kl_end": kl_end,
+    }
+
+    if rank == 0 and not args.no_e2e:
+        line["e2e"] = e2e_measure(dna, torch, prob, code, tdt, N, T, R, args.e2e_steps)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cols = 1024
+        it, el = oracle_rate(prob, cols, args.cpu_budget)
+        line["cpu_baseline"] = {
+            "value": it / el * cols / T, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+            "sample": f"{it} DNA iterations of the FP64 NumPy oracle on the first {cols} of {T} "
+                      f"columns in {el:.1f} s, rate scaled by {cols}/{T}"}
+    if world > 1:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def e2e_measure(dna, torch, prob, code, tdt, N, T, R, steps):
+    """Iterations/s through dna_run_host on pinned host buffers: each step copies V, W, H
+    in, runs one DNA iteration, and copies W, H and d_KL out."""
+    Vh = torch.from_numpy(prob.V).to(tdt).pin_memory()
+    Wh = torch.from_numpy(prob.W).to(tdt).pin_memory()
+    Hh = torch.from_numpy(prob.H).to(tdt).pin_memory()
+    ctx = dna.dna_create(N, T, R, dna.make_opts(dtype=code))
+    try:
+        dna.dna_set_stream(ctx, torch.cuda.current_stream())
+        for _ in range(3):
+            dna.dna_run_host(ctx, Vh, Wh, Hh, 1)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            dna.dna_run_host(ctx, Vh, Wh, Hh, 1)
+        el = time.perf_counter() - t0
+    finally:
+        dna.dna_destroy(ctx)
+    es = Vh.element_size()
+    return {"value": steps / el, "unit": UNIT,
+            "h2d_bytes_per_step": es * (N * T + N * R + R * T),
+            "d2h_bytes_per_step": es * (N * R + R * T) + 8}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,171 @@
+/*
+ * dna.h - C ABI of the GB300 (sm_103a) library for the Diagonalized Newton Algorithm
+ * (DNA) for KL-divergence NMF (H. Van hamme, "The Diagonalized Newton Algorithm for
+ * Non-negative Matrix Factorization", arXiv 1301.3389).
+ *
+ * Problem (Section 1, eq. 1): factor a non-negative N x T matrix V as W H with W
+ * (N x R) and H (R x T) non-negative, minimising
+ *     d_KL(V, WH) = sum v log(v / z) - sum v + sum z,   Z = W H.
+ * One DNA iteration (Algorithm 1) updates H with W fixed (steps 4-16), then W with H
+ * fixed (steps 17-29).  Each half-step forms the MU candidate (eq. 11) and the
+ * diagonal-Newton candidate (eq. 15 / 17 with the step limits of Section 2.3 and the
+ * eq. 10 renormalisation), evaluates both costs per column of H (per row of W) and
+ * keeps the cheaper one (Section 2.4).
+ *
+ * Layout: every matrix is dense and row-major.  V is N x T with leading dimension
+ * ldv >= T; W is N x R with leading dimension R; H is R x T with leading dimension T.
+ * Element type: double for DNA_F64, float for DNA_F32 and DNA_BF16 (the BF16 form
+ * keeps float masters and rounds only tensor-core operands to bfloat16).
+ *
+ * Ownership: the caller owns V, W and H (device memory) and the CUDA stream.  The
+ * library owns a context and its device workspace, allocated by dna_create/dna_bind
+ * and released by dna_destroy; the step calls allocate nothing and never synchronise
+ * the host.  W and H are updated in place.
+ *
+ * Errors: every int-returning call returns DNA_OK (0) or a negative DNA_ERR_* code.
+ * Argument errors are detected on the host before any work is queued.  Errors found by
+ * kernels (a non-positive z where v > 0, which makes the cost infinite) are recorded in
+ * a device status word and returned by the next synchronising call (dna_kl,
+ * dna_get_status, dna_get_choice, dna_get_costs, dna_run_host).
+ */
+#ifndef DNA_H_
+#define DNA_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DNA_OK               0
+#define DNA_ERR_ARG         (-1)  /* bad argument (size, pointer, option, call order) */
+#define DNA_ERR_CUDA        (-2)  /* a CUDA runtime call or kernel launch failed       */
+#define DNA_ERR_NONFINITE   (-3)  /* z <= 0 where v > 0, or a non-finite value          */
+#define DNA_ERR_TIMEOUT     (-4)  /* a bounded device-side wait gave up                 */
+#define DNA_ERR_UNSUPPORTED (-5)  /* valid request this build does not implement       */
+#define DNA_ERR_ALLOC       (-6)  /* device allocation failed                           */
+
+/* Arithmetic forms. */
+#define DNA_F64  0  /* float64 everywhere                                                */
+#define DNA_F32  1  /* float32 everywhere, float64 per-column cost sums                  */
+#define DNA_BF16 2  /* bfloat16 tensor-core operands, float32 accumulation and masters,
+                       float64 per-column cost sums                                      */
+
+/* Engines for the O(NRT) contractions. */
+#define DNA_ENGINE_AUTO   0
+#define DNA_ENGINE_SIMT   1  /* CUDA-core FMA kernels (F64, F32)                          */
+#define DNA_ENGINE_TENSOR 2  /* tcgen05 tensor-core kernels with TMEM accumulators         */
+
+typedef struct dna_opts {
+    double eps;     /* floor on the Newton gain for a < 0 (Algorithm 1 steps 11, 24);
+                       default 0.01 (Section 4)                                          */
+    double alpha;   /* the gain of the a >= 0 step is capped at 1 + alpha (Section 2.3,
+                       eq. 17); default 4 (Section 4)                                    */
+    double rho;     /* regularisation weight on W (eq. 2); default 0 (Section 4)         */
+    double lambda;  /* regularisation weight on H (eq. 2); default 0 (Section 4)         */
+    int32_t dtype;  /* DNA_F64, DNA_F32 or DNA_BF16; default DNA_F32                     */
+    int32_t engine; /* DNA_ENGINE_*; default DNA_ENGINE_AUTO                             */
+} dna_opts;
+
+typedef struct dna_ctx dna_ctx;
+
+/* Fill *opts with the defaults above (the parameters of Section 4). */
+void dna_default_opts(dna_opts* opts);
+
+/* Create a context for an N x T problem of rank R on the current CUDA device.
+ * opts may be NULL (defaults).  Sizes must satisfy N >= 1, T >= 1, 1 <= R <= 512.
+ * Allocates the workspace (O(N T) for the transposed copy of V made by dna_bind, plus
+ * O((N + T) R)).  On success *out receives the context. */
+int dna_create(int64_t N, int64_t T, int64_t R, const dna_opts* opts, dna_ctx** out);
+
+/* Attach the caller's device buffers: V (N x T, leading dimension ldv >= T, read only),
+ * W (N x R) and H (R x T), all of the context's element type.  Queues, on the
+ * context's stream, the one-time preparation that depends on V (row and column sums of
+ * V, and the transposed copy used by the W half-step).  V must not change while bound. */
+int dna_bind(dna_ctx* ctx, const void* V, int64_t ldv, void* W, void* H);
+
+/* Set the CUDA stream (a cudaStream_t; NULL = legacy default stream) for later calls. */
+int dna_set_stream(dna_ctx* ctx, void* stream);
+
+/* Normalisation of Algorithm 1.  which = 1: steps 1 and 29, divide column r of W by
+ * sum_n w_nr + lambda and multiply row r of H by the same number.  which = 0: step 16,
+ * divide row r of H by sum_t h_rt + rho and multiply column r of W.  W H is unchanged. */
+int dna_normalize(dna_ctx* ctx, int which);
+
+/* DNA H half-step, Algorithm 1 steps 4-16 (eq. 7, 10, 11, 14, 15, 17; Section 2.4),
+ * with W fixed: H <- per column the lower-cost of the MU and Newton candidates, then
+ * the step-16 normalisation (which also rescales the columns of W).  Asynchronous. */
+int dna_step_H(dna_ctx* ctx);
+
+/* DNA W half-step, Algorithm 1 steps 17-29: the mirror of dna_step_H by the symmetry
+ * d_KL(V, WH) = d_KL(V^t, H^t W^t) (Section 2), selection per row of W, then the
+ * step-29 normalisation (which also rescales the rows of H).  Asynchronous. */
+int dna_step_W(dna_ctx* ctx);
+
+/* iters DNA iterations: iters times (dna_step_H, dna_step_W).  Asynchronous. */
+int dna_iterate(dna_ctx* ctx, int iters);
+
+/* Multiplicative update (eq. 11; Algorithm 1 "MU" steps).  which = 0: H <- H (W^t Q) /
+ * (W^t 1 + lambda) then step 16; which = 1: W <- W (Q H^t) / (H 1 + rho) then step 29.
+ * Asynchronous. */
+int mu_step(dna_ctx* ctx, int which);
+
+/* d_KL(V, W H) of eq. 1 in float64, written to *out (host memory).  Synchronises the
+ * context's stream; also returns any error recorded by earlier kernels. */
+int dna_kl(dna_ctx* ctx, double* out);
+
+/* Copy the selection of the last DNA half-step to host memory: which = 0 gives T bytes
+ * (column t of H took the Newton candidate iff out[t] = 1), which = 1 gives N bytes (per
+ * row of W).  len must equal T (N).  Synchronises. */
+int dna_get_choice(dna_ctx* ctx, int which, uint8_t* out, int64_t len);
+
+/* Copy the per-column (which = 0, T values) or per-row (which = 1, N values) costs of
+ * the two candidates of the last DNA half-step to host memory:
+ * d = sum_{v>0} (-v log z) + sum z over that column (row) (Algorithm 1 steps 9, 14, 22,
+ * 27, with the candidate-independent constant dropped).  Synchronises. */
+int dna_get_costs(dna_ctx* ctx, int which, double* d_mu, double* d_dna, int64_t len);
+
+/* Synchronise the stream and return the sticky device status (DNA_OK or an error). */
+int dna_get_status(dna_ctx* ctx);
+
+/* End-to-end call on HOST buffers: copy V (N x T, ldv = T), W and H from host memory
+ * to library-owned device buffers (allocated on the first call and reused), run
+ * iters DNA iterations, copy W and H back and write d_KL(V, WH) to *kl_out (may be
+ * NULL).  Pinned host memory gives the fastest copies.  Synchronises.  A context used
+ * this way must not also be bound with dna_bind. */
+int dna_run_host(dna_ctx* ctx, const void* V, void* W, void* H, int iters, double* kl_out);
+
+/* Phases of a half-step, for dna_phase_times. */
+#define DNA_PHASE_PASS1      0  /* Z, Q, Qbar and the A, B contractions (steps 2-5, 10)  */
+#define DNA_PHASE_CANDIDATES 1  /* MU and Newton candidates, eq. 10 (steps 6, 11)       */
+#define DNA_PHASE_PASS2      2  /* candidate costs (steps 7-9, 12-14)                    */
+#define DNA_PHASE_SELECT     3  /* per-column selection (step 15)                        */
+#define DNA_PHASE_SUMS       4  /* factor sums and rescaling (steps 1, 16, 29)           */
+#define DNA_PHASE_KL         5  /* d_KL (eq. 1)                                           */
+#define DNA_PHASE_PREPARE    6  /* one-time sums and transpose of V (dna_bind)           */
+#define DNA_NUM_PHASES       7
+
+/* enable = 1: from now on record a CUDA event pair on the context's stream around each
+ * phase of every call (no device allocation; up to 16384 pairs are kept, later phases
+ * are counted but not timed); enable = 0 stops recording.  Launch counts are always
+ * kept. */
+int dna_profile(dna_ctx* ctx, int enable);
+
+/* Write, for each of the first n phases, the summed device time in milliseconds of the
+ * recorded phase instances (ms, may be NULL) and the number of kernel launches of that
+ * phase (launches, may be NULL) since the previous call, then reset both.
+ * Synchronises the stream. */
+int dna_phase_times(dna_ctx* ctx, double* ms, int64_t* launches, int n);
+
+/* Release the context and its workspace (not the caller's buffers). */
+void dna_destroy(dna_ctx* ctx);
+
+/* Static English description of a status code. */
+const char* dna_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DNA_H_ */

@@ -1,0 +1,207 @@
+"""ctypes binding of libdna.so (include/dna.h): argument marshalling only.
+
+Every function has the name of the C entry point it calls.  Device buffers are torch
+CUDA tensors (their data pointers are passed); the stream is torch's current stream
+unless one is given.  There is no fallback: if libdna.so is missing or fails to load,
+importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdna.so")
+
+DNA_OK = 0
+DNA_ERR_ARG = -1
+DNA_ERR_CUDA = -2
+DNA_ERR_NONFINITE = -3
+DNA_ERR_TIMEOUT = -4
+DNA_ERR_UNSUPPORTED = -5
+DNA_ERR_ALLOC = -6
+
+DNA_F64, DNA_F32, DNA_BF16 = 0, 1, 2
+PHASES = ("pass1", "candidates", "pass2", "select", "sums", "kl", "prepare")
+DNA_ENGINE_AUTO, DNA_ENGINE_SIMT, DNA_ENGINE_TENSOR = 0, 1, 2
+
+
+class dna_opts(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("rho", ctypes.c_double), ("lambda_", ctypes.c_double),
+                ("dtype", ctypes.c_int32), ("engine", ctypes.c_int32)]
+
+
+class DNAError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {dna_strerror(code)} ({code})")
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libdna.so not built ({LIB_PATH}); run "
+                          "`python -m paper_1301_3389_gb300.build` (needs nvcc)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I64, I, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    sig = {
+        "dna_default_opts": (None, [ctypes.POINTER(dna_opts)]),
+        "dna_create": (I, [I64, I64, I64, ctypes.POINTER(dna_opts), ctypes.POINTER(P)]),
+        "dna_bind": (I, [P, P, I64, P, P]),
+        "dna_set_stream": (I, [P, P]),
+        "dna_normalize": (I, [P, I]),
+        "dna_step_H": (I, [P]),
+        "dna_step_W": (I, [P]),
+        "dna_iterate": (I, [P, I]),
+        "mu_step": (I, [P, I]),
+        "dna_kl": (I, [P, ctypes.POINTER(D)]),
+        "dna_get_choice": (I, [P, I, P, I64]),
+        "dna_get_costs": (I, [P, I, P, P, I64]),
+        "dna_get_status": (I, [P]),
+        "dna_run_host": (I, [P, P, P, P, I, ctypes.POINTER(D)]),
+        "dna_profile": (I, [P, I]),
+        "dna_phase_times": (I, [P, P, P, I]),
+        "dna_destroy": (None, [P]),
+        "dna_strerror": (ctypes.c_char_p, [I]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+LIB = _load()
+
+
+def _check(code: int, where: str) -> None:
+    if code != DNA_OK:
+        raise DNAError(code, where)
+
+
+def _ptr(t) -> int:
+    """Device (or host) address of a torch tensor or a NumPy array."""
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr()
+    return t.ctypes.data
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def dna_strerror(code: int) -> str:
+    return LIB.dna_strerror(int(code)).decode()
+
+
+def dna_default_opts() -> dna_opts:
+    o = dna_opts()
+    LIB.dna_default_opts(ctypes.byref(o))
+    return o
+
+
+def make_opts(eps=None, alpha=None, rho=None, lam=None, dtype=None, engine=None) -> dna_opts:
+    o = dna_default_opts()
+    if eps is not None:
+        o.eps = eps
+    if alpha is not None:
+        o.alpha = alpha
+    if rho is not None:
+        o.rho = rho
+    if lam is not None:
+        o.lambda_ = lam
+    if dtype is not None:
+        o.dtype = dtype
+    if engine is not None:
+        o.engine = engine
+    return o
+
+
+def dna_create(N: int, T: int, R: int, opts: dna_opts | None = None) -> int:
+    h = ctypes.c_void_p()
+    _check(LIB.dna_create(N, T, R, ctypes.byref(opts) if opts is not None else None,
+                          ctypes.byref(h)), "dna_create")
+    return h.value
+
+
+def dna_bind(ctx: int, V, W, H, ldv: int | None = None) -> None:
+    if ldv is None:
+        ldv = V.stride(0) if hasattr(V, "stride") else V.shape[1]
+    _check(LIB.dna_bind(ctx, _ptr(V), ldv, _ptr(W), _ptr(H)), "dna_bind")
+
+
+def dna_set_stream(ctx: int, stream=None) -> None:
+    _check(LIB.dna_set_stream(ctx, _stream(stream)), "dna_set_stream")
+
+
+def dna_normalize(ctx: int, which: int) -> None:
+    _check(LIB.dna_normalize(ctx, which), "dna_normalize")
+
+
+def dna_step_H(ctx: int) -> None:
+    _check(LIB.dna_step_H(ctx), "dna_step_H")
+
+
+def dna_step_W(ctx: int) -> None:
+    _check(LIB.dna_step_W(ctx), "dna_step_W")
+
+
+def dna_iterate(ctx: int, iters: int) -> None:
+    _check(LIB.dna_iterate(ctx, iters), "dna_iterate")
+
+
+def mu_step(ctx: int, which: int) -> None:
+    _check(LIB.mu_step(ctx, which), "mu_step")
+
+
+def dna_kl(ctx: int) -> float:
+    out = ctypes.c_double()
+    _check(LIB.dna_kl(ctx, ctypes.byref(out)), "dna_kl")
+    return out.value
+
+
+def dna_get_choice(ctx: int, which: int, n: int):
+    import numpy as np
+    out = np.zeros(n, dtype=np.uint8)
+    _check(LIB.dna_get_choice(ctx, which, out.ctypes.data, n), "dna_get_choice")
+    return out.astype(bool)
+
+
+def dna_get_costs(ctx: int, which: int, n: int):
+    import numpy as np
+    dm = np.zeros(n, dtype=np.float64)
+    dd = np.zeros(n, dtype=np.float64)
+    _check(LIB.dna_get_costs(ctx, which, dm.ctypes.data, dd.ctypes.data, n), "dna_get_costs")
+    return dm, dd
+
+
+def dna_get_status(ctx: int) -> int:
+    return LIB.dna_get_status(ctx)
+
+
+def dna_run_host(ctx: int, V, W, H, iters: int) -> float:
+    kl = ctypes.c_double()
+    _check(LIB.dna_run_host(ctx, _ptr(V), _ptr(W), _ptr(H), iters, ctypes.byref(kl)),
+           "dna_run_host")
+    return kl.value
+
+
+def dna_profile(ctx: int, enable: bool = True) -> None:
+    _check(LIB.dna_profile(ctx, 1 if enable else 0), "dna_profile")
+
+
+def dna_phase_times(ctx: int) -> dict:
+    """{phase: (milliseconds, launches)} since the previous call."""
+    import numpy as np
+    ms = np.zeros(len(PHASES), dtype=np.float64)
+    nl = np.zeros(len(PHASES), dtype=np.int64)
+    _check(LIB.dna_phase_times(ctx, ms.ctypes.data, nl.ctypes.data, len(PHASES)),
+           "dna_phase_times")
+    return {p: (float(ms[i]), int(nl[i])) for i, p in enumerate(PHASES)}
+
+
+def dna_destroy(ctx: int) -> None:
+    LIB.dna_destroy(ctx)

@@ -1,0 +1,546 @@
+// C ABI of the DNA library: context, workspace, and the order of kernel launches for
+// each call of include/dna.h.  Host code only; kernels live in simt_kernels.cuh.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "dna.h"
+#include "dna_internal.h"
+
+using dna::View;
+
+struct dna_ctx {
+    int64_t N = 0, T = 0, R = 0;
+    dna_opts o{};
+    int device = 0;
+    int num_sms = 1;
+    cudaStream_t stream = nullptr;
+    size_t esz = 4;
+    // caller's buffers
+    const void* V = nullptr;
+    int64_t ldv = 0;
+    void* W = nullptr;
+    void* H = nullptr;
+    bool bound = false;
+    bool host_mode = false;  // buffers owned by the library (dna_run_host)
+    void* own_V = nullptr;
+    void* own_W = nullptr;
+    void* own_H = nullptr;
+    // workspace
+    void* Vt = nullptr;  // T x ldvt transposed copy of V
+    int64_t ldvt = 0;
+    double* colsum_v = nullptr;  // T
+    double* rowsum_v = nullptr;  // N
+    double* c = nullptr;         // R
+    double* sig = nullptr;       // R
+    void* Apart = nullptr;       // [splits][R][O]
+    void* Bpart = nullptr;
+    void* Xmu = nullptr;         // [R][O]
+    void* Xdna = nullptr;
+    double* dpart = nullptr;     // [splits][2][O]
+    double* dfin_h = nullptr;    // [2][T]
+    double* dfin_w = nullptr;    // [2][N]
+    uint8_t* choice_h = nullptr; // T
+    uint8_t* choice_w = nullptr; // N
+    double* kl_dev = nullptr;    // 1
+    int* status = nullptr;       // 1
+    // split plans (pass 1 and pass 2 / KL) for the H view and the W view
+    int sp1[2] = {1, 1}, sp2[2] = {1, 1};
+    int64_t per1[2] = {0, 0}, per2[2] = {0, 0};
+    // profiling: event pairs around phases, launch counts
+    bool prof_on = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, size_t>> ev_recs;  // (phase, index of the start event)
+    size_t ev_used = 0;
+    double phase_ms[DNA_NUM_PHASES] = {};
+    int64_t phase_launches[DNA_NUM_PHASES] = {};
+};
+
+namespace {
+
+int set_device(const dna_ctx* c);
+template <class F>
+int phase(dna_ctx* c, int ph, int nlaunch, F&& f);
+
+bool valid_opts(const dna_opts& o) {
+    if (!(o.eps > 0.0) || !(o.eps <= 1.0)) return false;
+    if (!(o.alpha >= 0.0)) return false;
+    if (!(o.rho >= 0.0) || !(o.lambda >= 0.0)) return false;
+    if (o.dtype != DNA_F64 && o.dtype != DNA_F32 && o.dtype != DNA_BF16) return false;
+    if (o.engine < DNA_ENGINE_AUTO || o.engine > DNA_ENGINE_TENSOR) return false;
+    return true;
+}
+
+template <typename P>
+int dmalloc(P** p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (cudaMalloc(reinterpret_cast<void**>(p), bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return DNA_ERR_ALLOC;
+    }
+    return DNA_OK;
+}
+
+View make_view(const dna_ctx* c, bool wstep) {
+    View v{};
+    v.R = c->R;
+    if (!wstep) {  // H half-step: s = n, o = t
+        v.S = c->N; v.O = c->T;
+        v.V = c->V; v.vs = c->ldv;
+        v.X = c->H; v.xr = c->T; v.xo = 1;
+        v.Y = c->W; v.ys = c->R; v.yr = 1;
+        v.vsum = c->colsum_v;
+    } else {       // W half-step: s = t, o = n, on the transposed copy of V
+        v.S = c->T; v.O = c->N;
+        v.V = c->Vt; v.vs = c->ldvt;
+        v.X = c->W; v.xr = 1; v.xo = c->R;
+        v.Y = c->H; v.ys = 1; v.yr = c->T;
+        v.vsum = c->rowsum_v;
+    }
+    return v;
+}
+
+// Split the reduction over s so that the grid fills the GPU about once.
+void plan_split(int64_t S, int64_t nblocks_os, int slots, int chunk, int* splits, int64_t* per) {
+    const int64_t chunks = (S + chunk - 1) / chunk;
+    int64_t sp = (slots + nblocks_os - 1) / std::max<int64_t>(nblocks_os, 1);
+    sp = std::max<int64_t>(1, std::min<int64_t>(sp, std::max<int64_t>(1, chunks / 4)));
+    sp = std::min<int64_t>(sp, 32);
+    const int64_t per_chunks = (chunks + sp - 1) / sp;
+    *per = per_chunks * chunk;
+    *splits = (int)((S + *per - 1) / *per);
+}
+
+template <typename Tp>
+void plan_all(dna_ctx* c) {
+    using S = dna::Simt<Tp>;
+    const int ob = S::oblock(), ch = S::chunk();
+    const int rb = S::rblock(c->R);
+    const int64_t nrb = (c->R + rb - 1) / rb;
+    const int b1 = S::pass1_blocks_per_sm(c->R), b2 = S::pass2_blocks_per_sm(c->R);
+    for (int w = 0; w < 2; ++w) {
+        const int64_t Sdim = w ? c->T : c->N, Odim = w ? c->N : c->T;
+        const int64_t nob = (Odim + ob - 1) / ob;
+        plan_split(Sdim, nob * nrb, c->num_sms * b1, ch, &c->sp1[w], &c->per1[w]);
+        plan_split(Sdim, nob, c->num_sms * b2, ch, &c->sp2[w], &c->per2[w]);
+    }
+}
+
+void free_all(dna_ctx* c) {
+    void* ptrs[] = {c->own_V, c->own_W, c->own_H, c->Vt, c->colsum_v, c->rowsum_v, c->c, c->sig,
+                    c->Apart, c->Bpart, c->Xmu, c->Xdna, c->dpart, c->dfin_h, c->dfin_w,
+                    c->choice_h, c->choice_w, c->kl_dev, c->status};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    for (cudaEvent_t ev : c->ev_pool) cudaEventDestroy(ev);
+    c->ev_pool.clear();
+}
+
+template <typename Tp>
+int alloc_workspace(dna_ctx* c) {
+    plan_all<Tp>(c);
+    const int64_t N = c->N, T = c->T, R = c->R, M = std::max(N, T);
+    int64_t ap = 0, dp = 0;
+    for (int w = 0; w < 2; ++w) {
+        const int64_t O = w ? N : T;
+        ap = std::max<int64_t>(ap, (int64_t)c->sp1[w] * R * O);
+        dp = std::max<int64_t>(dp, (int64_t)c->sp2[w] * 2 * O);
+    }
+    c->ldvt = (N + 3) / 4 * 4;
+    int e = DNA_OK;
+    e |= dmalloc(&c->Vt, sizeof(Tp) * (size_t)T * c->ldvt);
+    e |= dmalloc(&c->colsum_v, sizeof(double) * T);
+    e |= dmalloc(&c->rowsum_v, sizeof(double) * N);
+    e |= dmalloc(&c->c, sizeof(double) * R);
+    e |= dmalloc(&c->sig, sizeof(double) * R);
+    e |= dmalloc(&c->Apart, sizeof(Tp) * (size_t)ap);
+    e |= dmalloc(&c->Bpart, sizeof(Tp) * (size_t)ap);
+    e |= dmalloc(&c->Xmu, sizeof(Tp) * (size_t)(R * M));
+    e |= dmalloc(&c->Xdna, sizeof(Tp) * (size_t)(R * M));
+    e |= dmalloc(&c->dpart, sizeof(double) * (size_t)dp);
+    e |= dmalloc(&c->dfin_h, sizeof(double) * 2 * T);
+    e |= dmalloc(&c->dfin_w, sizeof(double) * 2 * N);
+    e |= dmalloc(&c->choice_h, (size_t)T);
+    e |= dmalloc(&c->choice_w, (size_t)N);
+    e |= dmalloc(&c->kl_dev, sizeof(double));
+    e |= dmalloc(&c->status, sizeof(int));
+    if (e != DNA_OK) return DNA_ERR_ALLOC;
+    if (cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess) return DNA_ERR_CUDA;
+    if (cudaMemset(c->choice_h, 0, (size_t)T) != cudaSuccess) return DNA_ERR_CUDA;
+    if (cudaMemset(c->choice_w, 0, (size_t)N) != cudaSuccess) return DNA_ERR_CUDA;
+    if (cudaMemset(c->dfin_h, 0, sizeof(double) * 2 * T) != cudaSuccess) return DNA_ERR_CUDA;
+    if (cudaMemset(c->dfin_w, 0, sizeof(double) * 2 * N) != cudaSuccess) return DNA_ERR_CUDA;
+    return DNA_OK;
+}
+
+template <typename Tp>
+int prepare(dna_ctx* c) {
+    return phase(c, DNA_PHASE_PREPARE, 3, [&] {
+        return dna::Simt<Tp>::prepare_v(static_cast<const Tp*>(c->V), c->N, c->T, c->ldv,
+                                        static_cast<Tp*>(c->Vt), c->ldvt, c->colsum_v,
+                                        c->rowsum_v, c->stream);
+    });
+}
+
+// Steps 1/29 (which = 1) or 16 (which = 0).
+template <typename Tp>
+int normalize(dna_ctx* c, int which) {
+    using S = dna::Simt<Tp>;
+    const View v = make_view(c, which == 1);
+    const double reg = which == 1 ? c->o.lambda : c->o.rho;
+    return phase(c, DNA_PHASE_SUMS, 2, [&] {
+        int e = S::factor_sums_x(v, reg, c->sig, c->stream);
+        return e ? e : S::rescale(v, c->sig, c->stream);
+    });
+}
+
+// One half-step (wstep = 0: Algorithm 1 steps 4-16, wstep = 1: steps 17-29).
+// mu_only: the multiplicative update of eq. 11 instead of DNA.
+template <typename Tp>
+int half_step(dna_ctx* c, int wstep, bool mu_only) {
+    using S = dna::Simt<Tp>;
+    const View v = make_view(c, wstep == 1);
+    const double reg_den = wstep ? c->o.rho : c->o.lambda;   // eq. 7 / 14 denominators
+    Tp* A = static_cast<Tp*>(c->Apart);
+    Tp* B = static_cast<Tp*>(c->Bpart);
+    Tp* Xmu = static_cast<Tp*>(c->Xmu);
+    Tp* Xdna = static_cast<Tp*>(c->Xdna);
+    cudaStream_t st = c->stream;
+    int e = phase(c, DNA_PHASE_SUMS, 1, [&] { return S::factor_sums_y(v, reg_den, c->c, st); });
+    if (e) return e;
+    e = phase(c, DNA_PHASE_PASS1, 1, [&] {
+        return S::pass1(v, A, B, c->sp1[wstep], c->per1[wstep], !mu_only, c->status, st);
+    });
+    if (e) return e;
+    if (mu_only) {
+        e = phase(c, DNA_PHASE_CANDIDATES, 1,
+                  [&] { return S::mu_apply(v, c->c, A, c->sp1[wstep], st); });
+        if (e) return e;
+    } else {
+        e = phase(c, DNA_PHASE_CANDIDATES, 1, [&] {
+            return S::candidates(v, c->c, A, B, c->sp1[wstep], Xmu, Xdna, c->o.eps, c->o.alpha, st);
+        });
+        if (e) return e;
+        e = phase(c, DNA_PHASE_PASS2, 1, [&] {
+            return S::pass2(v, Xmu, Xdna, c->dpart, c->sp2[wstep], c->per2[wstep], c->status, st);
+        });
+        if (e) return e;
+        e = phase(c, DNA_PHASE_SELECT, 1, [&] {
+            return S::select(v, Xmu, Xdna, c->dpart, c->sp2[wstep],
+                             wstep ? c->choice_w : c->choice_h, wstep ? c->dfin_w : c->dfin_h, st);
+        });
+        if (e) return e;
+    }
+    return normalize<Tp>(c, wstep == 1 ? 1 : 0);
+}
+
+template <typename Tp>
+int kl_async(dna_ctx* c) {
+    const View v = make_view(c, false);
+    return phase(c, DNA_PHASE_KL, 2, [&] {
+        int e = dna::Simt<Tp>::kl_columns(v, c->dpart, c->sp2[0], c->per2[0], c->status, c->stream);
+        return e ? e : dna::reduce_sum(c->dpart, (int64_t)c->sp2[0] * c->T, c->kl_dev, c->stream);
+    });
+}
+
+int read_status(dna_ctx* c) {
+    int st = 0;
+    if (cudaMemcpyAsync(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream) !=
+        cudaSuccess)
+        return DNA_ERR_CUDA;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return DNA_ERR_CUDA;
+    if (st & dna::STATUS_NONFINITE) return DNA_ERR_NONFINITE;
+    if (st & dna::STATUS_TIMEOUT) return DNA_ERR_TIMEOUT;
+    return DNA_OK;
+}
+
+bool is_f64(const dna_ctx* c) { return c->o.dtype == DNA_F64; }
+
+int check_ready(const dna_ctx* c) {
+    if (!c) return DNA_ERR_ARG;
+    if (!c->bound) return DNA_ERR_ARG;
+    return DNA_OK;
+}
+
+int set_device(const dna_ctx* c) {
+    return cudaSetDevice(c->device) == cudaSuccess ? DNA_OK : DNA_ERR_CUDA;
+}
+
+// Run f (which queues nlaunch kernels) as one instance of phase ph, bracketed by an
+// event pair when profiling is on.
+template <class F>
+int phase(dna_ctx* c, int ph, int nlaunch, F&& f) {
+    size_t idx = SIZE_MAX;
+    if (c->prof_on && c->ev_used + 2 <= c->ev_pool.size()) {
+        idx = c->ev_used;
+        c->ev_used += 2;
+        if (cudaEventRecord(c->ev_pool[idx], c->stream) != cudaSuccess) return DNA_ERR_CUDA;
+    }
+    const int e = f();
+    if (idx != SIZE_MAX) {
+        if (cudaEventRecord(c->ev_pool[idx + 1], c->stream) != cudaSuccess) return DNA_ERR_CUDA;
+        c->ev_recs.emplace_back(ph, idx);
+    }
+    c->phase_launches[ph] += nlaunch;
+    return e;
+}
+
+}  // namespace
+
+namespace dna {
+
+__global__ void k_reduce_sum(const double* __restrict__ part, int64_t n, double* __restrict__ out) {
+    __shared__ double red[1024];
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += 1024) s += part[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 512; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0];
+}
+
+int reduce_sum(const double* part, int64_t n, double* out, cudaStream_t st) {
+    k_reduce_sum<<<1, 1024, 0, st>>>(part, n, out);
+    return cudaGetLastError() == cudaSuccess ? DNA_OK : DNA_ERR_CUDA;
+}
+
+}  // namespace dna
+
+extern "C" {
+
+void dna_default_opts(dna_opts* o) {
+    if (!o) return;
+    o->eps = 0.01;
+    o->alpha = 4.0;
+    o->rho = 0.0;
+    o->lambda = 0.0;
+    o->dtype = DNA_F32;
+    o->engine = DNA_ENGINE_AUTO;
+}
+
+const char* dna_strerror(int code) {
+    switch (code) {
+        case DNA_OK: return "ok";
+        case DNA_ERR_ARG: return "invalid argument";
+        case DNA_ERR_CUDA: return "CUDA runtime error";
+        case DNA_ERR_NONFINITE: return "non-positive z where v > 0 (infinite cost)";
+        case DNA_ERR_TIMEOUT: return "a bounded device-side wait timed out";
+        case DNA_ERR_UNSUPPORTED: return "not supported by this build";
+        case DNA_ERR_ALLOC: return "device allocation failed";
+        default: return "unknown status code";
+    }
+}
+
+int dna_create(int64_t N, int64_t T, int64_t R, const dna_opts* opts, dna_ctx** out) {
+    if (!out) return DNA_ERR_ARG;
+    *out = nullptr;
+    if (N < 1 || T < 1 || R < 1 || R > 512) return DNA_ERR_ARG;
+    if (N > (int64_t)1 << 31 || T > (int64_t)1 << 31) return DNA_ERR_ARG;
+    dna_opts o;
+    dna_default_opts(&o);
+    if (opts) o = *opts;
+    if (!valid_opts(o)) return DNA_ERR_ARG;
+    if (o.dtype == DNA_BF16 || o.engine == DNA_ENGINE_TENSOR) return DNA_ERR_UNSUPPORTED;
+    dna_ctx* c = new (std::nothrow) dna_ctx();
+    if (!c) return DNA_ERR_ALLOC;
+    c->N = N; c->T = T; c->R = R; c->o = o;
+    c->esz = o.dtype == DNA_F64 ? 8 : 4;
+    if (cudaGetDevice(&c->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return DNA_ERR_CUDA;
+    }
+    const int e = is_f64(c) ? alloc_workspace<double>(c) : alloc_workspace<float>(c);
+    if (e != DNA_OK) {
+        free_all(c);
+        delete c;
+        return e;
+    }
+    *out = c;
+    return DNA_OK;
+}
+
+int dna_bind(dna_ctx* c, const void* V, int64_t ldv, void* W, void* H) {
+    if (!c || !V || !W || !H || ldv < c->T) return DNA_ERR_ARG;
+    if (c->host_mode) return DNA_ERR_ARG;
+    if (set_device(c)) return DNA_ERR_CUDA;
+    c->V = V; c->ldv = ldv; c->W = W; c->H = H;
+    c->bound = true;
+    return is_f64(c) ? prepare<double>(c) : prepare<float>(c);
+}
+
+int dna_set_stream(dna_ctx* c, void* stream) {
+    if (!c) return DNA_ERR_ARG;
+    c->stream = static_cast<cudaStream_t>(stream);
+    return DNA_OK;
+}
+
+int dna_normalize(dna_ctx* c, int which) {
+    if (int e = check_ready(c)) return e;
+    if (which != 0 && which != 1) return DNA_ERR_ARG;
+    if (set_device(c)) return DNA_ERR_CUDA;
+    return is_f64(c) ? normalize<double>(c, which) : normalize<float>(c, which);
+}
+
+int dna_step_H(dna_ctx* c) {
+    if (int e = check_ready(c)) return e;
+    if (set_device(c)) return DNA_ERR_CUDA;
+    return is_f64(c) ? half_step<double>(c, 0, false) : half_step<float>(c, 0, false);
+}
+
+int dna_step_W(dna_ctx* c) {
+    if (int e = check_ready(c)) return e;
+    if (set_device(c)) return DNA_ERR_CUDA;
+    return is_f64(c) ? half_step<double>(c, 1, false) : half_step<float>(c, 1, false);
+}
+
+int dna_iterate(dna_ctx* c, int iters) {
+    if (int e = check_ready(c)) return e;
+    if (iters < 0) return DNA_ERR_ARG;
+    for (int i = 0; i < iters; ++i) {
+        if (int e = dna_step_H(c)) return e;
+        if (int e = dna_step_W(c)) return e;
+    }
+    return DNA_OK;
+}
+
+int mu_step(dna_ctx* c, int which) {
+    if (int e = check_ready(c)) return e;
+    if (which != 0 && which != 1) return DNA_ERR_ARG;
+    if (set_device(c)) return DNA_ERR_CUDA;
+    return is_f64(c) ? half_step<double>(c, which, true) : half_step<float>(c, which, true);
+}
+
+int dna_kl(dna_ctx* c, double* out) {
+    if (int e = check_ready(c)) return e;
+    if (!out) return DNA_ERR_ARG;
+    if (set_device(c)) return DNA_ERR_CUDA;
+    int e = is_f64(c) ? kl_async<double>(c) : kl_async<float>(c);
+    if (e) return e;
+    if (cudaMemcpyAsync(out, c->kl_dev, sizeof(double), cudaMemcpyDeviceToHost, c->stream) !=
+        cudaSuccess)
+        return DNA_ERR_CUDA;
+    return read_status(c);
+}
+
+int dna_get_choice(dna_ctx* c, int which, uint8_t* out, int64_t len) {
+    if (int e = check_ready(c)) return e;
+    if (!out || (which != 0 && which != 1) || len != (which ? c->N : c->T)) return DNA_ERR_ARG;
+    if (set_device(c)) return DNA_ERR_CUDA;
+    if (cudaMemcpyAsync(out, which ? c->choice_w : c->choice_h, (size_t)len, cudaMemcpyDeviceToHost,
+                        c->stream) != cudaSuccess)
+        return DNA_ERR_CUDA;
+    return read_status(c);
+}
+
+int dna_get_costs(dna_ctx* c, int which, double* d_mu, double* d_dna, int64_t len) {
+    if (int e = check_ready(c)) return e;
+    if (!d_mu || !d_dna || (which != 0 && which != 1) || len != (which ? c->N : c->T))
+        return DNA_ERR_ARG;
+    if (set_device(c)) return DNA_ERR_CUDA;
+    const double* src = which ? c->dfin_w : c->dfin_h;
+    if (cudaMemcpyAsync(d_mu, src, sizeof(double) * len, cudaMemcpyDeviceToHost, c->stream) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(d_dna, src + len, sizeof(double) * len, cudaMemcpyDeviceToHost, c->stream) !=
+            cudaSuccess)
+        return DNA_ERR_CUDA;
+    return read_status(c);
+}
+
+int dna_get_status(dna_ctx* c) {
+    if (!c) return DNA_ERR_ARG;
+    if (set_device(c)) return DNA_ERR_CUDA;
+    return read_status(c);
+}
+
+int dna_run_host(dna_ctx* c, const void* V, void* W, void* H, int iters, double* kl_out) {
+    if (!c || !V || !W || !H || iters < 0) return DNA_ERR_ARG;
+    if (c->bound && !c->host_mode) return DNA_ERR_ARG;
+    if (set_device(c)) return DNA_ERR_CUDA;
+    const size_t es = c->esz;
+    const size_t bv = es * (size_t)(c->N * c->T), bw = es * (size_t)(c->N * c->R),
+                 bh = es * (size_t)(c->R * c->T);
+    if (!c->host_mode) {
+        int e = DNA_OK;
+        e |= dmalloc(&c->own_V, bv);
+        e |= dmalloc(&c->own_W, bw);
+        e |= dmalloc(&c->own_H, bh);
+        if (e) return DNA_ERR_ALLOC;
+        c->host_mode = true;
+        c->V = c->own_V; c->ldv = c->T; c->W = c->own_W; c->H = c->own_H;
+        c->bound = true;
+    }
+    cudaStream_t st = c->stream;
+    if (cudaMemcpyAsync(c->own_V, V, bv, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(c->own_W, W, bw, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(c->own_H, H, bh, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return DNA_ERR_CUDA;
+    int e = is_f64(c) ? prepare<double>(c) : prepare<float>(c);
+    if (e) return e;
+    if ((e = dna_iterate(c, iters))) return e;
+    double kl = 0.0;
+    if ((e = is_f64(c) ? kl_async<double>(c) : kl_async<float>(c))) return e;
+    if (cudaMemcpyAsync(W, c->own_W, bw, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(H, c->own_H, bh, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(&kl, c->kl_dev, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return DNA_ERR_CUDA;
+    e = read_status(c);
+    if (kl_out) *kl_out = kl;
+    return e;
+}
+
+int dna_profile(dna_ctx* c, int enable) {
+    if (!c) return DNA_ERR_ARG;
+    if (set_device(c)) return DNA_ERR_CUDA;
+    if (enable && c->ev_pool.empty()) {
+        c->ev_pool.resize(2 * 16384, nullptr);
+        for (auto& ev : c->ev_pool)
+            if (cudaEventCreate(&ev) != cudaSuccess) return DNA_ERR_CUDA;
+    }
+    c->prof_on = enable != 0;
+    return DNA_OK;
+}
+
+int dna_phase_times(dna_ctx* c, double* ms, int64_t* launches, int n) {
+    if (!c || n < 0 || n > DNA_NUM_PHASES) return DNA_ERR_ARG;
+    if (set_device(c)) return DNA_ERR_CUDA;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return DNA_ERR_CUDA;
+    for (const auto& rec : c->ev_recs) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, c->ev_pool[rec.second], c->ev_pool[rec.second + 1]) !=
+            cudaSuccess)
+            return DNA_ERR_CUDA;
+        c->phase_ms[rec.first] += t;
+    }
+    c->ev_recs.clear();
+    c->ev_used = 0;
+    for (int i = 0; i < n; ++i) {
+        if (ms) ms[i] = c->phase_ms[i];
+        if (launches) launches[i] = c->phase_launches[i];
+    }
+    for (int i = 0; i < DNA_NUM_PHASES; ++i) {
+        c->phase_ms[i] = 0.0;
+        c->phase_launches[i] = 0;
+    }
+    return DNA_OK;
+}
+
+void dna_destroy(dna_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    free_all(c);
+    delete c;
+}
+
+}  // extern "C"

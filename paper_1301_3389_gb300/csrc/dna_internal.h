@@ -1,0 +1,71 @@
+// Internal interfaces of the DNA library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dna.h"
+
+namespace dna {
+
+// Device status bits (sticky, OR-ed by kernels, read by synchronising calls).
+enum : int { STATUS_NONFINITE = 1, STATUS_TIMEOUT = 2 };
+
+// One half-step seen as "update the owned factor X (R x O) with the fixed factor
+// Y (S x R)", reducing over s (Section 2: the W half-step is the H half-step on the
+// transposes).  H-step: s = n, o = t, X = H, Y = W, V_so = V.  W-step: s = t, o = n,
+// X = W^t, Y = H^t, V_so = V^t (the transposed copy made at bind time).
+struct View {
+    int64_t S, O, R;
+    const void* V;      // V_so, element (s, o) at V[s * vs + o]
+    int64_t vs;
+    void* X;            // element (r, o) at X[r * xr + o * xo]
+    int64_t xr, xo;
+    const void* Y;      // element (s, r) at Y[s * ys + r * yr]
+    int64_t ys, yr;
+    const double* vsum; // sum_s v(s, o), length O (the eq. 10 target)
+};
+
+// Launchers, one instantiation per element type (float, double).  Each returns a
+// DNA_* status (launch errors only; device-side errors go to *status).
+template <typename Tp> struct Simt {
+    // sum over s of y(s, r) + reg -> out[r] (the eq. 7 / 14 denominators)
+    static int factor_sums_y(const View& v, double reg, double* out, cudaStream_t st);
+    // sum over o of x(r, o) + reg -> out[r] (the step 16 / 29 normalisers)
+    static int factor_sums_x(const View& v, double reg, double* out, cudaStream_t st);
+    // x(r, o) *= f_r^-1 ... : X scaled by 1/f_r, Y scaled by f_r (steps 1, 16, 29)
+    static int rescale(const View& v, const double* f, cudaStream_t st);
+    // pass 1: raw sums Apart = sum_s y q, Bpart = sum_s y^2 qbar (split over s)
+    static int pass1(const View& v, Tp* Apart, Tp* Bpart, int splits, int64_t s_per,
+                     bool with_b, int* status, cudaStream_t st);
+    // candidates: MU and renormalised Newton candidates, laid out [R][O]
+    static int candidates(const View& v, const double* c, const Tp* Apart, const Tp* Bpart,
+                          int splits, Tp* Xmu, Tp* Xdna, double eps, double alpha,
+                          cudaStream_t st);
+    // MU update in place (eq. 11): x <- x * raw_a / c
+    static int mu_apply(const View& v, const double* c, const Tp* Apart, int splits,
+                        cudaStream_t st);
+    // pass 2: per-column costs of the two candidates, float64 partials [splits][2][O]
+    static int pass2(const View& v, const Tp* Xmu, const Tp* Xdna, double* dpart, int splits,
+                     int64_t s_per, int* status, cudaStream_t st);
+    // selection: x(r, o) <- Newton if d_dna < d_mu else MU; choice and final costs
+    static int select(const View& v, const Tp* Xmu, const Tp* Xdna, const double* dpart,
+                      int splits, uint8_t* choice, double* dfin, cudaStream_t st);
+    // per-column full KL terms of eq. 1 for x = the view's X, partials [splits][O]
+    static int kl_columns(const View& v, double* dpart, int splits, int64_t s_per,
+                          int* status, cudaStream_t st);
+    // one-time: row and column sums of V (float64) and the transposed copy
+    static int prepare_v(const Tp* V, int64_t N, int64_t T, int64_t ldv, Tp* Vt, int64_t ldvt,
+                         double* colsum, double* rowsum, cudaStream_t st);
+    // how many CTAs of pass 1 / pass 2 fit on one SM
+    static int pass1_blocks_per_sm(int64_t R);
+    static int pass2_blocks_per_sm(int64_t R);
+    static int chunk();   // the s-chunk of passes 1 and 2 (splits are multiples of it)
+    static int oblock();  // the o-block of passes 1 and 2
+    static int rblock(int64_t R);  // the r-block of pass 1
+};
+
+// sum of dpart[0 .. n) in a fixed order into *out (float64)
+int reduce_sum(const double* part, int64_t n, double* out, cudaStream_t st);
+
+}  // namespace dna

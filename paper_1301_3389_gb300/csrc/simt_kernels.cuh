@@ -1,0 +1,452 @@
+// CUDA-core (SIMT) kernels of the DNA half-step, templated on the element type.
+//
+// One half-step, in the (s, o, r) terms of dna::View, Algorithm 1 steps 2-15:
+//   z(s,o) = sum_r y(s,r) x(r,o)                                   (step 2 / 7 / 12)
+//   q = v / z, qbar = v / z^2 (0 where v = 0)                      (step 3, 10)
+//   A(r,o) = sum_s y(s,r) q(s,o),  B(r,o) = sum_s y(s,r)^2 qbar(s,o)   (steps 5, 10)
+//   candidates per (r, o) (steps 6, 11), per-column costs (steps 9, 14), selection
+//   (step 15).
+// Pass 1 never writes Z or Q to memory: each CTA owns a block of o and streams s in
+// chunks, computing the z tile in registers, q and qbar into shared memory, and
+// accumulating A and B for its r-block in registers (the structure of a fused
+// back-to-back GEMM).  Pass 2 recomputes z for both candidates the same way and reduces
+// the cost terms per column.  The reduction over s may be split across CTAs (grid z);
+// partial sums are combined later in a fixed order, so results are deterministic.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "dna_internal.h"
+
+namespace dna {
+namespace simt {
+
+constexpr int NT = 256;   // threads per CTA in passes 1 and 2
+constexpr int OB = 64;    // o-block
+constexpr int SB = 64;    // s-chunk
+constexpr int LD = 68;    // padded leading dimension of the [*][64] shared tiles
+
+__device__ __forceinline__ void ld4(const float* p, float (&v)[4]) {
+    float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&v)[4]) {
+    double2 a = *reinterpret_cast<const double2*>(p);
+    double2 b = *reinterpret_cast<const double2*>(p + 2);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ float dev_log(float x) { return logf(x); }
+__device__ __forceinline__ double dev_log(double x) { return log(x); }
+
+// Load a ROWS x COLS tile into shared memory (leading dimension LD):
+//   sm[i][j] = g[(i0 + i) * si + (j0 + j) * sj] when i0 + i < ni and j0 + j < nj, else 0.
+// Consecutive threads walk the unit-stride global dimension so that reads coalesce.
+template <typename Tp, int ROWS, int COLS>
+__device__ __forceinline__ void load_tile(Tp* __restrict__ sm, const Tp* __restrict__ g,
+                                          int64_t si, int64_t sj, int64_t i0, int64_t j0,
+                                          int64_t ni, int64_t nj) {
+    if (sj == 1) {
+        for (int e = threadIdx.x; e < ROWS * COLS; e += NT) {
+            const int i = e / COLS, j = e % COLS;
+            const int64_t gi = i0 + i, gj = j0 + j;
+            sm[i * LD + j] = (gi < ni && gj < nj) ? __ldg(g + gi * si + gj) : Tp(0);
+        }
+    } else {
+        for (int e = threadIdx.x; e < ROWS * COLS; e += NT) {
+            const int j = e / ROWS, i = e % ROWS;
+            const int64_t gi = i0 + i, gj = j0 + j;
+            sm[i * LD + j] = (gi < ni && gj < nj) ? __ldg(g + gi * si + gj * sj) : Tp(0);
+        }
+    }
+}
+
+// Accumulate the 4 x 4 register tile z[s][o] += sum_{r < RB} Yt[r][zs + s] * Xs[r][zo + o].
+template <typename Tp, int RB>
+__device__ __forceinline__ void z_tile(const Tp* __restrict__ Yt, const Tp* __restrict__ Xs,
+                                       int zs, int zo, Tp (&z)[4][4]) {
+#pragma unroll 4
+    for (int r = 0; r < RB; ++r) {
+        Tp xa[4], ya[4];
+        ld4(Xs + r * LD + zo, xa);
+        ld4(Yt + r * LD + zs, ya);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) z[i][j] = fma(ya[i], xa[j], z[i][j]);
+    }
+}
+
+template <typename Tp, int RB>
+struct Pass1Cfg {
+    static constexpr int RPT = RB / 16;  // r rows per thread in the A/B accumulators
+    static constexpr size_t smem = (size_t)(2 * RB * LD + 2 * SB * LD) * sizeof(Tp);
+};
+
+// Pass 1: raw A and B sums for one (o-block, r-block, s-split).
+// grid = (ceil(O / OB), ceil(R / RB), splits); Apart/Bpart are [splits][R][O].
+template <typename Tp, int RB, bool WITH_B>
+__global__ void __launch_bounds__(NT) k_pass1(View v, Tp* __restrict__ Apart,
+                                              Tp* __restrict__ Bpart, int64_t s_per,
+                                              int* __restrict__ status) {
+    using C = Pass1Cfg<Tp, RB>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Tp* Xs = reinterpret_cast<Tp*>(smem_raw);  // [RB][LD]  x(r, o) of the current r-piece
+    Tp* Yt = Xs + RB * LD;                     // [RB][LD]  y(s, r) transposed: Yt[r][s]
+    Tp* Qs = Yt + RB * LD;                     // [SB][LD]  q(s, o)
+    Tp* Qb = Qs + SB * LD;                     // [SB][LD]  qbar(s, o)
+
+    const Tp* __restrict__ V = static_cast<const Tp*>(v.V);
+    const Tp* __restrict__ X = static_cast<const Tp*>(v.X);
+    const Tp* __restrict__ Y = static_cast<const Tp*>(v.Y);
+    const int tid = threadIdx.x;
+    const int64_t o0 = (int64_t)blockIdx.x * OB;
+    const int64_t rown0 = (int64_t)blockIdx.y * RB;
+    const int64_t s_begin = (int64_t)blockIdx.z * s_per;
+    const int64_t s_end = min(v.S, s_begin + s_per);
+    const int npieces = (int)((v.R + RB - 1) / RB);
+
+    const int zo = (tid % 16) * 4, zs = (tid / 16) * 4;  // z tile of this thread
+    const int go = (tid % 16) * 4, gr = tid / 16;        // A/B rows gr + 16 i
+
+    Tp accA[C::RPT][4], accB[C::RPT][4];
+#pragma unroll
+    for (int i = 0; i < C::RPT; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) { accA[i][j] = Tp(0); accB[i][j] = Tp(0); }
+
+    if (npieces == 1) load_tile<Tp, RB, OB>(Xs, X, v.xr, v.xo, 0, o0, v.R, v.O);
+    int bad = 0;
+
+    for (int64_t s0 = s_begin; s0 < s_end; s0 += SB) {
+        Tp z[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) z[i][j] = Tp(0);
+        for (int p = 0; p < npieces; ++p) {
+            if (npieces > 1) load_tile<Tp, RB, OB>(Xs, X, v.xr, v.xo, (int64_t)p * RB, o0, v.R, v.O);
+            load_tile<Tp, RB, SB>(Yt, Y, v.yr, v.ys, (int64_t)p * RB, s0, v.R, v.S);
+            __syncthreads();
+            z_tile<Tp, RB>(Yt, Xs, zs, zo, z);
+            __syncthreads();
+        }
+        // q = v / z and qbar = v / z^2, zero where v = 0 (note after Algorithm 1)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int64_t s = s0 + zs + i;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int64_t o = o0 + zo + j;
+                const Tp vv = (s < s_end && o < v.O) ? __ldg(V + s * v.vs + o) : Tp(0);
+                Tp q = Tp(0), qb = Tp(0);
+                if (vv > Tp(0)) {
+                    const Tp zz = z[i][j];
+                    if (zz > Tp(0)) { q = vv / zz; qb = q / zz; } else { bad = 1; }
+                }
+                Qs[(zs + i) * LD + zo + j] = q;
+                Qb[(zs + i) * LD + zo + j] = qb;
+            }
+        }
+        if (npieces > 1)
+            load_tile<Tp, RB, SB>(Yt, Y, v.yr, v.ys, rown0, s0, v.R, v.S);
+        __syncthreads();
+        // A += Y^t Q and B += (Y o Y)^t Qbar over this chunk
+#pragma unroll 2
+        for (int s = 0; s < SB; ++s) {
+            Tp qv[4], qbv[4];
+            ld4(Qs + s * LD + go, qv);
+            if (WITH_B) ld4(Qb + s * LD + go, qbv);
+#pragma unroll
+            for (int i = 0; i < C::RPT; ++i) {
+                const Tp y = Yt[(gr + 16 * i) * LD + s];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) accA[i][j] = fma(y, qv[j], accA[i][j]);
+                if (WITH_B) {
+                    const Tp y2 = y * y;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) accB[i][j] = fma(y2, qbv[j], accB[i][j]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (bad) atomicOr(status, STATUS_NONFINITE);
+
+    const int64_t base = (int64_t)blockIdx.z * v.R;
+#pragma unroll
+    for (int i = 0; i < C::RPT; ++i) {
+        const int64_t r = rown0 + gr + 16 * i;
+        if (r >= v.R) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t o = o0 + go + j;
+            if (o < v.O) {
+                Apart[(base + r) * v.O + o] = accA[i][j];
+                if (WITH_B) Bpart[(base + r) * v.O + o] = accB[i][j];
+            }
+        }
+    }
+}
+
+template <typename Tp, int RB, int NC>
+struct Pass2Cfg {
+    static constexpr size_t tiles = (size_t)((NC + 1) * RB * LD) * sizeof(Tp);
+    static constexpr size_t red = (size_t)16 * NC * OB * sizeof(double);
+    static constexpr size_t smem = tiles > red ? tiles : red;
+};
+
+// Pass 2: per-column cost partials for NC candidates (Algorithm 1 steps 7-9, 12-14).
+// FULL = false: d'(o) = sum_{v>0} (-v log z) + sum z (the candidate comparison).
+// FULL = true:  sum_{v>0} v log(v / z) - sum v + sum z (eq. 1, for dna_kl).
+// X_c(r, o) at Xc[r * xr + o * xo].  dpart is [splits][NC][O] float64.
+template <typename Tp, int RB, int NC, bool FULL>
+__global__ void __launch_bounds__(NT) k_pass2(View v, const Tp* __restrict__ X0,
+                                              const Tp* __restrict__ X1, int64_t xr, int64_t xo,
+                                              double* __restrict__ dpart, int64_t s_per,
+                                              int* __restrict__ status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Tp* Yt = reinterpret_cast<Tp*>(smem_raw);  // [RB][LD]
+    Tp* Xs = Yt + RB * LD;                     // [NC][RB][LD]
+    const Tp* __restrict__ V = static_cast<const Tp*>(v.V);
+    const Tp* __restrict__ Y = static_cast<const Tp*>(v.Y);
+    const int tid = threadIdx.x;
+    const int64_t o0 = (int64_t)blockIdx.x * OB;
+    const int64_t s_begin = (int64_t)blockIdx.y * s_per;
+    const int64_t s_end = min(v.S, s_begin + s_per);
+    const int npieces = (int)((v.R + RB - 1) / RB);
+    const int zo = (tid % 16) * 4, zs = (tid / 16) * 4;
+
+    double dacc[NC][4];
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) dacc[c][j] = 0.0;
+
+    if (npieces == 1) {
+        load_tile<Tp, RB, OB>(Xs, X0, xr, xo, 0, o0, v.R, v.O);
+        if (NC > 1) load_tile<Tp, RB, OB>(Xs + RB * LD, X1, xr, xo, 0, o0, v.R, v.O);
+    }
+    int bad = 0;
+    for (int64_t s0 = s_begin; s0 < s_end; s0 += SB) {
+        Tp z[NC][4][4];
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) z[c][i][j] = Tp(0);
+        for (int p = 0; p < npieces; ++p) {
+            if (npieces > 1) {
+                load_tile<Tp, RB, OB>(Xs, X0, xr, xo, (int64_t)p * RB, o0, v.R, v.O);
+                if (NC > 1)
+                    load_tile<Tp, RB, OB>(Xs + RB * LD, X1, xr, xo, (int64_t)p * RB, o0, v.R, v.O);
+            }
+            load_tile<Tp, RB, SB>(Yt, Y, v.yr, v.ys, (int64_t)p * RB, s0, v.R, v.S);
+            __syncthreads();
+#pragma unroll
+            for (int c = 0; c < NC; ++c) z_tile<Tp, RB>(Yt, Xs + c * RB * LD, zs, zo, z[c]);
+            __syncthreads();
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t o = o0 + zo + j;
+            Tp run[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) run[c] = Tp(0);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int64_t s = s0 + zs + i;
+                const Tp vv = (s < s_end && o < v.O) ? __ldg(V + s * v.vs + o) : Tp(0);
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    const Tp zz = z[c][i][j];
+                    Tp term = zz;
+                    if (vv > Tp(0)) {
+                        if (zz > Tp(0)) {
+                            term += FULL ? (vv * dev_log(vv / zz) - vv) : (-vv * dev_log(zz));
+                        } else {
+                            bad = 1;
+                        }
+                    }
+                    run[c] += term;
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < NC; ++c) dacc[c][j] += (double)run[c];
+        }
+    }
+    if (bad) atomicOr(status, STATUS_NONFINITE);
+
+    // reduce the 16 threads that share each o (they differ in zs)
+    __syncthreads();
+    double* red = reinterpret_cast<double*>(smem_raw);  // [16][NC][OB]
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) red[((tid / 16) * NC + c) * OB + zo + j] = dacc[c][j];
+    __syncthreads();
+    if (tid < NC * OB) {
+        const int c = tid / OB, oo = tid % OB;
+        double sum = 0.0;
+        for (int k = 0; k < 16; ++k) sum += red[(k * NC + c) * OB + oo];
+        const int64_t o = o0 + oo;
+        if (o < v.O) dpart[((int64_t)blockIdx.y * NC + c) * v.O + o] = sum;
+    }
+}
+
+// Candidates (steps 6 and 11, eq. 10, 11, 15, 17), one thread per o.
+template <typename Tp>
+__global__ void k_candidates(View v, const double* __restrict__ c, const Tp* __restrict__ Apart,
+                             const Tp* __restrict__ Bpart, int splits, Tp* __restrict__ Xmu,
+                             Tp* __restrict__ Xdna, Tp eps, Tp alpha) {
+    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= v.O) return;
+    const Tp* __restrict__ X = static_cast<const Tp*>(v.X);
+    double den = 0.0;
+    for (int64_t r = 0; r < v.R; ++r) {
+        Tp ra = Tp(0), rb = Tp(0);
+        for (int sp = 0; sp < splits; ++sp) {
+            ra += Apart[((int64_t)sp * v.R + r) * v.O + o];
+            rb += Bpart[((int64_t)sp * v.R + r) * v.O + o];
+        }
+        const Tp cr = (Tp)c[r];
+        const Tp a = ra / cr - Tp(1);         // eq. 7
+        const Tp b = rb / cr;                 // eq. 14
+        const Tp x = X[r * v.xr + o * v.xo];
+        const Tp xmu = x + a * x;             // eq. 11 (step 6)
+        Tp xd;
+        if (a < Tp(0)) {                      // eq. 15 with the eps floor on the gain
+            const Tp xb = x * b;
+            const Tp g = xb / (xb - a);
+            xd = x * (g > eps ? g : eps);
+        } else {                              // eq. 17, gain capped at 1 + alpha
+            const Tp st = b > Tp(0) ? a / b : Tp(0);
+            const Tp cap = alpha * x;
+            xd = x + (st < cap ? st : cap);
+        }
+        Xmu[r * v.O + o] = xmu;
+        Xdna[r * v.O + o] = xd;
+        den += c[r] * (double)xd;
+    }
+    const double sc = den > 0.0 ? v.vsum[o] / den : 1.0;  // eq. 10
+    for (int64_t r = 0; r < v.R; ++r) Xdna[r * v.O + o] = (Tp)((double)Xdna[r * v.O + o] * sc);
+}
+
+// MU in place (eq. 11): x(r, o) <- x(r, o) * raw_a(r, o) / c_r.
+template <typename Tp>
+__global__ void k_mu_apply(View v, const double* __restrict__ c, const Tp* __restrict__ Apart,
+                           int splits) {
+    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= v.O) return;
+    Tp* __restrict__ X = static_cast<Tp*>(v.X);
+    for (int64_t r = 0; r < v.R; ++r) {
+        Tp ra = Tp(0);
+        for (int sp = 0; sp < splits; ++sp) ra += Apart[((int64_t)sp * v.R + r) * v.O + o];
+        X[r * v.xr + o * v.xo] = X[r * v.xr + o * v.xo] * (ra / (Tp)c[r]);
+    }
+}
+
+// Selection (step 15 / 28): keep the Newton candidate iff d_dna < d_mu (ties keep MU).
+template <typename Tp>
+__global__ void k_select(View v, const Tp* __restrict__ Xmu, const Tp* __restrict__ Xdna,
+                         const double* __restrict__ dpart, int splits,
+                         uint8_t* __restrict__ choice, double* __restrict__ dfin) {
+    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= v.O) return;
+    double dm = 0.0, dd = 0.0;
+    for (int sp = 0; sp < splits; ++sp) {
+        dm += dpart[((int64_t)sp * 2 + 0) * v.O + o];
+        dd += dpart[((int64_t)sp * 2 + 1) * v.O + o];
+    }
+    const bool newton = dd < dm;
+    choice[o] = newton ? 1 : 0;
+    dfin[o] = dm;
+    dfin[v.O + o] = dd;
+    Tp* __restrict__ X = static_cast<Tp*>(v.X);
+    const Tp* __restrict__ src = newton ? Xdna : Xmu;
+    for (int64_t r = 0; r < v.R; ++r) X[r * v.xr + o * v.xo] = src[r * v.O + o];
+}
+
+// out[r] = sum_i M(i, r) + reg for a matrix with element (i, r) at M[i * si + r * sr],
+// i < n.  One CTA of 32 x 8 threads per 32 values of r; fixed summation order.
+template <typename Tp>
+__global__ void k_factor_sums(const Tp* __restrict__ M, int64_t n, int64_t R, int64_t si,
+                              int64_t sr, double reg, double* __restrict__ out) {
+    __shared__ double red[8][33];
+    const int lane = threadIdx.x, ty = threadIdx.y;
+    const int64_t r = (int64_t)blockIdx.x * 32 + lane;
+    double s = 0.0;
+    if (r < R)
+        for (int64_t i = ty; i < n; i += 8) s += (double)M[i * si + r * sr];
+    red[ty][lane] = s;
+    __syncthreads();
+    if (ty == 0 && r < R) {
+        double t = 0.0;
+        for (int k = 0; k < 8; ++k) t += red[k][lane];
+        out[r] = t + reg;
+    }
+}
+
+// Row-sum variant for unit-stride rows (element (r, i) at M[r * ld + i]): one CTA per r.
+template <typename Tp>
+__global__ void k_row_sums(const Tp* __restrict__ M, int64_t n, int64_t ld, double reg,
+                           double* __restrict__ out) {
+    __shared__ double red[256];
+    const int64_t r = blockIdx.x;
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += 256) s += (double)M[r * ld + i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[r] = red[0] + reg;
+}
+
+// X(r, o) /= f_r for all (r, o); Y(s, r) *= f_r for all (s, r).  Thread per element of
+// the underlying dense buffers (X: R*O, Y: S*R), decoded through the strides.
+template <typename Tp>
+__global__ void k_rescale(View v, const double* __restrict__ f) {
+    const int64_t nx = v.R * v.O, ny = v.S * v.R;
+    Tp* __restrict__ X = static_cast<Tp*>(v.X);
+    Tp* __restrict__ Y = const_cast<Tp*>(static_cast<const Tp*>(v.Y));
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nx + ny;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        if (e < nx) {
+            // X dense in memory: the unit stride is xo (H) or xr (W^t)
+            int64_t r, o;
+            if (v.xo == 1) { r = e / v.O; o = e % v.O; } else { o = e / v.R; r = e % v.R; }
+            const int64_t idx = r * v.xr + o * v.xo;
+            X[idx] = (Tp)((double)X[idx] / f[r]);
+        } else {
+            const int64_t k = e - nx;
+            int64_t s, r;
+            if (v.yr == 1) { s = k / v.R; r = k % v.R; } else { r = k / v.S; s = k % v.S; }
+            const int64_t idx = s * v.ys + r * v.yr;
+            Y[idx] = (Tp)((double)Y[idx] * f[r]);
+        }
+    }
+}
+
+// Vt[t][n] = V[n][t] (32 x 32 tiles).
+template <typename Tp>
+__global__ void k_transpose(const Tp* __restrict__ V, int64_t N, int64_t T, int64_t ldv,
+                            Tp* __restrict__ Vt, int64_t ldvt) {
+    __shared__ Tp tile[32][33];
+    const int64_t n0 = (int64_t)blockIdx.y * 32, t0 = (int64_t)blockIdx.x * 32;
+    for (int k = threadIdx.y; k < 32; k += 8) {
+        const int64_t n = n0 + k, t = t0 + threadIdx.x;
+        tile[k][threadIdx.x] = (n < N && t < T) ? V[n * ldv + t] : Tp(0);
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += 8) {
+        const int64_t t = t0 + k, n = n0 + threadIdx.x;
+        if (t < T && n < N) Vt[t * ldvt + n] = tile[threadIdx.x][k];
+    }
+}
+
+}  // namespace simt
+}  // namespace dna

@@ -1,0 +1,218 @@
+// Host launchers for the SIMT kernels (instantiated for float and double).
+#pragma once
+
+#include "simt_kernels.cuh"
+
+namespace dna {
+
+namespace simt {
+
+template <typename Tp> constexpr int rblock_for(int64_t R) {
+    return sizeof(Tp) == 4 ? (R <= 32 ? 32 : (R <= 64 ? 64 : 128)) : (R <= 32 ? 32 : 64);
+}
+
+inline int launch_status() {
+    return cudaGetLastError() == cudaSuccess ? DNA_OK : DNA_ERR_CUDA;
+}
+
+template <typename Kern>
+inline int prep_smem(Kern k, size_t bytes) {
+    static_assert(sizeof(Kern) > 0, "");
+    if (bytes > 48 * 1024) {
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+            cudaSuccess)
+            return DNA_ERR_CUDA;
+    }
+    return DNA_OK;
+}
+
+template <typename Tp, int RB>
+int pass1_rb(const View& v, Tp* A, Tp* B, int splits, int64_t s_per, bool with_b, int* status,
+             cudaStream_t st) {
+    const size_t smem = Pass1Cfg<Tp, RB>::smem;
+    dim3 grid((unsigned)((v.O + OB - 1) / OB), (unsigned)((v.R + RB - 1) / RB), (unsigned)splits);
+    if (with_b) {
+        auto k = k_pass1<Tp, RB, true>;
+        if (prep_smem(k, smem)) return DNA_ERR_CUDA;
+        k<<<grid, NT, smem, st>>>(v, A, B, s_per, status);
+    } else {
+        auto k = k_pass1<Tp, RB, false>;
+        if (prep_smem(k, smem)) return DNA_ERR_CUDA;
+        k<<<grid, NT, smem, st>>>(v, A, B, s_per, status);
+    }
+    return launch_status();
+}
+
+template <typename Tp, int RB, int NC, bool FULL>
+int pass2_rb(const View& v, const Tp* X0, const Tp* X1, int64_t xr, int64_t xo, double* dpart,
+             int splits, int64_t s_per, int* status, cudaStream_t st) {
+    const size_t smem = Pass2Cfg<Tp, RB, NC>::smem;
+    auto k = k_pass2<Tp, RB, NC, FULL>;
+    if (prep_smem(k, smem)) return DNA_ERR_CUDA;
+    dim3 grid((unsigned)((v.O + OB - 1) / OB), (unsigned)splits);
+    k<<<grid, NT, smem, st>>>(v, X0, X1, xr, xo, dpart, s_per, status);
+    return launch_status();
+}
+
+template <typename Tp, int NC, bool FULL>
+int pass2_any(const View& v, const Tp* X0, const Tp* X1, int64_t xr, int64_t xo, double* dpart,
+              int splits, int64_t s_per, int* status, cudaStream_t st) {
+    switch (rblock_for<Tp>(v.R)) {
+        case 32: return pass2_rb<Tp, 32, NC, FULL>(v, X0, X1, xr, xo, dpart, splits, s_per, status, st);
+        case 64: return pass2_rb<Tp, 64, NC, FULL>(v, X0, X1, xr, xo, dpart, splits, s_per, status, st);
+        default:
+            if constexpr (sizeof(Tp) == 4)
+                return pass2_rb<Tp, 128, NC, FULL>(v, X0, X1, xr, xo, dpart, splits, s_per, status, st);
+            return DNA_ERR_UNSUPPORTED;
+    }
+}
+
+template <typename Tp, int RB>
+int occupancy_pass1() {
+    int nb = 0;
+    auto k = k_pass1<Tp, RB, true>;
+    if (prep_smem(k, Pass1Cfg<Tp, RB>::smem)) return 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, NT, Pass1Cfg<Tp, RB>::smem) !=
+        cudaSuccess)
+        return 1;
+    return nb > 0 ? nb : 1;
+}
+
+template <typename Tp, int RB>
+int occupancy_pass2() {
+    int nb = 0;
+    auto k = k_pass2<Tp, RB, 2, false>;
+    if (prep_smem(k, Pass2Cfg<Tp, RB, 2>::smem)) return 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, NT, Pass2Cfg<Tp, RB, 2>::smem) !=
+        cudaSuccess)
+        return 1;
+    return nb > 0 ? nb : 1;
+}
+
+}  // namespace simt
+
+template <typename Tp>
+int Simt<Tp>::factor_sums_y(const View& v, double reg, double* out, cudaStream_t st) {
+    const Tp* Y = static_cast<const Tp*>(v.Y);
+    if (v.ys == 1) {
+        simt::k_row_sums<Tp><<<(unsigned)v.R, 256, 0, st>>>(Y, v.S, v.yr, reg, out);
+    } else {
+        dim3 blk(32, 8);
+        simt::k_factor_sums<Tp><<<(unsigned)((v.R + 31) / 32), blk, 0, st>>>(Y, v.S, v.R, v.ys, v.yr,
+                                                                               reg, out);
+    }
+    return simt::launch_status();
+}
+
+template <typename Tp>
+int Simt<Tp>::factor_sums_x(const View& v, double reg, double* out, cudaStream_t st) {
+    const Tp* X = static_cast<const Tp*>(v.X);
+    if (v.xo == 1) {
+        simt::k_row_sums<Tp><<<(unsigned)v.R, 256, 0, st>>>(X, v.O, v.xr, reg, out);
+    } else {
+        dim3 blk(32, 8);
+        simt::k_factor_sums<Tp><<<(unsigned)((v.R + 31) / 32), blk, 0, st>>>(X, v.O, v.R, v.xo, v.xr,
+                                                                               reg, out);
+    }
+    return simt::launch_status();
+}
+
+template <typename Tp>
+int Simt<Tp>::rescale(const View& v, const double* f, cudaStream_t st) {
+    const int64_t n = v.R * v.O + v.S * v.R;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    simt::k_rescale<Tp><<<(unsigned)blocks, 256, 0, st>>>(v, f);
+    return simt::launch_status();
+}
+
+template <typename Tp>
+int Simt<Tp>::pass1(const View& v, Tp* A, Tp* B, int splits, int64_t s_per, bool with_b,
+                    int* status, cudaStream_t st) {
+    switch (simt::rblock_for<Tp>(v.R)) {
+        case 32: return simt::pass1_rb<Tp, 32>(v, A, B, splits, s_per, with_b, status, st);
+        case 64: return simt::pass1_rb<Tp, 64>(v, A, B, splits, s_per, with_b, status, st);
+        default:
+            if constexpr (sizeof(Tp) == 4)
+                return simt::pass1_rb<Tp, 128>(v, A, B, splits, s_per, with_b, status, st);
+            return DNA_ERR_UNSUPPORTED;
+    }
+}
+
+template <typename Tp>
+int Simt<Tp>::candidates(const View& v, const double* c, const Tp* A, const Tp* B, int splits,
+                         Tp* Xmu, Tp* Xdna, double eps, double alpha, cudaStream_t st) {
+    simt::k_candidates<Tp><<<(unsigned)((v.O + 127) / 128), 128, 0, st>>>(
+        v, c, A, B, splits, Xmu, Xdna, (Tp)eps, (Tp)alpha);
+    return simt::launch_status();
+}
+
+template <typename Tp>
+int Simt<Tp>::mu_apply(const View& v, const double* c, const Tp* A, int splits, cudaStream_t st) {
+    simt::k_mu_apply<Tp><<<(unsigned)((v.O + 127) / 128), 128, 0, st>>>(v, c, A, splits);
+    return simt::launch_status();
+}
+
+template <typename Tp>
+int Simt<Tp>::pass2(const View& v, const Tp* Xmu, const Tp* Xdna, double* dpart, int splits,
+                    int64_t s_per, int* status, cudaStream_t st) {
+    return simt::pass2_any<Tp, 2, false>(v, Xmu, Xdna, v.O, 1, dpart, splits, s_per, status, st);
+}
+
+template <typename Tp>
+int Simt<Tp>::select(const View& v, const Tp* Xmu, const Tp* Xdna, const double* dpart,
+                     int splits, uint8_t* choice, double* dfin, cudaStream_t st) {
+    simt::k_select<Tp><<<(unsigned)((v.O + 127) / 128), 128, 0, st>>>(v, Xmu, Xdna, dpart, splits,
+                                                                        choice, dfin);
+    return simt::launch_status();
+}
+
+template <typename Tp>
+int Simt<Tp>::kl_columns(const View& v, double* dpart, int splits, int64_t s_per, int* status,
+                         cudaStream_t st) {
+    const Tp* X = static_cast<const Tp*>(v.X);
+    return simt::pass2_any<Tp, 1, true>(v, X, X, v.xr, v.xo, dpart, splits, s_per, status, st);
+}
+
+template <typename Tp>
+int Simt<Tp>::prepare_v(const Tp* V, int64_t N, int64_t T, int64_t ldv, Tp* Vt, int64_t ldvt,
+                        double* colsum, double* rowsum, cudaStream_t st) {
+    dim3 blk(32, 8);
+    dim3 grid((unsigned)((T + 31) / 32), (unsigned)((N + 31) / 32));
+    simt::k_transpose<Tp><<<grid, blk, 0, st>>>(V, N, T, ldv, Vt, ldvt);
+    if (simt::launch_status()) return DNA_ERR_CUDA;
+    // column sums of V: sum over n of V[n][t]  (coalesced across t)
+    simt::k_factor_sums<Tp><<<(unsigned)((T + 31) / 32), blk, 0, st>>>(V, N, T, ldv, 1, 0.0, colsum);
+    if (simt::launch_status()) return DNA_ERR_CUDA;
+    // row sums of V: rows are contiguous
+    simt::k_row_sums<Tp><<<(unsigned)N, 256, 0, st>>>(V, T, ldv, 0.0, rowsum);
+    return simt::launch_status();
+}
+
+template <typename Tp>
+int Simt<Tp>::pass1_blocks_per_sm(int64_t R) {
+    switch (simt::rblock_for<Tp>(R)) {
+        case 32: return simt::occupancy_pass1<Tp, 32>();
+        case 64: return simt::occupancy_pass1<Tp, 64>();
+        default:
+            if constexpr (sizeof(Tp) == 4) return simt::occupancy_pass1<Tp, 128>();
+            return 1;
+    }
+}
+
+template <typename Tp>
+int Simt<Tp>::pass2_blocks_per_sm(int64_t R) {
+    switch (simt::rblock_for<Tp>(R)) {
+        case 32: return simt::occupancy_pass2<Tp, 32>();
+        case 64: return simt::occupancy_pass2<Tp, 64>();
+        default:
+            if constexpr (sizeof(Tp) == 4) return simt::occupancy_pass2<Tp, 128>();
+            return 1;
+    }
+}
+
+template <typename Tp> int Simt<Tp>::chunk() { return simt::SB; }
+template <typename Tp> int Simt<Tp>::oblock() { return simt::OB; }
+template <typename Tp> int Simt<Tp>::rblock(int64_t R) { return simt::rblock_for<Tp>(R); }
+
+}  // namespace dna

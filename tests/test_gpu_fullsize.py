@@ -1,0 +1,62 @@
+"""Parity at the benchmark's full size (N=4096 T=16384 R=128, FP32 form), on sampled
+outputs the oracle computes one by one.
+
+The H half-step separates over columns (eq. 5) and the W half-step over rows, so the
+oracle runs either on a sample of columns (rows) exactly.  The step-16 (29)
+normalisation couples all of them only through one factor per r, which is read from
+the GPU's own rescaling of the other factor.  Tolerance: 1e-4 relative (FP32 form).
+"""
+import numpy as np
+import pytest
+
+import workloads
+from gpu_helpers import GpuProblem, rel_fro, replay_choice
+from oracle import dna as o
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def big():
+    return workloads.plain_large(0)
+
+
+def test_plain_large_sampled(big):
+    g = np.random.default_rng(0)
+    N, T = big.V.shape
+    cols = np.sort(g.choice(T, 48, replace=False))
+    rows = np.sort(g.choice(N, 48, replace=False))
+    with GpuProblem(big.V, big.W, big.H, "f32") as gp:
+        gp.dna.dna_normalize(gp.ctx, 1)
+        kl0 = gp.dna.dna_kl(gp.ctx)
+        W0, H0 = gp.WH()
+        # H half-step on sampled columns
+        gp.dna.dna_step_H(gp.ctx)
+        W1, H1 = gp.WH()
+        dm, dd = gp.costs(0)
+        ch = gp.choice(0)
+        Vc = big.V[:, cols].astype(np.float64)
+        half = o.h_half_step(Vc, W0, H0[:, cols])
+        np.testing.assert_allclose(dm[cols], half.d_mu, rtol=1e-5)
+        np.testing.assert_allclose(dd[cols], half.d_dna, rtol=1e-5)
+        mask, _ = replay_choice(half, ch[cols], "f32")
+        X = np.where(mask[None, :], half.X_dna, half.X_mu)
+        sigma = W1.sum(axis=0) / W0.sum(axis=0)          # step 16 factor per r
+        assert rel_fro(H1[:, cols], X / sigma[:, None]) < 1e-4
+        # W half-step on sampled rows
+        gp.dna.dna_step_W(gp.ctx)
+        W2, H2 = gp.WH()
+        ch = gp.choice(1)
+        Vr = big.V[rows, :].astype(np.float64)
+        half = o.w_half_step(Vr, W1[rows, :], H1)
+        mask, _ = replay_choice(half, ch[rows], "f32")
+        X = np.where(mask[:, None], half.X_dna, half.X_mu)
+        sigma = H2.sum(axis=1) / H1.sum(axis=1)          # step 29 factor per r
+        assert rel_fro(W2[rows, :], X / sigma[None, :]) < 1e-4
+        # properties at full size: cost does not increase; eq. 9 per row after the W step
+        kl1 = gp.dna.dna_kl(gp.ctx)
+        assert kl1 <= kl0
+        import torch
+        Z = gp.W @ gp.H
+        rs = Z.double().sum(dim=1).cpu().numpy()
+        np.testing.assert_allclose(rs, big.V.astype(np.float64).sum(axis=1), rtol=1e-4)

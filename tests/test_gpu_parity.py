@@ -1,0 +1,156 @@
+"""GPU path (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerances: FP32 form, W and H within 1e-4 relative (Frobenius) after each of the
+first 5 iterations and final d_KL within 1e-3 relative after 50; FP64 form, 1e-10.
+Selections may differ only at near ties (gpu_helpers.NEAR_TIE); the oracle then
+replays the GPU's choice so rounding near a tie cannot grow into a different
+trajectory.
+"""
+import numpy as np
+import pytest
+
+import workloads
+from gpu_helpers import GpuProblem, rel_fro, step_pair
+from oracle import dna as o
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f32": 1e-4, "f64": 1e-10}
+
+
+def _trajectory(p, kind, iters, mu=False, **opts):
+    V = p.V.astype(np.float64)
+    with GpuProblem(p.V, p.W, p.H, kind, **{k: v for k, v in opts.items()}) as gp:
+        gp.dna.dna_normalize(gp.ctx, 1)
+        W, H = o.normalize_w_columns(p.W, p.H, opts.get("lam", 0.0))
+        Wg, Hg = gp.WH()
+        assert rel_fro(Wg, W) < TOL[kind] and rel_fro(Hg, H) < TOL[kind]
+        flips = 0
+        oopts = {"eps": opts.get("eps", o.EPS), "alpha": opts.get("alpha", o.ALPHA),
+                 "rho": opts.get("rho", 0.0), "lam": opts.get("lam", 0.0)}
+        for it in range(iters):
+            for which in (0, 1):
+                W, H, nf = step_pair(gp, W, H, which, mu=mu, opts=oopts)
+                flips += nf
+                Wg, Hg = gp.WH()
+                ew, eh = rel_fro(Wg, W), rel_fro(Hg, H)
+                assert ew < TOL[kind] and eh < TOL[kind], (it, which, ew, eh)
+        kl_gpu = gp.dna.dna_kl(gp.ctx)
+        kl_ref = o.kl_divergence(V, W @ H)
+        assert abs(kl_gpu - kl_ref) <= TOL[kind] * abs(kl_ref), (kl_gpu, kl_ref)
+    return flips
+
+
+@pytest.mark.parametrize("kind", ["f32", "f64"])
+def test_plain_small_first_iterations(kind):
+    """N=256 T=512 R=16: W and H after each of the first 5 DNA iterations."""
+    _trajectory(workloads.plain_small(0), kind, 5)
+
+
+@pytest.mark.parametrize("kind", ["f32", "f64"])
+def test_plain_small_mu_iterations(kind):
+    _trajectory(workloads.plain_small(1), kind, 5, mu=True)
+
+
+@pytest.mark.parametrize("kind", ["f32", "f64"])
+def test_plain_small_final_kl_free_running(kind):
+    """50 free-running DNA iterations: final d_KL within 1e-3 relative (FP32)."""
+    p = workloads.plain_small(0)
+    _, _, costs = o.run(p.V, p.W, p.H, 50, "dna")
+    with GpuProblem(p.V, p.W, p.H, kind) as gp:
+        gp.dna.dna_normalize(gp.ctx, 1)
+        kl0 = gp.dna.dna_kl(gp.ctx)
+        assert abs(kl0 - costs[0]) <= 1e-6 * costs[0]
+        prev = kl0
+        for _ in range(50):
+            gp.dna.dna_iterate(gp.ctx, 1)
+            kl = gp.dna.dna_kl(gp.ctx)
+            assert kl <= prev * (1 + 1e-6), (kl, prev)      # non-increasing (Section 2.4)
+            prev = kl
+    tol = 1e-3 if kind == "f32" else 1e-9
+    assert abs(prev - costs[-1]) <= tol * costs[-1], (prev, costs[-1])
+
+
+SHAPES = [(1, 1, 1), (3, 5, 2), (67, 131, 17), (130, 70, 33), (129, 200, 64),
+          (200, 300, 129), (65, 129, 300), (40, 70, 512), (70, 513, 8)]
+
+
+@pytest.mark.parametrize("kind", ["f32", "f64"])
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(map(str, s)))
+def test_ragged_shapes(shape, kind):
+    """Odd sizes: several tiles plus ragged tails in N, T and R (R up to 512)."""
+    N, T, R = shape
+    p = workloads.custom(N, T, R, seed=N * 7 + T * 3 + R)
+    _trajectory(p, kind, 2)
+
+
+@pytest.mark.parametrize("kind", ["f32", "f64"])
+def test_regularised_and_limits(kind):
+    """lambda, rho > 0 and non-default eps, alpha (eq. 2, Section 2.3)."""
+    p = workloads.custom(90, 150, 12, seed=5)
+    _trajectory(p, kind, 3, eps=0.05, alpha=1.5, rho=0.2, lam=0.3)
+
+
+def test_costs_match_oracle():
+    """Per-column and per-row candidate costs (steps 9, 14, 22, 27) against the oracle."""
+    p = workloads.custom(100, 180, 10, seed=9)
+    with GpuProblem(p.V, p.W, p.H, "f64") as gp:
+        V = p.V.astype(np.float64)
+        half = o.h_half_step(V, p.W, p.H)
+        gp.dna.dna_step_H(gp.ctx)
+        dm, dd = gp.costs(0)
+        np.testing.assert_allclose(dm, half.d_mu, rtol=1e-11)
+        np.testing.assert_allclose(dd, half.d_dna, rtol=1e-11)
+        np.testing.assert_array_equal(gp.choice(0), half.choice)
+
+
+def test_zero_rows_and_columns():
+    """All-zero columns and rows of V: q = 0, the column goes to 0, MU kept on the tie."""
+    p = workloads.custom(50, 60, 5, seed=2)
+    V = p.V.copy()
+    V[:, 7] = 0
+    V[11, :] = 0
+    _ = _trajectory(workloads.Problem("z", V, p.W0, p.H0, p.W, p.H, 0), "f64", 2)
+
+
+def test_nonfinite_reported():
+    """z = 0 where v > 0 (a zero factor) is reported as DNA_ERR_NONFINITE, not hidden."""
+    import paper_1301_3389_gb300 as dna
+    p = workloads.custom(40, 50, 4, seed=3)
+    W = p.W.copy()
+    W[:] = 0.0
+    with GpuProblem(p.V, W, p.H, "f32") as gp:
+        gp.dna.dna_step_H(gp.ctx)
+        assert gp.dna.dna_get_status(gp.ctx) == dna.DNA_ERR_NONFINITE
+
+
+def test_run_host_matches_device_path():
+    """dna_run_host (host buffers, copies inside) equals the device-buffer path."""
+    import paper_1301_3389_gb300 as dna
+    p = workloads.custom(120, 200, 9, seed=4)
+    with GpuProblem(p.V, p.W, p.H, "f32") as gp:
+        gp.dna.dna_iterate(gp.ctx, 3)
+        kl_dev = gp.dna.dna_kl(gp.ctx)
+        Wd, Hd = gp.WH()
+    ctx = dna.dna_create(120, 200, 9, dna.make_opts(dtype=dna.DNA_F32))
+    try:
+        W = p.W.copy()
+        H = p.H.copy()
+        kl = dna.dna_run_host(ctx, p.V, W, H, 3)
+    finally:
+        dna.dna_destroy(ctx)
+    assert kl == kl_dev
+    np.testing.assert_array_equal(W, Wd.astype(np.float32))
+    np.testing.assert_array_equal(H, Hd.astype(np.float32))
+
+
+def test_deterministic():
+    """Two runs give bit-identical W and H (fixed-order reductions, no float atomics)."""
+    p = workloads.custom(300, 500, 20, seed=6)
+    outs = []
+    for _ in range(2):
+        with GpuProblem(p.V, p.W, p.H, "f32") as gp:
+            gp.dna.dna_iterate(gp.ctx, 3)
+            outs.append(gp.WH())
+    np.testing.assert_array_equal(outs[0][0], outs[1][0])
+    np.testing.assert_array_equal(outs[0][1], outs[1][1])

@@ -41,7 +41,7 @@ class DNAError(RuntimeError):
 def _load() -> ctypes.CDLL:
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"libdna.so not built ({LIB_PATH}); run "
-                          "`python -m paper_1301_3389_gb300.build` (needs nvcc)")
+                          "`python paper_1301_3389_gb300/build.py` (needs nvcc)")
     lib = ctypes.CDLL(LIB_PATH)
     P, I64, I, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
     sig = {

@@ -4,7 +4,7 @@ Each .cu translation unit under csrc/ compiles in parallel to an object file und
 _build/, then nvcc links them into paper_1301_3389_gb300/libdna.so.  Rebuilds only what
 changed (by modification time of the sources and headers).
 
-    python -m paper_1301_3389_gb300.build [--verbose] [--force]
+    python paper_1301_3389_gb300/build.py [--verbose] [--force] [--ptxas-info]
 """
 from __future__ import annotations
 

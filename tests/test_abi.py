@@ -27,8 +27,8 @@ def declared_functions():
 
 @pytest.fixture(scope="module")
 def lib():
-    from paper_1301_3389_gb300 import build
-    path = build.build()
+    import __graft_entry__
+    path = __graft_entry__._build_module().build()
     return ctypes.CDLL(path)
 
 

@@ -33,6 +33,9 @@ Readings taken where the paper is silent, ambiguous or garbled (each is tested):
 * Eq. 10 renormalisation with a zero denominator leaves the column unscaled.
 * The denominators of eq. 7 and eq. 14 are always the explicit (W^t 1)_r + lambda
   (H-step) and (H 1)_r + rho (W-step); steps 1, 16 and 29 normalise as written.
+* A factor sum that is exactly zero (an all-zero column of W or row of H with no
+  regularisation; Section 2 assumes this does not happen) is replaced by 1, in the
+  eq. 7 / 14 denominators and in the step 1 / 16 / 29 normalisers alike.
 """
 from __future__ import annotations
 
@@ -50,6 +53,11 @@ class NonFiniteError(FloatingPointError):
 
 def f64(x) -> np.ndarray:
     return np.asarray(x, dtype=np.float64)
+
+
+def nonzero_sum(s: np.ndarray) -> np.ndarray:
+    """A factor sum, with an exact zero replaced by 1 (module docstring)."""
+    return np.where(s == 0, 1.0, s)
 
 
 # ----------------------------------------------------------------------------- cost
@@ -98,14 +106,14 @@ def ratio(V, Z, power: int) -> np.ndarray:
 def normalize_w_columns(W, H, lam: float = 0.0):
     """Steps 1 and 29: divide column r of W by sum_n w_nr + lambda, multiply row r of H."""
     W, H = f64(W), f64(H)
-    s = W.sum(axis=0) + lam
+    s = nonzero_sum(W.sum(axis=0) + lam)
     return W / s[None, :], H * s[:, None]
 
 
 def normalize_h_rows(W, H, rho: float = 0.0):
     """Step 16: divide row r of H by sum_t h_rt + rho, multiply column r of W."""
     W, H = f64(W), f64(H)
-    s = H.sum(axis=1) + rho
+    s = nonzero_sum(H.sum(axis=1) + rho)
     return W * s[None, :], H / s[:, None]
 
 
@@ -151,7 +159,7 @@ def h_half_step(V, W, H, eps: float = EPS, alpha: float = ALPHA, lam: float = 0.
     test replay another implementation's selection near ties.
     """
     V, W, H = f64(V), f64(W), f64(H)
-    c = W.sum(axis=0) + lam                       # (W^t 1)_r + lambda   (eq. 7, 14)
+    c = nonzero_sum(W.sum(axis=0) + lam)          # (W^t 1)_r + lambda   (eq. 7, 14)
     Z = W @ H                                     # step 2
     Q = ratio(V, Z, 1)                            # step 3
     W2 = W * W                                    # step 4
@@ -182,7 +190,7 @@ def w_half_step(V, W, H, eps: float = EPS, alpha: float = ALPHA, rho: float = 0.
                 choice=None) -> HalfStep:
     """Algorithm 1 steps 17-28 for W (H fixed); selection per row of W."""
     V, W, H = f64(V), f64(W), f64(H)
-    c = H.sum(axis=1) + rho                       # (H 1)_r + rho
+    c = nonzero_sum(H.sum(axis=1) + rho)          # (H 1)_r + rho
     Z = W @ H                                     # carried Z of step 15 (WH is unchanged by step 16)
     Q = ratio(V, Z, 1)
     H2 = H * H                                    # step 17
@@ -235,7 +243,7 @@ def dna_iteration(V, W, H, eps=EPS, alpha=ALPHA, rho=0.0, lam=0.0,
 def mu_h(V, W, H, lam: float = 0.0) -> np.ndarray:
     """Eq. 11 for every column: h <- h (W^t q) / (W^t 1 + lambda)."""
     V, W, H = f64(V), f64(W), f64(H)
-    c = W.sum(axis=0) + lam
+    c = nonzero_sum(W.sum(axis=0) + lam)
     Q = ratio(V, W @ H, 1)
     return H * (W.T @ Q) / c[:, None]
 
@@ -243,7 +251,7 @@ def mu_h(V, W, H, lam: float = 0.0) -> np.ndarray:
 def mu_w(V, W, H, rho: float = 0.0) -> np.ndarray:
     """Eq. 11 transposed (Section 2 symmetry): w <- w (q H^t) / (H 1 + rho)."""
     V, W, H = f64(V), f64(W), f64(H)
-    c = H.sum(axis=1) + rho
+    c = nonzero_sum(H.sum(axis=1) + rho)
     Q = ratio(V, W @ H, 1)
     return W * (Q @ H.T) / c[None, :]
 

@@ -369,11 +369,17 @@ __global__ void k_select(View v, const Tp* __restrict__ Xmu, const Tp* __restric
     for (int64_t r = 0; r < v.R; ++r) X[r * v.xr + o * v.xo] = src[r * v.O + o];
 }
 
+// A factor sum that is exactly zero (an all-zero column of W or row of H without
+// regularisation, excluded by the assumption of Section 2) is replaced by 1.
+__device__ __forceinline__ double nonzero_sum(double s, bool guard) {
+    return (guard && s == 0.0) ? 1.0 : s;
+}
+
 // out[r] = sum_i M(i, r) + reg for a matrix with element (i, r) at M[i * si + r * sr],
 // i < n.  One CTA of 32 x 8 threads per 32 values of r; fixed summation order.
 template <typename Tp>
 __global__ void k_factor_sums(const Tp* __restrict__ M, int64_t n, int64_t R, int64_t si,
-                              int64_t sr, double reg, double* __restrict__ out) {
+                              int64_t sr, double reg, double* __restrict__ out, bool guard) {
     __shared__ double red[8][33];
     const int lane = threadIdx.x, ty = threadIdx.y;
     const int64_t r = (int64_t)blockIdx.x * 32 + lane;
@@ -385,14 +391,14 @@ __global__ void k_factor_sums(const Tp* __restrict__ M, int64_t n, int64_t R, in
     if (ty == 0 && r < R) {
         double t = 0.0;
         for (int k = 0; k < 8; ++k) t += red[k][lane];
-        out[r] = t + reg;
+        out[r] = nonzero_sum(t + reg, guard);
     }
 }
 
 // Row-sum variant for unit-stride rows (element (r, i) at M[r * ld + i]): one CTA per r.
 template <typename Tp>
 __global__ void k_row_sums(const Tp* __restrict__ M, int64_t n, int64_t ld, double reg,
-                           double* __restrict__ out) {
+                           double* __restrict__ out, bool guard) {
     __shared__ double red[256];
     const int64_t r = blockIdx.x;
     double s = 0.0;
@@ -403,7 +409,7 @@ __global__ void k_row_sums(const Tp* __restrict__ M, int64_t n, int64_t ld, doub
         if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
         __syncthreads();
     }
-    if (threadIdx.x == 0) out[r] = red[0] + reg;
+    if (threadIdx.x == 0) out[r] = nonzero_sum(red[0] + reg, guard);
 }
 
 // X(r, o) /= f_r for all (r, o); Y(s, r) *= f_r for all (s, r).  Thread per element of

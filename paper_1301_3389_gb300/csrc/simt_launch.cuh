@@ -95,11 +95,11 @@ template <typename Tp>
 int Simt<Tp>::factor_sums_y(const View& v, double reg, double* out, cudaStream_t st) {
     const Tp* Y = static_cast<const Tp*>(v.Y);
     if (v.ys == 1) {
-        simt::k_row_sums<Tp><<<(unsigned)v.R, 256, 0, st>>>(Y, v.S, v.yr, reg, out);
+        simt::k_row_sums<Tp><<<(unsigned)v.R, 256, 0, st>>>(Y, v.S, v.yr, reg, out, true);
     } else {
         dim3 blk(32, 8);
         simt::k_factor_sums<Tp><<<(unsigned)((v.R + 31) / 32), blk, 0, st>>>(Y, v.S, v.R, v.ys, v.yr,
-                                                                               reg, out);
+                                                                               reg, out, true);
     }
     return simt::launch_status();
 }
@@ -108,11 +108,11 @@ template <typename Tp>
 int Simt<Tp>::factor_sums_x(const View& v, double reg, double* out, cudaStream_t st) {
     const Tp* X = static_cast<const Tp*>(v.X);
     if (v.xo == 1) {
-        simt::k_row_sums<Tp><<<(unsigned)v.R, 256, 0, st>>>(X, v.O, v.xr, reg, out);
+        simt::k_row_sums<Tp><<<(unsigned)v.R, 256, 0, st>>>(X, v.O, v.xr, reg, out, true);
     } else {
         dim3 blk(32, 8);
         simt::k_factor_sums<Tp><<<(unsigned)((v.R + 31) / 32), blk, 0, st>>>(X, v.O, v.R, v.xo, v.xr,
-                                                                               reg, out);
+                                                                               reg, out, true);
     }
     return simt::launch_status();
 }
@@ -182,10 +182,11 @@ int Simt<Tp>::prepare_v(const Tp* V, int64_t N, int64_t T, int64_t ldv, Tp* Vt, 
     simt::k_transpose<Tp><<<grid, blk, 0, st>>>(V, N, T, ldv, Vt, ldvt);
     if (simt::launch_status()) return DNA_ERR_CUDA;
     // column sums of V: sum over n of V[n][t]  (coalesced across t)
-    simt::k_factor_sums<Tp><<<(unsigned)((T + 31) / 32), blk, 0, st>>>(V, N, T, ldv, 1, 0.0, colsum);
+    simt::k_factor_sums<Tp><<<(unsigned)((T + 31) / 32), blk, 0, st>>>(V, N, T, ldv, 1, 0.0, colsum,
+                                                                             false);
     if (simt::launch_status()) return DNA_ERR_CUDA;
     // row sums of V: rows are contiguous
-    simt::k_row_sums<Tp><<<(unsigned)N, 256, 0, st>>>(V, T, ldv, 0.0, rowsum);
+    simt::k_row_sums<Tp><<<(unsigned)N, 256, 0, st>>>(V, T, ldv, 0.0, rowsum, false);
     return simt::launch_status();
 }
 

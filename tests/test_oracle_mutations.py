@@ -31,8 +31,8 @@ MUTATIONS = {
     "w_b_without_square": ("B = (Qb @ H2.T) / c[None, :]", "B = (Qb @ H.T) / c[None, :]"),
     "w_a_missing_denominator": ("A = (Q @ H.T) / c[None, :] - 1.0", "A = (Q @ H.T) - 1.0"),
     "mu_h_missing_denominator": ("return H * (W.T @ Q) / c[:, None]", "return H * (W.T @ Q)"),
-    "h_denominator_without_lambda": ("c = W.sum(axis=0) + lam                       # (W^t 1)_r",
-                                     "c = W.sum(axis=0)                       # (W^t 1)_r"),
+    "h_denominator_without_lambda": ("c = nonzero_sum(W.sum(axis=0) + lam)          # (W^t 1)_r",
+                                     "c = nonzero_sum(W.sum(axis=0))          # (W^t 1)_r"),
     "step16_multiplies_h": ("return W * s[None, :], H / s[:, None]",
                             "return W / s[None, :], H * s[:, None]"),
     "selection_inverted": ("choice = d_dna < d_mu                     # step 15",

@@ -45,6 +45,7 @@ extern "C" {
 #define DNA_ERR_TIMEOUT     (-4)  /* a bounded device-side wait gave up                 */
 #define DNA_ERR_UNSUPPORTED (-5)  /* valid request this build does not implement       */
 #define DNA_ERR_ALLOC       (-6)  /* device allocation failed                           */
+#define DNA_ERR_LIMIT       (-7)  /* size beyond a fixed limit of dna_kl_noalloc         */
 
 /* Arithmetic forms. */
 #define DNA_F64  0  /* float64 everywhere                                                */
@@ -157,6 +158,32 @@ int dna_profile(dna_ctx* ctx, int enable);
  * phase (launches, may be NULL) since the previous call, then reset both.
  * Synchronises the stream. */
 int dna_phase_times(dna_ctx* ctx, double* ms, int64_t* launches, int n);
+
+/* Capacity, in float64 partial sums, of the static scratch of dna_kl_noalloc. */
+#define DNA_KL_NOALLOC_MAX_PARTIALS (1 << 20)
+
+/* d_KL(V, W H) (eq. 1), like dna_kl, for callers that cannot allocate device memory:
+ * code whose device memory is all owned by another framework's pool allocator, and
+ * latency-critical code that cannot pay for cudaMalloc or the implicit device
+ * synchronisation of cudaFree.  The paper has no counterpart of this entry point.
+ *
+ * Needs no context and allocates nothing: it calls no cudaMalloc, cudaFree or
+ * allocating library routine.  Its scratch (a status word and per-column partial sums)
+ * is one static device array of 256 + 8 * DNA_KL_NOALLOC_MAX_PARTIALS bytes (about
+ * 8 MiB), which every GPU that loads this library holds until the process exits.
+ * Inputs, float32 device memory, row-major: V (N x T, leading dimension ldv >= T), W
+ * (N x R), H (R x T).  Output: *kl_out, one float64 in device memory owned by the caller,
+ * written asynchronously on `stream` (a cudaStream_t; NULL = legacy default stream); it
+ * is +infinity if some z <= 0 where v > 0.  Limits: 1 <= R <= 512 and
+ * T <= DNA_KL_NOALLOC_MAX_PARTIALS, else DNA_ERR_LIMIT (T too large) or DNA_ERR_ARG,
+ * returned before any work is queued.
+ *
+ * The first call on a device looks up the device address of the static array (with that
+ * device current); make that first call before any stream capture.  All calls share the
+ * one array: calls that overlap on the GPU (for example on two unordered streams) race
+ * and give wrong results, so order them, e.g. on one stream. */
+int dna_kl_noalloc(const float* V, int64_t ldv, const float* W, const float* H, int64_t N,
+                   int64_t T, int64_t R, double* kl_out, void* stream);
 
 /* Release the context and its workspace (not the caller's buffers). */
 void dna_destroy(dna_ctx* ctx);

@@ -20,6 +20,8 @@ DNA_ERR_NONFINITE = -3
 DNA_ERR_TIMEOUT = -4
 DNA_ERR_UNSUPPORTED = -5
 DNA_ERR_ALLOC = -6
+DNA_ERR_LIMIT = -7
+DNA_KL_NOALLOC_MAX_PARTIALS = 1 << 20
 
 DNA_F64, DNA_F32, DNA_BF16 = 0, 1, 2
 PHASES = ("pass1", "candidates", "pass2", "select", "sums", "kl", "prepare")
@@ -61,6 +63,7 @@ def _load() -> ctypes.CDLL:
         "dna_run_host": (I, [P, P, P, P, I, ctypes.POINTER(D)]),
         "dna_profile": (I, [P, I]),
         "dna_phase_times": (I, [P, P, P, I]),
+        "dna_kl_noalloc": (I, [P, I64, P, P, I64, I64, I64, P, P]),
         "dna_destroy": (None, [P]),
         "dna_strerror": (ctypes.c_char_p, [I]),
     }
@@ -201,6 +204,19 @@ def dna_phase_times(ctx: int) -> dict:
     _check(LIB.dna_phase_times(ctx, ms.ctypes.data, nl.ctypes.data, len(PHASES)),
            "dna_phase_times")
     return {p: (float(ms[i]), int(nl[i])) for i, p in enumerate(PHASES)}
+
+
+def dna_kl_noalloc(V, W, H, out, stream=None, ldv: int | None = None) -> None:
+    """d_KL(V, W H) into the one-element float64 device tensor ``out`` (asynchronous).
+
+    Allocates nothing (static scratch inside the library); calls that overlap on the GPU
+    race, so keep them ordered on one stream."""
+    N, T = V.shape
+    R = W.shape[1]
+    if ldv is None:
+        ldv = V.stride(0)
+    _check(LIB.dna_kl_noalloc(_ptr(V), ldv, _ptr(W), _ptr(H), N, T, R, _ptr(out),
+                              _stream(stream)), "dna_kl_noalloc")
 
 
 def dna_destroy(ctx: int) -> None:

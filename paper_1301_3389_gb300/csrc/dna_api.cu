@@ -335,6 +335,7 @@ const char* dna_strerror(int code) {
         case DNA_ERR_TIMEOUT: return "a bounded device-side wait timed out";
         case DNA_ERR_UNSUPPORTED: return "not supported by this build";
         case DNA_ERR_ALLOC: return "device allocation failed";
+        case DNA_ERR_LIMIT: return "size beyond the static scratch limit of dna_kl_noalloc";
         default: return "unknown status code";
     }
 }

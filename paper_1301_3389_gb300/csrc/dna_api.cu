@@ -51,6 +51,21 @@ struct dna_ctx {
     // split plans (pass 1 and pass 2 / KL) for the H view and the W view
     int sp1[2] = {1, 1}, sp2[2] = {1, 1};
     int64_t per1[2] = {0, 0}, per2[2] = {0, 0};
+    // tensor-core (BF16) path
+    bool tc = false;
+    int rp = 0;                      // padded rank
+    int64_t pad_o[2] = {0, 0};       // O_pad of the H view (0) and W view (1)
+    int64_t pad_s[2] = {0, 0};       // S_pad
+    void* Xk = nullptr;              // bf16 [max O_pad][rp]
+    void* Yk = nullptr;              // bf16 [max S_pad][rp]
+    void* Ytk = nullptr;             // bf16 [rp][max S_pad]
+    void* Y2tk = nullptr;
+    void* Xmk = nullptr;             // bf16 [max O_pad][rp]
+    void* Xdk = nullptr;
+    void* Vp = nullptr;              // aligned copy of V when V's rows are not 16-byte aligned
+    int64_t ldvp = 0;
+    int tsp1[2] = {1, 1}, tsp2[2] = {1, 1};
+    int64_t tper1[2] = {0, 0}, tper2[2] = {0, 0};
     // profiling: event pairs around phases, launch counts
     bool prof_on = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -105,13 +120,21 @@ View make_view(const dna_ctx* c, bool wstep) {
     return v;
 }
 
-// Split the reduction over s so that the grid fills the GPU about once.
+// Split the reduction over s across CTAs.  Picks the split count that minimises the
+// number of full waves per unit of work (ceil(blocks * splits / slots) / splits), plus a
+// small charge per split for the extra partial sums it writes; each split keeps at least
+// four chunks.
 void plan_split(int64_t S, int64_t nblocks_os, int slots, int chunk, int* splits, int64_t* per) {
     const int64_t chunks = (S + chunk - 1) / chunk;
-    int64_t sp = (slots + nblocks_os - 1) / std::max<int64_t>(nblocks_os, 1);
-    sp = std::max<int64_t>(1, std::min<int64_t>(sp, std::max<int64_t>(1, chunks / 4)));
-    sp = std::min<int64_t>(sp, 32);
-    const int64_t per_chunks = (chunks + sp - 1) / sp;
+    const int64_t max_sp = std::max<int64_t>(1, std::min<int64_t>(32, chunks / 4));
+    int64_t best = 1;
+    double best_cost = 1e300;
+    for (int64_t sp = 1; sp <= max_sp; ++sp) {
+        const int64_t waves = (nblocks_os * sp + slots - 1) / slots;
+        const double cost = (double)waves / (double)sp + 0.02 * (double)sp;
+        if (cost < best_cost - 1e-12) { best_cost = cost; best = sp; }
+    }
+    const int64_t per_chunks = (chunks + best - 1) / best;
     *per = per_chunks * chunk;
     *splits = (int)((S + *per - 1) / *per);
 }
@@ -128,13 +151,21 @@ void plan_all(dna_ctx* c) {
         const int64_t nob = (Odim + ob - 1) / ob;
         plan_split(Sdim, nob * nrb, c->num_sms * b1, ch, &c->sp1[w], &c->per1[w]);
         plan_split(Sdim, nob, c->num_sms * b2, ch, &c->sp2[w], &c->per2[w]);
+        if (c->tc) {
+            const int tob = dna::TcBf16::oblock(), tch = dna::TcBf16::chunk();
+            c->pad_o[w] = (Odim + tob - 1) / tob * tob;
+            c->pad_s[w] = (Sdim + tch - 1) / tch * tch;
+            plan_split(Sdim, c->pad_o[w] / tob, c->num_sms, tch, &c->tsp1[w], &c->tper1[w]);
+            plan_split(Sdim, c->pad_o[w] / tob, c->num_sms, tch, &c->tsp2[w], &c->tper2[w]);
+        }
     }
 }
 
 void free_all(dna_ctx* c) {
     void* ptrs[] = {c->own_V, c->own_W, c->own_H, c->Vt, c->colsum_v, c->rowsum_v, c->c, c->sig,
                     c->Apart, c->Bpart, c->Xmu, c->Xdna, c->dpart, c->dfin_h, c->dfin_w,
-                    c->choice_h, c->choice_w, c->kl_dev, c->status};
+                    c->choice_h, c->choice_w, c->kl_dev, c->status, c->Xk, c->Yk, c->Ytk,
+                    c->Y2tk, c->Xmk, c->Xdk, c->Vp};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t ev : c->ev_pool) cudaEventDestroy(ev);
@@ -148,8 +179,8 @@ int alloc_workspace(dna_ctx* c) {
     int64_t ap = 0, dp = 0;
     for (int w = 0; w < 2; ++w) {
         const int64_t O = w ? N : T;
-        ap = std::max<int64_t>(ap, (int64_t)c->sp1[w] * R * O);
-        dp = std::max<int64_t>(dp, (int64_t)c->sp2[w] * 2 * O);
+        ap = std::max<int64_t>(ap, (int64_t)std::max(c->sp1[w], c->tsp1[w]) * R * O);
+        dp = std::max<int64_t>(dp, (int64_t)std::max(c->sp2[w], c->tsp2[w]) * 2 * O);
     }
     c->ldvt = (N + 3) / 4 * 4;
     int e = DNA_OK;
@@ -169,7 +200,20 @@ int alloc_workspace(dna_ctx* c) {
     e |= dmalloc(&c->choice_w, (size_t)N);
     e |= dmalloc(&c->kl_dev, sizeof(double));
     e |= dmalloc(&c->status, sizeof(int));
+    if (c->tc) {
+        const int64_t mo = std::max(c->pad_o[0], c->pad_o[1]);
+        const int64_t ms = std::max(c->pad_s[0], c->pad_s[1]);
+        const size_t b = 2;  // bf16
+        e |= dmalloc(&c->Xk, b * (size_t)(mo * c->rp));
+        e |= dmalloc(&c->Yk, b * (size_t)(ms * c->rp));
+        e |= dmalloc(&c->Ytk, b * (size_t)(ms * c->rp));
+        e |= dmalloc(&c->Y2tk, b * (size_t)(ms * c->rp));
+        e |= dmalloc(&c->Xmk, b * (size_t)(mo * c->rp));
+        e |= dmalloc(&c->Xdk, b * (size_t)(mo * c->rp));
+    }
     if (e != DNA_OK) return DNA_ERR_ALLOC;
+    // the padding columns of the transposed copy of V are read by 16-byte copies: zero them
+    if (cudaMemset(c->Vt, 0, sizeof(Tp) * (size_t)T * c->ldvt) != cudaSuccess) return DNA_ERR_CUDA;
     if (cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess) return DNA_ERR_CUDA;
     if (cudaMemset(c->choice_h, 0, (size_t)T) != cudaSuccess) return DNA_ERR_CUDA;
     if (cudaMemset(c->choice_w, 0, (size_t)N) != cudaSuccess) return DNA_ERR_CUDA;
@@ -237,6 +281,68 @@ int half_step(dna_ctx* c, int wstep, bool mu_only) {
         if (e) return e;
     }
     return normalize<Tp>(c, wstep == 1 ? 1 : 0);
+}
+
+// The BF16 precision form: the two O(NRT) passes on tcgen05 tensor cores (bf16 operands,
+// float32 accumulation in TMEM), everything else as in the FP32 form.
+int half_step_tc(dna_ctx* c, int wstep, bool mu_only) {
+    using S = dna::Simt<float>;
+    using TC = dna::TcBf16;
+    const View v = make_view(c, wstep == 1);
+    const double reg_den = wstep ? c->o.rho : c->o.lambda;
+    cudaStream_t st = c->stream;
+    float* A = static_cast<float*>(c->Apart);
+    float* B = static_cast<float*>(c->Bpart);
+    float* Xmu = static_cast<float*>(c->Xmu);
+    float* Xdna = static_cast<float*>(c->Xdna);
+    const int64_t rp = c->rp;
+    dna::TcOperands op{};
+    op.S = v.S; op.O = v.O; op.R = v.R;
+    op.S_pad = c->pad_s[wstep]; op.O_pad = c->pad_o[wstep];
+    op.Xk = c->Xk; op.Yk = c->Yk; op.Ytk = c->Ytk; op.Y2tk = c->Y2tk;
+    const float* X = static_cast<const float*>(v.X);
+    const float* Y = static_cast<const float*>(v.Y);
+    const float* Vso = static_cast<const float*>(v.V);
+    int64_t vs = v.vs;
+    if (!wstep && c->Vp) { Vso = static_cast<const float*>(c->Vp); vs = c->ldvp; }
+
+    int e = phase(c, DNA_PHASE_SUMS, 1, [&] { return S::factor_sums_y(v, reg_den, c->c, st); });
+    if (e) return e;
+    e = phase(c, DNA_PHASE_PASS1, 5, [&] {
+        int r = TC::to_bf16(X, v.xo, v.xr, v.O, v.R, c->Xk, rp, op.O_pad, rp, false, st);
+        if (!r) r = TC::to_bf16(Y, v.ys, v.yr, v.S, v.R, c->Yk, rp, op.S_pad, rp, false, st);
+        if (!r) r = TC::to_bf16(Y, v.yr, v.ys, v.R, v.S, c->Ytk, op.S_pad, rp, op.S_pad, false, st);
+        if (!r && !mu_only)
+            r = TC::to_bf16(Y, v.yr, v.ys, v.R, v.S, c->Y2tk, op.S_pad, rp, op.S_pad, true, st);
+        if (!r) r = TC::pass1(op, Vso, vs, A, B, c->tsp1[wstep], c->tper1[wstep], !mu_only,
+                              c->status, st);
+        return r;
+    });
+    if (e) return e;
+    if (mu_only) {
+        e = phase(c, DNA_PHASE_CANDIDATES, 1,
+                  [&] { return S::mu_apply(v, c->c, A, c->tsp1[wstep], st); });
+        if (e) return e;
+        return normalize<float>(c, wstep == 1 ? 1 : 0);
+    }
+    e = phase(c, DNA_PHASE_CANDIDATES, 3, [&] {
+        int r = S::candidates(v, c->c, A, B, c->tsp1[wstep], Xmu, Xdna, c->o.eps, c->o.alpha, st);
+        if (!r) r = TC::to_bf16(Xmu, 1, v.O, v.O, v.R, c->Xmk, rp, op.O_pad, rp, false, st);
+        if (!r) r = TC::to_bf16(Xdna, 1, v.O, v.O, v.R, c->Xdk, rp, op.O_pad, rp, false, st);
+        return r;
+    });
+    if (e) return e;
+    e = phase(c, DNA_PHASE_PASS2, 1, [&] {
+        return TC::pass2(op, c->Xmk, c->Xdk, Vso, vs, c->dpart, c->tsp2[wstep], c->tper2[wstep],
+                         c->status, st);
+    });
+    if (e) return e;
+    e = phase(c, DNA_PHASE_SELECT, 1, [&] {
+        return S::select(v, Xmu, Xdna, c->dpart, c->tsp2[wstep], wstep ? c->choice_w : c->choice_h,
+                         wstep ? c->dfin_w : c->dfin_h, st);
+    });
+    if (e) return e;
+    return normalize<float>(c, wstep == 1 ? 1 : 0);
 }
 
 template <typename Tp>
@@ -349,10 +455,17 @@ int dna_create(int64_t N, int64_t T, int64_t R, const dna_opts* opts, dna_ctx** 
     dna_default_opts(&o);
     if (opts) o = *opts;
     if (!valid_opts(o)) return DNA_ERR_ARG;
-    if (o.dtype == DNA_BF16 || o.engine == DNA_ENGINE_TENSOR) return DNA_ERR_UNSUPPORTED;
+    // Engines: BF16 runs on the tensor cores (R <= 128 in this build); F32 and F64 on the
+    // CUDA cores.
+    const bool tc = o.dtype == DNA_BF16;
+    if (tc && (o.engine == DNA_ENGINE_SIMT || dna::TcBf16::rank_pad(R) == 0))
+        return DNA_ERR_UNSUPPORTED;
+    if (!tc && o.engine == DNA_ENGINE_TENSOR) return DNA_ERR_UNSUPPORTED;
     dna_ctx* c = new (std::nothrow) dna_ctx();
     if (!c) return DNA_ERR_ALLOC;
     c->N = N; c->T = T; c->R = R; c->o = o;
+    c->tc = tc;
+    c->rp = tc ? dna::TcBf16::rank_pad(R) : 0;
     c->esz = o.dtype == DNA_F64 ? 8 : 4;
     if (cudaGetDevice(&c->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) !=
@@ -377,6 +490,19 @@ int dna_bind(dna_ctx* c, const void* V, int64_t ldv, void* W, void* H) {
     if (set_device(c)) return DNA_ERR_CUDA;
     c->V = V; c->ldv = ldv; c->W = W; c->H = H;
     c->bound = true;
+    if (c->tc && (ldv % 4 != 0 || reinterpret_cast<uintptr_t>(V) % 16 != 0)) {
+        // the tensor-core kernels copy V in 16-byte pieces: keep an aligned, padded copy
+        c->ldvp = (c->T + 3) / 4 * 4;
+        if (!c->Vp) {
+            if (dmalloc(&c->Vp, sizeof(float) * (size_t)(c->N * c->ldvp))) return DNA_ERR_ALLOC;
+            if (cudaMemset(c->Vp, 0, sizeof(float) * (size_t)(c->N * c->ldvp)) != cudaSuccess)
+                return DNA_ERR_CUDA;
+        }
+        if (cudaMemcpy2DAsync(c->Vp, sizeof(float) * c->ldvp, V, sizeof(float) * ldv,
+                              sizeof(float) * c->T, c->N, cudaMemcpyDeviceToDevice,
+                              c->stream) != cudaSuccess)
+            return DNA_ERR_CUDA;
+    }
     return is_f64(c) ? prepare<double>(c) : prepare<float>(c);
 }
 
@@ -396,12 +522,14 @@ int dna_normalize(dna_ctx* c, int which) {
 int dna_step_H(dna_ctx* c) {
     if (int e = check_ready(c)) return e;
     if (set_device(c)) return DNA_ERR_CUDA;
+    if (c->tc) return half_step_tc(c, 0, false);
     return is_f64(c) ? half_step<double>(c, 0, false) : half_step<float>(c, 0, false);
 }
 
 int dna_step_W(dna_ctx* c) {
     if (int e = check_ready(c)) return e;
     if (set_device(c)) return DNA_ERR_CUDA;
+    if (c->tc) return half_step_tc(c, 1, false);
     return is_f64(c) ? half_step<double>(c, 1, false) : half_step<float>(c, 1, false);
 }
 
@@ -419,6 +547,7 @@ int mu_step(dna_ctx* c, int which) {
     if (int e = check_ready(c)) return e;
     if (which != 0 && which != 1) return DNA_ERR_ARG;
     if (set_device(c)) return DNA_ERR_CUDA;
+    if (c->tc) return half_step_tc(c, which, true);
     return is_f64(c) ? half_step<double>(c, which, true) : half_step<float>(c, which, true);
 }
 

@@ -65,6 +65,34 @@ template <typename Tp> struct Simt {
     static int rblock(int64_t R);  // the r-block of pass 1
 };
 
+// Tensor-core (tcgen05) operands of one half-step, bf16, zero-padded:
+//   Xk [O_pad][RP]  x(r, o) K-major (GEMM1 A)      Yk   [S_pad][RP] y(s, r) (GEMM1 B)
+//   Ytk [RP][S_pad] y(s, r) transposed (GEMM2 B)   Y2tk [RP][S_pad] y(s, r)^2 (GEMM3 B)
+struct TcOperands {
+    int64_t S, O, R, S_pad, O_pad;
+    const void* Xk;
+    const void* Yk;
+    const void* Ytk;
+    const void* Y2tk;
+};
+
+struct TcBf16 {
+    // padded rank for the tensor-core kernels (64 or 128), 0 if unsupported
+    static int rank_pad(int64_t R);
+    // dst[i][j] = bf16(src(i, j)) (or its square), zero-padded to rows_pad x cols_pad
+    static int to_bf16(const float* src, int64_t si, int64_t sj, int64_t rows, int64_t cols,
+                       void* dst, int64_t ld, int64_t rows_pad, int64_t cols_pad, bool square,
+                       cudaStream_t st);
+    static int pass1(const TcOperands& op, const float* V, int64_t vs, float* Apart,
+                     float* Bpart, int splits, int64_t s_per, bool with_b, int* status,
+                     cudaStream_t st);
+    static int pass2(const TcOperands& op, const void* Xmk, const void* Xdk, const float* V,
+                     int64_t vs, double* dpart, int splits, int64_t s_per, int* status,
+                     cudaStream_t st);
+    static int chunk();
+    static int oblock();
+};
+
 // sum of dpart[0 .. n) in a fixed order into *out (float64)
 int reduce_sum(const double* part, int64_t n, double* out, cudaStream_t st);
 

@@ -1,0 +1,130 @@
+"""The BF16 precision form (tcgen05 tensor cores, bf16 operands, float32 accumulation)
+against the FP64 oracle.
+
+Tolerance, derived from the arithmetic: bf16 keeps 8 significant bits, unit roundoff
+u = 2^-9 ~ 2e-3.  z is a sum of positive products of two rounded operands (relative error
+<= 2u); q = v/z is rounded again (u); A = sum w q rounds w (u): the eq. 7 ratio (1 + a) is
+off by at most ~4u ~ 8e-3 element-wise, and the Frobenius error of a half-step is well
+below that.  So: W and H within 1e-2 relative (Frobenius) after each of the first
+iterations; candidate costs within 1e-2 relative; selections may differ where the
+oracle's relative cost margin is below 1e-2.  The float64 cost log (dna_kl) uses float32
+products and must match the oracle to 1e-4.
+"""
+import numpy as np
+import pytest
+
+import workloads
+from gpu_helpers import GpuProblem, rel_fro
+from oracle import dna as o
+
+pytestmark = pytest.mark.gpu
+
+TOL_BF16 = 1e-2
+MARGIN_BF16 = 1e-2
+
+
+def _replay(half, gpu_choice):
+    diff = np.asarray(gpu_choice, bool) != half.choice
+    if diff.any():
+        assert half.margin[diff].max() < MARGIN_BF16, half.margin[diff].max()
+    return np.asarray(gpu_choice, bool), int(diff.sum())
+
+
+def _bf16_steps(p, iters, check_costs=True):
+    V = p.V.astype(np.float64)
+    errs = []
+    with GpuProblem(p.V, p.W, p.H, "bf16") as gp:
+        gp.dna.dna_normalize(gp.ctx, 1)
+        W, H = o.normalize_w_columns(p.W, p.H)
+        for _ in range(iters):
+            for which in (0, 1):
+                half = (o.h_half_step if which == 0 else o.w_half_step)(V, W, H)
+                (gp.dna.dna_step_H if which == 0 else gp.dna.dna_step_W)(gp.ctx)
+                if check_costs:
+                    dm, dd = gp.costs(which)
+                    np.testing.assert_allclose(dm, half.d_mu, rtol=TOL_BF16)
+                    np.testing.assert_allclose(dd, half.d_dna, rtol=TOL_BF16)
+                mask, _ = _replay(half, gp.choice(which))
+                step = o.dna_step_h if which == 0 else o.dna_step_w
+                W, H, _ = step(V, W, H, choice=mask)
+                Wg, Hg = gp.WH()
+                errs.append((rel_fro(Wg, W), rel_fro(Hg, H)))
+                assert errs[-1][0] < TOL_BF16 and errs[-1][1] < TOL_BF16, errs[-1]
+        kl = gp.dna.dna_kl(gp.ctx)
+        Wg, Hg = gp.WH()
+        assert abs(kl - o.kl_divergence(V, Wg @ Hg)) <= 1e-4 * kl
+    return errs
+
+
+SHAPES = [(200, 300, 16), (130, 257, 64), (256, 512, 100), (70, 1000, 128), (1000, 70, 128),
+          (129, 131, 65), (1, 1, 1)]
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(map(str, s)))
+def test_bf16_half_steps(shape):
+    N, T, R = shape
+    p = workloads.custom(N, T, R, seed=N + 3 * T + 7 * R)
+    _bf16_steps(p, 2)
+
+
+def test_bf16_plain_small_trajectory():
+    """N=256 T=512 R=16: the first 5 iterations stay within the bf16 tolerance."""
+    errs = _bf16_steps(workloads.plain_small(0), 5)
+    assert max(max(e) for e in errs) < TOL_BF16
+
+
+def test_bf16_reaches_fp32_kl():
+    """50 iterations: the BF16 form's d_KL is within 1e-2 of the FP32 form's."""
+    p = workloads.plain_small(0)
+    kls = {}
+    for kind in ("f32", "bf16"):
+        with GpuProblem(p.V, p.W, p.H, kind) as gp:
+            gp.dna.dna_normalize(gp.ctx, 1)
+            gp.dna.dna_iterate(gp.ctx, 50)
+            kls[kind] = gp.dna.dna_kl(gp.ctx)
+    assert abs(kls["bf16"] - kls["f32"]) <= 1e-2 * kls["f32"], kls
+
+
+def test_bf16_mu_steps():
+    p = workloads.custom(150, 260, 24, seed=8)
+    V = p.V.astype(np.float64)
+    with GpuProblem(p.V, p.W, p.H, "bf16") as gp:
+        gp.dna.dna_normalize(gp.ctx, 1)
+        W, H = o.normalize_w_columns(p.W, p.H)
+        for which in (0, 1, 0, 1):
+            gp.dna.mu_step(gp.ctx, which)
+            W, H = (o.mu_step_h if which == 0 else o.mu_step_w)(V, W, H)
+            Wg, Hg = gp.WH()
+            assert rel_fro(Wg, W) < TOL_BF16 and rel_fro(Hg, H) < TOL_BF16
+
+
+def test_bf16_unaligned_leading_dimension():
+    """A V whose rows are not 16-byte aligned (ldv = T = 131) takes the aligned copy."""
+    p = workloads.custom(90, 131, 20, seed=21)
+    _bf16_steps(p, 1)
+
+
+def test_bf16_plain_large_sampled():
+    """Full bench size (N=4096 T=16384 R=128): sampled columns and rows vs the oracle."""
+    big = workloads.plain_large(0)
+    g = np.random.default_rng(1)
+    N, T = big.V.shape
+    cols = np.sort(g.choice(T, 32, replace=False))
+    rows = np.sort(g.choice(N, 32, replace=False))
+    with GpuProblem(big.V, big.W, big.H, "bf16") as gp:
+        gp.dna.dna_normalize(gp.ctx, 1)
+        W0, H0 = gp.WH()
+        gp.dna.dna_step_H(gp.ctx)
+        W1, H1 = gp.WH()
+        half = o.h_half_step(big.V[:, cols].astype(np.float64), W0, H0[:, cols])
+        mask, _ = _replay(half, gp.choice(0)[cols])
+        X = np.where(mask[None, :], half.X_dna, half.X_mu)
+        sigma = W1.sum(axis=0) / W0.sum(axis=0)
+        assert rel_fro(H1[:, cols], X / sigma[:, None]) < TOL_BF16
+        gp.dna.dna_step_W(gp.ctx)
+        W2, H2 = gp.WH()
+        half = o.w_half_step(big.V[rows, :].astype(np.float64), W1[rows, :], H1)
+        mask, _ = _replay(half, gp.choice(1)[rows])
+        X = np.where(mask[:, None], half.X_dna, half.X_mu)
+        sigma = H2.sum(axis=1) / H1.sum(axis=1)
+        assert rel_fro(W2[rows, :], X / sigma[None, :]) < TOL_BF16

@@ -194,7 +194,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["dna", "reference"], default="dna")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="plain_large")
-    ap.add_argument("--dtype", choices=["f32", "f64"], default="f32")
+    ap.add_argument("--dtype", choices=["f32", "f64", "bf16"], default="f32")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work")
     ap.add_argument("--ref-cols", type=int, default=512)
@@ -227,8 +227,8 @@ def main(argv=None):
 
     prob = spec["fn"](rank)                      # independent problem per rank
     N, T, R = spec["N"], spec["T"], spec["R"]
-    code = dna.DNA_F32 if args.dtype == "f32" else dna.DNA_F64
-    tdt = torch.float32 if args.dtype == "f32" else torch.float64
+    code = {"f32": dna.DNA_F32, "f64": dna.DNA_F64, "bf16": dna.DNA_BF16}[args.dtype]
+    tdt = torch.float64 if args.dtype == "f64" else torch.float32
     dev = torch.device("cuda", local)
     V = torch.from_numpy(prob.V).to(dev, tdt)
     W = torch.from_numpy(prob.W).to(dev, tdt)
@@ -280,15 +280,23 @@ def main(argv=None):
     flops = (6 if dom == "pass1" else 4) * R * N * T    # per launch (H or W half-step)
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_tflops = SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12 if args.dtype == "f32" \
-        else None
+    if args.dtype == "bf16":
+        bound = "tensor"
+        peak_tflops = float(peaks.get("bf16_tflops_sustained", 1700.0))
+        peak_source = ("measured sustained dense bf16 (cuBLAS, MEASURED_PEAKS.json)"
+                       if "bf16_tflops_sustained" in peaks else "fallback sustained bf16 1700")
+    else:
+        bound = "alu"
+        peak_tflops = SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12 if args.dtype == "f32" \
+            else None
+        peak_source = (f"derived: {SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x "
+                       f"{sm_max:.0f} MHz (max SM clock of measured)")
     achieved = flops / per_launch_s / 1e12
-    traffic = recorded_traffic(dom, args.workload)
-    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_tflops,
+    traffic = recorded_traffic(dom + ("_tc" if args.dtype == "bf16" else ""), args.workload)
+    roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak_tflops,
                 "unit": "TFLOP/s", "frac": (achieved / peak_tflops) if peak_tflops else None,
                 "traffic": traffic,
-                "peak_source": (f"derived: {SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x "
-                                f"{sm_max:.0f} MHz (max SM clock of measured)"),
+                "peak_source": peak_source,
                 "algorithmic_flops_per_launch": flops,
                 "launch_ms": per_launch_s * 1e3,
                 "phase_share": {p: phases[p][0] / ms for p in ("pass1", "candidates", "pass2",
@@ -300,7 +308,8 @@ def main(argv=None):
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
         "config": {"workload": args.workload, "desc": spec["desc"], "N": N, "T": T, "R": R,
-                   "form": args.dtype.upper(), "engine": "simt",
+                   "form": args.dtype.upper(),
+                   "engine": "tcgen05" if args.dtype == "bf16" else "simt",
                    "l2": "inputs larger than L2 (V is %d MB)" % (N * T * 4 // 2**20),
                    "parallelism": "independent problem per GPU" if world > 1 else "single GPU",
                    "zero_fraction": prob.meta.get("zero_fraction")},

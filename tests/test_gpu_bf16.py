@@ -41,9 +41,12 @@ def _bf16_steps(p, iters, check_costs=True):
                 half = (o.h_half_step if which == 0 else o.w_half_step)(V, W, H)
                 (gp.dna.dna_step_H if which == 0 else gp.dna.dna_step_W)(gp.ctx)
                 if check_costs:
+                    # the cost d' of a column is a sum of terms of size ~v (|log z| + 1); its
+                    # bf16 error scales with that sum, not with d' (which can cross zero)
                     dm, dd = gp.costs(which)
-                    np.testing.assert_allclose(dm, half.d_mu, rtol=TOL_BF16)
-                    np.testing.assert_allclose(dd, half.d_dna, rtol=TOL_BF16)
+                    scale = V.sum(axis=0 if which == 0 else 1) + 1.0
+                    assert np.all(np.abs(dm - half.d_mu) <= TOL_BF16 * (np.abs(half.d_mu) + scale))
+                    assert np.all(np.abs(dd - half.d_dna) <= TOL_BF16 * (np.abs(half.d_dna) + scale))
                 mask, _ = _replay(half, gp.choice(which))
                 step = o.dna_step_h if which == 0 else o.dna_step_w
                 W, H, _ = step(V, W, H, choice=mask)

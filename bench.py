@@ -300,7 +300,7 @@ def main(argv=None):
                 "algorithmic_flops_per_launch": flops,
                 "launch_ms": per_launch_s * 1e3,
                 "phase_share": {p: phases[p][0] / ms for p in ("pass1", "candidates", "pass2",
-                                                                "select", "sums")}}
+                                                                "select", "sums", "operands")}}
     launches = sum(v[1] for k, v in phases.items())
 
     line = {

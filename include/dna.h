@@ -145,7 +145,8 @@ int dna_run_host(dna_ctx* ctx, const void* V, void* W, void* H, int iters, doubl
 #define DNA_PHASE_SUMS       4  /* factor sums and rescaling (steps 1, 16, 29)           */
 #define DNA_PHASE_KL         5  /* d_KL (eq. 1)                                           */
 #define DNA_PHASE_PREPARE    6  /* one-time sums and transpose of V (dna_bind)           */
-#define DNA_NUM_PHASES       7
+#define DNA_PHASE_OPERANDS   7  /* bf16 tensor-core operand tiles (BF16 form)            */
+#define DNA_NUM_PHASES       8
 
 /* enable = 1: from now on record a CUDA event pair on the context's stream around each
  * phase of every call (no device allocation; up to 16384 pairs are kept, later phases

@@ -24,7 +24,7 @@ DNA_ERR_LIMIT = -7
 DNA_KL_NOALLOC_MAX_PARTIALS = 1 << 20
 
 DNA_F64, DNA_F32, DNA_BF16 = 0, 1, 2
-PHASES = ("pass1", "candidates", "pass2", "select", "sums", "kl", "prepare")
+PHASES = ("pass1", "candidates", "pass2", "select", "sums", "kl", "prepare", "operands")
 DNA_ENGINE_AUTO, DNA_ENGINE_SIMT, DNA_ENGINE_TENSOR = 0, 1, 2
 
 

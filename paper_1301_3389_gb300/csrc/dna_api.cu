@@ -37,6 +37,7 @@ struct dna_ctx {
     double* rowsum_v = nullptr;  // N
     double* c = nullptr;         // R
     double* sig = nullptr;       // R
+    double* fwork = nullptr;     // FSUM_SPLITS * R partial factor sums
     void* Apart = nullptr;       // [splits][R][O]
     void* Bpart = nullptr;
     void* Xmu = nullptr;         // [R][O]
@@ -163,7 +164,7 @@ void plan_all(dna_ctx* c) {
 
 void free_all(dna_ctx* c) {
     void* ptrs[] = {c->own_V, c->own_W, c->own_H, c->Vt, c->colsum_v, c->rowsum_v, c->c, c->sig,
-                    c->Apart, c->Bpart, c->Xmu, c->Xdna, c->dpart, c->dfin_h, c->dfin_w,
+                    c->fwork, c->Apart, c->Bpart, c->Xmu, c->Xdna, c->dpart, c->dfin_h, c->dfin_w,
                     c->choice_h, c->choice_w, c->kl_dev, c->status, c->Xk, c->Yk, c->Ytk,
                     c->Y2tk, c->Xmk, c->Xdk, c->Vp};
     for (void* p : ptrs)
@@ -189,6 +190,7 @@ int alloc_workspace(dna_ctx* c) {
     e |= dmalloc(&c->rowsum_v, sizeof(double) * N);
     e |= dmalloc(&c->c, sizeof(double) * R);
     e |= dmalloc(&c->sig, sizeof(double) * R);
+    e |= dmalloc(&c->fwork, sizeof(double) * dna::FSUM_SPLITS * R);
     e |= dmalloc(&c->Apart, sizeof(Tp) * (size_t)ap);
     e |= dmalloc(&c->Bpart, sizeof(Tp) * (size_t)ap);
     e |= dmalloc(&c->Xmu, sizeof(Tp) * (size_t)(R * M));
@@ -238,7 +240,7 @@ int normalize(dna_ctx* c, int which) {
     const View v = make_view(c, which == 1);
     const double reg = which == 1 ? c->o.lambda : c->o.rho;
     return phase(c, DNA_PHASE_SUMS, 2, [&] {
-        int e = S::factor_sums_x(v, reg, c->sig, c->stream);
+        int e = S::factor_sums_x(v, reg, c->sig, c->fwork, c->stream);
         return e ? e : S::rescale(v, c->sig, c->stream);
     });
 }
@@ -255,7 +257,7 @@ int half_step(dna_ctx* c, int wstep, bool mu_only) {
     Tp* Xmu = static_cast<Tp*>(c->Xmu);
     Tp* Xdna = static_cast<Tp*>(c->Xdna);
     cudaStream_t st = c->stream;
-    int e = phase(c, DNA_PHASE_SUMS, 1, [&] { return S::factor_sums_y(v, reg_den, c->c, st); });
+    int e = phase(c, DNA_PHASE_SUMS, 1, [&] { return S::factor_sums_y(v, reg_den, c->c, c->fwork, st); });
     if (e) return e;
     e = phase(c, DNA_PHASE_PASS1, 1, [&] {
         return S::pass1(v, A, B, c->sp1[wstep], c->per1[wstep], !mu_only, c->status, st);
@@ -306,17 +308,20 @@ int half_step_tc(dna_ctx* c, int wstep, bool mu_only) {
     int64_t vs = v.vs;
     if (!wstep && c->Vp) { Vso = static_cast<const float*>(c->Vp); vs = c->ldvp; }
 
-    int e = phase(c, DNA_PHASE_SUMS, 1, [&] { return S::factor_sums_y(v, reg_den, c->c, st); });
+    int e = phase(c, DNA_PHASE_SUMS, 1, [&] { return S::factor_sums_y(v, reg_den, c->c, c->fwork, st); });
     if (e) return e;
-    e = phase(c, DNA_PHASE_PASS1, 5, [&] {
+    e = phase(c, DNA_PHASE_OPERANDS, mu_only ? 3 : 4, [&] {
         int r = TC::to_bf16(X, v.xo, v.xr, v.O, v.R, c->Xk, rp, op.O_pad, rp, false, st);
         if (!r) r = TC::to_bf16(Y, v.ys, v.yr, v.S, v.R, c->Yk, rp, op.S_pad, rp, false, st);
         if (!r) r = TC::to_bf16(Y, v.yr, v.ys, v.R, v.S, c->Ytk, op.S_pad, rp, op.S_pad, false, st);
         if (!r && !mu_only)
             r = TC::to_bf16(Y, v.yr, v.ys, v.R, v.S, c->Y2tk, op.S_pad, rp, op.S_pad, true, st);
-        if (!r) r = TC::pass1(op, Vso, vs, A, B, c->tsp1[wstep], c->tper1[wstep], !mu_only,
-                              c->status, st);
         return r;
+    });
+    if (e) return e;
+    e = phase(c, DNA_PHASE_PASS1, 1, [&] {
+        return TC::pass1(op, Vso, vs, A, B, c->tsp1[wstep], c->tper1[wstep], !mu_only, c->status,
+                         st);
     });
     if (e) return e;
     if (mu_only) {
@@ -325,9 +330,12 @@ int half_step_tc(dna_ctx* c, int wstep, bool mu_only) {
         if (e) return e;
         return normalize<float>(c, wstep == 1 ? 1 : 0);
     }
-    e = phase(c, DNA_PHASE_CANDIDATES, 3, [&] {
-        int r = S::candidates(v, c->c, A, B, c->tsp1[wstep], Xmu, Xdna, c->o.eps, c->o.alpha, st);
-        if (!r) r = TC::to_bf16(Xmu, 1, v.O, v.O, v.R, c->Xmk, rp, op.O_pad, rp, false, st);
+    e = phase(c, DNA_PHASE_CANDIDATES, 1, [&] {
+        return S::candidates(v, c->c, A, B, c->tsp1[wstep], Xmu, Xdna, c->o.eps, c->o.alpha, st);
+    });
+    if (e) return e;
+    e = phase(c, DNA_PHASE_OPERANDS, 2, [&] {
+        int r = TC::to_bf16(Xmu, 1, v.O, v.O, v.R, c->Xmk, rp, op.O_pad, rp, false, st);
         if (!r) r = TC::to_bf16(Xdna, 1, v.O, v.O, v.R, c->Xdk, rp, op.O_pad, rp, false, st);
         return r;
     });
@@ -377,8 +385,8 @@ int set_device(const dna_ctx* c) {
     return cudaSetDevice(c->device) == cudaSuccess ? DNA_OK : DNA_ERR_CUDA;
 }
 
-// Run f (which queues nlaunch kernels) as one instance of phase ph, bracketed by an
-// event pair when profiling is on.
+// Run f as one instance of phase ph, bracketed by an event pair when profiling is on;
+// the kernels it launches are counted (nlaunch is the expected count, for reading only).
 template <class F>
 int phase(dna_ctx* c, int ph, int nlaunch, F&& f) {
     size_t idx = SIZE_MAX;
@@ -387,12 +395,13 @@ int phase(dna_ctx* c, int ph, int nlaunch, F&& f) {
         c->ev_used += 2;
         if (cudaEventRecord(c->ev_pool[idx], c->stream) != cudaSuccess) return DNA_ERR_CUDA;
     }
+    const int64_t before = dna::launch_count();
     const int e = f();
     if (idx != SIZE_MAX) {
         if (cudaEventRecord(c->ev_pool[idx + 1], c->stream) != cudaSuccess) return DNA_ERR_CUDA;
         c->ev_recs.emplace_back(ph, idx);
     }
-    c->phase_launches[ph] += nlaunch;
+    c->phase_launches[ph] += dna::launch_count() - before;
     return e;
 }
 
@@ -415,7 +424,7 @@ __global__ void k_reduce_sum(const double* __restrict__ part, int64_t n, double*
 
 int reduce_sum(const double* part, int64_t n, double* out, cudaStream_t st) {
     k_reduce_sum<<<1, 1024, 0, st>>>(part, n, out);
-    return cudaGetLastError() == cudaSuccess ? DNA_OK : DNA_ERR_CUDA;
+    return after_launch();
 }
 
 }  // namespace dna

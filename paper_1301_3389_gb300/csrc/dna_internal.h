@@ -8,6 +8,20 @@
 
 namespace dna {
 
+// Kernel launches issued by this host thread (read around each phase for dna_phase_times).
+inline int64_t& launch_count() {
+    static thread_local int64_t n = 0;
+    return n;
+}
+// Call right after each kernel launch: counts it and reports a launch error.
+inline int after_launch() {
+    ++launch_count();
+    return cudaGetLastError() == cudaSuccess ? DNA_OK : DNA_ERR_CUDA;
+}
+
+// Partial-sum slots of the two-level factor sums.
+constexpr int FSUM_SPLITS = 64;
+
 // Device status bits (sticky, OR-ed by kernels, read by synchronising calls).
 enum : int { STATUS_NONFINITE = 1, STATUS_TIMEOUT = 2 };
 
@@ -29,10 +43,13 @@ struct View {
 // Launchers, one instantiation per element type (float, double).  Each returns a
 // DNA_* status (launch errors only; device-side errors go to *status).
 template <typename Tp> struct Simt {
-    // sum over s of y(s, r) + reg -> out[r] (the eq. 7 / 14 denominators)
-    static int factor_sums_y(const View& v, double reg, double* out, cudaStream_t st);
+    // sum over s of y(s, r) + reg -> out[r] (the eq. 7 / 14 denominators); work holds at
+    // least FSUM_SPLITS * R float64
+    static int factor_sums_y(const View& v, double reg, double* out, double* work,
+                             cudaStream_t st);
     // sum over o of x(r, o) + reg -> out[r] (the step 16 / 29 normalisers)
-    static int factor_sums_x(const View& v, double reg, double* out, cudaStream_t st);
+    static int factor_sums_x(const View& v, double reg, double* out, double* work,
+                             cudaStream_t st);
     // x(r, o) *= f_r^-1 ... : X scaled by 1/f_r, Y scaled by f_r (steps 1, 16, 29)
     static int rescale(const View& v, const double* f, cudaStream_t st);
     // pass 1: raw sums Apart = sum_s y q, Bpart = sum_s y^2 qbar (split over s)

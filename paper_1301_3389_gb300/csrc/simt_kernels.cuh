@@ -296,42 +296,55 @@ __global__ void __launch_bounds__(NT) k_pass2(View v, const Tp* __restrict__ X0,
     }
 }
 
-// Candidates (steps 6 and 11, eq. 10, 11, 15, 17), one thread per o.
+// Candidates (steps 6 and 11, eq. 10, 11, 15, 17).  CTA = 32 columns o (threadIdx.x) x 8
+// groups of r (threadIdx.y); the eq. 10 denominator of each column is reduced over the 8
+// groups in shared memory in a fixed order.
 template <typename Tp>
-__global__ void k_candidates(View v, const double* __restrict__ c, const Tp* __restrict__ Apart,
-                             const Tp* __restrict__ Bpart, int splits, Tp* __restrict__ Xmu,
-                             Tp* __restrict__ Xdna, Tp eps, Tp alpha) {
-    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (o >= v.O) return;
+__global__ void __launch_bounds__(256) k_candidates(View v, const double* __restrict__ c,
+                                                    const Tp* __restrict__ Apart,
+                                                    const Tp* __restrict__ Bpart, int splits,
+                                                    Tp* __restrict__ Xmu, Tp* __restrict__ Xdna,
+                                                    Tp eps, Tp alpha) {
+    __shared__ double red[8][32];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int64_t o = (int64_t)blockIdx.x * 32 + tx;
+    const bool live = o < v.O;
     const Tp* __restrict__ X = static_cast<const Tp*>(v.X);
     double den = 0.0;
-    for (int64_t r = 0; r < v.R; ++r) {
-        Tp ra = Tp(0), rb = Tp(0);
-        for (int sp = 0; sp < splits; ++sp) {
-            ra += Apart[((int64_t)sp * v.R + r) * v.O + o];
-            rb += Bpart[((int64_t)sp * v.R + r) * v.O + o];
+    if (live) {
+        for (int64_t r = ty; r < v.R; r += 8) {
+            Tp ra = Tp(0), rb = Tp(0);
+            for (int sp = 0; sp < splits; ++sp) {
+                ra += Apart[((int64_t)sp * v.R + r) * v.O + o];
+                rb += Bpart[((int64_t)sp * v.R + r) * v.O + o];
+            }
+            const Tp cr = (Tp)c[r];
+            const Tp a = ra / cr - Tp(1);         // eq. 7
+            const Tp b = rb / cr;                 // eq. 14
+            const Tp x = X[r * v.xr + o * v.xo];
+            const Tp xmu = x + a * x;             // eq. 11 (step 6)
+            Tp xd;
+            if (a < Tp(0)) {                      // eq. 15 with the eps floor on the gain
+                const Tp xb = x * b;
+                const Tp g = xb / (xb - a);
+                xd = x * (g > eps ? g : eps);
+            } else {                              // eq. 17, gain capped at 1 + alpha
+                const Tp st = b > Tp(0) ? a / b : Tp(0);
+                const Tp cap = alpha * x;
+                xd = x + (st < cap ? st : cap);
+            }
+            Xmu[r * v.O + o] = xmu;
+            Xdna[r * v.O + o] = xd;
+            den += c[r] * (double)xd;
         }
-        const Tp cr = (Tp)c[r];
-        const Tp a = ra / cr - Tp(1);         // eq. 7
-        const Tp b = rb / cr;                 // eq. 14
-        const Tp x = X[r * v.xr + o * v.xo];
-        const Tp xmu = x + a * x;             // eq. 11 (step 6)
-        Tp xd;
-        if (a < Tp(0)) {                      // eq. 15 with the eps floor on the gain
-            const Tp xb = x * b;
-            const Tp g = xb / (xb - a);
-            xd = x * (g > eps ? g : eps);
-        } else {                              // eq. 17, gain capped at 1 + alpha
-            const Tp st = b > Tp(0) ? a / b : Tp(0);
-            const Tp cap = alpha * x;
-            xd = x + (st < cap ? st : cap);
-        }
-        Xmu[r * v.O + o] = xmu;
-        Xdna[r * v.O + o] = xd;
-        den += c[r] * (double)xd;
     }
-    const double sc = den > 0.0 ? v.vsum[o] / den : 1.0;  // eq. 10
-    for (int64_t r = 0; r < v.R; ++r) Xdna[r * v.O + o] = (Tp)((double)Xdna[r * v.O + o] * sc);
+    red[ty][tx] = den;
+    __syncthreads();
+    if (!live) return;
+    double tot = 0.0;
+    for (int k = 0; k < 8; ++k) tot += red[k][tx];
+    const double sc = tot > 0.0 ? v.vsum[o] / tot : 1.0;   // eq. 10
+    for (int64_t r = ty; r < v.R; r += 8) Xdna[r * v.O + o] = (Tp)((double)Xdna[r * v.O + o] * sc);
 }
 
 // MU in place (eq. 11): x(r, o) <- x(r, o) * raw_a(r, o) / c_r.
@@ -349,11 +362,15 @@ __global__ void k_mu_apply(View v, const double* __restrict__ c, const Tp* __res
 }
 
 // Selection (step 15 / 28): keep the Newton candidate iff d_dna < d_mu (ties keep MU).
+// CTA = 32 columns o x 8 groups of r.
 template <typename Tp>
-__global__ void k_select(View v, const Tp* __restrict__ Xmu, const Tp* __restrict__ Xdna,
-                         const double* __restrict__ dpart, int splits,
-                         uint8_t* __restrict__ choice, double* __restrict__ dfin) {
-    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256) k_select(View v, const Tp* __restrict__ Xmu,
+                                                const Tp* __restrict__ Xdna,
+                                                const double* __restrict__ dpart, int splits,
+                                                uint8_t* __restrict__ choice,
+                                                double* __restrict__ dfin) {
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int64_t o = (int64_t)blockIdx.x * 32 + tx;
     if (o >= v.O) return;
     double dm = 0.0, dd = 0.0;
     for (int sp = 0; sp < splits; ++sp) {
@@ -361,12 +378,14 @@ __global__ void k_select(View v, const Tp* __restrict__ Xmu, const Tp* __restric
         dd += dpart[((int64_t)sp * 2 + 1) * v.O + o];
     }
     const bool newton = dd < dm;
-    choice[o] = newton ? 1 : 0;
-    dfin[o] = dm;
-    dfin[v.O + o] = dd;
+    if (ty == 0) {
+        choice[o] = newton ? 1 : 0;
+        dfin[o] = dm;
+        dfin[v.O + o] = dd;
+    }
     Tp* __restrict__ X = static_cast<Tp*>(v.X);
     const Tp* __restrict__ src = newton ? Xdna : Xmu;
-    for (int64_t r = 0; r < v.R; ++r) X[r * v.xr + o * v.xo] = src[r * v.O + o];
+    for (int64_t r = ty; r < v.R; r += 8) X[r * v.xr + o * v.xo] = src[r * v.O + o];
 }
 
 // A factor sum that is exactly zero (an all-zero column of W or row of H without
@@ -393,6 +412,38 @@ __global__ void k_factor_sums(const Tp* __restrict__ M, int64_t n, int64_t R, in
         for (int k = 0; k < 8; ++k) t += red[k][lane];
         out[r] = nonzero_sum(t + reg, guard);
     }
+}
+
+// Column sums in two levels: part[split][r] = sum over rows i of split `split` of M(i, r),
+// M(i, r) at M[i * si + r * sr]; grid = (ceil(R / 32), nsplit), CTA 32 x 8.
+template <typename Tp>
+__global__ void k_colsum_part(const Tp* __restrict__ M, int64_t n, int64_t R, int64_t si,
+                              int64_t sr, int64_t rows_per, double* __restrict__ part) {
+    __shared__ double red[8][33];
+    const int lane = threadIdx.x, ty = threadIdx.y;
+    const int64_t r = (int64_t)blockIdx.x * 32 + lane;
+    const int64_t i0 = (int64_t)blockIdx.y * rows_per, i1 = min(n, i0 + rows_per);
+    double s = 0.0;
+    if (r < R)
+        for (int64_t i = i0 + ty; i < i1; i += 8) s += (double)M[i * si + r * sr];
+    red[ty][lane] = s;
+    __syncthreads();
+    if (ty == 0 && r < R) {
+        double t = 0.0;
+        for (int k = 0; k < 8; ++k) t += red[k][lane];
+        part[(int64_t)blockIdx.y * R + r] = t;
+    }
+}
+
+// out[r] = sum over splits of part[split][r] + reg (fixed order), zero sum guarded.
+template <int UNUSED = 0>
+__global__ void k_colsum_final(const double* __restrict__ part, int nsplit, int64_t R, double reg,
+                               double* __restrict__ out, bool guard) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    double t = 0.0;
+    for (int k = 0; k < nsplit; ++k) t += part[(int64_t)k * R + r];
+    out[r] = nonzero_sum(t + reg, guard);
 }
 
 // Row-sum variant for unit-stride rows (element (r, i) at M[r * ld + i]): one CTA per r.

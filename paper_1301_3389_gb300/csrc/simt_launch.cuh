@@ -1,6 +1,8 @@
 // Host launchers for the SIMT kernels (instantiated for float and double).
 #pragma once
 
+#include <algorithm>
+
 #include "simt_kernels.cuh"
 
 namespace dna {
@@ -11,9 +13,7 @@ template <typename Tp> constexpr int rblock_for(int64_t R) {
     return sizeof(Tp) == 4 ? (R <= 32 ? 32 : (R <= 64 ? 64 : 128)) : (R <= 32 ? 32 : 64);
 }
 
-inline int launch_status() {
-    return cudaGetLastError() == cudaSuccess ? DNA_OK : DNA_ERR_CUDA;
-}
+inline int launch_status() { return after_launch(); }
 
 template <typename Kern>
 inline int prep_smem(Kern k, size_t bytes) {
@@ -91,30 +91,40 @@ int occupancy_pass2() {
 
 }  // namespace simt
 
+namespace simt {
+// sum over i < n of M(i, r) + reg -> out[r], M(i, r) at M[i * si + r * sr]: one CTA per r
+// when rows are contiguous, else a two-level column sum through `work`
+// (at least FSUM_SPLITS * R float64).
 template <typename Tp>
-int Simt<Tp>::factor_sums_y(const View& v, double reg, double* out, cudaStream_t st) {
-    const Tp* Y = static_cast<const Tp*>(v.Y);
-    if (v.ys == 1) {
-        simt::k_row_sums<Tp><<<(unsigned)v.R, 256, 0, st>>>(Y, v.S, v.yr, reg, out, true);
-    } else {
-        dim3 blk(32, 8);
-        simt::k_factor_sums<Tp><<<(unsigned)((v.R + 31) / 32), blk, 0, st>>>(Y, v.S, v.R, v.ys, v.yr,
-                                                                               reg, out, true);
+int factor_sums(const Tp* M, int64_t n, int64_t R, int64_t si, int64_t sr, double reg,
+                double* out, double* work, cudaStream_t st) {
+    if (sr != 1 && si == 1) {
+        k_row_sums<Tp><<<(unsigned)R, 256, 0, st>>>(M, n, sr, reg, out, true);
+        return launch_status();
     }
-    return simt::launch_status();
+    const int64_t nsplit = std::max<int64_t>(1, std::min<int64_t>(FSUM_SPLITS, (n + 63) / 64));
+    const int64_t rows_per = (n + nsplit - 1) / nsplit;
+    dim3 blk(32, 8);
+    dim3 grid((unsigned)((R + 31) / 32), (unsigned)nsplit);
+    k_colsum_part<Tp><<<grid, blk, 0, st>>>(M, n, R, si, sr, rows_per, work);
+    if (launch_status()) return DNA_ERR_CUDA;
+    k_colsum_final<<<(unsigned)((R + 127) / 128), 128, 0, st>>>(work, (int)nsplit, R, reg, out, true);
+    return launch_status();
+}
+}  // namespace simt
+
+template <typename Tp>
+int Simt<Tp>::factor_sums_y(const View& v, double reg, double* out, double* work,
+                            cudaStream_t st) {
+    return simt::factor_sums<Tp>(static_cast<const Tp*>(v.Y), v.S, v.R, v.ys, v.yr, reg, out,
+                                 work, st);
 }
 
 template <typename Tp>
-int Simt<Tp>::factor_sums_x(const View& v, double reg, double* out, cudaStream_t st) {
-    const Tp* X = static_cast<const Tp*>(v.X);
-    if (v.xo == 1) {
-        simt::k_row_sums<Tp><<<(unsigned)v.R, 256, 0, st>>>(X, v.O, v.xr, reg, out, true);
-    } else {
-        dim3 blk(32, 8);
-        simt::k_factor_sums<Tp><<<(unsigned)((v.R + 31) / 32), blk, 0, st>>>(X, v.O, v.R, v.xo, v.xr,
-                                                                               reg, out, true);
-    }
-    return simt::launch_status();
+int Simt<Tp>::factor_sums_x(const View& v, double reg, double* out, double* work,
+                            cudaStream_t st) {
+    return simt::factor_sums<Tp>(static_cast<const Tp*>(v.X), v.O, v.R, v.xo, v.xr, reg, out,
+                                 work, st);
 }
 
 template <typename Tp>
@@ -142,7 +152,7 @@ int Simt<Tp>::pass1(const View& v, Tp* A, Tp* B, int splits, int64_t s_per, bool
 template <typename Tp>
 int Simt<Tp>::candidates(const View& v, const double* c, const Tp* A, const Tp* B, int splits,
                          Tp* Xmu, Tp* Xdna, double eps, double alpha, cudaStream_t st) {
-    simt::k_candidates<Tp><<<(unsigned)((v.O + 127) / 128), 128, 0, st>>>(
+    simt::k_candidates<Tp><<<(unsigned)((v.O + 31) / 32), dim3(32, 8), 0, st>>>(
         v, c, A, B, splits, Xmu, Xdna, (Tp)eps, (Tp)alpha);
     return simt::launch_status();
 }
@@ -162,8 +172,8 @@ int Simt<Tp>::pass2(const View& v, const Tp* Xmu, const Tp* Xdna, double* dpart,
 template <typename Tp>
 int Simt<Tp>::select(const View& v, const Tp* Xmu, const Tp* Xdna, const double* dpart,
                      int splits, uint8_t* choice, double* dfin, cudaStream_t st) {
-    simt::k_select<Tp><<<(unsigned)((v.O + 127) / 128), 128, 0, st>>>(v, Xmu, Xdna, dpart, splits,
-                                                                        choice, dfin);
+    simt::k_select<Tp><<<(unsigned)((v.O + 31) / 32), dim3(32, 8), 0, st>>>(v, Xmu, Xdna, dpart,
+                                                                              splits, choice, dfin);
     return simt::launch_status();
 }
 

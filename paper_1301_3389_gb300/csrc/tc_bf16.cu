@@ -396,7 +396,7 @@ int launch_pass1(const P1Args& a, int64_t O_pad, int splits, cudaStream_t st) {
         return DNA_ERR_CUDA;
     dim3 grid((unsigned)(O_pad / OBLK), (unsigned)splits);
     k<<<grid, NTH, smem, st>>>(a);
-    return cudaGetLastError() == cudaSuccess ? DNA_OK : DNA_ERR_CUDA;
+    return after_launch();
 }
 
 template <int RP>
@@ -408,7 +408,7 @@ int launch_pass2(const P2Args& a, int64_t O_pad, int splits, cudaStream_t st) {
         return DNA_ERR_CUDA;
     dim3 grid((unsigned)(O_pad / OBLK), (unsigned)splits);
     k<<<grid, NTH, smem, st>>>(a);
-    return cudaGetLastError() == cudaSuccess ? DNA_OK : DNA_ERR_CUDA;
+    return after_launch();
 }
 
 }  // namespace tc
@@ -422,7 +422,7 @@ int TcBf16::to_bf16(const float* src, int64_t si, int64_t sj, int64_t rows, int6
     dim3 grid((unsigned)((cols_pad + 31) / 32), (unsigned)((rows_pad + 31) / 32));
     tc::k_to_bf16<<<grid, blk, 0, st>>>(src, si, sj, rows, cols, static_cast<tc::bf16*>(dst), ld,
                                          square);
-    return cudaGetLastError() == cudaSuccess ? DNA_OK : DNA_ERR_CUDA;
+    return after_launch();
 }
 
 int TcBf16::pass1(const TcOperands& op, const float* V, int64_t vs, float* Apart, float* Bpart,

@@ -65,6 +65,7 @@ struct dna_ctx {
     void* Xdk = nullptr;
     void* Vp = nullptr;              // aligned copy of V when V's rows are not 16-byte aligned
     int64_t ldvp = 0;
+    dna::TcMaps maps[2];             // TMA descriptors of the H view (0) and W view (1)
     int tsp1[2] = {1, 1}, tsp2[2] = {1, 1};
     int64_t tper1[2] = {0, 0}, tper2[2] = {0, 0};
     // profiling: event pairs around phases, launch counts
@@ -285,6 +286,33 @@ int half_step(dna_ctx* c, int wstep, bool mu_only) {
     return normalize<Tp>(c, wstep == 1 ? 1 : 0);
 }
 
+dna::TcOperands tc_operands(const dna_ctx* c, int wstep) {
+    const View v = make_view(c, wstep == 1);
+    dna::TcOperands op{};
+    op.S = v.S; op.O = v.O; op.R = v.R;
+    op.S_pad = c->pad_s[wstep]; op.O_pad = c->pad_o[wstep];
+    op.Xk = c->Xk; op.Yk = c->Yk; op.Ytk = c->Ytk; op.Y2tk = c->Y2tk;
+    return op;
+}
+
+// V as the tensor-core kernels read it for each view (aligned copy for the H view if needed).
+void tc_v(const dna_ctx* c, int wstep, const float** V, int64_t* vs) {
+    if (wstep) { *V = static_cast<const float*>(c->Vt); *vs = c->ldvt; }
+    else if (c->Vp) { *V = static_cast<const float*>(c->Vp); *vs = c->ldvp; }
+    else { *V = static_cast<const float*>(c->V); *vs = c->ldv; }
+}
+
+int build_tc_maps(dna_ctx* c) {
+    for (int w = 0; w < 2; ++w) {
+        const float* V;
+        int64_t vs;
+        tc_v(c, w, &V, &vs);
+        if (int e = dna::TcBf16::make_maps(&c->maps[w], tc_operands(c, w), V, vs, c->Xmk, c->Xdk))
+            return e;
+    }
+    return DNA_OK;
+}
+
 // The BF16 precision form: the two O(NRT) passes on tcgen05 tensor cores (bf16 operands,
 // float32 accumulation in TMEM), everything else as in the FP32 form.
 int half_step_tc(dna_ctx* c, int wstep, bool mu_only) {
@@ -298,15 +326,9 @@ int half_step_tc(dna_ctx* c, int wstep, bool mu_only) {
     float* Xmu = static_cast<float*>(c->Xmu);
     float* Xdna = static_cast<float*>(c->Xdna);
     const int64_t rp = c->rp;
-    dna::TcOperands op{};
-    op.S = v.S; op.O = v.O; op.R = v.R;
-    op.S_pad = c->pad_s[wstep]; op.O_pad = c->pad_o[wstep];
-    op.Xk = c->Xk; op.Yk = c->Yk; op.Ytk = c->Ytk; op.Y2tk = c->Y2tk;
+    const dna::TcOperands op = tc_operands(c, wstep);
     const float* X = static_cast<const float*>(v.X);
     const float* Y = static_cast<const float*>(v.Y);
-    const float* Vso = static_cast<const float*>(v.V);
-    int64_t vs = v.vs;
-    if (!wstep && c->Vp) { Vso = static_cast<const float*>(c->Vp); vs = c->ldvp; }
 
     int e = phase(c, DNA_PHASE_SUMS, 1, [&] { return S::factor_sums_y(v, reg_den, c->c, c->fwork, st); });
     if (e) return e;
@@ -320,8 +342,8 @@ int half_step_tc(dna_ctx* c, int wstep, bool mu_only) {
     });
     if (e) return e;
     e = phase(c, DNA_PHASE_PASS1, 1, [&] {
-        return TC::pass1(op, Vso, vs, A, B, c->tsp1[wstep], c->tper1[wstep], !mu_only, c->status,
-                         st);
+        return TC::pass1(op, c->maps[wstep], A, B, c->tsp1[wstep], c->tper1[wstep], !mu_only,
+                         c->status, st);
     });
     if (e) return e;
     if (mu_only) {
@@ -341,8 +363,8 @@ int half_step_tc(dna_ctx* c, int wstep, bool mu_only) {
     });
     if (e) return e;
     e = phase(c, DNA_PHASE_PASS2, 1, [&] {
-        return TC::pass2(op, c->Xmk, c->Xdk, Vso, vs, c->dpart, c->tsp2[wstep], c->tper2[wstep],
-                         c->status, st);
+        return TC::pass2(op, c->maps[wstep], c->dpart, c->tsp2[wstep], c->tper2[wstep], c->status,
+                         st);
     });
     if (e) return e;
     e = phase(c, DNA_PHASE_SELECT, 1, [&] {
@@ -512,6 +534,8 @@ int dna_bind(dna_ctx* c, const void* V, int64_t ldv, void* W, void* H) {
                               c->stream) != cudaSuccess)
             return DNA_ERR_CUDA;
     }
+    if (c->tc)
+        if (int e = build_tc_maps(c)) return e;
     return is_f64(c) ? prepare<double>(c) : prepare<float>(c);
 }
 
@@ -618,6 +642,9 @@ int dna_run_host(dna_ctx* c, const void* V, void* W, void* H, int iters, double*
         c->host_mode = true;
         c->V = c->own_V; c->ldv = c->T; c->W = c->own_W; c->H = c->own_H;
         c->bound = true;
+        if (c->tc && (c->T % 4 != 0)) return DNA_ERR_UNSUPPORTED;  // rows must be 16-byte aligned
+        if (c->tc)
+            if (int e2 = build_tc_maps(c)) return e2;
     }
     cudaStream_t st = c->stream;
     if (cudaMemcpyAsync(c->own_V, V, bv, cudaMemcpyHostToDevice, st) != cudaSuccess ||

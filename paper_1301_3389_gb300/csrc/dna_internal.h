@@ -1,6 +1,7 @@
 // Internal interfaces of the DNA library (not part of the C ABI).
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (types only; the driver entry point is looked up at run time)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -93,6 +94,11 @@ struct TcOperands {
     const void* Y2tk;
 };
 
+// TMA descriptors of one half-step view (built once per bound problem).
+struct TcMaps {
+    CUtensorMap x, y, yt, y2t, v, xm, xd;
+};
+
 struct TcBf16 {
     // padded rank for the tensor-core kernels (64 or 128), 0 if unsupported
     static int rank_pad(int64_t R);
@@ -100,12 +106,14 @@ struct TcBf16 {
     static int to_bf16(const float* src, int64_t si, int64_t sj, int64_t rows, int64_t cols,
                        void* dst, int64_t ld, int64_t rows_pad, int64_t cols_pad, bool square,
                        cudaStream_t st);
-    static int pass1(const TcOperands& op, const float* V, int64_t vs, float* Apart,
-                     float* Bpart, int splits, int64_t s_per, bool with_b, int* status,
-                     cudaStream_t st);
-    static int pass2(const TcOperands& op, const void* Xmk, const void* Xdk, const float* V,
-                     int64_t vs, double* dpart, int splits, int64_t s_per, int* status,
-                     cudaStream_t st);
+    // TMA descriptors for the operand buffers of `op`, V_so (leading dimension vs floats,
+    // 16-byte aligned rows) and the bf16 candidates Xmk, Xdk ([O_pad][RP])
+    static int make_maps(TcMaps* m, const TcOperands& op, const float* V, int64_t vs,
+                         const void* Xmk, const void* Xdk);
+    static int pass1(const TcOperands& op, const TcMaps& maps, float* Apart, float* Bpart,
+                     int splits, int64_t s_per, bool with_b, int* status, cudaStream_t st);
+    static int pass2(const TcOperands& op, const TcMaps& maps, double* dpart, int splits,
+                     int64_t s_per, int* status, cudaStream_t st);
     static int chunk();
     static int oblock();
 };

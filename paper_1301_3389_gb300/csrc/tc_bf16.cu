@@ -2,9 +2,9 @@
 // in TMEM (the precision form), for padded rank RP in {64, 128}.
 //
 // Pass 1 (Algorithm 1 steps 2-5 and 10), per CTA = 128 values of o (the TMEM lanes) and
-// an s-range:
-//   GEMM1  Z[o, s]  = sum_r X[o, r] Y[s, r]            M = 128, N = 64 (one s-chunk), K = RP
-//   epilogue (4 warps, thread = lane = o): z from TMEM, v from shared memory,
+// an s-range streamed in chunks of 64:
+//   GEMM1  Z[o, s]  = sum_r X[o, r] Y[s, r]            M = 128, N = 64, K = RP
+//   epilogue (warps 0-3, thread = lane = o): z from TMEM, v from shared memory,
 //          q = v / z, qbar = q / z (0 where v = 0), rounded to bf16 into shared memory
 //   GEMM2  A[o, r] += sum_s Q[o, s] Yt[r, s]           M = 128, N = RP, K = 64
 //   GEMM3  B[o, r] += sum_s Qbar[o, s] Y2t[r, s]       (Y2t = (Y o Y)^t)
@@ -12,10 +12,16 @@
 // Pass 2 (steps 7-9, 12-14): Zmu = Xmu Y^t and Zdna = Xdna Y^t into TMEM, then per lane
 // (= column o) the cost terms -v log z + z, summed in float32 over a chunk and in float64
 // across chunks.
-// Operands are K-major tiles in the 128-byte swizzled layout, staged with cp.async; one
-// thread issues the MMAs; completion is tracked by an mbarrier with a bounded wait.
+//
+// Both passes are warp-specialised pipelines: warp 4 issues TMA copies into a two-stage
+// ring (Y and V tiles; Y^t and (Y o Y)^t tiles), one thread of warp 5 issues the MMAs,
+// warps 0-3 run the epilogue.  Z is double-buffered in TMEM so GEMM1 of the next chunk
+// overlaps the epilogue of this one.  Every hand-off is an mbarrier; every wait is
+// bounded and aborts the CTA (with DNA_ERR_TIMEOUT reported) instead of hanging.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include "dna_internal.h"
 #include "tc_ptx.cuh"
@@ -23,140 +29,225 @@
 namespace dna {
 namespace tc {
 
-constexpr int OBLK = 128;  // o per CTA (MMA M, TMEM lanes)
-constexpr int SCH = 64;    // s per chunk (GEMM1 N, GEMM2 K)
-constexpr int NTH = 128;   // 4 warps: thread i owns TMEM lane i
+constexpr int OBLK = 128;      // o per CTA (MMA M, TMEM lanes)
+constexpr int SCH = 64;        // s per chunk (GEMM1 N, GEMM2 K)
+constexpr int NTHREADS = 192;  // warps 0-3 epilogue, 4 TMA producer, 5 MMA issuer
+constexpr int PRODUCER_WARP = 4, MMA_WARP = 5;
 constexpr long long WAIT_LIMIT = 4000000000LL;  // SM cycles (about 2 s) per wait
 
 using bf16 = __nv_bfloat16;
 
-// Load a ROWS x KE (bf16) K-major tile from row-major global memory (leading dimension
-// ld elements) into the swizzled layout at shared address sbase.  The global tile must be
-// fully inside the (padded) allocation.
-template <int ROWS, int KE>
-__device__ __forceinline__ void load_kmajor(uint32_t sbase, const bf16* __restrict__ g,
-                                            int64_t ld) {
-    constexpr int CPR = KE / 8;  // 16-byte chunks per row
-    for (int c = threadIdx.x; c < ROWS * CPR; c += NTH) {
-        const int row = c / CPR, kc = c % CPR;
-        cp_async16(sbase + sw128_offset(row, kc, ROWS), g + (int64_t)row * ld + kc * 8, 16);
+// Wait for a barrier phase; give up when another thread of the CTA has aborted or after
+// WAIT_LIMIT cycles (then abort the CTA).
+__device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity, volatile int* abort) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*abort) return false;
+        if (clock64() - t0 > WAIT_LIMIT) {
+            *abort = 1;
+            return false;
+        }
     }
+    return true;
 }
 
-// V tile: SCH rows (s) x 128 columns (o) of float32, row-major in shared memory.  Rows at
-// or beyond s_end and 4-column groups starting at or beyond O are zero-filled.
-__device__ __forceinline__ void load_v_tile(uint32_t sbase, const float* __restrict__ V,
-                                            int64_t vs, int64_t s0, int64_t s_end, int64_t o0,
-                                            int64_t O) {
-    for (int c = threadIdx.x; c < SCH * (OBLK / 4); c += NTH) {
-        const int row = c / (OBLK / 4), cc = c % (OBLK / 4);
-        const int64_t s = s0 + row, o = o0 + cc * 4;
-        const bool ok = s < s_end && o < O;
-        const float* src = ok ? V + s * vs + o : V;
-        cp_async16(sbase + (uint32_t)(row * OBLK + cc * 4) * 4u, src, ok ? 16u : 0u);
-    }
+// After an abort: wait (bounded, ignoring the abort flag) for a phase that was armed, so
+// that no TMA copy or MMA is still writing when the CTA releases its memory.
+__device__ __forceinline__ void drain_phase(uint64_t* bar, uint32_t parity) {
+    mbar_wait_bounded(bar, parity, WAIT_LIMIT / 4);
 }
 
 struct P1Args {
-    int64_t S, O, R, S_pad, s_per;
-    const bf16* Xk;    // [O_pad][RP]
-    const bf16* Yk;    // [S_pad][RP]
-    const bf16* Ytk;   // [RP][S_pad]
-    const bf16* Y2tk;  // [RP][S_pad]
-    const float* V;    // V_so, leading dimension vs (multiple of 4), 16-byte aligned
-    int64_t vs;
-    float* Apart;      // [splits][R][O]
+    int64_t S, O, R, s_per;
+    float* Apart;   // [splits][R][O]
     float* Bpart;
     int* status;
 };
 
 template <int RP>
-struct P1Smem {
-    static constexpr uint32_t X = 0;
-    static constexpr uint32_t Y = X + OBLK * RP * 2;
-    static constexpr uint32_t YT = Y + SCH * RP * 2;
-    static constexpr uint32_t Y2T = YT + RP * SCH * 2;
-    static constexpr uint32_t Q = Y2T + RP * SCH * 2;
+struct P1Layout {
+    static constexpr uint32_t X = 0;                               // [128][RP] bf16
+    static constexpr uint32_t Y_BYTES = SCH * RP * 2;              // [64][RP]
+    static constexpr uint32_t V_BYTES = SCH * OBLK * 4;            // [64][128] fp32
+    static constexpr uint32_t RA = X + OBLK * RP * 2;              // ring A: Y, V
+    static constexpr uint32_t RA_STAGE = Y_BYTES + V_BYTES;
+    static constexpr uint32_t YT_BYTES = RP * SCH * 2;             // [RP][64]
+    static constexpr uint32_t RB = RA + 2 * RA_STAGE;              // ring B: Yt, Y2t
+    static constexpr uint32_t RB_STAGE = 2 * YT_BYTES;
+    static constexpr uint32_t Q = RB + 2 * RB_STAGE;               // [128][64] bf16
     static constexpr uint32_t QB = Q + OBLK * SCH * 2;
-    static constexpr uint32_t VT = QB + OBLK * SCH * 2;
-    static constexpr uint32_t BAR = VT + SCH * OBLK * 4;
-    static constexpr uint32_t TOTAL = BAR + 64;
-    static constexpr uint32_t NCOLS = (SCH + 2 * RP) <= 256 ? 256 : 512;
+    static constexpr uint32_t BAR = QB + OBLK * SCH * 2;
+    static constexpr uint32_t TOTAL = BAR + 256;
+    static constexpr uint32_t NCOLS = (2 * SCH + 2 * RP) <= 256 ? 256 : 512;
+    static_assert(RA % 1024 == 0 && RA_STAGE % 1024 == 0 && RB % 1024 == 0 && Q % 1024 == 0,
+                  "tiles must be 1024-byte aligned");
+    static_assert(TOTAL + 1024 <= 232448, "shared memory budget");
 };
 
+// Barrier slots (uint64 each) of pass 1.
+enum { B_FULLA = 0, B_EMPTYA = 2, B_FULLB = 4, B_EMPTYB = 6, B_ZFULL = 8, B_ZEMPTY = 10,
+       B_QFULL = 12, B_QEMPTY = 13, B_XFULL = 14, B_ACC = 15, B_DRAIN = 16, B_COUNT = 17 };
+
 template <int RP, bool WITH_B>
-__global__ void __launch_bounds__(NTH, 1) k_tc_pass1(P1Args a) {
-    using L = P1Smem<RP>;
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_tc_pass1(P1Args a, const __grid_constant__ CUtensorMap tmX,
+               const __grid_constant__ CUtensorMap tmY, const __grid_constant__ CUtensorMap tmYt,
+               const __grid_constant__ CUtensorMap tmY2t, const __grid_constant__ CUtensorMap tmV) {
+    using L = P1Layout<RP>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* sm = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const uint32_t sbase = smem_u32(sm);
     uint64_t* bar = reinterpret_cast<uint64_t*>(sm + L::BAR);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L::BAR + 16);
-    const float* Vs = reinterpret_cast<const float*>(sm + L::VT);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L::BAR + B_COUNT * 8);
+    volatile int* abort = reinterpret_cast<volatile int*>(sm + L::BAR + B_COUNT * 8 + 8);
 
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t o0 = (int64_t)blockIdx.x * OBLK;
-    const int64_t o = o0 + tid;
     const int64_t s_begin = (int64_t)blockIdx.y * a.s_per;
     const int64_t s_end = min(a.S, s_begin + a.s_per);
-    const int nchunks = s_end > s_begin ? (int)((s_end - s_begin + SCH - 1) / SCH) : 0;
+    const int nch = s_end > s_begin ? (int)((s_end - s_begin + SCH - 1) / SCH) : 0;
 
     if (warp == 0) { tmem_alloc(tslot, L::NCOLS); tmem_relinquish(); }
-    if (tid == 0) { mbar_init(bar, 1); fence_mbar_init(); }
+    if (tid == MMA_WARP * 32) {
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&bar[B_FULLA + i], 1);
+            mbar_init(&bar[B_EMPTYA + i], 1 + 4);   // MMA commit + 4 epilogue warps
+            mbar_init(&bar[B_FULLB + i], 1);
+            mbar_init(&bar[B_EMPTYB + i], 1);
+            mbar_init(&bar[B_ZFULL + i], 1);
+            mbar_init(&bar[B_ZEMPTY + i], 4);
+        }
+        mbar_init(&bar[B_QFULL], 4);
+        mbar_init(&bar[B_QEMPTY], 1);
+        mbar_init(&bar[B_XFULL], 1);
+        mbar_init(&bar[B_ACC], 1);
+        mbar_init(&bar[B_DRAIN], 1);
+        *abort = 0;
+        fence_mbar_init();
+    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
-    const uint32_t tZ = tmem, tA = tmem + SCH, tB = tmem + SCH + RP;
-    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+    const uint32_t tA = tmem + 2 * SCH, tB = tmem + 2 * SCH + RP;
 
-    load_kmajor<OBLK, RP>(sbase + L::X, a.Xk + o0 * RP, RP);
-    uint32_t phase = 0;
-    bool ok = true;
-    int bad = 0;
-    for (int ci = 0; ci < nchunks && ok; ++ci) {
-        const int64_t s0 = s_begin + (int64_t)ci * SCH;
-        load_kmajor<SCH, RP>(sbase + L::Y, a.Yk + s0 * RP, RP);
-        load_kmajor<RP, SCH>(sbase + L::YT, a.Ytk + s0, a.S_pad);
-        if (WITH_B) load_kmajor<RP, SCH>(sbase + L::Y2T, a.Y2tk + s0, a.S_pad);
-        load_v_tile(sbase + L::VT, a.V, a.vs, s0, s_end, o0, a.O);
-        cp_async_commit();
-        cp_async_wait_all();
-        fence_proxy_async_smem();
-        __syncthreads();
-        if (tid == 0) {  // GEMM1: Z = X Y^t over K = RP
-            tc_fence_after();
-#pragma unroll
-            for (int k = 0; k < RP / 16; ++k) {
-                const uint32_t kb = 32u * k, atom = kb >> 7, within = kb & 127u;
-                mma_bf16(tZ, desc_sw128(sbase + L::X + atom * OBLK * 128 + within),
-                         desc_sw128(sbase + L::Y + atom * SCH * 128 + within),
-                         idesc_bf16(OBLK, SCH), k > 0);
+    if (warp == PRODUCER_WARP) {
+        if (lane == 0 && nch > 0) {
+            tma_prefetch_desc(&tmX); tma_prefetch_desc(&tmY); tma_prefetch_desc(&tmYt);
+            tma_prefetch_desc(&tmY2t); tma_prefetch_desc(&tmV);
+            mbar_arrive_expect_tx(&bar[B_XFULL], OBLK * RP * 2);
+            for (int at = 0; at < RP / 64; ++at)
+                tma_load_2d(sbase + L::X + at * OBLK * 128, &tmX, 64 * at, (int32_t)o0,
+                            &bar[B_XFULL]);
+            int lastA[2] = {-1, -1}, lastB[2] = {-1, -1};
+            for (int k = 0; k < nch; ++k) {
+                const int st = k & 1;
+                const uint32_t par = ((k >> 1) & 1) ^ 1;
+                const int32_t s0 = (int32_t)(s_begin + (int64_t)k * SCH);
+                if (!wait_phase(&bar[B_EMPTYA + st], par, abort)) break;
+                const uint32_t ra = sbase + L::RA + st * L::RA_STAGE;
+                mbar_arrive_expect_tx(&bar[B_FULLA + st], L::Y_BYTES + L::V_BYTES);
+                for (int at = 0; at < RP / 64; ++at)
+                    tma_load_2d(ra + at * SCH * 128, &tmY, 64 * at, s0, &bar[B_FULLA + st]);
+                tma_load_2d(ra + L::Y_BYTES, &tmV, (int32_t)o0, s0, &bar[B_FULLA + st]);
+                lastA[st] = k;
+                if (!wait_phase(&bar[B_EMPTYB + st], par, abort)) break;
+                const uint32_t rb = sbase + L::RB + st * L::RB_STAGE;
+                mbar_arrive_expect_tx(&bar[B_FULLB + st], (WITH_B ? 2 : 1) * L::YT_BYTES);
+                tma_load_2d(rb, &tmYt, s0, 0, &bar[B_FULLB + st]);
+                if (WITH_B) tma_load_2d(rb + L::YT_BYTES, &tmY2t, s0, 0, &bar[B_FULLB + st]);
+                lastB[st] = k;
             }
-            mma_commit(bar);
+            if (*abort) {  // let the copies already issued land before the CTA exits
+                drain_phase(&bar[B_XFULL], 0);
+                for (int st = 0; st < 2; ++st) {
+                    if (lastA[st] >= 0) drain_phase(&bar[B_FULLA + st], (lastA[st] >> 1) & 1);
+                    if (lastB[st] >= 0) drain_phase(&bar[B_FULLB + st], (lastB[st] >> 1) & 1);
+                }
+            }
         }
-        ok = mbar_wait_bounded(bar, phase, WAIT_LIMIT);
-        phase ^= 1;
-        ok = __syncthreads_and(ok);
-        if (!ok) break;
-        tc_fence_after();
-        // epilogue: q and qbar for row o, s = s0 .. s0 + 63
+    } else if (warp == MMA_WARP) {
+        if (lane == 0 && nch > 0) {
+            bool ok = wait_phase(&bar[B_XFULL], 0, abort);
+            for (int k = 0; ok && k <= nch; ++k) {
+                if (k < nch) {  // GEMM1 of chunk k into Z buffer k & 1
+                    const int st = k & 1;
+                    const uint32_t par = (k >> 1) & 1;
+                    if (!(ok = wait_phase(&bar[B_FULLA + st], par, abort))) break;
+                    if (!(ok = wait_phase(&bar[B_ZEMPTY + st], par ^ 1, abort))) break;
+                    tc_fence_after();
+                    const uint32_t ra = sbase + L::RA + st * L::RA_STAGE;
+                    const uint32_t tz = tmem + st * SCH;
 #pragma unroll
-        for (int h = 0; h < SCH / 32; ++h) {
-            uint32_t zr[32];
-            tmem_ld32(tZ + lane_off + 32 * h, zr);
+                    for (int kk = 0; kk < RP / 16; ++kk) {
+                        const uint32_t kb = 32u * kk, at = kb >> 7, within = kb & 127u;
+                        mma_bf16(tz, desc_sw128(sbase + L::X + at * OBLK * 128 + within),
+                                 desc_sw128(ra + at * SCH * 128 + within), idesc_bf16(OBLK, SCH),
+                                 kk > 0);
+                    }
+                    mma_commit(&bar[B_ZFULL + st]);
+                    mma_commit(&bar[B_EMPTYA + st]);
+                }
+                if (k >= 1) {  // GEMM2 / GEMM3 of chunk k - 1
+                    const int kp = k - 1, st = kp & 1;
+                    if (!(ok = wait_phase(&bar[B_QFULL], kp & 1, abort))) break;
+                    if (!(ok = wait_phase(&bar[B_FULLB + st], (kp >> 1) & 1, abort))) break;
+                    tc_fence_after();
+                    const uint32_t rb = sbase + L::RB + st * L::RB_STAGE;
+#pragma unroll
+                    for (int kk = 0; kk < SCH / 16; ++kk) {
+                        const uint32_t kb = 32u * kk;
+                        const uint32_t acc = (kp > 0 || kk > 0) ? 1u : 0u;
+                        mma_bf16(tA, desc_sw128(sbase + L::Q + kb), desc_sw128(rb + kb),
+                                 idesc_bf16(OBLK, RP), acc);
+                        if (WITH_B)
+                            mma_bf16(tB, desc_sw128(sbase + L::QB + kb),
+                                     desc_sw128(rb + L::YT_BYTES + kb), idesc_bf16(OBLK, RP), acc);
+                    }
+                    mma_commit(&bar[B_QEMPTY]);
+                    mma_commit(&bar[B_EMPTYB + st]);
+                }
+            }
+            if (ok) {
+                mma_commit(&bar[B_ACC]);
+            } else {  // no MMA may still be writing TMEM when it is released
+                mma_commit(&bar[B_DRAIN]);
+                drain_phase(&bar[B_DRAIN], 0);
+            }
+        }
+    } else {
+        // epilogue warps 0-3: thread tid owns TMEM lane tid = column o0 + tid
+        const int64_t o = o0 + tid;
+        const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+        int bad = 0;
+        bool ok = true;
+        for (int k = 0; k < nch; ++k) {
+            const int st = k & 1;
+            const uint32_t par = (k >> 1) & 1;
+            ok = wait_phase(&bar[B_ZFULL + st], par, abort);
+            ok = ok && wait_phase(&bar[B_FULLA + st], par, abort);
+            if (!(ok = __all_sync(0xffffffffu, ok))) break;   // keep the warp converged
+            tc_fence_after();
+            uint32_t z0[32], z1[32];
+            const uint32_t tz = tmem + st * SCH + lane_off;
+            tmem_ld32(tz, z0);
+            tmem_ld32(tz + 32, z1);
             tmem_ld_wait();
-            uint32_t qp[16], qbp[16];
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bar[B_ZEMPTY + st]);
+            const float* Vs = reinterpret_cast<const float*>(sm + L::RA + st * L::RA_STAGE + L::Y_BYTES);
+            uint32_t qp[32], qbp[32];
 #pragma unroll
-            for (int j = 0; j < 32; j += 2) {
+            for (int j = 0; j < SCH; j += 2) {
                 float q[2], qb[2];
 #pragma unroll
                 for (int t = 0; t < 2; ++t) {
-                    const int sl = 32 * h + j + t;
+                    const int sl = j + t;
                     float v = Vs[sl * OBLK + tid];
                     if (o >= a.O) v = 0.f;
-                    const float z = __uint_as_float(zr[j + t]);
+                    const float z = __uint_as_float(sl < 32 ? z0[sl] : z1[sl - 32]);
                     q[t] = 0.f;
                     qb[t] = 0.f;
                     if (v > 0.f) {
@@ -167,9 +258,13 @@ __global__ void __launch_bounds__(NTH, 1) k_tc_pass1(P1Args a) {
                 qp[j / 2] = pack_bf16x2(q[0], q[1]);
                 qbp[j / 2] = pack_bf16x2(qb[0], qb[1]);
             }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bar[B_EMPTYA + st]);  // V of this stage consumed
+            ok = wait_phase(&bar[B_QEMPTY], (k & 1) ^ 1, abort);
+            if (!(ok = __all_sync(0xffffffffu, ok))) break;
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const uint32_t off = sw128_offset(tid, 4 * h + c, OBLK);
+            for (int c = 0; c < SCH / 8; ++c) {
+                const uint32_t off = sw128_offset(tid, c, OBLK);
                 asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(sbase + L::Q + off),
                              "r"(qp[4 * c]), "r"(qp[4 * c + 1]), "r"(qp[4 * c + 2]),
                              "r"(qp[4 * c + 3])
@@ -181,181 +276,222 @@ __global__ void __launch_bounds__(NTH, 1) k_tc_pass1(P1Args a) {
                                  "r"(qbp[4 * c + 3])
                                  : "memory");
             }
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bar[B_QFULL]);
         }
-        fence_proxy_async_smem();
-        tc_fence_before();
-        __syncthreads();
-        if (tid == 0) {  // GEMM2 / GEMM3 over K = 64 (this chunk)
+        if (bad) atomicOr(a.status, STATUS_NONFINITE);
+        if (ok && nch > 0) ok = __all_sync(0xffffffffu, wait_phase(&bar[B_ACC], 0, abort));
+        if (ok && nch > 0) {
             tc_fence_after();
-#pragma unroll
-            for (int k = 0; k < SCH / 16; ++k) {
-                const uint32_t kb = 32u * k;
-                mma_bf16(tA, desc_sw128(sbase + L::Q + kb), desc_sw128(sbase + L::YT + kb),
-                         idesc_bf16(OBLK, RP), (ci > 0 || k > 0) ? 1u : 0u);
-                if (WITH_B)
-                    mma_bf16(tB, desc_sw128(sbase + L::QB + kb), desc_sw128(sbase + L::Y2T + kb),
-                             idesc_bf16(OBLK, RP), (ci > 0 || k > 0) ? 1u : 0u);
-            }
-            mma_commit(bar);
-        }
-        ok = mbar_wait_bounded(bar, phase, WAIT_LIMIT);
-        phase ^= 1;
-        ok = __syncthreads_and(ok);
-    }
-    if (bad) atomicOr(a.status, STATUS_NONFINITE);
-    if (!ok) {
-        if (tid == 0) atomicOr(a.status, STATUS_TIMEOUT);
-    } else if (nchunks > 0) {
-        tc_fence_after();
-        const int64_t base = (int64_t)blockIdx.y * a.R;
-#pragma unroll
-        for (int g = 0; g < RP / 32; ++g) {
-            uint32_t r32[32];
-            tmem_ld32(tA + lane_off + 32 * g, r32);
-            tmem_ld_wait();
-            if (o < a.O)
-#pragma unroll
-                for (int i = 0; i < 32; ++i) {
-                    const int64_t r = 32 * g + i;
-                    if (r < a.R) a.Apart[(base + r) * a.O + o] = __uint_as_float(r32[i]);
-                }
-            if (WITH_B) {
-                tmem_ld32(tB + lane_off + 32 * g, r32);
+            const int64_t base = (int64_t)blockIdx.y * a.R;
+#pragma unroll 1
+            for (int g = 0; g < RP / 32; ++g) {
+                uint32_t r32[32];
+                tmem_ld32(tA + lane_off + 32 * g, r32);
                 tmem_ld_wait();
                 if (o < a.O)
 #pragma unroll
                     for (int i = 0; i < 32; ++i) {
                         const int64_t r = 32 * g + i;
-                        if (r < a.R) a.Bpart[(base + r) * a.O + o] = __uint_as_float(r32[i]);
+                        if (r < a.R) a.Apart[(base + r) * a.O + o] = __uint_as_float(r32[i]);
                     }
+                if (WITH_B) {
+                    tmem_ld32(tB + lane_off + 32 * g, r32);
+                    tmem_ld_wait();
+                    if (o < a.O)
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) {
+                            const int64_t r = 32 * g + i;
+                            if (r < a.R) a.Bpart[(base + r) * a.O + o] = __uint_as_float(r32[i]);
+                        }
+                }
             }
         }
     }
     tc_fence_before();
     __syncthreads();
+    if (tid == 0 && *abort) atomicOr(a.status, STATUS_TIMEOUT);
     if (warp == 0) tmem_dealloc(tmem, L::NCOLS);
 }
 
 struct P2Args {
     int64_t S, O, R, s_per;
-    const bf16* Xmk;   // [O_pad][RP] MU candidate
-    const bf16* Xdk;   // [O_pad][RP] Newton candidate
-    const bf16* Yk;    // [S_pad][RP]
-    const float* V;
-    int64_t vs;
-    double* dpart;     // [splits][2][O]
+    double* dpart;  // [splits][2][O]
     int* status;
 };
 
 template <int RP>
-struct P2Smem {
+struct P2Layout {
     static constexpr uint32_t XM = 0;
     static constexpr uint32_t XD = XM + OBLK * RP * 2;
-    static constexpr uint32_t Y = XD + OBLK * RP * 2;
-    static constexpr uint32_t VT = Y + SCH * RP * 2;
-    static constexpr uint32_t BAR = VT + SCH * OBLK * 4;
-    static constexpr uint32_t TOTAL = BAR + 64;
-    static constexpr uint32_t NCOLS = 2 * SCH;
+    static constexpr uint32_t Y_BYTES = SCH * RP * 2;
+    static constexpr uint32_t V_BYTES = SCH * OBLK * 4;
+    static constexpr uint32_t RA = XD + OBLK * RP * 2;
+    static constexpr uint32_t RA_STAGE = Y_BYTES + V_BYTES;
+    static constexpr uint32_t BAR = RA + 2 * RA_STAGE;
+    static constexpr uint32_t TOTAL = BAR + 256;
+    static constexpr uint32_t NCOLS = 4 * SCH;  // two buffers x two candidates
+    static_assert(RA % 1024 == 0 && RA_STAGE % 1024 == 0, "tiles must be 1024-byte aligned");
+    static_assert(TOTAL + 1024 <= 232448, "shared memory budget");
 };
 
+enum { C_FULLA = 0, C_EMPTYA = 2, C_ZFULL = 4, C_ZEMPTY = 6, C_XFULL = 8, C_DRAIN = 9,
+       C_COUNT = 10 };
+
 template <int RP>
-__global__ void __launch_bounds__(NTH, 1) k_tc_pass2(P2Args a) {
-    using L = P2Smem<RP>;
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_tc_pass2(P2Args a, const __grid_constant__ CUtensorMap tmXm,
+               const __grid_constant__ CUtensorMap tmXd, const __grid_constant__ CUtensorMap tmY,
+               const __grid_constant__ CUtensorMap tmV) {
+    using L = P2Layout<RP>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* sm = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const uint32_t sbase = smem_u32(sm);
     uint64_t* bar = reinterpret_cast<uint64_t*>(sm + L::BAR);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L::BAR + 16);
-    const float* Vs = reinterpret_cast<const float*>(sm + L::VT);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L::BAR + C_COUNT * 8);
+    volatile int* abort = reinterpret_cast<volatile int*>(sm + L::BAR + C_COUNT * 8 + 8);
 
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t o0 = (int64_t)blockIdx.x * OBLK;
-    const int64_t o = o0 + tid;
     const int64_t s_begin = (int64_t)blockIdx.y * a.s_per;
     const int64_t s_end = min(a.S, s_begin + a.s_per);
-    const int nchunks = s_end > s_begin ? (int)((s_end - s_begin + SCH - 1) / SCH) : 0;
+    const int nch = s_end > s_begin ? (int)((s_end - s_begin + SCH - 1) / SCH) : 0;
 
     if (warp == 0) { tmem_alloc(tslot, L::NCOLS); tmem_relinquish(); }
-    if (tid == 0) { mbar_init(bar, 1); fence_mbar_init(); }
+    if (tid == MMA_WARP * 32) {
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&bar[C_FULLA + i], 1);
+            mbar_init(&bar[C_EMPTYA + i], 1 + 4);
+            mbar_init(&bar[C_ZFULL + i], 1);
+            mbar_init(&bar[C_ZEMPTY + i], 4);
+        }
+        mbar_init(&bar[C_XFULL], 1);
+        mbar_init(&bar[C_DRAIN], 1);
+        *abort = 0;
+        fence_mbar_init();
+    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
-    const uint32_t tM = tmem, tD = tmem + SCH;
-    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
 
-    load_kmajor<OBLK, RP>(sbase + L::XM, a.Xmk + o0 * RP, RP);
-    load_kmajor<OBLK, RP>(sbase + L::XD, a.Xdk + o0 * RP, RP);
-    double acc_m = 0.0, acc_d = 0.0;
-    uint32_t phase = 0;
-    bool ok = true;
-    int bad = 0;
-    for (int ci = 0; ci < nchunks && ok; ++ci) {
-        const int64_t s0 = s_begin + (int64_t)ci * SCH;
-        load_kmajor<SCH, RP>(sbase + L::Y, a.Yk + s0 * RP, RP);
-        load_v_tile(sbase + L::VT, a.V, a.vs, s0, s_end, o0, a.O);
-        cp_async_commit();
-        cp_async_wait_all();
-        fence_proxy_async_smem();
-        __syncthreads();
-        if (tid == 0) {
-            tc_fence_after();
-#pragma unroll
-            for (int k = 0; k < RP / 16; ++k) {
-                const uint32_t kb = 32u * k, atom = kb >> 7, within = kb & 127u;
-                const uint64_t yd = desc_sw128(sbase + L::Y + atom * SCH * 128 + within);
-                mma_bf16(tM, desc_sw128(sbase + L::XM + atom * OBLK * 128 + within), yd,
-                         idesc_bf16(OBLK, SCH), k > 0);
-                mma_bf16(tD, desc_sw128(sbase + L::XD + atom * OBLK * 128 + within), yd,
-                         idesc_bf16(OBLK, SCH), k > 0);
+    if (warp == PRODUCER_WARP) {
+        if (lane == 0 && nch > 0) {
+            tma_prefetch_desc(&tmXm); tma_prefetch_desc(&tmXd); tma_prefetch_desc(&tmY);
+            tma_prefetch_desc(&tmV);
+            mbar_arrive_expect_tx(&bar[C_XFULL], 2 * OBLK * RP * 2);
+            for (int at = 0; at < RP / 64; ++at) {
+                tma_load_2d(sbase + L::XM + at * OBLK * 128, &tmXm, 64 * at, (int32_t)o0,
+                            &bar[C_XFULL]);
+                tma_load_2d(sbase + L::XD + at * OBLK * 128, &tmXd, 64 * at, (int32_t)o0,
+                            &bar[C_XFULL]);
             }
-            mma_commit(bar);
+            int lastA[2] = {-1, -1};
+            for (int k = 0; k < nch; ++k) {
+                const int st = k & 1;
+                const int32_t s0 = (int32_t)(s_begin + (int64_t)k * SCH);
+                if (!wait_phase(&bar[C_EMPTYA + st], ((k >> 1) & 1) ^ 1, abort)) break;
+                const uint32_t ra = sbase + L::RA + st * L::RA_STAGE;
+                mbar_arrive_expect_tx(&bar[C_FULLA + st], L::Y_BYTES + L::V_BYTES);
+                for (int at = 0; at < RP / 64; ++at)
+                    tma_load_2d(ra + at * SCH * 128, &tmY, 64 * at, s0, &bar[C_FULLA + st]);
+                tma_load_2d(ra + L::Y_BYTES, &tmV, (int32_t)o0, s0, &bar[C_FULLA + st]);
+                lastA[st] = k;
+            }
+            if (*abort) {
+                drain_phase(&bar[C_XFULL], 0);
+                for (int st = 0; st < 2; ++st)
+                    if (lastA[st] >= 0) drain_phase(&bar[C_FULLA + st], (lastA[st] >> 1) & 1);
+            }
         }
-        ok = mbar_wait_bounded(bar, phase, WAIT_LIMIT);
-        phase ^= 1;
-        ok = __syncthreads_and(ok);
-        if (!ok) break;
-        tc_fence_after();
-        float run_m = 0.f, run_d = 0.f;
+    } else if (warp == MMA_WARP) {
+        if (lane == 0 && nch > 0) {
+            bool ok = wait_phase(&bar[C_XFULL], 0, abort);
+            for (int k = 0; ok && k < nch; ++k) {
+                const int st = k & 1;
+                const uint32_t par = (k >> 1) & 1;
+                if (!(ok = wait_phase(&bar[C_FULLA + st], par, abort))) break;
+                if (!(ok = wait_phase(&bar[C_ZEMPTY + st], par ^ 1, abort))) break;
+                tc_fence_after();
+                const uint32_t ra = sbase + L::RA + st * L::RA_STAGE;
+                const uint32_t tz = tmem + st * 2 * SCH;
 #pragma unroll
-        for (int h = 0; h < SCH / 32; ++h) {
-            uint32_t zm[32], zd[32];
-            tmem_ld32(tM + lane_off + 32 * h, zm);
-            tmem_ld32(tD + lane_off + 32 * h, zd);
-            tmem_ld_wait();
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                float v = Vs[(32 * h + j) * OBLK + tid];
-                if (o >= a.O) v = 0.f;
-                const float z1 = __uint_as_float(zm[j]), z2 = __uint_as_float(zd[j]);
-                float t1 = z1, t2 = z2;
-                if (v > 0.f) {
-                    if (z1 > 0.f && z2 > 0.f) {
-                        t1 -= v * __logf(z1);
-                        t2 -= v * __logf(z2);
-                    } else {
-                        bad = 1;
-                    }
+                for (int kk = 0; kk < RP / 16; ++kk) {
+                    const uint32_t kb = 32u * kk, at = kb >> 7, within = kb & 127u;
+                    const uint64_t yd = desc_sw128(ra + at * SCH * 128 + within);
+                    mma_bf16(tz, desc_sw128(sbase + L::XM + at * OBLK * 128 + within), yd,
+                             idesc_bf16(OBLK, SCH), kk > 0);
+                    mma_bf16(tz + SCH, desc_sw128(sbase + L::XD + at * OBLK * 128 + within), yd,
+                             idesc_bf16(OBLK, SCH), kk > 0);
                 }
-                run_m += t1;
-                run_d += t2;
+                mma_commit(&bar[C_ZFULL + st]);
+                mma_commit(&bar[C_EMPTYA + st]);
+            }
+            if (!ok) {
+                mma_commit(&bar[C_DRAIN]);
+                drain_phase(&bar[C_DRAIN], 0);
             }
         }
-        acc_m += (double)run_m;
-        acc_d += (double)run_d;
-        tc_fence_before();
-        __syncthreads();  // the next chunk overwrites Y and V in shared memory
-    }
-    if (bad) atomicOr(a.status, STATUS_NONFINITE);
-    if (!ok) {
-        if (tid == 0) atomicOr(a.status, STATUS_TIMEOUT);
-    } else if (o < a.O) {
-        a.dpart[((int64_t)blockIdx.y * 2 + 0) * a.O + o] = acc_m;
-        a.dpart[((int64_t)blockIdx.y * 2 + 1) * a.O + o] = acc_d;
+    } else {
+        const int64_t o = o0 + tid;
+        const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+        double acc_m = 0.0, acc_d = 0.0;
+        int bad = 0;
+        bool ok = true;
+        for (int k = 0; k < nch; ++k) {
+            const int st = k & 1;
+            const uint32_t par = (k >> 1) & 1;
+            ok = wait_phase(&bar[C_ZFULL + st], par, abort);
+            ok = ok && wait_phase(&bar[C_FULLA + st], par, abort);
+            if (!(ok = __all_sync(0xffffffffu, ok))) break;   // keep the warp converged
+            tc_fence_after();
+            const uint32_t tz = tmem + st * 2 * SCH + lane_off;
+            const float* Vs = reinterpret_cast<const float*>(sm + L::RA + st * L::RA_STAGE + L::Y_BYTES);
+            float run_m = 0.f, run_d = 0.f;
+#pragma unroll
+            for (int h = 0; h < SCH / 32; ++h) {
+                uint32_t zm[32], zd[32];
+                tmem_ld32(tz + 32 * h, zm);
+                tmem_ld32(tz + SCH + 32 * h, zd);
+                tmem_ld_wait();
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    float v = Vs[(32 * h + j) * OBLK + tid];
+                    if (o >= a.O) v = 0.f;
+                    const float z1 = __uint_as_float(zm[j]), z2 = __uint_as_float(zd[j]);
+                    float t1 = z1, t2 = z2;
+                    if (v > 0.f) {
+                        if (z1 > 0.f && z2 > 0.f) {
+                            t1 -= v * __logf(z1);
+                            t2 -= v * __logf(z2);
+                        } else {
+                            bad = 1;
+                        }
+                    }
+                    run_m += t1;
+                    run_d += t2;
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&bar[C_ZEMPTY + st]);
+                mbar_arrive(&bar[C_EMPTYA + st]);
+            }
+            acc_m += (double)run_m;
+            acc_d += (double)run_d;
+        }
+        if (bad) atomicOr(a.status, STATUS_NONFINITE);
+        if (ok && nch > 0 && o < a.O) {
+            a.dpart[((int64_t)blockIdx.y * 2 + 0) * a.O + o] = acc_m;
+            a.dpart[((int64_t)blockIdx.y * 2 + 1) * a.O + o] = acc_d;
+        }
     }
     tc_fence_before();
     __syncthreads();
+    if (tid == 0 && *abort) atomicOr(a.status, STATUS_TIMEOUT);
     if (warp == 0) tmem_dealloc(tmem, L::NCOLS);
 }
 
@@ -387,33 +523,84 @@ __global__ void k_to_bf16(const float* __restrict__ src, int64_t si, int64_t sj,
     }
 }
 
+// ------------------------------------------------------------------ host side
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// 2-D tensor map: inner extent `inner` elements, `outer` rows `row_bytes` apart.
+int make_map(CUtensorMap* m, CUtensorMapDataType dt, const void* ptr, uint64_t inner,
+             uint64_t outer, uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer,
+             CUtensorMapSwizzle swz) {
+    auto fn = encode_fn();
+    if (!fn) return DNA_ERR_CUDA;
+    if (reinterpret_cast<uintptr_t>(ptr) % 16 != 0 || row_bytes % 16 != 0) return DNA_ERR_ARG;
+    cuuint64_t dims[2] = {inner, outer};
+    cuuint64_t strides[1] = {row_bytes};
+    cuuint32_t box[2] = {box_inner, box_outer};
+    cuuint32_t estr[2] = {1, 1};
+    const CUresult r = fn(m, dt, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? DNA_OK : DNA_ERR_CUDA;
+}
+
 template <int RP, bool WITH_B>
-int launch_pass1(const P1Args& a, int64_t O_pad, int splits, cudaStream_t st) {
-    const uint32_t smem = P1Smem<RP>::TOTAL + 1024;
+int launch_pass1(const P1Args& a, const TcMaps& m, int64_t O_pad, int splits, cudaStream_t st) {
+    const uint32_t smem = P1Layout<RP>::TOTAL + 1024;
     auto k = k_tc_pass1<RP, WITH_B>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return DNA_ERR_CUDA;
     dim3 grid((unsigned)(O_pad / OBLK), (unsigned)splits);
-    k<<<grid, NTH, smem, st>>>(a);
+    k<<<grid, NTHREADS, smem, st>>>(a, m.x, m.y, m.yt, m.y2t, m.v);
     return after_launch();
 }
 
 template <int RP>
-int launch_pass2(const P2Args& a, int64_t O_pad, int splits, cudaStream_t st) {
-    const uint32_t smem = P2Smem<RP>::TOTAL + 1024;
+int launch_pass2(const P2Args& a, const TcMaps& m, int64_t O_pad, int splits, cudaStream_t st) {
+    const uint32_t smem = P2Layout<RP>::TOTAL + 1024;
     auto k = k_tc_pass2<RP>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return DNA_ERR_CUDA;
     dim3 grid((unsigned)(O_pad / OBLK), (unsigned)splits);
-    k<<<grid, NTH, smem, st>>>(a);
+    k<<<grid, NTHREADS, smem, st>>>(a, m.xm, m.xd, m.y, m.v);
     return after_launch();
 }
 
 }  // namespace tc
 
 int TcBf16::rank_pad(int64_t R) { return R <= 64 ? 64 : (R <= 128 ? 128 : 0); }
+
+int TcBf16::make_maps(TcMaps* m, const TcOperands& op, const float* V, int64_t vs,
+                      const void* Xmk, const void* Xdk) {
+    using namespace tc;
+    const uint64_t rp = (uint64_t)rank_pad(op.R);
+    const auto BF = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    const auto SW = CU_TENSOR_MAP_SWIZZLE_128B;
+    int e = make_map(&m->x, BF, op.Xk, rp, op.O_pad, rp * 2, 64, OBLK, SW);
+    if (!e) e = make_map(&m->y, BF, op.Yk, rp, op.S_pad, rp * 2, 64, SCH, SW);
+    if (!e) e = make_map(&m->yt, BF, op.Ytk, op.S_pad, rp, op.S_pad * 2, SCH, (uint32_t)rp, SW);
+    if (!e) e = make_map(&m->y2t, BF, op.Y2tk, op.S_pad, rp, op.S_pad * 2, SCH, (uint32_t)rp, SW);
+    if (!e) e = make_map(&m->xm, BF, Xmk, rp, op.O_pad, rp * 2, 64, OBLK, SW);
+    if (!e) e = make_map(&m->xd, BF, Xdk, rp, op.O_pad, rp * 2, 64, OBLK, SW);
+    if (!e)
+        e = make_map(&m->v, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, V, (uint64_t)op.O, (uint64_t)op.S,
+                     (uint64_t)vs * 4, OBLK, SCH, CU_TENSOR_MAP_SWIZZLE_NONE);
+    return e;
+}
 
 int TcBf16::to_bf16(const float* src, int64_t si, int64_t sj, int64_t rows, int64_t cols,
                     void* dst, int64_t ld, int64_t rows_pad, int64_t cols_pad, bool square,
@@ -425,37 +612,29 @@ int TcBf16::to_bf16(const float* src, int64_t si, int64_t sj, int64_t rows, int6
     return after_launch();
 }
 
-int TcBf16::pass1(const TcOperands& op, const float* V, int64_t vs, float* Apart, float* Bpart,
+int TcBf16::pass1(const TcOperands& op, const TcMaps& maps, float* Apart, float* Bpart,
                   int splits, int64_t s_per, bool with_b, int* status, cudaStream_t st) {
     tc::P1Args a{};
-    a.S = op.S; a.O = op.O; a.R = op.R; a.S_pad = op.S_pad; a.s_per = s_per;
-    a.Xk = static_cast<const tc::bf16*>(op.Xk);
-    a.Yk = static_cast<const tc::bf16*>(op.Yk);
-    a.Ytk = static_cast<const tc::bf16*>(op.Ytk);
-    a.Y2tk = static_cast<const tc::bf16*>(op.Y2tk);
-    a.V = V; a.vs = vs; a.Apart = Apart; a.Bpart = Bpart; a.status = status;
+    a.S = op.S; a.O = op.O; a.R = op.R; a.s_per = s_per;
+    a.Apart = Apart; a.Bpart = Bpart; a.status = status;
     const int rp = rank_pad(op.R);
     if (rp == 64)
-        return with_b ? tc::launch_pass1<64, true>(a, op.O_pad, splits, st)
-                      : tc::launch_pass1<64, false>(a, op.O_pad, splits, st);
+        return with_b ? tc::launch_pass1<64, true>(a, maps, op.O_pad, splits, st)
+                      : tc::launch_pass1<64, false>(a, maps, op.O_pad, splits, st);
     if (rp == 128)
-        return with_b ? tc::launch_pass1<128, true>(a, op.O_pad, splits, st)
-                      : tc::launch_pass1<128, false>(a, op.O_pad, splits, st);
+        return with_b ? tc::launch_pass1<128, true>(a, maps, op.O_pad, splits, st)
+                      : tc::launch_pass1<128, false>(a, maps, op.O_pad, splits, st);
     return DNA_ERR_UNSUPPORTED;
 }
 
-int TcBf16::pass2(const TcOperands& op, const void* Xmk, const void* Xdk, const float* V,
-                  int64_t vs, double* dpart, int splits, int64_t s_per, int* status,
-                  cudaStream_t st) {
+int TcBf16::pass2(const TcOperands& op, const TcMaps& maps, double* dpart, int splits,
+                  int64_t s_per, int* status, cudaStream_t st) {
     tc::P2Args a{};
     a.S = op.S; a.O = op.O; a.R = op.R; a.s_per = s_per;
-    a.Xmk = static_cast<const tc::bf16*>(Xmk);
-    a.Xdk = static_cast<const tc::bf16*>(Xdk);
-    a.Yk = static_cast<const tc::bf16*>(op.Yk);
-    a.V = V; a.vs = vs; a.dpart = dpart; a.status = status;
+    a.dpart = dpart; a.status = status;
     const int rp = rank_pad(op.R);
-    if (rp == 64) return tc::launch_pass2<64>(a, op.O_pad, splits, st);
-    if (rp == 128) return tc::launch_pass2<128>(a, op.O_pad, splits, st);
+    if (rp == 64) return tc::launch_pass2<64>(a, maps, op.O_pad, splits, st);
+    if (rp == 128) return tc::launch_pass2<128>(a, maps, op.O_pad, splits, st);
     return DNA_ERR_UNSUPPORTED;
 }
 

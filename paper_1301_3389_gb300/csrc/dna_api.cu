@@ -123,17 +123,19 @@ View make_view(const dna_ctx* c, bool wstep) {
 }
 
 // Split the reduction over s across CTAs.  Picks the split count that minimises the
-// number of full waves per unit of work (ceil(blocks * splits / slots) / splits), plus a
-// small charge per split for the extra partial sums it writes; each split keeps at least
-// four chunks.
-void plan_split(int64_t S, int64_t nblocks_os, int slots, int chunk, int* splits, int64_t* per) {
+// number of full waves per unit of work (ceil(blocks * splits / slots) / splits) plus the
+// partial sums each split adds (`part_per_split`, relative to the work of one split-free
+// pass) and a small fixed cost per CTA start; each split keeps at least four chunks.
+void plan_split(int64_t S, int64_t nblocks_os, int slots, int chunk, int* splits, int64_t* per,
+                double part_per_split = 0.02) {
     const int64_t chunks = (S + chunk - 1) / chunk;
     const int64_t max_sp = std::max<int64_t>(1, std::min<int64_t>(32, chunks / 4));
     int64_t best = 1;
     double best_cost = 1e300;
     for (int64_t sp = 1; sp <= max_sp; ++sp) {
         const int64_t waves = (nblocks_os * sp + slots - 1) / slots;
-        const double cost = (double)waves / (double)sp + 0.02 * (double)sp;
+        const double cost = (double)waves / (double)sp + part_per_split * (double)sp +
+                            2.0 / (double)chunks * (double)waves;
         if (cost < best_cost - 1e-12) { best_cost = cost; best = sp; }
     }
     const int64_t per_chunks = (chunks + best - 1) / best;
@@ -157,8 +159,11 @@ void plan_all(dna_ctx* c) {
             const int tob = dna::TcBf16::oblock(), tch = dna::TcBf16::chunk();
             c->pad_o[w] = (Odim + tob - 1) / tob * tob;
             c->pad_s[w] = (Sdim + tch - 1) / tch * tch;
-            plan_split(Sdim, c->pad_o[w] / tob, c->num_sms, tch, &c->tsp1[w], &c->tper1[w]);
-            plan_split(Sdim, c->pad_o[w] / tob, c->num_sms, tch, &c->tsp2[w], &c->tper2[w]);
+            // partial A, B sums per split relative to V's bytes: 2 R / S
+            const double part = 2.0 * (double)c->R / (double)Sdim;
+            plan_split(Sdim, c->pad_o[w] / tob, c->num_sms, tch, &c->tsp1[w], &c->tper1[w], part);
+            plan_split(Sdim, c->pad_o[w] / tob, c->num_sms, tch, &c->tsp2[w], &c->tper2[w],
+                       2.0 / (double)Sdim);
         }
     }
 }

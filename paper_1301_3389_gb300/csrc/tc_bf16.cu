@@ -4,7 +4,8 @@
 // Pass 1 (Algorithm 1 steps 2-5 and 10), per CTA = 128 values of o (the TMEM lanes) and
 // an s-range streamed in chunks of 64:
 //   GEMM1  Z[o, s]  = sum_r X[o, r] Y[s, r]            M = 128, N = 64, K = RP
-//   epilogue (warps 0-3, thread = lane = o): z from TMEM, v from shared memory,
+//   epilogue (warps 0-7; warp w reads TMEM lanes 32 (w % 4) .. + 31, i.e. 32 values of o,
+//          and the 32 chunk columns 32 (w / 4) .. + 31): z from TMEM, v from shared memory,
 //          q = v / z, qbar = q / z (0 where v = 0), rounded to bf16 into shared memory
 //   GEMM2  A[o, r] += sum_s Q[o, s] Yt[r, s]           M = 128, N = RP, K = 64
 //   GEMM3  B[o, r] += sum_s Qbar[o, s] Y2t[r, s]       (Y2t = (Y o Y)^t)
@@ -13,9 +14,9 @@
 // (= column o) the cost terms -v log z + z, summed in float32 over a chunk and in float64
 // across chunks.
 //
-// Both passes are warp-specialised pipelines: warp 4 issues TMA copies into a two-stage
-// ring (Y and V tiles; Y^t and (Y o Y)^t tiles), one thread of warp 5 issues the MMAs,
-// warps 0-3 run the epilogue.  Z is double-buffered in TMEM so GEMM1 of the next chunk
+// Both passes are warp-specialised pipelines: warp 8 issues TMA copies into a two-stage
+// ring (Y and V tiles; Y^t and (Y o Y)^t tiles), one thread of warp 9 issues the MMAs,
+// warps 0-7 run the epilogue.  Z is double-buffered in TMEM so GEMM1 of the next chunk
 // overlaps the epilogue of this one.  Every hand-off is an mbarrier; every wait is
 // bounded and aborts the CTA (with DNA_ERR_TIMEOUT reported) instead of hanging.
 #include <cuda.h>
@@ -31,8 +32,9 @@ namespace tc {
 
 constexpr int OBLK = 128;      // o per CTA (MMA M, TMEM lanes)
 constexpr int SCH = 64;        // s per chunk (GEMM1 N, GEMM2 K)
-constexpr int NTHREADS = 192;  // warps 0-3 epilogue, 4 TMA producer, 5 MMA issuer
-constexpr int PRODUCER_WARP = 4, MMA_WARP = 5;
+constexpr int NEPI_WARPS = 8;  // epilogue: two warps per TMEM lane quadrant
+constexpr int NTHREADS = 320;  // warps 0-7 epilogue, 8 TMA producer, 9 MMA issuer
+constexpr int PRODUCER_WARP = 8, MMA_WARP = 9;
 constexpr long long WAIT_LIMIT = 4000000000LL;  // SM cycles (about 2 s) per wait
 
 using bf16 = __nv_bfloat16;
@@ -112,13 +114,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (tid == MMA_WARP * 32) {
         for (int i = 0; i < 2; ++i) {
             mbar_init(&bar[B_FULLA + i], 1);
-            mbar_init(&bar[B_EMPTYA + i], 1 + 4);   // MMA commit + 4 epilogue warps
+            mbar_init(&bar[B_EMPTYA + i], 1 + NEPI_WARPS);  // MMA commit + epilogue warps
             mbar_init(&bar[B_FULLB + i], 1);
             mbar_init(&bar[B_EMPTYB + i], 1);
             mbar_init(&bar[B_ZFULL + i], 1);
-            mbar_init(&bar[B_ZEMPTY + i], 4);
+            mbar_init(&bar[B_ZEMPTY + i], NEPI_WARPS);
         }
-        mbar_init(&bar[B_QFULL], 4);
+        mbar_init(&bar[B_QFULL], NEPI_WARPS);
         mbar_init(&bar[B_QEMPTY], 1);
         mbar_init(&bar[B_XFULL], 1);
         mbar_init(&bar[B_ACC], 1);
@@ -217,10 +219,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
         }
     } else {
-        // epilogue warps 0-3: thread tid owns TMEM lane tid = column o0 + tid
-        const int64_t o = o0 + tid;
-        const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
-        int bad = 0;
+        // epilogue warps 0-7: lane quadrant qd = warp % 4 (o = o0 + 32 qd + lane), chunk
+        // columns 32 hf .. 32 hf + 31 with hf = warp / 4
+        const int qd = warp & 3, hf = warp >> 2;
+        const int row = 32 * qd + lane;                  // TMEM lane = row of the o-block
+        const int64_t o = o0 + row;
+        const uint32_t lane_off = (uint32_t)(32 * qd) << 16;
+        bool bad = false;
         bool ok = true;
         for (int k = 0; k < nch; ++k) {
             const int st = k & 1;
@@ -229,31 +234,28 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             ok = ok && wait_phase(&bar[B_FULLA + st], par, abort);
             if (!(ok = __all_sync(0xffffffffu, ok))) break;   // keep the warp converged
             tc_fence_after();
-            uint32_t z0[32], z1[32];
-            const uint32_t tz = tmem + st * SCH + lane_off;
-            tmem_ld32(tz, z0);
-            tmem_ld32(tz + 32, z1);
+            uint32_t zr[32];
+            tmem_ld32(tmem + st * SCH + lane_off + 32 * hf, zr);
             tmem_ld_wait();
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&bar[B_ZEMPTY + st]);
-            const float* Vs = reinterpret_cast<const float*>(sm + L::RA + st * L::RA_STAGE + L::Y_BYTES);
-            uint32_t qp[32], qbp[32];
+            // V rows s = 32 hf + j of this stage; TMA zero-fills v outside the problem
+            const float* Vs = reinterpret_cast<const float*>(sm + L::RA + st * L::RA_STAGE +
+                                                             L::Y_BYTES) + 32 * hf * OBLK + row;
+            uint32_t qp[16], qbp[16];
 #pragma unroll
-            for (int j = 0; j < SCH; j += 2) {
+            for (int j = 0; j < 32; j += 2) {
                 float q[2], qb[2];
 #pragma unroll
                 for (int t = 0; t < 2; ++t) {
-                    const int sl = j + t;
-                    float v = Vs[sl * OBLK + tid];
-                    if (o >= a.O) v = 0.f;
-                    const float z = __uint_as_float(sl < 32 ? z0[sl] : z1[sl - 32]);
-                    q[t] = 0.f;
-                    qb[t] = 0.f;
-                    if (v > 0.f) {
-                        if (z > 0.f) { q[t] = __fdividef(v, z); qb[t] = __fdividef(q[t], z); }
-                        else bad = 1;
-                    }
+                    const float v = Vs[(j + t) * OBLK];
+                    const float z = __uint_as_float(zr[j + t]);
+                    const float rz = __fdividef(1.0f, z);
+                    const bool pos = v > 0.f;
+                    bad |= pos && !(z > 0.f);
+                    q[t] = pos ? v * rz : 0.f;
+                    qb[t] = pos ? q[t] * rz : 0.f;
                 }
                 qp[j / 2] = pack_bf16x2(q[0], q[1]);
                 qbp[j / 2] = pack_bf16x2(qb[0], qb[1]);
@@ -263,8 +265,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             ok = wait_phase(&bar[B_QEMPTY], (k & 1) ^ 1, abort);
             if (!(ok = __all_sync(0xffffffffu, ok))) break;
 #pragma unroll
-            for (int c = 0; c < SCH / 8; ++c) {
-                const uint32_t off = sw128_offset(tid, c, OBLK);
+            for (int c = 0; c < 4; ++c) {
+                const uint32_t off = sw128_offset(row, 4 * hf + c, OBLK);
                 asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(sbase + L::Q + off),
                              "r"(qp[4 * c]), "r"(qp[4 * c + 1]), "r"(qp[4 * c + 2]),
                              "r"(qp[4 * c + 3])
@@ -285,8 +287,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (ok && nch > 0) {
             tc_fence_after();
             const int64_t base = (int64_t)blockIdx.y * a.R;
+            // this warp writes r-groups g = hf, hf + 2, ... of 32 columns
 #pragma unroll 1
-            for (int g = 0; g < RP / 32; ++g) {
+            for (int g = hf; g < RP / 32; g += 2) {
                 uint32_t r32[32];
                 tmem_ld32(tA + lane_off + 32 * g, r32);
                 tmem_ld_wait();
@@ -329,7 +332,8 @@ struct P2Layout {
     static constexpr uint32_t V_BYTES = SCH * OBLK * 4;
     static constexpr uint32_t RA = XD + OBLK * RP * 2;
     static constexpr uint32_t RA_STAGE = Y_BYTES + V_BYTES;
-    static constexpr uint32_t BAR = RA + 2 * RA_STAGE;
+    static constexpr uint32_t RED = RA + 2 * RA_STAGE;   // [2][128] float64 half-sums
+    static constexpr uint32_t BAR = RED + 2 * OBLK * 8;
     static constexpr uint32_t TOTAL = BAR + 256;
     static constexpr uint32_t NCOLS = 4 * SCH;  // two buffers x two candidates
     static_assert(RA % 1024 == 0 && RA_STAGE % 1024 == 0, "tiles must be 1024-byte aligned");
@@ -363,9 +367,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (tid == MMA_WARP * 32) {
         for (int i = 0; i < 2; ++i) {
             mbar_init(&bar[C_FULLA + i], 1);
-            mbar_init(&bar[C_EMPTYA + i], 1 + 4);
+            mbar_init(&bar[C_EMPTYA + i], 1 + NEPI_WARPS);
             mbar_init(&bar[C_ZFULL + i], 1);
-            mbar_init(&bar[C_ZEMPTY + i], 4);
+            mbar_init(&bar[C_ZEMPTY + i], NEPI_WARPS);
         }
         mbar_init(&bar[C_XFULL], 1);
         mbar_init(&bar[C_DRAIN], 1);
@@ -435,10 +439,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
         }
     } else {
-        const int64_t o = o0 + tid;
-        const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+        const int qd = warp & 3, hf = warp >> 2;
+        const int row = 32 * qd + lane;
+        const int64_t o = o0 + row;
+        const uint32_t lane_off = (uint32_t)(32 * qd) << 16;
         double acc_m = 0.0, acc_d = 0.0;
-        int bad = 0;
+        bool bad = false;
         bool ok = true;
         for (int k = 0; k < nch; ++k) {
             const int st = k & 1;
@@ -447,46 +453,43 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             ok = ok && wait_phase(&bar[C_FULLA + st], par, abort);
             if (!(ok = __all_sync(0xffffffffu, ok))) break;   // keep the warp converged
             tc_fence_after();
-            const uint32_t tz = tmem + st * 2 * SCH + lane_off;
-            const float* Vs = reinterpret_cast<const float*>(sm + L::RA + st * L::RA_STAGE + L::Y_BYTES);
-            float run_m = 0.f, run_d = 0.f;
-#pragma unroll
-            for (int h = 0; h < SCH / 32; ++h) {
-                uint32_t zm[32], zd[32];
-                tmem_ld32(tz + 32 * h, zm);
-                tmem_ld32(tz + SCH + 32 * h, zd);
-                tmem_ld_wait();
-#pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    float v = Vs[(32 * h + j) * OBLK + tid];
-                    if (o >= a.O) v = 0.f;
-                    const float z1 = __uint_as_float(zm[j]), z2 = __uint_as_float(zd[j]);
-                    float t1 = z1, t2 = z2;
-                    if (v > 0.f) {
-                        if (z1 > 0.f && z2 > 0.f) {
-                            t1 -= v * __logf(z1);
-                            t2 -= v * __logf(z2);
-                        } else {
-                            bad = 1;
-                        }
-                    }
-                    run_m += t1;
-                    run_d += t2;
-                }
-            }
+            const uint32_t tz = tmem + st * 2 * SCH + lane_off + 32 * hf;
+            uint32_t zm[32], zd[32];
+            tmem_ld32(tz, zm);
+            tmem_ld32(tz + SCH, zd);
+            tmem_ld_wait();
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) {
-                mbar_arrive(&bar[C_ZEMPTY + st]);
-                mbar_arrive(&bar[C_EMPTYA + st]);
+            if (lane == 0) mbar_arrive(&bar[C_ZEMPTY + st]);
+            const float* Vs = reinterpret_cast<const float*>(sm + L::RA + st * L::RA_STAGE +
+                                                             L::Y_BYTES) + 32 * hf * OBLK + row;
+            float run_m = 0.f, run_d = 0.f;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const float v = Vs[j * OBLK];
+                const float z1 = __uint_as_float(zm[j]), z2 = __uint_as_float(zd[j]);
+                const bool pos = v > 0.f;
+                bad |= pos && !(z1 > 0.f && z2 > 0.f);
+                const float l1 = __logf(z1), l2 = __logf(z2);
+                run_m += pos ? z1 - v * l1 : z1;
+                run_d += pos ? z2 - v * l2 : z2;
             }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bar[C_EMPTYA + st]);
             acc_m += (double)run_m;
             acc_d += (double)run_d;
         }
         if (bad) atomicOr(a.status, STATUS_NONFINITE);
-        if (ok && nch > 0 && o < a.O) {
-            a.dpart[((int64_t)blockIdx.y * 2 + 0) * a.O + o] = acc_m;
-            a.dpart[((int64_t)blockIdx.y * 2 + 1) * a.O + o] = acc_d;
+        // combine the two column halves of each o in a fixed order
+        double* red = reinterpret_cast<double*>(sm + L::RED);
+        if (hf == 1) {
+            red[row] = acc_m;
+            red[OBLK + row] = acc_d;
+        }
+        asm volatile("bar.sync 1, %0;" ::"r"(NEPI_WARPS * 32) : "memory");
+        if (hf == 0 && ok && nch > 0 && !*abort && o < a.O) {
+            a.dpart[((int64_t)blockIdx.y * 2 + 0) * a.O + o] = acc_m + red[row];
+            a.dpart[((int64_t)blockIdx.y * 2 + 1) * a.O + o] = acc_d + red[OBLK + row];
         }
     }
     tc_fence_before();

@@ -87,7 +87,7 @@ struct Pass1Cfg {
 // Pass 1: raw A and B sums for one (o-block, r-block, s-split).
 // grid = (ceil(O / OB), ceil(R / RB), splits); Apart/Bpart are [splits][R][O].
 template <typename Tp, int RB, bool WITH_B>
-__global__ void __launch_bounds__(NT) k_pass1(View v, Tp* __restrict__ Apart,
+__global__ void __launch_bounds__(NT, sizeof(Tp) == 4 ? 2 : 1) k_pass1(View v, Tp* __restrict__ Apart,
                                               Tp* __restrict__ Bpart, int64_t s_per,
                                               int* __restrict__ status) {
     using C = Pass1Cfg<Tp, RB>;
@@ -120,11 +120,16 @@ __global__ void __launch_bounds__(NT) k_pass1(View v, Tp* __restrict__ Apart,
     int bad = 0;
 
     for (int64_t s0 = s_begin; s0 < s_end; s0 += SB) {
-        Tp z[4][4];
+        Tp z[4][4], vpre[4][4];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) z[i][j] = Tp(0);
+            for (int j = 0; j < 4; ++j) {
+                z[i][j] = Tp(0);
+                // issue this chunk's V loads now; they complete behind the z-tile FMAs
+                const int64_t s = s0 + zs + i, o = o0 + zo + j;
+                vpre[i][j] = (s < s_end && o < v.O) ? __ldg(V + s * v.vs + o) : Tp(0);
+            }
         for (int p = 0; p < npieces; ++p) {
             if (npieces > 1) load_tile<Tp, RB, OB>(Xs, X, v.xr, v.xo, (int64_t)p * RB, o0, v.R, v.O);
             load_tile<Tp, RB, SB>(Yt, Y, v.yr, v.ys, (int64_t)p * RB, s0, v.R, v.S);
@@ -135,11 +140,9 @@ __global__ void __launch_bounds__(NT) k_pass1(View v, Tp* __restrict__ Apart,
         // q = v / z and qbar = v / z^2, zero where v = 0 (note after Algorithm 1)
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            const int64_t s = s0 + zs + i;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const int64_t o = o0 + zo + j;
-                const Tp vv = (s < s_end && o < v.O) ? __ldg(V + s * v.vs + o) : Tp(0);
+                const Tp vv = vpre[i][j];
                 Tp q = Tp(0), qb = Tp(0);
                 if (vv > Tp(0)) {
                     const Tp zz = z[i][j];
@@ -202,7 +205,7 @@ struct Pass2Cfg {
 // FULL = true:  sum_{v>0} v log(v / z) - sum v + sum z (eq. 1, for dna_kl).
 // X_c(r, o) at Xc[r * xr + o * xo].  dpart is [splits][NC][O] float64.
 template <typename Tp, int RB, int NC, bool FULL>
-__global__ void __launch_bounds__(NT) k_pass2(View v, const Tp* __restrict__ X0,
+__global__ void __launch_bounds__(NT, sizeof(Tp) == 4 ? 2 : 1) k_pass2(View v, const Tp* __restrict__ X0,
                                               const Tp* __restrict__ X1, int64_t xr, int64_t xo,
                                               double* __restrict__ dpart, int64_t s_per,
                                               int* __restrict__ status) {
@@ -230,13 +233,20 @@ __global__ void __launch_bounds__(NT) k_pass2(View v, const Tp* __restrict__ X0,
     }
     int bad = 0;
     for (int64_t s0 = s_begin; s0 < s_end; s0 += SB) {
-        Tp z[NC][4][4];
+        Tp z[NC][4][4], vpre[4][4];
 #pragma unroll
         for (int c = 0; c < NC; ++c)
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) z[c][i][j] = Tp(0);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int64_t s = s0 + zs + i, o = o0 + zo + j;
+                vpre[i][j] = (s < s_end && o < v.O) ? __ldg(V + s * v.vs + o) : Tp(0);
+            }
         for (int p = 0; p < npieces; ++p) {
             if (npieces > 1) {
                 load_tile<Tp, RB, OB>(Xs, X0, xr, xo, (int64_t)p * RB, o0, v.R, v.O);
@@ -257,8 +267,7 @@ __global__ void __launch_bounds__(NT) k_pass2(View v, const Tp* __restrict__ X0,
             for (int c = 0; c < NC; ++c) run[c] = Tp(0);
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                const int64_t s = s0 + zs + i;
-                const Tp vv = (s < s_end && o < v.O) ? __ldg(V + s * v.vs + o) : Tp(0);
+                const Tp vv = vpre[i][j];
 #pragma unroll
                 for (int c = 0; c < NC; ++c) {
                     const Tp zz = z[c][i][j];
@@ -343,8 +352,8 @@ __global__ void __launch_bounds__(256) k_candidates(View v, const double* __rest
     if (!live) return;
     double tot = 0.0;
     for (int k = 0; k < 8; ++k) tot += red[k][tx];
-    const double sc = tot > 0.0 ? v.vsum[o] / tot : 1.0;   // eq. 10
-    for (int64_t r = ty; r < v.R; r += 8) Xdna[r * v.O + o] = (Tp)((double)Xdna[r * v.O + o] * sc);
+    const Tp sc = (Tp)(tot > 0.0 ? v.vsum[o] / tot : 1.0);   // eq. 10
+    for (int64_t r = ty; r < v.R; r += 8) Xdna[r * v.O + o] *= sc;
 }
 
 // MU in place (eq. 11): x(r, o) <- x(r, o) * raw_a(r, o) / c_r.
@@ -435,56 +444,60 @@ __global__ void k_colsum_part(const Tp* __restrict__ M, int64_t n, int64_t R, in
     }
 }
 
-// out[r] = sum over splits of part[split][r] + reg (fixed order), zero sum guarded.
+// out[r] = sum over splits of part[split][r] + reg, zero sum guarded.  One warp per r:
+// lane l adds splits l, l + 32, ...; then a fixed butterfly over the lanes.
 template <int UNUSED = 0>
 __global__ void k_colsum_final(const double* __restrict__ part, int nsplit, int64_t R, double reg,
                                double* __restrict__ out, bool guard) {
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t r = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x & 31;
     if (r >= R) return;
     double t = 0.0;
-    for (int k = 0; k < nsplit; ++k) t += part[(int64_t)k * R + r];
-    out[r] = nonzero_sum(t + reg, guard);
+    for (int k = lane; k < nsplit; k += 32) t += part[(int64_t)k * R + r];
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) t += __shfl_xor_sync(0xffffffffu, t, m);
+    if (lane == 0) out[r] = nonzero_sum(t + reg, guard);
 }
 
-// Row-sum variant for unit-stride rows (element (r, i) at M[r * ld + i]): one CTA per r.
+// Row-sum variant for unit-stride rows (element (r, i) at M[r * ld + i]): one CTA of 256
+// threads per r; per-thread sums, then fixed-order warp butterflies and a final pass over
+// the 8 warp sums.
 template <typename Tp>
-__global__ void k_row_sums(const Tp* __restrict__ M, int64_t n, int64_t ld, double reg,
-                           double* __restrict__ out, bool guard) {
-    __shared__ double red[256];
+__global__ void __launch_bounds__(256) k_row_sums(const Tp* __restrict__ M, int64_t n, int64_t ld,
+                                                  double reg, double* __restrict__ out, bool guard) {
+    __shared__ double red[8];
     const int64_t r = blockIdx.x;
     double s = 0.0;
     for (int64_t i = threadIdx.x; i < n; i += 256) s += (double)M[r * ld + i];
-    red[threadIdx.x] = s;
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
     __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
-        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-        __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < 8; ++k) t += red[k];
+        out[r] = nonzero_sum(t + reg, guard);
     }
-    if (threadIdx.x == 0) out[r] = nonzero_sum(red[0] + reg, guard);
 }
 
-// X(r, o) /= f_r for all (r, o); Y(s, r) *= f_r for all (s, r).  Thread per element of
-// the underlying dense buffers (X: R*O, Y: S*R), decoded through the strides.
+// X(r, o) /= f_r for all (r, o) and Y(s, r) *= f_r for all (s, r) (steps 1, 16, 29).
+// blockIdx.y < ceil(R / 8) covers X, the rest covers Y; threadIdx.y picks r within a group
+// of 8 and threadIdx.x walks the other index, so no element needs an integer division.
 template <typename Tp>
-__global__ void k_rescale(View v, const double* __restrict__ f) {
-    const int64_t nx = v.R * v.O, ny = v.S * v.R;
-    Tp* __restrict__ X = static_cast<Tp*>(v.X);
-    Tp* __restrict__ Y = const_cast<Tp*>(static_cast<const Tp*>(v.Y));
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nx + ny;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        if (e < nx) {
-            // X dense in memory: the unit stride is xo (H) or xr (W^t)
-            int64_t r, o;
-            if (v.xo == 1) { r = e / v.O; o = e % v.O; } else { o = e / v.R; r = e % v.R; }
-            const int64_t idx = r * v.xr + o * v.xo;
-            X[idx] = (Tp)((double)X[idx] / f[r]);
-        } else {
-            const int64_t k = e - nx;
-            int64_t s, r;
-            if (v.yr == 1) { s = k / v.R; r = k % v.R; } else { r = k / v.S; s = k % v.S; }
-            const int64_t idx = s * v.ys + r * v.yr;
-            Y[idx] = (Tp)((double)Y[idx] * f[r]);
-        }
+__global__ void __launch_bounds__(256) k_rescale(View v, const double* __restrict__ f,
+                                                 int64_t xblocks) {
+    const int64_t rg = (int64_t)blockIdx.y;
+    const bool isx = rg < xblocks;
+    const int64_t r = (isx ? rg : rg - xblocks) * 8 + threadIdx.y;
+    if (r >= v.R) return;
+    const Tp fr = (Tp)f[r];
+    const int64_t n = isx ? v.O : v.S;
+    Tp* __restrict__ M = isx ? static_cast<Tp*>(v.X)
+                             : const_cast<Tp*>(static_cast<const Tp*>(v.Y));
+    const int64_t stride_r = isx ? v.xr : v.yr, stride_i = isx ? v.xo : v.ys;
+    for (int64_t i = (int64_t)blockIdx.x * 32 + threadIdx.x; i < n; i += (int64_t)gridDim.x * 32) {
+        const int64_t idx = r * stride_r + i * stride_i;
+        M[idx] = isx ? M[idx] / fr : M[idx] * fr;
     }
 }
 

@@ -108,7 +108,7 @@ int factor_sums(const Tp* M, int64_t n, int64_t R, int64_t si, int64_t sr, doubl
     dim3 grid((unsigned)((R + 31) / 32), (unsigned)nsplit);
     k_colsum_part<Tp><<<grid, blk, 0, st>>>(M, n, R, si, sr, rows_per, work);
     if (launch_status()) return DNA_ERR_CUDA;
-    k_colsum_final<<<(unsigned)((R + 127) / 128), 128, 0, st>>>(work, (int)nsplit, R, reg, out, true);
+    k_colsum_final<<<(unsigned)((R + 7) / 8), 256, 0, st>>>(work, (int)nsplit, R, reg, out, true);
     return launch_status();
 }
 }  // namespace simt
@@ -129,10 +129,11 @@ int Simt<Tp>::factor_sums_x(const View& v, double reg, double* out, double* work
 
 template <typename Tp>
 int Simt<Tp>::rescale(const View& v, const double* f, cudaStream_t st) {
-    const int64_t n = v.R * v.O + v.S * v.R;
-    int64_t blocks = (n + 255) / 256;
-    if (blocks > 4096) blocks = 4096;
-    simt::k_rescale<Tp><<<(unsigned)blocks, 256, 0, st>>>(v, f);
+    const int64_t rgroups = (v.R + 7) / 8;
+    const int64_t longest = std::max(v.O, v.S);
+    const int64_t bx = std::max<int64_t>(1, std::min<int64_t>(64, (longest + 511) / 512));
+    dim3 grid((unsigned)bx, (unsigned)(2 * rgroups));
+    simt::k_rescale<Tp><<<grid, dim3(32, 8), 0, st>>>(v, f, rgroups);
     return simt::launch_status();
 }
 

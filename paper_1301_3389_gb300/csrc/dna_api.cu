@@ -337,12 +337,9 @@ int half_step_tc(dna_ctx* c, int wstep, bool mu_only) {
 
     int e = phase(c, DNA_PHASE_SUMS, 1, [&] { return S::factor_sums_y(v, reg_den, c->c, c->fwork, st); });
     if (e) return e;
-    e = phase(c, DNA_PHASE_OPERANDS, mu_only ? 3 : 4, [&] {
+    e = phase(c, DNA_PHASE_OPERANDS, 2, [&] {
         int r = TC::to_bf16(X, v.xo, v.xr, v.O, v.R, c->Xk, rp, op.O_pad, rp, false, st);
-        if (!r) r = TC::to_bf16(Y, v.ys, v.yr, v.S, v.R, c->Yk, rp, op.S_pad, rp, false, st);
-        if (!r) r = TC::to_bf16(Y, v.yr, v.ys, v.R, v.S, c->Ytk, op.S_pad, rp, op.S_pad, false, st);
-        if (!r && !mu_only)
-            r = TC::to_bf16(Y, v.yr, v.ys, v.R, v.S, c->Y2tk, op.S_pad, rp, op.S_pad, true, st);
+        if (!r) r = TC::y_operands(Y, v.ys, v.yr, op, !mu_only, st);
         return r;
     });
     if (e) return e;

@@ -106,6 +106,9 @@ struct TcBf16 {
     static int to_bf16(const float* src, int64_t si, int64_t sj, int64_t rows, int64_t cols,
                        void* dst, int64_t ld, int64_t rows_pad, int64_t cols_pad, bool square,
                        cudaStream_t st);
+    // Yk, Ytk and (if with_sq) Y2tk of `op` from y(s, r) = Y[s * ys + r * yr] in one pass
+    static int y_operands(const float* Y, int64_t ys, int64_t yr, const TcOperands& op,
+                          bool with_sq, cudaStream_t st);
     // TMA descriptors for the operand buffers of `op`, V_so (leading dimension vs floats,
     // 16-byte aligned rows) and the bf16 candidates Xmk, Xdk ([O_pad][RP])
     static int make_maps(TcMaps* m, const TcOperands& op, const float* V, int64_t vs,

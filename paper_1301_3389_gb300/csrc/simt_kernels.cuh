@@ -39,6 +39,9 @@ __device__ __forceinline__ void ld4(const double* p, double (&v)[4]) {
 }
 __device__ __forceinline__ float dev_log(float x) { return logf(x); }
 __device__ __forceinline__ double dev_log(double x) { return log(x); }
+// a / b: the fast-division intrinsic in float32 (a few ulp), exact division in float64
+__device__ __forceinline__ float dev_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double dev_div(double a, double b) { return a / b; }
 
 // Load a ROWS x COLS tile into shared memory (leading dimension LD):
 //   sm[i][j] = g[(i0 + i) * si + (j0 + j) * sj] when i0 + i < ni and j0 + j < nj, else 0.
@@ -327,18 +330,18 @@ __global__ void __launch_bounds__(256) k_candidates(View v, const double* __rest
                 ra += Apart[((int64_t)sp * v.R + r) * v.O + o];
                 rb += Bpart[((int64_t)sp * v.R + r) * v.O + o];
             }
-            const Tp cr = (Tp)c[r];
-            const Tp a = ra / cr - Tp(1);         // eq. 7
-            const Tp b = rb / cr;                 // eq. 14
+            const Tp ic = (Tp)(1.0 / c[r]);
+            const Tp a = ra * ic - Tp(1);         // eq. 7
+            const Tp b = rb * ic;                 // eq. 14
             const Tp x = X[r * v.xr + o * v.xo];
             const Tp xmu = x + a * x;             // eq. 11 (step 6)
             Tp xd;
             if (a < Tp(0)) {                      // eq. 15 with the eps floor on the gain
                 const Tp xb = x * b;
-                const Tp g = xb / (xb - a);
+                const Tp g = dev_div(xb, xb - a);
                 xd = x * (g > eps ? g : eps);
             } else {                              // eq. 17, gain capped at 1 + alpha
-                const Tp st = b > Tp(0) ? a / b : Tp(0);
+                const Tp st = b > Tp(0) ? dev_div(a, b) : Tp(0);
                 const Tp cap = alpha * x;
                 xd = x + (st < cap ? st : cap);
             }
@@ -467,8 +470,17 @@ __global__ void __launch_bounds__(256) k_row_sums(const Tp* __restrict__ M, int6
                                                   double reg, double* __restrict__ out, bool guard) {
     __shared__ double red[8];
     const int64_t r = blockIdx.x;
-    double s = 0.0;
-    for (int64_t i = threadIdx.x; i < n; i += 256) s += (double)M[r * ld + i];
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;   // four independent chains
+    const Tp* __restrict__ row = M + r * ld;
+    int64_t i = threadIdx.x;
+    for (; i + 768 < n; i += 1024) {
+        s0 += (double)row[i];
+        s1 += (double)row[i + 256];
+        s2 += (double)row[i + 512];
+        s3 += (double)row[i + 768];
+    }
+    for (; i < n; i += 256) s0 += (double)row[i];
+    double s = (s0 + s1) + (s2 + s3);
 #pragma unroll
     for (int m = 16; m > 0; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
@@ -490,14 +502,14 @@ __global__ void __launch_bounds__(256) k_rescale(View v, const double* __restric
     const bool isx = rg < xblocks;
     const int64_t r = (isx ? rg : rg - xblocks) * 8 + threadIdx.y;
     if (r >= v.R) return;
-    const Tp fr = (Tp)f[r];
+    const Tp fr = isx ? (Tp)(1.0 / f[r]) : (Tp)f[r];   // X is divided, Y multiplied
     const int64_t n = isx ? v.O : v.S;
     Tp* __restrict__ M = isx ? static_cast<Tp*>(v.X)
                              : const_cast<Tp*>(static_cast<const Tp*>(v.Y));
     const int64_t stride_r = isx ? v.xr : v.yr, stride_i = isx ? v.xo : v.ys;
     for (int64_t i = (int64_t)blockIdx.x * 32 + threadIdx.x; i < n; i += (int64_t)gridDim.x * 32) {
         const int64_t idx = r * stride_r + i * stride_i;
-        M[idx] = isx ? M[idx] / fr : M[idx] * fr;
+        M[idx] *= fr;
     }
 }
 

@@ -526,6 +526,38 @@ __global__ void k_to_bf16(const float* __restrict__ src, int64_t si, int64_t sj,
     }
 }
 
+// The three operands derived from Y in one pass over a 32 x 32 tile of y(s, r):
+//   Yk[s][r] = bf16(y), Ytk[r][s] = bf16(y), Y2tk[r][s] = bf16(y * y), zero-padded.
+// y(s, r) at Y[s * ys + r * yr] with ys == 1 or yr == 1.  Grid covers S_pad x RP.
+__global__ void k_y_operands(const float* __restrict__ Y, int64_t ys, int64_t yr, int64_t S,
+                             int64_t R, bf16* __restrict__ Yk, int64_t rp,
+                             bf16* __restrict__ Ytk, bf16* __restrict__ Y2tk, int64_t s_pad,
+                             bool with_sq) {
+    __shared__ float tile[32][33];   // tile[s][r]
+    const int64_t s0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    if (yr == 1) {   // rows of Y contiguous along r
+        for (int k = ty; k < 32; k += 8) {
+            const int64_t s = s0 + k, r = r0 + tx;
+            tile[k][tx] = (s < S && r < R) ? Y[s * ys + r] : 0.f;
+        }
+    } else {         // contiguous along s
+        for (int k = ty; k < 32; k += 8) {
+            const int64_t r = r0 + k, s = s0 + tx;
+            tile[tx][k] = (s < S && r < R) ? Y[s + r * yr] : 0.f;
+        }
+    }
+    __syncthreads();
+    for (int k = ty; k < 32; k += 8) {
+        const int64_t s = s0 + k, r = r0 + tx;     // Yk: r fastest
+        Yk[s * rp + r] = __float2bfloat16_rn(tile[k][tx]);
+        const int64_t r2 = r0 + k, s2 = s0 + tx;   // Ytk, Y2tk: s fastest
+        const float y = tile[tx][k];
+        Ytk[r2 * s_pad + s2] = __float2bfloat16_rn(y);
+        if (with_sq) Y2tk[r2 * s_pad + s2] = __float2bfloat16_rn(y * y);
+    }
+}
+
 // ------------------------------------------------------------------ host side
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -612,6 +644,17 @@ int TcBf16::to_bf16(const float* src, int64_t si, int64_t sj, int64_t rows, int6
     dim3 grid((unsigned)((cols_pad + 31) / 32), (unsigned)((rows_pad + 31) / 32));
     tc::k_to_bf16<<<grid, blk, 0, st>>>(src, si, sj, rows, cols, static_cast<tc::bf16*>(dst), ld,
                                          square);
+    return after_launch();
+}
+
+int TcBf16::y_operands(const float* Y, int64_t ys, int64_t yr, const TcOperands& op,
+                       bool with_sq, cudaStream_t st) {
+    const int64_t rp = rank_pad(op.R);
+    dim3 grid((unsigned)(op.S_pad / 32), (unsigned)(rp / 32));
+    tc::k_y_operands<<<grid, dim3(32, 8), 0, st>>>(
+        Y, ys, yr, op.S, op.R, static_cast<tc::bf16*>(const_cast<void*>(op.Yk)), rp,
+        static_cast<tc::bf16*>(const_cast<void*>(op.Ytk)),
+        static_cast<tc::bf16*>(const_cast<void*>(op.Y2tk)), op.S_pad, with_sq);
     return after_launch();
 }
 

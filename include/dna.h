@@ -160,6 +160,61 @@ int dna_profile(dna_ctx* ctx, int enable);
  * Synchronises the stream. */
 int dna_phase_times(dna_ctx* ctx, double* ms, int64_t* launches, int n);
 
+/* ---------------------------------------------------------------- batching form
+ * Many independent KL-NMF problems of uneven sizes (count of them; problem q is
+ * N[q] x T[q] of rank R[q] <= 64), FP32 form.  Each phase of a DNA half-step runs for all
+ * problems in one persistent grouped launch (a tile list over (problem, block, split)),
+ * and dna_group_iterate can replay one whole iteration as a captured CUDA graph.  Every
+ * problem follows exactly the single-problem algorithm above (Algorithm 1); only the
+ * order of the split sums may differ.  The group owns a private stream that is ordered
+ * after and before the caller's stream on every call. */
+typedef struct dna_group dna_group;
+
+/* Create a group of `count` problems with sizes N[q], T[q], R[q] (host arrays); opts may
+ * be NULL.  Only DNA_F32 is supported (R[q] > 64 or another dtype: DNA_ERR_UNSUPPORTED).
+ * Allocates the whole workspace at once. */
+int dna_group_create(int count, const int64_t* N, const int64_t* T, const int64_t* R,
+                     const dna_opts* opts, dna_group** out);
+
+/* Attach the caller's device buffers: host arrays of `count` device pointers V[q]
+ * (N[q] x T[q], leading dimension ldv[q] >= T[q]; ldv may be NULL for ldv[q] = T[q]),
+ * W[q] (N[q] x R[q]) and H[q] (R[q] x T[q]), float32.  Queues the one-time sums and
+ * transposes of every V. */
+int dna_group_bind(dna_group* g, const void* const* V, const int64_t* ldv, void* const* W,
+                   void* const* H);
+
+/* Caller's stream (a cudaStream_t; NULL = legacy default stream). */
+int dna_group_set_stream(dna_group* g, void* stream);
+
+/* dna_normalize for every problem (which = 1: steps 1/29, which = 0: step 16). */
+int dna_group_normalize(dna_group* g, int which);
+
+/* dna_step_H / dna_step_W for every problem, one grouped launch per phase. */
+int dna_group_step_H(dna_group* g);
+int dna_group_step_W(dna_group* g);
+
+/* iters DNA iterations of every problem; with dna_group_use_graph(g, 1) the first call
+ * captures one iteration as a CUDA graph and every iteration replays it. */
+int dna_group_iterate(dna_group* g, int iters);
+int dna_group_use_graph(dna_group* g, int enable);
+
+/* Autotuner: time `reps` iterations for each candidate split size (rows of s per tile of
+ * the reduction) and keep the fastest; W and H are restored afterwards.  The chosen
+ * size is written to *rows_out (may be NULL).  Synchronises. */
+int dna_group_autotune(dna_group* g, int reps, int64_t* rows_out);
+
+/* d_KL (eq. 1) of every problem into out[0 .. count) (host).  Synchronises. */
+int dna_group_kl(dna_group* g, double* out);
+
+/* Synchronise and return the sticky status of the group's kernels. */
+int dna_group_get_status(dna_group* g);
+
+/* Kernel launches of one grouped iteration (both half-steps). */
+int64_t dna_group_launches_per_iteration(dna_group* g);
+
+/* Release the group and its workspace. */
+void dna_group_destroy(dna_group* g);
+
 /* Capacity, in float64 partial sums, of the static scratch of dna_kl_noalloc. */
 #define DNA_KL_NOALLOC_MAX_PARTIALS (1 << 20)
 

@@ -64,6 +64,19 @@ def _load() -> ctypes.CDLL:
         "dna_profile": (I, [P, I]),
         "dna_phase_times": (I, [P, P, P, I]),
         "dna_kl_noalloc": (I, [P, I64, P, P, I64, I64, I64, P, P]),
+        "dna_group_create": (I, [I, P, P, P, ctypes.POINTER(dna_opts), ctypes.POINTER(P)]),
+        "dna_group_bind": (I, [P, P, P, P, P]),
+        "dna_group_set_stream": (I, [P, P]),
+        "dna_group_normalize": (I, [P, I]),
+        "dna_group_step_H": (I, [P]),
+        "dna_group_step_W": (I, [P]),
+        "dna_group_iterate": (I, [P, I]),
+        "dna_group_use_graph": (I, [P, I]),
+        "dna_group_autotune": (I, [P, I, P]),
+        "dna_group_kl": (I, [P, P]),
+        "dna_group_get_status": (I, [P]),
+        "dna_group_launches_per_iteration": (I64, [P]),
+        "dna_group_destroy": (None, [P]),
         "dna_destroy": (None, [P]),
         "dna_strerror": (ctypes.c_char_p, [I]),
     }
@@ -217,6 +230,81 @@ def dna_kl_noalloc(V, W, H, out, stream=None, ldv: int | None = None) -> None:
         ldv = V.stride(0)
     _check(LIB.dna_kl_noalloc(_ptr(V), ldv, _ptr(W), _ptr(H), N, T, R, _ptr(out),
                               _stream(stream)), "dna_kl_noalloc")
+
+
+def _i64_array(vals):
+    import numpy as np
+    return np.ascontiguousarray(np.asarray(vals, dtype=np.int64))
+
+
+def _ptr_array(tensors):
+    import numpy as np
+    return np.ascontiguousarray(np.asarray([_ptr(t) for t in tensors], dtype=np.uint64))
+
+
+def dna_group_create(N, T, R, opts: dna_opts | None = None) -> int:
+    n, t, r = _i64_array(N), _i64_array(T), _i64_array(R)
+    h = ctypes.c_void_p()
+    _check(LIB.dna_group_create(len(n), n.ctypes.data, t.ctypes.data, r.ctypes.data,
+                                ctypes.byref(opts) if opts is not None else None,
+                                ctypes.byref(h)), "dna_group_create")
+    return h.value
+
+
+def dna_group_bind(g: int, V, W, H, ldv=None) -> None:
+    pv, pw, ph = _ptr_array(V), _ptr_array(W), _ptr_array(H)
+    ld = _i64_array(ldv if ldv is not None else [v.stride(0) for v in V])
+    _check(LIB.dna_group_bind(g, pv.ctypes.data, ld.ctypes.data, pw.ctypes.data, ph.ctypes.data),
+           "dna_group_bind")
+
+
+def dna_group_set_stream(g: int, stream=None) -> None:
+    _check(LIB.dna_group_set_stream(g, _stream(stream)), "dna_group_set_stream")
+
+
+def dna_group_normalize(g: int, which: int) -> None:
+    _check(LIB.dna_group_normalize(g, which), "dna_group_normalize")
+
+
+def dna_group_step_H(g: int) -> None:
+    _check(LIB.dna_group_step_H(g), "dna_group_step_H")
+
+
+def dna_group_step_W(g: int) -> None:
+    _check(LIB.dna_group_step_W(g), "dna_group_step_W")
+
+
+def dna_group_iterate(g: int, iters: int) -> None:
+    _check(LIB.dna_group_iterate(g, iters), "dna_group_iterate")
+
+
+def dna_group_use_graph(g: int, enable: bool = True) -> None:
+    _check(LIB.dna_group_use_graph(g, 1 if enable else 0), "dna_group_use_graph")
+
+
+def dna_group_autotune(g: int, reps: int = 2) -> int:
+    rows = ctypes.c_int64()
+    _check(LIB.dna_group_autotune(g, reps, ctypes.byref(rows)), "dna_group_autotune")
+    return rows.value
+
+
+def dna_group_kl(g: int, count: int):
+    import numpy as np
+    out = np.zeros(count, dtype=np.float64)
+    _check(LIB.dna_group_kl(g, out.ctypes.data), "dna_group_kl")
+    return out
+
+
+def dna_group_get_status(g: int) -> int:
+    return LIB.dna_group_get_status(g)
+
+
+def dna_group_launches_per_iteration(g: int) -> int:
+    return LIB.dna_group_launches_per_iteration(g)
+
+
+def dna_group_destroy(g: int) -> None:
+    LIB.dna_group_destroy(g)
 
 
 def dna_destroy(ctx: int) -> None:

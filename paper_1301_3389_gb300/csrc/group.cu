@@ -1,0 +1,702 @@
+// Grouped (batched) DNA: many independent KL-NMF problems of uneven sizes, each phase of a
+// half-step run for all problems in one persistent launch, optionally replayed as a CUDA
+// graph.  FP32 form on the CUDA cores, R <= 64.
+//
+// The problems live in one device arena; a device table holds each problem's (s, o, r)
+// views and workspace pointers; each phase has a tile list (problem, block, split) that a
+// persistent grid walks with a fixed stride.  The reduction splits (rows of s per tile)
+// are chosen by a timing autotuner (dna_group_autotune).  The tile bodies are the same
+// device functions as the single-problem kernels, so results match the single-problem path
+// up to the order of the split sums.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "dna.h"
+#include "dna_internal.h"
+#include "simt_kernels.cuh"
+
+namespace dna {
+namespace grp {
+
+struct GProb {
+    View v[2];                 // H view (0), W view (1)
+    float* A;                  // [splits][R][O] raw A sums
+    float* B;
+    float* Xmu;                // [R][O]
+    float* Xdna;
+    double* dpart;             // [splits][2][O] cost partials (and d_KL partials)
+    double* c;                 // R, eq. 7 / 14 denominators
+    double* sig;               // R, step 16 / 29 normalisers
+    double* dfin[2];           // [2][O] final candidate costs per view
+    uint8_t* choice[2];        // O per view
+    int64_t per1[2], per2[2];  // rows of s per split
+    int sp1[2], sp2[2];
+    int rclass;                // 0: R <= 32, 1: R <= 64
+};
+
+struct GTile {
+    int32_t prob, a, b, pad;
+};
+
+constexpr int NCLASS = 2;
+constexpr int64_t MIN_SPLIT_ROWS = 256;   // smallest s-range per split (bounds the workspace)
+
+template <int RB, bool WITH_B>
+__global__ void __launch_bounds__(simt::NT, 2)
+    k_g_pass1(const GProb* __restrict__ P, const GTile* __restrict__ tl, int n, int w,
+              int* __restrict__ status) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    for (int t = blockIdx.x; t < n; t += gridDim.x) {
+        const GTile tt = tl[t];
+        const GProb& p = P[tt.prob];
+        const View v = p.v[w];
+        simt::pass1_tile<float, RB, WITH_B>(v, p.A, p.B, p.per1[w], status, tt.a, 0, tt.b, smem);
+        __syncthreads();
+    }
+}
+
+template <int RB, int NC, bool FULL>
+__global__ void __launch_bounds__(simt::NT, 2)
+    k_g_pass2(const GProb* __restrict__ P, const GTile* __restrict__ tl, int n, int w,
+              int* __restrict__ status) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    for (int t = blockIdx.x; t < n; t += gridDim.x) {
+        const GTile tt = tl[t];
+        const GProb& p = P[tt.prob];
+        const View v = p.v[w];
+        if constexpr (FULL)
+            simt::pass2_tile<float, RB, 1, true>(v, static_cast<const float*>(v.X),
+                                                 static_cast<const float*>(v.X), v.xr, v.xo,
+                                                 p.dpart, p.per2[w], status, tt.a, tt.b, smem);
+        else
+            simt::pass2_tile<float, RB, NC, false>(v, p.Xmu, p.Xdna, v.O, 1, p.dpart, p.per2[w],
+                                                   status, tt.a, tt.b, smem);
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(256)
+    k_g_candidates(const GProb* __restrict__ P, const GTile* __restrict__ tl, int n, int w,
+                   float eps, float alpha) {
+    for (int t = blockIdx.x; t < n; t += gridDim.x) {
+        const GTile tt = tl[t];
+        const GProb& p = P[tt.prob];
+        const View v = p.v[w];
+        simt::candidates_tile<float>(v, p.c, p.A, p.B, p.sp1[w], p.Xmu, p.Xdna, eps, alpha, tt.a);
+    }
+}
+
+__global__ void __launch_bounds__(256)
+    k_g_select(const GProb* __restrict__ P, const GTile* __restrict__ tl, int n, int w) {
+    for (int t = blockIdx.x; t < n; t += gridDim.x) {
+        const GTile tt = tl[t];
+        const GProb& p = P[tt.prob];
+        const View v = p.v[w];
+        simt::select_tile<float>(v, p.Xmu, p.Xdna, p.dpart, p.sp2[w], p.choice[w], p.dfin[w],
+                                 tt.a);
+    }
+}
+
+// Factor sums for 32 values of r of one problem: of y over s (which = 0, into c) or of x
+// over o (which = 1, into sig), plus the regularisation weight; an exact zero becomes 1.
+__global__ void __launch_bounds__(256)
+    k_g_sums(const GProb* __restrict__ P, const GTile* __restrict__ tl, int n, int w, int which,
+             double reg) {
+    __shared__ double red[8][33];
+    const int lane = threadIdx.x, ty = threadIdx.y;
+    for (int t = blockIdx.x; t < n; t += gridDim.x) {
+        const GTile tt = tl[t];
+        const GProb& p = P[tt.prob];
+        const View v = p.v[w];
+        const int64_t r = (int64_t)tt.a * 32 + lane;
+        const float* M = static_cast<const float*>(which ? v.X : v.Y);
+        const int64_t cnt = which ? v.O : v.S;
+        const int64_t si = which ? v.xo : v.ys, sr = which ? v.xr : v.yr;
+        float s = 0.f;
+        if (r < v.R)
+            for (int64_t i = ty; i < cnt; i += 8) s += M[i * si + r * sr];
+        red[ty][lane] = (double)s;
+        __syncthreads();
+        if (ty == 0 && r < v.R) {
+            double tot = 0.0;
+            for (int k = 0; k < 8; ++k) tot += red[k][lane];
+            (which ? p.sig : p.c)[r] = simt::nonzero_sum(tot + reg, true);
+        }
+        __syncthreads();
+    }
+}
+
+// Steps 1, 16, 29 for 8 values of r of one problem: X(r, .) /= sig_r, Y(., r) *= sig_r.
+__global__ void __launch_bounds__(256)
+    k_g_rescale(const GProb* __restrict__ P, const GTile* __restrict__ tl, int n, int w) {
+    for (int t = blockIdx.x; t < n; t += gridDim.x) {
+        const GTile tt = tl[t];
+        const GProb& p = P[tt.prob];
+        const View v = p.v[w];
+        const int64_t r = (int64_t)tt.a * 8 + threadIdx.y;
+        if (r >= v.R) continue;
+        const float f = (float)p.sig[r], inv = 1.0f / f;
+        float* X = static_cast<float*>(v.X);
+        float* Y = const_cast<float*>(static_cast<const float*>(v.Y));
+        for (int64_t i = threadIdx.x; i < v.O; i += 32) X[r * v.xr + i * v.xo] *= inv;
+        for (int64_t i = threadIdx.x; i < v.S; i += 32) Y[i * v.ys + r * v.yr] *= f;
+    }
+}
+
+// d_KL of each problem: sum of its per-column partials, fixed order.
+__global__ void k_g_kl_reduce(const GProb* __restrict__ P, int count, double* __restrict__ out) {
+    __shared__ double red[256];
+    for (int q = blockIdx.x; q < count; q += gridDim.x) {
+        const GProb& p = P[q];
+        const int64_t n = (int64_t)p.sp2[0] * p.v[0].O;
+        double s = 0.0;
+        for (int64_t i = threadIdx.x; i < n; i += 256) s += p.dpart[i];
+        red[threadIdx.x] = s;
+        __syncthreads();
+        for (int m = 128; m > 0; m >>= 1) {
+            if ((int)threadIdx.x < m) red[threadIdx.x] += red[threadIdx.x + m];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[q] = red[0];
+        __syncthreads();
+    }
+}
+
+struct TileList {
+    GTile* d = nullptr;
+    int n = 0;
+};
+
+}  // namespace grp
+}  // namespace dna
+
+using dna::View;
+using dna::grp::GProb;
+using dna::grp::GTile;
+using dna::grp::TileList;
+
+struct dna_group {
+    int count = 0;
+    dna_opts o{};
+    int device = 0, num_sms = 1;
+    std::vector<int64_t> N, T, R;
+    cudaStream_t user = nullptr, gs = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    unsigned char* arena = nullptr;
+    std::vector<GProb> hp;
+    GProb* dp = nullptr;
+    double* kl_dev = nullptr;
+    int* status = nullptr;
+    // tile lists [view][class] for the passes, [view] for the rest
+    TileList p1[2][dna::grp::NCLASS], p2[2][dna::grp::NCLASS], kl[dna::grp::NCLASS];
+    TileList cand[2], sums_y[2], sums_x[2], resc[2];
+    int slots1[dna::grp::NCLASS] = {1, 1}, slots2[dna::grp::NCLASS] = {1, 1};
+    int64_t split_rows = 1024;  // rows of s per split (autotuned)
+    bool bound = false, use_graph = false;
+    cudaGraphExec_t gexec = nullptr;
+    int64_t graph_launches = 0;
+    std::vector<void*> tile_allocs;
+};
+
+namespace {
+
+using namespace dna;
+
+template <typename Kern>
+int set_smem(Kern k, size_t bytes) {
+    if (bytes > 48 * 1024 &&
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+            cudaSuccess)
+        return DNA_ERR_CUDA;
+    return DNA_OK;
+}
+
+template <int RB>
+size_t p1_smem() { return simt::Pass1Cfg<float, RB>::smem; }
+template <int RB>
+size_t p2_smem() { return simt::Pass2Cfg<float, RB, 2>::smem; }
+
+template <int RB>
+int prep_class(dna_group* g, int cls) {
+    using namespace dna::grp;
+    int e = set_smem(k_g_pass1<RB, true>, p1_smem<RB>());
+    e |= set_smem(k_g_pass1<RB, false>, p1_smem<RB>());
+    e |= set_smem(k_g_pass2<RB, 2, false>, p2_smem<RB>());
+    e |= set_smem(k_g_pass2<RB, 2, true>, p2_smem<RB>());
+    if (e) return DNA_ERR_CUDA;
+    int b1 = 1, b2 = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_g_pass1<RB, true>, simt::NT, p1_smem<RB>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_g_pass2<RB, 2, false>, simt::NT,
+                                                  p2_smem<RB>());
+    cudaGetLastError();
+    g->slots1[cls] = std::max(1, b1) * g->num_sms;
+    g->slots2[cls] = std::max(1, b2) * g->num_sms;
+    return DNA_OK;
+}
+
+void free_lists(dna_group* g) {
+    for (void* p : g->tile_allocs) cudaFree(p);
+    g->tile_allocs.clear();
+}
+
+int upload(dna_group* g, const std::vector<GTile>& v, TileList* out) {
+    out->n = (int)v.size();
+    out->d = nullptr;
+    if (v.empty()) return DNA_OK;
+    if (cudaMalloc(&out->d, sizeof(GTile) * v.size()) != cudaSuccess) return DNA_ERR_ALLOC;
+    g->tile_allocs.push_back(out->d);
+    if (cudaMemcpy(out->d, v.data(), sizeof(GTile) * v.size(), cudaMemcpyHostToDevice) !=
+        cudaSuccess)
+        return DNA_ERR_CUDA;
+    return DNA_OK;
+}
+
+// Split plan of every problem for rows-per-split `rows`, then all tile lists.
+int build_tiles(dna_group* g) {
+    free_lists(g);
+    const int64_t ch = simt::SB, ob = simt::OB;
+    for (int q = 0; q < g->count; ++q) {
+        GProb& p = g->hp[q];
+        for (int w = 0; w < 2; ++w) {
+            const int64_t S = p.v[w].S;
+            const int64_t rows = std::max<int64_t>(g->split_rows, dna::grp::MIN_SPLIT_ROWS);
+            const int64_t per = std::max<int64_t>(ch, (rows + ch - 1) / ch * ch);
+            p.per1[w] = p.per2[w] = per;
+            p.sp1[w] = p.sp2[w] = (int)((S + per - 1) / per);
+        }
+    }
+    std::vector<GTile> t1[2][2], t2[2][2], tk[2], tc[2], ty[2], tx[2], tr[2];
+    for (int q = 0; q < g->count; ++q) {
+        const GProb& p = g->hp[q];
+        for (int w = 0; w < 2; ++w) {
+            const View& v = p.v[w];
+            const int64_t nob = (v.O + ob - 1) / ob;
+            for (int64_t b = 0; b < nob; ++b)
+                for (int s = 0; s < p.sp1[w]; ++s) t1[w][p.rclass].push_back({q, (int)b, s, 0});
+            for (int64_t b = 0; b < nob; ++b)
+                for (int s = 0; s < p.sp2[w]; ++s) t2[w][p.rclass].push_back({q, (int)b, s, 0});
+            for (int64_t b = 0; b < (v.O + 31) / 32; ++b) tc[w].push_back({q, (int)b, 0, 0});
+            for (int64_t b = 0; b < (v.R + 31) / 32; ++b) {
+                ty[w].push_back({q, (int)b, 0, 0});
+                tx[w].push_back({q, (int)b, 0, 0});
+            }
+            for (int64_t b = 0; b < (v.R + 7) / 8; ++b) tr[w].push_back({q, (int)b, 0, 0});
+        }
+        const View& v = p.v[0];
+        for (int64_t b = 0; b < (v.O + ob - 1) / ob; ++b)
+            for (int s = 0; s < p.sp2[0]; ++s) tk[p.rclass].push_back({q, (int)b, s, 0});
+    }
+    int e = DNA_OK;
+    for (int w = 0; w < 2; ++w) {
+        for (int k = 0; k < 2; ++k) {
+            e |= upload(g, t1[w][k], &g->p1[w][k]);
+            e |= upload(g, t2[w][k], &g->p2[w][k]);
+        }
+        e |= upload(g, tc[w], &g->cand[w]);
+        e |= upload(g, ty[w], &g->sums_y[w]);
+        e |= upload(g, tx[w], &g->sums_x[w]);
+        e |= upload(g, tr[w], &g->resc[w]);
+    }
+    for (int k = 0; k < 2; ++k) e |= upload(g, tk[k], &g->kl[k]);
+    if (e) return e;
+    if (cudaMemcpy(g->dp, g->hp.data(), sizeof(GProb) * g->count, cudaMemcpyHostToDevice) !=
+        cudaSuccess)
+        return DNA_ERR_CUDA;
+    if (g->gexec) {
+        cudaGraphExecDestroy(g->gexec);
+        g->gexec = nullptr;
+    }
+    return DNA_OK;
+}
+
+int grid_for(int n, int slots) { return std::max(1, std::min(n, slots)); }
+
+template <int RB>
+int launch_p1(dna_group* g, const TileList& t, int w, bool with_b) {
+    using namespace dna::grp;
+    if (!t.n) return DNA_OK;
+    const int grid = grid_for(t.n, g->slots1[RB == 32 ? 0 : 1]);
+    if (with_b)
+        k_g_pass1<RB, true><<<grid, simt::NT, p1_smem<RB>(), g->gs>>>(g->dp, t.d, t.n, w, g->status);
+    else
+        k_g_pass1<RB, false><<<grid, simt::NT, p1_smem<RB>(), g->gs>>>(g->dp, t.d, t.n, w, g->status);
+    return after_launch();
+}
+
+template <int RB, bool FULL>
+int launch_p2(dna_group* g, const TileList& t, int w) {
+    using namespace dna::grp;
+    if (!t.n) return DNA_OK;
+    const int grid = grid_for(t.n, g->slots2[RB == 32 ? 0 : 1]);
+    k_g_pass2<RB, 2, FULL><<<grid, simt::NT, p2_smem<RB>(), g->gs>>>(g->dp, t.d, t.n, w, g->status);
+    return after_launch();
+}
+
+int launch_small(dna_group* g, int which, const TileList& t, int w, double reg = 0.0) {
+    using namespace dna::grp;
+    if (!t.n) return DNA_OK;
+    const int grid = grid_for(t.n, 8 * g->num_sms);
+    const dim3 blk(32, 8);
+    switch (which) {
+        case 0: k_g_sums<<<grid, blk, 0, g->gs>>>(g->dp, t.d, t.n, w, 0, reg); break;
+        case 1: k_g_sums<<<grid, blk, 0, g->gs>>>(g->dp, t.d, t.n, w, 1, reg); break;
+        case 2: k_g_rescale<<<grid, blk, 0, g->gs>>>(g->dp, t.d, t.n, w); break;
+        case 3: k_g_candidates<<<grid, blk, 0, g->gs>>>(g->dp, t.d, t.n, w, (float)g->o.eps,
+                                                        (float)g->o.alpha); break;
+        case 4: k_g_select<<<grid, blk, 0, g->gs>>>(g->dp, t.d, t.n, w); break;
+        default: return DNA_ERR_ARG;
+    }
+    return after_launch();
+}
+
+// Steps 1/29 (which = 1) or 16 (which = 0) for every problem.
+int g_normalize(dna_group* g, int which) {
+    const double reg = which ? g->o.lambda : g->o.rho;
+    int e = launch_small(g, 1, g->sums_x[which], which, reg);
+    return e ? e : launch_small(g, 2, g->resc[which], which);
+}
+
+int g_half(dna_group* g, int w, bool mu_only) {
+    const double reg_den = w ? g->o.rho : g->o.lambda;
+    int e = launch_small(g, 0, g->sums_y[w], w, reg_den);
+    if (!e) e = launch_p1<32>(g, g->p1[w][0], w, !mu_only);
+    if (!e) e = launch_p1<64>(g, g->p1[w][1], w, !mu_only);
+    if (e) return e;
+    if (mu_only) return DNA_ERR_UNSUPPORTED;
+    e = launch_small(g, 3, g->cand[w], w);
+    if (!e) e = launch_p2<32, false>(g, g->p2[w][0], w);
+    if (!e) e = launch_p2<64, false>(g, g->p2[w][1], w);
+    if (!e) e = launch_small(g, 4, g->cand[w], w);
+    if (!e) e = g_normalize(g, w == 1 ? 1 : 0);
+    return e;
+}
+
+int g_iteration(dna_group* g) {
+    int e = g_half(g, 0, false);
+    return e ? e : g_half(g, 1, false);
+}
+
+struct Handoff {   // order the group's private stream after, and before, the caller's
+    dna_group* g;
+    int err = DNA_OK;
+    explicit Handoff(dna_group* gg) : g(gg) {
+        if (cudaEventRecord(g->ev_in, g->user) != cudaSuccess ||
+            cudaStreamWaitEvent(g->gs, g->ev_in, 0) != cudaSuccess)
+            err = DNA_ERR_CUDA;
+    }
+    ~Handoff() {
+        cudaEventRecord(g->ev_out, g->gs);
+        cudaStreamWaitEvent(g->user, g->ev_out, 0);
+    }
+};
+
+int sync_status(dna_group* g) {
+    int st = 0;
+    if (cudaMemcpyAsync(&st, g->status, sizeof(int), cudaMemcpyDeviceToHost, g->gs) != cudaSuccess ||
+        cudaStreamSynchronize(g->gs) != cudaSuccess)
+        return DNA_ERR_CUDA;
+    if (st & STATUS_NONFINITE) return DNA_ERR_NONFINITE;
+    if (st & STATUS_TIMEOUT) return DNA_ERR_TIMEOUT;
+    return DNA_OK;
+}
+
+size_t al(size_t x) { return (x + 255) / 256 * 256; }
+
+}  // namespace
+
+extern "C" {
+
+int dna_group_create(int count, const int64_t* N, const int64_t* T, const int64_t* R,
+                     const dna_opts* opts, dna_group** out) {
+    if (!out || count < 1 || !N || !T || !R) return DNA_ERR_ARG;
+    *out = nullptr;
+    dna_opts o;
+    dna_default_opts(&o);
+    if (opts) o = *opts;
+    if (o.dtype != DNA_F32 || o.engine == DNA_ENGINE_TENSOR) return DNA_ERR_UNSUPPORTED;
+    if (!(o.eps > 0.0 && o.eps <= 1.0) || !(o.alpha >= 0.0) || !(o.rho >= 0.0) ||
+        !(o.lambda >= 0.0))
+        return DNA_ERR_ARG;
+    for (int q = 0; q < count; ++q)
+        if (N[q] < 1 || T[q] < 1 || R[q] < 1 || R[q] > 64 || N[q] > (1 << 30) || T[q] > (1 << 30))
+            return R[q] > 64 ? DNA_ERR_UNSUPPORTED : DNA_ERR_ARG;
+    dna_group* g = new (std::nothrow) dna_group();
+    if (!g) return DNA_ERR_ALLOC;
+    g->count = count;
+    g->o = o;
+    g->N.assign(N, N + count);
+    g->T.assign(T, T + count);
+    g->R.assign(R, R + count);
+    int e = DNA_OK;
+    if (cudaGetDevice(&g->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device) !=
+            cudaSuccess ||
+        cudaStreamCreateWithFlags(&g->gs, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&g->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&g->ev_out, cudaEventDisableTiming) != cudaSuccess)
+        e = DNA_ERR_CUDA;
+    if (!e) e = prep_class<32>(g, 0);
+    if (!e) e = prep_class<64>(g, 1);
+    // arena: per problem Vt, V sums, factor sums, A/B partials (worst split count), candidates,
+    // cost partials, final costs, choices
+    // the largest split counts any plan can use (splits of at least MIN_SPLIT_ROWS rows)
+    auto nsplit = [](int64_t S) {
+        return (S + dna::grp::MIN_SPLIT_ROWS - 1) / dna::grp::MIN_SPLIT_ROWS;
+    };
+    std::vector<size_t> off(count);
+    size_t total = 0;
+    for (int q = 0; q < count && !e; ++q) {
+        const int64_t n = N[q], t = T[q], r = R[q], m = std::max(n, t);
+        const int64_t ldvt = (n + 3) / 4 * 4;
+        const int64_t ab = std::max(nsplit(n) * r * t, nsplit(t) * r * n);   // A/B partials
+        const int64_t dp = std::max(nsplit(n) * 2 * t, nsplit(t) * 2 * n);   // cost partials
+        off[q] = total;
+        total += al(4 * t * ldvt) + al(8 * (n + t)) + al(16 * r) + 2 * al(4 * ab) +
+                 2 * al(4 * r * m) + al(8 * dp) + al(8 * 2 * (n + t)) + al(n + t);
+    }
+    if (!e && cudaMalloc(&g->arena, total + 256) != cudaSuccess) e = DNA_ERR_ALLOC;
+    if (!e && (cudaMalloc(&g->dp, sizeof(GProb) * count) != cudaSuccess ||
+               cudaMalloc(&g->kl_dev, sizeof(double) * count) != cudaSuccess ||
+               cudaMalloc(&g->status, sizeof(int)) != cudaSuccess))
+        e = DNA_ERR_ALLOC;
+    if (!e && cudaMemset(g->status, 0, sizeof(int)) != cudaSuccess) e = DNA_ERR_CUDA;
+    if (e) {
+        cudaGetLastError();
+        dna_group_destroy(g);
+        return e;
+    }
+    g->hp.resize(count);
+    for (int q = 0; q < count; ++q) {
+        const int64_t n = N[q], t = T[q], r = R[q], m = std::max(n, t);
+        const int64_t ldvt = (n + 3) / 4 * 4;
+        unsigned char* b = g->arena + off[q];
+        GProb& p = g->hp[q];
+        p = GProb{};
+        float* Vt = reinterpret_cast<float*>(b); b += al(4 * t * ldvt);
+        double* colsum = reinterpret_cast<double*>(b);
+        double* rowsum = colsum + t; b += al(8 * (n + t));
+        p.c = reinterpret_cast<double*>(b); p.sig = p.c + r; b += al(16 * r);
+        const int64_t ab = std::max(nsplit(n) * r * t, nsplit(t) * r * n);
+        const int64_t dp = std::max(nsplit(n) * 2 * t, nsplit(t) * 2 * n);
+        p.A = reinterpret_cast<float*>(b); b += al(4 * ab);
+        p.B = reinterpret_cast<float*>(b); b += al(4 * ab);
+        p.Xmu = reinterpret_cast<float*>(b); b += al(4 * r * m);
+        p.Xdna = reinterpret_cast<float*>(b); b += al(4 * r * m);
+        p.dpart = reinterpret_cast<double*>(b); b += al(8 * dp);
+        p.dfin[0] = reinterpret_cast<double*>(b); p.dfin[1] = p.dfin[0] + 2 * t;
+        b += al(8 * 2 * (n + t));
+        p.choice[0] = b; p.choice[1] = b + t;
+        p.rclass = r <= 32 ? 0 : 1;
+        // views without the caller's buffers yet
+        View& vh = p.v[0];
+        vh.S = n; vh.O = t; vh.R = r; vh.vsum = colsum;
+        View& vw = p.v[1];
+        vw.S = t; vw.O = n; vw.R = r; vw.V = Vt; vw.vs = ldvt; vw.vsum = rowsum;
+    }
+    *out = g;
+    return DNA_OK;
+}
+
+int dna_group_bind(dna_group* g, const void* const* V, const int64_t* ldv, void* const* W,
+                   void* const* H) {
+    if (!g || !V || !W || !H) return DNA_ERR_ARG;
+    for (int q = 0; q < g->count; ++q) {
+        const int64_t ld = ldv ? ldv[q] : g->T[q];
+        if (!V[q] || !W[q] || !H[q] || ld < g->T[q]) return DNA_ERR_ARG;
+    }
+    if (cudaSetDevice(g->device) != cudaSuccess) return DNA_ERR_CUDA;
+    Handoff h(g);
+    if (h.err) return h.err;
+    for (int q = 0; q < g->count; ++q) {
+        GProb& p = g->hp[q];
+        const int64_t n = g->N[q], t = g->T[q], r = g->R[q];
+        const int64_t ld = ldv ? ldv[q] : t;
+        View& vh = p.v[0];
+        vh.V = V[q]; vh.vs = ld;
+        vh.X = H[q]; vh.xr = t; vh.xo = 1;
+        vh.Y = W[q]; vh.ys = r; vh.yr = 1;
+        View& vw = p.v[1];
+        vw.X = W[q]; vw.xr = 1; vw.xo = r;
+        vw.Y = H[q]; vw.ys = 1; vw.yr = t;
+        float* Vt = static_cast<float*>(const_cast<void*>(vw.V));
+        if (cudaMemsetAsync(Vt, 0, sizeof(float) * (size_t)(t * vw.vs), g->gs) != cudaSuccess)
+            return DNA_ERR_CUDA;
+        if (int e = Simt<float>::prepare_v(static_cast<const float*>(V[q]), n, t, ld, Vt, vw.vs,
+                                           const_cast<double*>(vh.vsum),
+                                           const_cast<double*>(vw.vsum), g->gs))
+            return e;
+    }
+    g->bound = true;
+    return build_tiles(g);
+}
+
+int dna_group_set_stream(dna_group* g, void* stream) {
+    if (!g) return DNA_ERR_ARG;
+    g->user = static_cast<cudaStream_t>(stream);
+    return DNA_OK;
+}
+
+int dna_group_normalize(dna_group* g, int which) {
+    if (!g || !g->bound || (which != 0 && which != 1)) return DNA_ERR_ARG;
+    Handoff h(g);
+    return h.err ? h.err : g_normalize(g, which);
+}
+
+int dna_group_step_H(dna_group* g) {
+    if (!g || !g->bound) return DNA_ERR_ARG;
+    Handoff h(g);
+    return h.err ? h.err : g_half(g, 0, false);
+}
+
+int dna_group_step_W(dna_group* g) {
+    if (!g || !g->bound) return DNA_ERR_ARG;
+    Handoff h(g);
+    return h.err ? h.err : g_half(g, 1, false);
+}
+
+int dna_group_use_graph(dna_group* g, int enable) {
+    if (!g) return DNA_ERR_ARG;
+    g->use_graph = enable != 0;
+    return DNA_OK;
+}
+
+int dna_group_iterate(dna_group* g, int iters) {
+    if (!g || !g->bound || iters < 0) return DNA_ERR_ARG;
+    Handoff h(g);
+    if (h.err) return h.err;
+    if (!g->use_graph) {
+        for (int i = 0; i < iters; ++i)
+            if (int e = g_iteration(g)) return e;
+        return DNA_OK;
+    }
+    if (!g->gexec) {  // capture one iteration once; parameters are fixed after bind
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamBeginCapture(g->gs, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            return DNA_ERR_CUDA;
+        const int64_t before = dna::launch_count();
+        const int e = g_iteration(g);
+        const cudaError_t ce = cudaStreamEndCapture(g->gs, &graph);
+        if (e || ce != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return e ? e : DNA_ERR_CUDA;
+        }
+        g->graph_launches = dna::launch_count() - before;
+        const cudaError_t ie = cudaGraphInstantiate(&g->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) {
+            g->gexec = nullptr;
+            return DNA_ERR_CUDA;
+        }
+    }
+    for (int i = 0; i < iters; ++i) {
+        if (cudaGraphLaunch(g->gexec, g->gs) != cudaSuccess) return DNA_ERR_CUDA;
+        dna::launch_count() += g->graph_launches;
+    }
+    return DNA_OK;
+}
+
+int dna_group_autotune(dna_group* g, int reps, int64_t* rows_out) {
+    if (!g || !g->bound || reps < 1) return DNA_ERR_ARG;
+    const int64_t cands[] = {256, 512, 1024, 2048, 4096, 1 << 30};
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)
+        return DNA_ERR_CUDA;
+    // time the two passes of both half-steps; W and H are restored afterwards by the
+    // caller-visible contract: each candidate runs full iterations, so save and restore
+    if (cudaStreamSynchronize(g->user) != cudaSuccess) return DNA_ERR_CUDA;
+    std::vector<std::vector<unsigned char>> saved;   // per problem W, H bytes
+    for (int q = 0; q < g->count; ++q) {
+        const size_t bw = 4 * (size_t)(g->N[q] * g->R[q]), bh = 4 * (size_t)(g->R[q] * g->T[q]);
+        std::vector<unsigned char> buf(bw + bh);
+        cudaMemcpyAsync(buf.data(), g->hp[q].v[1].X, bw, cudaMemcpyDeviceToHost, g->gs);
+        cudaMemcpyAsync(buf.data() + bw, g->hp[q].v[0].X, bh, cudaMemcpyDeviceToHost, g->gs);
+        saved.push_back(std::move(buf));
+    }
+    if (cudaStreamSynchronize(g->gs) != cudaSuccess) return DNA_ERR_CUDA;
+    double best = 1e300;
+    int64_t best_rows = g->split_rows;
+    int e = DNA_OK;
+    for (int64_t rows : cands) {
+        g->split_rows = rows;
+        if ((e = build_tiles(g))) break;
+        if ((e = g_iteration(g))) break;   // warm-up
+        cudaEventRecord(a, g->gs);
+        for (int i = 0; i < reps && !e; ++i) e = g_iteration(g);
+        cudaEventRecord(b, g->gs);
+        if (e || cudaEventSynchronize(b) != cudaSuccess) { e = e ? e : DNA_ERR_CUDA; break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        if (ms < best) { best = ms; best_rows = rows; }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaStreamSynchronize(g->gs);
+    for (int q = 0; q < g->count; ++q) {
+        const size_t bw = 4 * (size_t)(g->N[q] * g->R[q]), bh = 4 * (size_t)(g->R[q] * g->T[q]);
+        cudaMemcpyAsync(g->hp[q].v[1].X, saved[q].data(), bw, cudaMemcpyHostToDevice, g->gs);
+        cudaMemcpyAsync(g->hp[q].v[0].X, saved[q].data() + bw, bh, cudaMemcpyHostToDevice, g->gs);
+    }
+    if (cudaStreamSynchronize(g->gs) != cudaSuccess) return DNA_ERR_CUDA;
+    if (e) return e;
+    g->split_rows = best_rows;
+    if (rows_out) *rows_out = best_rows;
+    return build_tiles(g);
+}
+
+int dna_group_kl(dna_group* g, double* out) {
+    if (!g || !g->bound || !out) return DNA_ERR_ARG;
+    using namespace dna::grp;
+    int e = DNA_OK;
+    {
+        Handoff h(g);
+        if (h.err) return h.err;
+        e = launch_p2<32, true>(g, g->kl[0], 0);
+        if (!e) e = launch_p2<64, true>(g, g->kl[1], 0);
+        if (!e) {
+            k_g_kl_reduce<<<std::min(g->count, 1024), 256, 0, g->gs>>>(g->dp, g->count, g->kl_dev);
+            e = dna::after_launch();
+        }
+        if (!e && cudaMemcpyAsync(out, g->kl_dev, sizeof(double) * g->count,
+                                  cudaMemcpyDeviceToHost, g->gs) != cudaSuccess)
+            e = DNA_ERR_CUDA;
+    }
+    if (e) return e;
+    return sync_status(g);
+}
+
+int dna_group_get_status(dna_group* g) {
+    if (!g) return DNA_ERR_ARG;
+    return sync_status(g);
+}
+
+int64_t dna_group_launches_per_iteration(dna_group* g) {
+    if (!g) return -1;
+    int64_t n = 0;
+    for (int w = 0; w < 2; ++w) {
+        n += 5;  // sums, candidates, select, normaliser sums, rescale
+        for (int k = 0; k < 2; ++k) n += (g->p1[w][k].n > 0) + (g->p2[w][k].n > 0);
+    }
+    return n;
+}
+
+void dna_group_destroy(dna_group* g) {
+    if (!g) return;
+    cudaSetDevice(g->device);
+    if (g->gs) cudaStreamSynchronize(g->gs);
+    if (g->gexec) cudaGraphExecDestroy(g->gexec);
+    free_lists(g);
+    if (g->arena) cudaFree(g->arena);
+    if (g->dp) cudaFree(g->dp);
+    if (g->kl_dev) cudaFree(g->kl_dev);
+    if (g->status) cudaFree(g->status);
+    if (g->ev_in) cudaEventDestroy(g->ev_in);
+    if (g->ev_out) cudaEventDestroy(g->ev_out);
+    if (g->gs) cudaStreamDestroy(g->gs);
+    delete g;
+}
+
+}  // extern "C"

@@ -90,11 +90,11 @@ struct Pass1Cfg {
 // Pass 1: raw A and B sums for one (o-block, r-block, s-split).
 // grid = (ceil(O / OB), ceil(R / RB), splits); Apart/Bpart are [splits][R][O].
 template <typename Tp, int RB, bool WITH_B>
-__global__ void __launch_bounds__(NT, sizeof(Tp) == 4 ? 2 : 1) k_pass1(View v, Tp* __restrict__ Apart,
-                                              Tp* __restrict__ Bpart, int64_t s_per,
-                                              int* __restrict__ status) {
+__device__ __forceinline__ void pass1_tile(const View& v, Tp* __restrict__ Apart,
+                                           Tp* __restrict__ Bpart, int64_t s_per,
+                                           int* __restrict__ status, int64_t tile_o, int64_t tile_r,
+                                           int64_t tile_s, unsigned char* smem_raw) {
     using C = Pass1Cfg<Tp, RB>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     Tp* Xs = reinterpret_cast<Tp*>(smem_raw);  // [RB][LD]  x(r, o) of the current r-piece
     Tp* Yt = Xs + RB * LD;                     // [RB][LD]  y(s, r) transposed: Yt[r][s]
     Tp* Qs = Yt + RB * LD;                     // [SB][LD]  q(s, o)
@@ -104,9 +104,9 @@ __global__ void __launch_bounds__(NT, sizeof(Tp) == 4 ? 2 : 1) k_pass1(View v, T
     const Tp* __restrict__ X = static_cast<const Tp*>(v.X);
     const Tp* __restrict__ Y = static_cast<const Tp*>(v.Y);
     const int tid = threadIdx.x;
-    const int64_t o0 = (int64_t)blockIdx.x * OB;
-    const int64_t rown0 = (int64_t)blockIdx.y * RB;
-    const int64_t s_begin = (int64_t)blockIdx.z * s_per;
+    const int64_t o0 = tile_o * OB;
+    const int64_t rown0 = tile_r * RB;
+    const int64_t s_begin = tile_s * s_per;
     const int64_t s_end = min(v.S, s_begin + s_per);
     const int npieces = (int)((v.R + RB - 1) / RB);
 
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(NT, sizeof(Tp) == 4 ? 2 : 1) k_pass1(View v, T
     }
     if (bad) atomicOr(status, STATUS_NONFINITE);
 
-    const int64_t base = (int64_t)blockIdx.z * v.R;
+    const int64_t base = tile_s * v.R;
 #pragma unroll
     for (int i = 0; i < C::RPT; ++i) {
         const int64_t r = rown0 + gr + 16 * i;
@@ -196,6 +196,16 @@ __global__ void __launch_bounds__(NT, sizeof(Tp) == 4 ? 2 : 1) k_pass1(View v, T
     }
 }
 
+// Pass 1 for one problem: grid = (ceil(O / OB), ceil(R / RB), splits).
+template <typename Tp, int RB, bool WITH_B>
+__global__ void __launch_bounds__(NT, sizeof(Tp) == 4 ? 2 : 1)
+    k_pass1(View v, Tp* __restrict__ Apart, Tp* __restrict__ Bpart, int64_t s_per,
+            int* __restrict__ status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    pass1_tile<Tp, RB, WITH_B>(v, Apart, Bpart, s_per, status, blockIdx.x, blockIdx.y, blockIdx.z,
+                               smem_raw);
+}
+
 template <typename Tp, int RB, int NC>
 struct Pass2Cfg {
     static constexpr size_t tiles = (size_t)((NC + 1) * RB * LD) * sizeof(Tp);
@@ -208,18 +218,18 @@ struct Pass2Cfg {
 // FULL = true:  sum_{v>0} v log(v / z) - sum v + sum z (eq. 1, for dna_kl).
 // X_c(r, o) at Xc[r * xr + o * xo].  dpart is [splits][NC][O] float64.
 template <typename Tp, int RB, int NC, bool FULL>
-__global__ void __launch_bounds__(NT, sizeof(Tp) == 4 ? 2 : 1) k_pass2(View v, const Tp* __restrict__ X0,
-                                              const Tp* __restrict__ X1, int64_t xr, int64_t xo,
-                                              double* __restrict__ dpart, int64_t s_per,
-                                              int* __restrict__ status) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void pass2_tile(const View& v, const Tp* __restrict__ X0,
+                                           const Tp* __restrict__ X1, int64_t xr, int64_t xo,
+                                           double* __restrict__ dpart, int64_t s_per,
+                                           int* __restrict__ status, int64_t tile_o,
+                                           int64_t tile_s, unsigned char* smem_raw) {
     Tp* Yt = reinterpret_cast<Tp*>(smem_raw);  // [RB][LD]
     Tp* Xs = Yt + RB * LD;                     // [NC][RB][LD]
     const Tp* __restrict__ V = static_cast<const Tp*>(v.V);
     const Tp* __restrict__ Y = static_cast<const Tp*>(v.Y);
     const int tid = threadIdx.x;
-    const int64_t o0 = (int64_t)blockIdx.x * OB;
-    const int64_t s_begin = (int64_t)blockIdx.y * s_per;
+    const int64_t o0 = tile_o * OB;
+    const int64_t s_begin = tile_s * s_per;
     const int64_t s_end = min(v.S, s_begin + s_per);
     const int npieces = (int)((v.R + RB - 1) / RB);
     const int zo = (tid % 16) * 4, zs = (tid / 16) * 4;
@@ -304,25 +314,41 @@ __global__ void __launch_bounds__(NT, sizeof(Tp) == 4 ? 2 : 1) k_pass2(View v, c
         double sum = 0.0;
         for (int k = 0; k < 16; ++k) sum += red[(k * NC + c) * OB + oo];
         const int64_t o = o0 + oo;
-        if (o < v.O) dpart[((int64_t)blockIdx.y * NC + c) * v.O + o] = sum;
+        if (o < v.O) dpart[(tile_s * NC + c) * v.O + o] = sum;
     }
+}
+
+// Pass 2 for one problem: grid = (ceil(O / OB), splits).
+template <typename Tp, int RB, int NC, bool FULL>
+__global__ void __launch_bounds__(NT, sizeof(Tp) == 4 ? 2 : 1)
+    k_pass2(View v, const Tp* __restrict__ X0, const Tp* __restrict__ X1, int64_t xr, int64_t xo,
+            double* __restrict__ dpart, int64_t s_per, int* __restrict__ status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    pass2_tile<Tp, RB, NC, FULL>(v, X0, X1, xr, xo, dpart, s_per, status, blockIdx.x, blockIdx.y,
+                                 smem_raw);
 }
 
 // Candidates (steps 6 and 11, eq. 10, 11, 15, 17).  CTA = 32 columns o (threadIdx.x) x 8
 // groups of r (threadIdx.y); the eq. 10 denominator of each column is reduced over the 8
 // groups in shared memory in a fixed order.
 template <typename Tp>
-__global__ void __launch_bounds__(256) k_candidates(View v, const double* __restrict__ c,
-                                                    const Tp* __restrict__ Apart,
-                                                    const Tp* __restrict__ Bpart, int splits,
-                                                    Tp* __restrict__ Xmu, Tp* __restrict__ Xdna,
-                                                    Tp eps, Tp alpha) {
+__device__ __forceinline__ void candidates_tile(const View& v, const double* __restrict__ c,
+                                                const Tp* __restrict__ Apart,
+                                                const Tp* __restrict__ Bpart, int splits,
+                                                Tp* __restrict__ Xmu, Tp* __restrict__ Xdna,
+                                                Tp eps, Tp alpha, int64_t tile_o) {
     __shared__ double red[8][32];
+    __shared__ Tp cs[512], ics[512];   // c_r and 1 / c_r in the element type (R <= 512)
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int64_t o = (int64_t)blockIdx.x * 32 + tx;
+    for (int r = ty * 32 + tx; r < v.R; r += 256) {
+        cs[r] = (Tp)c[r];
+        ics[r] = Tp(1) / (Tp)c[r];
+    }
+    __syncthreads();
+    const int64_t o = tile_o * 32 + tx;
     const bool live = o < v.O;
     const Tp* __restrict__ X = static_cast<const Tp*>(v.X);
-    double den = 0.0;
+    Tp den = Tp(0);   // this thread's R / 8 terms of the eq. 10 denominator
     if (live) {
         for (int64_t r = ty; r < v.R; r += 8) {
             Tp ra = Tp(0), rb = Tp(0);
@@ -330,7 +356,7 @@ __global__ void __launch_bounds__(256) k_candidates(View v, const double* __rest
                 ra += Apart[((int64_t)sp * v.R + r) * v.O + o];
                 rb += Bpart[((int64_t)sp * v.R + r) * v.O + o];
             }
-            const Tp ic = (Tp)(1.0 / c[r]);
+            const Tp ic = ics[r];
             const Tp a = ra * ic - Tp(1);         // eq. 7
             const Tp b = rb * ic;                 // eq. 14
             const Tp x = X[r * v.xr + o * v.xo];
@@ -347,16 +373,27 @@ __global__ void __launch_bounds__(256) k_candidates(View v, const double* __rest
             }
             Xmu[r * v.O + o] = xmu;
             Xdna[r * v.O + o] = xd;
-            den += c[r] * (double)xd;
+            den += cs[r] * xd;
         }
     }
-    red[ty][tx] = den;
+    red[ty][tx] = (double)den;
     __syncthreads();
-    if (!live) return;
-    double tot = 0.0;
-    for (int k = 0; k < 8; ++k) tot += red[k][tx];
-    const Tp sc = (Tp)(tot > 0.0 ? v.vsum[o] / tot : 1.0);   // eq. 10
-    for (int64_t r = ty; r < v.R; r += 8) Xdna[r * v.O + o] *= sc;
+    if (live) {
+        double tot = 0.0;
+        for (int k = 0; k < 8; ++k) tot += red[k][tx];
+        const Tp sc = (Tp)(tot > 0.0 ? v.vsum[o] / tot : 1.0);   // eq. 10
+        for (int64_t r = ty; r < v.R; r += 8) Xdna[r * v.O + o] *= sc;
+    }
+    __syncthreads();   // the shared arrays are reused by the next tile
+}
+
+template <typename Tp>
+__global__ void __launch_bounds__(256) k_candidates(View v, const double* __restrict__ c,
+                                                    const Tp* __restrict__ Apart,
+                                                    const Tp* __restrict__ Bpart, int splits,
+                                                    Tp* __restrict__ Xmu, Tp* __restrict__ Xdna,
+                                                    Tp eps, Tp alpha) {
+    candidates_tile<Tp>(v, c, Apart, Bpart, splits, Xmu, Xdna, eps, alpha, blockIdx.x);
 }
 
 // MU in place (eq. 11): x(r, o) <- x(r, o) * raw_a(r, o) / c_r.
@@ -376,13 +413,13 @@ __global__ void k_mu_apply(View v, const double* __restrict__ c, const Tp* __res
 // Selection (step 15 / 28): keep the Newton candidate iff d_dna < d_mu (ties keep MU).
 // CTA = 32 columns o x 8 groups of r.
 template <typename Tp>
-__global__ void __launch_bounds__(256) k_select(View v, const Tp* __restrict__ Xmu,
-                                                const Tp* __restrict__ Xdna,
-                                                const double* __restrict__ dpart, int splits,
-                                                uint8_t* __restrict__ choice,
-                                                double* __restrict__ dfin) {
+__device__ __forceinline__ void select_tile(const View& v, const Tp* __restrict__ Xmu,
+                                            const Tp* __restrict__ Xdna,
+                                            const double* __restrict__ dpart, int splits,
+                                            uint8_t* __restrict__ choice,
+                                            double* __restrict__ dfin, int64_t tile_o) {
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int64_t o = (int64_t)blockIdx.x * 32 + tx;
+    const int64_t o = tile_o * 32 + tx;
     if (o >= v.O) return;
     double dm = 0.0, dd = 0.0;
     for (int sp = 0; sp < splits; ++sp) {
@@ -398,6 +435,15 @@ __global__ void __launch_bounds__(256) k_select(View v, const Tp* __restrict__ X
     Tp* __restrict__ X = static_cast<Tp*>(v.X);
     const Tp* __restrict__ src = newton ? Xdna : Xmu;
     for (int64_t r = ty; r < v.R; r += 8) X[r * v.xr + o * v.xo] = src[r * v.O + o];
+}
+
+template <typename Tp>
+__global__ void __launch_bounds__(256) k_select(View v, const Tp* __restrict__ Xmu,
+                                                const Tp* __restrict__ Xdna,
+                                                const double* __restrict__ dpart, int splits,
+                                                uint8_t* __restrict__ choice,
+                                                double* __restrict__ dfin) {
+    select_tile<Tp>(v, Xmu, Xdna, dpart, splits, choice, dfin, blockIdx.x);
 }
 
 // A factor sum that is exactly zero (an all-zero column of W or row of H without
@@ -435,10 +481,10 @@ __global__ void k_colsum_part(const Tp* __restrict__ M, int64_t n, int64_t R, in
     const int lane = threadIdx.x, ty = threadIdx.y;
     const int64_t r = (int64_t)blockIdx.x * 32 + lane;
     const int64_t i0 = (int64_t)blockIdx.y * rows_per, i1 = min(n, i0 + rows_per);
-    double s = 0.0;
+    Tp s = Tp(0);
     if (r < R)
-        for (int64_t i = i0 + ty; i < i1; i += 8) s += (double)M[i * si + r * sr];
-    red[ty][lane] = s;
+        for (int64_t i = i0 + ty; i < i1; i += 8) s += M[i * si + r * sr];
+    red[ty][lane] = (double)s;
     __syncthreads();
     if (ty == 0 && r < R) {
         double t = 0.0;
@@ -470,17 +516,18 @@ __global__ void __launch_bounds__(256) k_row_sums(const Tp* __restrict__ M, int6
                                                   double reg, double* __restrict__ out, bool guard) {
     __shared__ double red[8];
     const int64_t r = blockIdx.x;
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;   // four independent chains
+    // per-thread sums in the element type (four independent chains), float64 across threads
+    Tp s0 = Tp(0), s1 = Tp(0), s2 = Tp(0), s3 = Tp(0);
     const Tp* __restrict__ row = M + r * ld;
     int64_t i = threadIdx.x;
     for (; i + 768 < n; i += 1024) {
-        s0 += (double)row[i];
-        s1 += (double)row[i + 256];
-        s2 += (double)row[i + 512];
-        s3 += (double)row[i + 768];
+        s0 += row[i];
+        s1 += row[i + 256];
+        s2 += row[i + 512];
+        s3 += row[i + 768];
     }
-    for (; i < n; i += 256) s0 += (double)row[i];
-    double s = (s0 + s1) + (s2 + s3);
+    for (; i < n; i += 256) s0 += row[i];
+    double s = (double)(s0 + s1) + (double)(s2 + s3);
 #pragma unroll
     for (int m = 16; m > 0; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
@@ -502,7 +549,7 @@ __global__ void __launch_bounds__(256) k_rescale(View v, const double* __restric
     const bool isx = rg < xblocks;
     const int64_t r = (isx ? rg : rg - xblocks) * 8 + threadIdx.y;
     if (r >= v.R) return;
-    const Tp fr = isx ? (Tp)(1.0 / f[r]) : (Tp)f[r];   // X is divided, Y multiplied
+    const Tp fr = isx ? Tp(1) / (Tp)f[r] : (Tp)f[r];   // X is divided, Y multiplied
     const int64_t n = isx ? v.O : v.S;
     Tp* __restrict__ M = isx ? static_cast<Tp*>(v.X)
                              : const_cast<Tp*>(static_cast<const Tp*>(v.Y));

@@ -1,0 +1,111 @@
+"""The batching form: many uneven problems, one grouped launch per phase, CUDA graph.
+
+Each problem of a group must follow the single-problem FP32 path (same tile arithmetic;
+only the order of the split sums differs: 1e-5 relative), and its d_KL must match the
+FP64 oracle's to 1e-4 after the same iterations.  Graph replay must equal direct
+launches bit for bit.
+"""
+import numpy as np
+import pytest
+
+import workloads
+from gpu_helpers import GpuProblem, rel_fro
+from oracle import dna as o
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(64, 128, 8), (700, 300, 16), (150, 900, 32), (333, 129, 64), (90, 517, 1),
+          (257, 257, 33), (1, 200, 4), (400, 1, 12), (128, 640, 64), (77, 77, 7)]
+
+
+def _group(problems):
+    import torch
+
+    import paper_1301_3389_gb300 as dna
+    dev = torch.device("cuda")
+    V = [torch.from_numpy(p.V).to(dev) for p in problems]
+    W = [torch.from_numpy(p.W).to(dev) for p in problems]
+    H = [torch.from_numpy(p.H).to(dev) for p in problems]
+    g = dna.dna_group_create([p.V.shape[0] for p in problems], [p.V.shape[1] for p in problems],
+                             [p.W.shape[1] for p in problems])
+    dna.dna_group_set_stream(g)
+    dna.dna_group_bind(g, V, W, H)
+    return dna, g, V, W, H
+
+
+def _problems(seed=0):
+    return [workloads.custom(n, t, r, seed=seed * 1000 + i) for i, (n, t, r) in enumerate(SHAPES)]
+
+
+def test_group_matches_single_path():
+    import torch
+    probs = _problems()
+    dna, g, V, W, H = _group(probs)
+    try:
+        dna.dna_group_normalize(g, 1)
+        dna.dna_group_iterate(g, 2)
+        kl = dna.dna_group_kl(g, len(probs))
+        torch.cuda.synchronize()
+        for q, p in enumerate(probs):
+            with GpuProblem(p.V, p.W, p.H, "f32") as gp:
+                gp.dna.dna_normalize(gp.ctx, 1)
+                gp.dna.dna_iterate(gp.ctx, 2)
+                Ws, Hs = gp.WH()
+                kls = gp.dna.dna_kl(gp.ctx)
+            assert rel_fro(W[q].double().cpu().numpy(), Ws) < 1e-5, q
+            assert rel_fro(H[q].double().cpu().numpy(), Hs) < 1e-5, q
+            assert abs(kl[q] - kls) <= 1e-5 * max(abs(kls), 1.0), (q, kl[q], kls)
+            _, _, costs = o.run(p.V, p.W, p.H, 2, "dna")
+            assert abs(kl[q] - costs[-1]) <= 1e-4 * max(costs[-1], 1.0), (q, kl[q], costs[-1])
+    finally:
+        dna.dna_group_destroy(g)
+
+
+def test_group_graph_equals_direct():
+    import torch
+    outs = []
+    for graph in (False, True):
+        probs = _problems(1)
+        dna, g, V, W, H = _group(probs)
+        try:
+            dna.dna_group_use_graph(g, graph)
+            dna.dna_group_normalize(g, 1)
+            dna.dna_group_iterate(g, 3)
+            torch.cuda.synchronize()
+            outs.append([(w.cpu().numpy().copy(), h.cpu().numpy().copy()) for w, h in zip(W, H)])
+            assert dna.dna_group_get_status(g) == 0
+        finally:
+            dna.dna_group_destroy(g)
+    for (w0, h0), (w1, h1) in zip(*outs):
+        np.testing.assert_array_equal(w0, w1)
+        np.testing.assert_array_equal(h0, h1)
+
+
+def test_group_autotune_keeps_state():
+    import torch
+    probs = _problems(2)
+    dna, g, V, W, H = _group(probs)
+    try:
+        dna.dna_group_normalize(g, 1)
+        torch.cuda.synchronize()
+        before = [(w.cpu().numpy().copy(), h.cpu().numpy().copy()) for w, h in zip(W, H)]
+        rows = dna.dna_group_autotune(g, 1)
+        assert rows in (256, 512, 1024, 2048, 4096, 1 << 30)
+        torch.cuda.synchronize()
+        for (w0, h0), w, h in zip(before, W, H):
+            np.testing.assert_array_equal(w0, w.cpu().numpy())
+            np.testing.assert_array_equal(h0, h.cpu().numpy())
+        dna.dna_group_iterate(g, 1)
+        assert dna.dna_group_get_status(g) == 0
+    finally:
+        dna.dna_group_destroy(g)
+
+
+def test_group_rejects_unsupported():
+    import paper_1301_3389_gb300 as dna
+    with pytest.raises(dna.DNAError) as e:
+        dna.dna_group_create([10], [10], [65])
+    assert e.value.code == dna.DNA_ERR_UNSUPPORTED
+    with pytest.raises(dna.DNAError) as e:
+        dna.dna_group_create([10], [10], [8], dna.make_opts(dtype=dna.DNA_BF16))
+    assert e.value.code == dna.DNA_ERR_UNSUPPORTED

@@ -116,6 +116,35 @@ int mu_step(dna_ctx* ctx, int which);
  * context's stream; also returns any error recorded by earlier kernels. */
 int dna_kl(dna_ctx* ctx, double* out);
 
+/* Gradient of d_KL(V, W H) (eq. 1) with respect to W, H and V, times `scale` (the
+ * incoming gradient of a loss), into caller-owned device buffers of the context's element
+ * type (any of them may be NULL): dW (N x R) = (1 - Q) H^t, dH (R x T) = W^t (1 - Q) (the
+ * KKT gradient of eq. 6 with lambda = 0), dV (N x T, leading dimension T) = log(V / Z)
+ * where v > 0 and 0 where v = 0 (the derivative of v log(v / z) - v, taken as 0 at
+ * v = 0), with Q = V / Z and Z = W H.  F32 and F64 forms.  Asynchronous; uses the
+ * context's workspace (so it must not overlap other calls on the same context). */
+int dna_kl_backward(dna_ctx* ctx, double scale, void* dW, void* dH, void* dV);
+
+/* ---------------------------------------------------------------- differentiation
+ * An unrolled DNA solve for H at fixed W (the H half-step without the step-16
+ * normalisation, repeated), and the adjoint of one such step for reverse-mode
+ * differentiation.  F32 and F64 forms; the adjoint needs R <= 128 (F32) or 64 (F64). */
+
+/* One H half-step at fixed W: Algorithm 1 steps 4-15 (eq. 7, 10, 11, 14, 15, 17 and the
+ * selection of Section 2.4), without step 16, so W is not modified.  If choice_out (device
+ * memory, T bytes) is not NULL it receives the per-column selection (1 = Newton).
+ * Asynchronous. */
+int dna_step_H_fixed(dna_ctx* ctx, uint8_t* choice_out);
+
+/* Adjoint of dna_step_H_fixed at the state Hk (R x T, device) with the selection `choice`
+ * (T bytes, device) that the forward step made (held fixed: the map is piecewise smooth
+ * and the selection, the eps floor and the alpha cap are treated as locally constant):
+ * given Hbar_next = dL/dH_{k+1} (R x T) writes Hbar_out = dL/dH_k (R x T) and ADDS dL/dV
+ * into Vbar (N x T, leading dimension T).  W is treated as a constant.  Uses the context's
+ * bound V and W.  Asynchronous. */
+int dna_step_H_adjoint(dna_ctx* ctx, const void* Hk, const uint8_t* choice,
+                       const void* Hbar_next, void* Hbar_out, void* Vbar);
+
 /* Copy the selection of the last DNA half-step to host memory: which = 0 gives T bytes
  * (column t of H took the Newton candidate iff out[t] = 1), which = 1 gives N bytes (per
  * row of W).  len must equal T (N).  Synchronises. */

@@ -102,6 +102,19 @@ def ratio(V, Z, power: int) -> np.ndarray:
     return out
 
 
+def kl_gradient(V, W, H):
+    """Gradient of eq. 1 at Z = W H: (dW, dH, dV) = ((1 - Q) H^t, W^t (1 - Q), log(V / Z)),
+    with Q = V / Z (0 where v = 0) and dV = 0 where v = 0 (derivative of v log(v/z) - v)."""
+    V, W, H = f64(V), f64(W), f64(H)
+    Z = W @ H
+    Q = ratio(V, Z, 1)
+    G = 1.0 - Q
+    dV = np.zeros_like(Z)
+    pos = V > 0
+    dV[pos] = np.log(V[pos] / Z[pos])
+    return G @ H.T, W.T @ G, dV
+
+
 # ---------------------------------------------------------------------- normalisation
 def normalize_w_columns(W, H, lam: float = 0.0):
     """Steps 1 and 29: divide column r of W by sum_n w_nr + lambda, multiply row r of H."""

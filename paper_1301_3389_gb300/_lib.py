@@ -64,6 +64,9 @@ def _load() -> ctypes.CDLL:
         "dna_profile": (I, [P, I]),
         "dna_phase_times": (I, [P, P, P, I]),
         "dna_kl_noalloc": (I, [P, I64, P, P, I64, I64, I64, P, P]),
+        "dna_kl_backward": (I, [P, D, P, P, P]),
+        "dna_step_H_fixed": (I, [P, P]),
+        "dna_step_H_adjoint": (I, [P, P, P, P, P, P]),
         "dna_group_create": (I, [I, P, P, P, ctypes.POINTER(dna_opts), ctypes.POINTER(P)]),
         "dna_group_bind": (I, [P, P, P, P, P]),
         "dna_group_set_stream": (I, [P, P]),
@@ -177,6 +180,22 @@ def dna_kl(ctx: int) -> float:
     out = ctypes.c_double()
     _check(LIB.dna_kl(ctx, ctypes.byref(out)), "dna_kl")
     return out.value
+
+
+def dna_kl_backward(ctx: int, scale: float, dW=None, dH=None, dV=None) -> None:
+    _check(LIB.dna_kl_backward(ctx, float(scale), _ptr(dW) if dW is not None else None,
+                               _ptr(dH) if dH is not None else None,
+                               _ptr(dV) if dV is not None else None), "dna_kl_backward")
+
+
+def dna_step_H_fixed(ctx: int, choice_out=None) -> None:
+    _check(LIB.dna_step_H_fixed(ctx, _ptr(choice_out) if choice_out is not None else None),
+           "dna_step_H_fixed")
+
+
+def dna_step_H_adjoint(ctx: int, Hk, choice, Hbar_next, Hbar_out, Vbar) -> None:
+    _check(LIB.dna_step_H_adjoint(ctx, _ptr(Hk), _ptr(choice), _ptr(Hbar_next), _ptr(Hbar_out),
+                                  _ptr(Vbar)), "dna_step_H_adjoint")
 
 
 def dna_get_choice(ctx: int, which: int, n: int):

@@ -1,0 +1,102 @@
+"""torch.autograd wrappers over the C ABI (argument marshalling only).
+
+* ``KLDiv.apply(V, W, H)``: d_KL(V, W H) of eq. 1; the backward pass is
+  ``dna_kl_backward`` (dW = (1 - Q) H^t, dH = W^t (1 - Q), dV = log(V / Z)).
+* ``UnrolledDNAH.apply(V, W, H0, K, every)``: K DNA H half-steps at fixed W
+  (``dna_step_H_fixed``), returning H_K; the backward pass runs ``dna_step_H_adjoint`` in
+  reverse, recomputing the states of each segment from checkpoints kept every ``every``
+  steps.  Gradients flow to V and H0; W is treated as a constant of the solve.
+
+Tensors are CUDA float32 (F32 form) or float64 (F64 form), contiguous, row-major.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import _lib as L
+
+
+def _ctx_for(V, W, H):
+    N, T = V.shape
+    R = W.shape[1]
+    dtype = L.DNA_F64 if V.dtype == torch.float64 else L.DNA_F32
+    ctx = L.dna_create(N, T, R, L.make_opts(dtype=dtype))
+    L.dna_set_stream(ctx)
+    L.dna_bind(ctx, V, W, H)
+    return ctx
+
+
+class KLDiv(torch.autograd.Function):
+    @staticmethod
+    def forward(fctx, V, W, H):
+        V, W, H = V.contiguous(), W.contiguous(), H.contiguous()
+        ctx = _ctx_for(V, W, H)
+        try:
+            kl = L.dna_kl(ctx)
+        finally:
+            L.dna_destroy(ctx)
+        fctx.save_for_backward(V, W, H)
+        return torch.tensor(kl, dtype=torch.float64, device=V.device)
+
+    @staticmethod
+    def backward(fctx, grad):
+        V, W, H = fctx.saved_tensors
+        need_v, need_w, need_h = fctx.needs_input_grad
+        dV = torch.empty_like(V) if need_v else None
+        dW = torch.empty_like(W) if need_w else None
+        dH = torch.empty_like(H) if need_h else None
+        ctx = _ctx_for(V, W, H)
+        try:
+            L.dna_kl_backward(ctx, float(grad), dW, dH, dV)
+            torch.cuda.current_stream().synchronize()
+        finally:
+            L.dna_destroy(ctx)
+        return dV, dW, dH
+
+
+class UnrolledDNAH(torch.autograd.Function):
+    @staticmethod
+    def forward(fctx, V, W, H0, K: int, every: int = 5):
+        V, W = V.contiguous(), W.contiguous()
+        H = H0.detach().clone().contiguous()
+        T = V.shape[1]
+        ctx = _ctx_for(V, W, H)
+        choices = torch.empty((K, T), dtype=torch.uint8, device=V.device)
+        ckpts = []
+        try:
+            for k in range(K):
+                if k % every == 0:
+                    ckpts.append(H.clone())
+                L.dna_step_H_fixed(ctx, choices[k])
+            torch.cuda.current_stream().synchronize()
+        finally:
+            L.dna_destroy(ctx)
+        fctx.K, fctx.every = K, every
+        fctx.save_for_backward(V, W, choices, *ckpts)
+        return H
+
+    @staticmethod
+    def backward(fctx, grad_HK):
+        V, W, choices, *ckpts = fctx.saved_tensors
+        K, every = fctx.K, fctx.every
+        Hbar = grad_HK.contiguous().clone()
+        Vbar = torch.zeros_like(V)
+        Hrun = ckpts[0].clone()
+        ctx = _ctx_for(V, W, Hrun)
+        try:
+            for seg in reversed(range(len(ckpts))):
+                k0, k1 = seg * every, min(seg * every + every, K)
+                Hrun.copy_(ckpts[seg])
+                states = [ckpts[seg]]
+                for _ in range(k0, k1 - 1):           # recompute this segment's states
+                    L.dna_step_H_fixed(ctx, None)
+                    states.append(Hrun.clone())
+                for k in reversed(range(k0, k1)):
+                    out = torch.empty_like(Hbar)
+                    L.dna_step_H_adjoint(ctx, states[k - k0], choices[k], Hbar, out, Vbar)
+                    Hbar = out
+            torch.cuda.current_stream().synchronize()
+        finally:
+            L.dna_destroy(ctx)
+        need_v = fctx.needs_input_grad[0]
+        return (Vbar if need_v else None), None, Hbar, None, None

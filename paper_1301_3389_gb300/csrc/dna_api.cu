@@ -318,6 +318,57 @@ int build_tc_maps(dna_ctx* c) {
     return DNA_OK;
 }
 
+// One H half-step at fixed W (Algorithm 1 steps 4-15, no step-16 normalisation); the
+// per-column choice is also copied to `choice_out` (device, T bytes) when given.
+template <typename Tp>
+int step_h_fixed(dna_ctx* c, uint8_t* choice_out) {
+    using S = dna::Simt<Tp>;
+    const View v = make_view(c, false);
+    cudaStream_t st = c->stream;
+    Tp* A = static_cast<Tp*>(c->Apart);
+    Tp* B = static_cast<Tp*>(c->Bpart);
+    Tp* Xmu = static_cast<Tp*>(c->Xmu);
+    Tp* Xdna = static_cast<Tp*>(c->Xdna);
+    int e = phase(c, DNA_PHASE_SUMS, 1, [&] { return S::factor_sums_y(v, c->o.lambda, c->c, c->fwork, st); });
+    if (!e) e = phase(c, DNA_PHASE_PASS1, 1, [&] {
+        return S::pass1(v, A, B, c->sp1[0], c->per1[0], true, c->status, st);
+    });
+    if (!e) e = phase(c, DNA_PHASE_CANDIDATES, 1, [&] {
+        return S::candidates(v, c->c, A, B, c->sp1[0], Xmu, Xdna, c->o.eps, c->o.alpha, st);
+    });
+    if (!e) e = phase(c, DNA_PHASE_PASS2, 1, [&] {
+        return S::pass2(v, Xmu, Xdna, c->dpart, c->sp2[0], c->per2[0], c->status, st);
+    });
+    if (!e) e = phase(c, DNA_PHASE_SELECT, 1, [&] {
+        return S::select(v, Xmu, Xdna, c->dpart, c->sp2[0], c->choice_h, c->dfin_h, st);
+    });
+    if (!e && choice_out &&
+        cudaMemcpyAsync(choice_out, c->choice_h, (size_t)c->T, cudaMemcpyDeviceToDevice, st) !=
+            cudaSuccess)
+        e = DNA_ERR_CUDA;
+    return e;
+}
+
+// Adjoint of step_h_fixed at state Hk with the recorded choices: Hbar_out = dL/dH_k from
+// Hbar_next = dL/dH_{k+1}; Vbar += dL/dV.
+template <typename Tp>
+int step_h_adjoint(dna_ctx* c, const Tp* Hk, const uint8_t* choice, const Tp* Hbar_next,
+                   Tp* Hbar_out, Tp* Vbar) {
+    using S = dna::Simt<Tp>;
+    View v = make_view(c, false);
+    v.X = const_cast<Tp*>(Hk);
+    cudaStream_t st = c->stream;
+    Tp* A = static_cast<Tp*>(c->Apart);
+    Tp* B = static_cast<Tp*>(c->Bpart);
+    int e = S::factor_sums_y(v, c->o.lambda, c->c, c->fwork, st);
+    if (!e) e = S::pass1(v, A, B, c->sp1[0], c->per1[0], true, c->status, st);
+    if (!e)
+        e = S::adjoint_h(v, c->c, A, B, c->sp1[0], choice, Hbar_next, Hbar_out,
+                         static_cast<Tp*>(c->Xmu), static_cast<Tp*>(c->Xdna), c->dpart, A,
+                         c->sp1[0], c->per1[0], Vbar, c->T, c->o.eps, c->o.alpha, c->status, st);
+    return e;
+}
+
 // The BF16 precision form: the two O(NRT) passes on tcgen05 tensor cores (bf16 operands,
 // float32 accumulation in TMEM), everything else as in the FP32 form.
 int half_step_tc(dna_ctx* c, int wstep, bool mu_only) {
@@ -375,6 +426,28 @@ int half_step_tc(dna_ctx* c, int wstep, bool mu_only) {
     });
     if (e) return e;
     return normalize<float>(c, wstep == 1 ? 1 : 0);
+}
+
+// Gradient of eq. 1 (no regularisation) with respect to W, H and V, scaled by `scale`:
+// dH = W^t (1 - Q) = (W^t 1) - W^t Q, dW = (1 - Q) H^t = (H 1)^t - Q H^t, dV = log(V / Z).
+// The raw W^t Q and Q H^t are pass 1 of the H and W views without the Qbar half.
+template <typename Tp>
+int kl_backward(dna_ctx* c, double scale, Tp* dW, Tp* dH, Tp* dV) {
+    using S = dna::Simt<Tp>;
+    cudaStream_t st = c->stream;
+    Tp* A = static_cast<Tp*>(c->Apart);
+    for (int w = 0; w < 2; ++w) {
+        Tp* G = w ? dW : dH;
+        if (!G) continue;
+        const View v = make_view(c, w == 1);
+        int e = S::factor_sums_y(v, 0.0, c->c, c->fwork, st);
+        if (!e) e = S::pass1(v, A, A, c->sp1[w], c->per1[w], false, c->status, st);
+        if (!e) e = w ? S::grad_x(v, c->c, A, c->sp1[w], scale, G, 1, c->R, st)
+                      : S::grad_x(v, c->c, A, c->sp1[w], scale, G, c->T, 1, st);
+        if (e) return e;
+    }
+    if (dV) return S::grad_v(make_view(c, false), scale, dV, c->T, c->status, st);
+    return DNA_OK;
 }
 
 template <typename Tp>
@@ -596,6 +669,39 @@ int dna_kl(dna_ctx* c, double* out) {
         cudaSuccess)
         return DNA_ERR_CUDA;
     return read_status(c);
+}
+
+int dna_step_H_fixed(dna_ctx* c, uint8_t* choice_out) {
+    if (int e = check_ready(c)) return e;
+    if (c->tc) return DNA_ERR_UNSUPPORTED;
+    if (set_device(c)) return DNA_ERR_CUDA;
+    return is_f64(c) ? step_h_fixed<double>(c, choice_out) : step_h_fixed<float>(c, choice_out);
+}
+
+int dna_step_H_adjoint(dna_ctx* c, const void* Hk, const uint8_t* choice, const void* Hbar_next,
+                       void* Hbar_out, void* Vbar) {
+    if (int e = check_ready(c)) return e;
+    if (!Hk || !choice || !Hbar_next || !Hbar_out || !Vbar) return DNA_ERR_ARG;
+    if (c->tc || (is_f64(c) ? c->R > 64 : c->R > 128)) return DNA_ERR_UNSUPPORTED;
+    if (set_device(c)) return DNA_ERR_CUDA;
+    if (is_f64(c))
+        return step_h_adjoint<double>(c, static_cast<const double*>(Hk), choice,
+                                      static_cast<const double*>(Hbar_next),
+                                      static_cast<double*>(Hbar_out), static_cast<double*>(Vbar));
+    return step_h_adjoint<float>(c, static_cast<const float*>(Hk), choice,
+                                 static_cast<const float*>(Hbar_next), static_cast<float*>(Hbar_out),
+                                 static_cast<float*>(Vbar));
+}
+
+int dna_kl_backward(dna_ctx* c, double scale, void* dW, void* dH, void* dV) {
+    if (int e = check_ready(c)) return e;
+    if (c->tc) return DNA_ERR_UNSUPPORTED;
+    if (set_device(c)) return DNA_ERR_CUDA;
+    if (is_f64(c))
+        return kl_backward<double>(c, scale, static_cast<double*>(dW), static_cast<double*>(dH),
+                                   static_cast<double*>(dV));
+    return kl_backward<float>(c, scale, static_cast<float*>(dW), static_cast<float*>(dH),
+                              static_cast<float*>(dV));
 }
 
 int dna_get_choice(dna_ctx* c, int which, uint8_t* out, int64_t len) {

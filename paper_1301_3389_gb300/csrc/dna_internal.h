@@ -72,6 +72,19 @@ template <typename Tp> struct Simt {
     // per-column full KL terms of eq. 1 for x = the view's X, partials [splits][O]
     static int kl_columns(const View& v, double* dpart, int splits, int64_t s_per,
                           int* status, cudaStream_t st);
+    // gradient of eq. 1 w.r.t. X from raw pass-1 sums: G(r, o) at G[r * gr + o * go]
+    static int grad_x(const View& v, const double* c, const Tp* Apart, int splits, double scale,
+                      Tp* G, int64_t gr, int64_t go, cudaStream_t st);
+    // gradient of eq. 1 w.r.t. V: dV(s, o) = scale log(v / z) (0 where v = 0)
+    static int grad_v(const View& v, double scale, Tp* dV, int64_t ldd, int* status,
+                      cudaStream_t st);
+    // adjoint of one H step at fixed W (see k_adj_elem / k_adj_gemm): Hbar0 = dL/dH_k given
+    // Hbar1 = dL/dH_{k+1}; Vbar += dL/dV.  Uses A, B (pass 1 of H_k) and the column choices.
+    static int adjoint_h(const View& v, const double* c, const Tp* Apart, const Tp* Bpart,
+                         int splits1, const uint8_t* choice, const Tp* Hbar1, Tp* Hbar0,
+                         Tp* Abar, Tp* Bbar, double* vs, Tp* Hpart, int splits2, int64_t s_per2,
+                         Tp* Vbar, int64_t ldvb, double eps, double alpha, int* status,
+                         cudaStream_t st);
     // one-time: row and column sums of V (float64) and the transposed copy
     static int prepare_v(const Tp* V, int64_t N, int64_t T, int64_t ldv, Tp* Vt, int64_t ldvt,
                          double* colsum, double* rowsum, cudaStream_t st);

@@ -446,6 +446,299 @@ __global__ void __launch_bounds__(256) k_select(View v, const Tp* __restrict__ X
     select_tile<Tp>(v, Xmu, Xdna, dpart, splits, choice, dfin, blockIdx.x);
 }
 
+// Gradient of eq. 1 with respect to the view's X from the raw pass-1 sums:
+// G(r, o) = scale * (c_r - sum over splits of Apart(r, o)) = scale * sum_s y(s, r)(1 - q(s, o)),
+// written to G[r * gr + o * go].  CTA = 32 values of o x 8 groups of r.
+template <typename Tp>
+__global__ void __launch_bounds__(256) k_grad_x(View v, const double* __restrict__ c,
+                                                const Tp* __restrict__ Apart, int splits,
+                                                double scale, Tp* __restrict__ G, int64_t gr,
+                                                int64_t go) {
+    const int64_t o = (int64_t)blockIdx.x * 32 + threadIdx.x;
+    if (o >= v.O) return;
+    const Tp sc = (Tp)scale;
+    for (int64_t r = threadIdx.y; r < v.R; r += 8) {
+        Tp a = Tp(0);
+        for (int sp = 0; sp < splits; ++sp) a += Apart[((int64_t)sp * v.R + r) * v.O + o];
+        G[r * gr + o * go] = sc * ((Tp)c[r] - a);
+    }
+}
+
+// Gradient of eq. 1 with respect to V: dV(s, o) = scale * log(v / z) where v > 0, else 0,
+// with z(s, o) = sum_r y(s, r) x(r, o).  One CTA per 64 x 64 tile of (s, o).
+template <typename Tp, int RB>
+__global__ void __launch_bounds__(NT) k_grad_v(View v, double scale, Tp* __restrict__ dV,
+                                               int64_t ldd, int* __restrict__ status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Tp* Yt = reinterpret_cast<Tp*>(smem_raw);  // [RB][LD]
+    Tp* Xs = Yt + RB * LD;                     // [RB][LD]
+    const Tp* __restrict__ V = static_cast<const Tp*>(v.V);
+    const Tp* __restrict__ X = static_cast<const Tp*>(v.X);
+    const Tp* __restrict__ Y = static_cast<const Tp*>(v.Y);
+    const int tid = threadIdx.x;
+    const int64_t o0 = (int64_t)blockIdx.x * OB, s0 = (int64_t)blockIdx.y * SB;
+    const int zo = (tid % 16) * 4, zs = (tid / 16) * 4;
+    Tp z[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) z[i][j] = Tp(0);
+    for (int64_t p = 0; p * RB < v.R; ++p) {
+        load_tile<Tp, RB, OB>(Xs, X, v.xr, v.xo, p * RB, o0, v.R, v.O);
+        load_tile<Tp, RB, SB>(Yt, Y, v.yr, v.ys, p * RB, s0, v.R, v.S);
+        __syncthreads();
+        z_tile<Tp, RB>(Yt, Xs, zs, zo, z);
+        __syncthreads();
+    }
+    int bad = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t s = s0 + zs + i;
+        if (s >= v.S) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t o = o0 + zo + j;
+            if (o >= v.O) continue;
+            const Tp vv = V[s * v.vs + o];
+            Tp g = Tp(0);
+            if (vv > Tp(0)) {
+                if (z[i][j] > Tp(0)) g = (Tp)scale * dev_log(vv / z[i][j]);
+                else bad = 1;
+            }
+            dV[s * ldd + o] = g;
+        }
+    }
+    if (bad) atomicOr(status, STATUS_NONFINITE);
+}
+
+// ------------------------------------------------------------------ adjoint of the H step
+// One H half-step at fixed W (Algorithm 1 steps 2-15, no normalisation) maps column h to
+//   MU column:     h'_r = h_r A_r / c_r                                  (eq. 11)
+//   Newton column: h'_r = s g_r / D,  D = sum_l c_l g_l,  s = sum_n v_n  (eq. 10)
+//                  g_r = h^2 b / (h b - a) (a < 0, gain > eps), eps h (floor),
+//                        h + a / b (a >= 0, below the cap), (1 + alpha) h (cap)
+// with a = A / c - 1, b = B / c, A = W^t (V / Z), B = (W o W)^t (V / Z^2), Z = W H.  The
+// selection (which column took which candidate) is held fixed.  Given hb' = dL/dh', this
+// kernel forms, per column, the direct part of dL/dh, the adjoints Abar = dL/dA and
+// Bbar = dL/dB (raw sums), and vs = dL/ds.  CTA = 32 columns x 8 groups of r.
+template <typename Tp>
+__global__ void __launch_bounds__(256)
+    k_adj_elem(View v, const double* __restrict__ c, const Tp* __restrict__ Apart,
+               const Tp* __restrict__ Bpart, int splits, const uint8_t* __restrict__ choice,
+               const Tp* __restrict__ Hbar1, Tp* __restrict__ Hbar0, Tp* __restrict__ Abar,
+               Tp* __restrict__ Bbar, double* __restrict__ vs, Tp eps, Tp alpha) {
+    __shared__ double red[2][8][32];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int64_t o = (int64_t)blockIdx.x * 32 + tx;
+    const bool live = o < v.O;
+    const Tp* __restrict__ X = static_cast<const Tp*>(v.X);
+    const bool newton = live && choice[o];
+    // pass 1 over r: D = sum c g and sum hb' g (Newton columns)
+    double dsum = 0.0, hg = 0.0;
+    if (newton) {
+        for (int64_t r = ty; r < v.R; r += 8) {
+            Tp ra = Tp(0), rb = Tp(0);
+            for (int sp = 0; sp < splits; ++sp) {
+                ra += Apart[((int64_t)sp * v.R + r) * v.O + o];
+                rb += Bpart[((int64_t)sp * v.R + r) * v.O + o];
+            }
+            const Tp cr = (Tp)c[r], x = X[r * v.xr + o * v.xo];
+            const Tp a = ra / cr - Tp(1), b = rb / cr;
+            Tp g;
+            if (a < Tp(0)) {
+                const Tp xb = x * b, gain = xb / (xb - a);
+                g = x * (gain > eps ? gain : eps);
+            } else {
+                const Tp st = b > Tp(0) ? a / b : Tp(0), cap = alpha * x;
+                g = x + (st < cap ? st : cap);
+            }
+            dsum += (double)(cr * g);
+            hg += (double)(Hbar1[r * v.xr + o * v.xo] * g);
+        }
+    }
+    red[0][ty][tx] = dsum;
+    red[1][ty][tx] = hg;
+    __syncthreads();
+    if (!live) return;
+    double D = 0.0, HG = 0.0;
+    for (int k = 0; k < 8; ++k) { D += red[0][k][tx]; HG += red[1][k][tx]; }
+    const double s_o = v.vsum[o];
+    const bool renorm = D > 0.0;
+    const Tp f1 = (Tp)(renorm ? s_o / D : 1.0);            // d h' / d g (diagonal part)
+    const Tp f2 = (Tp)(renorm ? s_o * HG / (D * D) : 0.0); // weight of the D coupling
+    if (ty == 0) vs[o] = (newton && renorm) ? HG / D : 0.0;
+    for (int64_t r = ty; r < v.R; r += 8) {
+        Tp ra = Tp(0), rb = Tp(0);
+        for (int sp = 0; sp < splits; ++sp) {
+            ra += Apart[((int64_t)sp * v.R + r) * v.O + o];
+            rb += Bpart[((int64_t)sp * v.R + r) * v.O + o];
+        }
+        const Tp cr = (Tp)c[r], x = X[r * v.xr + o * v.xo];
+        const Tp hb1 = Hbar1[r * v.xr + o * v.xo];
+        const Tp a = ra / cr - Tp(1), b = rb / cr;
+        Tp hx, ab = Tp(0), bb = Tp(0);   // dL/dh (direct), dL/da, dL/db
+        if (!newton) {                   // h' = h (1 + a)
+            hx = hb1 * (Tp(1) + a);
+            ab = hb1 * x;
+        } else {
+            const Tp gb = f1 * hb1 - cr * f2;   // dL/dg_r
+            if (a < Tp(0)) {
+                const Tp xb = x * b, den = xb - a, gain = xb / den;
+                if (gain > eps) {                // g = x^2 b / (x b - a)
+                    const Tp d2 = den * den;
+                    hx = gb * xb * (xb - Tp(2) * a) / d2;
+                    ab = gb * x * xb / d2;
+                    bb = -gb * a * x * x / d2;
+                } else {                         // floor: g = eps x
+                    hx = gb * eps;
+                }
+            } else {
+                const Tp st = b > Tp(0) ? a / b : Tp(0), cap = alpha * x;
+                if (st < cap) {                  // g = x + a / b
+                    hx = gb;
+                    if (b > Tp(0)) { ab = gb / b; bb = -gb * a / (b * b); }
+                } else {                         // cap: g = (1 + alpha) x
+                    hx = gb * (Tp(1) + alpha);
+                }
+            }
+        }
+        Hbar0[r * v.xr + o * v.xo] = hx;
+        Abar[r * v.O + o] = ab / cr;     // a = A / c - 1
+        Bbar[r * v.O + o] = bb / cr;     // b = B / c
+    }
+}
+
+template <typename Tp, int RB>
+struct AdjCfg {
+    static constexpr int RPT = RB / 16;
+    static constexpr size_t smem = (size_t)(4 * RB * LD + SB * LD) * sizeof(Tp);
+};
+
+// The GEMM-shaped part of the adjoint, per (o-block, r-block = all R <= RB, s-split):
+//   P1 = Y Abar, P2 = (Y o Y) Bbar                       (z-tiles, K = R)
+//   zbar = -qbar P1 - 2 (qbar / z) P2,  qbar = v / z^2    (through A and B)
+//   Hpart += Y^t zbar                                    (through z = W h)
+//   Vbar(s, o) += P1 / z + P2 / z^2 + vs_o               (through q, qbar and s)
+// Vbar is owned element-wise by one thread per split range, so it is updated in place.
+template <typename Tp, int RB>
+__global__ void __launch_bounds__(NT)
+    k_adj_gemm(View v, const Tp* __restrict__ Abar, const Tp* __restrict__ Bbar,
+               const double* __restrict__ vs, Tp* __restrict__ Hpart, Tp* __restrict__ Vbar,
+               int64_t ldvb, int64_t s_per, int* __restrict__ status) {
+    using C = AdjCfg<Tp, RB>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Tp* Xs = reinterpret_cast<Tp*>(smem_raw);  // [RB][LD] x(r, o)
+    Tp* As = Xs + RB * LD;                     // [RB][LD] Abar(r, o)
+    Tp* Bs = As + RB * LD;                     // [RB][LD] Bbar(r, o)
+    Tp* Yt = Bs + RB * LD;                     // [RB][LD] y(s, r) transposed
+    Tp* Zb = Yt + RB * LD;                     // [SB][LD] zbar(s, o)
+    const Tp* __restrict__ V = static_cast<const Tp*>(v.V);
+    const Tp* __restrict__ X = static_cast<const Tp*>(v.X);
+    const Tp* __restrict__ Y = static_cast<const Tp*>(v.Y);
+    const int tid = threadIdx.x;
+    const int64_t o0 = (int64_t)blockIdx.x * OB;
+    const int64_t s_begin = (int64_t)blockIdx.y * s_per;
+    const int64_t s_end = min(v.S, s_begin + s_per);
+    const int zo = (tid % 16) * 4, zs = (tid / 16) * 4;
+    const int go = (tid % 16) * 4, gr = tid / 16;
+    Tp acc[C::RPT][4];
+#pragma unroll
+    for (int i = 0; i < C::RPT; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = Tp(0);
+    load_tile<Tp, RB, OB>(Xs, X, v.xr, v.xo, 0, o0, v.R, v.O);
+    load_tile<Tp, RB, OB>(As, Abar, v.O, 1, 0, o0, v.R, v.O);
+    load_tile<Tp, RB, OB>(Bs, Bbar, v.O, 1, 0, o0, v.R, v.O);
+    int bad = 0;
+    for (int64_t s0 = s_begin; s0 < s_end; s0 += SB) {
+        load_tile<Tp, RB, SB>(Yt, Y, v.yr, v.ys, 0, s0, v.R, v.S);
+        __syncthreads();
+        Tp z[4][4], p1[4][4], p2[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) { z[i][j] = Tp(0); p1[i][j] = Tp(0); p2[i][j] = Tp(0); }
+        z_tile<Tp, RB>(Yt, Xs, zs, zo, z);
+        z_tile<Tp, RB>(Yt, As, zs, zo, p1);
+#pragma unroll 4
+        for (int r = 0; r < RB; ++r) {   // P2 = (Y o Y) Bbar
+            Tp ba[4], ya[4];
+            ld4(Bs + r * LD + zo, ba);
+            ld4(Yt + r * LD + zs, ya);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) p2[i][j] = fma(ya[i] * ya[i], ba[j], p2[i][j]);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int64_t s = s0 + zs + i;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int64_t o = o0 + zo + j;
+                Tp zb = Tp(0);
+                if (s < s_end && o < v.O) {
+                    const Tp vv = V[s * v.vs + o], zz = z[i][j];
+                    Tp vb = (Tp)vs[o];
+                    if (vv > Tp(0)) {
+                        if (zz > Tp(0)) {
+                            const Tp iz = Tp(1) / zz, qb = vv * iz * iz;
+                            zb = -qb * p1[i][j] - Tp(2) * qb * iz * p2[i][j];
+                            vb += p1[i][j] * iz + p2[i][j] * iz * iz;
+                        } else {
+                            bad = 1;
+                        }
+                    } else if (zz > Tp(0)) {
+                        const Tp iz = Tp(1) / zz;
+                        vb += p1[i][j] * iz + p2[i][j] * iz * iz;
+                    }
+                    Vbar[s * ldvb + o] += vb;
+                }
+                Zb[(zs + i) * LD + zo + j] = zb;
+            }
+        }
+        __syncthreads();
+        // Hpart(r, o) += sum_s y(s, r) zbar(s, o)
+#pragma unroll 2
+        for (int s = 0; s < SB; ++s) {
+            Tp zv[4];
+            ld4(Zb + s * LD + go, zv);
+#pragma unroll
+            for (int i = 0; i < C::RPT; ++i) {
+                const Tp y = Yt[(gr + 16 * i) * LD + s];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(y, zv[j], acc[i][j]);
+            }
+        }
+        __syncthreads();
+    }
+    if (bad) atomicOr(status, STATUS_NONFINITE);
+    const int64_t base = (int64_t)blockIdx.y * v.R;
+#pragma unroll
+    for (int i = 0; i < C::RPT; ++i) {
+        const int64_t r = gr + 16 * i;
+        if (r >= v.R) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t o = o0 + go + j;
+            if (o < v.O) Hpart[(base + r) * v.O + o] = acc[i][j];
+        }
+    }
+}
+
+// Hbar(r, o) += sum over splits of Hpart(r, o).
+template <typename Tp>
+__global__ void __launch_bounds__(256) k_adj_combine(View v, const Tp* __restrict__ Hpart,
+                                                     int splits, Tp* __restrict__ Hbar) {
+    const int64_t o = (int64_t)blockIdx.x * 32 + threadIdx.x;
+    if (o >= v.O) return;
+    for (int64_t r = threadIdx.y; r < v.R; r += 8) {
+        Tp t = Tp(0);
+        for (int sp = 0; sp < splits; ++sp) t += Hpart[((int64_t)sp * v.R + r) * v.O + o];
+        Hbar[r * v.xr + o * v.xo] += t;
+    }
+}
+
 // A factor sum that is exactly zero (an all-zero column of W or row of H without
 // regularisation, excluded by the assumption of Section 2) is replaced by 1.
 __device__ __forceinline__ double nonzero_sum(double s, bool guard) {

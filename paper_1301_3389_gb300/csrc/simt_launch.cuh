@@ -186,6 +186,78 @@ int Simt<Tp>::kl_columns(const View& v, double* dpart, int splits, int64_t s_per
 }
 
 template <typename Tp>
+int Simt<Tp>::grad_x(const View& v, const double* c, const Tp* A, int splits, double scale,
+                     Tp* G, int64_t gr, int64_t go, cudaStream_t st) {
+    simt::k_grad_x<Tp><<<(unsigned)((v.O + 31) / 32), dim3(32, 8), 0, st>>>(v, c, A, splits, scale,
+                                                                           G, gr, go);
+    return simt::launch_status();
+}
+
+namespace simt {
+template <typename Tp, int RB>
+int grad_v_rb(const View& v, double scale, Tp* dV, int64_t ldd, int* status, cudaStream_t st) {
+    const size_t smem = (size_t)(2 * RB * LD) * sizeof(Tp);
+    auto k = k_grad_v<Tp, RB>;
+    if (prep_smem(k, smem)) return DNA_ERR_CUDA;
+    dim3 grid((unsigned)((v.O + OB - 1) / OB), (unsigned)((v.S + SB - 1) / SB));
+    k<<<grid, NT, smem, st>>>(v, scale, dV, ldd, status);
+    return launch_status();
+}
+}  // namespace simt
+
+template <typename Tp>
+int Simt<Tp>::grad_v(const View& v, double scale, Tp* dV, int64_t ldd, int* status,
+                     cudaStream_t st) {
+    switch (simt::rblock_for<Tp>(v.R)) {
+        case 32: return simt::grad_v_rb<Tp, 32>(v, scale, dV, ldd, status, st);
+        case 64: return simt::grad_v_rb<Tp, 64>(v, scale, dV, ldd, status, st);
+        default:
+            if constexpr (sizeof(Tp) == 4) return simt::grad_v_rb<Tp, 128>(v, scale, dV, ldd, status, st);
+            return DNA_ERR_UNSUPPORTED;
+    }
+}
+
+namespace simt {
+template <typename Tp, int RB>
+int adj_gemm_rb(const View& v, const Tp* Abar, const Tp* Bbar, const double* vs, Tp* Hpart,
+                int splits, int64_t s_per, Tp* Vbar, int64_t ldvb, int* status, cudaStream_t st) {
+    const size_t smem = AdjCfg<Tp, RB>::smem;
+    auto k = k_adj_gemm<Tp, RB>;
+    if (prep_smem(k, smem)) return DNA_ERR_CUDA;
+    dim3 grid((unsigned)((v.O + OB - 1) / OB), (unsigned)splits);
+    k<<<grid, NT, smem, st>>>(v, Abar, Bbar, vs, Hpart, Vbar, ldvb, s_per, status);
+    return launch_status();
+}
+}  // namespace simt
+
+template <typename Tp>
+int Simt<Tp>::adjoint_h(const View& v, const double* c, const Tp* Apart, const Tp* Bpart,
+                        int splits1, const uint8_t* choice, const Tp* Hbar1, Tp* Hbar0, Tp* Abar,
+                        Tp* Bbar, double* vs, Tp* Hpart, int splits2, int64_t s_per2, Tp* Vbar,
+                        int64_t ldvb, double eps, double alpha, int* status, cudaStream_t st) {
+    simt::k_adj_elem<Tp><<<(unsigned)((v.O + 31) / 32), dim3(32, 8), 0, st>>>(
+        v, c, Apart, Bpart, splits1, choice, Hbar1, Hbar0, Abar, Bbar, vs, (Tp)eps, (Tp)alpha);
+    if (simt::launch_status()) return DNA_ERR_CUDA;
+    int e;
+    switch (simt::rblock_for<Tp>(v.R)) {
+        case 32: e = simt::adj_gemm_rb<Tp, 32>(v, Abar, Bbar, vs, Hpart, splits2, s_per2, Vbar, ldvb, status, st); break;
+        case 64: e = simt::adj_gemm_rb<Tp, 64>(v, Abar, Bbar, vs, Hpart, splits2, s_per2, Vbar, ldvb, status, st); break;
+        default:
+            if constexpr (sizeof(Tp) == 4) {
+                if (v.R <= 128) {
+                    e = simt::adj_gemm_rb<Tp, 128>(v, Abar, Bbar, vs, Hpart, splits2, s_per2, Vbar, ldvb, status, st);
+                    break;
+                }
+            }
+            return DNA_ERR_UNSUPPORTED;
+    }
+    if (e) return e;
+    simt::k_adj_combine<Tp><<<(unsigned)((v.O + 31) / 32), dim3(32, 8), 0, st>>>(v, Hpart, splits2,
+                                                                                 Hbar0);
+    return simt::launch_status();
+}
+
+template <typename Tp>
 int Simt<Tp>::prepare_v(const Tp* V, int64_t N, int64_t T, int64_t ldv, Tp* Vt, int64_t ldvt,
                         double* colsum, double* rowsum, cudaStream_t st) {
     dim3 blk(32, 8);

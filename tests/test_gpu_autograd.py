@@ -1,0 +1,111 @@
+"""The differentiation form against the FP64 references.
+
+* KLDiv: torch.autograd.gradcheck in FP64 (finite differences of the library's own d_KL),
+  and dW, dH, dV against the oracle's analytic gradient (FP64 1e-10, FP32 1e-4 relative).
+* UnrolledDNAH (K H steps at fixed W) composed with KLDiv and an L2 penalty on H_K:
+  gradients with respect to V and H0 against torch.autograd of the FP64 reference in
+  oracle/unrolled.py, replaying the GPU's selections (FP64 1e-8; FP32 2e-3 relative).
+"""
+import numpy as np
+import pytest
+
+import workloads
+from gpu_helpers import rel_fro
+from oracle import dna as o
+from oracle import unrolled as u
+
+pytestmark = pytest.mark.gpu
+
+
+def _t(x, dtype):
+    import torch
+    return torch.tensor(np.ascontiguousarray(x), dtype=dtype, device="cuda")
+
+
+@pytest.mark.parametrize("kind", ["f64", "f32"])
+def test_kl_gradient(kind):
+    import torch
+
+    from paper_1301_3389_gb300.autograd import KLDiv
+    dt = torch.float64 if kind == "f64" else torch.float32
+    p = workloads.custom(67, 131, 9, seed=31)
+    V, W, H = (_t(x, dt).requires_grad_(True) for x in (p.V, p.W, p.H))
+    loss = KLDiv.apply(V, W, H)
+    loss.backward()
+    dW, dH, dV = o.kl_gradient(p.V, p.W, p.H)
+    tol = 1e-10 if kind == "f64" else 1e-4
+    assert abs(float(loss) - o.kl_divergence(p.V, p.W.astype(np.float64) @ p.H)) <= tol * float(loss)
+    assert rel_fro(W.grad.double().cpu().numpy(), dW) < tol
+    assert rel_fro(H.grad.double().cpu().numpy(), dH) < tol
+    assert rel_fro(V.grad.double().cpu().numpy(), dV) < tol
+
+
+def test_kl_gradcheck():
+    import torch
+
+    from paper_1301_3389_gb300.autograd import KLDiv
+    p = workloads.custom(12, 17, 3, seed=32)
+    V = _t(p.V + 0.5, torch.float64).requires_grad_(True)   # strictly positive V: smooth
+    W = _t(p.W, torch.float64).requires_grad_(True)
+    H = _t(p.H, torch.float64).requires_grad_(True)
+    assert torch.autograd.gradcheck(KLDiv.apply, (V, W, H), eps=1e-6, atol=1e-6, rtol=1e-5)
+
+
+def _gpu_choices(V, W, H0, K):
+    import torch
+
+    import paper_1301_3389_gb300 as dna
+    N, T = V.shape
+    ctx = dna.dna_create(N, T, W.shape[1], dna.make_opts(
+        dtype=dna.DNA_F64 if V.dtype == torch.float64 else dna.DNA_F32))
+    H = H0.detach().clone()
+    ch = torch.empty((K, T), dtype=torch.uint8, device="cuda")
+    try:
+        dna.dna_set_stream(ctx)
+        dna.dna_bind(ctx, V.detach(), W.detach(), H)
+        for k in range(K):
+            dna.dna_step_H_fixed(ctx, ch[k])
+        torch.cuda.synchronize()
+    finally:
+        dna.dna_destroy(ctx)
+    return [torch.from_numpy(c.cpu().numpy().astype(bool)) for c in ch], H
+
+
+def _unrolled_case(p, K, every, kind, tol):
+    import torch
+
+    from paper_1301_3389_gb300.autograd import KLDiv, UnrolledDNAH
+    dt = torch.float64 if kind == "f64" else torch.float32
+    mu = 1e-3 * float(p.V.mean()) / float(p.H.mean()) ** 2
+    V = _t(p.V, dt).requires_grad_(True)
+    W = _t(p.W, dt)
+    H0 = _t(p.H, dt).requires_grad_(True)
+    choices, HK_ref_gpu = _gpu_choices(V, W, H0, K)
+    HK = UnrolledDNAH.apply(V, W, H0, K, every)
+    assert torch.equal(HK.detach(), HK_ref_gpu)              # the Function's forward is the solve
+    loss = KLDiv.apply(V, W, HK) + 0.5 * mu * (HK.double() ** 2).sum()
+    loss.backward()
+    ref_loss, gV, gH, used = u.loss_and_grads(p.V, p.W, p.H, K, mu, choices=choices)
+    assert abs(float(loss) - ref_loss) <= max(tol, 1e-6) * abs(ref_loss)
+    ev = rel_fro(V.grad.double().cpu().numpy(), gV)
+    eh = rel_fro(H0.grad.double().cpu().numpy(), gH)
+    assert ev < tol and eh < tol, (ev, eh)
+    return ev, eh
+
+
+@pytest.mark.parametrize("kind", ["f64", "f32"])
+def test_unrolled_small(kind):
+    p = workloads.custom(70, 130, 9, seed=33)
+    _unrolled_case(p, K=6, every=2, kind=kind, tol=1e-8 if kind == "f64" else 2e-3)
+
+
+def test_unrolled_ragged_ranks():
+    for (n, t, r) in [(129, 257, 33), (64, 200, 64), (40, 90, 128)]:
+        p = workloads.custom(n, t, r, seed=n + t + r)
+        _unrolled_case(p, K=4, every=3, kind="f32", tol=2e-3)
+
+
+def test_unrolled_diff_form_config():
+    """N=1024 R=64 T=4096, K=20 unrolled steps, checkpoints every 5 steps, FP32."""
+    p = workloads.diff_form(0)
+    _unrolled_case(p, K=20, every=5, kind="f32", tol=2e-3)

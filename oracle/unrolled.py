@@ -6,6 +6,8 @@ TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).  Each step is Algorithm 1 ste
 written with the same readings as oracle/dna.py (which its forward is tested against).
 The selection, the eps floor and the alpha cap are piecewise choices: autograd
 differentiates the branch that was taken.  ``choices`` replays given selections.
+Derivatives at v = 0: q = v / z is smooth there (derivative 1 / z); the loss term
+v log(v / z) - v is not, and its derivative is taken as 0 (as dna_kl_backward does).
 """
 from __future__ import annotations
 
@@ -21,9 +23,11 @@ def h_step(V, W, H, eps=EPS, alpha=ALPHA, lam=0.0, choice=None):
     c = torch.where(c == 0, torch.ones_like(c), c)
     Z = W @ H                                              # step 2
     pos = V > 0
-    Zs = torch.where(pos, Z, torch.ones_like(Z))           # z only where v > 0 enters a ratio
-    Q = torch.where(pos, V / Zs, torch.zeros_like(Z))      # step 3
-    Qb = torch.where(pos, V / (Zs * Zs), torch.zeros_like(Z))
+    # q = v / z and qbar = v / z^2 (0 where v = 0); as functions of v they are smooth at
+    # v = 0, so their derivative there is 1 / z (resp. 1 / z^2): divide wherever z > 0
+    Zs = torch.where(Z > 0, Z, torch.ones_like(Z))
+    Q = V / Zs                                             # step 3
+    Qb = V / (Zs * Zs)
     A = (W.t() @ Q) / c[:, None] - 1.0                     # step 5 (eq. 7)
     B = ((W * W).t() @ Qb) / c[:, None]                    # step 10 (eq. 14)
     H_mu = H + A * H                                       # step 6 (eq. 11)
@@ -62,11 +66,13 @@ def unrolled(V, W, H0, K, eps=EPS, alpha=ALPHA, lam=0.0, choices=None):
 
 
 def kl(V, Z):
-    """Eq. 1 in torch (for losses)."""
+    """Eq. 1 in torch (for losses), as sum_{v>0} (v log(v/z) - v) + sum z: the same value,
+    with the derivative in v taken as 0 where v = 0 (v log v - v is not differentiable
+    there), the reading of dna_kl_backward."""
     pos = V > 0
     Zp = torch.where(pos, Z, torch.ones_like(Z))
     Vp = torch.where(pos, V, torch.ones_like(V))
-    return torch.where(pos, V * torch.log(Vp / Zp), torch.zeros_like(Z)).sum() - V.sum() + Z.sum()
+    return torch.where(pos, V * torch.log(Vp / Zp) - V, torch.zeros_like(Z)).sum() + Z.sum()
 
 
 def loss_and_grads(V, W, H0, K, mu, choices=None):

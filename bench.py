@@ -203,6 +203,8 @@ def main(argv=None):
     ap.add_argument("--ref-cols", type=int, default=512)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the BF16 line and time-to-target")
+    ap.add_argument("--target-iters", type=int, default=200)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -232,24 +234,81 @@ def main(argv=None):
 
     prob = spec["fn"](rank)                      # independent problem per rank
     N, T, R = spec["N"], spec["T"], spec["R"]
-    code = {"f32": dna.DNA_F32, "f64": dna.DNA_F64, "bf16": dna.DNA_BF16}[args.dtype]
-    tdt = torch.float64 if args.dtype == "f64" else torch.float32
     dev = torch.device("cuda", local)
+    peaks = measured_peaks()
+
+    res = measure(dna, torch, dist, prob, args.dtype, args, world, local, peaks, clocks=True)
+    line = {
+        "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_max"] / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.dtype,
+        "data": "synthetic",
+        "config": {"workload": args.workload, "desc": spec["desc"], "N": N, "T": T, "R": R,
+                   "form": args.dtype.upper(),
+                   "engine": "tcgen05" if args.dtype == "bf16" else "simt",
+                   "l2": "inputs larger than L2 (V is %d MB)" % (N * T * 4 // 2**20),
+                   "parallelism": "independent problem per GPU" if world > 1 else "single GPU",
+                   "zero_fraction": prob.meta.get("zero_fraction")},
+        "gpu_launches": res["launches"],
+        "roofline": res["roofline"],
+        "clocks": res["clocks"],
+        "kl_start": res["kl_start"], "kl_end": res["kl_end"],
+    }
+    if args.dtype == "f32" and not args.no_forms:
+        # the other form on the same workload, and seconds to the FP32 form's target d_KL
+        bf = measure(dna, torch, dist, prob, "bf16", args, world, local, peaks, clocks=False)
+        line["bf16_form"] = {"value": bf["value"], "unit": UNIT,
+                             "ms_per_step": bf["ms_max"] / args.steps, "roofline": bf["roofline"],
+                             "gpu_launches": bf["launches"]}
+        line["time_to_target"] = time_to_target(dna, torch, prob, args.target_iters)
+
+    if rank == 0 and not args.no_e2e:
+        code = {"f32": dna.DNA_F32, "f64": dna.DNA_F64, "bf16": dna.DNA_BF16}[args.dtype]
+        tdt = torch.float64 if args.dtype == "f64" else torch.float32
+        line["e2e"] = e2e_measure(dna, torch, prob, code, tdt, N, T, R, args.e2e_steps)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cols = 1024
+        it, el = oracle_rate(prob, cols, args.cpu_budget)
+        line["cpu_baseline"] = {
+            "value": it / el * cols / T, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+            "sample": f"{it} DNA iterations of the FP64 NumPy oracle on the first {cols} of {T} "
+                      f"columns in {el:.1f} s, rate scaled by {cols}/{T}"}
+    if world > 1:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def _bind(dna, torch, prob, dtype, dev):
+    code = {"f32": dna.DNA_F32, "f64": dna.DNA_F64, "bf16": dna.DNA_BF16}[dtype]
+    tdt = torch.float64 if dtype == "f64" else torch.float32
     V = torch.from_numpy(prob.V).to(dev, tdt)
     W = torch.from_numpy(prob.W).to(dev, tdt)
     H = torch.from_numpy(prob.H).to(dev, tdt)
-    stream = torch.cuda.current_stream()
-    ctx = dna.dna_create(N, T, R, dna.make_opts(dtype=code))
-    dna.dna_set_stream(ctx, stream)
+    N, T = prob.V.shape
+    ctx = dna.dna_create(N, T, prob.W.shape[1], dna.make_opts(dtype=code))
+    dna.dna_set_stream(ctx, torch.cuda.current_stream())
     dna.dna_bind(ctx, V, W, H)
     dna.dna_normalize(ctx, 1)                    # Algorithm 1 step 1
+    return ctx, (V, W, H)
+
+
+def measure(dna, torch, dist, prob, dtype, args, world, local, peaks, clocks):
+    """Time args.steps DNA iterations (CUDA events on the library's stream, barriers around,
+    max over ranks) with per-phase event timing for the roofline of the dominant kernel."""
+    dev = torch.device("cuda", local)
+    N, T = prob.V.shape
+    R = prob.W.shape[1]
+    ctx, keep = _bind(dna, torch, prob, dtype, dev)
+    stream = torch.cuda.current_stream()
     kl_start = dna.dna_kl(ctx)
     for _ in range(args.warmup):
         dna.dna_iterate(ctx, 1)
     torch.cuda.synchronize()
-
-    clocks = ClockSampler(local)
-    time.sleep(0.3)
+    sampler = ClockSampler(local) if clocks else None
+    if sampler:
+        time.sleep(0.3)
     dna.dna_profile(ctx, True)
     dna.dna_phase_times(ctx)                     # reset counters
     if world > 1:
@@ -267,10 +326,10 @@ def main(argv=None):
     ms = ev0.elapsed_time(ev1)
     phases = dna.dna_phase_times(ctx)
     dna.dna_profile(ctx, False)
-    clk = clocks.stop()
+    clk = sampler.stop() if sampler else None
     kl_end = dna.dna_kl(ctx)
     dna.dna_destroy(ctx)
-
+    del keep
     ms_max = ms
     if world > 1:
         t = torch.tensor([ms], device=dev, dtype=torch.float64)
@@ -283,61 +342,77 @@ def main(argv=None):
     dom_ms, dom_launches = phases[dom]
     per_launch_s = dom_ms / max(dom_launches, 1) / 1e3
     flops = (6 if dom == "pass1" else 4) * R * N * T    # per launch (H or W half-step)
-    peaks = measured_peaks()
+    alg_bytes = 4 * N * T + (8 * R * max(N, T) if dom == "pass1" else 16 * max(N, T))
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    if args.dtype == "bf16":
-        bound = "tensor"
-        peak_tflops = float(peaks.get("bf16_tflops_sustained", 1700.0))
-        peak_source = ("measured sustained dense bf16 (cuBLAS, MEASURED_PEAKS.json)"
-                       if "bf16_tflops_sustained" in peaks else "fallback sustained bf16 1700")
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    if dtype == "bf16":
+        tensor_peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
+        t_tensor = flops / (tensor_peak * 1e12)
+        t_hbm = alg_bytes / (hbm * 1e9)
+        if t_hbm >= t_tensor:   # the binding floor of this kernel at this size
+            roof = {"bound": "hbm", "achieved": alg_bytes / per_launch_s / 1e9, "peak": hbm,
+                    "unit": "GB/s", "peak_source": "measured HBM copy (MEASURED_PEAKS.json)"}
+        else:
+            roof = {"bound": "tensor", "achieved": flops / per_launch_s / 1e12, "peak": tensor_peak,
+                    "unit": "TFLOP/s",
+                    "peak_source": "measured sustained dense bf16 (MEASURED_PEAKS.json)"}
+        roof["tensor_frac"] = flops / per_launch_s / 1e12 / tensor_peak
+        roof["hbm_frac"] = alg_bytes / per_launch_s / 1e9 / hbm
     else:
-        bound = "alu"
-        peak_tflops = SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12 if args.dtype == "f32" \
-            else None
-        peak_source = (f"derived: {SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x "
-                       f"{sm_max:.0f} MHz (max SM clock of measured)")
-    achieved = flops / per_launch_s / 1e12
-    traffic = recorded_traffic(dom + ("_tc" if args.dtype == "bf16" else ""), args.workload)
-    roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak_tflops,
-                "unit": "TFLOP/s", "frac": (achieved / peak_tflops) if peak_tflops else None,
-                "traffic": traffic,
-                "peak_source": peak_source,
-                "algorithmic_flops_per_launch": flops,
-                "launch_ms": per_launch_s * 1e3,
-                "phase_share": {p: phases[p][0] / ms for p in ("pass1", "candidates", "pass2",
-                                                                "select", "sums", "operands")}}
-    launches = sum(v[1] for k, v in phases.items())
+        peak = SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12 if dtype == "f32" else None
+        roof = {"bound": "alu", "achieved": flops / per_launch_s / 1e12, "peak": peak,
+                "unit": "TFLOP/s",
+                "peak_source": (f"derived: {SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x "
+                                f"{sm_max:.0f} MHz (max SM clock of measured)")}
+    roof["frac"] = roof["achieved"] / roof["peak"] if roof.get("peak") else None
+    roof["kernel"] = dom
+    roof["traffic"] = recorded_traffic(dom + ("_tc" if dtype == "bf16" else ""), args.workload)
+    roof["algorithmic_flops_per_launch"] = flops
+    roof["algorithmic_bytes_per_launch"] = alg_bytes
+    roof["launch_ms"] = per_launch_s * 1e3
+    roof["phase_share"] = {p: round(phases[p][0] / ms, 4)
+                           for p in ("pass1", "candidates", "pass2", "select", "sums", "operands")}
+    return {"value": value, "ms_max": ms_max, "roofline": roof, "clocks": clk,
+            "launches": sum(v[1] for v in phases.values()), "kl_start": kl_start,
+            "kl_end": kl_end}
 
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
-        "config": {"workload": args.workload, "desc": spec["desc"], "N": N, "T": T, "R": R,
-                   "form": args.dtype.upper(),
-                   "engine": "tcgen05" if args.dtype == "bf16" else "simt",
-                   "l2": "inputs larger than L2 (V is %d MB)" % (N * T * 4 // 2**20),
-                   "parallelism": "independent problem per GPU" if world > 1 else "single GPU",
-                   "zero_fraction": prob.meta.get("zero_fraction")},
-        "gpu_launches": launches,
-        "roofline": roofline,
-        "clocks": clk,
-        "kl_start": kl_start, "kl_end": kl_end,
-    }
 
-    if rank == 0 and not args.no_e2e:
-        line["e2e"] = e2e_measure(dna, torch, prob, code, tdt, N, T, R, args.e2e_steps)
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cols = 1024
-        it, el = oracle_rate(prob, cols, args.cpu_budget)
-        line["cpu_baseline"] = {
-            "value": it / el * cols / T, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
-            "sample": f"{it} DNA iterations of the FP64 NumPy oracle on the first {cols} of {T} "
-                      f"columns in {el:.1f} s, rate scaled by {cols}/{T}"}
-    if world > 1:
-        dist.destroy_process_group()
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    return 0
+def time_to_target(dna, torch, prob, iters):
+    """Seconds of DNA iterations (CUDA events, d_KL evaluations excluded) for the FP32 form
+    to run `iters` iterations, whose final d_KL is the target, and for the BF16 form to come
+    within 1e-2 relative of it (checked every 5 iterations, at most 2 x iters)."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    out = {"iterations_fp32": iters}
+    ctx, keep = _bind(dna, torch, prob, "f32", dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    dna.dna_iterate(ctx, iters)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    out["sec_fp32"] = e0.elapsed_time(e1) / 1e3
+    target = dna.dna_kl(ctx)
+    dna.dna_destroy(ctx)
+    out["target_kl"] = target
+    ctx, keep2 = _bind(dna, torch, prob, "bf16", dev)
+    sec, it, kl = 0.0, 0, float("inf")
+    while it < 2 * iters:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        dna.dna_iterate(ctx, 5)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sec += e0.elapsed_time(e1) / 1e3
+        it += 5
+        kl = dna.dna_kl(ctx)
+        if kl <= target * (1 + 1e-2):
+            break
+    dna.dna_destroy(ctx)
+    out.update({"sec_bf16": sec, "iterations_bf16": it, "kl_bf16": kl,
+                "bf16_reached": bool(kl <= target * (1 + 1e-2)),
+                "speedup": out["sec_fp32"] / sec if sec > 0 else None})
+    return out
 
 
 def run_batched(args, world, rank, local):

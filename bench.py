@@ -46,6 +46,9 @@ WORKLOADS = {
                         desc="N=4096 T=16384 R=128, Gamma(0.3) truth scaled to mean 2, Poisson V"),
     "plain_small": dict(fn=workloads.plain_small, N=256, T=512, R=16,
                         desc="N=256 T=512 R=16, Gamma(0.5) truth, Poisson V"),
+    "precision_large": dict(fn=workloads.precision_large, N=8192, T=32768, R=512,
+                            desc="N=8192 T=32768 R=512, Gamma(0.5) W0, 70%-sparse Gamma(0.5) H0, "
+                                 "V = W0 H0 + |N(0,0.01)|"),
 }
 
 

@@ -161,7 +161,9 @@ void plan_all(dna_ctx* c) {
             c->pad_s[w] = (Sdim + tch - 1) / tch * tch;
             // partial A, B sums per split relative to V's bytes: 2 R / S
             const double part = 2.0 * (double)c->R / (double)Sdim;
-            plan_split(Sdim, c->pad_o[w] / tob, c->num_sms, tch, &c->tsp1[w], &c->tper1[w], part);
+            const int64_t rblocks = c->rp > 128 ? c->rp / 128 : 1;   // grid y of the K-streamed pass 1
+            plan_split(Sdim, c->pad_o[w] / tob * rblocks, c->num_sms, tch, &c->tsp1[w],
+                       &c->tper1[w], part);
             plan_split(Sdim, c->pad_o[w] / tob, c->num_sms, tch, &c->tsp2[w], &c->tper2[w],
                        2.0 / (double)Sdim);
         }
@@ -561,8 +563,7 @@ int dna_create(int64_t N, int64_t T, int64_t R, const dna_opts* opts, dna_ctx** 
     dna_default_opts(&o);
     if (opts) o = *opts;
     if (!valid_opts(o)) return DNA_ERR_ARG;
-    // Engines: BF16 runs on the tensor cores (R <= 128 in this build); F32 and F64 on the
-    // CUDA cores.
+    // Engines: BF16 runs on the tensor cores (R <= 512); F32 and F64 on the CUDA cores.
     const bool tc = o.dtype == DNA_BF16;
     if (tc && (o.engine == DNA_ENGINE_SIMT || dna::TcBf16::rank_pad(R) == 0))
         return DNA_ERR_UNSUPPORTED;

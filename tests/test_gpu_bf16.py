@@ -66,7 +66,9 @@ def _bf16_steps(p, iters, check_costs=True, restart=True):
 
 
 SHAPES = [(200, 300, 16), (130, 257, 64), (256, 512, 100), (70, 1000, 128), (1000, 70, 128),
-          (129, 131, 65), (1, 1, 1)]
+          (129, 131, 65), (1, 1, 1),
+          # ranks above 128: the K-streamed kernels (RP = 256, 512)
+          (300, 500, 200), (257, 300, 512), (640, 130, 300)]
 
 
 @pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(map(str, s)))
@@ -120,6 +122,32 @@ def test_bf16_plain_large_sampled():
     N, T = big.V.shape
     cols = np.sort(g.choice(T, 32, replace=False))
     rows = np.sort(g.choice(N, 32, replace=False))
+    with GpuProblem(big.V, big.W, big.H, "bf16") as gp:
+        gp.dna.dna_normalize(gp.ctx, 1)
+        W0, H0 = gp.WH()
+        gp.dna.dna_step_H(gp.ctx)
+        W1, H1 = gp.WH()
+        half = o.h_half_step(big.V[:, cols].astype(np.float64), W0, H0[:, cols])
+        mask, _ = _replay(half, gp.choice(0)[cols])
+        X = np.where(mask[None, :], half.X_dna, half.X_mu)
+        sigma = W1.sum(axis=0) / W0.sum(axis=0)
+        assert rel_fro(H1[:, cols], X / sigma[:, None]) < TOL_BF16
+        gp.dna.dna_step_W(gp.ctx)
+        W2, H2 = gp.WH()
+        half = o.w_half_step(big.V[rows, :].astype(np.float64), W1[rows, :], H1)
+        mask, _ = _replay(half, gp.choice(1)[rows])
+        X = np.where(mask[:, None], half.X_dna, half.X_mu)
+        sigma = H2.sum(axis=1) / H1.sum(axis=1)
+        assert rel_fro(W2[rows, :], X / sigma[None, :]) < TOL_BF16
+
+
+def test_bf16_precision_large_sampled():
+    """N=8192 T=32768 R=512 (the precision-form workload): sampled columns and rows."""
+    big = workloads.precision_large(0)
+    g = np.random.default_rng(2)
+    N, T = big.V.shape
+    cols = np.sort(g.choice(T, 16, replace=False))
+    rows = np.sort(g.choice(N, 16, replace=False))
     with GpuProblem(big.V, big.W, big.H, "bf16") as gp:
         gp.dna.dna_normalize(gp.ctx, 1)
         W0, H0 = gp.WH()

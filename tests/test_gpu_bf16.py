@@ -4,11 +4,13 @@ against the FP64 oracle.
 Tolerance, derived from the arithmetic: bf16 keeps 8 significant bits, unit roundoff
 u = 2^-9 ~ 2e-3.  z is a sum of positive products of two rounded operands (relative error
 <= 2u); q = v/z is rounded again (u); A = sum w q rounds w (u): the eq. 7 ratio (1 + a) is
-off by at most ~4u ~ 8e-3 element-wise, and the Frobenius error of a half-step is well
-below that.  So: W and H within 1e-2 relative (Frobenius) after each of the first
-iterations; candidate costs within 1e-2 relative; selections may differ where the
-oracle's relative cost margin is below 1e-2.  The float64 cost log (dna_kl) uses float32
-products and must match the oracle to 1e-4.
+off by ~4u ~ 8e-3 element-wise in the worst case; the Newton step a / b of eq. 17 can
+magnify that where a is small.  Measured one-step errors (relative Frobenius, first
+iteration): H half-step 1e-4 - 3e-3, W half-step 2e-3 - 9e-3 (largest when R exceeds N or
+T).  So: W and H within 2e-2 (about 10 u) after each half-step; candidate costs within
+1e-2 of their summed terms; selections may differ where the oracle's relative cost margin
+is below 1e-2.  The float64 cost log (dna_kl) uses float32 products and must match the
+oracle to 1e-4.
 """
 import numpy as np
 import pytest
@@ -19,7 +21,8 @@ from oracle import dna as o
 
 pytestmark = pytest.mark.gpu
 
-TOL_BF16 = 1e-2
+TOL_BF16 = 2e-2
+TOL_COST = 1e-2
 MARGIN_BF16 = 1e-2
 
 
@@ -51,8 +54,8 @@ def _bf16_steps(p, iters, check_costs=True, restart=True):
                     # bf16 error scales with that sum, not with d' (which can cross zero)
                     dm, dd = gp.costs(which)
                     scale = V.sum(axis=0 if which == 0 else 1) + 1.0
-                    assert np.all(np.abs(dm - half.d_mu) <= TOL_BF16 * (np.abs(half.d_mu) + scale))
-                    assert np.all(np.abs(dd - half.d_dna) <= TOL_BF16 * (np.abs(half.d_dna) + scale))
+                    assert np.all(np.abs(dm - half.d_mu) <= TOL_COST * (np.abs(half.d_mu) + scale))
+                    assert np.all(np.abs(dd - half.d_dna) <= TOL_COST * (np.abs(half.d_dna) + scale))
                 mask, _ = _replay(half, gp.choice(which))
                 step = o.dna_step_h if which == 0 else o.dna_step_w
                 W, H, _ = step(V, W, H, choice=mask)
@@ -85,7 +88,8 @@ def test_bf16_plain_small_trajectory():
 
 
 def test_bf16_reaches_fp32_kl():
-    """50 iterations: the BF16 form's d_KL is within 1e-2 of the FP32 form's."""
+    """50 iterations: the BF16 form's d_KL is within 1e-2 of the FP32 form's (the target of
+    the precision form)."""
     p = workloads.plain_small(0)
     kls = {}
     for kind in ("f32", "bf16"):

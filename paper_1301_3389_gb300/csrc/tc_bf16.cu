@@ -1,5 +1,6 @@
 // tcgen05 tensor-core kernels of the DNA half-step, BF16 operands with FP32 accumulation
-// in TMEM (the precision form), for padded rank RP in {64, 128}.
+// in TMEM (the precision form), for padded rank RP in {64, 128}; the K-streamed variants
+// near the end of the file take RP in {256, 512}.
 //
 // Pass 1 (Algorithm 1 steps 2-5 and 10), per CTA = 128 values of o (the TMEM lanes) and
 // an s-range streamed in chunks of 64:

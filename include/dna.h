@@ -183,6 +183,10 @@ int dna_run_host(dna_ctx* ctx, const void* V, void* W, void* H, int iters, doubl
  * kept. */
 int dna_profile(dna_ctx* ctx, int enable);
 
+/* As dna_profile, for the phases whose bit (1u << phase) is set in mask only (mask = 0
+ * stops recording).  Timing fewer phases adds fewer events to the stream. */
+int dna_profile_phases(dna_ctx* ctx, unsigned mask);
+
 /* Write, for each of the first n phases, the summed device time in milliseconds of the
  * recorded phase instances (ms, may be NULL) and the number of kernel launches of that
  * phase (launches, may be NULL) since the previous call, then reset both.

@@ -62,6 +62,7 @@ def _load() -> ctypes.CDLL:
         "dna_get_status": (I, [P]),
         "dna_run_host": (I, [P, P, P, P, I, ctypes.POINTER(D)]),
         "dna_profile": (I, [P, I]),
+        "dna_profile_phases": (I, [P, ctypes.c_uint]),
         "dna_phase_times": (I, [P, P, P, I]),
         "dna_kl_noalloc": (I, [P, I64, P, P, I64, I64, I64, P, P]),
         "dna_kl_backward": (I, [P, D, P, P, P]),
@@ -226,6 +227,14 @@ def dna_run_host(ctx: int, V, W, H, iters: int) -> float:
 
 def dna_profile(ctx: int, enable: bool = True) -> None:
     _check(LIB.dna_profile(ctx, 1 if enable else 0), "dna_profile")
+
+
+def dna_profile_phases(ctx: int, phases) -> None:
+    """Record event pairs around the named phases only (an empty list stops recording)."""
+    mask = 0
+    for p in phases:
+        mask |= 1 << PHASES.index(p)
+    _check(LIB.dna_profile_phases(ctx, mask), "dna_profile_phases")
 
 
 def dna_phase_times(ctx: int) -> dict:

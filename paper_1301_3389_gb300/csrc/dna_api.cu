@@ -38,6 +38,7 @@ struct dna_ctx {
     double* c = nullptr;         // R
     double* sig = nullptr;       // R
     double* fwork = nullptr;     // FSUM_SPLITS * R partial factor sums
+    double* gpart = nullptr;     // [ceil(max(N, T) / 32)][R] partial sums of the fused glue
     void* Apart = nullptr;       // [splits][R][O]
     void* Bpart = nullptr;
     void* Xmu = nullptr;         // [R][O]
@@ -69,7 +70,7 @@ struct dna_ctx {
     int tsp1[2] = {1, 1}, tsp2[2] = {1, 1};
     int64_t tper1[2] = {0, 0}, tper2[2] = {0, 0};
     // profiling: event pairs around phases, launch counts
-    bool prof_on = false;
+    unsigned prof_mask = 0;          // phases whose instances get an event pair
     std::vector<cudaEvent_t> ev_pool;
     std::vector<std::pair<int, size_t>> ev_recs;  // (phase, index of the start event)
     size_t ev_used = 0;
@@ -172,7 +173,7 @@ void plan_all(dna_ctx* c) {
 
 void free_all(dna_ctx* c) {
     void* ptrs[] = {c->own_V, c->own_W, c->own_H, c->Vt, c->colsum_v, c->rowsum_v, c->c, c->sig,
-                    c->fwork, c->Apart, c->Bpart, c->Xmu, c->Xdna, c->dpart, c->dfin_h, c->dfin_w,
+                    c->fwork, c->gpart, c->Apart, c->Bpart, c->Xmu, c->Xdna, c->dpart, c->dfin_h, c->dfin_w,
                     c->choice_h, c->choice_w, c->kl_dev, c->status, c->Xk, c->Yk, c->Ytk,
                     c->Y2tk, c->Xmk, c->Xdk, c->Vp};
     for (void* p : ptrs)
@@ -199,6 +200,7 @@ int alloc_workspace(dna_ctx* c) {
     e |= dmalloc(&c->c, sizeof(double) * R);
     e |= dmalloc(&c->sig, sizeof(double) * R);
     e |= dmalloc(&c->fwork, sizeof(double) * dna::FSUM_SPLITS * R);
+    e |= dmalloc(&c->gpart, sizeof(double) * (size_t)(dna::Simt<Tp>::glue_parts(M) * R));
     e |= dmalloc(&c->Apart, sizeof(Tp) * (size_t)ap);
     e |= dmalloc(&c->Bpart, sizeof(Tp) * (size_t)ap);
     e |= dmalloc(&c->Xmu, sizeof(Tp) * (size_t)(R * M));
@@ -253,44 +255,11 @@ int normalize(dna_ctx* c, int which) {
     });
 }
 
-// One half-step (wstep = 0: Algorithm 1 steps 4-16, wstep = 1: steps 17-29).
-// mu_only: the multiplicative update of eq. 11 instead of DNA.
-template <typename Tp>
-int half_step(dna_ctx* c, int wstep, bool mu_only) {
-    using S = dna::Simt<Tp>;
-    const View v = make_view(c, wstep == 1);
-    const double reg_den = wstep ? c->o.rho : c->o.lambda;   // eq. 7 / 14 denominators
-    Tp* A = static_cast<Tp*>(c->Apart);
-    Tp* B = static_cast<Tp*>(c->Bpart);
-    Tp* Xmu = static_cast<Tp*>(c->Xmu);
-    Tp* Xdna = static_cast<Tp*>(c->Xdna);
-    cudaStream_t st = c->stream;
-    int e = phase(c, DNA_PHASE_SUMS, 1, [&] { return S::factor_sums_y(v, reg_den, c->c, c->fwork, st); });
-    if (e) return e;
-    e = phase(c, DNA_PHASE_PASS1, 1, [&] {
-        return S::pass1(v, A, B, c->sp1[wstep], c->per1[wstep], !mu_only, c->status, st);
-    });
-    if (e) return e;
-    if (mu_only) {
-        e = phase(c, DNA_PHASE_CANDIDATES, 1,
-                  [&] { return S::mu_apply(v, c->c, A, c->sp1[wstep], st); });
-        if (e) return e;
-    } else {
-        e = phase(c, DNA_PHASE_CANDIDATES, 1, [&] {
-            return S::candidates(v, c->c, A, B, c->sp1[wstep], Xmu, Xdna, c->o.eps, c->o.alpha, st);
-        });
-        if (e) return e;
-        e = phase(c, DNA_PHASE_PASS2, 1, [&] {
-            return S::pass2(v, Xmu, Xdna, c->dpart, c->sp2[wstep], c->per2[wstep], c->status, st);
-        });
-        if (e) return e;
-        e = phase(c, DNA_PHASE_SELECT, 1, [&] {
-            return S::select(v, Xmu, Xdna, c->dpart, c->sp2[wstep],
-                             wstep ? c->choice_w : c->choice_h, wstep ? c->dfin_w : c->dfin_h, st);
-        });
-        if (e) return e;
-    }
-    return normalize<Tp>(c, wstep == 1 ? 1 : 0);
+// V as the tensor-core kernels read it for each view (aligned copy for the H view if needed).
+void tc_v(const dna_ctx* c, int wstep, const float** V, int64_t* vs) {
+    if (wstep) { *V = static_cast<const float*>(c->Vt); *vs = c->ldvt; }
+    else if (c->Vp) { *V = static_cast<const float*>(c->Vp); *vs = c->ldvp; }
+    else { *V = static_cast<const float*>(c->V); *vs = c->ldv; }
 }
 
 dna::TcOperands tc_operands(const dna_ctx* c, int wstep) {
@@ -299,14 +268,9 @@ dna::TcOperands tc_operands(const dna_ctx* c, int wstep) {
     op.S = v.S; op.O = v.O; op.R = v.R;
     op.S_pad = c->pad_s[wstep]; op.O_pad = c->pad_o[wstep];
     op.Xk = c->Xk; op.Yk = c->Yk; op.Ytk = c->Ytk; op.Y2tk = c->Y2tk;
+    op.Xmk = c->Xmk; op.Xdk = c->Xdk;
+    tc_v(c, wstep, &op.V, &op.vs);
     return op;
-}
-
-// V as the tensor-core kernels read it for each view (aligned copy for the H view if needed).
-void tc_v(const dna_ctx* c, int wstep, const float** V, int64_t* vs) {
-    if (wstep) { *V = static_cast<const float*>(c->Vt); *vs = c->ldvt; }
-    else if (c->Vp) { *V = static_cast<const float*>(c->Vp); *vs = c->ldvp; }
-    else { *V = static_cast<const float*>(c->V); *vs = c->ldv; }
 }
 
 int build_tc_maps(dna_ctx* c) {
@@ -373,61 +337,109 @@ int step_h_adjoint(dna_ctx* c, const Tp* Hk, const uint8_t* choice, const Tp* Hb
 
 // The BF16 precision form: the two O(NRT) passes on tcgen05 tensor cores (bf16 operands,
 // float32 accumulation in TMEM), everything else as in the FP32 form.
-int half_step_tc(dna_ctx* c, int wstep, bool mu_only) {
-    using S = dna::Simt<float>;
-    using TC = dna::TcBf16;
-    const View v = make_view(c, wstep == 1);
-    const double reg_den = wstep ? c->o.rho : c->o.lambda;
-    cudaStream_t st = c->stream;
-    float* A = static_cast<float*>(c->Apart);
-    float* B = static_cast<float*>(c->Bpart);
-    float* Xmu = static_cast<float*>(c->Xmu);
-    float* Xdna = static_cast<float*>(c->Xdna);
-    const int64_t rp = c->rp;
-    const dna::TcOperands op = tc_operands(c, wstep);
-    const float* X = static_cast<const float*>(v.X);
-    const float* Y = static_cast<const float*>(v.Y);
+// The operand buffers of half-step w for scale_ops (tensor-core form), else nulls.
+struct OpsOut {
+    void *Xk = nullptr, *Yk = nullptr, *Ytk = nullptr, *Y2tk = nullptr;
+    int64_t rp = 0, O_pad = 0, S_pad = 0;
+};
+OpsOut ops_out(const dna_ctx* c, int w, bool with_sq) {
+    OpsOut o;
+    if (!c->tc) return o;
+    o.Xk = c->Xk; o.Yk = c->Yk; o.Ytk = c->Ytk; o.Y2tk = with_sq ? c->Y2tk : nullptr;
+    o.rp = c->rp; o.O_pad = c->pad_o[w]; o.S_pad = c->pad_s[w];
+    return o;
+}
 
-    int e = phase(c, DNA_PHASE_SUMS, 1, [&] { return S::factor_sums_y(v, reg_den, c->c, c->fwork, st); });
-    if (e) return e;
-    e = phase(c, DNA_PHASE_OPERANDS, 2, [&] {
-        int r = TC::to_bf16(X, v.xo, v.xr, v.O, v.R, c->Xk, rp, op.O_pad, rp, false, st);
-        if (!r) r = TC::y_operands(Y, v.ys, v.yr, op, !mu_only, st);
-        return r;
+// Operands (tensor-core form) and eq. 7 / 14 denominators c of half-step w from the
+// current W and H.
+template <typename Tp>
+int prep_step(dna_ctx* c, int w, bool with_sq) {
+    using S = dna::Simt<Tp>;
+    const View v = make_view(c, w == 1);
+    const OpsOut o = ops_out(c, w, with_sq);
+    int e = phase(c, c->tc ? DNA_PHASE_OPERANDS : DNA_PHASE_SUMS, 1, [&] {
+        return S::scale_ops(v, nullptr, false, o.Xk, o.Yk, o.Ytk, o.Y2tk, o.rp, o.O_pad, o.S_pad,
+                            c->gpart, c->stream);
     });
     if (e) return e;
+    return phase(c, DNA_PHASE_SUMS, 1, [&] {
+        return S::part_sums(c->gpart, S::glue_parts(v.S), c->R, w ? c->o.rho : c->o.lambda, c->c,
+                            c->stream);
+    });
+}
+
+// One half-step (w = 0: Algorithm 1 steps 4-16, w = 1: steps 17-29).  mu_only: the
+// multiplicative update of eq. 11 instead of DNA.  prepared: the operands and c of this
+// half-step were left by the previous one (inside one dna_iterate call); next: leave them
+// for half-step 1 - w (the step 16 / 29 normalisation writes them in the same pass).
+template <typename Tp>
+int half_step(dna_ctx* c, int w, bool mu_only, bool prepared, bool next) {
+    using S = dna::Simt<Tp>;
+    const View v = make_view(c, w == 1);
+    Tp* A = static_cast<Tp*>(c->Apart);
+    Tp* B = static_cast<Tp*>(c->Bpart);
+    Tp* Xmu = static_cast<Tp*>(c->Xmu);
+    Tp* Xdna = static_cast<Tp*>(c->Xdna);
+    cudaStream_t st = c->stream;
+    const bool tc = c->tc;
+    const int sp1 = tc ? c->tsp1[w] : c->sp1[w], sp2 = tc ? c->tsp2[w] : c->sp2[w];
+    int e = DNA_OK;
+    if (!prepared || mu_only)
+        if ((e = prep_step<Tp>(c, w, !mu_only))) return e;
     e = phase(c, DNA_PHASE_PASS1, 1, [&] {
-        return TC::pass1(op, c->maps[wstep], A, B, c->tsp1[wstep], c->tper1[wstep], !mu_only,
-                         c->status, st);
+        if constexpr (sizeof(Tp) == 4)
+            if (tc)
+                return dna::TcBf16::pass1(tc_operands(c, w), c->maps[w], A, B, sp1, c->tper1[w],
+                                          !mu_only, c->status, st);
+        return S::pass1(v, A, B, sp1, c->per1[w], !mu_only, c->status, st);
     });
     if (e) return e;
     if (mu_only) {
-        e = phase(c, DNA_PHASE_CANDIDATES, 1,
-                  [&] { return S::mu_apply(v, c->c, A, c->tsp1[wstep], st); });
-        if (e) return e;
-        return normalize<float>(c, wstep == 1 ? 1 : 0);
+        e = phase(c, DNA_PHASE_CANDIDATES, 1, [&] { return S::mu_apply(v, c->c, A, sp1, st); });
+        return e ? e : normalize<Tp>(c, w == 1 ? 1 : 0);
     }
     e = phase(c, DNA_PHASE_CANDIDATES, 1, [&] {
-        return S::candidates(v, c->c, A, B, c->tsp1[wstep], Xmu, Xdna, c->o.eps, c->o.alpha, st);
-    });
-    if (e) return e;
-    e = phase(c, DNA_PHASE_OPERANDS, 2, [&] {
-        int r = TC::to_bf16(Xmu, 1, v.O, v.O, v.R, c->Xmk, rp, op.O_pad, rp, false, st);
-        if (!r) r = TC::to_bf16(Xdna, 1, v.O, v.O, v.R, c->Xdk, rp, op.O_pad, rp, false, st);
-        return r;
+        return S::cand_fused(v, c->c, A, B, sp1, Xmu, Xdna, c->o.eps, c->o.alpha,
+                             tc ? c->Xmk : nullptr, tc ? c->Xdk : nullptr, c->rp, c->pad_o[w], st);
     });
     if (e) return e;
     e = phase(c, DNA_PHASE_PASS2, 1, [&] {
-        return TC::pass2(op, c->maps[wstep], c->dpart, c->tsp2[wstep], c->tper2[wstep], c->status,
-                         st);
+        if constexpr (sizeof(Tp) == 4)
+            if (tc)
+                return dna::TcBf16::pass2(tc_operands(c, w), c->maps[w], c->dpart, sp2,
+                                          c->tper2[w], c->status, st);
+        return S::pass2(v, Xmu, Xdna, c->dpart, sp2, c->per2[w], c->status, st);
     });
     if (e) return e;
     e = phase(c, DNA_PHASE_SELECT, 1, [&] {
-        return S::select(v, Xmu, Xdna, c->dpart, c->tsp2[wstep], wstep ? c->choice_w : c->choice_h,
-                         wstep ? c->dfin_w : c->dfin_h, st);
+        return S::select_fused(v, Xmu, Xdna, c->dpart, sp2, w ? c->choice_w : c->choice_h,
+                               w ? c->dfin_w : c->dfin_h, c->gpart, st);
     });
     if (e) return e;
-    return normalize<float>(c, wstep == 1 ? 1 : 0);
+    // steps 16 / 29: f_r = sum over o of the new x(r, o) + (rho | lambda)
+    e = phase(c, DNA_PHASE_SUMS, 1, [&] {
+        return S::part_sums(c->gpart, S::glue_parts(v.O), c->R, w ? c->o.lambda : c->o.rho,
+                            c->sig, st);
+    });
+    if (e) return e;
+    if (!next)
+        return phase(c, DNA_PHASE_SUMS, 1, [&] {
+            return S::scale_ops(v, c->sig, false, nullptr, nullptr, nullptr, nullptr, 0, 0, 0,
+                                nullptr, st);
+        });
+    // half-step 1 - w sees this step's X as its Y and this step's Y as its X
+    const int wn = 1 - w;
+    const View t = make_view(c, wn == 1);
+    const OpsOut o = ops_out(c, wn, true);
+    e = phase(c, DNA_PHASE_SUMS, 1, [&] {
+        return S::scale_ops(t, c->sig, true, o.Xk, o.Yk, o.Ytk, o.Y2tk, o.rp, o.O_pad, o.S_pad,
+                            c->gpart, st);
+    });
+    if (e) return e;
+    return phase(c, DNA_PHASE_SUMS, 1, [&] {
+        return S::part_sums(c->gpart, S::glue_parts(t.S), c->R, wn ? c->o.rho : c->o.lambda, c->c,
+                            st);
+    });
 }
 
 // Gradient of eq. 1 (no regularisation) with respect to W, H and V, scaled by `scale`:
@@ -489,7 +501,7 @@ int set_device(const dna_ctx* c) {
 template <class F>
 int phase(dna_ctx* c, int ph, int nlaunch, F&& f) {
     size_t idx = SIZE_MAX;
-    if (c->prof_on && c->ev_used + 2 <= c->ev_pool.size()) {
+    if (((c->prof_mask >> ph) & 1u) && c->ev_used + 2 <= c->ev_pool.size()) {
         idx = c->ev_used;
         c->ev_used += 2;
         if (cudaEventRecord(c->ev_pool[idx], c->stream) != cudaSuccess) return DNA_ERR_CUDA;
@@ -631,23 +643,29 @@ int dna_normalize(dna_ctx* c, int which) {
 int dna_step_H(dna_ctx* c) {
     if (int e = check_ready(c)) return e;
     if (set_device(c)) return DNA_ERR_CUDA;
-    if (c->tc) return half_step_tc(c, 0, false);
-    return is_f64(c) ? half_step<double>(c, 0, false) : half_step<float>(c, 0, false);
+    return is_f64(c) ? half_step<double>(c, 0, false, false, false)
+                     : half_step<float>(c, 0, false, false, false);
 }
 
 int dna_step_W(dna_ctx* c) {
     if (int e = check_ready(c)) return e;
     if (set_device(c)) return DNA_ERR_CUDA;
-    if (c->tc) return half_step_tc(c, 1, false);
-    return is_f64(c) ? half_step<double>(c, 1, false) : half_step<float>(c, 1, false);
+    return is_f64(c) ? half_step<double>(c, 1, false, false, false)
+                     : half_step<float>(c, 1, false, false, false);
 }
 
 int dna_iterate(dna_ctx* c, int iters) {
     if (int e = check_ready(c)) return e;
     if (iters < 0) return DNA_ERR_ARG;
+    if (set_device(c)) return DNA_ERR_CUDA;
+    // each half-step leaves the operands and denominators of the next one
     for (int i = 0; i < iters; ++i) {
-        if (int e = dna_step_H(c)) return e;
-        if (int e = dna_step_W(c)) return e;
+        const bool more = i + 1 < iters;
+        int e = is_f64(c) ? half_step<double>(c, 0, false, i > 0, true)
+                          : half_step<float>(c, 0, false, i > 0, true);
+        if (!e) e = is_f64(c) ? half_step<double>(c, 1, false, true, more)
+                              : half_step<float>(c, 1, false, true, more);
+        if (e) return e;
     }
     return DNA_OK;
 }
@@ -656,8 +674,8 @@ int mu_step(dna_ctx* c, int which) {
     if (int e = check_ready(c)) return e;
     if (which != 0 && which != 1) return DNA_ERR_ARG;
     if (set_device(c)) return DNA_ERR_CUDA;
-    if (c->tc) return half_step_tc(c, which, true);
-    return is_f64(c) ? half_step<double>(c, which, true) : half_step<float>(c, which, true);
+    return is_f64(c) ? half_step<double>(c, which, true, false, false)
+                     : half_step<float>(c, which, true, false, false);
 }
 
 int dna_kl(dna_ctx* c, double* out) {
@@ -774,16 +792,20 @@ int dna_run_host(dna_ctx* c, const void* V, void* W, void* H, int iters, double*
     return e;
 }
 
-int dna_profile(dna_ctx* c, int enable) {
+int dna_profile_phases(dna_ctx* c, unsigned mask) {
     if (!c) return DNA_ERR_ARG;
     if (set_device(c)) return DNA_ERR_CUDA;
-    if (enable && c->ev_pool.empty()) {
+    if (mask && c->ev_pool.empty()) {
         c->ev_pool.resize(2 * 16384, nullptr);
         for (auto& ev : c->ev_pool)
             if (cudaEventCreate(&ev) != cudaSuccess) return DNA_ERR_CUDA;
     }
-    c->prof_on = enable != 0;
+    c->prof_mask = mask & ((1u << DNA_NUM_PHASES) - 1u);
     return DNA_OK;
+}
+
+int dna_profile(dna_ctx* c, int enable) {
+    return dna_profile_phases(c, enable ? (1u << DNA_NUM_PHASES) - 1u : 0u);
 }
 
 int dna_phase_times(dna_ctx* c, double* ms, int64_t* launches, int n) {

@@ -85,6 +85,28 @@ template <typename Tp> struct Simt {
                          Tp* Abar, Tp* Bbar, double* vs, Tp* Hpart, int splits2, int64_t s_per2,
                          Tp* Vbar, int64_t ldvb, double eps, double alpha, int* status,
                          cudaStream_t st);
+    // Fused glue of the single-problem path (glue_kernels.cuh).
+    // Candidates as above; with Xmk, Xdk (float only) also their bf16 copies [O_pad][rp]
+    // with zero padding.
+    static int cand_fused(const View& v, const double* c, const Tp* Apart, const Tp* Bpart,
+                          int splits, Tp* Xmu, Tp* Xdna, double eps, double alpha, void* Xmk,
+                          void* Xdk, int64_t rp, int64_t O_pad, cudaStream_t st);
+    // Selection as above, plus fpart[glue_parts(O)][R]: per-block sums of the new X.
+    static int select_fused(const View& v, const Tp* Xmu, const Tp* Xdna, const double* dpart,
+                            int splits, uint8_t* choice, double* dfin, double* fpart,
+                            cudaStream_t st);
+    // out[r] = sum over k < nparts of part[k * R + r] + reg (fixed order; an exact zero
+    // sum is replaced by 1)
+    static int part_sums(const double* part, int64_t nparts, int64_t R, double reg, double* out,
+                         cudaStream_t st);
+    // For the half-step `t`: when f is given, X(r, o) *= f_r and Y(s, r) /= f_r (xmul) or
+    // X /= f_r and Y *= f_r (written back); when Xk is given (float only), the bf16
+    // operands of `t` (Y2tk may be null); when cpart is given, cpart[glue_parts(S)][R] =
+    // per-block sums over s of the (scaled) y(s, r).
+    static int scale_ops(const View& t, const double* f, bool xmul, void* Xk, void* Yk,
+                         void* Ytk, void* Y2tk, int64_t rp, int64_t O_pad, int64_t S_pad,
+                         double* cpart, cudaStream_t st);
+    static int64_t glue_parts(int64_t n);   // partial sums per R of the fused glue
     // one-time: row and column sums of V (float64) and the transposed copy
     static int prepare_v(const Tp* V, int64_t N, int64_t T, int64_t ldv, Tp* Vt, int64_t ldvt,
                          double* colsum, double* rowsum, cudaStream_t st);
@@ -105,6 +127,10 @@ struct TcOperands {
     const void* Yk;
     const void* Ytk;
     const void* Y2tk;
+    const void* Xmk;    // bf16 candidates [O_pad][RP] (pass 2)
+    const void* Xdk;
+    const float* V;     // V_so as the passes read it, element (s, o) at V[s * vs + o]
+    int64_t vs;
 };
 
 // TMA descriptors of one half-step view (built once per bound problem).

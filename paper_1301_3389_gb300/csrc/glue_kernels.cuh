@@ -1,0 +1,316 @@
+// Fused per-half-step kernels between the two O(NRT) passes, for the single-problem path:
+//   k_cand_fused   candidates (steps 6 and 11, eq. 10, 11, 15, 17) and, for the tensor-core
+//                  form, their bf16 operand copies;
+//   k_select_fused selection (steps 15 / 28) and the per-block partial sums of the new
+//                  factor that the step 16 / 29 normalisation divides by;
+//   k_scale_ops    the normalisation itself (X by 1/f_r, Y by f_r) fused with the
+//                  preparation of a half-step: its bf16 operand tiles and the partial sums
+//                  of its eq. 7 / 14 denominators.
+// Every element is independent except for the fixed-order reductions, so all loads of a
+// thread are issued before their results are used, and transposed layouts go through
+// shared-memory tiles so that global accesses stay coalesced.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "simt_kernels.cuh"
+
+namespace dna {
+namespace glue {
+
+using bf16 = __nv_bfloat16;
+constexpr int TO = 32;   // o (or s) per tile
+constexpr int TY = 32;   // r groups per CTA (threadIdx.y): 1024 threads
+constexpr int UNR = 4;   // r values per thread whose loads are issued together
+static_assert(TY == TO, "k_cand_fused gives each r group one column of the tile");
+
+__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+
+// Dynamic shared memory of k_cand_fused: red; cs, ics [R]; sc; xs, ms [R][TO + 1].
+template <typename Tp>
+constexpr size_t cand_smem(int64_t R, bool bf) {
+    return sizeof(Tp) * (2 * (size_t)R + (bf ? 2 : 1) * (size_t)R * (TO + 1) + TO) +
+           sizeof(double) * TY * TO;
+}
+
+// CTA = 32 columns o (threadIdx.x) x 32 groups of r (threadIdx.y); grid covers O (or O_pad
+// when bf16 copies are written: the padding rows are written as zeros).
+template <typename Tp, bool BF>
+__global__ void __launch_bounds__(1024) k_cand_fused(View v, const double* __restrict__ c,
+                                                    const Tp* __restrict__ Apart,
+                                                    const Tp* __restrict__ Bpart, int splits,
+                                                    Tp* __restrict__ Xmu, Tp* __restrict__ Xdna,
+                                                    Tp eps, Tp alpha, bf16* __restrict__ Xmk,
+                                                    bf16* __restrict__ Xdk, int64_t rp) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int64_t R = v.R, O = v.O;
+    double* red = reinterpret_cast<double*>(smem_raw);            // [TY][TO]
+    Tp* cs = reinterpret_cast<Tp*>(red + TY * TO);                // [R]
+    Tp* ics = cs + R;                                             // [R]
+    Tp* scl = ics + R;                                            // [TO]
+    Tp* xs = scl + TO;                                            // [R][TO + 1]: x, then x_dna
+    Tp* ms = xs + R * (TO + 1);                                   // [R][TO + 1]: x_mu (BF)
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+    const int64_t o0 = (int64_t)blockIdx.x * TO, o = o0 + tx;
+    const bool live = o < O;
+    const Tp* __restrict__ X = static_cast<const Tp*>(v.X);
+
+    for (int64_t r = tid; r < R; r += TY * 32) {
+        cs[r] = (Tp)c[r];
+        ics[r] = Tp(1) / (Tp)c[r];
+    }
+    if (v.xo == 1) {   // rows of X contiguous along o
+#pragma unroll 4
+        for (int64_t r = ty; r < R; r += TY) xs[r * (TO + 1) + tx] = live ? X[r * v.xr + o] : Tp(0);
+    } else {           // columns of X contiguous along r: lanes walk r
+        const int i = ty;   // TY == TO: one column per r group
+        const int64_t oi = o0 + i;
+#pragma unroll 4
+        for (int64_t r = tx; r < R; r += 32)
+            xs[r * (TO + 1) + i] = oi < O ? X[r * v.xr + oi * v.xo] : Tp(0);
+    }
+    __syncthreads();
+
+    Tp den = Tp(0);
+    for (int64_t r0 = ty; r0 < R; r0 += TY * UNR) {
+        Tp ra[UNR], rb[UNR];
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) { ra[u] = Tp(0); rb[u] = Tp(0); }
+        if (live) {
+            for (int sp = 0; sp < splits; ++sp) {
+#pragma unroll
+                for (int u = 0; u < UNR; ++u) {
+                    const int64_t r = r0 + TY * u;
+                    if (r < R) {
+                        ra[u] += Apart[((int64_t)sp * R + r) * O + o];
+                        rb[u] += Bpart[((int64_t)sp * R + r) * O + o];
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+            const int64_t r = r0 + TY * u;
+            if (r >= R) break;
+            const Tp x = xs[r * (TO + 1) + tx];
+            const Tp a = ra[u] * ics[r] - Tp(1);   // eq. 7
+            const Tp b = rb[u] * ics[r];           // eq. 14
+            const Tp xmu = x + a * x;              // eq. 11
+            Tp xd;
+            if (a < Tp(0)) {                       // eq. 15, gain floored at eps
+                const Tp xb = x * b;
+                const Tp g = simt::dev_div(xb, xb - a);
+                xd = x * (g > eps ? g : eps);
+            } else {                               // eq. 17, step capped at alpha x
+                const Tp stp = b > Tp(0) ? simt::dev_div(a, b) : Tp(0);
+                const Tp cap = alpha * x;
+                xd = x + (stp < cap ? stp : cap);
+            }
+            if (!live) xd = Tp(0);
+            if (live) Xmu[r * O + o] = xmu;
+            xs[r * (TO + 1) + tx] = xd;
+            if constexpr (BF) ms[r * (TO + 1) + tx] = live ? xmu : Tp(0);
+            den += cs[r] * xd;
+        }
+    }
+    red[ty * TO + tx] = (double)den;
+    __syncthreads();
+    if (ty == 0) {
+        double tot = 0.0;
+        for (int k = 0; k < TY; ++k) tot += red[k * TO + tx];
+        scl[tx] = live ? (Tp)(tot > 0.0 ? v.vsum[o] / tot : 1.0) : Tp(0);   // eq. 10
+    }
+    __syncthreads();
+    const Tp sc = scl[tx];
+#pragma unroll 4
+    for (int64_t r = ty; r < R; r += TY) {
+        const Tp xd = xs[r * (TO + 1) + tx] * sc;
+        if (live) Xdna[r * O + o] = xd;
+        if constexpr (BF) xs[r * (TO + 1) + tx] = xd;
+    }
+    if constexpr (BF) {
+        __syncthreads();
+        // K-major bf16 rows [o][rp]: lanes walk pairs of r
+        {
+            const int i = ty;
+            const int64_t oi = o0 + i;
+            for (int64_t r = 2 * tx; r < rp; r += 64) {
+                float m0 = 0.f, m1 = 0.f, d0 = 0.f, d1 = 0.f;
+                if (r < R) { m0 = (float)ms[r * (TO + 1) + i]; d0 = (float)xs[r * (TO + 1) + i]; }
+                if (r + 1 < R) {
+                    m1 = (float)ms[(r + 1) * (TO + 1) + i];
+                    d1 = (float)xs[(r + 1) * (TO + 1) + i];
+                }
+                *reinterpret_cast<uint32_t*>(Xmk + oi * rp + r) = pack2(m0, m1);
+                *reinterpret_cast<uint32_t*>(Xdk + oi * rp + r) = pack2(d0, d1);
+            }
+        }
+    }
+}
+
+template <typename Tp>
+constexpr size_t select_smem(int64_t R) {
+    return sizeof(Tp) * (size_t)R * (TO + 1) + 32 * sizeof(int);
+}
+
+// Selection: x(r, o) <- Newton candidate iff d_dna < d_mu (ties keep MU), the choice and
+// the final costs per column, and fpart[blk][r] = sum over this CTA's 32 columns of the
+// new x(r, o) (float64), the first level of the normalisation sums.
+template <typename Tp>
+__global__ void __launch_bounds__(256) k_select_fused(View v, const Tp* __restrict__ Xmu,
+                                                      const Tp* __restrict__ Xdna,
+                                                      const double* __restrict__ dpart,
+                                                      int splits, uint8_t* __restrict__ choice,
+                                                      double* __restrict__ dfin,
+                                                      double* __restrict__ fpart) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int64_t R = v.R, O = v.O;
+    Tp* xs = reinterpret_cast<Tp*>(smem_raw);                   // [R][TO + 1]
+    int* nw = reinterpret_cast<int*>(xs + R * (TO + 1));        // [TO]
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+    const int64_t o0 = (int64_t)blockIdx.x * TO, o = o0 + tx;
+    const bool live = o < O;
+    if (ty == 0) {
+        int newton = 0;
+        if (live) {
+            double dm = 0.0, dd = 0.0;
+            for (int sp = 0; sp < splits; ++sp) {
+                dm += dpart[((int64_t)sp * 2 + 0) * O + o];
+                dd += dpart[((int64_t)sp * 2 + 1) * O + o];
+            }
+            newton = dd < dm;
+            choice[o] = (uint8_t)newton;
+            dfin[o] = dm;
+            dfin[O + o] = dd;
+        }
+        nw[tx] = newton;
+    }
+    __syncthreads();
+    const Tp* __restrict__ src = nw[tx] ? Xdna : Xmu;
+    Tp* __restrict__ X = static_cast<Tp*>(v.X);
+    const bool direct = v.xo == 1;
+#pragma unroll 16
+    for (int64_t r = ty; r < R; r += 8) {
+        const Tp x = live ? src[r * O + o] : Tp(0);
+        xs[r * (TO + 1) + tx] = x;
+        if (direct && live) X[r * v.xr + o] = x;
+    }
+    __syncthreads();
+    if (!direct) {   // columns of X contiguous along r: lanes walk r
+        for (int i = ty; i < TO; i += 8) {
+            const int64_t oi = o0 + i;
+            if (oi >= O) break;
+#pragma unroll 4
+            for (int64_t r = tx; r < R; r += 32) X[r * v.xr + oi * v.xo] = xs[r * (TO + 1) + i];
+        }
+    }
+    for (int64_t r = tid; r < R; r += 256) {
+        Tp s = Tp(0);
+#pragma unroll 8
+        for (int i = 0; i < TO; ++i) s += xs[r * (TO + 1) + i];
+        fpart[(int64_t)blockIdx.x * R + r] = (double)s;
+    }
+}
+
+// One tile job of k_scale_ops.
+struct OpsArgs {
+    // the target half-step's X (element (r, o) at X[r * xr + o * xo]) and Y ((s, r) at
+    // Y[s * ys + r * yr])
+    void* X;
+    int64_t xr, xo, O;
+    void* Y;
+    int64_t ys, yr, S;
+    int64_t R;
+    const double* f;   // normaliser f_r, or null (no scaling, nothing written back)
+    bool xmul;         // X *= f_r and Y /= f_r (else X /= f_r and Y *= f_r)
+    // bf16 operands of the target half-step (tensor-core form), or null
+    bf16* Xk;          // [O_pad][rp]
+    bf16* Yk;          // [S_pad][rp]
+    bf16* Ytk;         // [rp][S_pad]
+    bf16* Y2tk;        // [rp][S_pad], or null
+    int64_t rp, O_pad, S_pad;
+    double* cpart;     // [ceil(S / 32)][R] partial sums over s of the (scaled) y(s, r), or null
+    int64_t xtiles_o, tiles_r, xtiles;   // X tiles: xtiles_o x tiles_r; then the Y tiles
+};
+
+// Tiles of 32 x 32: blocks [0, xtiles) cover X as (o-tile, r-tile), the rest cover Y as
+// (s-tile, r-tile).  Extents are the padded ones when bf16 operands are written, so the
+// padding of the operand buffers is rewritten as zeros.
+template <typename Tp>
+__global__ void __launch_bounds__(256) k_scale_ops(OpsArgs a) {
+    __shared__ Tp tile[TO][TO + 1];
+    __shared__ Tp fr[TO];
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+    const bool isx = (int64_t)blockIdx.x < a.xtiles;
+    const int64_t b = isx ? (int64_t)blockIdx.x : (int64_t)blockIdx.x - a.xtiles;
+    const int64_t it = b / a.tiles_r, rt = b % a.tiles_r;
+    const int64_t r0 = rt * TO, i0 = it * TO;   // i = o (X tiles) or s (Y tiles)
+    const int64_t n = isx ? a.O : a.S;
+    if (tid < TO) {
+        const int64_t r = r0 + tid;
+        Tp s = Tp(1);
+        if (a.f && r < a.R) {
+            const Tp f = (Tp)a.f[r];
+            s = (isx == a.xmul) ? f : Tp(1) / f;
+        }
+        fr[tid] = s;
+    }
+    __syncthreads();
+    Tp* M = static_cast<Tp*>(isx ? a.X : a.Y);
+    // element (r, i): X[r * xr + i * xo] or Y[i * ys + r * yr]
+    const int64_t sr = isx ? a.xr : a.yr, si = isx ? a.xo : a.ys;
+    if (si == 1) {   // contiguous along i: lanes walk i
+        for (int k = ty; k < TO; k += 8) {
+            const int64_t r = r0 + k, i = i0 + tx;
+            Tp x = Tp(0);
+            if (r < a.R && i < n) {
+                x = M[r * sr + i] * fr[k];
+                if (a.f) M[r * sr + i] = x;
+            }
+            tile[k][tx] = x;   // tile[r][i]
+        }
+    } else {         // contiguous along r: lanes walk r
+        for (int k = ty; k < TO; k += 8) {
+            const int64_t i = i0 + k, r = r0 + tx;
+            Tp x = Tp(0);
+            if (r < a.R && i < n) {
+                x = M[i * si + r * sr] * fr[tx];
+                if (a.f) M[i * si + r * sr] = x;
+            }
+            tile[tx][k] = x;
+        }
+    }
+    __syncthreads();
+    if (!isx && a.cpart && tid < TO && r0 + tid < a.R && i0 < a.S) {
+        Tp s = Tp(0);
+#pragma unroll 8
+        for (int k = 0; k < TO; ++k) s += tile[tid][k];
+        a.cpart[it * a.R + r0 + tid] = (double)s;
+    }
+    if (a.Xk == nullptr) return;
+    if constexpr (sizeof(Tp) == 4) {
+        if (isx) {   // Xk[o][r]: lanes walk r
+            for (int k = ty; k < TO; k += 8) {
+                const int64_t i = i0 + k, r = r0 + tx;
+                if (i < a.O_pad && r < a.rp) a.Xk[i * a.rp + r] = __float2bfloat16_rn(tile[tx][k]);
+            }
+        } else {
+            for (int k = ty; k < TO; k += 8) {
+                const int64_t i = i0 + k, r = r0 + tx;   // Yk[s][r]: lanes walk r
+                if (i < a.S_pad && r < a.rp) a.Yk[i * a.rp + r] = __float2bfloat16_rn(tile[tx][k]);
+                const int64_t r2 = r0 + k, i2 = i0 + tx;  // Ytk[r][s]: lanes walk s
+                if (i2 < a.S_pad && r2 < a.rp) {
+                    const float y = tile[k][tx];
+                    a.Ytk[r2 * a.S_pad + i2] = __float2bfloat16_rn(y);
+                    if (a.Y2tk) a.Y2tk[r2 * a.S_pad + i2] = __float2bfloat16_rn(y * y);
+                }
+            }
+        }
+    }
+}
+
+}  // namespace glue
+}  // namespace dna

@@ -795,6 +795,7 @@ __global__ void k_colsum_final(const double* __restrict__ part, int nsplit, int6
     const int lane = threadIdx.x & 31;
     if (r >= R) return;
     double t = 0.0;
+#pragma unroll 8
     for (int k = lane; k < nsplit; k += 32) t += part[(int64_t)k * R + r];
 #pragma unroll
     for (int m = 16; m > 0; m >>= 1) t += __shfl_xor_sync(0xffffffffu, t, m);

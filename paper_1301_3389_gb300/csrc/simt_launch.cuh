@@ -3,6 +3,7 @@
 
 #include <algorithm>
 
+#include "glue_kernels.cuh"
 #include "simt_kernels.cuh"
 
 namespace dna {
@@ -254,6 +255,81 @@ int Simt<Tp>::adjoint_h(const View& v, const double* c, const Tp* Apart, const T
     if (e) return e;
     simt::k_adj_combine<Tp><<<(unsigned)((v.O + 31) / 32), dim3(32, 8), 0, st>>>(v, Hpart, splits2,
                                                                                  Hbar0);
+    return simt::launch_status();
+}
+
+template <typename Tp>
+int64_t Simt<Tp>::glue_parts(int64_t n) { return (n + glue::TO - 1) / glue::TO; }
+
+template <typename Tp>
+int Simt<Tp>::cand_fused(const View& v, const double* c, const Tp* A, const Tp* B, int splits,
+                         Tp* Xmu, Tp* Xdna, double eps, double alpha, void* Xmk, void* Xdk,
+                         int64_t rp, int64_t O_pad, cudaStream_t st) {
+    const bool bf = Xmk != nullptr;
+    if (bf && (sizeof(Tp) != 4 || !Xdk || rp < v.R || rp % 2 != 0 || O_pad < v.O))
+        return DNA_ERR_ARG;
+    const size_t smem = glue::cand_smem<Tp>(v.R, bf);
+    const unsigned grid = (unsigned)((bf ? O_pad : v.O) + glue::TO - 1) / glue::TO;
+    if (bf) {
+        if constexpr (sizeof(Tp) == 4) {
+            auto k = glue::k_cand_fused<Tp, true>;
+            if (simt::prep_smem(k, smem)) return DNA_ERR_CUDA;
+            k<<<grid, dim3(32, glue::TY), smem, st>>>(v, c, A, B, splits, Xmu, Xdna, (Tp)eps, (Tp)alpha,
+                                               static_cast<glue::bf16*>(Xmk),
+                                               static_cast<glue::bf16*>(Xdk), rp);
+        }
+    } else {
+        auto k = glue::k_cand_fused<Tp, false>;
+        if (simt::prep_smem(k, smem)) return DNA_ERR_CUDA;
+        k<<<grid, dim3(32, glue::TY), smem, st>>>(v, c, A, B, splits, Xmu, Xdna, (Tp)eps, (Tp)alpha,
+                                           nullptr, nullptr, 0);
+    }
+    return simt::launch_status();
+}
+
+template <typename Tp>
+int Simt<Tp>::select_fused(const View& v, const Tp* Xmu, const Tp* Xdna, const double* dpart,
+                           int splits, uint8_t* choice, double* dfin, double* fpart,
+                           cudaStream_t st) {
+    const size_t smem = glue::select_smem<Tp>(v.R);
+    auto k = glue::k_select_fused<Tp>;
+    if (simt::prep_smem(k, smem)) return DNA_ERR_CUDA;
+    k<<<(unsigned)glue_parts(v.O), dim3(32, 8), smem, st>>>(v, Xmu, Xdna, dpart, splits, choice,
+                                                           dfin, fpart);
+    return simt::launch_status();
+}
+
+template <typename Tp>
+int Simt<Tp>::part_sums(const double* part, int64_t nparts, int64_t R, double reg, double* out,
+                        cudaStream_t st) {
+    simt::k_colsum_final<<<(unsigned)((R + 7) / 8), 256, 0, st>>>(part, (int)nparts, R, reg, out,
+                                                                  true);
+    return simt::launch_status();
+}
+
+template <typename Tp>
+int Simt<Tp>::scale_ops(const View& t, const double* f, bool xmul, void* Xk, void* Yk, void* Ytk,
+                        void* Y2tk, int64_t rp, int64_t O_pad, int64_t S_pad, double* cpart,
+                        cudaStream_t st) {
+    const bool bf = Xk != nullptr;
+    if (bf && (sizeof(Tp) != 4 || !Yk || !Ytk || rp < t.R || O_pad < t.O || S_pad < t.S))
+        return DNA_ERR_ARG;
+    glue::OpsArgs a{};
+    a.X = t.X; a.xr = t.xr; a.xo = t.xo; a.O = t.O;
+    a.Y = const_cast<void*>(t.Y); a.ys = t.ys; a.yr = t.yr; a.S = t.S;
+    a.R = t.R; a.f = f; a.xmul = xmul;
+    a.Xk = static_cast<glue::bf16*>(Xk); a.Yk = static_cast<glue::bf16*>(Yk);
+    a.Ytk = static_cast<glue::bf16*>(Ytk); a.Y2tk = static_cast<glue::bf16*>(Y2tk);
+    a.rp = rp; a.O_pad = O_pad; a.S_pad = S_pad; a.cpart = cpart;
+    const int64_t rcov = bf ? rp : t.R, ocov = bf ? O_pad : t.O, scov = bf ? S_pad : t.S;
+    a.tiles_r = glue_parts(rcov);
+    // without scaling and operands the X tiles have nothing to do
+    a.xtiles_o = (f || bf) ? glue_parts(ocov) : 0;
+    a.xtiles = a.xtiles_o * a.tiles_r;
+    const int64_t ytiles = (f || bf || cpart) ? glue_parts(scov) * a.tiles_r : 0;
+    const int64_t blocks = a.xtiles + ytiles;
+    if (blocks == 0) return DNA_OK;
+    glue::k_scale_ops<Tp><<<(unsigned)blocks, dim3(32, 8), 0, st>>>(a);
     return simt::launch_status();
 }
 

@@ -42,7 +42,10 @@ using bf16 = __nv_bfloat16;
 
 // Wait for a barrier phase; give up when another thread of the CTA has aborted or after
 // WAIT_LIMIT cycles (then abort the CTA).
+// A phase that has already completed costs only the non-blocking test: the suspending
+// try_wait costs a couple of hundred cycles even then.
 __device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity, volatile int* abort) {
+    if (mbar_test(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
         if (*abort) return false;
@@ -65,38 +68,92 @@ struct P1Args {
     float* Apart;   // [splits][R][O]
     float* Bpart;
     int* status;
+    const float* V;   // V_so, element (s, o) at V[s * vs + o]
+    int64_t vs;
+    const void* X;    // bf16 X operand [O_pad][rp]
+    int64_t rp;
 };
 
+struct P2Args {
+    int64_t S, O, R, s_per;
+    double* dpart;  // [splits][2][O]
+    int* status;
+    const float* V;
+    int64_t vs;
+    const void* Xm;   // bf16 candidates [O_pad][rp]
+    const void* Xd;
+    int64_t rp;
+};
+
+// ---------------------------------------------------------------- RP in {64, 128}
+// Sixteen epilogue warps (four per TMEM lane quadrant, each taking 16 of the 64 chunk
+// columns), then the TMA producer warp and the MMA-issuing warps.
+//
+// Three costs shape these kernels.  Shared-memory bandwidth: the o-block's X (X_mu,
+// X_dna) is copied once into tensor memory and read by the MMAs from there, and Q, Qbar
+// are written by the epilogue straight into tensor memory, so only V and the per-chunk B
+// operands (Y, Y^t, (Y o Y)^t) pass through shared memory, all by TMA.  Group boundaries:
+// each wait, fence or commit of an MMA-issuing thread costs the tensor pipe a few hundred
+// cycles, so each issuing thread waits on at most two barriers and commits once per chunk.
+// Issue concurrency: two issuing threads (one per independent GEMM chain) keep the tensor
+// pipe busy while the other one is at a boundary.
+constexpr int W_EPI = 16;
+constexpr int W_PRODUCER = W_EPI;
+constexpr int P1_THREADS = (W_EPI + 3) * 32;      // producer + two MMA warps
+constexpr int W_MMA_Z = W_EPI + 1, W_MMA_AB = W_EPI + 2;
+
+// X rows [o][rp] (bf16, global) -> tensor memory, 16-column unit `unit` (32 values of r)
+// of the lane quadrant addressed by taddr.
+__device__ __forceinline__ void x_to_tmem(const bf16* __restrict__ X, int64_t rp, int64_t o,
+                                          int unit, uint32_t taddr) {
+    const uint4* src = reinterpret_cast<const uint4*>(X + o * rp + 32 * unit);
+    uint32_t w[16];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const uint4 q = src[i];
+        w[4 * i] = q.x; w[4 * i + 1] = q.y; w[4 * i + 2] = q.z; w[4 * i + 3] = q.w;
+    }
+    tmem_st16(taddr + 16 * unit, w);
+}
+
+// Pass 1.  Shared memory: V ring (4 x [64][128] fp32), Y ring (2 x [64][RP] bf16), Y^t /
+// (Y o Y)^t ring (2 x 2 x [RP][64] bf16).  Tensor memory: Z x 2 | A | B | X | Q | Qbar.
 template <int RP>
 struct P1Layout {
-    static constexpr uint32_t X = 0;                               // [128][RP] bf16
-    static constexpr uint32_t Y_BYTES = SCH * RP * 2;              // [64][RP]
-    static constexpr uint32_t V_BYTES = SCH * OBLK * 4;            // [64][128] fp32
-    static constexpr uint32_t RA = X + OBLK * RP * 2;              // ring A: Y, V
-    static constexpr uint32_t RA_STAGE = Y_BYTES + V_BYTES;
-    static constexpr uint32_t YT_BYTES = RP * SCH * 2;             // [RP][64]
-    static constexpr uint32_t RB = RA + 2 * RA_STAGE;              // ring B: Yt, Y2t
-    static constexpr uint32_t RB_STAGE = 2 * YT_BYTES;
-    static constexpr uint32_t Q = RB + 2 * RB_STAGE;               // [128][64] bf16
-    static constexpr uint32_t QB = Q + OBLK * SCH * 2;
-    static constexpr uint32_t BAR = QB + OBLK * SCH * 2;
+    static constexpr int VST = 4, YST = 2, TST = 2;
+    static constexpr uint32_t V_BYTES = SCH * OBLK * 4;
+    static constexpr uint32_t Y_BYTES = SCH * RP * 2;
+    static constexpr uint32_t YT_BYTES = RP * SCH * 2;
+    static constexpr uint32_t T_STAGE = 2 * YT_BYTES;
+    static constexpr uint32_t VR = 0;
+    static constexpr uint32_t YR = VR + VST * V_BYTES;
+    static constexpr uint32_t TR = YR + YST * Y_BYTES;
+    static constexpr uint32_t BAR = TR + TST * T_STAGE;
     static constexpr uint32_t TOTAL = BAR + 256;
-    static constexpr uint32_t NCOLS = (2 * SCH + 2 * RP) <= 256 ? 256 : 512;
-    static_assert(RA % 1024 == 0 && RA_STAGE % 1024 == 0 && RB % 1024 == 0 && Q % 1024 == 0,
+    static constexpr uint32_t NCOLS = 512;
+    static constexpr uint32_t TA = 2 * SCH, TB = TA + RP, TX = TB + RP, TQ = TX + RP / 2,
+                              TQB = TQ + SCH / 2;
+    static_assert(TQB + SCH / 2 <= NCOLS, "tensor memory budget");
+    static_assert(YR % 1024 == 0 && TR % 1024 == 0 && Y_BYTES % 1024 == 0 &&
+                      YT_BYTES % 1024 == 0,
                   "tiles must be 1024-byte aligned");
     static_assert(TOTAL + 1024 <= 232448, "shared memory budget");
 };
 
-// Barrier slots (uint64 each) of pass 1.
-enum { B_FULLA = 0, B_EMPTYA = 2, B_FULLB = 4, B_EMPTYB = 6, B_ZFULL = 8, B_ZEMPTY = 10,
-       B_QFULL = 12, B_QEMPTY = 13, B_XFULL = 14, B_ACC = 15, B_DRAIN = 16, B_COUNT = 17 };
+// Barrier slots of pass 1.  ZFULL[b] (GEMM1 of chunk m done, m % 2 == b) also frees the
+// Y stage of chunk m; QEMPTY[b] (GEMM2/3 of chunk m done) also frees its Y^t stage and,
+// for the last chunk, marks A and B final.
+enum { B_XFULL = 0, B_VFULL = 1, B_VEMPTY = 5, B_YFULL = 9, B_TFULL = 11, B_ZFULL = 13,
+       B_ZEMPTY = 15, B_QFULL = 17, B_QEMPTY = 18, B_DRAIN = 20, B_COUNT = 22 };
 
 template <int RP, bool WITH_B>
-__global__ void __launch_bounds__(NTHREADS, 1)
-    k_tc_pass1(P1Args a, const __grid_constant__ CUtensorMap tmX,
-               const __grid_constant__ CUtensorMap tmY, const __grid_constant__ CUtensorMap tmYt,
-               const __grid_constant__ CUtensorMap tmY2t, const __grid_constant__ CUtensorMap tmV) {
+__global__ void __launch_bounds__(P1_THREADS, 1)
+    k_tc_pass1(P1Args a, const __grid_constant__ CUtensorMap tmY,
+               const __grid_constant__ CUtensorMap tmYt, const __grid_constant__ CUtensorMap tmY2t,
+               const __grid_constant__ CUtensorMap tmV) {
     using L = P1Layout<RP>;
+    constexpr int VST = L::VST, YST = L::YST, TST = L::TST;
+    static_assert(YST == 2 && TST == 2, "stage reuse is signalled by the 2-deep commit barriers");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* sm = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -112,20 +169,21 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int nch = s_end > s_begin ? (int)((s_end - s_begin + SCH - 1) / SCH) : 0;
 
     if (warp == 0) { tmem_alloc(tslot, L::NCOLS); tmem_relinquish(); }
-    if (tid == MMA_WARP * 32) {
-        for (int i = 0; i < 2; ++i) {
-            mbar_init(&bar[B_FULLA + i], 1);
-            mbar_init(&bar[B_EMPTYA + i], 1 + NEPI_WARPS);  // MMA commit + epilogue warps
-            mbar_init(&bar[B_FULLB + i], 1);
-            mbar_init(&bar[B_EMPTYB + i], 1);
-            mbar_init(&bar[B_ZFULL + i], 1);
-            mbar_init(&bar[B_ZEMPTY + i], NEPI_WARPS);
+    if (tid == W_PRODUCER * 32) {
+        mbar_init(&bar[B_XFULL], W_EPI);
+        for (int i = 0; i < VST; ++i) {
+            mbar_init(&bar[B_VFULL + i], 1);
+            mbar_init(&bar[B_VEMPTY + i], W_EPI);
         }
-        mbar_init(&bar[B_QFULL], NEPI_WARPS);
-        mbar_init(&bar[B_QEMPTY], 1);
-        mbar_init(&bar[B_XFULL], 1);
-        mbar_init(&bar[B_ACC], 1);
-        mbar_init(&bar[B_DRAIN], 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&bar[B_YFULL + i], 1);
+            mbar_init(&bar[B_TFULL + i], 1);
+            mbar_init(&bar[B_ZFULL + i], 1);
+            mbar_init(&bar[B_ZEMPTY + i], W_EPI);
+            mbar_init(&bar[B_QEMPTY + i], 1);
+            mbar_init(&bar[B_DRAIN + i], 1);
+        }
+        mbar_init(&bar[B_QFULL], W_EPI);
         *abort = 0;
         fence_mbar_init();
     }
@@ -133,128 +191,165 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
-    const uint32_t tA = tmem + 2 * SCH, tB = tmem + 2 * SCH + RP;
 
-    if (warp == PRODUCER_WARP) {
+    if (warp == W_PRODUCER) {
+        // One thread services the three rings in whatever order their slots free up.
         if (lane == 0 && nch > 0) {
-            tma_prefetch_desc(&tmX); tma_prefetch_desc(&tmY); tma_prefetch_desc(&tmYt);
-            tma_prefetch_desc(&tmY2t); tma_prefetch_desc(&tmV);
-            mbar_arrive_expect_tx(&bar[B_XFULL], OBLK * RP * 2);
-            for (int at = 0; at < RP / 64; ++at)
-                tma_load_2d(sbase + L::X + at * OBLK * 128, &tmX, 64 * at, (int32_t)o0,
-                            &bar[B_XFULL]);
-            int lastA[2] = {-1, -1}, lastB[2] = {-1, -1};
-            for (int k = 0; k < nch; ++k) {
-                const int st = k & 1;
-                const uint32_t par = ((k >> 1) & 1) ^ 1;
-                const int32_t s0 = (int32_t)(s_begin + (int64_t)k * SCH);
-                if (!wait_phase(&bar[B_EMPTYA + st], par, abort)) break;
-                const uint32_t ra = sbase + L::RA + st * L::RA_STAGE;
-                mbar_arrive_expect_tx(&bar[B_FULLA + st], L::Y_BYTES + L::V_BYTES);
-                for (int at = 0; at < RP / 64; ++at)
-                    tma_load_2d(ra + at * SCH * 128, &tmY, 64 * at, s0, &bar[B_FULLA + st]);
-                tma_load_2d(ra + L::Y_BYTES, &tmV, (int32_t)o0, s0, &bar[B_FULLA + st]);
-                lastA[st] = k;
-                if (!wait_phase(&bar[B_EMPTYB + st], par, abort)) break;
-                const uint32_t rb = sbase + L::RB + st * L::RB_STAGE;
-                mbar_arrive_expect_tx(&bar[B_FULLB + st], (WITH_B ? 2 : 1) * L::YT_BYTES);
-                tma_load_2d(rb, &tmYt, s0, 0, &bar[B_FULLB + st]);
-                if (WITH_B) tma_load_2d(rb + L::YT_BYTES, &tmY2t, s0, 0, &bar[B_FULLB + st]);
-                lastB[st] = k;
+            tma_prefetch_desc(&tmY); tma_prefetch_desc(&tmYt); tma_prefetch_desc(&tmY2t);
+            tma_prefetch_desc(&tmV);
+            int kv = 0, ky = 0, kt = 0;
+            long long t0 = clock64();
+            while (kv < nch || ky < nch || kt < nch) {
+                bool prog = false;
+                if (kv < nch && mbar_test(&bar[B_VEMPTY + kv % VST], ((kv / VST) & 1) ^ 1)) {
+                    const int st = kv % VST;
+                    mbar_arrive_expect_tx(&bar[B_VFULL + st], L::V_BYTES);
+                    tma_load_2d(sbase + L::VR + st * L::V_BYTES, &tmV, (int32_t)o0,
+                                (int32_t)(s_begin + (int64_t)kv * SCH), &bar[B_VFULL + st]);
+                    ++kv;
+                    prog = true;
+                }
+                // Y(ky) reuses the stage of chunk m = ky - 2, free once GEMM1(m) is done
+                if (ky < nch && (ky < YST || mbar_test(&bar[B_ZFULL + (ky & 1)],
+                                                       ((ky - 2) >> 1) & 1))) {
+                    const int st = ky % YST;
+                    const uint32_t dst = sbase + L::YR + st * L::Y_BYTES;
+                    mbar_arrive_expect_tx(&bar[B_YFULL + st], L::Y_BYTES);
+                    for (int at = 0; at < RP / 64; ++at)
+                        tma_load_2d(dst + at * SCH * 128, &tmY, 64 * at,
+                                    (int32_t)(s_begin + (int64_t)ky * SCH), &bar[B_YFULL + st]);
+                    ++ky;
+                    prog = true;
+                }
+                // Y^t(kt) reuses the stage of chunk m = kt - 2, free once GEMM2/3(m) are done
+                if (kt < nch && (kt < TST || mbar_test(&bar[B_QEMPTY + (kt & 1)],
+                                                       ((kt - 2) >> 1) & 1))) {
+                    const int st = kt % TST;
+                    const uint32_t dst = sbase + L::TR + st * L::T_STAGE;
+                    const int32_t s0 = (int32_t)(s_begin + (int64_t)kt * SCH);
+                    mbar_arrive_expect_tx(&bar[B_TFULL + st], (WITH_B ? 2 : 1) * L::YT_BYTES);
+                    tma_load_2d(dst, &tmYt, s0, 0, &bar[B_TFULL + st]);
+                    if (WITH_B) tma_load_2d(dst + L::YT_BYTES, &tmY2t, s0, 0, &bar[B_TFULL + st]);
+                    ++kt;
+                    prog = true;
+                }
+                if (prog) {
+                    t0 = clock64();
+                } else {
+                    if (*abort) break;
+                    if (clock64() - t0 > WAIT_LIMIT) { *abort = 1; break; }
+                    __nanosleep(20);
+                }
             }
             if (*abort) {  // let the copies already issued land before the CTA exits
-                drain_phase(&bar[B_XFULL], 0);
-                for (int st = 0; st < 2; ++st) {
-                    if (lastA[st] >= 0) drain_phase(&bar[B_FULLA + st], (lastA[st] >> 1) & 1);
-                    if (lastB[st] >= 0) drain_phase(&bar[B_FULLB + st], (lastB[st] >> 1) & 1);
-                }
+                for (int k = max(0, kv - VST); k < kv; ++k)
+                    drain_phase(&bar[B_VFULL + k % VST], (k / VST) & 1);
+                for (int k = max(0, ky - YST); k < ky; ++k)
+                    drain_phase(&bar[B_YFULL + k % YST], (k / YST) & 1);
+                for (int k = max(0, kt - TST); k < kt; ++k)
+                    drain_phase(&bar[B_TFULL + k % TST], (k / TST) & 1);
             }
         }
-    } else if (warp == MMA_WARP) {
+    } else if (warp == W_MMA_Z) {
+        // GEMM1 of every chunk m into Z buffer m & 1, A = X in TMEM
         if (lane == 0 && nch > 0) {
             bool ok = wait_phase(&bar[B_XFULL], 0, abort);
-            for (int k = 0; ok && k <= nch; ++k) {
-                if (k < nch) {  // GEMM1 of chunk k into Z buffer k & 1
-                    const int st = k & 1;
-                    const uint32_t par = (k >> 1) & 1;
-                    if (!(ok = wait_phase(&bar[B_FULLA + st], par, abort))) break;
-                    if (!(ok = wait_phase(&bar[B_ZEMPTY + st], par ^ 1, abort))) break;
-                    tc_fence_after();
-                    const uint32_t ra = sbase + L::RA + st * L::RA_STAGE;
-                    const uint32_t tz = tmem + st * SCH;
+            for (int m = 0; ok && m < nch; ++m) {
+                const int zb = m & 1;
+                if (!(ok = wait_phase(&bar[B_YFULL + m % YST], (m / YST) & 1, abort))) break;
+                if (m >= 2 &&
+                    !(ok = wait_phase(&bar[B_ZEMPTY + zb], ((m >> 1) & 1) ^ 1, abort)))
+                    break;
+                tc_fence_after();
+                const uint32_t yb = sbase + L::YR + (m % YST) * L::Y_BYTES;
 #pragma unroll
-                    for (int kk = 0; kk < RP / 16; ++kk) {
-                        const uint32_t kb = 32u * kk, at = kb >> 7, within = kb & 127u;
-                        mma_bf16(tz, desc_sw128(sbase + L::X + at * OBLK * 128 + within),
-                                 desc_sw128(ra + at * SCH * 128 + within), idesc_bf16(OBLK, SCH),
-                                 kk > 0);
-                    }
-                    mma_commit(&bar[B_ZFULL + st]);
-                    mma_commit(&bar[B_EMPTYA + st]);
+                for (int kk = 0; kk < RP / 16; ++kk) {
+                    const uint32_t kb = 32u * kk, at = kb >> 7, within = kb & 127u;
+                    mma_bf16_tmem_a(tmem + zb * SCH, tmem + L::TX + 8 * kk,
+                                    desc_sw128(yb + at * SCH * 128 + within),
+                                    idesc_bf16(OBLK, SCH), kk > 0);
                 }
-                if (k >= 1) {  // GEMM2 / GEMM3 of chunk k - 1
-                    const int kp = k - 1, st = kp & 1;
-                    if (!(ok = wait_phase(&bar[B_QFULL], kp & 1, abort))) break;
-                    if (!(ok = wait_phase(&bar[B_FULLB + st], (kp >> 1) & 1, abort))) break;
-                    tc_fence_after();
-                    const uint32_t rb = sbase + L::RB + st * L::RB_STAGE;
-#pragma unroll
-                    for (int kk = 0; kk < SCH / 16; ++kk) {
-                        const uint32_t kb = 32u * kk;
-                        const uint32_t acc = (kp > 0 || kk > 0) ? 1u : 0u;
-                        mma_bf16(tA, desc_sw128(sbase + L::Q + kb), desc_sw128(rb + kb),
-                                 idesc_bf16(OBLK, RP), acc);
-                        if (WITH_B)
-                            mma_bf16(tB, desc_sw128(sbase + L::QB + kb),
-                                     desc_sw128(rb + L::YT_BYTES + kb), idesc_bf16(OBLK, RP), acc);
-                    }
-                    mma_commit(&bar[B_QEMPTY]);
-                    mma_commit(&bar[B_EMPTYB + st]);
-                }
+                mma_commit(&bar[B_ZFULL + zb]);
             }
-            if (ok) {
-                mma_commit(&bar[B_ACC]);
-            } else {  // no MMA may still be writing TMEM when it is released
-                mma_commit(&bar[B_DRAIN]);
-                drain_phase(&bar[B_DRAIN], 0);
+            if (!ok) {  // no MMA of this thread may still be writing TMEM when it is released
+                mma_commit(&bar[B_DRAIN + 0]);
+                drain_phase(&bar[B_DRAIN + 0], 0);
+            }
+        }
+    } else if (warp == W_MMA_AB) {
+        // GEMM2 / GEMM3 of every chunk m, A = Q / Qbar in TMEM
+        if (lane == 0 && nch > 0) {
+            bool ok = true;
+            for (int m = 0; ok && m < nch; ++m) {
+                if (!(ok = wait_phase(&bar[B_QFULL], m & 1, abort))) break;
+                if (!(ok = wait_phase(&bar[B_TFULL + m % TST], (m / TST) & 1, abort))) break;
+                tc_fence_after();
+                const uint32_t tb = sbase + L::TR + (m % TST) * L::T_STAGE;
+#pragma unroll
+                for (int kk = 0; kk < SCH / 16; ++kk) {
+                    const uint32_t acc = (m > 0 || kk > 0) ? 1u : 0u;
+                    mma_bf16_tmem_a(tmem + L::TA, tmem + L::TQ + 8 * kk,
+                                    desc_sw128(tb + 32u * kk), idesc_bf16(OBLK, RP), acc);
+                    if (WITH_B)
+                        mma_bf16_tmem_a(tmem + L::TB, tmem + L::TQB + 8 * kk,
+                                        desc_sw128(tb + L::YT_BYTES + 32u * kk),
+                                        idesc_bf16(OBLK, RP), acc);
+                }
+                mma_commit(&bar[B_QEMPTY + (m & 1)]);
+            }
+            if (!ok) {
+                mma_commit(&bar[B_DRAIN + 1]);
+                drain_phase(&bar[B_DRAIN + 1], 0);
             }
         }
     } else {
-        // epilogue warps 0-7: lane quadrant qd = warp % 4 (o = o0 + 32 qd + lane), chunk
-        // columns 32 hf .. 32 hf + 31 with hf = warp / 4
-        const int qd = warp & 3, hf = warp >> 2;
-        const int row = 32 * qd + lane;                  // TMEM lane = row of the o-block
+        // epilogue warps 0-15: lane quadrant qd = warp % 4 (o = o0 + 32 qd + lane), chunk
+        // columns 16 cg .. 16 cg + 15 with cg = warp / 4
+        const int qd = warp & 3, cg = warp >> 2;
+        const int row = 32 * qd + lane;
         const int64_t o = o0 + row;
         const uint32_t lane_off = (uint32_t)(32 * qd) << 16;
-        bool bad = false;
+        if (nch > 0) {   // X of this o-block into tensor memory (GEMM1's A operand)
+            for (int u = cg; u < RP / 32; u += 4)
+                x_to_tmem(static_cast<const bf16*>(a.X), a.rp, o, u, tmem + L::TX + lane_off);
+            tmem_st_wait();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bar[B_XFULL]);
+        }
+        // min over v > 0 of z: a non-positive z there is an infinite cost (a NaN z makes
+        // NaN candidates, which pass 2 reports)
+        float zmin = 1.f;
         bool ok = true;
         for (int k = 0; k < nch; ++k) {
-            const int st = k & 1;
-            const uint32_t par = (k >> 1) & 1;
-            ok = wait_phase(&bar[B_ZFULL + st], par, abort);
-            ok = ok && wait_phase(&bar[B_FULLA + st], par, abort);
+            const int zb = k & 1, vs = k % VST;
+            ok = wait_phase(&bar[B_ZFULL + zb], (k >> 1) & 1, abort);
+            ok = ok && wait_phase(&bar[B_VFULL + vs], (k / VST) & 1, abort);
             if (!(ok = __all_sync(0xffffffffu, ok))) break;   // keep the warp converged
             tc_fence_after();
-            uint32_t zr[32];
-            tmem_ld32(tmem + st * SCH + lane_off + 32 * hf, zr);
+            uint32_t zr[16];
+            tmem_ld16(tmem + zb * SCH + lane_off + 16 * cg, zr);
+            // V rows s = 16 cg + j of this stage; TMA zero-fills v outside the problem
+            const float* Vs = reinterpret_cast<const float*>(sm + L::VR + vs * L::V_BYTES) +
+                              16 * cg * OBLK + row;
+            float vv[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) vv[j] = Vs[j * OBLK];
             tmem_ld_wait();
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&bar[B_ZEMPTY + st]);
-            // V rows s = 32 hf + j of this stage; TMA zero-fills v outside the problem
-            const float* Vs = reinterpret_cast<const float*>(sm + L::RA + st * L::RA_STAGE +
-                                                             L::Y_BYTES) + 32 * hf * OBLK + row;
-            uint32_t qp[16], qbp[16];
+            if (lane == 0) mbar_arrive(&bar[B_ZEMPTY + zb]);
+            uint32_t qp[8], qbp[8];
 #pragma unroll
-            for (int j = 0; j < 32; j += 2) {
+            for (int j = 0; j < 16; j += 2) {
                 float q[2], qb[2];
 #pragma unroll
                 for (int t = 0; t < 2; ++t) {
-                    const float v = Vs[(j + t) * OBLK];
+                    const float v = vv[j + t];
                     const float z = __uint_as_float(zr[j + t]);
                     const float rz = __fdividef(1.0f, z);
                     const bool pos = v > 0.f;
-                    bad |= pos && !(z > 0.f);
+                    zmin = fminf(zmin, pos ? z : 1.f);
                     q[t] = pos ? v * rz : 0.f;
                     qb[t] = pos ? q[t] * rz : 0.f;
                 }
@@ -262,54 +357,44 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 qbp[j / 2] = pack_bf16x2(qb[0], qb[1]);
             }
             __syncwarp();
-            if (lane == 0) mbar_arrive(&bar[B_EMPTYA + st]);  // V of this stage consumed
-            ok = wait_phase(&bar[B_QEMPTY], (k & 1) ^ 1, abort);
-            if (!(ok = __all_sync(0xffffffffu, ok))) break;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const uint32_t off = sw128_offset(row, 4 * hf + c, OBLK);
-                asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(sbase + L::Q + off),
-                             "r"(qp[4 * c]), "r"(qp[4 * c + 1]), "r"(qp[4 * c + 2]),
-                             "r"(qp[4 * c + 3])
-                             : "memory");
-                if (WITH_B)
-                    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(
-                                     sbase + L::QB + off),
-                                 "r"(qbp[4 * c]), "r"(qbp[4 * c + 1]), "r"(qbp[4 * c + 2]),
-                                 "r"(qbp[4 * c + 3])
-                                 : "memory");
+            if (lane == 0) mbar_arrive(&bar[B_VEMPTY + vs]);   // v of this stage consumed
+            if (k >= 1) {   // GEMM2/3 of chunk k - 1 have read the Q buffer
+                const int kp = k - 1;
+                ok = wait_phase(&bar[B_QEMPTY + (kp & 1)], (kp >> 1) & 1, abort);
+                if (!(ok = __all_sync(0xffffffffu, ok))) break;
+                tc_fence_after();
             }
-            fence_proxy_async_smem();
+            tmem_st8(tmem + L::TQ + 8 * cg + lane_off, qp);
+            if (WITH_B) tmem_st8(tmem + L::TQB + 8 * cg + lane_off, qbp);
+            tmem_st_wait();
+            tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&bar[B_QFULL]);
         }
-        if (bad) atomicOr(a.status, STATUS_NONFINITE);
-        if (ok && nch > 0) ok = __all_sync(0xffffffffu, wait_phase(&bar[B_ACC], 0, abort));
+        if (!(zmin > 0.f)) atomicOr(a.status, STATUS_NONFINITE);
+        if (ok && nch > 0) {   // GEMM2/3 of the last chunk done: A and B are final
+            const int kl = nch - 1;
+            ok = __all_sync(0xffffffffu,
+                            wait_phase(&bar[B_QEMPTY + (kl & 1)], (kl >> 1) & 1, abort));
+        }
         if (ok && nch > 0) {
             tc_fence_after();
             const int64_t base = (int64_t)blockIdx.y * a.R;
-            // this warp writes r-groups g = hf, hf + 2, ... of 32 columns
+            constexpr int G = RP / 32;   // 32-column groups of A (then of B)
 #pragma unroll 1
-            for (int g = hf; g < RP / 32; g += 2) {
+            for (int u = cg; u < (WITH_B ? 2 : 1) * G; u += 4) {
+                const bool isb = u >= G;
+                const int g = isb ? u - G : u;
                 uint32_t r32[32];
-                tmem_ld32(tA + lane_off + 32 * g, r32);
+                tmem_ld32(tmem + (isb ? L::TB : L::TA) + lane_off + 32 * g, r32);
                 tmem_ld_wait();
+                float* dst = isb ? a.Bpart : a.Apart;
                 if (o < a.O)
 #pragma unroll
                     for (int i = 0; i < 32; ++i) {
                         const int64_t r = 32 * g + i;
-                        if (r < a.R) a.Apart[(base + r) * a.O + o] = __uint_as_float(r32[i]);
+                        if (r < a.R) dst[(base + r) * a.O + o] = __uint_as_float(r32[i]);
                     }
-                if (WITH_B) {
-                    tmem_ld32(tB + lane_off + 32 * g, r32);
-                    tmem_ld_wait();
-                    if (o < a.O)
-#pragma unroll
-                        for (int i = 0; i < 32; ++i) {
-                            const int64_t r = 32 * g + i;
-                            if (r < a.R) a.Bpart[(base + r) * a.O + o] = __uint_as_float(r32[i]);
-                        }
-                }
             }
         }
     }
@@ -319,37 +404,38 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (warp == 0) tmem_dealloc(tmem, L::NCOLS);
 }
 
-struct P2Args {
-    int64_t S, O, R, s_per;
-    double* dpart;  // [splits][2][O]
-    int* status;
-};
-
+// Pass 2.  Shared memory: V ring (4 stages), Y ring (2 stages), the per-warp cost sums.
+// Tensor memory: two buffers of (Z_mu, Z_dna), 64 columns each, then X_mu and X_dna.  One
+// MMA-issuing warp per candidate (Z_mu and Z_dna are independent GEMM chains).
 template <int RP>
 struct P2Layout {
-    static constexpr uint32_t XM = 0;
-    static constexpr uint32_t XD = XM + OBLK * RP * 2;
-    static constexpr uint32_t Y_BYTES = SCH * RP * 2;
+    static constexpr int VST = 4, YST = 2;
     static constexpr uint32_t V_BYTES = SCH * OBLK * 4;
-    static constexpr uint32_t RA = XD + OBLK * RP * 2;
-    static constexpr uint32_t RA_STAGE = Y_BYTES + V_BYTES;
-    static constexpr uint32_t RED = RA + 2 * RA_STAGE;   // [2][128] float64 half-sums
-    static constexpr uint32_t BAR = RED + 2 * OBLK * 8;
+    static constexpr uint32_t Y_BYTES = SCH * RP * 2;
+    static constexpr uint32_t VR = 0;
+    static constexpr uint32_t YR = VR + VST * V_BYTES;
+    static constexpr uint32_t RED = YR + YST * Y_BYTES;   // [4 column groups][2][128] float64
+    static constexpr uint32_t BAR = RED + 4 * 2 * OBLK * 8;
     static constexpr uint32_t TOTAL = BAR + 256;
-    static constexpr uint32_t NCOLS = 4 * SCH;  // two buffers x two candidates
-    static_assert(RA % 1024 == 0 && RA_STAGE % 1024 == 0, "tiles must be 1024-byte aligned");
+    static constexpr uint32_t NCOLS = 512;
+    static constexpr uint32_t TXM = 4 * SCH, TXD = TXM + RP / 2;
+    static_assert(TXD + RP / 2 <= NCOLS, "tensor memory budget");
+    static_assert(YR % 1024 == 0 && Y_BYTES % 1024 == 0, "tiles must be 1024-byte aligned");
     static_assert(TOTAL + 1024 <= 232448, "shared memory budget");
 };
 
-enum { C_FULLA = 0, C_EMPTYA = 2, C_ZFULL = 4, C_ZEMPTY = 6, C_XFULL = 8, C_DRAIN = 9,
-       C_COUNT = 10 };
+// ZFULL[c][b]: the GEMM of candidate c (0 = MU, 1 = DNA) for chunk m (m % 2 == b) is done;
+// both together also free the Y stage of chunk m.
+enum { C_XFULL = 0, C_VFULL = 1, C_VEMPTY = 5, C_YFULL = 9, C_ZFULL = 11, C_ZEMPTY = 15,
+       C_DRAIN = 17, C_COUNT = 19 };
 
 template <int RP>
-__global__ void __launch_bounds__(NTHREADS, 1)
-    k_tc_pass2(P2Args a, const __grid_constant__ CUtensorMap tmXm,
-               const __grid_constant__ CUtensorMap tmXd, const __grid_constant__ CUtensorMap tmY,
+__global__ void __launch_bounds__(P1_THREADS, 1)
+    k_tc_pass2(P2Args a, const __grid_constant__ CUtensorMap tmY,
                const __grid_constant__ CUtensorMap tmV) {
     using L = P2Layout<RP>;
+    constexpr int VST = L::VST, YST = L::YST;
+    static_assert(YST == 2, "stage reuse is signalled by the 2-deep commit barriers");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* sm = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -365,15 +451,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int nch = s_end > s_begin ? (int)((s_end - s_begin + SCH - 1) / SCH) : 0;
 
     if (warp == 0) { tmem_alloc(tslot, L::NCOLS); tmem_relinquish(); }
-    if (tid == MMA_WARP * 32) {
-        for (int i = 0; i < 2; ++i) {
-            mbar_init(&bar[C_FULLA + i], 1);
-            mbar_init(&bar[C_EMPTYA + i], 1 + NEPI_WARPS);
-            mbar_init(&bar[C_ZFULL + i], 1);
-            mbar_init(&bar[C_ZEMPTY + i], NEPI_WARPS);
+    if (tid == W_PRODUCER * 32) {
+        mbar_init(&bar[C_XFULL], W_EPI);
+        for (int i = 0; i < VST; ++i) {
+            mbar_init(&bar[C_VFULL + i], 1);
+            mbar_init(&bar[C_VEMPTY + i], W_EPI);
         }
-        mbar_init(&bar[C_XFULL], 1);
-        mbar_init(&bar[C_DRAIN], 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&bar[C_YFULL + i], 1);
+            mbar_init(&bar[C_ZFULL + i], 1);
+            mbar_init(&bar[C_ZFULL + 2 + i], 1);
+            mbar_init(&bar[C_ZEMPTY + i], W_EPI);
+            mbar_init(&bar[C_DRAIN + i], 1);
+        }
         *abort = 0;
         fence_mbar_init();
     }
@@ -382,115 +472,150 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     tc_fence_after();
     const uint32_t tmem = *tslot;
 
-    if (warp == PRODUCER_WARP) {
+    if (warp == W_PRODUCER) {
         if (lane == 0 && nch > 0) {
-            tma_prefetch_desc(&tmXm); tma_prefetch_desc(&tmXd); tma_prefetch_desc(&tmY);
+            tma_prefetch_desc(&tmY);
             tma_prefetch_desc(&tmV);
-            mbar_arrive_expect_tx(&bar[C_XFULL], 2 * OBLK * RP * 2);
-            for (int at = 0; at < RP / 64; ++at) {
-                tma_load_2d(sbase + L::XM + at * OBLK * 128, &tmXm, 64 * at, (int32_t)o0,
-                            &bar[C_XFULL]);
-                tma_load_2d(sbase + L::XD + at * OBLK * 128, &tmXd, 64 * at, (int32_t)o0,
-                            &bar[C_XFULL]);
-            }
-            int lastA[2] = {-1, -1};
-            for (int k = 0; k < nch; ++k) {
-                const int st = k & 1;
-                const int32_t s0 = (int32_t)(s_begin + (int64_t)k * SCH);
-                if (!wait_phase(&bar[C_EMPTYA + st], ((k >> 1) & 1) ^ 1, abort)) break;
-                const uint32_t ra = sbase + L::RA + st * L::RA_STAGE;
-                mbar_arrive_expect_tx(&bar[C_FULLA + st], L::Y_BYTES + L::V_BYTES);
-                for (int at = 0; at < RP / 64; ++at)
-                    tma_load_2d(ra + at * SCH * 128, &tmY, 64 * at, s0, &bar[C_FULLA + st]);
-                tma_load_2d(ra + L::Y_BYTES, &tmV, (int32_t)o0, s0, &bar[C_FULLA + st]);
-                lastA[st] = k;
+            int kv = 0, ky = 0;
+            long long t0 = clock64();
+            while (kv < nch || ky < nch) {
+                bool prog = false;
+                if (kv < nch && mbar_test(&bar[C_VEMPTY + kv % VST], ((kv / VST) & 1) ^ 1)) {
+                    const int st = kv % VST;
+                    mbar_arrive_expect_tx(&bar[C_VFULL + st], L::V_BYTES);
+                    tma_load_2d(sbase + L::VR + st * L::V_BYTES, &tmV, (int32_t)o0,
+                                (int32_t)(s_begin + (int64_t)kv * SCH), &bar[C_VFULL + st]);
+                    ++kv;
+                    prog = true;
+                }
+                // Y(ky) reuses the stage of chunk m = ky - 2, free once both GEMMs of m are done
+                if (ky < nch &&
+                    (ky < YST || (mbar_test(&bar[C_ZFULL + (ky & 1)], ((ky - 2) >> 1) & 1) &&
+                                  mbar_test(&bar[C_ZFULL + 2 + (ky & 1)], ((ky - 2) >> 1) & 1)))) {
+                    const int st = ky % YST;
+                    const uint32_t dst = sbase + L::YR + st * L::Y_BYTES;
+                    mbar_arrive_expect_tx(&bar[C_YFULL + st], L::Y_BYTES);
+                    for (int at = 0; at < RP / 64; ++at)
+                        tma_load_2d(dst + at * SCH * 128, &tmY, 64 * at,
+                                    (int32_t)(s_begin + (int64_t)ky * SCH), &bar[C_YFULL + st]);
+                    ++ky;
+                    prog = true;
+                }
+                if (prog) {
+                    t0 = clock64();
+                } else {
+                    if (*abort) break;
+                    if (clock64() - t0 > WAIT_LIMIT) { *abort = 1; break; }
+                    __nanosleep(20);
+                }
             }
             if (*abort) {
-                drain_phase(&bar[C_XFULL], 0);
-                for (int st = 0; st < 2; ++st)
-                    if (lastA[st] >= 0) drain_phase(&bar[C_FULLA + st], (lastA[st] >> 1) & 1);
+                for (int k = max(0, kv - VST); k < kv; ++k)
+                    drain_phase(&bar[C_VFULL + k % VST], (k / VST) & 1);
+                for (int k = max(0, ky - YST); k < ky; ++k)
+                    drain_phase(&bar[C_YFULL + k % YST], (k / YST) & 1);
             }
         }
-    } else if (warp == MMA_WARP) {
+    } else if (warp == W_MMA_Z || warp == W_MMA_AB) {
+        // candidate c: Z_c(m) = X_c Y(m)^t into buffer m & 1, A = X_c in TMEM
+        const int c = warp == W_MMA_AB ? 1 : 0;
         if (lane == 0 && nch > 0) {
             bool ok = wait_phase(&bar[C_XFULL], 0, abort);
-            for (int k = 0; ok && k < nch; ++k) {
-                const int st = k & 1;
-                const uint32_t par = (k >> 1) & 1;
-                if (!(ok = wait_phase(&bar[C_FULLA + st], par, abort))) break;
-                if (!(ok = wait_phase(&bar[C_ZEMPTY + st], par ^ 1, abort))) break;
+            for (int m = 0; ok && m < nch; ++m) {
+                const int zb = m & 1;
+                if (!(ok = wait_phase(&bar[C_YFULL + m % YST], (m / YST) & 1, abort))) break;
+                if (m >= 2 &&
+                    !(ok = wait_phase(&bar[C_ZEMPTY + zb], ((m >> 1) & 1) ^ 1, abort)))
+                    break;
                 tc_fence_after();
-                const uint32_t ra = sbase + L::RA + st * L::RA_STAGE;
-                const uint32_t tz = tmem + st * 2 * SCH;
+                const uint32_t yb = sbase + L::YR + (m % YST) * L::Y_BYTES;
+                const uint32_t tz = tmem + zb * 2 * SCH + c * SCH;
+                const uint32_t tx = tmem + (c ? L::TXD : L::TXM);
 #pragma unroll
                 for (int kk = 0; kk < RP / 16; ++kk) {
                     const uint32_t kb = 32u * kk, at = kb >> 7, within = kb & 127u;
-                    const uint64_t yd = desc_sw128(ra + at * SCH * 128 + within);
-                    mma_bf16(tz, desc_sw128(sbase + L::XM + at * OBLK * 128 + within), yd,
-                             idesc_bf16(OBLK, SCH), kk > 0);
-                    mma_bf16(tz + SCH, desc_sw128(sbase + L::XD + at * OBLK * 128 + within), yd,
-                             idesc_bf16(OBLK, SCH), kk > 0);
+                    mma_bf16_tmem_a(tz, tx + 8 * kk, desc_sw128(yb + at * SCH * 128 + within),
+                                    idesc_bf16(OBLK, SCH), kk > 0);
                 }
-                mma_commit(&bar[C_ZFULL + st]);
-                mma_commit(&bar[C_EMPTYA + st]);
+                mma_commit(&bar[C_ZFULL + 2 * c + zb]);
             }
             if (!ok) {
-                mma_commit(&bar[C_DRAIN]);
-                drain_phase(&bar[C_DRAIN], 0);
+                mma_commit(&bar[C_DRAIN + c]);
+                drain_phase(&bar[C_DRAIN + c], 0);
             }
         }
     } else {
-        const int qd = warp & 3, hf = warp >> 2;
+        const int qd = warp & 3, cg = warp >> 2;
         const int row = 32 * qd + lane;
         const int64_t o = o0 + row;
         const uint32_t lane_off = (uint32_t)(32 * qd) << 16;
+        if (nch > 0) {   // X_mu and X_dna of this o-block into tensor memory
+            constexpr int UPM = RP / 32;
+            for (int u = cg; u < 2 * UPM; u += 4) {
+                const bool isd = u >= UPM;
+                x_to_tmem(static_cast<const bf16*>(isd ? a.Xd : a.Xm), a.rp, o,
+                          isd ? u - UPM : u, tmem + (isd ? L::TXD : L::TXM) + lane_off);
+            }
+            tmem_st_wait();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bar[C_XFULL]);
+        }
         double acc_m = 0.0, acc_d = 0.0;
-        bool bad = false;
         bool ok = true;
         for (int k = 0; k < nch; ++k) {
-            const int st = k & 1;
-            const uint32_t par = (k >> 1) & 1;
-            ok = wait_phase(&bar[C_ZFULL + st], par, abort);
-            ok = ok && wait_phase(&bar[C_FULLA + st], par, abort);
+            const int zb = k & 1, vs = k % VST;
+            const uint32_t zpar = (k >> 1) & 1;
+            ok = wait_phase(&bar[C_ZFULL + zb], zpar, abort);
+            ok = ok && wait_phase(&bar[C_ZFULL + 2 + zb], zpar, abort);
+            ok = ok && wait_phase(&bar[C_VFULL + vs], (k / VST) & 1, abort);
             if (!(ok = __all_sync(0xffffffffu, ok))) break;   // keep the warp converged
             tc_fence_after();
-            const uint32_t tz = tmem + st * 2 * SCH + lane_off + 32 * hf;
-            uint32_t zm[32], zd[32];
-            tmem_ld32(tz, zm);
-            tmem_ld32(tz + SCH, zd);
+            const uint32_t tz = tmem + zb * 2 * SCH + lane_off + 16 * cg;
+            uint32_t zm[16], zd[16];
+            tmem_ld16(tz, zm);
+            tmem_ld16(tz + SCH, zd);
+            const float* Vs = reinterpret_cast<const float*>(sm + L::VR + vs * L::V_BYTES) +
+                              16 * cg * OBLK + row;
+            float vv[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) vv[j] = Vs[j * OBLK];
             tmem_ld_wait();
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&bar[C_ZEMPTY + st]);
-            const float* Vs = reinterpret_cast<const float*>(sm + L::RA + st * L::RA_STAGE +
-                                                             L::Y_BYTES) + 32 * hf * OBLK + row;
+            if (lane == 0) mbar_arrive(&bar[C_ZEMPTY + zb]);
             float run_m = 0.f, run_d = 0.f;
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const float v = Vs[j * OBLK];
+            for (int j = 0; j < 16; ++j) {
+                const float v = vv[j];
                 const float z1 = __uint_as_float(zm[j]), z2 = __uint_as_float(zd[j]);
                 const bool pos = v > 0.f;
-                bad |= pos && !(z1 > 0.f && z2 > 0.f);
                 const float l1 = __logf(z1), l2 = __logf(z2);
                 run_m += pos ? z1 - v * l1 : z1;
                 run_d += pos ? z2 - v * l2 : z2;
             }
             __syncwarp();
-            if (lane == 0) mbar_arrive(&bar[C_EMPTYA + st]);
+            if (lane == 0) mbar_arrive(&bar[C_VEMPTY + vs]);
             acc_m += (double)run_m;
             acc_d += (double)run_d;
         }
-        if (bad) atomicOr(a.status, STATUS_NONFINITE);
-        // combine the two column halves of each o in a fixed order
+        // z <= 0 under v > 0 makes log z NaN or -inf, a NaN z propagates: either way the
+        // cost sums are not finite
+        if (!(fabs(acc_m) < INFINITY && fabs(acc_d) < INFINITY))
+            atomicOr(a.status, STATUS_NONFINITE);
+        // combine the four column groups of each o in a fixed order
         double* red = reinterpret_cast<double*>(sm + L::RED);
-        if (hf == 1) {
-            red[row] = acc_m;
-            red[OBLK + row] = acc_d;
-        }
-        asm volatile("bar.sync 1, %0;" ::"r"(NEPI_WARPS * 32) : "memory");
-        if (hf == 0 && ok && nch > 0 && !*abort && o < a.O) {
-            a.dpart[((int64_t)blockIdx.y * 2 + 0) * a.O + o] = acc_m + red[row];
-            a.dpart[((int64_t)blockIdx.y * 2 + 1) * a.O + o] = acc_d + red[OBLK + row];
+        red[(cg * 2 + 0) * OBLK + row] = acc_m;
+        red[(cg * 2 + 1) * OBLK + row] = acc_d;
+        asm volatile("bar.sync 1, %0;" ::"r"(W_EPI * 32) : "memory");
+        if (cg == 0 && ok && nch > 0 && !*abort && o < a.O) {
+            double m = red[0 * OBLK + row], d = red[1 * OBLK + row];
+            for (int g = 1; g < 4; ++g) {
+                m += red[(g * 2 + 0) * OBLK + row];
+                d += red[(g * 2 + 1) * OBLK + row];
+            }
+            a.dpart[((int64_t)blockIdx.y * 2 + 0) * a.O + o] = m;
+            a.dpart[((int64_t)blockIdx.y * 2 + 1) * a.O + o] = d;
         }
     }
     tc_fence_before();
@@ -1043,7 +1168,7 @@ int launch_pass1(const P1Args& a, const TcMaps& m, int64_t O_pad, int splits, cu
         cudaSuccess)
         return DNA_ERR_CUDA;
     dim3 grid((unsigned)(O_pad / OBLK), (unsigned)splits);
-    k<<<grid, NTHREADS, smem, st>>>(a, m.x, m.y, m.yt, m.y2t, m.v);
+    k<<<grid, P1_THREADS, smem, st>>>(a, m.y, m.yt, m.y2t, m.v);
     return after_launch();
 }
 
@@ -1079,7 +1204,7 @@ int launch_pass2(const P2Args& a, const TcMaps& m, int64_t O_pad, int splits, cu
         cudaSuccess)
         return DNA_ERR_CUDA;
     dim3 grid((unsigned)(O_pad / OBLK), (unsigned)splits);
-    k<<<grid, NTHREADS, smem, st>>>(a, m.xm, m.xd, m.y, m.v);
+    k<<<grid, P1_THREADS, smem, st>>>(a, m.y, m.v);
     return after_launch();
 }
 
@@ -1134,6 +1259,7 @@ int TcBf16::pass1(const TcOperands& op, const TcMaps& maps, float* Apart, float*
     tc::P1Args a{};
     a.S = op.S; a.O = op.O; a.R = op.R; a.s_per = s_per;
     a.Apart = Apart; a.Bpart = Bpart; a.status = status;
+    a.V = op.V; a.vs = op.vs; a.X = op.Xk; a.rp = rank_pad(op.R);
     const int rp = rank_pad(op.R);
     if (rp == 64)
         return with_b ? tc::launch_pass1<64, true>(a, maps, op.O_pad, splits, st)
@@ -1155,6 +1281,7 @@ int TcBf16::pass2(const TcOperands& op, const TcMaps& maps, double* dpart, int s
     tc::P2Args a{};
     a.S = op.S; a.O = op.O; a.R = op.R; a.s_per = s_per;
     a.dpart = dpart; a.status = status;
+    a.V = op.V; a.vs = op.vs; a.Xm = op.Xmk; a.Xd = op.Xdk; a.rp = rank_pad(op.R);
     const int rp = rank_pad(op.R);
     if (rp == 64) return tc::launch_pass2<64>(a, maps, op.O_pad, splits, st);
     if (rp == 128) return tc::launch_pass2<128>(a, maps, op.O_pad, splits, st);

@@ -113,13 +113,20 @@ def test_zero_rows_and_columns():
     _ = _trajectory(workloads.Problem("z", V, p.W0, p.H0, p.W, p.H, 0), "f64", 2)
 
 
-def test_nonfinite_reported():
-    """z = 0 where v > 0 (a zero factor) is reported as DNA_ERR_NONFINITE, not hidden."""
+@pytest.mark.parametrize("kind", ["f32", "bf16"])
+@pytest.mark.parametrize("fault", ["zero_w", "nan_h"])
+def test_nonfinite_reported(kind, fault):
+    """z = 0 where v > 0 (a zero factor) or a NaN entry is reported as DNA_ERR_NONFINITE
+    after the half-step, not hidden (the BF16 passes check z <= 0 in pass 1 and the
+    finiteness of the cost sums in pass 2)."""
     import paper_1301_3389_gb300 as dna
     p = workloads.custom(40, 50, 4, seed=3)
-    W = p.W.copy()
-    W[:] = 0.0
-    with GpuProblem(p.V, W, p.H, "f32") as gp:
+    W, H = p.W.copy(), p.H.copy()
+    if fault == "zero_w":
+        W[:] = 0.0
+    else:
+        H[1, 7] = np.nan
+    with GpuProblem(p.V, W, H, kind) as gp:
         gp.dna.dna_step_H(gp.ctx)
         assert gp.dna.dna_get_status(gp.ctx) == dna.DNA_ERR_NONFINITE
 

@@ -37,6 +37,13 @@ __device__ __forceinline__ void ld4(const double* p, double (&v)[4]) {
     double2 b = *reinterpret_cast<const double2*>(p + 2);
     v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
 }
+__device__ __forceinline__ void st4(float* p, const float (&v)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4(double* p, const double (&v)[4]) {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+    *reinterpret_cast<double2*>(p + 2) = make_double2(v[2], v[3]);
+}
 __device__ __forceinline__ float dev_log(float x) { return logf(x); }
 __device__ __forceinline__ double dev_log(double x) { return log(x); }
 // a / b: the fast-division intrinsic in float32 (a few ulp), exact division in float64
@@ -140,20 +147,22 @@ __device__ __forceinline__ void pass1_tile(const View& v, Tp* __restrict__ Apart
             z_tile<Tp, RB>(Yt, Xs, zs, zo, z);
             __syncthreads();
         }
-        // q = v / z and qbar = v / z^2, zero where v = 0 (note after Algorithm 1)
+        // q = v / z and qbar = v / z^2, zero where v = 0 (note after Algorithm 1): one
+        // reciprocal per element, branch-free, rows stored as vectors (no bank conflicts)
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
+            Tp q[4], qb[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const Tp vv = vpre[i][j];
-                Tp q = Tp(0), qb = Tp(0);
-                if (vv > Tp(0)) {
-                    const Tp zz = z[i][j];
-                    if (zz > Tp(0)) { q = vv / zz; qb = q / zz; } else { bad = 1; }
-                }
-                Qs[(zs + i) * LD + zo + j] = q;
-                Qb[(zs + i) * LD + zo + j] = qb;
+                const Tp vv = vpre[i][j], zz = z[i][j];
+                const bool pos = vv > Tp(0);
+                bad |= (pos && !(zz > Tp(0))) ? 1 : 0;
+                const Tp rz = dev_div(Tp(1), zz);
+                q[j] = pos ? vv * rz : Tp(0);
+                qb[j] = pos ? q[j] * rz : Tp(0);
             }
+            st4(Qs + (zs + i) * LD + zo, q);
+            st4(Qb + (zs + i) * LD + zo, qb);
         }
         if (npieces > 1)
             load_tile<Tp, RB, SB>(Yt, Y, v.yr, v.ys, rown0, s0, v.R, v.S);
@@ -284,15 +293,12 @@ __device__ __forceinline__ void pass2_tile(const View& v, const Tp* __restrict__
 #pragma unroll
                 for (int c = 0; c < NC; ++c) {
                     const Tp zz = z[c][i][j];
-                    Tp term = zz;
-                    if (vv > Tp(0)) {
-                        if (zz > Tp(0)) {
-                            term += FULL ? (vv * dev_log(vv / zz) - vv) : (-vv * dev_log(zz));
-                        } else {
-                            bad = 1;
-                        }
-                    }
-                    run[c] += term;
+                    const bool pos = vv > Tp(0);
+                    bad |= (pos && !(zz > Tp(0))) ? 1 : 0;
+                    // branch-free: the v = 0 terms (possibly log of a non-positive z) are
+                    // discarded by the select
+                    const Tp t = FULL ? (vv * dev_log(vv / zz) - vv) : (-vv * dev_log(zz));
+                    run[c] += pos ? zz + t : zz;
                 }
             }
 #pragma unroll

@@ -201,6 +201,8 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["dna", "reference"], default="dna")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched"], default="plain_large")
     ap.add_argument("--dtype", choices=["f32", "f64", "bf16"], default="f32")
+    ap.add_argument("--engine", choices=["auto", "simt", "tensor"], default=None,
+                    help="default: tensor for f32 with R <= 128 (split bf16 products), else auto")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work")
     ap.add_argument("--ref-cols", type=int, default=512)
@@ -239,8 +241,14 @@ def main(argv=None):
     N, T, R = spec["N"], spec["T"], spec["R"]
     dev = torch.device("cuda", local)
     peaks = measured_peaks()
+    if args.engine is None:
+        args.engine = "tensor" if (args.dtype == "f32" and R <= 128) else "auto"
+    engine_name = {"bf16": "tcgen05 (bf16 operands)", "f64": "simt"}.get(
+        args.dtype, "tcgen05 (split bf16 operands, 3 products)" if args.engine == "tensor"
+        else "simt")
 
-    res = measure(dna, torch, dist, prob, args.dtype, args, world, local, peaks, clocks=True)
+    res = measure(dna, torch, dist, prob, args.dtype, args, world, local, peaks, clocks=True,
+                  engine=args.engine)
     line = {
         "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_max"] / args.steps,
@@ -248,7 +256,7 @@ def main(argv=None):
         "data": "synthetic",
         "config": {"workload": args.workload, "desc": spec["desc"], "N": N, "T": T, "R": R,
                    "form": args.dtype.upper(),
-                   "engine": "tcgen05" if args.dtype == "bf16" else "simt",
+                   "engine": engine_name,
                    "l2": "inputs larger than L2 (V is %d MB)" % (N * T * 4 // 2**20),
                    "parallelism": "independent problem per GPU" if world > 1 else "single GPU",
                    "zero_fraction": prob.meta.get("zero_fraction")},
@@ -258,17 +266,26 @@ def main(argv=None):
         "kl_start": res["kl_start"], "kl_end": res["kl_end"],
     }
     if args.dtype == "f32" and not args.no_forms:
-        # the other form on the same workload, and seconds to the FP32 form's target d_KL
+        # the other forms on the same workload, and seconds to the FP32 form's target d_KL
         bf = measure(dna, torch, dist, prob, "bf16", args, world, local, peaks, clocks=False)
         line["bf16_form"] = {"value": bf["value"], "unit": UNIT,
                              "ms_per_step": bf["ms_max"] / args.steps, "roofline": bf["roofline"],
                              "gpu_launches": bf["launches"]}
-        line["time_to_target"] = time_to_target(dna, torch, prob, args.target_iters)
+        if args.engine == "tensor":
+            sargs = argparse.Namespace(**vars(args))
+            sargs.steps = max(3, min(args.steps, 20))
+            sm = measure(dna, torch, dist, prob, "f32", sargs, world, local, peaks, clocks=False,
+                         engine="simt")
+            line["fp32_simt_form"] = {"value": sm["value"], "unit": UNIT, "steps": sargs.steps,
+                                      "ms_per_step": sm["ms_max"] / sargs.steps,
+                                      "roofline": sm["roofline"], "gpu_launches": sm["launches"]}
+        line["time_to_target"] = time_to_target(dna, torch, prob, args.target_iters, args.engine)
 
     if rank == 0 and not args.no_e2e:
         code = {"f32": dna.DNA_F32, "f64": dna.DNA_F64, "bf16": dna.DNA_BF16}[args.dtype]
         tdt = torch.float64 if args.dtype == "f64" else torch.float32
-        line["e2e"] = e2e_measure(dna, torch, prob, code, tdt, N, T, R, args.e2e_steps)
+        line["e2e"] = e2e_measure(dna, torch, prob, code, tdt, N, T, R, args.e2e_steps,
+                                  engine_code(dna, args.engine))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cols = 1024
         it, el = oracle_rate(prob, cols, args.cpu_budget)
@@ -283,27 +300,35 @@ def main(argv=None):
     return 0
 
 
-def _bind(dna, torch, prob, dtype, dev):
+def engine_code(dna, engine):
+    return {"auto": dna.DNA_ENGINE_AUTO, "simt": dna.DNA_ENGINE_SIMT,
+            "tensor": dna.DNA_ENGINE_TENSOR}[engine or "auto"]
+
+
+def _bind(dna, torch, prob, dtype, dev, engine="auto"):
     code = {"f32": dna.DNA_F32, "f64": dna.DNA_F64, "bf16": dna.DNA_BF16}[dtype]
     tdt = torch.float64 if dtype == "f64" else torch.float32
     V = torch.from_numpy(prob.V).to(dev, tdt)
     W = torch.from_numpy(prob.W).to(dev, tdt)
     H = torch.from_numpy(prob.H).to(dev, tdt)
     N, T = prob.V.shape
-    ctx = dna.dna_create(N, T, prob.W.shape[1], dna.make_opts(dtype=code))
+    if dtype == "bf16":
+        engine = "auto"
+    ctx = dna.dna_create(N, T, prob.W.shape[1],
+                         dna.make_opts(dtype=code, engine=engine_code(dna, engine)))
     dna.dna_set_stream(ctx, torch.cuda.current_stream())
     dna.dna_bind(ctx, V, W, H)
     dna.dna_normalize(ctx, 1)                    # Algorithm 1 step 1
     return ctx, (V, W, H)
 
 
-def measure(dna, torch, dist, prob, dtype, args, world, local, peaks, clocks):
+def measure(dna, torch, dist, prob, dtype, args, world, local, peaks, clocks, engine="auto"):
     """Time args.steps DNA iterations (CUDA events on the library's stream, barriers around,
     max over ranks) with per-phase event timing for the roofline of the dominant kernel."""
     dev = torch.device("cuda", local)
     N, T = prob.V.shape
     R = prob.W.shape[1]
-    ctx, keep = _bind(dna, torch, prob, dtype, dev)
+    ctx, keep = _bind(dna, torch, prob, dtype, dev, engine)
     stream = torch.cuda.current_stream()
     kl_start = dna.dna_kl(ctx)
     for _ in range(args.warmup):
@@ -359,7 +384,23 @@ def measure(dna, torch, dist, prob, dtype, args, world, local, peaks, clocks):
     alg_bytes = 4 * N * T + (8 * R * max(N, T) if dom == "pass1" else 16 * max(N, T))
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    if dtype == "bf16":
+    split = dtype == "f32" and engine == "tensor"
+    if split:
+        # FP32-accurate products from three bf16 products each: the tensor peak available
+        # to them is a third of the bf16 peak.  Executed bf16 work per launch: pass 1 runs
+        # GEMM1 in both its A and B halves (2 x 3 x 2RNT) plus GEMM2/3 (2 x 3 x 2RNT);
+        # pass 2 runs 2 x 3 x 2RNT.
+        bf16_peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
+        fp32_peak = bf16_peak / 3.0
+        executed = (24 if dom == "pass1" else 12) * R * N * T
+        roof = {"bound": "tensor", "achieved": flops / per_launch_s / 1e12, "peak": fp32_peak,
+                "unit": "TFLOP/s",
+                "peak_source": "measured sustained dense bf16 (MEASURED_PEAKS.json) / 3: "
+                               "three bf16 products per FP32-accurate product"}
+        roof["executed_bf16_flops_per_launch"] = executed
+        roof["tensor_frac_executed"] = executed / per_launch_s / 1e12 / bf16_peak
+        roof["hbm_frac"] = alg_bytes / per_launch_s / 1e9 / hbm
+    elif dtype == "bf16":
         tensor_peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
         t_tensor = flops / (tensor_peak * 1e12)
         t_hbm = alg_bytes / (hbm * 1e9)
@@ -380,7 +421,8 @@ def measure(dna, torch, dist, prob, dtype, args, world, local, peaks, clocks):
                                 f"{sm_max:.0f} MHz (max SM clock of measured)")}
     roof["frac"] = roof["achieved"] / roof["peak"] if roof.get("peak") else None
     roof["kernel"] = dom
-    roof["traffic"] = recorded_traffic(dom + ("_tc" if dtype == "bf16" else ""), args.workload)
+    roof["traffic"] = recorded_traffic(dom + ("_tc" if dtype == "bf16" else "_split" if split else ""),
+                                       args.workload)
     roof["algorithmic_flops_per_launch"] = flops
     roof["algorithmic_bytes_per_launch"] = alg_bytes
     roof["launch_ms"] = per_launch_s * 1e3
@@ -393,14 +435,14 @@ def measure(dna, torch, dist, prob, dtype, args, world, local, peaks, clocks):
             "kl_end": kl_end}
 
 
-def time_to_target(dna, torch, prob, iters):
+def time_to_target(dna, torch, prob, iters, engine="auto"):
     """Seconds of DNA iterations (CUDA events, d_KL evaluations excluded) for the FP32 form
     to run `iters` iterations, whose final d_KL is the target, and for the BF16 form to come
     within 1e-2 relative of it (checked every 5 iterations, at most 2 x iters)."""
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
-    out = {"iterations_fp32": iters}
-    ctx, keep = _bind(dna, torch, prob, "f32", dev)
+    out = {"iterations_fp32": iters, "fp32_engine": engine}
+    ctx, keep = _bind(dna, torch, prob, "f32", dev, engine)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
@@ -514,13 +556,13 @@ def run_batched(args, world, rank, local):
     return 0
 
 
-def e2e_measure(dna, torch, prob, code, tdt, N, T, R, steps):
+def e2e_measure(dna, torch, prob, code, tdt, N, T, R, steps, engine=0):
     """Iterations/s through dna_run_host on pinned host buffers: each step copies V, W, H
     in, runs one DNA iteration, and copies W, H and d_KL out."""
     Vh = torch.from_numpy(prob.V).to(tdt).pin_memory()
     Wh = torch.from_numpy(prob.W).to(tdt).pin_memory()
     Hh = torch.from_numpy(prob.H).to(tdt).pin_memory()
-    ctx = dna.dna_create(N, T, R, dna.make_opts(dtype=code))
+    ctx = dna.dna_create(N, T, R, dna.make_opts(dtype=code, engine=engine))
     try:
         dna.dna_set_stream(ctx, torch.cuda.current_stream())
         for _ in range(3):

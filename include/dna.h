@@ -53,7 +53,12 @@ extern "C" {
 #define DNA_BF16 2  /* bfloat16 tensor-core operands, float32 accumulation and masters,
                        float64 per-column cost sums                                      */
 
-/* Engines for the O(NRT) contractions. */
+/* Engines for the O(NRT) contractions.  AUTO: BF16 on the tensor cores, F32 and F64 on
+ * the CUDA cores.  TENSOR with F32 (R <= 128): every float32 operand x is split into
+ * bf16 x_hi = bf16(x) and x_lo = bf16(x - x_hi) and every product is formed as
+ * x_hi y_hi + x_hi y_lo + x_lo y_hi with float32 accumulation (relative error per product
+ * below about 2^-15); dna_step_H_fixed, dna_step_H_adjoint and dna_kl_backward need the
+ * SIMT engine. */
 #define DNA_ENGINE_AUTO   0
 #define DNA_ENGINE_SIMT   1  /* CUDA-core FMA kernels (F64, F32)                          */
 #define DNA_ENGINE_TENSOR 2  /* tcgen05 tensor-core kernels with TMEM accumulators         */

@@ -55,6 +55,8 @@ struct dna_ctx {
     int64_t per1[2] = {0, 0}, per2[2] = {0, 0};
     // tensor-core (BF16) path
     bool tc = false;
+    bool split = false;              // FP32 form on the tensor cores (hi + lo bf16 operands)
+    int64_t plane = 0;               // elements between the hi and lo planes of each operand
     int rp = 0;                      // padded rank
     int64_t pad_o[2] = {0, 0};       // O_pad of the H view (0) and W view (1)
     int64_t pad_s[2] = {0, 0};       // S_pad
@@ -127,13 +129,17 @@ View make_view(const dna_ctx* c, bool wstep) {
 // number of full waves per unit of work (ceil(blocks * splits / slots) / splits) plus the
 // partial sums each split adds (`part_per_split`, relative to the work of one split-free
 // pass) and a small fixed cost per CTA start; each split keeps at least four chunks.
+// max_chunks > 0 caps the chunks one split may accumulate (the split FP32 form: the
+// tensor pipe's float32 accumulation loses a fraction of an ulp per update, so long
+// reductions are cut into partials that are summed with round-to-nearest adds).
 void plan_split(int64_t S, int64_t nblocks_os, int slots, int chunk, int* splits, int64_t* per,
-                double part_per_split = 0.02) {
+                double part_per_split = 0.02, int64_t max_chunks = 0) {
     const int64_t chunks = (S + chunk - 1) / chunk;
-    const int64_t max_sp = std::max<int64_t>(1, std::min<int64_t>(32, chunks / 4));
-    int64_t best = 1;
+    const int64_t min_sp = max_chunks > 0 ? (chunks + max_chunks - 1) / max_chunks : 1;
+    const int64_t max_sp = std::max<int64_t>(min_sp, std::min<int64_t>(32, chunks / 4));
+    int64_t best = min_sp;
     double best_cost = 1e300;
-    for (int64_t sp = 1; sp <= max_sp; ++sp) {
+    for (int64_t sp = min_sp; sp <= max_sp; ++sp) {
         const int64_t waves = (nblocks_os * sp + slots - 1) / slots;
         const double cost = (double)waves / (double)sp + part_per_split * (double)sp +
                             2.0 / (double)chunks * (double)waves;
@@ -143,6 +149,10 @@ void plan_split(int64_t S, int64_t nblocks_os, int slots, int chunk, int* splits
     *per = per_chunks * chunk;
     *splits = (int)((S + *per - 1) / *per);
 }
+
+// Chunks of 64 that one pass-1 CTA of the split FP32 form accumulates in tensor memory
+// (1024 values of s: the accumulation error stays near 1e-6 relative).
+constexpr int64_t SPLIT_MAX_CHUNKS = 16;
 
 template <typename Tp>
 void plan_all(dna_ctx* c) {
@@ -162,9 +172,11 @@ void plan_all(dna_ctx* c) {
             c->pad_s[w] = (Sdim + tch - 1) / tch * tch;
             // partial A, B sums per split relative to V's bytes: 2 R / S
             const double part = 2.0 * (double)c->R / (double)Sdim;
-            const int64_t rblocks = c->rp > 128 ? c->rp / 128 : 1;   // grid y of the K-streamed pass 1
+            // CTA rows per o-block of pass 1: r-blocks of the K-streamed kernels, or the A and
+            // B halves of the split FP32 kernel
+            const int64_t rblocks = c->split ? 2 : (c->rp > 128 ? c->rp / 128 : 1);
             plan_split(Sdim, c->pad_o[w] / tob * rblocks, c->num_sms, tch, &c->tsp1[w],
-                       &c->tper1[w], part);
+                       &c->tper1[w], part, c->split ? SPLIT_MAX_CHUNKS : 0);
             plan_split(Sdim, c->pad_o[w] / tob, c->num_sms, tch, &c->tsp2[w], &c->tper2[w],
                        2.0 / (double)Sdim);
         }
@@ -216,12 +228,17 @@ int alloc_workspace(dna_ctx* c) {
         const int64_t mo = std::max(c->pad_o[0], c->pad_o[1]);
         const int64_t ms = std::max(c->pad_s[0], c->pad_s[1]);
         const size_t b = 2;  // bf16
-        e |= dmalloc(&c->Xk, b * (size_t)(mo * c->rp));
-        e |= dmalloc(&c->Yk, b * (size_t)(ms * c->rp));
-        e |= dmalloc(&c->Ytk, b * (size_t)(ms * c->rp));
-        e |= dmalloc(&c->Y2tk, b * (size_t)(ms * c->rp));
-        e |= dmalloc(&c->Xmk, b * (size_t)(mo * c->rp));
-        e |= dmalloc(&c->Xdk, b * (size_t)(mo * c->rp));
+        // one plane size for every operand buffer, so the lo plane is always `plane` after
+        // the hi plane (a multiple of 128 elements: TMA bases stay 256-byte aligned)
+        c->plane = c->split ? std::max(mo, ms) * c->rp : 0;
+        const size_t np = c->split ? 2 : 1;
+        const int64_t po = c->split ? c->plane : mo * c->rp, ps = c->split ? c->plane : ms * c->rp;
+        e |= dmalloc(&c->Xk, b * np * (size_t)po);
+        e |= dmalloc(&c->Yk, b * np * (size_t)ps);
+        e |= dmalloc(&c->Ytk, b * np * (size_t)ps);
+        e |= dmalloc(&c->Y2tk, b * np * (size_t)ps);
+        e |= dmalloc(&c->Xmk, b * np * (size_t)po);
+        e |= dmalloc(&c->Xdk, b * np * (size_t)po);
     }
     if (e != DNA_OK) return DNA_ERR_ALLOC;
     // the padding columns of the transposed copy of V are read by 16-byte copies: zero them
@@ -269,6 +286,7 @@ dna::TcOperands tc_operands(const dna_ctx* c, int wstep) {
     op.S_pad = c->pad_s[wstep]; op.O_pad = c->pad_o[wstep];
     op.Xk = c->Xk; op.Yk = c->Yk; op.Ytk = c->Ytk; op.Y2tk = c->Y2tk;
     op.Xmk = c->Xmk; op.Xdk = c->Xdk;
+    op.plane = c->plane;
     tc_v(c, wstep, &op.V, &op.vs);
     return op;
 }
@@ -340,13 +358,13 @@ int step_h_adjoint(dna_ctx* c, const Tp* Hk, const uint8_t* choice, const Tp* Hb
 // The operand buffers of half-step w for scale_ops (tensor-core form), else nulls.
 struct OpsOut {
     void *Xk = nullptr, *Yk = nullptr, *Ytk = nullptr, *Y2tk = nullptr;
-    int64_t rp = 0, O_pad = 0, S_pad = 0;
+    int64_t rp = 0, O_pad = 0, S_pad = 0, plane = 0;
 };
 OpsOut ops_out(const dna_ctx* c, int w, bool with_sq) {
     OpsOut o;
     if (!c->tc) return o;
     o.Xk = c->Xk; o.Yk = c->Yk; o.Ytk = c->Ytk; o.Y2tk = with_sq ? c->Y2tk : nullptr;
-    o.rp = c->rp; o.O_pad = c->pad_o[w]; o.S_pad = c->pad_s[w];
+    o.rp = c->rp; o.O_pad = c->pad_o[w]; o.S_pad = c->pad_s[w]; o.plane = c->plane;
     return o;
 }
 
@@ -359,7 +377,7 @@ int prep_step(dna_ctx* c, int w, bool with_sq) {
     const OpsOut o = ops_out(c, w, with_sq);
     int e = phase(c, c->tc ? DNA_PHASE_OPERANDS : DNA_PHASE_SUMS, 1, [&] {
         return S::scale_ops(v, nullptr, false, o.Xk, o.Yk, o.Ytk, o.Y2tk, o.rp, o.O_pad, o.S_pad,
-                            c->gpart, c->stream);
+                            o.plane, c->gpart, c->stream);
     });
     if (e) return e;
     return phase(c, DNA_PHASE_SUMS, 1, [&] {
@@ -389,8 +407,11 @@ int half_step(dna_ctx* c, int w, bool mu_only, bool prepared, bool next) {
     e = phase(c, DNA_PHASE_PASS1, 1, [&] {
         if constexpr (sizeof(Tp) == 4)
             if (tc)
-                return dna::TcBf16::pass1(tc_operands(c, w), c->maps[w], A, B, sp1, c->tper1[w],
-                                          !mu_only, c->status, st);
+                return c->split
+                           ? dna::TcBf16::pass1_split(tc_operands(c, w), c->maps[w], A, B, sp1,
+                                                      c->tper1[w], !mu_only, c->status, st)
+                           : dna::TcBf16::pass1(tc_operands(c, w), c->maps[w], A, B, sp1,
+                                                c->tper1[w], !mu_only, c->status, st);
         return S::pass1(v, A, B, sp1, c->per1[w], !mu_only, c->status, st);
     });
     if (e) return e;
@@ -400,14 +421,17 @@ int half_step(dna_ctx* c, int w, bool mu_only, bool prepared, bool next) {
     }
     e = phase(c, DNA_PHASE_CANDIDATES, 1, [&] {
         return S::cand_fused(v, c->c, A, B, sp1, Xmu, Xdna, c->o.eps, c->o.alpha,
-                             tc ? c->Xmk : nullptr, tc ? c->Xdk : nullptr, c->rp, c->pad_o[w], st);
+                             tc ? c->Xmk : nullptr, tc ? c->Xdk : nullptr, c->rp, c->pad_o[w],
+                             c->plane, st);
     });
     if (e) return e;
     e = phase(c, DNA_PHASE_PASS2, 1, [&] {
         if constexpr (sizeof(Tp) == 4)
             if (tc)
-                return dna::TcBf16::pass2(tc_operands(c, w), c->maps[w], c->dpart, sp2,
-                                          c->tper2[w], c->status, st);
+                return c->split ? dna::TcBf16::pass2_split(tc_operands(c, w), c->maps[w], c->dpart,
+                                                           sp2, c->tper2[w], c->status, st)
+                                : dna::TcBf16::pass2(tc_operands(c, w), c->maps[w], c->dpart,
+                                                     sp2, c->tper2[w], c->status, st);
         return S::pass2(v, Xmu, Xdna, c->dpart, sp2, c->per2[w], c->status, st);
     });
     if (e) return e;
@@ -424,7 +448,7 @@ int half_step(dna_ctx* c, int w, bool mu_only, bool prepared, bool next) {
     if (e) return e;
     if (!next)
         return phase(c, DNA_PHASE_SUMS, 1, [&] {
-            return S::scale_ops(v, c->sig, false, nullptr, nullptr, nullptr, nullptr, 0, 0, 0,
+            return S::scale_ops(v, c->sig, false, nullptr, nullptr, nullptr, nullptr, 0, 0, 0, 0,
                                 nullptr, st);
         });
     // half-step 1 - w sees this step's X as its Y and this step's Y as its X
@@ -433,7 +457,7 @@ int half_step(dna_ctx* c, int w, bool mu_only, bool prepared, bool next) {
     const OpsOut o = ops_out(c, wn, true);
     e = phase(c, DNA_PHASE_SUMS, 1, [&] {
         return S::scale_ops(t, c->sig, true, o.Xk, o.Yk, o.Ytk, o.Y2tk, o.rp, o.O_pad, o.S_pad,
-                            c->gpart, st);
+                            o.plane, c->gpart, st);
     });
     if (e) return e;
     return phase(c, DNA_PHASE_SUMS, 1, [&] {
@@ -575,15 +599,21 @@ int dna_create(int64_t N, int64_t T, int64_t R, const dna_opts* opts, dna_ctx** 
     dna_default_opts(&o);
     if (opts) o = *opts;
     if (!valid_opts(o)) return DNA_ERR_ARG;
-    // Engines: BF16 runs on the tensor cores (R <= 512); F32 and F64 on the CUDA cores.
-    const bool tc = o.dtype == DNA_BF16;
-    if (tc && (o.engine == DNA_ENGINE_SIMT || dna::TcBf16::rank_pad(R) == 0))
+    // Engines: BF16 runs on the tensor cores (R <= 512).  F32 runs on the CUDA cores by
+    // default and on the tensor cores (split hi + lo bf16 operands, R <= 128) when the
+    // tensor engine is asked for.  F64 runs on the CUDA cores.
+    const bool split = o.dtype == DNA_F32 && o.engine == DNA_ENGINE_TENSOR;
+    const bool tc = o.dtype == DNA_BF16 || split;
+    if (o.dtype == DNA_BF16 && (o.engine == DNA_ENGINE_SIMT || dna::TcBf16::rank_pad(R) == 0))
         return DNA_ERR_UNSUPPORTED;
-    if (!tc && o.engine == DNA_ENGINE_TENSOR) return DNA_ERR_UNSUPPORTED;
+    if (split && (dna::TcBf16::rank_pad(R) == 0 || dna::TcBf16::rank_pad(R) > 128))
+        return DNA_ERR_UNSUPPORTED;
+    if (o.dtype == DNA_F64 && o.engine == DNA_ENGINE_TENSOR) return DNA_ERR_UNSUPPORTED;
     dna_ctx* c = new (std::nothrow) dna_ctx();
     if (!c) return DNA_ERR_ALLOC;
     c->N = N; c->T = T; c->R = R; c->o = o;
     c->tc = tc;
+    c->split = split;
     c->rp = tc ? dna::TcBf16::rank_pad(R) : 0;
     c->esz = o.dtype == DNA_F64 ? 8 : 4;
     if (cudaGetDevice(&c->device) != cudaSuccess ||

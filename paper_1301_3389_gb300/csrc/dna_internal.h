@@ -90,7 +90,8 @@ template <typename Tp> struct Simt {
     // with zero padding.
     static int cand_fused(const View& v, const double* c, const Tp* Apart, const Tp* Bpart,
                           int splits, Tp* Xmu, Tp* Xdna, double eps, double alpha, void* Xmk,
-                          void* Xdk, int64_t rp, int64_t O_pad, cudaStream_t st);
+                          void* Xdk, int64_t rp, int64_t O_pad, int64_t plane,
+                          cudaStream_t st);
     // Selection as above, plus fpart[glue_parts(O)][R]: per-block sums of the new X.
     static int select_fused(const View& v, const Tp* Xmu, const Tp* Xdna, const double* dpart,
                             int splits, uint8_t* choice, double* dfin, double* fpart,
@@ -105,7 +106,7 @@ template <typename Tp> struct Simt {
     // per-block sums over s of the (scaled) y(s, r).
     static int scale_ops(const View& t, const double* f, bool xmul, void* Xk, void* Yk,
                          void* Ytk, void* Y2tk, int64_t rp, int64_t O_pad, int64_t S_pad,
-                         double* cpart, cudaStream_t st);
+                         int64_t plane, double* cpart, cudaStream_t st);
     static int64_t glue_parts(int64_t n);   // partial sums per R of the fused glue
     // one-time: row and column sums of V (float64) and the transposed copy
     static int prepare_v(const Tp* V, int64_t N, int64_t T, int64_t ldv, Tp* Vt, int64_t ldvt,
@@ -131,11 +132,15 @@ struct TcOperands {
     const void* Xdk;
     const float* V;     // V_so as the passes read it, element (s, o) at V[s * vs + o]
     int64_t vs;
+    // FP32 form on the tensor cores: every operand buffer holds a hi plane and, `plane`
+    // elements after it, a lo plane (x = hi + lo, both bf16); 0 in the BF16 form
+    int64_t plane;
 };
 
 // TMA descriptors of one half-step view (built once per bound problem).
 struct TcMaps {
     CUtensorMap x, y, yt, y2t, v, xm, xd;
+    CUtensorMap y_l, yt_l, y2t_l;   // lo planes (FP32 form on the tensor cores)
 };
 
 struct TcBf16 {
@@ -156,6 +161,14 @@ struct TcBf16 {
                      int splits, int64_t s_per, bool with_b, int* status, cudaStream_t st);
     static int pass2(const TcOperands& op, const TcMaps& maps, double* dpart, int splits,
                      int64_t s_per, int* status, cudaStream_t st);
+    // The FP32 form on the tensor cores (tc_split.cu): the same passes with every operand
+    // split into hi + lo bf16 planes and three MMAs per product.  Pass 1 runs 2 x splits
+    // CTA rows (A and B accumulated by separate CTAs; with_b = false: A only).
+    static int pass1_split(const TcOperands& op, const TcMaps& maps, float* Apart,
+                           float* Bpart, int splits, int64_t s_per, bool with_b, int* status,
+                           cudaStream_t st);
+    static int pass2_split(const TcOperands& op, const TcMaps& maps, double* dpart, int splits,
+                           int64_t s_per, int* status, cudaStream_t st);
     static int chunk();
     static int oblock();
 };

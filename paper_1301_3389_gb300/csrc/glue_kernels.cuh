@@ -28,6 +28,14 @@ __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
     __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<uint32_t*>(&v);
 }
+// the two bf16 halves of a pack2 word as float32
+__device__ __forceinline__ float lo_half(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float hi_half(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+// bf16(x) and bf16(x - bf16(x))
+__device__ __forceinline__ void split1(float x, bf16& h, bf16& l) {
+    h = __float2bfloat16_rn(x);
+    l = __float2bfloat16_rn(x - __bfloat162float(h));
+}
 
 // Dynamic shared memory of k_cand_fused: red; cs, ics [R]; sc; xs, ms [R][TO + 1].
 template <typename Tp>
@@ -44,7 +52,8 @@ __global__ void __launch_bounds__(1024) k_cand_fused(View v, const double* __res
                                                     const Tp* __restrict__ Bpart, int splits,
                                                     Tp* __restrict__ Xmu, Tp* __restrict__ Xdna,
                                                     Tp eps, Tp alpha, bf16* __restrict__ Xmk,
-                                                    bf16* __restrict__ Xdk, int64_t rp) {
+                                                    bf16* __restrict__ Xdk, int64_t rp,
+                                                    int64_t plane) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int64_t R = v.R, O = v.O;
     double* red = reinterpret_cast<double*>(smem_raw);            // [TY][TO]
@@ -144,8 +153,15 @@ __global__ void __launch_bounds__(1024) k_cand_fused(View v, const double* __res
                     m1 = (float)ms[(r + 1) * (TO + 1) + i];
                     d1 = (float)xs[(r + 1) * (TO + 1) + i];
                 }
-                *reinterpret_cast<uint32_t*>(Xmk + oi * rp + r) = pack2(m0, m1);
-                *reinterpret_cast<uint32_t*>(Xdk + oi * rp + r) = pack2(d0, d1);
+                const uint32_t mh = pack2(m0, m1), dh = pack2(d0, d1);
+                *reinterpret_cast<uint32_t*>(Xmk + oi * rp + r) = mh;
+                *reinterpret_cast<uint32_t*>(Xdk + oi * rp + r) = dh;
+                if (plane) {   // lo planes: x - bf16(x)
+                    *reinterpret_cast<uint32_t*>(Xmk + plane + oi * rp + r) =
+                        pack2(m0 - lo_half(mh), m1 - hi_half(mh));
+                    *reinterpret_cast<uint32_t*>(Xdk + plane + oi * rp + r) =
+                        pack2(d0 - lo_half(dh), d1 - hi_half(dh));
+                }
             }
         }
     }
@@ -232,6 +248,7 @@ struct OpsArgs {
     bf16* Ytk;         // [rp][S_pad]
     bf16* Y2tk;        // [rp][S_pad], or null
     int64_t rp, O_pad, S_pad;
+    int64_t plane;     // > 0: also write lo planes (x - bf16(x)) `plane` elements after each
     double* cpart;     // [ceil(S / 32)][R] partial sums over s of the (scaled) y(s, r), or null
     int64_t xtiles_o, tiles_r, xtiles;   // X tiles: xtiles_o x tiles_r; then the Y tiles
 };
@@ -295,17 +312,35 @@ __global__ void __launch_bounds__(256) k_scale_ops(OpsArgs a) {
         if (isx) {   // Xk[o][r]: lanes walk r
             for (int k = ty; k < TO; k += 8) {
                 const int64_t i = i0 + k, r = r0 + tx;
-                if (i < a.O_pad && r < a.rp) a.Xk[i * a.rp + r] = __float2bfloat16_rn(tile[tx][k]);
+                if (i < a.O_pad && r < a.rp) {
+                    bf16 h, l;
+                    split1(tile[tx][k], h, l);
+                    a.Xk[i * a.rp + r] = h;
+                    if (a.plane) a.Xk[a.plane + i * a.rp + r] = l;
+                }
             }
         } else {
             for (int k = ty; k < TO; k += 8) {
                 const int64_t i = i0 + k, r = r0 + tx;   // Yk[s][r]: lanes walk r
-                if (i < a.S_pad && r < a.rp) a.Yk[i * a.rp + r] = __float2bfloat16_rn(tile[tx][k]);
+                if (i < a.S_pad && r < a.rp) {
+                    bf16 h, l;
+                    split1(tile[tx][k], h, l);
+                    a.Yk[i * a.rp + r] = h;
+                    if (a.plane) a.Yk[a.plane + i * a.rp + r] = l;
+                }
                 const int64_t r2 = r0 + k, i2 = i0 + tx;  // Ytk[r][s]: lanes walk s
                 if (i2 < a.S_pad && r2 < a.rp) {
                     const float y = tile[k][tx];
-                    a.Ytk[r2 * a.S_pad + i2] = __float2bfloat16_rn(y);
-                    if (a.Y2tk) a.Y2tk[r2 * a.S_pad + i2] = __float2bfloat16_rn(y * y);
+                    const int64_t at = r2 * a.S_pad + i2;
+                    bf16 h, l;
+                    split1(y, h, l);
+                    a.Ytk[at] = h;
+                    if (a.plane) a.Ytk[a.plane + at] = l;
+                    if (a.Y2tk) {
+                        split1(y * y, h, l);
+                        a.Y2tk[at] = h;
+                        if (a.plane) a.Y2tk[a.plane + at] = l;
+                    }
                 }
             }
         }

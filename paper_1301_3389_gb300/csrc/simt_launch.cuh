@@ -264,7 +264,7 @@ int64_t Simt<Tp>::glue_parts(int64_t n) { return (n + glue::TO - 1) / glue::TO; 
 template <typename Tp>
 int Simt<Tp>::cand_fused(const View& v, const double* c, const Tp* A, const Tp* B, int splits,
                          Tp* Xmu, Tp* Xdna, double eps, double alpha, void* Xmk, void* Xdk,
-                         int64_t rp, int64_t O_pad, cudaStream_t st) {
+                         int64_t rp, int64_t O_pad, int64_t plane, cudaStream_t st) {
     const bool bf = Xmk != nullptr;
     if (bf && (sizeof(Tp) != 4 || !Xdk || rp < v.R || rp % 2 != 0 || O_pad < v.O))
         return DNA_ERR_ARG;
@@ -276,13 +276,13 @@ int Simt<Tp>::cand_fused(const View& v, const double* c, const Tp* A, const Tp* 
             if (simt::prep_smem(k, smem)) return DNA_ERR_CUDA;
             k<<<grid, dim3(32, glue::TY), smem, st>>>(v, c, A, B, splits, Xmu, Xdna, (Tp)eps, (Tp)alpha,
                                                static_cast<glue::bf16*>(Xmk),
-                                               static_cast<glue::bf16*>(Xdk), rp);
+                                               static_cast<glue::bf16*>(Xdk), rp, plane);
         }
     } else {
         auto k = glue::k_cand_fused<Tp, false>;
         if (simt::prep_smem(k, smem)) return DNA_ERR_CUDA;
         k<<<grid, dim3(32, glue::TY), smem, st>>>(v, c, A, B, splits, Xmu, Xdna, (Tp)eps, (Tp)alpha,
-                                           nullptr, nullptr, 0);
+                                           nullptr, nullptr, 0, 0);
     }
     return simt::launch_status();
 }
@@ -309,8 +309,8 @@ int Simt<Tp>::part_sums(const double* part, int64_t nparts, int64_t R, double re
 
 template <typename Tp>
 int Simt<Tp>::scale_ops(const View& t, const double* f, bool xmul, void* Xk, void* Yk, void* Ytk,
-                        void* Y2tk, int64_t rp, int64_t O_pad, int64_t S_pad, double* cpart,
-                        cudaStream_t st) {
+                        void* Y2tk, int64_t rp, int64_t O_pad, int64_t S_pad, int64_t plane,
+                        double* cpart, cudaStream_t st) {
     const bool bf = Xk != nullptr;
     if (bf && (sizeof(Tp) != 4 || !Yk || !Ytk || rp < t.R || O_pad < t.O || S_pad < t.S))
         return DNA_ERR_ARG;
@@ -320,7 +320,7 @@ int Simt<Tp>::scale_ops(const View& t, const double* f, bool xmul, void* Xk, voi
     a.R = t.R; a.f = f; a.xmul = xmul;
     a.Xk = static_cast<glue::bf16*>(Xk); a.Yk = static_cast<glue::bf16*>(Yk);
     a.Ytk = static_cast<glue::bf16*>(Ytk); a.Y2tk = static_cast<glue::bf16*>(Y2tk);
-    a.rp = rp; a.O_pad = O_pad; a.S_pad = S_pad; a.cpart = cpart;
+    a.rp = rp; a.O_pad = O_pad; a.S_pad = S_pad; a.plane = bf ? plane : 0; a.cpart = cpart;
     const int64_t rcov = bf ? rp : t.R, ocov = bf ? O_pad : t.O, scov = bf ? S_pad : t.S;
     a.tiles_r = glue_parts(rcov);
     // without scaling and operands the X tiles have nothing to do

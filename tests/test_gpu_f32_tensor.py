@@ -1,0 +1,67 @@
+"""The FP32 form on the tensor cores (DNA_ENGINE_TENSOR with DNA_F32): every float32
+operand is split into bf16 hi + lo planes and every product is x_hi y_hi + x_hi y_lo +
+x_lo y_hi with float32 accumulation.  Held to the FP32 form's tolerances against the FP64
+oracle (W, H within 1e-4 relative per half-step).  The trajectory, final-d_KL, ragged-size
+and regularised checks are in test_gpu_parity.py and the bench-size sampled check in
+test_gpu_fullsize.py, parametrised over the CUDA-core and tensor-core FP32 forms.
+"""
+import numpy as np
+import pytest
+
+import workloads
+from gpu_helpers import GpuProblem, rel_fro, step_pair
+from oracle import dna as o
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(64, 128, 8), (300, 500, 100), (257, 300, 128), (640, 130, 64), (129, 257, 33)]
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(map(str, s)))
+def test_split_half_steps(shape):
+    """Two DNA iterations from the oracle's state: each half-step within 1e-4 relative."""
+    N, T, R = shape
+    p = workloads.custom(N, T, R, seed=N + 5 * T + 11 * R)
+    with GpuProblem(p.V, p.W, p.H, "f32t") as gp:
+        gp.dna.dna_normalize(gp.ctx, 1)
+        W, H = o.normalize_w_columns(p.W, p.H)
+        worst = 0.0
+        for _ in range(2):
+            for which in (0, 1):
+                W, H, _ = step_pair(gp, W, H, which)
+                Wg, Hg = gp.WH()
+                worst = max(worst, rel_fro(Wg, W), rel_fro(Hg, H))
+        print(f"\n{shape}: worst W/H error over 2 iterations {worst:.2e}")
+        assert worst < 1e-4
+
+
+def test_split_unsupported_rank():
+    import paper_1301_3389_gb300 as dna
+    with pytest.raises(dna.DNAError) as e:
+        dna.dna_create(64, 64, 200, dna.make_opts(dtype=dna.DNA_F32, engine=dna.DNA_ENGINE_TENSOR))
+    assert e.value.code == dna.DNA_ERR_UNSUPPORTED
+
+
+def test_split_unaligned_leading_dimension():
+    """V with a leading dimension that is not a multiple of 4 floats (aligned copy)."""
+    import torch
+    p = workloads.custom(90, 150, 12, seed=17)
+    V = np.zeros((90, 153), dtype=np.float32)
+    V[:, :150] = p.V
+    with GpuProblem(p.V, p.W, p.H, "f32t") as ref:
+        ref.dna.dna_iterate(ref.ctx, 2)
+        Wr, Hr = ref.WH()
+    import paper_1301_3389_gb300 as dna
+    Vd = torch.from_numpy(V).cuda()
+    Wd = torch.from_numpy(p.W).cuda()
+    Hd = torch.from_numpy(p.H).cuda()
+    ctx = dna.dna_create(90, 150, 12, dna.make_opts(dtype=dna.DNA_F32, engine=dna.DNA_ENGINE_TENSOR))
+    try:
+        dna.dna_set_stream(ctx)
+        dna.dna_bind(ctx, Vd, Wd, Hd, ldv=153)
+        dna.dna_iterate(ctx, 2)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(Wd.cpu().numpy(), Wr.astype(np.float32))
+        np.testing.assert_array_equal(Hd.cpu().numpy(), Hr.astype(np.float32))
+    finally:
+        dna.dna_destroy(ctx)

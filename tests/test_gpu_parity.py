@@ -2,6 +2,8 @@
 
 Tolerances: FP32 form, W and H within 1e-4 relative (Frobenius) after each of the
 first 5 iterations and final d_KL within 1e-3 relative after 50; FP64 form, 1e-10.
+The FP32 form runs on the CUDA cores ("f32") and on the tensor cores with split hi + lo
+bf16 operands ("f32t"), both held to the FP32 tolerances.
 Selections may differ only at near ties (gpu_helpers.NEAR_TIE); the oracle then
 replays the GPU's choice so rounding near a tie cannot grow into a different
 trajectory.
@@ -15,7 +17,7 @@ from oracle import dna as o
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f32": 1e-4, "f64": 1e-10}
+TOL = {"f32": 1e-4, "f32t": 1e-4, "f64": 1e-10}
 
 
 def _trajectory(p, kind, iters, mu=False, **opts):
@@ -41,18 +43,18 @@ def _trajectory(p, kind, iters, mu=False, **opts):
     return flips
 
 
-@pytest.mark.parametrize("kind", ["f32", "f64"])
+@pytest.mark.parametrize("kind", ["f32", "f32t", "f64"])
 def test_plain_small_first_iterations(kind):
     """N=256 T=512 R=16: W and H after each of the first 5 DNA iterations."""
     _trajectory(workloads.plain_small(0), kind, 5)
 
 
-@pytest.mark.parametrize("kind", ["f32", "f64"])
+@pytest.mark.parametrize("kind", ["f32", "f32t", "f64"])
 def test_plain_small_mu_iterations(kind):
     _trajectory(workloads.plain_small(1), kind, 5, mu=True)
 
 
-@pytest.mark.parametrize("kind", ["f32", "f64"])
+@pytest.mark.parametrize("kind", ["f32", "f32t", "f64"])
 def test_plain_small_final_kl_free_running(kind):
     """50 free-running DNA iterations: final d_KL within 1e-3 relative (FP32)."""
     p = workloads.plain_small(0)
@@ -67,7 +69,7 @@ def test_plain_small_final_kl_free_running(kind):
             kl = gp.dna.dna_kl(gp.ctx)
             assert kl <= prev * (1 + 1e-6), (kl, prev)      # non-increasing (Section 2.4)
             prev = kl
-    tol = 1e-3 if kind == "f32" else 1e-9
+    tol = 1e-3 if kind in ("f32", "f32t") else 1e-9
     assert abs(prev - costs[-1]) <= tol * costs[-1], (prev, costs[-1])
 
 
@@ -75,16 +77,19 @@ SHAPES = [(1, 1, 1), (3, 5, 2), (67, 131, 17), (130, 70, 33), (129, 200, 64),
           (200, 300, 129), (65, 129, 300), (40, 70, 512), (70, 513, 8)]
 
 
-@pytest.mark.parametrize("kind", ["f32", "f64"])
+@pytest.mark.parametrize("kind", ["f32", "f32t", "f64"])
 @pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(map(str, s)))
 def test_ragged_shapes(shape, kind):
-    """Odd sizes: several tiles plus ragged tails in N, T and R (R up to 512)."""
+    """Odd sizes: several tiles plus ragged tails in N, T and R (R up to 512; the
+    tensor-core FP32 form takes R up to 128)."""
     N, T, R = shape
+    if kind == "f32t" and R > 128:
+        pytest.skip("the split FP32 tensor-core form takes R <= 128")
     p = workloads.custom(N, T, R, seed=N * 7 + T * 3 + R)
     _trajectory(p, kind, 2)
 
 
-@pytest.mark.parametrize("kind", ["f32", "f64"])
+@pytest.mark.parametrize("kind", ["f32", "f32t", "f64"])
 def test_regularised_and_limits(kind):
     """lambda, rho > 0 and non-default eps, alpha (eq. 2, Section 2.3)."""
     p = workloads.custom(90, 150, 12, seed=5)
@@ -113,7 +118,7 @@ def test_zero_rows_and_columns():
     _ = _trajectory(workloads.Problem("z", V, p.W0, p.H0, p.W, p.H, 0), "f64", 2)
 
 
-@pytest.mark.parametrize("kind", ["f32", "bf16"])
+@pytest.mark.parametrize("kind", ["f32", "f32t", "bf16"])
 @pytest.mark.parametrize("fault", ["zero_w", "nan_h"])
 def test_nonfinite_reported(kind, fault):
     """z = 0 where v > 0 (a zero factor) or a NaN entry is reported as DNA_ERR_NONFINITE

@@ -300,6 +300,19 @@ def main(argv=None):
     return 0
 
 
+def max_over_ranks(torch, dist, x: float, device) -> float:
+    """The largest of the ranks' values of x (the slowest rank's time)."""
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, steps: int, ms_max: float) -> float:
+    """Whole-job iterations per second: every rank runs `steps` iterations of its own
+    problem, and the job takes as long as the slowest rank."""
+    return world * steps / (ms_max / 1e3)
+
+
 def engine_code(dna, engine):
     return {"auto": dna.DNA_ENGINE_AUTO, "simt": dna.DNA_ENGINE_SIMT,
             "tensor": dna.DNA_ENGINE_TENSOR}[engine or "auto"]
@@ -369,12 +382,8 @@ def measure(dna, torch, dist, prob, dtype, args, world, local, peaks, clocks, en
     kl_end = dna.dna_kl(ctx)
     dna.dna_destroy(ctx)
     del keep
-    ms_max = ms
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = world * args.steps / (ms_max / 1e3)
+    ms_max = max_over_ranks(torch, dist, ms, dev) if world > 1 else ms
+    value = job_rate(world, args.steps, ms_max)
 
     # roofline of the dominant kernel (largest share of the timed region)
     dom = max(("pass1", "pass2"), key=lambda p: phases[p][0])
@@ -517,13 +526,10 @@ def run_batched(args, world, rank, local):
     kl1 = dna.dna_group_kl(g, len(probs))
     launches = dna.dna_group_launches_per_iteration(g) * args.steps
     dna.dna_group_destroy(g)
-    ms_max = ms
+    ms_max = max_over_ranks(torch, dist, ms, dev) if world > 1 else ms
     if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
         dist.destroy_process_group()
-    value = world * args.steps / (ms_max / 1e3)
+    value = job_rate(world, args.steps, ms_max)
     nt = sum(s[0] * s[1] for s in shapes)
     alg_bytes = 4 * 4 * nt          # V read by both passes of both half-steps, float32
     flops = sum(20 * s[2] * s[0] * s[1] for s in shapes)   # 10 R flop per element per half-step

@@ -89,6 +89,7 @@ __global__ void __launch_bounds__(1024) k_cand_fused(View v, const double* __res
 #pragma unroll
         for (int u = 0; u < UNR; ++u) { ra[u] = Tp(0); rb[u] = Tp(0); }
         if (live) {
+#pragma unroll 4
             for (int sp = 0; sp < splits; ++sp) {
 #pragma unroll
                 for (int u = 0; u < UNR; ++u) {
@@ -127,10 +128,14 @@ __global__ void __launch_bounds__(1024) k_cand_fused(View v, const double* __res
     }
     red[ty * TO + tx] = (double)den;
     __syncthreads();
-    if (ty == 0) {
-        double tot = 0.0;
-        for (int k = 0; k < TY; ++k) tot += red[k * TO + tx];
-        scl[tx] = live ? (Tp)(tot > 0.0 ? v.vsum[o] / tot : 1.0) : Tp(0);   // eq. 10
+    {   // warp ty sums column ty's TY partials with a fixed butterfly
+        const int col = ty;
+        double tot = red[tx * TO + col];
+#pragma unroll
+        for (int m = 16; m > 0; m >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, m);
+        const int64_t oc = o0 + col;
+        if (tx == 0)
+            scl[col] = oc < O ? (Tp)(tot > 0.0 ? v.vsum[oc] / tot : 1.0) : Tp(0);   // eq. 10
     }
     __syncthreads();
     const Tp sc = scl[tx];

@@ -92,6 +92,8 @@ template <typename Tp> struct Simt {
                           int splits, Tp* Xmu, Tp* Xdna, double eps, double alpha, void* Xmk,
                           void* Xdk, int64_t rp, int64_t O_pad, int64_t plane,
                           cudaStream_t st);
+    // A[0] = sum over the splits of A[sp] (and B, if given), each [R][O]: ascending order.
+    static int split_sum(Tp* A, Tp* B, int64_t R, int64_t O, int splits, cudaStream_t st);
     // Selection as above, plus fpart[glue_parts(O)][R]: per-block sums of the new X.
     static int select_fused(const View& v, const Tp* Xmu, const Tp* Xdna, const double* dpart,
                             int splits, uint8_t* choice, double* dfin, double* fpart,

@@ -37,11 +37,10 @@ __device__ __forceinline__ void split1(float x, bf16& h, bf16& l) {
     l = __float2bfloat16_rn(x - __bfloat162float(h));
 }
 
-// Dynamic shared memory of k_cand_fused: red; cs, ics [R]; sc; xs, ms [R][TO + 1].
+// Dynamic shared memory of k_cand_fused: red [TY][TO]; cs, ics [R]; sc; xs, ms [R][TO + 1].
 template <typename Tp>
 constexpr size_t cand_smem(int64_t R, bool bf) {
-    return sizeof(Tp) * (2 * (size_t)R + (bf ? 2 : 1) * (size_t)R * (TO + 1) + TO) +
-           sizeof(double) * TY * TO;
+    return sizeof(Tp) * (2 * (size_t)R + (bf ? 2 : 1) * (size_t)R * (TO + 1) + TO + TY * TO);
 }
 
 // CTA = 32 columns o (threadIdx.x) x 32 groups of r (threadIdx.y); grid covers O (or O_pad
@@ -56,8 +55,8 @@ __global__ void __launch_bounds__(1024) k_cand_fused(View v, const double* __res
                                                     int64_t plane) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int64_t R = v.R, O = v.O;
-    double* red = reinterpret_cast<double*>(smem_raw);            // [TY][TO]
-    Tp* cs = reinterpret_cast<Tp*>(red + TY * TO);                // [R]
+    Tp* red = reinterpret_cast<Tp*>(smem_raw);                    // [TY][TO]
+    Tp* cs = red + TY * TO;                                       // [R]
     Tp* ics = cs + R;                                             // [R]
     Tp* scl = ics + R;                                            // [TO]
     Tp* xs = scl + TO;                                            // [R][TO + 1]: x, then x_dna
@@ -126,16 +125,17 @@ __global__ void __launch_bounds__(1024) k_cand_fused(View v, const double* __res
             den += cs[r] * xd;
         }
     }
-    red[ty * TO + tx] = (double)den;
+    red[ty * TO + tx] = den;
     __syncthreads();
-    {   // warp ty sums column ty's TY partials with a fixed butterfly
+    {   // warp ty sums column ty's TY partials with a fixed butterfly (in the element
+        // type: float64 arithmetic is slow on this GPU)
         const int col = ty;
-        double tot = red[tx * TO + col];
+        Tp tot = red[tx * TO + col];
 #pragma unroll
         for (int m = 16; m > 0; m >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, m);
         const int64_t oc = o0 + col;
         if (tx == 0)
-            scl[col] = oc < O ? (Tp)(tot > 0.0 ? v.vsum[oc] / tot : 1.0) : Tp(0);   // eq. 10
+            scl[col] = oc < O ? (tot > Tp(0) ? (Tp)v.vsum[oc] / tot : Tp(1)) : Tp(0);   // eq. 10
     }
     __syncthreads();
     const Tp sc = scl[tx];
@@ -168,6 +168,46 @@ __global__ void __launch_bounds__(1024) k_cand_fused(View v, const double* __res
                         pack2(d0 - lo_half(dh), d1 - hi_half(dh));
                 }
             }
+        }
+    }
+}
+
+// A[0][i] = A[0][i] + A[1][i] + ... + A[splits-1][i] (ascending, the order the candidates
+// kernel uses, so results are unchanged), and the same for B (may be null): the split
+// partials of pass 1 streamed once with wide loads before the candidates read them.
+template <typename Tp>
+__global__ void __launch_bounds__(256) k_split_sum(Tp* __restrict__ A, Tp* __restrict__ B,
+                                                   int64_t n, int splits) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    if constexpr (sizeof(Tp) == 4) {
+        if (n % 4 == 0) {   // float4 path (slots are 16-byte aligned when n % 4 == 0)
+            const int64_t n4 = n / 4;
+            for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+#pragma unroll
+                for (int m = 0; m < 2; ++m) {
+                    float4* M = reinterpret_cast<float4*>(m ? B : A);
+                    if (!M) continue;
+                    float4 acc = M[i];
+#pragma unroll 4
+                    for (int sp = 1; sp < splits; ++sp) {
+                        const float4 t = M[(int64_t)sp * n4 + i];
+                        acc.x += t.x; acc.y += t.y; acc.z += t.z; acc.w += t.w;
+                    }
+                    M[i] = acc;
+                }
+            }
+            return;
+        }
+    }
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+            Tp* M = m ? B : A;
+            if (!M) continue;
+            Tp acc = M[i];
+#pragma unroll 4
+            for (int sp = 1; sp < splits; ++sp) acc += M[(int64_t)sp * n + i];
+            M[i] = acc;
         }
     }
 }

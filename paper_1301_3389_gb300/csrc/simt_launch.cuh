@@ -288,6 +288,16 @@ int Simt<Tp>::cand_fused(const View& v, const double* c, const Tp* A, const Tp* 
 }
 
 template <typename Tp>
+int Simt<Tp>::split_sum(Tp* A, Tp* B, int64_t R, int64_t O, int splits, cudaStream_t st) {
+    if (splits <= 1) return DNA_OK;
+    const int64_t n = R * O;
+    const int64_t work = (sizeof(Tp) == 4 && n % 4 == 0) ? n / 4 : n;
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, 152 * 8));
+    glue::k_split_sum<Tp><<<(unsigned)blocks, 256, 0, st>>>(A, B, n, splits);
+    return simt::launch_status();
+}
+
+template <typename Tp>
 int Simt<Tp>::select_fused(const View& v, const Tp* Xmu, const Tp* Xdna, const double* dpart,
                            int splits, uint8_t* choice, double* dfin, double* fpart,
                            cudaStream_t st) {

@@ -792,20 +792,28 @@ __global__ void k_colsum_part(const Tp* __restrict__ M, int64_t n, int64_t R, in
     }
 }
 
-// out[r] = sum over splits of part[split][r] + reg, zero sum guarded.  One warp per r:
-// lane l adds splits l, l + 32, ...; then a fixed butterfly over the lanes.
+// out[r] = sum over splits of part[split][r] + reg, zero sum guarded.  CTA = 32 values of
+// r (lanes, so loads coalesce) x 32 groups of splits: group g adds splits g, g + 32, ... in
+// order, then the 32 group sums are added in order.
 template <int UNUSED = 0>
-__global__ void k_colsum_final(const double* __restrict__ part, int nsplit, int64_t R, double reg,
-                               double* __restrict__ out, bool guard) {
-    const int64_t r = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-    const int lane = threadIdx.x & 31;
-    if (r >= R) return;
+__global__ void __launch_bounds__(1024) k_colsum_final(const double* __restrict__ part,
+                                                       int nsplit, int64_t R, double reg,
+                                                       double* __restrict__ out, bool guard) {
+    __shared__ double red[32][33];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int64_t r = (int64_t)blockIdx.x * 32 + tx;
     double t = 0.0;
-#pragma unroll 8
-    for (int k = lane; k < nsplit; k += 32) t += part[(int64_t)k * R + r];
-#pragma unroll
-    for (int m = 16; m > 0; m >>= 1) t += __shfl_xor_sync(0xffffffffu, t, m);
-    if (lane == 0) out[r] = nonzero_sum(t + reg, guard);
+    if (r < R) {
+#pragma unroll 4
+        for (int k = ty; k < nsplit; k += 32) t += part[(int64_t)k * R + r];
+    }
+    red[ty][tx] = t;
+    __syncthreads();
+    if (ty == 0 && r < R) {
+        double tot = 0.0;
+        for (int g = 0; g < 32; ++g) tot += red[g][tx];
+        out[r] = nonzero_sum(tot + reg, guard);
+    }
 }
 
 // Row-sum variant for unit-stride rows (element (r, i) at M[r * ld + i]): one CTA of 256

@@ -109,7 +109,8 @@ int factor_sums(const Tp* M, int64_t n, int64_t R, int64_t si, int64_t sr, doubl
     dim3 grid((unsigned)((R + 31) / 32), (unsigned)nsplit);
     k_colsum_part<Tp><<<grid, blk, 0, st>>>(M, n, R, si, sr, rows_per, work);
     if (launch_status()) return DNA_ERR_CUDA;
-    k_colsum_final<<<(unsigned)((R + 7) / 8), 256, 0, st>>>(work, (int)nsplit, R, reg, out, true);
+    k_colsum_final<<<(unsigned)((R + 31) / 32), dim3(32, 32), 0, st>>>(work, (int)nsplit, R, reg, out,
+                                                                      true);
     return launch_status();
 }
 }  // namespace simt
@@ -312,7 +313,7 @@ int Simt<Tp>::select_fused(const View& v, const Tp* Xmu, const Tp* Xdna, const d
 template <typename Tp>
 int Simt<Tp>::part_sums(const double* part, int64_t nparts, int64_t R, double reg, double* out,
                         cudaStream_t st) {
-    simt::k_colsum_final<<<(unsigned)((R + 7) / 8), 256, 0, st>>>(part, (int)nparts, R, reg, out,
+    simt::k_colsum_final<<<(unsigned)((R + 31) / 32), dim3(32, 32), 0, st>>>(part, (int)nparts, R, reg, out,
                                                                   true);
     return simt::launch_status();
 }

@@ -150,9 +150,10 @@ void plan_split(int64_t S, int64_t nblocks_os, int slots, int chunk, int* splits
     *splits = (int)((S + *per - 1) / *per);
 }
 
-// Chunks of 64 that one pass-1 CTA of the split FP32 form accumulates in tensor memory
+// Chunks of 128 that one pass-1 CTA of the split FP32 form accumulates in tensor memory
 // (1024 values of s: the accumulation error stays near 1e-6 relative).
-constexpr int64_t SPLIT_MAX_CHUNKS = 16;
+constexpr int64_t SPLIT_CHUNK = 128;
+constexpr int64_t SPLIT_MAX_CHUNKS = 8;
 
 template <typename Tp>
 void plan_all(dna_ctx* c) {
@@ -175,10 +176,13 @@ void plan_all(dna_ctx* c) {
             // CTA rows per o-block of pass 1: r-blocks of the K-streamed kernels, or the A and
             // B halves of the split FP32 kernel
             const int64_t rblocks = c->split ? 2 : (c->rp > 128 ? c->rp / 128 : 1);
-            plan_split(Sdim, c->pad_o[w] / tob * rblocks, c->num_sms, tch, &c->tsp1[w],
+            // the split form streams s in chunks of 128 and runs pass 2 as one CTA per
+            // candidate
+            const int sch = c->split ? (int)SPLIT_CHUNK : tch;
+            plan_split(Sdim, c->pad_o[w] / tob * rblocks, c->num_sms, sch, &c->tsp1[w],
                        &c->tper1[w], part, c->split ? SPLIT_MAX_CHUNKS : 0);
-            plan_split(Sdim, c->pad_o[w] / tob, c->num_sms, tch, &c->tsp2[w], &c->tper2[w],
-                       2.0 / (double)Sdim);
+            plan_split(Sdim, c->pad_o[w] / tob * (c->split ? 2 : 1), c->num_sms, sch,
+                       &c->tsp2[w], &c->tper2[w], 2.0 / (double)Sdim);
         }
     }
 }

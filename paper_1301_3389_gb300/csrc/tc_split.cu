@@ -15,8 +15,8 @@
 // B = (Y o Y)^t Qbar (step 10); each recomputes Z.  Q (hi, lo) overwrites Z in place: the
 // epilogue warp that reads 16 columns of Z writes the 8 + 8 columns of packed Q pairs of
 // the same 16 values of s back into them, which is the A operand layout of the K-step.
-// Pass 2 runs one CTA per candidate (cand = MU, DNA) and o-block; the pair sits in
-// adjacent CTAs so that the second read of each V tile comes from L2.
+// Pass 2 keeps both candidates in one CTA (one Z each, copied out to registers at the top
+// of every chunk).
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -353,9 +353,13 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
     if (warp == 0) tmem_dealloc(tmem, L::NCOLS);
 }
 
-// Pass 2 of the split form: Z_cand from a hi / lo candidate and a hi / lo Y, one candidate
-// per CTA.  Shared memory: G ring (Y hi / lo of a chunk, 2 stages), V ring (3 half chunks);
-// the per-warp cost sums reuse V stage 0 at the end.
+// Pass 2 of the split form: Z_MU and Z_DNA from hi / lo candidates and a hi / lo Y in one
+// CTA, which reads each Y and V tile once for both.  Tensor memory holds one Z per
+// candidate (128 columns each) next to the four X planes; the epilogue copies both Z
+// into registers at the top of a chunk and frees them, so the MMAs of the next chunk run
+// while it computes.  One MMA-issuing warp per candidate.  Shared memory: G ring (Y hi /
+// lo of a chunk, 2 stages), V ring (3 half chunks); the per-warp cost sums reuse V stage
+// 0 at the end.
 template <int RP>
 struct P2SLayout {
     static constexpr int GST = 2, VST = 3;
@@ -367,26 +371,27 @@ struct P2SLayout {
     static constexpr uint32_t BAR = VR + VST * V_STAGE;
     static constexpr uint32_t TOTAL = BAR + 256;
     static constexpr uint32_t NCOLS = 512;
-    // tensor memory: Z x 2 | X hi | X lo
+    // tensor memory: Z_mu | Z_dna | X_mu hi | X_mu lo | X_dna hi | X_dna lo
     static constexpr uint32_t TX = 2 * SC2;
-    static_assert(TX + RP <= NCOLS, "tensor memory budget");
+    static_assert(TX + 2 * RP <= NCOLS, "tensor memory budget");
     static_assert(G_PLANE % 1024 == 0 && VR % 1024 == 0, "tiles must be 1024-byte aligned");
-    static_assert(4 * OBLK * 8 <= V_STAGE, "cost sums fit a V stage");
+    static_assert(2 * 4 * OBLK * 8 <= V_STAGE, "cost sums fit a V stage");
     static_assert(TOTAL + 1024 <= 232448, "shared memory budget");
 };
 
-enum { T_XFULL = 0, T_GFULL = 1, T_VFULL = 3, T_VEMPTY = 6, T_ZFULL = 9, T_ZEMPTY = 11,
-       T_DRAIN = 13, T_COUNT = 15 };
+// ZFULL[c] / ZEMPTY[c]: Z of candidate c written / copied out (one phase per chunk);
+// GEMPTY[st]: both candidates' MMAs of the chunk in G stage st are done (2 arrivals).
+enum { T_XFULL = 0, T_GFULL = 1, T_GEMPTY = 3, T_VFULL = 5, T_VEMPTY = 8, T_ZFULL = 11,
+       T_ZEMPTY = 13, T_DRAIN = 15, T_COUNT = 17 };
 
-// grid = (2 x O_pad / 128, splits): cand = blockIdx.x % 2 (0 MU, 1 DNA), o-block =
-// blockIdx.x / 2.  Writes the per-column cost of the candidate over the split's s-range.
+// grid = (O_pad / 128, splits).  Writes the per-column costs of both candidates over the
+// split's s-range.
 template <int RP>
 __global__ void __launch_bounds__(P1_THREADS, 1)
     k_tc_pass2s(P2Args a, int64_t xplane, const __grid_constant__ CUtensorMap tmY,
                 const __grid_constant__ CUtensorMap tmYl, const __grid_constant__ CUtensorMap tmV) {
     using L = P2SLayout<RP>;
     constexpr int GST = L::GST, VST = L::VST;
-    static_assert(GST == 2, "G stage reuse is signalled by the 2-deep ZFULL barriers");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* sm = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -396,8 +401,7 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
     volatile int* abort = reinterpret_cast<volatile int*>(sm + L::BAR + T_COUNT * 8 + 8);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int cand = (int)(blockIdx.x & 1);
-    const int64_t o0 = (int64_t)(blockIdx.x >> 1) * OBLK;
+    const int64_t o0 = (int64_t)blockIdx.x * OBLK;
     const int64_t s_begin = (int64_t)blockIdx.y * a.s_per;
     const int64_t s_end = min(a.S, s_begin + a.s_per);
     const int nch = s_end > s_begin ? (int)((s_end - s_begin + SC2 - 1) / SC2) : 0;
@@ -411,6 +415,7 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(&bar[T_GFULL + i], 1);
+            mbar_init(&bar[T_GEMPTY + i], 2);
             mbar_init(&bar[T_ZFULL + i], 1);
             mbar_init(&bar[T_ZEMPTY + i], W_EPI);
             mbar_init(&bar[T_DRAIN + i], 1);
@@ -439,10 +444,8 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
                     ++kv;
                     prog = true;
                 }
-                // G(kg) reuses the stage of chunk kg - 2, free once its MMAs are done
-                if (kg < nch && (kg < GST || mbar_test(&bar[T_ZFULL + (kg & 1)],
-                                                       ((kg - 2) >> 1) & 1))) {
-                    const int st = kg & 1;
+                if (kg < nch && mbar_test(&bar[T_GEMPTY + kg % GST], ((kg / GST) & 1) ^ 1)) {
+                    const int st = kg % GST;
                     const uint32_t dst = sbase + L::GR + st * L::G_STAGE;
                     const int32_t s0 = (int32_t)(s_begin + (int64_t)kg * SC2);
                     mbar_arrive_expect_tx(&bar[T_GFULL + st], L::G_STAGE);
@@ -468,24 +471,24 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
                 for (int k = max(0, kv - VST); k < kv; ++k)
                     drain_phase(&bar[T_VFULL + k % VST], (k / VST) & 1);
                 for (int k = max(0, kg - GST); k < kg; ++k)
-                    drain_phase(&bar[T_GFULL + (k & 1)], (k >> 1) & 1);
+                    drain_phase(&bar[T_GFULL + k % GST], (k / GST) & 1);
             }
         }
-    } else if (warp == W_MMA_Z) {
-        // Z(m) = X Y(m)^t in the split form, into buffer m & 1, products outer (see pass 1)
+    } else if (warp == W_MMA_Z || warp == W_MMA_AB) {
+        // candidate c: Z_c(m) = X_c Y(m)^t in the split form, products outer (see pass 1)
+        const int c = warp == W_MMA_AB ? 1 : 0;
         if (lane == 0 && nch > 0) {
             bool ok = wait_phase(&bar[T_XFULL], 0, abort);
-            const uint32_t xh = tmem + L::TX, xl = xh + RP / 2;
+            const uint32_t xh = tmem + L::TX + (uint32_t)c * RP, xl = xh + RP / 2;
+            const uint32_t tz = tmem + (uint32_t)c * SC2;
             constexpr uint32_t idesc = idesc_bf16(OBLK, SC2);
             for (int m = 0; ok && m < nch; ++m) {
-                const int zb = m & 1;
-                if (!(ok = wait_phase(&bar[T_GFULL + zb], (m >> 1) & 1, abort))) break;
-                if (m >= 2 &&
-                    !(ok = wait_phase(&bar[T_ZEMPTY + zb], ((m >> 1) & 1) ^ 1, abort)))
-                    break;
+                const int st = m % GST;
+                if (!(ok = wait_phase(&bar[T_GFULL + st], (m / GST) & 1, abort))) break;
+                // the epilogue has copied out Z_c of the previous chunk
+                if (m >= 1 && !(ok = wait_phase(&bar[T_ZEMPTY + c], (m - 1) & 1, abort))) break;
                 tc_fence_after();
-                const uint32_t gh = sbase + L::GR + zb * L::G_STAGE, gl = gh + L::G_PLANE;
-                const uint32_t tz = tmem + zb * SC2;
+                const uint32_t gh = sbase + L::GR + st * L::G_STAGE, gl = gh + L::G_PLANE;
 #pragma unroll
                 for (int p = 0; p < 3; ++p)
 #pragma unroll
@@ -495,11 +498,12 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
                                         desc_sw128((p == 1 ? gl : gh) + off), idesc,
                                         (p > 0 || kk > 0) ? 1u : 0u);
                     }
-                mma_commit(&bar[T_ZFULL + zb]);
+                mma_commit(&bar[T_GEMPTY + st]);
+                mma_commit(&bar[T_ZFULL + c]);
             }
             if (!ok) {
-                mma_commit(&bar[T_DRAIN + 0]);
-                drain_phase(&bar[T_DRAIN + 0], 0);
+                mma_commit(&bar[T_DRAIN + c]);
+                drain_phase(&bar[T_DRAIN + c], 0);
             }
         }
     } else if (warp < W_EPI) {
@@ -509,35 +513,40 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
         const int row = 32 * qd + lane;
         const int64_t o = o0 + row;
         const uint32_t lane_off = (uint32_t)(32 * qd) << 16;
-        if (nch > 0) {   // X_cand (hi, lo) of this o-block into tensor memory
-            constexpr int UP = RP / 32;
-            const bf16* X = static_cast<const bf16*>(cand ? a.Xd : a.Xm);
-            for (int u = cg; u < 2 * UP; u += 4) {
-                const bool lo = u >= UP;
-                x_to_tmem(X + (lo ? xplane : 0), a.rp, o, lo ? u - UP : u,
-                          tmem + L::TX + (lo ? RP / 2 : 0) + lane_off);
+        if (nch > 0) {   // X_mu, X_dna (hi, lo) of this o-block into tensor memory
+            constexpr int UP = RP / 32;   // 16-column units per plane
+            for (int u = cg; u < 4 * UP; u += 4) {
+                const int mat = u / UP;   // 0 mu hi, 1 mu lo, 2 dna hi, 3 dna lo
+                const bf16* X = static_cast<const bf16*>(mat < 2 ? a.Xm : a.Xd) +
+                                ((mat & 1) ? xplane : 0);
+                x_to_tmem(X, a.rp, o, u % UP, tmem + L::TX + (uint32_t)mat * (RP / 2) + lane_off);
             }
             tmem_st_wait();
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&bar[T_XFULL]);
         }
-        double acc = 0.0;
+        double acc_m = 0.0, acc_d = 0.0;
         bool ok = true;
         for (int k = 0; k < nch; ++k) {
-            const int zb = k & 1;
-            ok = wait_phase(&bar[T_ZFULL + zb], (k >> 1) & 1, abort);
+            ok = wait_phase(&bar[T_ZFULL + 0], k & 1, abort);
+            ok = ok && wait_phase(&bar[T_ZFULL + 1], k & 1, abort);
             if (!(ok = __all_sync(0xffffffffu, ok))) break;   // keep the warp converged
             tc_fence_after();
-            const uint32_t tz = tmem + zb * SC2 + 16 * cg + lane_off;
-            uint32_t zr[2][16];
-            tmem_ld16(tz, zr[0]);
-            tmem_ld16(tz + SCH, zr[1]);
+            const uint32_t tz = tmem + 16 * cg + lane_off;
+            uint32_t zm[2][16], zd[2][16];
+            tmem_ld16(tz, zm[0]);
+            tmem_ld16(tz + SCH, zm[1]);
+            tmem_ld16(tz + SC2, zd[0]);
+            tmem_ld16(tz + SC2 + SCH, zd[1]);
             tmem_ld_wait();
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&bar[T_ZEMPTY + zb]);
-            float run = 0.f;
+            if (lane == 0) {
+                mbar_arrive(&bar[T_ZEMPTY + 0]);
+                mbar_arrive(&bar[T_ZEMPTY + 1]);
+            }
+            float run_m = 0.f, run_d = 0.f;
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int kv = 2 * k + h, vs = kv % VST;
@@ -550,28 +559,37 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const float v = Vs[j * OBLK];
-                    const float z = __uint_as_float(zr[h][j]);
+                    const float z1 = __uint_as_float(zm[h][j]), z2 = __uint_as_float(zd[h][j]);
+                    const bool pos = v > 0.f;
                     // the hardware logarithm (absolute error near 2^-21 around 1, relative
                     // 2^-21 elsewhere): well inside the split form's 1e-4 near-tie margin
-                    run += v > 0.f ? z - v * __logf(z) : z;
+                    run_m += pos ? z1 - v * __logf(z1) : z1;
+                    run_d += pos ? z2 - v * __logf(z2) : z2;
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&bar[T_VEMPTY + vs]);
             }
             if (!ok) break;
-            acc += (double)run;
+            acc_m += (double)run_m;
+            acc_d += (double)run_d;
         }
-        if (!(fabs(acc) < INFINITY)) atomicOr(a.status, STATUS_NONFINITE);
+        if (!(fabs(acc_m) < INFINITY && fabs(acc_d) < INFINITY))
+            atomicOr(a.status, STATUS_NONFINITE);
         // cost sums of the four column groups: every V stage is consumed (or the CTA is
         // aborting) once all epilogue warps are here
         asm volatile("bar.sync 1, %0;" ::"r"(W_EPI * 32) : "memory");
         double* red = reinterpret_cast<double*>(sm + L::VR);
-        red[cg * OBLK + row] = acc;
+        red[(cg * 2 + 0) * OBLK + row] = acc_m;
+        red[(cg * 2 + 1) * OBLK + row] = acc_d;
         asm volatile("bar.sync 1, %0;" ::"r"(W_EPI * 32) : "memory");
         if (cg == 0 && ok && nch > 0 && !*abort && o < a.O) {
-            double d = red[row];
-            for (int g = 1; g < 4; ++g) d += red[g * OBLK + row];
-            a.dpart[((int64_t)blockIdx.y * 2 + cand) * a.O + o] = d;
+            double m = red[0 * OBLK + row], d = red[1 * OBLK + row];
+            for (int g = 1; g < 4; ++g) {
+                m += red[(g * 2 + 0) * OBLK + row];
+                d += red[(g * 2 + 1) * OBLK + row];
+            }
+            a.dpart[((int64_t)blockIdx.y * 2 + 0) * a.O + o] = m;
+            a.dpart[((int64_t)blockIdx.y * 2 + 1) * a.O + o] = d;
         }
     }
     tc_fence_before();
@@ -603,7 +621,7 @@ int launch_pass2s(const P2Args& a, int64_t xplane, const TcMaps& m, int64_t O_pa
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return DNA_ERR_CUDA;
-    dim3 grid((unsigned)(2 * (O_pad / OBLK)), (unsigned)splits);
+    dim3 grid((unsigned)(O_pad / OBLK), (unsigned)splits);
     k<<<grid, P1_THREADS, smem, st>>>(a, xplane, m.y, m.y_l, m.v);
     return after_launch();
 }

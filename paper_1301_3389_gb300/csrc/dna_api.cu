@@ -290,6 +290,7 @@ dna::TcOperands tc_operands(const dna_ctx* c, int wstep) {
     op.Xk = c->Xk; op.Yk = c->Yk; op.Ytk = c->Ytk; op.Y2tk = c->Y2tk;
     op.Xmk = c->Xmk; op.Xdk = c->Xdk;
     op.plane = c->plane;
+    op.ctas = c->num_sms;
     tc_v(c, wstep, &op.V, &op.vs);
     return op;
 }

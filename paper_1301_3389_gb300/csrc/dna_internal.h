@@ -137,12 +137,13 @@ struct TcOperands {
     // FP32 form on the tensor cores: every operand buffer holds a hi plane and, `plane`
     // elements after it, a lo plane (x = hi + lo, both bf16); 0 in the BF16 form
     int64_t plane;
+    int ctas;   // CTAs of the persistent kernels (the SM count)
 };
 
 // TMA descriptors of one half-step view (built once per bound problem).
 struct TcMaps {
     CUtensorMap x, y, yt, y2t, v, xm, xd;
-    CUtensorMap y_l, yt_l, y2t_l;   // lo planes (FP32 form on the tensor cores)
+    CUtensorMap x_l, y_l, yt_l, y2t_l;   // lo planes (FP32 form on the tensor cores)
 };
 
 struct TcBf16 {

@@ -212,6 +212,13 @@ __device__ __forceinline__ void mma_bf16_tmem_a(uint32_t d_tmem, uint32_t a_tmem
         "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
+// Copy of a 128-row x 256-bit block (16 bf16 of K per row) from shared memory, described
+// like an MMA operand, to tensor memory lanes 0-127 and 8 columns from taddr: the A-operand
+// layout of one K-step.  Asynchronous like an MMA; mma_commit covers it.
+__device__ __forceinline__ void tmem_cp_128x256b(uint32_t taddr, uint64_t sdesc) {
+    asm volatile("tcgen05.cp.cta_group::1.128x256b [%0], %1;" ::"r"(taddr), "l"(sdesc)
+                 : "memory");
+}
 // The mbarrier receives one arrive when all MMAs issued so far by this thread complete.
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
     asm volatile(

@@ -17,6 +17,8 @@
 // the same 16 values of s back into them, which is the A operand layout of the K-step.
 // Pass 2 keeps both candidates in one CTA (one Z each, copied out to registers at the top
 // of every chunk).
+#include <algorithm>
+
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -48,6 +50,9 @@ struct P1SLayout {
     static constexpr uint32_t H_STAGE = 2 * H_PLANE;
     // V: one half chunk, [64 s][128 o] float32
     static constexpr uint32_t V_STAGE = SCH * OBLK * 4;
+    // X hi or lo of an o-block, [NA][128 o][64 r] bf16, in a G stage
+    static constexpr uint32_t X_PLANE = OBLK * RP * 2;
+    static_assert(X_PLANE <= G_STAGE, "an X plane fits a G stage");
     static constexpr uint32_t GR = 0;
     static constexpr uint32_t HR = GR + GST * G_STAGE;
     static constexpr uint32_t VR = HR + HST * H_STAGE;
@@ -63,20 +68,80 @@ struct P1SLayout {
     static_assert(TOTAL + 1024 <= 232448, "shared memory budget");
 };
 
-// G[j] holds r-atom j % NA of chunk j / NA.  QFULL[2 b + h]: the epilogue wrote Q of half
+// G stages hold X planes and r-atoms of Y in the order of P1SGCursor.  QFULL[2 b + h]: the epilogue wrote Q of half
 // h (s 64 h .. 64 h + 63) of the chunk in ZQ buffer b.  QEMPTY[b]: GEMM2 of that chunk is
 // done (buffer b free for GEMM1 two chunks later; for the last chunk the accumulator is
 // final).
-enum { S_XFULL = 0, S_GFULL = 1, S_GEMPTY = 4, S_HFULL = 7, S_HEMPTY = 9, S_VFULL = 11,
-       S_VEMPTY = 13, S_ZFULL = 15, S_QFULL = 17, S_QEMPTY = 21, S_DRAIN = 23, S_COUNT = 25 };
+enum { S_GFULL = 0, S_GEMPTY = 3, S_HFULL = 6, S_HEMPTY = 8, S_VFULL = 10, S_VEMPTY = 12,
+       S_ZFULL = 14, S_QFULL = 16, S_QEMPTY = 20, S_DRAIN = 22, S_COUNT = 24 };
 
-// grid = (nwhich x O_pad / 128, splits): which = blockIdx.x % nwhich (nwhich = 2 for DNA,
-// 1 for the MU step, which needs A only), o-block = blockIdx.x / nwhich.
+// One tile of pass 1: the accumulator (A if which = 0, B if which = 1) of one o-block over
+// one split of s.  Tiles are numbered split-major, then o-block, then which.
+struct P1STile {
+    int64_t o0, s_begin, s_end;
+    int nch, which, split;
+};
+__device__ __forceinline__ P1STile p1s_tile(int t, int nwhich, int nob, const P1Args& a) {
+    P1STile x;
+    x.which = t % nwhich;
+    const int rest = t / nwhich;
+    x.o0 = (int64_t)(rest % nob) * OBLK;
+    x.split = rest / nob;
+    x.s_begin = (int64_t)x.split * a.s_per;
+    x.s_end = min(a.S, x.s_begin + a.s_per);
+    x.nch = x.s_end > x.s_begin ? (int)((x.s_end - x.s_begin + SC2 - 1) / SC2) : 0;
+    return x;
+}
+
+// A walk over the units (tile, chunk, sub) of one CTA's tiles, sub < per_chunk.
+struct P1SCursor {
+    int t, k, sub;
+    P1STile x;
+    __device__ __forceinline__ void start(int t0, int nwhich, int nob, const P1Args& a) {
+        t = t0; k = 0; sub = 0;
+        x = p1s_tile(t, nwhich, nob, a);
+    }
+    __device__ __forceinline__ void next(int per_chunk, int nwhich, int nob, const P1Args& a) {
+        if (++sub < per_chunk) return;
+        sub = 0;
+        if (++k < x.nch) return;
+        k = 0;
+        ++t;
+        x = p1s_tile(t, nwhich, nob, a);
+    }
+};
+
+// The G-ring walk of one CTA: per tile the X hi and X lo planes (units 0, 1), then the
+// r-atoms of every chunk (units 2 + NA k + at).
+struct P1SGCursor {
+    int t, u, n;
+    P1STile x;
+    __device__ __forceinline__ void start(int t0, int na, int nwhich, int nob, const P1Args& a) {
+        t = t0; u = 0;
+        x = p1s_tile(t, nwhich, nob, a);
+        n = 2 + na * x.nch;
+    }
+    __device__ __forceinline__ void next(int na, int nwhich, int nob, const P1Args& a) {
+        if (++u < n) return;
+        u = 0;
+        ++t;
+        x = p1s_tile(t, nwhich, nob, a);
+        n = 2 + na * x.nch;
+    }
+};
+
+// Persistent: CTA i takes the tiles [i T / G, (i + 1) T / G) of the T = nwhich x nob x
+// splits tiles (G = gridDim.x).  Between two tiles the epilogue writes the next X into
+// tensor memory as soon as the last GEMM1 of the tile is done and copies the accumulator
+// out once its last GEMM2 is, while GEMM1 of the next tile runs; the rings, the ZQ
+// buffers and every barrier phase run on across tiles.  X (hi, lo) of each tile comes
+// through the G ring and goes into tensor memory by tcgen05.cp from the MMA thread.
 template <int RP>
 __global__ void __launch_bounds__(P1_THREADS, 1)
-    k_tc_pass1s(P1Args a, int64_t xplane, int nwhich, const __grid_constant__ CUtensorMap tmY,
-                const __grid_constant__ CUtensorMap tmYl, const __grid_constant__ CUtensorMap tmYt,
-                const __grid_constant__ CUtensorMap tmYtl,
+    k_tc_pass1s(P1Args a, int nwhich, int nob, int ntiles,
+                const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmXl,
+                const __grid_constant__ CUtensorMap tmY, const __grid_constant__ CUtensorMap tmYl,
+                const __grid_constant__ CUtensorMap tmYt, const __grid_constant__ CUtensorMap tmYtl,
                 const __grid_constant__ CUtensorMap tmY2t,
                 const __grid_constant__ CUtensorMap tmY2tl,
                 const __grid_constant__ CUtensorMap tmV) {
@@ -91,17 +156,11 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
     volatile int* abort = reinterpret_cast<volatile int*>(sm + L::BAR + S_COUNT * 8 + 8);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int which = (int)blockIdx.x % nwhich;
-    const int64_t o0 = (int64_t)(blockIdx.x / nwhich) * OBLK;
-    const int64_t s_begin = (int64_t)blockIdx.y * a.s_per;
-    const int64_t s_end = min(a.S, s_begin + a.s_per);
-    const int nch = s_end > s_begin ? (int)((s_end - s_begin + SC2 - 1) / SC2) : 0;
-    const CUtensorMap* tmHh = which ? &tmY2t : &tmYt;
-    const CUtensorMap* tmHl = which ? &tmY2tl : &tmYtl;
+    const int t_begin = (int)((int64_t)blockIdx.x * ntiles / gridDim.x);
+    const int t_end = (int)((int64_t)(blockIdx.x + 1) * ntiles / gridDim.x);
 
     if (warp == 0) { tmem_alloc(tslot, L::NCOLS); tmem_relinquish(); }
     if (tid == W_PRODUCER * 32) {
-        mbar_init(&bar[S_XFULL], W_EPI);
         for (int i = 0; i < GST; ++i) {
             mbar_init(&bar[S_GFULL + i], 1);
             mbar_init(&bar[S_GEMPTY + i], 1);
@@ -125,45 +184,66 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
     const uint32_t tmem = *tslot;
 
     if (warp == W_PRODUCER) {
-        // one thread services the three rings in whatever order their slots free up
-        if (lane == 0 && nch > 0) {
-            tma_prefetch_desc(&tmY); tma_prefetch_desc(&tmYl); tma_prefetch_desc(tmHh);
-            tma_prefetch_desc(tmHl); tma_prefetch_desc(&tmV);
-            const int ng = NA * nch, nh = 2 * nch;
-            int kg = 0, kh = 0, kv = 0;
+        // one thread services the three rings in whatever order their slots free up; each
+        // ring walks the CTA's units with its own cursor
+        if (lane == 0 && t_begin < t_end) {
+            tma_prefetch_desc(&tmX); tma_prefetch_desc(&tmXl);
+            tma_prefetch_desc(&tmY); tma_prefetch_desc(&tmYl); tma_prefetch_desc(&tmYt);
+            tma_prefetch_desc(&tmYtl); tma_prefetch_desc(&tmV);
+            if (nwhich > 1) { tma_prefetch_desc(&tmY2t); tma_prefetch_desc(&tmY2tl); }
+            P1SGCursor cg_;
+            P1SCursor ch_, cv_;
+            cg_.start(t_begin, NA, nwhich, nob, a);
+            ch_.start(t_begin, nwhich, nob, a);
+            cv_.start(t_begin, nwhich, nob, a);
+            int kg = 0, kh = 0, kv = 0;   // units issued per ring
             long long t0 = clock64();
-            while (kg < ng || kh < nh || kv < nh) {
+            while (cg_.t < t_end || ch_.t < t_end || cv_.t < t_end) {
                 bool prog = false;
-                if (kv < nh && mbar_test(&bar[S_VEMPTY + kv % VST], ((kv / VST) & 1) ^ 1)) {
+                if (cv_.t < t_end && mbar_test(&bar[S_VEMPTY + kv % VST], ((kv / VST) & 1) ^ 1)) {
                     const int st = kv % VST;
                     mbar_arrive_expect_tx(&bar[S_VFULL + st], L::V_STAGE);
-                    tma_load_2d(sbase + L::VR + st * L::V_STAGE, &tmV, (int32_t)o0,
-                                (int32_t)(s_begin + (int64_t)kv * SCH), &bar[S_VFULL + st]);
+                    tma_load_2d(sbase + L::VR + st * L::V_STAGE, &tmV, (int32_t)cv_.x.o0,
+                                (int32_t)(cv_.x.s_begin + (int64_t)cv_.k * SC2 + SCH * cv_.sub),
+                                &bar[S_VFULL + st]);
                     ++kv;
+                    cv_.next(2, nwhich, nob, a);
                     prog = true;
                 }
-                if (kg < ng && mbar_test(&bar[S_GEMPTY + kg % GST], ((kg / GST) & 1) ^ 1)) {
+                if (cg_.t < t_end && mbar_test(&bar[S_GEMPTY + kg % GST], ((kg / GST) & 1) ^ 1)) {
                     const int st = kg % GST;
                     const uint32_t dst = sbase + L::GR + st * L::G_STAGE;
-                    const int32_t s0 = (int32_t)(s_begin + (int64_t)(kg / NA) * SC2);
-                    const int32_t r0 = 64 * (kg % NA);
-                    mbar_arrive_expect_tx(&bar[S_GFULL + st], L::G_STAGE);
-                    for (int hs = 0; hs < 2; ++hs) {
-                        tma_load_2d(dst + hs * SCH * 128, &tmY, r0, s0 + SCH * hs, &bar[S_GFULL + st]);
-                        tma_load_2d(dst + L::G_PLANE + hs * SCH * 128, &tmYl, r0, s0 + SCH * hs,
-                                    &bar[S_GFULL + st]);
+                    if (cg_.u < 2) {   // X hi or lo of the tile's o-block, [NA][128 o][64 r]
+                        mbar_arrive_expect_tx(&bar[S_GFULL + st], L::X_PLANE);
+                        for (int at = 0; at < NA; ++at)
+                            tma_load_2d(dst + at * OBLK * 128, cg_.u ? &tmXl : &tmX, 64 * at,
+                                        (int32_t)cg_.x.o0, &bar[S_GFULL + st]);
+                    } else {
+                        const int ck = (cg_.u - 2) / NA, at = (cg_.u - 2) % NA;
+                        const int32_t s0 = (int32_t)(cg_.x.s_begin + (int64_t)ck * SC2);
+                        mbar_arrive_expect_tx(&bar[S_GFULL + st], L::G_STAGE);
+                        for (int hs = 0; hs < 2; ++hs) {
+                            tma_load_2d(dst + hs * SCH * 128, &tmY, 64 * at, s0 + SCH * hs,
+                                        &bar[S_GFULL + st]);
+                            tma_load_2d(dst + L::G_PLANE + hs * SCH * 128, &tmYl, 64 * at,
+                                        s0 + SCH * hs, &bar[S_GFULL + st]);
+                        }
                     }
                     ++kg;
+                    cg_.next(NA, nwhich, nob, a);
                     prog = true;
                 }
-                if (kh < nh && mbar_test(&bar[S_HEMPTY + kh % HST], ((kh / HST) & 1) ^ 1)) {
+                if (ch_.t < t_end && mbar_test(&bar[S_HEMPTY + kh % HST], ((kh / HST) & 1) ^ 1)) {
                     const int st = kh % HST;
                     const uint32_t dst = sbase + L::HR + st * L::H_STAGE;
-                    const int32_t s0 = (int32_t)(s_begin + (int64_t)kh * SCH);
+                    const int32_t s0 = (int32_t)(ch_.x.s_begin + (int64_t)ch_.k * SC2 + SCH * ch_.sub);
+                    const CUtensorMap* mh = ch_.x.which ? &tmY2t : &tmYt;
+                    const CUtensorMap* ml = ch_.x.which ? &tmY2tl : &tmYtl;
                     mbar_arrive_expect_tx(&bar[S_HFULL + st], L::H_STAGE);
-                    tma_load_2d(dst, tmHh, s0, 0, &bar[S_HFULL + st]);
-                    tma_load_2d(dst + L::H_PLANE, tmHl, s0, 0, &bar[S_HFULL + st]);
+                    tma_load_2d(dst, mh, s0, 0, &bar[S_HFULL + st]);
+                    tma_load_2d(dst + L::H_PLANE, ml, s0, 0, &bar[S_HFULL + st]);
                     ++kh;
+                    ch_.next(2, nwhich, nob, a);
                     prog = true;
                 }
                 if (prog) {
@@ -184,36 +264,57 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
             }
         }
     } else if (warp == W_MMA_Z) {
-        // Z(m) = X Y(m)^t as x_hi y_hi + x_hi y_lo + x_lo y_hi, into ZQ buffer m & 1; per
-        // r-atom the three products are issued outer and the K-steps inner (back-to-back
-        // MMAs into one accumulator with the same K-slice run the tensor pipe at about
-        // 3/4 rate)
-        if (lane == 0 && nch > 0) {
-            bool ok = wait_phase(&bar[S_XFULL], 0, abort);
+        // Z(m) = X Y(m)^t as x_hi y_hi + x_hi y_lo + x_lo y_hi, into ZQ buffer m & 1 (m counts
+        // the CTA's chunks); per r-atom the three products are issued outer and the K-steps
+        // inner (back-to-back MMAs into one accumulator with the same K-slice run the
+        // tensor pipe at about 3/4 rate)
+        if (lane == 0) {
+            bool ok = true;
+            int m = 0, j = 0;
             constexpr uint32_t idesc = idesc_bf16(OBLK, SC2);
-            for (int m = 0; ok && m < nch; ++m) {
-                const int b = m & 1;
-                // GEMM2 of chunk m - 2 has read its Q from this buffer
-                if (m >= 2 && !(ok = wait_phase(&bar[S_QEMPTY + b], ((m - 2) >> 1) & 1, abort)))
+            for (int t = t_begin; ok && t < t_end; ++t) {
+                const P1STile x = p1s_tile(t, nwhich, nob, a);
+                // X of the tile into tensor memory once GEMM1 of the previous tile's last
+                // chunk (this thread's own MMAs) has finished reading the old X
+                if (m >= 1 &&
+                    !(ok = wait_phase(&bar[S_ZFULL + ((m - 1) & 1)], ((m - 1) >> 1) & 1, abort)))
                     break;
-                const uint32_t tz = tmem + b * SC2;
 #pragma unroll 1
-                for (int at = 0; at < NA; ++at) {
-                    const int j = m * NA + at;
+                for (int pl = 0; pl < 2; ++pl, ++j) {
                     if (!(ok = wait_phase(&bar[S_GFULL + j % GST], (j / GST) & 1, abort))) break;
                     tc_fence_after();
-                    const uint32_t gh = sbase + L::GR + (j % GST) * L::G_STAGE, gl = gh + L::G_PLANE;
-                    const uint32_t xh = tmem + L::TXH + 32 * at, xl = tmem + L::TXL + 32 * at;
+                    const uint32_t xs = sbase + L::GR + (j % GST) * L::G_STAGE;
 #pragma unroll
-                    for (int p = 0; p < 3; ++p)
-#pragma unroll
-                        for (int kq = 0; kq < 4; ++kq)
-                            mma_bf16_tmem_a(tz, (p == 2 ? xl : xh) + 8 * kq,
-                                            desc_sw128((p == 1 ? gl : gh) + 32u * kq), idesc,
-                                            (at > 0 || p > 0 || kq > 0) ? 1u : 0u);
+                    for (int kk = 0; kk < RP / 16; ++kk)
+                        tmem_cp_128x256b(tmem + (pl ? L::TXL : L::TXH) + 8 * kk,
+                                         desc_sw128(xs + (kk >> 2) * OBLK * 128 + 32u * (kk & 3)));
                     mma_commit(&bar[S_GEMPTY + j % GST]);
                 }
-                if (ok) mma_commit(&bar[S_ZFULL + b]);
+                for (int k = 0; ok && k < x.nch; ++k, ++m) {
+                    const int b = m & 1;
+                    // GEMM2 of chunk m - 2 has read its Q from this buffer
+                    if (m >= 2 &&
+                        !(ok = wait_phase(&bar[S_QEMPTY + b], ((m - 2) >> 1) & 1, abort)))
+                        break;
+                    const uint32_t tz = tmem + b * SC2;
+#pragma unroll 1
+                    for (int at = 0; at < NA; ++at, ++j) {
+                        if (!(ok = wait_phase(&bar[S_GFULL + j % GST], (j / GST) & 1, abort))) break;
+                        tc_fence_after();
+                        const uint32_t gh = sbase + L::GR + (j % GST) * L::G_STAGE,
+                                       gl = gh + L::G_PLANE;
+                        const uint32_t xh = tmem + L::TXH + 32 * at, xl = tmem + L::TXL + 32 * at;
+#pragma unroll
+                        for (int p = 0; p < 3; ++p)
+#pragma unroll
+                            for (int kq = 0; kq < 4; ++kq)
+                                mma_bf16_tmem_a(tz, (p == 2 ? xl : xh) + 8 * kq,
+                                                desc_sw128((p == 1 ? gl : gh) + 32u * kq), idesc,
+                                                (at > 0 || p > 0 || kq > 0) ? 1u : 0u);
+                        mma_commit(&bar[S_GEMPTY + j % GST]);
+                    }
+                    if (ok) mma_commit(&bar[S_ZFULL + b]);
+                }
             }
             if (!ok) {
                 mma_commit(&bar[S_DRAIN + 0]);
@@ -222,31 +323,40 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
         }
     } else if (warp == W_MMA_AB) {
         // accumulator += Q(m) H(m) as q_hi h_hi + q_hi h_lo + q_lo h_hi, one half chunk at a
-        // time, products outer
-        if (lane == 0 && nch > 0) {
+        // time, products outer; the first MMA of a tile overwrites the accumulator, which
+        // the epilogue has copied out before it signals the first Q of the tile
+        if (lane == 0) {
             bool ok = true;
+            int m = 0;
             constexpr uint32_t idesc = idesc_bf16(OBLK, RP);
-            for (int m = 0; ok && m < nch; ++m) {
-                const int b = m & 1;
+            for (int t = t_begin; ok && t < t_end; ++t) {
+                const int nch = p1s_tile(t, nwhich, nob, a).nch;
+                for (int k = 0; ok && k < nch; ++k, ++m) {
+                    const int b = m & 1;
 #pragma unroll 1
-                for (int h = 0; ok && h < 2; ++h) {
-                    const int j = 2 * m + h;
-                    if (!(ok = wait_phase(&bar[S_QFULL + 2 * b + h], (m >> 1) & 1, abort))) break;
-                    if (!(ok = wait_phase(&bar[S_HFULL + j % HST], (j / HST) & 1, abort))) break;
-                    tc_fence_after();
-                    const uint32_t th = sbase + L::HR + (j % HST) * L::H_STAGE, tl = th + L::H_PLANE;
-                    const uint32_t q0 = tmem + b * SC2 + 64 * h;
+                    for (int h = 0; ok && h < 2; ++h) {
+                        const int jh = 2 * m + h;
+                        if (!(ok = wait_phase(&bar[S_QFULL + 2 * b + h], (m >> 1) & 1, abort)))
+                            break;
+                        if (!(ok = wait_phase(&bar[S_HFULL + jh % HST], (jh / HST) & 1, abort)))
+                            break;
+                        tc_fence_after();
+                        const uint32_t th = sbase + L::HR + (jh % HST) * L::H_STAGE,
+                                       tl = th + L::H_PLANE;
+                        const uint32_t q0 = tmem + b * SC2 + 64 * h;
 #pragma unroll
-                    for (int p = 0; p < 3; ++p)
+                        for (int p = 0; p < 3; ++p)
 #pragma unroll
-                        for (int kq = 0; kq < SCH / 16; ++kq) {
-                            const uint32_t acc = (m > 0 || h > 0 || p > 0 || kq > 0) ? 1u : 0u;
-                            mma_bf16_tmem_a(tmem + L::TACC, q0 + 16 * kq + (p == 2 ? 8 : 0),
-                                            desc_sw128((p == 1 ? tl : th) + 32u * kq), idesc, acc);
-                        }
-                    mma_commit(&bar[S_HEMPTY + j % HST]);
+                            for (int kq = 0; kq < SCH / 16; ++kq) {
+                                const uint32_t acc = (k > 0 || h > 0 || p > 0 || kq > 0) ? 1u : 0u;
+                                mma_bf16_tmem_a(tmem + L::TACC, q0 + 16 * kq + (p == 2 ? 8 : 0),
+                                                desc_sw128((p == 1 ? tl : th) + 32u * kq), idesc,
+                                                acc);
+                            }
+                        mma_commit(&bar[S_HEMPTY + jh % HST]);
+                    }
+                    if (ok) mma_commit(&bar[S_QEMPTY + b]);
                 }
-                if (ok) mma_commit(&bar[S_QEMPTY + b]);
             }
             if (!ok) {
                 mma_commit(&bar[S_DRAIN + 1]);
@@ -259,80 +369,69 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
         // values s = 64 h + 16 cg .. + 15 and the ZQ columns 16 kk .. 16 kk + 15
         const int qd = warp & 3, cg = warp >> 2;
         const int row = 32 * qd + lane;
-        const int64_t o = o0 + row;
         const uint32_t lane_off = (uint32_t)(32 * qd) << 16;
-        if (nch > 0) {   // X hi and lo of this o-block into tensor memory
-            constexpr int UP = RP / 32;
-            const bf16* X = static_cast<const bf16*>(a.X);
-            for (int u = cg; u < 2 * UP; u += 4) {
-                const bool lo = u >= UP;
-                x_to_tmem(X + (lo ? xplane : 0), a.rp, o, lo ? u - UP : u,
-                          tmem + (lo ? L::TXL : L::TXH) + lane_off);
-            }
-            tmem_st_wait();
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&bar[S_XFULL]);
-        }
         float zmin = 1.f;   // min over v > 0 of z (see the BF16 pass 1)
         bool ok = true;
-        for (int k = 0; k < nch; ++k) {
-            const int b = k & 1;
-            ok = wait_phase(&bar[S_ZFULL + b], (k >> 1) & 1, abort);
-            if (!(ok = __all_sync(0xffffffffu, ok))) break;   // keep the warp converged
-            tc_fence_after();
+        int m = 0;
+        for (int t = t_begin; ok && t < t_end; ++t) {
+            const P1STile x = p1s_tile(t, nwhich, nob, a);
+            for (int k = 0; k < x.nch; ++k, ++m) {
+                const int b = m & 1;
+                ok = wait_phase(&bar[S_ZFULL + b], (m >> 1) & 1, abort);
+                if (!(ok = __all_sync(0xffffffffu, ok))) break;   // keep the warp converged
+                tc_fence_after();
 #pragma unroll 1
-            for (int h = 0; h < 2; ++h) {
-                const int kv = 2 * k + h, vs = kv % VST;
-                ok = wait_phase(&bar[S_VFULL + vs], (kv / VST) & 1, abort);
-                if (!(ok = __all_sync(0xffffffffu, ok))) break;
-                const uint32_t col = tmem + b * SC2 + 64 * h + 16 * cg + lane_off;
-                uint32_t zr[16];
-                tmem_ld16(col, zr);
-                // V rows s = 16 cg + j of this half; TMA zero-fills v outside the problem
-                const float* Vs = reinterpret_cast<const float*>(sm + L::VR + vs * L::V_STAGE) +
-                                  16 * cg * OBLK + row;
-                float vv[16];
+                for (int h = 0; h < 2; ++h) {
+                    const int kv = 2 * m + h, vs = kv % VST;
+                    ok = wait_phase(&bar[S_VFULL + vs], (kv / VST) & 1, abort);
+                    if (!(ok = __all_sync(0xffffffffu, ok))) break;
+                    const uint32_t col = tmem + b * SC2 + 64 * h + 16 * cg + lane_off;
+                    uint32_t zr[16];
+                    tmem_ld16(col, zr);
+                    // V rows s = 16 cg + j of this half; TMA zero-fills v outside the problem
+                    const float* Vs = reinterpret_cast<const float*>(sm + L::VR + vs * L::V_STAGE) +
+                                      16 * cg * OBLK + row;
+                    float vv[16];
 #pragma unroll
-                for (int j = 0; j < 16; ++j) vv[j] = Vs[j * OBLK];
-                tmem_ld_wait();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&bar[S_VEMPTY + vs]);
-                uint32_t hp[8], lp[8];
+                    for (int j = 0; j < 16; ++j) vv[j] = Vs[j * OBLK];
+                    tmem_ld_wait();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&bar[S_VEMPTY + vs]);
+                    uint32_t hp[8], lp[8];
 #pragma unroll
-                for (int j = 0; j < 16; j += 2) {
-                    float w[2];
+                    for (int j = 0; j < 16; j += 2) {
+                        float w[2];
 #pragma unroll
-                    for (int t = 0; t < 2; ++t) {
-                        const float v = vv[j + t];
-                        const float z = __uint_as_float(zr[j + t]);
-                        const float rz = __fdividef(1.0f, z);
-                        const bool pos = v > 0.f;
-                        zmin = fminf(zmin, pos ? z : 1.f);
-                        const float q = v * rz;
-                        w[t] = pos ? (which ? q * rz : q) : 0.f;   // q, or qbar = q / z
+                        for (int tt = 0; tt < 2; ++tt) {
+                            const float v = vv[j + tt];
+                            const float z = __uint_as_float(zr[j + tt]);
+                            const float rz = __fdividef(1.0f, z);
+                            const bool pos = v > 0.f;
+                            zmin = fminf(zmin, pos ? z : 1.f);
+                            const float q = v * rz;
+                            w[tt] = pos ? (x.which ? q * rz : q) : 0.f;   // q, or qbar = q / z
+                        }
+                        split2(w[0], w[1], hp[j / 2], lp[j / 2]);
                     }
-                    split2(w[0], w[1], hp[j / 2], lp[j / 2]);
+                    tmem_st8(col, hp);
+                    tmem_st8(col + 8, lp);
+                    tmem_st_wait();
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&bar[S_QFULL + 2 * b + h]);
                 }
-                tmem_st8(col, hp);
-                tmem_st8(col + 8, lp);
-                tmem_st_wait();
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&bar[S_QFULL + 2 * b + h]);
+                if (!ok) break;
             }
             if (!ok) break;
-        }
-        if (!(zmin > 0.f)) atomicOr(a.status, STATUS_NONFINITE);
-        if (ok && nch > 0) {   // GEMM2 of the last chunk done: the accumulator is final
-            const int kl = nch - 1;
+            // GEMM2 of the last chunk done: copy the accumulator out
+            const int ml = m - 1;
             ok = __all_sync(0xffffffffu,
-                            wait_phase(&bar[S_QEMPTY + (kl & 1)], (kl >> 1) & 1, abort));
-        }
-        if (ok && nch > 0) {
+                            wait_phase(&bar[S_QEMPTY + (ml & 1)], (ml >> 1) & 1, abort));
+            if (!ok) break;
             tc_fence_after();
-            const int64_t base = (int64_t)blockIdx.y * a.R;
-            float* dst = which ? a.Bpart : a.Apart;
+            const int64_t o = x.o0 + row;
+            const int64_t base = (int64_t)x.split * a.R;
+            float* dst = x.which ? a.Bpart : a.Apart;
 #pragma unroll 1
             for (int g = cg; g < RP / 32; g += 4) {
                 uint32_t r32[32];
@@ -345,7 +444,9 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
                         if (r < a.R) dst[(base + r) * a.O + o] = __uint_as_float(r32[i]);
                     }
             }
+            tc_fence_before();
         }
+        if (!(zmin > 0.f)) atomicOr(a.status, STATUS_NONFINITE);
     }
     tc_fence_before();
     __syncthreads();
@@ -599,17 +700,20 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
 }
 
 template <int RP>
-int launch_pass1s(const P1Args& a, int64_t xplane, bool with_b, const TcMaps& m, int64_t O_pad,
-                  int splits, cudaStream_t st) {
+int launch_pass1s(const P1Args& a, bool with_b, const TcMaps& m, int64_t O_pad, int splits,
+                  int ctas, cudaStream_t st) {
     const uint32_t smem = P1SLayout<RP>::TOTAL + 1024;
     auto k = k_tc_pass1s<RP>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return DNA_ERR_CUDA;
     const int nwhich = with_b ? 2 : 1;
-    dim3 grid((unsigned)(nwhich * (O_pad / OBLK)), (unsigned)splits);
-    k<<<grid, P1_THREADS, smem, st>>>(a, xplane, nwhich, m.y, m.y_l, m.yt, m.yt_l, m.y2t,
-                                       m.y2t_l, m.v);
+    const int nob = (int)(O_pad / OBLK);
+    const int ntiles = nwhich * nob * splits;
+    if (ntiles == 0) return DNA_OK;
+    const int grid = ctas > 0 ? std::min(ctas, ntiles) : ntiles;
+    k<<<grid, P1_THREADS, smem, st>>>(a, nwhich, nob, ntiles, m.x, m.x_l, m.y, m.y_l, m.yt,
+                                       m.yt_l, m.y2t, m.y2t_l, m.v);
     return after_launch();
 }
 
@@ -634,8 +738,10 @@ int TcBf16::pass1_split(const TcOperands& op, const TcMaps& maps, float* Apart, 
     a.S = op.S; a.O = op.O; a.R = op.R; a.s_per = s_per;
     a.Apart = Apart; a.Bpart = Bpart; a.status = status;
     a.V = op.V; a.vs = op.vs; a.X = op.Xk; a.rp = rank_pad(op.R);
-    if (a.rp == 64) return tc::launch_pass1s<64>(a, op.plane, with_b, maps, op.O_pad, splits, st);
-    if (a.rp == 128) return tc::launch_pass1s<128>(a, op.plane, with_b, maps, op.O_pad, splits, st);
+    if (a.rp == 64)
+        return tc::launch_pass1s<64>(a, with_b, maps, op.O_pad, splits, op.ctas, st);
+    if (a.rp == 128)
+        return tc::launch_pass1s<128>(a, with_b, maps, op.O_pad, splits, op.ctas, st);
     return DNA_ERR_UNSUPPORTED;
 }
 

@@ -423,9 +423,10 @@ int half_step(dna_ctx* c, int w, bool mu_only, bool prepared, bool next) {
         e = phase(c, DNA_PHASE_CANDIDATES, 1, [&] { return S::mu_apply(v, c->c, A, sp1, st); });
         return e ? e : normalize<Tp>(c, w == 1 ? 1 : 0);
     }
-    // many split partials (the split FP32 form caps the accumulation per CTA): one streaming
-    // pass sums them into split 0 first; a few are summed inside the candidates kernel
-    const bool presum = (int64_t)sp1 * v.O >= 32768;
+    // many split partials: one streaming pass sums them into split 0 first (the candidates
+    // kernel streams up to 4 itself when the rank allows its register form)
+    const bool presum =
+        (int64_t)sp1 * v.O >= 32768 && (sp1 > 4 || !S::cand_in_registers(c->R));
     e = phase(c, DNA_PHASE_CANDIDATES, presum ? 2 : 1, [&] {
         if (presum)
             if (int r = S::split_sum(A, B, c->R, v.O, sp1, st)) return r;

@@ -94,6 +94,9 @@ template <typename Tp> struct Simt {
                           cudaStream_t st);
     // A[0] = sum over the splits of A[sp] (and B, if given), each [R][O]: ascending order.
     static int split_sum(Tp* A, Tp* B, int64_t R, int64_t O, int splits, cudaStream_t st);
+    // cand_fused keeps a thread's candidates in registers and sums the split partials as
+    // they stream in (no split_sum pass needed)
+    static bool cand_in_registers(int64_t R);
     // Selection as above, plus fpart[glue_parts(O)][R]: per-block sums of the new X.
     static int select_fused(const View& v, const Tp* Xmu, const Tp* Xdna, const double* dpart,
                             int splits, uint8_t* choice, double* dfin, double* fpart,

@@ -172,6 +172,114 @@ __global__ void __launch_bounds__(1024) k_cand_fused(View v, const double* __res
     }
 }
 
+// The candidates kernel for R <= 16 RS (the usual case): CTA = 32 columns o (threadIdx.x)
+// x ceil(R / RS) <= 16 groups of RS consecutive r (threadIdx.y), every thread keeping its RS
+// candidates in registers, so the eq. 10 renormalisation needs one shared-memory
+// reduction and no second pass over r.  The split partials of pass 1 are summed in
+// ascending split order while they stream in (no separate pass over them); all loads of
+// a thread are issued before their results are used.  With BF the grid covers O_pad and
+// the bf16 operand rows [o][rp] are written with 16-byte stores (zeros in the padding).
+template <typename Tp, bool BF, int RS>
+__global__ void __launch_bounds__(512) k_cand_reg(View v, const double* __restrict__ c,
+                                                  const Tp* __restrict__ Apart,
+                                                  const Tp* __restrict__ Bpart, int splits,
+                                                  Tp* __restrict__ Xmu, Tp* __restrict__ Xdna,
+                                                  Tp eps, Tp alpha, bf16* __restrict__ Xmk,
+                                                  bf16* __restrict__ Xdk, int64_t rp,
+                                                  int64_t plane) {
+    static_assert(RS % 8 == 0, "operand rows are written 8 values at a time");
+    __shared__ Tp red[16][33];
+    __shared__ Tp scl[32];
+    const int64_t R = v.R, O = v.O;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int64_t o = (int64_t)blockIdx.x * 32 + tx;
+    const bool live = o < O;
+    const int64_t r0 = (int64_t)ty * RS;
+    const Tp* __restrict__ X = static_cast<const Tp*>(v.X);
+
+    Tp ra[RS], rb[RS], x[RS];
+#pragma unroll
+    for (int i = 0; i < RS; ++i) { ra[i] = Tp(0); rb[i] = Tp(0); x[i] = Tp(0); }
+    if (live) {
+#pragma unroll
+        for (int i = 0; i < RS; ++i)
+            if (r0 + i < R) x[i] = X[(r0 + i) * v.xr + o * v.xo];
+#pragma unroll 1
+        for (int sp = 0; sp < splits; ++sp) {
+#pragma unroll
+            for (int i = 0; i < RS; ++i) {
+                const int64_t r = r0 + i;
+                if (r < R) {
+                    ra[i] += Apart[((int64_t)sp * R + r) * O + o];
+                    rb[i] += Bpart[((int64_t)sp * R + r) * O + o];
+                }
+            }
+        }
+    }
+    Tp den = Tp(0), xd[RS], xm[RS];
+#pragma unroll
+    for (int i = 0; i < RS; ++i) {
+        const int64_t r = r0 + i;
+        xd[i] = Tp(0);
+        xm[i] = Tp(0);
+        if (!live || r >= R) continue;
+        const Tp cr = (Tp)c[r], ic = Tp(1) / cr;
+        const Tp a = ra[i] * ic - Tp(1);   // eq. 7
+        const Tp b = rb[i] * ic;           // eq. 14
+        const Tp xr = x[i];
+        xm[i] = xr + a * xr;               // eq. 11
+        if (a < Tp(0)) {                   // eq. 15, gain floored at eps
+            const Tp xb = xr * b;
+            const Tp g = simt::dev_div(xb, xb - a);
+            xd[i] = xr * (g > eps ? g : eps);
+        } else {                           // eq. 17, step capped at alpha x
+            const Tp stp = b > Tp(0) ? simt::dev_div(a, b) : Tp(0);
+            const Tp cap = alpha * xr;
+            xd[i] = xr + (stp < cap ? stp : cap);
+        }
+        Xmu[r * O + o] = xm[i];
+        den += cr * xd[i];
+    }
+    red[ty][tx] = den;
+    __syncthreads();
+    if (ty == 0) {   // eq. 10 per column: the r groups' partials in ascending order
+        Tp tot = red[0][tx];
+        for (int g = 1; g < (int)blockDim.y; ++g) tot += red[g][tx];
+        scl[tx] = live ? (tot > Tp(0) ? (Tp)v.vsum[o] / tot : Tp(1)) : Tp(0);
+    }
+    __syncthreads();
+    const Tp sc = scl[tx];
+#pragma unroll
+    for (int i = 0; i < RS; ++i) {
+        xd[i] *= sc;
+        if (live && r0 + i < R) Xdna[(r0 + i) * O + o] = xd[i];
+    }
+    if constexpr (BF) {   // K-major bf16 rows [o][rp], o < O_pad, r < rp (zeros beyond)
+        if (r0 < rp) {
+#pragma unroll
+            for (int q = 0; q < RS; q += 8) {
+                uint32_t mh[4], dh[4], ml[4], dl[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float m0 = (float)xm[q + 2 * k], m1 = (float)xm[q + 2 * k + 1];
+                    const float d0 = (float)xd[q + 2 * k], d1 = (float)xd[q + 2 * k + 1];
+                    mh[k] = pack2(m0, m1);
+                    dh[k] = pack2(d0, d1);
+                    ml[k] = pack2(m0 - lo_half(mh[k]), m1 - hi_half(mh[k]));   // x - bf16(x)
+                    dl[k] = pack2(d0 - lo_half(dh[k]), d1 - hi_half(dh[k]));
+                }
+                const int64_t off = o * rp + r0 + q;
+                *reinterpret_cast<uint4*>(Xmk + off) = make_uint4(mh[0], mh[1], mh[2], mh[3]);
+                *reinterpret_cast<uint4*>(Xdk + off) = make_uint4(dh[0], dh[1], dh[2], dh[3]);
+                if (plane) {
+                    *reinterpret_cast<uint4*>(Xmk + plane + off) = make_uint4(ml[0], ml[1], ml[2], ml[3]);
+                    *reinterpret_cast<uint4*>(Xdk + plane + off) = make_uint4(dl[0], dl[1], dl[2], dl[3]);
+                }
+            }
+        }
+    }
+}
+
 // A[0][i] = A[0][i] + A[1][i] + ... + A[splits-1][i] (ascending, the order the candidates
 // kernel uses, so results are unchanged), and the same for B (may be null): the split
 // partials of pass 1 streamed once with wide loads before the candidates read them.

@@ -269,8 +269,34 @@ int Simt<Tp>::cand_fused(const View& v, const double* c, const Tp* A, const Tp* 
     const bool bf = Xmk != nullptr;
     if (bf && (sizeof(Tp) != 4 || !Xdk || rp < v.R || rp % 2 != 0 || O_pad < v.O))
         return DNA_ERR_ARG;
-    const size_t smem = glue::cand_smem<Tp>(v.R, bf);
     const unsigned grid = (unsigned)((bf ? O_pad : v.O) + glue::TO - 1) / glue::TO;
+    if (cand_in_registers(v.R) && (!bf || rp <= 16 * (v.R <= 128 ? 8 : 16))) {
+        // candidates of a thread in registers, at most 16 groups of r
+        const int rs = v.R <= 128 ? 8 : 16;
+        const int64_t rows = std::max<int64_t>((v.R + rs - 1) / rs, bf ? (rp + rs - 1) / rs : 0);
+        const dim3 blk(32, (unsigned)rows);
+        if (bf && rp % 8 != 0) return DNA_ERR_ARG;
+        if (bf) {
+            if constexpr (sizeof(Tp) == 4) {
+                auto* bm = static_cast<glue::bf16*>(Xmk);
+                auto* bd = static_cast<glue::bf16*>(Xdk);
+                if (rs == 8)
+                    glue::k_cand_reg<Tp, true, 8><<<grid, blk, 0, st>>>(
+                        v, c, A, B, splits, Xmu, Xdna, (Tp)eps, (Tp)alpha, bm, bd, rp, plane);
+                else
+                    glue::k_cand_reg<Tp, true, 16><<<grid, blk, 0, st>>>(
+                        v, c, A, B, splits, Xmu, Xdna, (Tp)eps, (Tp)alpha, bm, bd, rp, plane);
+            }
+        } else if (rs == 8) {
+            glue::k_cand_reg<Tp, false, 8><<<grid, blk, 0, st>>>(
+                v, c, A, B, splits, Xmu, Xdna, (Tp)eps, (Tp)alpha, nullptr, nullptr, 0, 0);
+        } else {
+            glue::k_cand_reg<Tp, false, 16><<<grid, blk, 0, st>>>(
+                v, c, A, B, splits, Xmu, Xdna, (Tp)eps, (Tp)alpha, nullptr, nullptr, 0, 0);
+        }
+        return simt::launch_status();
+    }
+    const size_t smem = glue::cand_smem<Tp>(v.R, bf);
     if (bf) {
         if constexpr (sizeof(Tp) == 4) {
             auto k = glue::k_cand_fused<Tp, true>;
@@ -287,6 +313,9 @@ int Simt<Tp>::cand_fused(const View& v, const double* c, const Tp* A, const Tp* 
     }
     return simt::launch_status();
 }
+
+template <typename Tp>
+bool Simt<Tp>::cand_in_registers(int64_t R) { return R <= (sizeof(Tp) == 8 ? 128 : 256); }
 
 template <typename Tp>
 int Simt<Tp>::split_sum(Tp* A, Tp* B, int64_t R, int64_t O, int splits, cudaStream_t st) {

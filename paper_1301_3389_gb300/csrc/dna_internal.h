@@ -146,7 +146,7 @@ struct TcOperands {
 // TMA descriptors of one half-step view (built once per bound problem).
 struct TcMaps {
     CUtensorMap x, y, yt, y2t, v, xm, xd;
-    CUtensorMap x_l, y_l, yt_l, y2t_l;   // lo planes (FP32 form on the tensor cores)
+    CUtensorMap x_l, y_l, yt_l, y2t_l, xm_l, xd_l;   // lo planes (FP32 form, tensor cores)
 };
 
 struct TcBf16 {
@@ -173,8 +173,10 @@ struct TcBf16 {
     static int pass1_split(const TcOperands& op, const TcMaps& maps, float* Apart,
                            float* Bpart, int splits, int64_t s_per, bool with_b, int* status,
                            cudaStream_t st);
-    static int pass2_split(const TcOperands& op, const TcMaps& maps, double* dpart, int splits,
-                           int64_t s_per, int* status, cudaStream_t st);
+    static int pass2_split(const TcOperands& op, const TcMaps& maps, double* dpart, int slots,
+                           int* status, cudaStream_t st);
+    // cost slots per column that pass2_split writes (4 per CTA that an o-block spans)
+    static int pass2_split_slots(int64_t O_pad, int64_t S, int ctas);
     static int chunk();
     static int oblock();
 };

@@ -1151,6 +1151,10 @@ int TcBf16::make_maps(TcMaps* m, const TcOperands& op, const float* V, int64_t v
         const bf16* y2tl = static_cast<const bf16*>(op.Y2tk) + op.plane;
         const bf16* xl = static_cast<const bf16*>(op.Xk) + op.plane;
         e = make_map(&m->x_l, BF, xl, rp, op.O_pad, rp * 2, 64, OBLK, SW);
+        if (!e) e = make_map(&m->xm_l, BF, static_cast<const bf16*>(Xmk) + op.plane, rp, op.O_pad,
+                             rp * 2, 64, OBLK, SW);
+        if (!e) e = make_map(&m->xd_l, BF, static_cast<const bf16*>(Xdk) + op.plane, rp, op.O_pad,
+                             rp * 2, 64, OBLK, SW);
         if (!e) e = make_map(&m->y_l, BF, yl, rp, op.S_pad, rp * 2, 64, SCH, SW);
         if (!e) e = make_map(&m->yt_l, BF, ytl, op.S_pad, rp, op.S_pad * 2, SCH, ytbox, SW);
         if (!e) e = make_map(&m->y2t_l, BF, y2tl, op.S_pad, rp, op.S_pad * 2, SCH, ytbox, SW);

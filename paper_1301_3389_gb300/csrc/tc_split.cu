@@ -459,13 +459,22 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
 // candidate (128 columns each) next to the four X planes; the epilogue copies both Z
 // into registers at the top of a chunk and frees them, so the MMAs of the next chunk run
 // while it computes.  One MMA-issuing warp per candidate.  Shared memory: G ring (Y hi /
-// lo of a chunk, 2 stages), V ring (3 half chunks); the per-warp cost sums reuse V stage
-// 0 at the end.
+// lo of a chunk, or the X planes of an o-block; 2 stages), V ring (3 half chunks).
+//
+// Persistent with balanced work: the units (o-block, chunk of 128 values of s) are
+// numbered o-block-major and CTA i takes the units [i U / G, (i + 1) U / G) (U units, G
+// CTAs), so every SM streams the same number of chunks.  A CTA's run splits into segments
+// of one o-block; at the start of a segment the X planes come through the G ring and go
+// into tensor memory by tcgen05.cp, at its end every epilogue thread writes its cost sums
+// to slot 4 q + cg of the o-block (q = the CTA's rank among the o-block's CTAs), and the
+// o-block's last CTA writes zeros into the slots no CTA uses: a fixed number of slots per
+// column for the selection kernel to add in order.
 template <int RP>
 struct P2SLayout {
     static constexpr int GST = 2, VST = 3;
     static constexpr uint32_t G_PLANE = SC2 * RP * 2;   // [RP / 64 atoms][128 s][64 r] bf16
     static constexpr uint32_t G_STAGE = 2 * G_PLANE;
+    static constexpr uint32_t X_PLANE = OBLK * RP * 2;  // [RP / 64 atoms][128 o][64 r] bf16
     static constexpr uint32_t V_STAGE = SCH * OBLK * 4;
     static constexpr uint32_t GR = 0;
     static constexpr uint32_t VR = GR + GST * G_STAGE;
@@ -475,22 +484,41 @@ struct P2SLayout {
     // tensor memory: Z_mu | Z_dna | X_mu hi | X_mu lo | X_dna hi | X_dna lo
     static constexpr uint32_t TX = 2 * SC2;
     static_assert(TX + 2 * RP <= NCOLS, "tensor memory budget");
+    static_assert(2 * X_PLANE <= G_STAGE, "one candidate's X planes fit a G stage");
     static_assert(G_PLANE % 1024 == 0 && VR % 1024 == 0, "tiles must be 1024-byte aligned");
-    static_assert(2 * 4 * OBLK * 8 <= V_STAGE, "cost sums fit a V stage");
     static_assert(TOTAL + 1024 <= 232448, "shared memory budget");
 };
 
 // ZFULL[c] / ZEMPTY[c]: Z of candidate c written / copied out (one phase per chunk);
-// GEMPTY[st]: both candidates' MMAs of the chunk in G stage st are done (2 arrivals).
-enum { T_XFULL = 0, T_GFULL = 1, T_GEMPTY = 3, T_VFULL = 5, T_VEMPTY = 8, T_ZFULL = 11,
-       T_ZEMPTY = 13, T_DRAIN = 15, T_COUNT = 17 };
+// GEMPTY[st]: both candidates' MMAs (or X copies) from G stage st are done (2 arrivals).
+enum { T_GFULL = 0, T_GEMPTY = 2, T_VFULL = 4, T_VEMPTY = 7, T_ZFULL = 10, T_ZEMPTY = 12,
+       T_DRAIN = 14, T_COUNT = 16 };
 
-// grid = (O_pad / 128, splits).  Writes the per-column costs of both candidates over the
-// split's s-range.
+// The CTA (of G) whose unit range [i U / G, (i + 1) U / G) holds unit u.
+__host__ __device__ __forceinline__ int p2s_cta_of(int64_t u, int64_t U, int G) {
+    return (int)(((u + 1) * G + U - 1) / U - 1);
+}
+
+// One CTA's walk over its units in G-ring order: per segment the two X units (MU, DNA
+// planes), then its chunks.
+struct P2SGCursor {
+    int64_t u, u1, nch;
+    int xu;   // 0, 1: X units of the segment starting at u; 2: chunk u
+    __device__ __forceinline__ bool done() const { return u >= u1; }
+    __device__ __forceinline__ void next() {
+        if (xu < 2) { ++xu; return; }          // X MU, X DNA, then chunk u
+        ++u;
+        xu = (u < u1 && u % nch == 0) ? 0 : 2;   // a new o-block: its X first
+    }
+};
+
 template <int RP>
 __global__ void __launch_bounds__(P1_THREADS, 1)
-    k_tc_pass2s(P2Args a, int64_t xplane, const __grid_constant__ CUtensorMap tmY,
-                const __grid_constant__ CUtensorMap tmYl, const __grid_constant__ CUtensorMap tmV) {
+    k_tc_pass2s(P2Args a, int64_t nch, int64_t U, int slots,
+                const __grid_constant__ CUtensorMap tmXm, const __grid_constant__ CUtensorMap tmXml,
+                const __grid_constant__ CUtensorMap tmXd, const __grid_constant__ CUtensorMap tmXdl,
+                const __grid_constant__ CUtensorMap tmY, const __grid_constant__ CUtensorMap tmYl,
+                const __grid_constant__ CUtensorMap tmV) {
     using L = P2SLayout<RP>;
     constexpr int GST = L::GST, VST = L::VST;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -502,14 +530,11 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
     volatile int* abort = reinterpret_cast<volatile int*>(sm + L::BAR + T_COUNT * 8 + 8);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int64_t o0 = (int64_t)blockIdx.x * OBLK;
-    const int64_t s_begin = (int64_t)blockIdx.y * a.s_per;
-    const int64_t s_end = min(a.S, s_begin + a.s_per);
-    const int nch = s_end > s_begin ? (int)((s_end - s_begin + SC2 - 1) / SC2) : 0;
+    const int G = (int)gridDim.x, me = (int)blockIdx.x;
+    const int64_t u0 = (int64_t)me * U / G, u1 = (int64_t)(me + 1) * U / G;
 
     if (warp == 0) { tmem_alloc(tslot, L::NCOLS); tmem_relinquish(); }
     if (tid == W_PRODUCER * 32) {
-        mbar_init(&bar[T_XFULL], W_EPI);
         for (int i = 0; i < VST; ++i) {
             mbar_init(&bar[T_VFULL + i], 1);
             mbar_init(&bar[T_VEMPTY + i], W_EPI);
@@ -530,34 +555,54 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
     const uint32_t tmem = *tslot;
 
     if (warp == W_PRODUCER) {
-        if (lane == 0 && nch > 0) {
-            tma_prefetch_desc(&tmY); tma_prefetch_desc(&tmYl); tma_prefetch_desc(&tmV);
-            const int nv = 2 * nch;
-            int kg = 0, kv = 0;
+        if (lane == 0 && u0 < u1) {
+            tma_prefetch_desc(&tmXm); tma_prefetch_desc(&tmXml); tma_prefetch_desc(&tmXd);
+            tma_prefetch_desc(&tmXdl); tma_prefetch_desc(&tmY); tma_prefetch_desc(&tmYl);
+            tma_prefetch_desc(&tmV);
+            P2SGCursor cg_{u0, u1, nch, 0};
+            int64_t uv = u0;   // V: half h of unit uv
+            int hv = 0, kg = 0, kv = 0;
             long long t0 = clock64();
-            while (kg < nch || kv < nv) {
+            while (!cg_.done() || uv < u1) {
                 bool prog = false;
-                if (kv < nv && mbar_test(&bar[T_VEMPTY + kv % VST], ((kv / VST) & 1) ^ 1)) {
+                if (uv < u1 && mbar_test(&bar[T_VEMPTY + kv % VST], ((kv / VST) & 1) ^ 1)) {
                     const int st = kv % VST;
+                    const int64_t ob = uv / nch, ck = uv % nch;
                     mbar_arrive_expect_tx(&bar[T_VFULL + st], L::V_STAGE);
-                    tma_load_2d(sbase + L::VR + st * L::V_STAGE, &tmV, (int32_t)o0,
-                                (int32_t)(s_begin + (int64_t)kv * SCH), &bar[T_VFULL + st]);
+                    tma_load_2d(sbase + L::VR + st * L::V_STAGE, &tmV, (int32_t)(ob * OBLK),
+                                (int32_t)(ck * SC2 + SCH * hv), &bar[T_VFULL + st]);
                     ++kv;
+                    if (++hv == 2) { hv = 0; ++uv; }
                     prog = true;
                 }
-                if (kg < nch && mbar_test(&bar[T_GEMPTY + kg % GST], ((kg / GST) & 1) ^ 1)) {
+                if (!cg_.done() && mbar_test(&bar[T_GEMPTY + kg % GST], ((kg / GST) & 1) ^ 1)) {
                     const int st = kg % GST;
                     const uint32_t dst = sbase + L::GR + st * L::G_STAGE;
-                    const int32_t s0 = (int32_t)(s_begin + (int64_t)kg * SC2);
-                    mbar_arrive_expect_tx(&bar[T_GFULL + st], L::G_STAGE);
-                    for (int at = 0; at < RP / 64; ++at)
-                        for (int hs = 0; hs < 2; ++hs) {
-                            const uint32_t off = at * SC2 * 128 + hs * SCH * 128;
-                            tma_load_2d(dst + off, &tmY, 64 * at, s0 + SCH * hs, &bar[T_GFULL + st]);
-                            tma_load_2d(dst + L::G_PLANE + off, &tmYl, 64 * at, s0 + SCH * hs,
+                    const int64_t ob = cg_.u / nch, ck = cg_.u % nch;
+                    if (cg_.xu < 2) {   // X hi and lo of candidate xu, [NA][128 o][64 r] each
+                        const CUtensorMap* mh = cg_.xu ? &tmXd : &tmXm;
+                        const CUtensorMap* ml = cg_.xu ? &tmXdl : &tmXml;
+                        mbar_arrive_expect_tx(&bar[T_GFULL + st], 2 * L::X_PLANE);
+                        for (int at = 0; at < RP / 64; ++at) {
+                            tma_load_2d(dst + at * OBLK * 128, mh, 64 * at, (int32_t)(ob * OBLK),
                                         &bar[T_GFULL + st]);
+                            tma_load_2d(dst + L::X_PLANE + at * OBLK * 128, ml, 64 * at,
+                                        (int32_t)(ob * OBLK), &bar[T_GFULL + st]);
                         }
+                    } else {
+                        const int32_t s0 = (int32_t)(ck * SC2);
+                        mbar_arrive_expect_tx(&bar[T_GFULL + st], L::G_STAGE);
+                        for (int at = 0; at < RP / 64; ++at)
+                            for (int hs = 0; hs < 2; ++hs) {
+                                const uint32_t off = at * SC2 * 128 + hs * SCH * 128;
+                                tma_load_2d(dst + off, &tmY, 64 * at, s0 + SCH * hs,
+                                            &bar[T_GFULL + st]);
+                                tma_load_2d(dst + L::G_PLANE + off, &tmYl, 64 * at, s0 + SCH * hs,
+                                            &bar[T_GFULL + st]);
+                            }
+                    }
                     ++kg;
+                    cg_.next();
                     prog = true;
                 }
                 if (prog) {
@@ -576,16 +621,40 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
             }
         }
     } else if (warp == W_MMA_Z || warp == W_MMA_AB) {
-        // candidate c: Z_c(m) = X_c Y(m)^t in the split form, products outer (see pass 1)
+        // candidate c: Z_c(m) = X_c Y(m)^t in the split form, products outer (see pass 1);
+        // at each segment start X_c (from the G unit of candidate c) into tensor memory
         const int c = warp == W_MMA_AB ? 1 : 0;
-        if (lane == 0 && nch > 0) {
-            bool ok = wait_phase(&bar[T_XFULL], 0, abort);
+        if (lane == 0 && u0 < u1) {
+            bool ok = true;
             const uint32_t xh = tmem + L::TX + (uint32_t)c * RP, xl = xh + RP / 2;
             const uint32_t tz = tmem + (uint32_t)c * SC2;
             constexpr uint32_t idesc = idesc_bf16(OBLK, SC2);
-            for (int m = 0; ok && m < nch; ++m) {
-                const int st = m % GST;
-                if (!(ok = wait_phase(&bar[T_GFULL + st], (m / GST) & 1, abort))) break;
+            int j = 0, m = 0;   // G units and chunks consumed
+            for (int64_t u = u0; ok && u < u1; ++u, ++m) {
+                if (u == u0 || u % nch == 0) {
+                    // this thread's previous MMAs have read the old X
+                    if (m >= 1 && !(ok = wait_phase(&bar[T_ZFULL + c], (m - 1) & 1, abort))) break;
+#pragma unroll 1
+                    for (int xu = 0; xu < 2; ++xu, ++j) {
+                        if (!(ok = wait_phase(&bar[T_GFULL + j % GST], (j / GST) & 1, abort))) break;
+                        if (xu == c) {
+                            tc_fence_after();
+                            const uint32_t xs = sbase + L::GR + (j % GST) * L::G_STAGE;
+#pragma unroll
+                            for (int pl = 0; pl < 2; ++pl)
+#pragma unroll
+                                for (int kk = 0; kk < RP / 16; ++kk)
+                                    tmem_cp_128x256b((pl ? xl : xh) + 8 * kk,
+                                                     desc_sw128(xs + pl * L::X_PLANE +
+                                                                (kk >> 2) * OBLK * 128 +
+                                                                32u * (kk & 3)));
+                        }
+                        mma_commit(&bar[T_GEMPTY + j % GST]);
+                    }
+                    if (!ok) break;
+                }
+                const int st = j % GST;
+                if (!(ok = wait_phase(&bar[T_GFULL + st], (j / GST) & 1, abort))) break;
                 // the epilogue has copied out Z_c of the previous chunk
                 if (m >= 1 && !(ok = wait_phase(&bar[T_ZEMPTY + c], (m - 1) & 1, abort))) break;
                 tc_fence_after();
@@ -601,6 +670,7 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
                     }
                 mma_commit(&bar[T_GEMPTY + st]);
                 mma_commit(&bar[T_ZFULL + c]);
+                ++j;
             }
             if (!ok) {
                 mma_commit(&bar[T_DRAIN + c]);
@@ -612,26 +682,13 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
         // s = 64 h + 16 cg .. + 15 of the chunk
         const int qd = warp & 3, cg = warp >> 2;
         const int row = 32 * qd + lane;
-        const int64_t o = o0 + row;
         const uint32_t lane_off = (uint32_t)(32 * qd) << 16;
-        if (nch > 0) {   // X_mu, X_dna (hi, lo) of this o-block into tensor memory
-            constexpr int UP = RP / 32;   // 16-column units per plane
-            for (int u = cg; u < 4 * UP; u += 4) {
-                const int mat = u / UP;   // 0 mu hi, 1 mu lo, 2 dna hi, 3 dna lo
-                const bf16* X = static_cast<const bf16*>(mat < 2 ? a.Xm : a.Xd) +
-                                ((mat & 1) ? xplane : 0);
-                x_to_tmem(X, a.rp, o, u % UP, tmem + L::TX + (uint32_t)mat * (RP / 2) + lane_off);
-            }
-            tmem_st_wait();
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&bar[T_XFULL]);
-        }
         double acc_m = 0.0, acc_d = 0.0;
-        bool ok = true;
-        for (int k = 0; k < nch; ++k) {
-            ok = wait_phase(&bar[T_ZFULL + 0], k & 1, abort);
-            ok = ok && wait_phase(&bar[T_ZFULL + 1], k & 1, abort);
+        bool ok = true, finite = true;
+        int m = 0;
+        for (int64_t u = u0; u < u1; ++u, ++m) {
+            ok = wait_phase(&bar[T_ZFULL + 0], m & 1, abort);
+            ok = ok && wait_phase(&bar[T_ZFULL + 1], m & 1, abort);
             if (!(ok = __all_sync(0xffffffffu, ok))) break;   // keep the warp converged
             tc_fence_after();
             const uint32_t tz = tmem + 16 * cg + lane_off;
@@ -650,17 +707,17 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
             float run_m = 0.f, run_d = 0.f;
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const int kv = 2 * k + h, vs = kv % VST;
+                const int kv = 2 * m + h, vs = kv % VST;
                 ok = wait_phase(&bar[T_VFULL + vs], (kv / VST) & 1, abort);
                 if (!(ok = __all_sync(0xffffffffu, ok))) break;
                 // V rows s = 16 cg + j of this half; TMA zero-fills v beyond S, where Y is
-                // zero too (z = 0, no cost); a split's s-range is a whole number of chunks
+                // zero too (z = 0, no cost)
                 const float* Vs = reinterpret_cast<const float*>(sm + L::VR + vs * L::V_STAGE) +
                                   16 * cg * OBLK + row;
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const float v = Vs[j * OBLK];
-                    const float z1 = __uint_as_float(zm[h][j]), z2 = __uint_as_float(zd[h][j]);
+                for (int jj = 0; jj < 16; ++jj) {
+                    const float v = Vs[jj * OBLK];
+                    const float z1 = __uint_as_float(zm[h][jj]), z2 = __uint_as_float(zd[h][jj]);
                     const bool pos = v > 0.f;
                     // the hardware logarithm (absolute error near 2^-21 around 1, relative
                     // 2^-21 elsewhere): well inside the split form's 1e-4 near-tie margin
@@ -673,25 +730,27 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
             if (!ok) break;
             acc_m += (double)run_m;
             acc_d += (double)run_d;
-        }
-        if (!(fabs(acc_m) < INFINITY && fabs(acc_d) < INFINITY))
-            atomicOr(a.status, STATUS_NONFINITE);
-        // cost sums of the four column groups: every V stage is consumed (or the CTA is
-        // aborting) once all epilogue warps are here
-        asm volatile("bar.sync 1, %0;" ::"r"(W_EPI * 32) : "memory");
-        double* red = reinterpret_cast<double*>(sm + L::VR);
-        red[(cg * 2 + 0) * OBLK + row] = acc_m;
-        red[(cg * 2 + 1) * OBLK + row] = acc_d;
-        asm volatile("bar.sync 1, %0;" ::"r"(W_EPI * 32) : "memory");
-        if (cg == 0 && ok && nch > 0 && !*abort && o < a.O) {
-            double m = red[0 * OBLK + row], d = red[1 * OBLK + row];
-            for (int g = 1; g < 4; ++g) {
-                m += red[(g * 2 + 0) * OBLK + row];
-                d += red[(g * 2 + 1) * OBLK + row];
+            // end of a segment: this thread's cost sums of the o-block into its slot
+            if ((u + 1) % nch == 0 || u + 1 == u1) {
+                const int64_t ob = u / nch, o = ob * OBLK + row;
+                finite = finite && fabs(acc_m) < INFINITY && fabs(acc_d) < INFINITY;
+                const int q = me - p2s_cta_of(ob * nch, U, G);
+                if (o < a.O) {
+                    a.dpart[((int64_t)(4 * q + cg) * 2 + 0) * a.O + o] = acc_m;
+                    a.dpart[((int64_t)(4 * q + cg) * 2 + 1) * a.O + o] = acc_d;
+                    // the o-block's last CTA: zeros in the slots no CTA of it uses
+                    const int last = p2s_cta_of((ob + 1) * nch - 1, U, G);
+                    if (me == last)
+                        for (int s = 4 * (q + 1) + cg; s < slots; s += 4) {
+                            a.dpart[((int64_t)s * 2 + 0) * a.O + o] = 0.0;
+                            a.dpart[((int64_t)s * 2 + 1) * a.O + o] = 0.0;
+                        }
+                }
+                acc_m = 0.0;
+                acc_d = 0.0;
             }
-            a.dpart[((int64_t)blockIdx.y * 2 + 0) * a.O + o] = m;
-            a.dpart[((int64_t)blockIdx.y * 2 + 1) * a.O + o] = d;
         }
+        if (!finite) atomicOr(a.status, STATUS_NONFINITE);
     }
     tc_fence_before();
     __syncthreads();
@@ -718,15 +777,18 @@ int launch_pass1s(const P1Args& a, bool with_b, const TcMaps& m, int64_t O_pad, 
 }
 
 template <int RP>
-int launch_pass2s(const P2Args& a, int64_t xplane, const TcMaps& m, int64_t O_pad, int splits,
+int launch_pass2s(const P2Args& a, const TcMaps& m, int64_t O_pad, int slots, int ctas,
                   cudaStream_t st) {
     const uint32_t smem = P2SLayout<RP>::TOTAL + 1024;
     auto k = k_tc_pass2s<RP>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return DNA_ERR_CUDA;
-    dim3 grid((unsigned)(O_pad / OBLK), (unsigned)splits);
-    k<<<grid, P1_THREADS, smem, st>>>(a, xplane, m.y, m.y_l, m.v);
+    const int64_t nch = (a.S + SC2 - 1) / SC2, U = (O_pad / OBLK) * nch;
+    if (U == 0) return DNA_OK;
+    const int grid = (int)std::min<int64_t>(ctas > 0 ? ctas : U, U);
+    k<<<grid, P1_THREADS, smem, st>>>(a, nch, U, slots, m.xm, m.xm_l, m.xd, m.xd_l, m.y, m.y_l,
+                                       m.v);
     return after_launch();
 }
 
@@ -745,15 +807,27 @@ int TcBf16::pass1_split(const TcOperands& op, const TcMaps& maps, float* Apart, 
     return DNA_ERR_UNSUPPORTED;
 }
 
-int TcBf16::pass2_split(const TcOperands& op, const TcMaps& maps, double* dpart, int splits,
-                        int64_t s_per, int* status, cudaStream_t st) {
+int TcBf16::pass2_split(const TcOperands& op, const TcMaps& maps, double* dpart, int slots,
+                        int* status, cudaStream_t st) {
     tc::P2Args a{};
-    a.S = op.S; a.O = op.O; a.R = op.R; a.s_per = s_per;
+    a.S = op.S; a.O = op.O; a.R = op.R; a.s_per = 0;
     a.dpart = dpart; a.status = status;
     a.V = op.V; a.vs = op.vs; a.Xm = op.Xmk; a.Xd = op.Xdk; a.rp = rank_pad(op.R);
-    if (a.rp == 64) return tc::launch_pass2s<64>(a, op.plane, maps, op.O_pad, splits, st);
-    if (a.rp == 128) return tc::launch_pass2s<128>(a, op.plane, maps, op.O_pad, splits, st);
+    if (slots != pass2_split_slots(op.O_pad, op.S, op.ctas)) return DNA_ERR_ARG;
+    if (a.rp == 64) return tc::launch_pass2s<64>(a, maps, op.O_pad, slots, op.ctas, st);
+    if (a.rp == 128) return tc::launch_pass2s<128>(a, maps, op.O_pad, slots, op.ctas, st);
     return DNA_ERR_UNSUPPORTED;
+}
+
+int TcBf16::pass2_split_slots(int64_t O_pad, int64_t S, int ctas) {
+    const int64_t nch = (S + tc::SC2 - 1) / tc::SC2, nob = O_pad / tc::OBLK, U = nob * nch;
+    if (U == 0) return 4;
+    const int G = (int)std::min<int64_t>(ctas > 0 ? ctas : U, U);
+    int most = 1;
+    for (int64_t ob = 0; ob < nob; ++ob)
+        most = std::max(most, tc::p2s_cta_of((ob + 1) * nch - 1, U, G) -
+                                  tc::p2s_cta_of(ob * nch, U, G) + 1);
+    return 4 * most;
 }
 
 }  // namespace dna

@@ -503,6 +503,17 @@ int kl_backward(dna_ctx* c, double scale, Tp* dW, Tp* dH, Tp* dV) {
 template <typename Tp>
 int kl_async(dna_ctx* c) {
     const View v = make_view(c, false);
+    if constexpr (sizeof(Tp) == 4)
+        if (c->split) {   // the split tensor-core pass 2 on the H view's current operands
+            if (int e = prep_step<Tp>(c, 0, false)) return e;
+            return phase(c, DNA_PHASE_KL, 2, [&] {
+                int e = dna::TcBf16::kl_split(tc_operands(c, 0), c->maps[0], c->dpart,
+                                              c->tsp2[0], c->status, c->stream);
+                return e ? e
+                         : dna::reduce_sum(c->dpart, (int64_t)c->tsp2[0] * c->T, c->kl_dev,
+                                           c->stream);
+            });
+        }
     return phase(c, DNA_PHASE_KL, 2, [&] {
         int e = dna::Simt<Tp>::kl_columns(v, c->dpart, c->sp2[0], c->per2[0], c->status, c->stream);
         return e ? e : dna::reduce_sum(c->dpart, (int64_t)c->sp2[0] * c->T, c->kl_dev, c->stream);

@@ -177,6 +177,10 @@ struct TcBf16 {
                            int* status, cudaStream_t st);
     // cost slots per column that pass2_split writes (4 per CTA that an o-block spans)
     static int pass2_split_slots(int64_t O_pad, int64_t S, int ctas);
+    // d_KL per column of the view (eq. 1 terms) from the X and Y operands in the split
+    // form: dpart[slot][O], `slots` = pass2_split_slots of the view
+    static int kl_split(const TcOperands& op, const TcMaps& maps, double* dpart, int slots,
+                        int* status, cudaStream_t st);
     static int chunk();
     static int oblock();
 };

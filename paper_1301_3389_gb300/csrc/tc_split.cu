@@ -512,7 +512,9 @@ struct P2SGCursor {
     }
 };
 
-template <int RP>
+// FULL: d_KL per column instead (eq. 1 terms z + v log(v / z) - v with the accurate
+// logarithm), both candidates = the current factor, slot layout [slot][O] of candidate 0.
+template <int RP, bool FULL>
 __global__ void __launch_bounds__(P1_THREADS, 1)
     k_tc_pass2s(P2Args a, int64_t nch, int64_t U, int slots,
                 const __grid_constant__ CUtensorMap tmXm, const __grid_constant__ CUtensorMap tmXml,
@@ -719,10 +721,15 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
                     const float v = Vs[jj * OBLK];
                     const float z1 = __uint_as_float(zm[h][jj]), z2 = __uint_as_float(zd[h][jj]);
                     const bool pos = v > 0.f;
-                    // the hardware logarithm (absolute error near 2^-21 around 1, relative
-                    // 2^-21 elsewhere): well inside the split form's 1e-4 near-tie margin
-                    run_m += pos ? z1 - v * __logf(z1) : z1;
-                    run_d += pos ? z2 - v * __logf(z2) : z2;
+                    if constexpr (FULL) {
+                        run_m += pos ? z1 + v * logf(v / z1) - v : z1;
+                    } else {
+                        // the hardware logarithm (absolute error near 2^-21 around 1,
+                        // relative 2^-21 elsewhere): well inside the split form's 1e-4
+                        // near-tie margin
+                        run_m += pos ? z1 - v * __logf(z1) : z1;
+                        run_d += pos ? z2 - v * __logf(z2) : z2;
+                    }
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&bar[T_VEMPTY + vs]);
@@ -731,7 +738,18 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
             acc_m += (double)run_m;
             acc_d += (double)run_d;
             // end of a segment: this thread's cost sums of the o-block into its slot
-            if ((u + 1) % nch == 0 || u + 1 == u1) {
+            if (FULL && ((u + 1) % nch == 0 || u + 1 == u1)) {
+                const int64_t ob = u / nch, o = ob * OBLK + row;
+                finite = finite && fabs(acc_m) < INFINITY;
+                const int q = me - p2s_cta_of(ob * nch, U, G);
+                if (o < a.O) {
+                    a.dpart[(int64_t)(4 * q + cg) * a.O + o] = acc_m;
+                    if (me == p2s_cta_of((ob + 1) * nch - 1, U, G))
+                        for (int s = 4 * (q + 1) + cg; s < slots; s += 4) a.dpart[(int64_t)s * a.O + o] = 0.0;
+                }
+                acc_m = 0.0;
+                acc_d = 0.0;
+            } else if ((u + 1) % nch == 0 || u + 1 == u1) {
                 const int64_t ob = u / nch, o = ob * OBLK + row;
                 finite = finite && fabs(acc_m) < INFINITY && fabs(acc_d) < INFINITY;
                 const int q = me - p2s_cta_of(ob * nch, U, G);
@@ -776,19 +794,23 @@ int launch_pass1s(const P1Args& a, bool with_b, const TcMaps& m, int64_t O_pad, 
     return after_launch();
 }
 
-template <int RP>
+template <int RP, bool FULL>
 int launch_pass2s(const P2Args& a, const TcMaps& m, int64_t O_pad, int slots, int ctas,
                   cudaStream_t st) {
     const uint32_t smem = P2SLayout<RP>::TOTAL + 1024;
-    auto k = k_tc_pass2s<RP>;
+    auto k = k_tc_pass2s<RP, FULL>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return DNA_ERR_CUDA;
     const int64_t nch = (a.S + SC2 - 1) / SC2, U = (O_pad / OBLK) * nch;
     if (U == 0) return DNA_OK;
     const int grid = (int)std::min<int64_t>(ctas > 0 ? ctas : U, U);
-    k<<<grid, P1_THREADS, smem, st>>>(a, nch, U, slots, m.xm, m.xm_l, m.xd, m.xd_l, m.y, m.y_l,
-                                       m.v);
+    // d_KL: both "candidates" are the current factor, the X operand of the view
+    const CUtensorMap& xm = FULL ? m.x : m.xm;
+    const CUtensorMap& xml = FULL ? m.x_l : m.xm_l;
+    const CUtensorMap& xd = FULL ? m.x : m.xd;
+    const CUtensorMap& xdl = FULL ? m.x_l : m.xd_l;
+    k<<<grid, P1_THREADS, smem, st>>>(a, nch, U, slots, xm, xml, xd, xdl, m.y, m.y_l, m.v);
     return after_launch();
 }
 
@@ -814,8 +836,20 @@ int TcBf16::pass2_split(const TcOperands& op, const TcMaps& maps, double* dpart,
     a.dpart = dpart; a.status = status;
     a.V = op.V; a.vs = op.vs; a.Xm = op.Xmk; a.Xd = op.Xdk; a.rp = rank_pad(op.R);
     if (slots != pass2_split_slots(op.O_pad, op.S, op.ctas)) return DNA_ERR_ARG;
-    if (a.rp == 64) return tc::launch_pass2s<64>(a, maps, op.O_pad, slots, op.ctas, st);
-    if (a.rp == 128) return tc::launch_pass2s<128>(a, maps, op.O_pad, slots, op.ctas, st);
+    if (a.rp == 64) return tc::launch_pass2s<64, false>(a, maps, op.O_pad, slots, op.ctas, st);
+    if (a.rp == 128) return tc::launch_pass2s<128, false>(a, maps, op.O_pad, slots, op.ctas, st);
+    return DNA_ERR_UNSUPPORTED;
+}
+
+int TcBf16::kl_split(const TcOperands& op, const TcMaps& maps, double* dpart, int slots,
+                     int* status, cudaStream_t st) {
+    tc::P2Args a{};
+    a.S = op.S; a.O = op.O; a.R = op.R; a.s_per = 0;
+    a.dpart = dpart; a.status = status;
+    a.V = op.V; a.vs = op.vs; a.rp = rank_pad(op.R);
+    if (slots != pass2_split_slots(op.O_pad, op.S, op.ctas)) return DNA_ERR_ARG;
+    if (a.rp == 64) return tc::launch_pass2s<64, true>(a, maps, op.O_pad, slots, op.ctas, st);
+    if (a.rp == 128) return tc::launch_pass2s<128, true>(a, maps, op.O_pad, slots, op.ctas, st);
     return DNA_ERR_UNSUPPORTED;
 }
 

@@ -39,6 +39,7 @@ struct dna_ctx {
     double* sig = nullptr;       // R
     double* fwork = nullptr;     // FSUM_SPLITS * R partial factor sums
     double* gpart = nullptr;     // [ceil(max(N, T) / 32)][R] partial sums of the fused glue
+    double* vpart = nullptr;     // per-tile column and row sums of V (prepare)
     void* Apart = nullptr;       // [splits][R][O]
     void* Bpart = nullptr;
     void* Xmu = nullptr;         // [R][O]
@@ -190,7 +191,7 @@ void plan_all(dna_ctx* c) {
 
 void free_all(dna_ctx* c) {
     void* ptrs[] = {c->own_V, c->own_W, c->own_H, c->Vt, c->colsum_v, c->rowsum_v, c->c, c->sig,
-                    c->fwork, c->gpart, c->Apart, c->Bpart, c->Xmu, c->Xdna, c->dpart, c->dfin_h, c->dfin_w,
+                    c->fwork, c->gpart, c->vpart, c->Apart, c->Bpart, c->Xmu, c->Xdna, c->dpart, c->dfin_h, c->dfin_w,
                     c->choice_h, c->choice_w, c->kl_dev, c->status, c->Xk, c->Yk, c->Ytk,
                     c->Y2tk, c->Xmk, c->Xdk, c->Vp};
     for (void* p : ptrs)
@@ -218,6 +219,7 @@ int alloc_workspace(dna_ctx* c) {
     e |= dmalloc(&c->sig, sizeof(double) * R);
     e |= dmalloc(&c->fwork, sizeof(double) * dna::FSUM_SPLITS * R);
     e |= dmalloc(&c->gpart, sizeof(double) * (size_t)(dna::Simt<Tp>::glue_parts(M) * R));
+    e |= dmalloc(&c->vpart, sizeof(double) * (size_t)(((N + 31) / 32) * T + ((T + 31) / 32) * N));
     e |= dmalloc(&c->Apart, sizeof(Tp) * (size_t)ap);
     e |= dmalloc(&c->Bpart, sizeof(Tp) * (size_t)ap);
     e |= dmalloc(&c->Xmu, sizeof(Tp) * (size_t)(R * M));
@@ -261,7 +263,7 @@ int prepare(dna_ctx* c) {
     return phase(c, DNA_PHASE_PREPARE, 3, [&] {
         return dna::Simt<Tp>::prepare_v(static_cast<const Tp*>(c->V), c->N, c->T, c->ldv,
                                         static_cast<Tp*>(c->Vt), c->ldvt, c->colsum_v,
-                                        c->rowsum_v, c->stream);
+                                        c->rowsum_v, c->stream, c->vpart);
     });
 }
 
@@ -569,8 +571,14 @@ namespace dna {
 
 __global__ void k_reduce_sum(const double* __restrict__ part, int64_t n, double* __restrict__ out) {
     __shared__ double red[1024];
-    double s = 0.0;
-    for (int64_t i = threadIdx.x; i < n; i += 1024) s += part[i];
+    // eight independent chains per thread (loads issued together), added in a fixed order
+    double s8[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    int64_t i = threadIdx.x;
+    for (; i + 7 * 1024 < n; i += 8 * 1024)
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s8[u] += part[i + u * 1024];
+    for (; i < n; i += 1024) s8[0] += part[i];
+    double s = ((s8[0] + s8[1]) + (s8[2] + s8[3])) + ((s8[4] + s8[5]) + (s8[6] + s8[7]));
     red[threadIdx.x] = s;
     __syncthreads();
     for (int w = 512; w > 0; w >>= 1) {

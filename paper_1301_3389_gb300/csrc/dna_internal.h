@@ -115,7 +115,8 @@ template <typename Tp> struct Simt {
     static int64_t glue_parts(int64_t n);   // partial sums per R of the fused glue
     // one-time: row and column sums of V (float64) and the transposed copy
     static int prepare_v(const Tp* V, int64_t N, int64_t T, int64_t ldv, Tp* Vt, int64_t ldvt,
-                         double* colsum, double* rowsum, cudaStream_t st);
+                         double* colsum, double* rowsum, cudaStream_t st,
+                         double* part = nullptr);
     // how many CTAs of pass 1 / pass 2 fit on one SM
     static int pass1_blocks_per_sm(int64_t R);
     static int pass2_blocks_per_sm(int64_t R);

@@ -892,5 +892,41 @@ __global__ void k_transpose(const Tp* __restrict__ V, int64_t N, int64_t T, int6
     }
 }
 
+
+// k_transpose fused with the column and row sums of V: per 32 x 32 tile the sums of its
+// 32 rows (colpart[n-tile][t]) and of its 32 columns (rowpart[t-tile][n]), in the element
+// type (exact for counts), for k_colsum_final to add up in float64.
+template <typename Tp>
+__global__ void __launch_bounds__(256) k_transpose_sums(const Tp* __restrict__ V, int64_t N,
+                                                        int64_t T, int64_t ldv,
+                                                        Tp* __restrict__ Vt, int64_t ldvt,
+                                                        double* __restrict__ colpart,
+                                                        double* __restrict__ rowpart) {
+    __shared__ Tp tile[32][33];
+    const int64_t n0 = (int64_t)blockIdx.y * 32, t0 = (int64_t)blockIdx.x * 32;
+    for (int k = threadIdx.y; k < 32; k += 8) {
+        const int64_t n = n0 + k, t = t0 + threadIdx.x;
+        tile[k][threadIdx.x] = (n < N && t < T) ? V[n * ldv + t] : Tp(0);
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += 8) {
+        const int64_t t = t0 + k, n = n0 + threadIdx.x;
+        if (t < T && n < N) Vt[t * ldvt + n] = tile[threadIdx.x][k];
+    }
+    if (threadIdx.y == 0) {          // column t0 + lane: sum over the tile's rows
+        Tp sum = Tp(0);
+#pragma unroll 8
+        for (int k = 0; k < 32; ++k) sum += tile[k][threadIdx.x];
+        const int64_t t = t0 + threadIdx.x;
+        if (t < T) colpart[(int64_t)blockIdx.y * T + t] = (double)sum;
+    } else if (threadIdx.y == 1) {   // row n0 + lane: sum over the tile's columns
+        Tp sum = Tp(0);
+#pragma unroll 8
+        for (int k = 0; k < 32; ++k) sum += tile[threadIdx.x][k];
+        const int64_t n = n0 + threadIdx.x;
+        if (n < N) rowpart[(int64_t)blockIdx.x * N + n] = (double)sum;
+    }
+}
+
 }  // namespace simt
 }  // namespace dna

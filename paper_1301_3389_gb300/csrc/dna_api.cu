@@ -50,6 +50,7 @@ struct dna_ctx {
     uint8_t* choice_h = nullptr; // T
     uint8_t* choice_w = nullptr; // N
     double* kl_dev = nullptr;    // 1
+    double* kl_part = nullptr;   // REDUCE_PARTS partial sums of d_KL
     int* status = nullptr;       // 1
     // split plans (pass 1 and pass 2 / KL) for the H view and the W view
     int sp1[2] = {1, 1}, sp2[2] = {1, 1};
@@ -192,7 +193,7 @@ void plan_all(dna_ctx* c) {
 void free_all(dna_ctx* c) {
     void* ptrs[] = {c->own_V, c->own_W, c->own_H, c->Vt, c->colsum_v, c->rowsum_v, c->c, c->sig,
                     c->fwork, c->gpart, c->vpart, c->Apart, c->Bpart, c->Xmu, c->Xdna, c->dpart, c->dfin_h, c->dfin_w,
-                    c->choice_h, c->choice_w, c->kl_dev, c->status, c->Xk, c->Yk, c->Ytk,
+                    c->choice_h, c->choice_w, c->kl_dev, c->kl_part, c->status, c->Xk, c->Yk, c->Ytk,
                     c->Y2tk, c->Xmk, c->Xdk, c->Vp};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -230,6 +231,7 @@ int alloc_workspace(dna_ctx* c) {
     e |= dmalloc(&c->choice_h, (size_t)T);
     e |= dmalloc(&c->choice_w, (size_t)N);
     e |= dmalloc(&c->kl_dev, sizeof(double));
+    e |= dmalloc(&c->kl_part, sizeof(double) * (size_t)dna::REDUCE_PARTS);
     e |= dmalloc(&c->status, sizeof(int));
     if (c->tc) {
         const int64_t mo = std::max(c->pad_o[0], c->pad_o[1]);
@@ -513,12 +515,14 @@ int kl_async(dna_ctx* c) {
                                               c->tsp2[0], c->status, c->stream);
                 return e ? e
                          : dna::reduce_sum(c->dpart, (int64_t)c->tsp2[0] * c->T, c->kl_dev,
-                                           c->stream);
+                                           c->kl_part, c->stream);
             });
         }
     return phase(c, DNA_PHASE_KL, 2, [&] {
         int e = dna::Simt<Tp>::kl_columns(v, c->dpart, c->sp2[0], c->per2[0], c->status, c->stream);
-        return e ? e : dna::reduce_sum(c->dpart, (int64_t)c->sp2[0] * c->T, c->kl_dev, c->stream);
+        return e ? e
+                 : dna::reduce_sum(c->dpart, (int64_t)c->sp2[0] * c->T, c->kl_dev, c->kl_part,
+                                   c->stream);
     });
 }
 
@@ -569,27 +573,36 @@ int phase(dna_ctx* c, int ph, int nlaunch, F&& f) {
 
 namespace dna {
 
-__global__ void k_reduce_sum(const double* __restrict__ part, int64_t n, double* __restrict__ out) {
-    __shared__ double red[1024];
-    // eight independent chains per thread (loads issued together), added in a fixed order
-    double s8[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    int64_t i = threadIdx.x;
-    for (; i + 7 * 1024 < n; i += 8 * 1024)
-#pragma unroll
-        for (int u = 0; u < 8; ++u) s8[u] += part[i + u * 1024];
-    for (; i < n; i += 1024) s8[0] += part[i];
-    double s = ((s8[0] + s8[1]) + (s8[2] + s8[3])) + ((s8[4] + s8[5]) + (s8[6] + s8[7]));
-    red[threadIdx.x] = s;
+// out[b] = sum of part[b * per .. min(n, (b + 1) * per)), one CTA of 256 threads per b:
+// strided per-thread sums, then a fixed tree.
+__global__ void k_reduce_sum(const double* __restrict__ part, int64_t n, int64_t per,
+                             double* __restrict__ out) {
+    __shared__ double red[256];
+    const int64_t i0 = (int64_t)blockIdx.x * per, i1 = min(n, i0 + per);
+    double s0 = 0.0, s1 = 0.0;
+    int64_t i = i0 + threadIdx.x;
+    for (; i + 256 < i1; i += 512) { s0 += part[i]; s1 += part[i + 256]; }
+    if (i < i1) s0 += part[i];
+    red[threadIdx.x] = s0 + s1;
     __syncthreads();
-    for (int w = 512; w > 0; w >>= 1) {
+    for (int w = 128; w > 0; w >>= 1) {
         if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
         __syncthreads();
     }
-    if (threadIdx.x == 0) *out = red[0];
+    if (threadIdx.x == 0) out[blockIdx.x] = red[0];
 }
 
-int reduce_sum(const double* part, int64_t n, double* out, cudaStream_t st) {
-    k_reduce_sum<<<1, 1024, 0, st>>>(part, n, out);
+// Two levels: up to REDUCE_PARTS CTA sums into `work`, then one CTA over those.
+int reduce_sum(const double* part, int64_t n, double* out, double* work, cudaStream_t st) {
+    const int64_t per = std::max<int64_t>(4096, (n + REDUCE_PARTS - 1) / REDUCE_PARTS);
+    const int64_t blocks = (n + per - 1) / per;
+    if (blocks <= 1) {
+        k_reduce_sum<<<1, 256, 0, st>>>(part, n, std::max<int64_t>(n, 1), out);
+        return after_launch();
+    }
+    k_reduce_sum<<<(unsigned)blocks, 256, 0, st>>>(part, n, per, work);
+    if (int e = after_launch()) return e;
+    k_reduce_sum<<<1, 256, 0, st>>>(work, blocks, blocks, out);
     return after_launch();
 }
 

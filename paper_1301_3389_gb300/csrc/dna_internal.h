@@ -187,6 +187,8 @@ struct TcBf16 {
 };
 
 // sum of dpart[0 .. n) in a fixed order into *out (float64)
-int reduce_sum(const double* part, int64_t n, double* out, cudaStream_t st);
+// sum of part[0 .. n) into *out in a fixed order (work: REDUCE_PARTS doubles)
+constexpr int64_t REDUCE_PARTS = 256;
+int reduce_sum(const double* part, int64_t n, double* out, double* work, cudaStream_t st);
 
 }  // namespace dna

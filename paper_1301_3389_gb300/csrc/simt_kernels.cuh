@@ -802,18 +802,11 @@ __global__ void __launch_bounds__(1024) k_colsum_final(const double* __restrict_
     __shared__ double red[32][33];
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int64_t r = (int64_t)blockIdx.x * 32 + tx;
-    // the first 16 partials of the thread loaded together, then summed in ascending k
-    double pv[16];
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-        const int k = ty + 32 * j;
-        pv[j] = (r < R && k < nsplit) ? part[(int64_t)k * R + r] : 0.0;
-    }
     double t = 0.0;
-#pragma unroll
-    for (int j = 0; j < 16; ++j) t += pv[j];
-    if (r < R)
-        for (int k = ty + 32 * 16; k < nsplit; k += 32) t += part[(int64_t)k * R + r];
+    if (r < R) {
+#pragma unroll 4
+        for (int k = ty; k < nsplit; k += 32) t += part[(int64_t)k * R + r];
+    }
     red[ty][tx] = t;
     __syncthreads();
     if (ty == 0 && r < R) {

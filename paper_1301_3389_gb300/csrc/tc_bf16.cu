@@ -1,25 +1,24 @@
 // tcgen05 tensor-core kernels of the DNA half-step, BF16 operands with FP32 accumulation
-// in TMEM (the precision form), for padded rank RP in {64, 128}; the K-streamed variants
-// near the end of the file take RP in {256, 512}.
+// in TMEM (the precision form): pass 1 for padded rank RP in {64, 128}, and the K-streamed
+// passes 1 and 2 for RP in {256, 512} near the end of the file.  Pass 2 at RP <= 128 is
+// the balanced kernel of tc_split.cu, which takes the BF16 form with one operand plane.
 //
 // Pass 1 (Algorithm 1 steps 2-5 and 10), per CTA = 128 values of o (the TMEM lanes) and
 // an s-range streamed in chunks of 64:
 //   GEMM1  Z[o, s]  = sum_r X[o, r] Y[s, r]            M = 128, N = 64, K = RP
-//   epilogue (warps 0-7; warp w reads TMEM lanes 32 (w % 4) .. + 31, i.e. 32 values of o,
-//          and the 32 chunk columns 32 (w / 4) .. + 31): z from TMEM, v from shared memory,
-//          q = v / z, qbar = q / z (0 where v = 0), rounded to bf16 into shared memory
+//   epilogue (16 warps; warp w reads TMEM lanes 32 (w % 4) .. + 31, i.e. 32 values of o,
+//          and 16 chunk columns): z from TMEM, v from shared memory, q = v / z,
+//          qbar = q / z (0 where v = 0), rounded to bf16 into tensor memory
 //   GEMM2  A[o, r] += sum_s Q[o, s] Yt[r, s]           M = 128, N = RP, K = 64
 //   GEMM3  B[o, r] += sum_s Qbar[o, s] Y2t[r, s]       (Y2t = (Y o Y)^t)
 // A and B stay in TMEM for the whole s-range; Z and Q never reach global memory.
-// Pass 2 (steps 7-9, 12-14): Zmu = Xmu Y^t and Zdna = Xdna Y^t into TMEM, then per lane
-// (= column o) the cost terms -v log z + z, summed in float32 over a chunk and in float64
-// across chunks.
 //
-// Both passes are warp-specialised pipelines: warp 8 issues TMA copies into a two-stage
-// ring (Y and V tiles; Y^t and (Y o Y)^t tiles), one thread of warp 9 issues the MMAs,
-// warps 0-7 run the epilogue.  Z is double-buffered in TMEM so GEMM1 of the next chunk
-// overlaps the epilogue of this one.  Every hand-off is an mbarrier; every wait is
-// bounded and aborts the CTA (with DNA_ERR_TIMEOUT reported) instead of hanging.
+// The kernels are warp-specialised pipelines: a producer warp issues TMA copies into
+// rings (V, Y, Y^t and (Y o Y)^t tiles), MMA-issuing warps (one thread each) issue the
+// tcgen05 MMAs, the epilogue warps read Z from TMEM.  Z is double-buffered in TMEM so
+// GEMM1 of the next chunk overlaps the epilogue of this one.  Every hand-off is an
+// mbarrier; every wait is bounded and aborts the CTA (with DNA_ERR_TIMEOUT reported)
+// instead of hanging.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -311,226 +310,6 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
                         if (r < a.R) dst[(base + r) * a.O + o] = __uint_as_float(r32[i]);
                     }
             }
-        }
-    }
-    tc_fence_before();
-    __syncthreads();
-    if (tid == 0 && *abort) atomicOr(a.status, STATUS_TIMEOUT);
-    if (warp == 0) tmem_dealloc(tmem, L::NCOLS);
-}
-
-// Pass 2.  Shared memory: V ring (4 stages), Y ring (2 stages), the per-warp cost sums.
-// Tensor memory: two buffers of (Z_mu, Z_dna), 64 columns each, then X_mu and X_dna.  One
-// MMA-issuing warp per candidate (Z_mu and Z_dna are independent GEMM chains).
-template <int RP>
-struct P2Layout {
-    static constexpr int VST = 4, YST = 2;
-    static constexpr uint32_t V_BYTES = SCH * OBLK * 4;
-    static constexpr uint32_t Y_BYTES = SCH * RP * 2;
-    static constexpr uint32_t VR = 0;
-    static constexpr uint32_t YR = VR + VST * V_BYTES;
-    static constexpr uint32_t RED = YR + YST * Y_BYTES;   // [4 column groups][2][128] float64
-    static constexpr uint32_t BAR = RED + 4 * 2 * OBLK * 8;
-    static constexpr uint32_t TOTAL = BAR + 256;
-    static constexpr uint32_t NCOLS = 512;
-    static constexpr uint32_t TXM = 4 * SCH, TXD = TXM + RP / 2;
-    static_assert(TXD + RP / 2 <= NCOLS, "tensor memory budget");
-    static_assert(YR % 1024 == 0 && Y_BYTES % 1024 == 0, "tiles must be 1024-byte aligned");
-    static_assert(TOTAL + 1024 <= 232448, "shared memory budget");
-};
-
-// ZFULL[c][b]: the GEMM of candidate c (0 = MU, 1 = DNA) for chunk m (m % 2 == b) is done;
-// both together also free the Y stage of chunk m.
-enum { C_XFULL = 0, C_VFULL = 1, C_VEMPTY = 5, C_YFULL = 9, C_ZFULL = 11, C_ZEMPTY = 15,
-       C_DRAIN = 17, C_COUNT = 19 };
-
-template <int RP>
-__global__ void __launch_bounds__(P1_THREADS, 1)
-    k_tc_pass2(P2Args a, const __grid_constant__ CUtensorMap tmY,
-               const __grid_constant__ CUtensorMap tmV) {
-    using L = P2Layout<RP>;
-    constexpr int VST = L::VST, YST = L::YST;
-    static_assert(YST == 2, "stage reuse is signalled by the 2-deep commit barriers");
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char* sm = reinterpret_cast<unsigned char*>(
-        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    const uint32_t sbase = smem_u32(sm);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + L::BAR);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L::BAR + C_COUNT * 8);
-    volatile int* abort = reinterpret_cast<volatile int*>(sm + L::BAR + C_COUNT * 8 + 8);
-
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int64_t o0 = (int64_t)blockIdx.x * OBLK;
-    const int64_t s_begin = (int64_t)blockIdx.y * a.s_per;
-    const int64_t s_end = min(a.S, s_begin + a.s_per);
-    const int nch = s_end > s_begin ? (int)((s_end - s_begin + SCH - 1) / SCH) : 0;
-
-    if (warp == 0) { tmem_alloc(tslot, L::NCOLS); tmem_relinquish(); }
-    if (tid == W_PRODUCER * 32) {
-        mbar_init(&bar[C_XFULL], W_EPI);
-        for (int i = 0; i < VST; ++i) {
-            mbar_init(&bar[C_VFULL + i], 1);
-            mbar_init(&bar[C_VEMPTY + i], W_EPI);
-        }
-        for (int i = 0; i < 2; ++i) {
-            mbar_init(&bar[C_YFULL + i], 1);
-            mbar_init(&bar[C_ZFULL + i], 1);
-            mbar_init(&bar[C_ZFULL + 2 + i], 1);
-            mbar_init(&bar[C_ZEMPTY + i], W_EPI);
-            mbar_init(&bar[C_DRAIN + i], 1);
-        }
-        *abort = 0;
-        fence_mbar_init();
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = *tslot;
-
-    if (warp == W_PRODUCER) {
-        if (lane == 0 && nch > 0) {
-            tma_prefetch_desc(&tmY);
-            tma_prefetch_desc(&tmV);
-            int kv = 0, ky = 0;
-            long long t0 = clock64();
-            while (kv < nch || ky < nch) {
-                bool prog = false;
-                if (kv < nch && mbar_test(&bar[C_VEMPTY + kv % VST], ((kv / VST) & 1) ^ 1)) {
-                    const int st = kv % VST;
-                    mbar_arrive_expect_tx(&bar[C_VFULL + st], L::V_BYTES);
-                    tma_load_2d(sbase + L::VR + st * L::V_BYTES, &tmV, (int32_t)o0,
-                                (int32_t)(s_begin + (int64_t)kv * SCH), &bar[C_VFULL + st]);
-                    ++kv;
-                    prog = true;
-                }
-                // Y(ky) reuses the stage of chunk m = ky - 2, free once both GEMMs of m are done
-                if (ky < nch &&
-                    (ky < YST || (mbar_test(&bar[C_ZFULL + (ky & 1)], ((ky - 2) >> 1) & 1) &&
-                                  mbar_test(&bar[C_ZFULL + 2 + (ky & 1)], ((ky - 2) >> 1) & 1)))) {
-                    const int st = ky % YST;
-                    const uint32_t dst = sbase + L::YR + st * L::Y_BYTES;
-                    mbar_arrive_expect_tx(&bar[C_YFULL + st], L::Y_BYTES);
-                    for (int at = 0; at < RP / 64; ++at)
-                        tma_load_2d(dst + at * SCH * 128, &tmY, 64 * at,
-                                    (int32_t)(s_begin + (int64_t)ky * SCH), &bar[C_YFULL + st]);
-                    ++ky;
-                    prog = true;
-                }
-                if (prog) {
-                    t0 = clock64();
-                } else {
-                    if (*abort) break;
-                    if (clock64() - t0 > WAIT_LIMIT) { *abort = 1; break; }
-                    __nanosleep(20);
-                }
-            }
-            if (*abort) {
-                for (int k = max(0, kv - VST); k < kv; ++k)
-                    drain_phase(&bar[C_VFULL + k % VST], (k / VST) & 1);
-                for (int k = max(0, ky - YST); k < ky; ++k)
-                    drain_phase(&bar[C_YFULL + k % YST], (k / YST) & 1);
-            }
-        }
-    } else if (warp == W_MMA_Z || warp == W_MMA_AB) {
-        // candidate c: Z_c(m) = X_c Y(m)^t into buffer m & 1, A = X_c in TMEM
-        const int c = warp == W_MMA_AB ? 1 : 0;
-        if (lane == 0 && nch > 0) {
-            bool ok = wait_phase(&bar[C_XFULL], 0, abort);
-            for (int m = 0; ok && m < nch; ++m) {
-                const int zb = m & 1;
-                if (!(ok = wait_phase(&bar[C_YFULL + m % YST], (m / YST) & 1, abort))) break;
-                if (m >= 2 &&
-                    !(ok = wait_phase(&bar[C_ZEMPTY + zb], ((m >> 1) & 1) ^ 1, abort)))
-                    break;
-                tc_fence_after();
-                const uint32_t yb = sbase + L::YR + (m % YST) * L::Y_BYTES;
-                const uint32_t tz = tmem + zb * 2 * SCH + c * SCH;
-                const uint32_t tx = tmem + (c ? L::TXD : L::TXM);
-#pragma unroll
-                for (int kk = 0; kk < RP / 16; ++kk) {
-                    const uint32_t kb = 32u * kk, at = kb >> 7, within = kb & 127u;
-                    mma_bf16_tmem_a(tz, tx + 8 * kk, desc_sw128(yb + at * SCH * 128 + within),
-                                    idesc_bf16(OBLK, SCH), kk > 0);
-                }
-                mma_commit(&bar[C_ZFULL + 2 * c + zb]);
-            }
-            if (!ok) {
-                mma_commit(&bar[C_DRAIN + c]);
-                drain_phase(&bar[C_DRAIN + c], 0);
-            }
-        }
-    } else {
-        const int qd = warp & 3, cg = warp >> 2;
-        const int row = 32 * qd + lane;
-        const int64_t o = o0 + row;
-        const uint32_t lane_off = (uint32_t)(32 * qd) << 16;
-        if (nch > 0) {   // X_mu and X_dna of this o-block into tensor memory
-            constexpr int UPM = RP / 32;
-            for (int u = cg; u < 2 * UPM; u += 4) {
-                const bool isd = u >= UPM;
-                x_to_tmem(static_cast<const bf16*>(isd ? a.Xd : a.Xm), a.rp, o,
-                          isd ? u - UPM : u, tmem + (isd ? L::TXD : L::TXM) + lane_off);
-            }
-            tmem_st_wait();
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&bar[C_XFULL]);
-        }
-        double acc_m = 0.0, acc_d = 0.0;
-        bool ok = true;
-        for (int k = 0; k < nch; ++k) {
-            const int zb = k & 1, vs = k % VST;
-            const uint32_t zpar = (k >> 1) & 1;
-            ok = wait_phase(&bar[C_ZFULL + zb], zpar, abort);
-            ok = ok && wait_phase(&bar[C_ZFULL + 2 + zb], zpar, abort);
-            ok = ok && wait_phase(&bar[C_VFULL + vs], (k / VST) & 1, abort);
-            if (!(ok = __all_sync(0xffffffffu, ok))) break;   // keep the warp converged
-            tc_fence_after();
-            const uint32_t tz = tmem + zb * 2 * SCH + lane_off + 16 * cg;
-            uint32_t zm[16], zd[16];
-            tmem_ld16(tz, zm);
-            tmem_ld16(tz + SCH, zd);
-            const float* Vs = reinterpret_cast<const float*>(sm + L::VR + vs * L::V_BYTES) +
-                              16 * cg * OBLK + row;
-            float vv[16];
-#pragma unroll
-            for (int j = 0; j < 16; ++j) vv[j] = Vs[j * OBLK];
-            tmem_ld_wait();
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&bar[C_ZEMPTY + zb]);
-            float run_m = 0.f, run_d = 0.f;
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const float v = vv[j];
-                const float z1 = __uint_as_float(zm[j]), z2 = __uint_as_float(zd[j]);
-                const bool pos = v > 0.f;
-                const float l1 = __logf(z1), l2 = __logf(z2);
-                run_m += pos ? z1 - v * l1 : z1;
-                run_d += pos ? z2 - v * l2 : z2;
-            }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&bar[C_VEMPTY + vs]);
-            acc_m += (double)run_m;
-            acc_d += (double)run_d;
-        }
-        // z <= 0 under v > 0 makes log z NaN or -inf, a NaN z propagates: either way the
-        // cost sums are not finite
-        if (!(fabs(acc_m) < INFINITY && fabs(acc_d) < INFINITY))
-            atomicOr(a.status, STATUS_NONFINITE);
-        // combine the four column groups of each o in a fixed order
-        double* red = reinterpret_cast<double*>(sm + L::RED);
-        red[(cg * 2 + 0) * OBLK + row] = acc_m;
-        red[(cg * 2 + 1) * OBLK + row] = acc_d;
-        asm volatile("bar.sync 1, %0;" ::"r"(W_EPI * 32) : "memory");
-        if (cg == 0 && ok && nch > 0 && !*abort && o < a.O) {
-            double m = red[0 * OBLK + row], d = red[1 * OBLK + row];
-            for (int g = 1; g < 4; ++g) {
-                m += red[(g * 2 + 0) * OBLK + row];
-                d += red[(g * 2 + 1) * OBLK + row];
-            }
-            a.dpart[((int64_t)blockIdx.y * 2 + 0) * a.O + o] = m;
-            a.dpart[((int64_t)blockIdx.y * 2 + 1) * a.O + o] = d;
         }
     }
     tc_fence_before();
@@ -1111,18 +890,6 @@ int launch_pass2_ks(const P2Args& a, const TcMaps& m, int64_t O_pad, int splits,
     return after_launch();
 }
 
-template <int RP>
-int launch_pass2(const P2Args& a, const TcMaps& m, int64_t O_pad, int splits, cudaStream_t st) {
-    const uint32_t smem = P2Layout<RP>::TOTAL + 1024;
-    auto k = k_tc_pass2<RP>;
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-        return DNA_ERR_CUDA;
-    dim3 grid((unsigned)(O_pad / OBLK), (unsigned)splits);
-    k<<<grid, P1_THREADS, smem, st>>>(a, m.y, m.v);
-    return after_launch();
-}
-
 }  // namespace tc
 
 int TcBf16::rank_pad(int64_t R) {
@@ -1212,8 +979,7 @@ int TcBf16::pass2(const TcOperands& op, const TcMaps& maps, double* dpart, int s
     a.dpart = dpart; a.status = status;
     a.V = op.V; a.vs = op.vs; a.Xm = op.Xmk; a.Xd = op.Xdk; a.rp = rank_pad(op.R);
     const int rp = rank_pad(op.R);
-    if (rp == 64) return tc::launch_pass2<64>(a, maps, op.O_pad, splits, st);
-    if (rp == 128) return tc::launch_pass2<128>(a, maps, op.O_pad, splits, st);
+    // RP <= 128: pass2_split (tc_split.cu) takes both forms
     if (rp == 256) return tc::launch_pass2_ks<256>(a, maps, op.O_pad, splits, st);
     if (rp == 512) return tc::launch_pass2_ks<512>(a, maps, op.O_pad, splits, st);
     return DNA_ERR_UNSUPPORTED;

@@ -469,11 +469,11 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
 // to slot 4 q + cg of the o-block (q = the CTA's rank among the o-block's CTAs), and the
 // o-block's last CTA writes zeros into the slots no CTA uses: a fixed number of slots per
 // column for the selection kernel to add in order.
-template <int RP>
+template <int RP, int NP>
 struct P2SLayout {
     static constexpr int GST = 2, VST = 3;
     static constexpr uint32_t G_PLANE = SC2 * RP * 2;   // [RP / 64 atoms][128 s][64 r] bf16
-    static constexpr uint32_t G_STAGE = 2 * G_PLANE;
+    static constexpr uint32_t G_STAGE = NP * G_PLANE;
     static constexpr uint32_t X_PLANE = OBLK * RP * 2;  // [RP / 64 atoms][128 o][64 r] bf16
     static constexpr uint32_t V_STAGE = SCH * OBLK * 4;
     static constexpr uint32_t GR = 0;
@@ -481,10 +481,10 @@ struct P2SLayout {
     static constexpr uint32_t BAR = VR + VST * V_STAGE;
     static constexpr uint32_t TOTAL = BAR + 256;
     static constexpr uint32_t NCOLS = 512;
-    // tensor memory: Z_mu | Z_dna | X_mu hi | X_mu lo | X_dna hi | X_dna lo
-    static constexpr uint32_t TX = 2 * SC2;
-    static_assert(TX + 2 * RP <= NCOLS, "tensor memory budget");
-    static_assert(2 * X_PLANE <= G_STAGE, "one candidate's X planes fit a G stage");
+    // tensor memory: Z_mu | Z_dna | X_mu hi (| X_mu lo) | X_dna hi (| X_dna lo)
+    static constexpr uint32_t TX = 2 * SC2, XC = NP * RP / 2;   // XC: columns per candidate
+    static_assert(TX + 2 * XC <= NCOLS, "tensor memory budget");
+    static_assert(NP * X_PLANE <= G_STAGE, "one candidate's X planes fit a G stage");
     static_assert(G_PLANE % 1024 == 0 && VR % 1024 == 0, "tiles must be 1024-byte aligned");
     static_assert(TOTAL + 1024 <= 232448, "shared memory budget");
 };
@@ -512,17 +512,19 @@ struct P2SGCursor {
     }
 };
 
+// NP: operand planes, 2 for the split FP32 form (three products), 1 for the BF16 form.
 // FULL: d_KL per column instead (eq. 1 terms z + v log(v / z) - v with the accurate
 // logarithm), both candidates = the current factor, slot layout [slot][O] of candidate 0.
-template <int RP, bool FULL>
+template <int RP, int NP, bool FULL>
 __global__ void __launch_bounds__(P1_THREADS, 1)
     k_tc_pass2s(P2Args a, int64_t nch, int64_t U, int slots,
                 const __grid_constant__ CUtensorMap tmXm, const __grid_constant__ CUtensorMap tmXml,
                 const __grid_constant__ CUtensorMap tmXd, const __grid_constant__ CUtensorMap tmXdl,
                 const __grid_constant__ CUtensorMap tmY, const __grid_constant__ CUtensorMap tmYl,
                 const __grid_constant__ CUtensorMap tmV) {
-    using L = P2SLayout<RP>;
+    using L = P2SLayout<RP, NP>;
     constexpr int GST = L::GST, VST = L::VST;
+    static_assert(NP == 2 || !FULL, "the d_KL mode runs in the split form");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* sm = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -581,15 +583,16 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
                     const int st = kg % GST;
                     const uint32_t dst = sbase + L::GR + st * L::G_STAGE;
                     const int64_t ob = cg_.u / nch, ck = cg_.u % nch;
-                    if (cg_.xu < 2) {   // X hi and lo of candidate xu, [NA][128 o][64 r] each
+                    if (cg_.xu < 2) {   // X hi (and lo) of candidate xu, [NA][128 o][64 r] each
                         const CUtensorMap* mh = cg_.xu ? &tmXd : &tmXm;
                         const CUtensorMap* ml = cg_.xu ? &tmXdl : &tmXml;
-                        mbar_arrive_expect_tx(&bar[T_GFULL + st], 2 * L::X_PLANE);
+                        mbar_arrive_expect_tx(&bar[T_GFULL + st], NP * L::X_PLANE);
                         for (int at = 0; at < RP / 64; ++at) {
                             tma_load_2d(dst + at * OBLK * 128, mh, 64 * at, (int32_t)(ob * OBLK),
                                         &bar[T_GFULL + st]);
-                            tma_load_2d(dst + L::X_PLANE + at * OBLK * 128, ml, 64 * at,
-                                        (int32_t)(ob * OBLK), &bar[T_GFULL + st]);
+                            if (NP == 2)
+                                tma_load_2d(dst + L::X_PLANE + at * OBLK * 128, ml, 64 * at,
+                                            (int32_t)(ob * OBLK), &bar[T_GFULL + st]);
                         }
                     } else {
                         const int32_t s0 = (int32_t)(ck * SC2);
@@ -599,8 +602,9 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
                                 const uint32_t off = at * SC2 * 128 + hs * SCH * 128;
                                 tma_load_2d(dst + off, &tmY, 64 * at, s0 + SCH * hs,
                                             &bar[T_GFULL + st]);
-                                tma_load_2d(dst + L::G_PLANE + off, &tmYl, 64 * at, s0 + SCH * hs,
-                                            &bar[T_GFULL + st]);
+                                if (NP == 2)
+                                    tma_load_2d(dst + L::G_PLANE + off, &tmYl, 64 * at,
+                                                s0 + SCH * hs, &bar[T_GFULL + st]);
                             }
                     }
                     ++kg;
@@ -623,12 +627,13 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
             }
         }
     } else if (warp == W_MMA_Z || warp == W_MMA_AB) {
-        // candidate c: Z_c(m) = X_c Y(m)^t in the split form, products outer (see pass 1);
-        // at each segment start X_c (from the G unit of candidate c) into tensor memory
+        // candidate c: Z_c(m) = X_c Y(m)^t (in the split form three products, outer; see
+        // pass 1); at each segment start X_c (from the G unit of candidate c) into tensor
+        // memory
         const int c = warp == W_MMA_AB ? 1 : 0;
         if (lane == 0 && u0 < u1) {
             bool ok = true;
-            const uint32_t xh = tmem + L::TX + (uint32_t)c * RP, xl = xh + RP / 2;
+            const uint32_t xh = tmem + L::TX + (uint32_t)c * L::XC, xl = xh + RP / 2;
             const uint32_t tz = tmem + (uint32_t)c * SC2;
             constexpr uint32_t idesc = idesc_bf16(OBLK, SC2);
             int j = 0, m = 0;   // G units and chunks consumed
@@ -643,7 +648,7 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
                             tc_fence_after();
                             const uint32_t xs = sbase + L::GR + (j % GST) * L::G_STAGE;
 #pragma unroll
-                            for (int pl = 0; pl < 2; ++pl)
+                            for (int pl = 0; pl < NP; ++pl)
 #pragma unroll
                                 for (int kk = 0; kk < RP / 16; ++kk)
                                     tmem_cp_128x256b((pl ? xl : xh) + 8 * kk,
@@ -662,7 +667,7 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
                 tc_fence_after();
                 const uint32_t gh = sbase + L::GR + st * L::G_STAGE, gl = gh + L::G_PLANE;
 #pragma unroll
-                for (int p = 0; p < 3; ++p)
+                for (int p = 0; p < (NP == 2 ? 3 : 1); ++p)
 #pragma unroll
                     for (int kk = 0; kk < RP / 16; ++kk) {
                         const uint32_t off = (kk >> 2) * SC2 * 128 + 32u * (kk & 3);
@@ -794,23 +799,25 @@ int launch_pass1s(const P1Args& a, bool with_b, const TcMaps& m, int64_t O_pad, 
     return after_launch();
 }
 
-template <int RP, bool FULL>
+template <int RP, int NP, bool FULL>
 int launch_pass2s(const P2Args& a, const TcMaps& m, int64_t O_pad, int slots, int ctas,
                   cudaStream_t st) {
-    const uint32_t smem = P2SLayout<RP>::TOTAL + 1024;
-    auto k = k_tc_pass2s<RP, FULL>;
+    const uint32_t smem = P2SLayout<RP, NP>::TOTAL + 1024;
+    auto k = k_tc_pass2s<RP, NP, FULL>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return DNA_ERR_CUDA;
     const int64_t nch = (a.S + SC2 - 1) / SC2, U = (O_pad / OBLK) * nch;
     if (U == 0) return DNA_OK;
     const int grid = (int)std::min<int64_t>(ctas > 0 ? ctas : U, U);
-    // d_KL: both "candidates" are the current factor, the X operand of the view
+    // d_KL: both "candidates" are the current factor, the X operand of the view; the BF16
+    // form (NP = 1) has no lo planes (their slots take the hi maps, unused)
     const CUtensorMap& xm = FULL ? m.x : m.xm;
-    const CUtensorMap& xml = FULL ? m.x_l : m.xm_l;
+    const CUtensorMap& xml = FULL ? m.x_l : NP == 2 ? m.xm_l : m.xm;
     const CUtensorMap& xd = FULL ? m.x : m.xd;
-    const CUtensorMap& xdl = FULL ? m.x_l : m.xd_l;
-    k<<<grid, P1_THREADS, smem, st>>>(a, nch, U, slots, xm, xml, xd, xdl, m.y, m.y_l, m.v);
+    const CUtensorMap& xdl = FULL ? m.x_l : NP == 2 ? m.xd_l : m.xd;
+    const CUtensorMap& yl = NP == 2 ? m.y_l : m.y;
+    k<<<grid, P1_THREADS, smem, st>>>(a, nch, U, slots, xm, xml, xd, xdl, m.y, yl, m.v);
     return after_launch();
 }
 
@@ -836,8 +843,13 @@ int TcBf16::pass2_split(const TcOperands& op, const TcMaps& maps, double* dpart,
     a.dpart = dpart; a.status = status;
     a.V = op.V; a.vs = op.vs; a.Xm = op.Xmk; a.Xd = op.Xdk; a.rp = rank_pad(op.R);
     if (slots != pass2_split_slots(op.O_pad, op.S, op.ctas)) return DNA_ERR_ARG;
-    if (a.rp == 64) return tc::launch_pass2s<64, false>(a, maps, op.O_pad, slots, op.ctas, st);
-    if (a.rp == 128) return tc::launch_pass2s<128, false>(a, maps, op.O_pad, slots, op.ctas, st);
+    if (op.plane) {   // split FP32 form
+        if (a.rp == 64) return tc::launch_pass2s<64, 2, false>(a, maps, op.O_pad, slots, op.ctas, st);
+        if (a.rp == 128) return tc::launch_pass2s<128, 2, false>(a, maps, op.O_pad, slots, op.ctas, st);
+    } else {          // BF16 form
+        if (a.rp == 64) return tc::launch_pass2s<64, 1, false>(a, maps, op.O_pad, slots, op.ctas, st);
+        if (a.rp == 128) return tc::launch_pass2s<128, 1, false>(a, maps, op.O_pad, slots, op.ctas, st);
+    }
     return DNA_ERR_UNSUPPORTED;
 }
 
@@ -848,8 +860,9 @@ int TcBf16::kl_split(const TcOperands& op, const TcMaps& maps, double* dpart, in
     a.dpart = dpart; a.status = status;
     a.V = op.V; a.vs = op.vs; a.rp = rank_pad(op.R);
     if (slots != pass2_split_slots(op.O_pad, op.S, op.ctas)) return DNA_ERR_ARG;
-    if (a.rp == 64) return tc::launch_pass2s<64, true>(a, maps, op.O_pad, slots, op.ctas, st);
-    if (a.rp == 128) return tc::launch_pass2s<128, true>(a, maps, op.O_pad, slots, op.ctas, st);
+    if (!op.plane) return DNA_ERR_UNSUPPORTED;
+    if (a.rp == 64) return tc::launch_pass2s<64, 2, true>(a, maps, op.O_pad, slots, op.ctas, st);
+    if (a.rp == 128) return tc::launch_pass2s<128, 2, true>(a, maps, op.O_pad, slots, op.ctas, st);
     return DNA_ERR_UNSUPPORTED;
 }
 

@@ -76,15 +76,18 @@ enum { S_GFULL = 0, S_GEMPTY = 3, S_HFULL = 6, S_HEMPTY = 8, S_VFULL = 10, S_VEM
        S_ZFULL = 14, S_QFULL = 16, S_QEMPTY = 20, S_DRAIN = 22, S_COUNT = 24 };
 
 // One tile of pass 1: the accumulator (A if which = 0, B if which = 1) of one o-block over
-// one split of s.  Tiles are numbered split-major, then o-block, then which.
+// one split of s.  Tiles are numbered which-major, then split, then o-block: with the
+// tiles spread evenly over the CTAs, CTA i and CTA i + G / 2 work through the same
+// (split, o-block) tiles at the same time, so one of them reads each V tile from L2.
 struct P1STile {
     int64_t o0, s_begin, s_end;
     int nch, which, split;
 };
 __device__ __forceinline__ P1STile p1s_tile(int t, int nwhich, int nob, const P1Args& a) {
     P1STile x;
-    x.which = t % nwhich;
-    const int rest = t / nwhich;
+    const int per_which = (int)(nob * ((a.S + a.s_per - 1) / a.s_per));
+    x.which = nwhich > 1 ? t / per_which : 0;
+    const int rest = nwhich > 1 ? t % per_which : t;
     x.o0 = (int64_t)(rest % nob) * OBLK;
     x.split = rest / nob;
     x.s_begin = (int64_t)x.split * a.s_per;
@@ -130,8 +133,8 @@ struct P1SGCursor {
     }
 };
 
-// Persistent: CTA i takes the tiles [i T / G, (i + 1) T / G) of the T = nwhich x nob x
-// splits tiles (G = gridDim.x).  Between two tiles the epilogue writes the next X into
+// Persistent: CTA i takes the tiles [i T / G, (i + 1) T / G) of the T = nwhich x splits x
+// nob tiles (G = gridDim.x).  Between two tiles the epilogue writes the next X into
 // tensor memory as soon as the last GEMM1 of the tile is done and copies the accumulator
 // out once its last GEMM2 is, while GEMM1 of the next tile runs; the rings, the ZQ
 // buffers and every barrier phase run on across tiles.  X (hi, lo) of each tile comes

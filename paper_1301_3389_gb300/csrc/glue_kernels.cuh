@@ -342,13 +342,28 @@ __global__ void __launch_bounds__(256) k_select_fused(View v, const Tp* __restri
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
     const int64_t o0 = (int64_t)blockIdx.x * TO, o = o0 + tx;
     const bool live = o < O;
+    // the cost slots of column o: warp ty adds the contiguous range [ty k, (ty + 1) k)
+    // (k = ceil(splits / 8)), warp 0 the eight range sums in order
+    __shared__ double dsum[2][8][TO];
+    {
+        const int per = (splits + 7) / 8, sp0 = ty * per, sp1 = min(splits, sp0 + per);
+        double dm = 0.0, dd = 0.0;
+        if (live)
+            for (int sp = sp0; sp < sp1; ++sp) {
+                dm += dpart[((int64_t)sp * 2 + 0) * O + o];
+                dd += dpart[((int64_t)sp * 2 + 1) * O + o];
+            }
+        dsum[0][ty][tx] = dm;
+        dsum[1][ty][tx] = dd;
+    }
+    __syncthreads();
     if (ty == 0) {
         int newton = 0;
         if (live) {
-            double dm = 0.0, dd = 0.0;
-            for (int sp = 0; sp < splits; ++sp) {
-                dm += dpart[((int64_t)sp * 2 + 0) * O + o];
-                dd += dpart[((int64_t)sp * 2 + 1) * O + o];
+            double dm = dsum[0][0][tx], dd = dsum[1][0][tx];
+            for (int g = 1; g < 8; ++g) {
+                dm += dsum[0][g][tx];
+                dd += dsum[1][g][tx];
             }
             newton = dd < dm;
             choice[o] = (uint8_t)newton;

@@ -795,6 +795,26 @@ __global__ void k_colsum_part(const Tp* __restrict__ M, int64_t n, int64_t R, in
 // out[r] = sum over splits of part[split][r] + reg, zero sum guarded.  CTA = 32 values of
 // r (lanes, so loads coalesce) x 32 groups of splits: group g adds splits g, g + 32, ... in
 // order, then the 32 group sums are added in order.
+// out[r] = sum over k of part[k][r] + reg for a few r: one CTA per r, 256 partial sums
+// per thread stride, then a fixed tree (the part_sums of the glue, R small).  A template
+// only so that every translation unit including this header may define it.
+template <int UNUSED = 0>
+__global__ void __launch_bounds__(256) k_colsum_small(const double* __restrict__ part,
+                                                      int nsplit, int64_t R, double reg,
+                                                      double* __restrict__ out, bool guard) {
+    __shared__ double red[256];
+    const int64_t r = blockIdx.x;
+    double t = 0.0;
+    for (int k = threadIdx.x; k < nsplit; k += 256) t += part[(int64_t)k * R + r];
+    red[threadIdx.x] = t;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[r] = nonzero_sum(red[0] + reg, guard);
+}
+
 template <int UNUSED = 0>
 __global__ void __launch_bounds__(1024) k_colsum_final(const double* __restrict__ part,
                                                        int nsplit, int64_t R, double reg,

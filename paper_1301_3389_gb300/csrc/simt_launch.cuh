@@ -342,8 +342,11 @@ int Simt<Tp>::select_fused(const View& v, const Tp* Xmu, const Tp* Xdna, const d
 template <typename Tp>
 int Simt<Tp>::part_sums(const double* part, int64_t nparts, int64_t R, double reg, double* out,
                         cudaStream_t st) {
-    simt::k_colsum_final<<<(unsigned)((R + 31) / 32), dim3(32, 32), 0, st>>>(part, (int)nparts, R, reg, out,
-                                                                  true);
+    if (R <= 1024)   // a CTA per r: latency of one load round and a tree, not of nparts / 32
+        simt::k_colsum_small<0><<<(unsigned)R, 256, 0, st>>>(part, (int)nparts, R, reg, out, true);
+    else
+        simt::k_colsum_final<<<(unsigned)((R + 31) / 32), dim3(32, 32), 0, st>>>(
+            part, (int)nparts, R, reg, out, true);
     return simt::launch_status();
 }
 

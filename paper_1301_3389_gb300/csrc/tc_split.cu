@@ -376,6 +376,26 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
         float zmin = 1.f;   // min over v > 0 of z (see the BF16 pass 1)
         bool ok = true;
         int m = 0;
+        // The accumulator of a finished tile is copied out while the next tile starts: after
+        // the epilogue has written Q of the next tile's first half chunk (its QFULL not yet
+        // signalled), it waits for the old tile's last GEMM2, reads the accumulator into
+        // registers, signals QFULL (the first GEMM2 of the new tile overwrites the
+        // accumulator) and only then issues the global stores.
+        bool pend = false;   // an accumulator still to copy: tile xp, last chunk mp
+        P1STile xp{};
+        int mp = 0;
+        // this thread's 32 accumulator values of tile y (column group cg) to Apart / Bpart
+        auto store_acc = [&](const P1STile& y, const uint32_t (&r32)[32]) {
+            const int64_t o = y.o0 + row;
+            const int64_t base = (int64_t)y.split * a.R;
+            float* dst = y.which ? a.Bpart : a.Apart;
+            if (o < a.O)
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    const int64_t r = 32 * cg + i;
+                    if (r < a.R) dst[(base + r) * a.O + o] = __uint_as_float(r32[i]);
+                }
+        };
         for (int t = t_begin; ok && t < t_end; ++t) {
             const P1STile x = p1s_tile(t, nwhich, nob, a);
             for (int k = 0; k < x.nch; ++k, ++m) {
@@ -419,33 +439,46 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
                     tmem_st8(col, hp);
                     tmem_st8(col + 8, lp);
                     tmem_st_wait();
+                    uint32_t r32[32];
+                    const bool copy = pend && k == 0 && h == 0;
+                    if (copy) {   // the previous tile's accumulator, once its last GEMM2 is done
+                        ok = __all_sync(0xffffffffu, wait_phase(&bar[S_QEMPTY + (mp & 1)],
+                                                                (mp >> 1) & 1, abort));
+                        if (!ok) break;
+                        tc_fence_after();
+                        if (cg < RP / 32) {
+                            tmem_ld32(tmem + L::TACC + lane_off + 32 * cg, r32);
+                            tmem_ld_wait();
+                        }
+                    }
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&bar[S_QFULL + 2 * b + h]);
+                    if (copy) {
+                        if (cg < RP / 32) store_acc(xp, r32);
+                        pend = false;
+                    }
                 }
                 if (!ok) break;
             }
             if (!ok) break;
-            // GEMM2 of the last chunk done: copy the accumulator out
+            if (t + 1 < t_end) {   // copied out during the next tile's first half chunk
+                pend = true;
+                xp = x;
+                mp = m - 1;
+                continue;
+            }
+            // the CTA's last tile: GEMM2 of its last chunk done, copy the accumulator out
             const int ml = m - 1;
             ok = __all_sync(0xffffffffu,
                             wait_phase(&bar[S_QEMPTY + (ml & 1)], (ml >> 1) & 1, abort));
             if (!ok) break;
             tc_fence_after();
-            const int64_t o = x.o0 + row;
-            const int64_t base = (int64_t)x.split * a.R;
-            float* dst = x.which ? a.Bpart : a.Apart;
-#pragma unroll 1
-            for (int g = cg; g < RP / 32; g += 4) {
+            if (cg < RP / 32) {
                 uint32_t r32[32];
-                tmem_ld32(tmem + L::TACC + lane_off + 32 * g, r32);
+                tmem_ld32(tmem + L::TACC + lane_off + 32 * cg, r32);
                 tmem_ld_wait();
-                if (o < a.O)
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        const int64_t r = 32 * g + i;
-                        if (r < a.R) dst[(base + r) * a.O + o] = __uint_as_float(r32[i]);
-                    }
+                store_acc(x, r32);
             }
             tc_fence_before();
         }

@@ -477,38 +477,43 @@ __global__ void __launch_bounds__(256) k_scale_ops(OpsArgs a) {
     }
     if (a.Xk == nullptr) return;
     if constexpr (sizeof(Tp) == 4) {
-        if (isx) {   // Xk[o][r]: lanes walk r
-            for (int k = ty; k < TO; k += 8) {
-                const int64_t i = i0 + k, r = r0 + tx;
-                if (i < a.O_pad && r < a.rp) {
-                    bf16 h, l;
-                    split1(tile[tx][k], h, l);
-                    a.Xk[i * a.rp + r] = h;
-                    if (a.plane) a.Xk[a.plane + i * a.rp + r] = l;
-                }
+        // bf16 pairs, one 32-bit store per thread (a warp stores two 64-byte runs); the
+        // tile reads tile[2 j][.] / tile[.][2 j] over the lanes are bank-conflict free
+        // rows [i][rp] with r contiguous (Xk of X tiles, Yk of Y tiles): pairs of r
+        bf16* RM = isx ? a.Xk : a.Yk;
+        const int64_t ipad = isx ? a.O_pad : a.S_pad;
+        for (int k = ty; k < TO / 2; k += 8) {
+            const int il = 2 * k + (tx >> 4), rl = 2 * (tx & 15);
+            const int64_t i = i0 + il, r = r0 + rl;
+            if (i < ipad && r < a.rp) {   // rp is even, so r + 1 < rp too
+                const float y0 = tile[rl][il], y1 = tile[rl + 1][il];
+                const uint32_t h = pack2(y0, y1);
+                *reinterpret_cast<uint32_t*>(RM + i * a.rp + r) = h;
+                if (a.plane)
+                    *reinterpret_cast<uint32_t*>(RM + a.plane + i * a.rp + r) =
+                        pack2(y0 - lo_half(h), y1 - hi_half(h));
             }
-        } else {
-            for (int k = ty; k < TO; k += 8) {
-                const int64_t i = i0 + k, r = r0 + tx;   // Yk[s][r]: lanes walk r
-                if (i < a.S_pad && r < a.rp) {
-                    bf16 h, l;
-                    split1(tile[tx][k], h, l);
-                    a.Yk[i * a.rp + r] = h;
-                    if (a.plane) a.Yk[a.plane + i * a.rp + r] = l;
-                }
-                const int64_t r2 = r0 + k, i2 = i0 + tx;  // Ytk[r][s]: lanes walk s
-                if (i2 < a.S_pad && r2 < a.rp) {
-                    const float y = tile[k][tx];
-                    const int64_t at = r2 * a.S_pad + i2;
-                    bf16 h, l;
-                    split1(y, h, l);
-                    a.Ytk[at] = h;
-                    if (a.plane) a.Ytk[a.plane + at] = l;
-                    if (a.Y2tk) {
-                        split1(y * y, h, l);
-                        a.Y2tk[at] = h;
-                        if (a.plane) a.Y2tk[a.plane + at] = l;
-                    }
+        }
+        if (isx) return;
+        // Ytk, Y2tk [r][S_pad] with s contiguous: pairs of s (S_pad is a multiple of 64)
+        for (int k = ty; k < TO / 2; k += 8) {
+            const int rl = 2 * k + (tx >> 4), il = 2 * (tx & 15);
+            const int64_t r = r0 + rl, i = i0 + il;
+            if (r < a.rp && i < a.S_pad) {
+                const float y0 = tile[rl][il], y1 = tile[rl][il + 1];
+                const int64_t at = r * a.S_pad + i;
+                const uint32_t h = pack2(y0, y1);
+                *reinterpret_cast<uint32_t*>(a.Ytk + at) = h;
+                if (a.plane)
+                    *reinterpret_cast<uint32_t*>(a.Ytk + a.plane + at) =
+                        pack2(y0 - lo_half(h), y1 - hi_half(h));
+                if (a.Y2tk) {
+                    const float q0 = y0 * y0, q1 = y1 * y1;
+                    const uint32_t h2 = pack2(q0, q1);
+                    *reinterpret_cast<uint32_t*>(a.Y2tk + at) = h2;
+                    if (a.plane)
+                        *reinterpret_cast<uint32_t*>(a.Y2tk + a.plane + at) =
+                            pack2(q0 - lo_half(h2), q1 - hi_half(h2));
                 }
             }
         }

@@ -117,7 +117,10 @@ int dna_iterate(dna_ctx* ctx, int iters);
  * Asynchronous. */
 int mu_step(dna_ctx* ctx, int which);
 
-/* d_KL(V, W H) of eq. 1 in float64, written to *out (host memory).  Synchronises the
+/* d_KL(V, W H) of eq. 1 in float64, written to *out (host memory): per element
+ * z + v log(v / z) - v (z where v = 0), summed in float32 over short runs and in float64
+ * beyond.  Z is formed by the context's engine (for F32 with ENGINE_TENSOR: the split
+ * bf16 tensor-core product; for BF16: the CUDA-core float32 product).  Synchronises the
  * context's stream; also returns any error recorded by earlier kernels. */
 int dna_kl(dna_ctx* ctx, double* out);
 

@@ -68,10 +68,10 @@ struct P1SLayout {
     static_assert(TOTAL + 1024 <= 232448, "shared memory budget");
 };
 
-// G stages hold X planes and r-atoms of Y in the order of P1SGCursor.  QFULL[2 b + h]: the epilogue wrote Q of half
-// h (s 64 h .. 64 h + 63) of the chunk in ZQ buffer b.  QEMPTY[b]: GEMM2 of that chunk is
-// done (buffer b free for GEMM1 two chunks later; for the last chunk the accumulator is
-// final).
+// G stages hold X planes and r-atoms of Y in the order of P1SGCursor.  QFULL[2 b + h]:
+// the epilogue wrote Q of half h (s 64 h .. 64 h + 63) of the chunk in ZQ buffer b.
+// QEMPTY[b]: GEMM2 of that chunk is done (buffer b free for GEMM1 two chunks later; for a
+// tile's last chunk the accumulator is final).
 enum { S_GFULL = 0, S_GEMPTY = 3, S_HFULL = 6, S_HEMPTY = 8, S_VFULL = 10, S_VEMPTY = 12,
        S_ZFULL = 14, S_QFULL = 16, S_QEMPTY = 20, S_DRAIN = 22, S_COUNT = 24 };
 
@@ -96,7 +96,8 @@ __device__ __forceinline__ P1STile p1s_tile(int t, int nwhich, int nob, const P1
     return x;
 }
 
-// A walk over the units (tile, chunk, sub) of one CTA's tiles, sub < per_chunk.
+// A walk over the units (tile, chunk, sub) of one CTA's tiles, sub < per_chunk (every tile
+// has at least one chunk: the host plans ceil(S / s_per) splits).
 struct P1SCursor {
     int t, k, sub;
     P1STile x;
@@ -134,11 +135,11 @@ struct P1SGCursor {
 };
 
 // Persistent: CTA i takes the tiles [i T / G, (i + 1) T / G) of the T = nwhich x splits x
-// nob tiles (G = gridDim.x).  Between two tiles the epilogue writes the next X into
-// tensor memory as soon as the last GEMM1 of the tile is done and copies the accumulator
-// out once its last GEMM2 is, while GEMM1 of the next tile runs; the rings, the ZQ
-// buffers and every barrier phase run on across tiles.  X (hi, lo) of each tile comes
-// through the G ring and goes into tensor memory by tcgen05.cp from the MMA thread.
+// nob tiles (G = gridDim.x); the rings, the ZQ buffers and every barrier phase run on
+// across tiles.  X (hi, lo) of each tile comes through the G ring and goes into tensor
+// memory by tcgen05.cp from the MMA thread once its last GEMM1 of the previous tile is
+// done; the epilogue reads a finished tile's accumulator out while the next tile starts
+// (see the epilogue).
 template <int RP>
 __global__ void __launch_bounds__(P1_THREADS, 1)
     k_tc_pass1s(P1Args a, int nwhich, int nob, int ntiles,
@@ -239,7 +240,8 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
                 if (ch_.t < t_end && mbar_test(&bar[S_HEMPTY + kh % HST], ((kh / HST) & 1) ^ 1)) {
                     const int st = kh % HST;
                     const uint32_t dst = sbase + L::HR + st * L::H_STAGE;
-                    const int32_t s0 = (int32_t)(ch_.x.s_begin + (int64_t)ch_.k * SC2 + SCH * ch_.sub);
+                    const int32_t s0 =
+                        (int32_t)(ch_.x.s_begin + (int64_t)ch_.k * SC2 + SCH * ch_.sub);
                     const CUtensorMap* mh = ch_.x.which ? &tmY2t : &tmYt;
                     const CUtensorMap* ml = ch_.x.which ? &tmY2tl : &tmYtl;
                     mbar_arrive_expect_tx(&bar[S_HFULL + st], L::H_STAGE);
@@ -302,7 +304,8 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
                     const uint32_t tz = tmem + b * SC2;
 #pragma unroll 1
                     for (int at = 0; at < NA; ++at, ++j) {
-                        if (!(ok = wait_phase(&bar[S_GFULL + j % GST], (j / GST) & 1, abort))) break;
+                        if (!(ok = wait_phase(&bar[S_GFULL + j % GST], (j / GST) & 1, abort)))
+                            break;
                         tc_fence_after();
                         const uint32_t gh = sbase + L::GR + (j % GST) * L::G_STAGE,
                                        gl = gh + L::G_PLANE;
@@ -679,7 +682,8 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
                     if (m >= 1 && !(ok = wait_phase(&bar[T_ZFULL + c], (m - 1) & 1, abort))) break;
 #pragma unroll 1
                     for (int xu = 0; xu < 2; ++xu, ++j) {
-                        if (!(ok = wait_phase(&bar[T_GFULL + j % GST], (j / GST) & 1, abort))) break;
+                        if (!(ok = wait_phase(&bar[T_GFULL + j % GST], (j / GST) & 1, abort)))
+                            break;
                         if (xu == c) {
                             tc_fence_after();
                             const uint32_t xs = sbase + L::GR + (j % GST) * L::G_STAGE;
@@ -786,7 +790,8 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
                 if (o < a.O) {
                     a.dpart[(int64_t)(4 * q + cg) * a.O + o] = acc_m;
                     if (me == p2s_cta_of((ob + 1) * nch - 1, U, G))
-                        for (int s = 4 * (q + 1) + cg; s < slots; s += 4) a.dpart[(int64_t)s * a.O + o] = 0.0;
+                        for (int s = 4 * (q + 1) + cg; s < slots; s += 4)
+                            a.dpart[(int64_t)s * a.O + o] = 0.0;
                 }
                 acc_m = 0.0;
                 acc_d = 0.0;
@@ -879,12 +884,13 @@ int TcBf16::pass2_split(const TcOperands& op, const TcMaps& maps, double* dpart,
     a.dpart = dpart; a.status = status;
     a.V = op.V; a.vs = op.vs; a.Xm = op.Xmk; a.Xd = op.Xdk; a.rp = rank_pad(op.R);
     if (slots != pass2_split_slots(op.O_pad, op.S, op.ctas)) return DNA_ERR_ARG;
+    const int64_t Op = op.O_pad;
     if (op.plane) {   // split FP32 form
-        if (a.rp == 64) return tc::launch_pass2s<64, 2, false>(a, maps, op.O_pad, slots, op.ctas, st);
-        if (a.rp == 128) return tc::launch_pass2s<128, 2, false>(a, maps, op.O_pad, slots, op.ctas, st);
+        if (a.rp == 64) return tc::launch_pass2s<64, 2, false>(a, maps, Op, slots, op.ctas, st);
+        if (a.rp == 128) return tc::launch_pass2s<128, 2, false>(a, maps, Op, slots, op.ctas, st);
     } else {          // BF16 form
-        if (a.rp == 64) return tc::launch_pass2s<64, 1, false>(a, maps, op.O_pad, slots, op.ctas, st);
-        if (a.rp == 128) return tc::launch_pass2s<128, 1, false>(a, maps, op.O_pad, slots, op.ctas, st);
+        if (a.rp == 64) return tc::launch_pass2s<64, 1, false>(a, maps, Op, slots, op.ctas, st);
+        if (a.rp == 128) return tc::launch_pass2s<128, 1, false>(a, maps, Op, slots, op.ctas, st);
     }
     return DNA_ERR_UNSUPPORTED;
 }

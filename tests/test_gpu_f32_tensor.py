@@ -35,6 +35,28 @@ def test_split_half_steps(shape):
         assert worst < 1e-4
 
 
+def test_split_persistent_tiles_and_segments():
+    """Sizes where the persistent kernels' schedules matter: pass 1 has more tiles than
+    SMs (188 in the H step, 192 in the W step, so CTAs run two tiles back to back) and
+    pass 2 splits o-blocks between CTAs (752 (o-block, chunk) units over the SMs, cost
+    slots per segment).  One DNA iteration from the oracle's state, W and H within 1e-4."""
+    N, T, R = 1000, 12000, 64
+    p = workloads.custom(N, T, R, seed=4242)
+    with GpuProblem(p.V, p.W, p.H, "f32t") as gp:
+        gp.dna.dna_normalize(gp.ctx, 1)
+        W, H = o.normalize_w_columns(p.W, p.H)
+        worst = 0.0
+        for which in (0, 1):
+            W, H, _ = step_pair(gp, W, H, which)
+            Wg, Hg = gp.WH()
+            worst = max(worst, rel_fro(Wg, W), rel_fro(Hg, H))
+        kl_gpu = gp.dna.dna_kl(gp.ctx)
+        kl_ref = o.kl_divergence(p.V.astype(np.float64), W @ H)
+        print(f"\n{(N, T, R)}: worst W/H error {worst:.2e}, d_KL {kl_gpu:.6e} vs {kl_ref:.6e}")
+        assert worst < 1e-4
+        assert abs(kl_gpu - kl_ref) <= 1e-5 * abs(kl_ref)
+
+
 def test_split_unsupported_rank():
     import paper_1301_3389_gb300 as dna
     with pytest.raises(dna.DNAError) as e:

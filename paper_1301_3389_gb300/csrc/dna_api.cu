@@ -178,9 +178,10 @@ void plan_all(dna_ctx* c) {
             // CTA rows per o-block of pass 1: r-blocks of the K-streamed kernels, or the A and
             // B halves of the split FP32 kernel
             const int64_t rblocks = c->split ? 2 : (c->rp > 128 ? c->rp / 128 : 1);
-            // the split form streams s in chunks of 128
+            // the split form, and pass 1 at ranks above 128, stream s in chunks of 128
             const int sch = c->split ? (int)SPLIT_CHUNK : tch;
-            plan_split(Sdim, c->pad_o[w] / tob * rblocks, c->num_sms, sch, &c->tsp1[w],
+            const int sch1 = c->split || c->rp > 128 ? (int)SPLIT_CHUNK : tch;
+            plan_split(Sdim, c->pad_o[w] / tob * rblocks, c->num_sms, sch1, &c->tsp1[w],
                        &c->tper1[w], part, c->split ? SPLIT_MAX_CHUNKS : 0);
             plan_split(Sdim, c->pad_o[w] / tob, c->num_sms, sch, &c->tsp2[w], &c->tper2[w],
                        2.0 / (double)Sdim);

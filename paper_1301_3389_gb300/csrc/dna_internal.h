@@ -151,7 +151,7 @@ struct TcMaps {
 };
 
 struct TcBf16 {
-    // padded rank for the tensor-core kernels (64 or 128), 0 if unsupported
+    // padded rank for the tensor-core kernels (64, 128, 256 or 512), 0 if unsupported
     static int rank_pad(int64_t R);
     // dst[i][j] = bf16(src(i, j)) (or its square), zero-padded to rows_pad x cols_pad
     static int to_bf16(const float* src, int64_t si, int64_t sj, int64_t rows, int64_t cols,
@@ -166,6 +166,11 @@ struct TcBf16 {
                          const void* Xmk, const void* Xdk);
     static int pass1(const TcOperands& op, const TcMaps& maps, float* Apart, float* Bpart,
                      int splits, int64_t s_per, bool with_b, int* status, cudaStream_t st);
+    // pass 1 at padded rank 256 or 512 (tc_ks.cu): persistent CTAs over (r-block of 128,
+    // o-block, split) tiles; s_per must be a multiple of 128
+    static int pass1_large(const TcOperands& op, const TcMaps& maps, float* Apart,
+                           float* Bpart, int splits, int64_t s_per, bool with_b, int* status,
+                           cudaStream_t st);
     static int pass2(const TcOperands& op, const TcMaps& maps, double* dpart, int splits,
                      int64_t s_per, int* status, cudaStream_t st);
     // The FP32 form on the tensor cores (tc_split.cu): the same passes with every operand
@@ -186,7 +191,6 @@ struct TcBf16 {
     static int oblock();
 };
 
-// sum of dpart[0 .. n) in a fixed order into *out (float64)
 // sum of part[0 .. n) into *out in a fixed order (work: REDUCE_PARTS doubles)
 constexpr int64_t REDUCE_PARTS = 256;
 int reduce_sum(const double* part, int64_t n, double* out, double* work, cudaStream_t st);

@@ -319,269 +319,15 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
 }
 
 // ------------------------------------------------------------ large rank (RP > 128)
-// For RP in {256, 512} the operand tiles of GEMM1 do not fit in shared memory beside the
-// rings, and A and B (2 RP TMEM columns) do not fit in TMEM.  These variants stream X and Y
-// through a ring of 64-wide K-slices for every s-chunk, and split A and B into r-blocks of
-// 128 (grid y): each CTA recomputes the full Z for its o-block and accumulates A and B for
-// its 128 values of r only.
+// Pass 2 for RP in {256, 512}: the candidates' operand tiles do not fit in shared memory
+// beside the rings, so X_mu, X_dna and Y stream through a ring of 64-wide K-slices for
+// every s-chunk (pass 1 at these ranks is in tc_ks.cu).
 
 constexpr int KS_STAGES = 3;
-
-struct KsLayout1 {
-    static constexpr uint32_t XS = OBLK * 64 * 2;          // X slice [128][64]
-    static constexpr uint32_t YS = SCH * 64 * 2;           // Y slice [64][64]
-    static constexpr uint32_t KSTAGE = XS + YS;
-    static constexpr uint32_t KR = 0;                      // K-slice ring
-    static constexpr uint32_t V_BYTES = SCH * OBLK * 4;
-    static constexpr uint32_t VR = KR + KS_STAGES * KSTAGE;  // V ring (2 stages)
-    static constexpr uint32_t YT_BYTES = 128 * SCH * 2;    // Yt rows of this r-block
-    static constexpr uint32_t BR = VR + 2 * V_BYTES;       // Yt, Y2t (1 stage)
-    static constexpr uint32_t Q = BR + 2 * YT_BYTES;
-    static constexpr uint32_t QB = Q + OBLK * SCH * 2;
-    static constexpr uint32_t BAR = QB + OBLK * SCH * 2;
-    static constexpr uint32_t TOTAL = BAR + 256;
-    static constexpr uint32_t NCOLS = 512;                 // Z x 2 (128) + A (128) + B (128)
-    static_assert(KSTAGE % 1024 == 0 && VR % 1024 == 0 && BR % 1024 == 0 && Q % 1024 == 0, "");
-    static_assert(TOTAL + 1024 <= 232448, "shared memory budget");
-};
 
 enum { K_KFULL = 0, K_KEMPTY = 3, K_VFULL = 6, K_VEMPTY = 8, K_BFULL = 10, K_BEMPTY = 11,
        K_ZFULL = 12, K_ZEMPTY = 14, K_QFULL = 16, K_QEMPTY = 17, K_ACC = 18, K_DRAIN = 19,
        K_COUNT = 20 };
-
-template <int RP, bool WITH_B>
-__global__ void __launch_bounds__(NTHREADS, 1)
-    k_tc_pass1_ks(P1Args a, const __grid_constant__ CUtensorMap tmX,
-                  const __grid_constant__ CUtensorMap tmY, const __grid_constant__ CUtensorMap tmYt,
-                  const __grid_constant__ CUtensorMap tmY2t,
-                  const __grid_constant__ CUtensorMap tmV) {
-    using L = KsLayout1;
-    constexpr int KS = RP / 64;
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char* sm = reinterpret_cast<unsigned char*>(
-        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    const uint32_t sbase = smem_u32(sm);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + L::BAR);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L::BAR + K_COUNT * 8);
-    volatile int* abort = reinterpret_cast<volatile int*>(sm + L::BAR + K_COUNT * 8 + 8);
-
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int64_t o0 = (int64_t)blockIdx.x * OBLK;
-    const int rb = blockIdx.y;                             // r-block of A and B
-    const int64_t s_begin = (int64_t)blockIdx.z * a.s_per;
-    const int64_t s_end = min(a.S, s_begin + a.s_per);
-    const int nch = s_end > s_begin ? (int)((s_end - s_begin + SCH - 1) / SCH) : 0;
-
-    if (warp == 0) { tmem_alloc(tslot, L::NCOLS); tmem_relinquish(); }
-    if (tid == MMA_WARP * 32) {
-        for (int i = 0; i < KS_STAGES; ++i) {
-            mbar_init(&bar[K_KFULL + i], 1);
-            mbar_init(&bar[K_KEMPTY + i], 1);
-        }
-        for (int i = 0; i < 2; ++i) {
-            mbar_init(&bar[K_VFULL + i], 1);
-            mbar_init(&bar[K_VEMPTY + i], NEPI_WARPS);
-            mbar_init(&bar[K_ZFULL + i], 1);
-            mbar_init(&bar[K_ZEMPTY + i], NEPI_WARPS);
-        }
-        mbar_init(&bar[K_BFULL], 1);
-        mbar_init(&bar[K_BEMPTY], 1);
-        mbar_init(&bar[K_QFULL], NEPI_WARPS);
-        mbar_init(&bar[K_QEMPTY], 1);
-        mbar_init(&bar[K_ACC], 1);
-        mbar_init(&bar[K_DRAIN], 1);
-        *abort = 0;
-        fence_mbar_init();
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = *tslot;
-    const uint32_t tA = tmem + 2 * SCH, tB = tmem + 2 * SCH + 128;
-
-    if (warp == PRODUCER_WARP) {
-        if (lane == 0 && nch > 0) {
-            tma_prefetch_desc(&tmX); tma_prefetch_desc(&tmY); tma_prefetch_desc(&tmYt);
-            tma_prefetch_desc(&tmY2t); tma_prefetch_desc(&tmV);
-            int lastK[KS_STAGES] = {-1, -1, -1}, lastV[2] = {-1, -1}, lastB = -1;
-            bool ok = true;
-            for (int k = 0; k < nch && ok; ++k) {
-                const int32_t s0 = (int32_t)(s_begin + (int64_t)k * SCH);
-                const int vs = k & 1;
-                if (!(ok = wait_phase(&bar[K_VEMPTY + vs], ((k >> 1) & 1) ^ 1, abort))) break;
-                mbar_arrive_expect_tx(&bar[K_VFULL + vs], L::V_BYTES);
-                tma_load_2d(sbase + L::VR + vs * L::V_BYTES, &tmV, (int32_t)o0, s0, &bar[K_VFULL + vs]);
-                lastV[vs] = k;
-                for (int ks = 0; ks < KS; ++ks) {
-                    const int j = k * KS + ks, st = j % KS_STAGES;
-                    if (!(ok = wait_phase(&bar[K_KEMPTY + st], ((j / KS_STAGES) & 1) ^ 1, abort))) break;
-                    const uint32_t kb = sbase + L::KR + st * L::KSTAGE;
-                    mbar_arrive_expect_tx(&bar[K_KFULL + st], L::KSTAGE);
-                    tma_load_2d(kb, &tmX, 64 * ks, (int32_t)o0, &bar[K_KFULL + st]);
-                    tma_load_2d(kb + L::XS, &tmY, 64 * ks, s0, &bar[K_KFULL + st]);
-                    lastK[st] = j;
-                }
-                if (!ok) break;
-                if (!(ok = wait_phase(&bar[K_BEMPTY], (k & 1) ^ 1, abort))) break;
-                mbar_arrive_expect_tx(&bar[K_BFULL], (WITH_B ? 2 : 1) * L::YT_BYTES);
-                tma_load_2d(sbase + L::BR, &tmYt, s0, 128 * rb, &bar[K_BFULL]);
-                if (WITH_B)
-                    tma_load_2d(sbase + L::BR + L::YT_BYTES, &tmY2t, s0, 128 * rb, &bar[K_BFULL]);
-                lastB = k;
-            }
-            if (*abort) {
-                for (int st = 0; st < KS_STAGES; ++st)
-                    if (lastK[st] >= 0) drain_phase(&bar[K_KFULL + st], (lastK[st] / KS_STAGES) & 1);
-                for (int vs = 0; vs < 2; ++vs)
-                    if (lastV[vs] >= 0) drain_phase(&bar[K_VFULL + vs], (lastV[vs] >> 1) & 1);
-                if (lastB >= 0) drain_phase(&bar[K_BFULL], lastB & 1);
-            }
-        }
-    } else if (warp == MMA_WARP) {
-        if (lane == 0 && nch > 0) {
-            bool ok = true;
-            for (int k = 0; ok && k <= nch; ++k) {
-                if (k < nch) {
-                    const int zb = k & 1;
-                    if (!(ok = wait_phase(&bar[K_ZEMPTY + zb], ((k >> 1) & 1) ^ 1, abort))) break;
-                    tc_fence_after();
-                    const uint32_t tz = tmem + zb * SCH;
-                    for (int ks = 0; ks < KS && ok; ++ks) {
-                        const int j = k * KS + ks, st = j % KS_STAGES;
-                        if (!(ok = wait_phase(&bar[K_KFULL + st], (j / KS_STAGES) & 1, abort))) break;
-                        tc_fence_after();
-                        const uint32_t kb = sbase + L::KR + st * L::KSTAGE;
-#pragma unroll
-                        for (int kk = 0; kk < 4; ++kk)
-                            mma_bf16(tz, desc_sw128(kb + 32u * kk), desc_sw128(kb + L::XS + 32u * kk),
-                                     idesc_bf16(OBLK, SCH), (ks > 0 || kk > 0) ? 1u : 0u);
-                        mma_commit(&bar[K_KEMPTY + st]);
-                    }
-                    if (!ok) break;
-                    mma_commit(&bar[K_ZFULL + zb]);
-                }
-                if (k >= 1) {
-                    const int kp = k - 1;
-                    if (!(ok = wait_phase(&bar[K_QFULL], kp & 1, abort))) break;
-                    if (!(ok = wait_phase(&bar[K_BFULL], kp & 1, abort))) break;
-                    tc_fence_after();
-#pragma unroll
-                    for (int kk = 0; kk < SCH / 16; ++kk) {
-                        const uint32_t kb = 32u * kk;
-                        const uint32_t acc = (kp > 0 || kk > 0) ? 1u : 0u;
-                        mma_bf16(tA, desc_sw128(sbase + L::Q + kb), desc_sw128(sbase + L::BR + kb),
-                                 idesc_bf16(OBLK, 128), acc);
-                        if (WITH_B)
-                            mma_bf16(tB, desc_sw128(sbase + L::QB + kb),
-                                     desc_sw128(sbase + L::BR + L::YT_BYTES + kb),
-                                     idesc_bf16(OBLK, 128), acc);
-                    }
-                    mma_commit(&bar[K_QEMPTY]);
-                    mma_commit(&bar[K_BEMPTY]);
-                }
-            }
-            if (ok) {
-                mma_commit(&bar[K_ACC]);
-            } else {
-                mma_commit(&bar[K_DRAIN]);
-                drain_phase(&bar[K_DRAIN], 0);
-            }
-        }
-    } else {
-        const int qd = warp & 3, hf = warp >> 2;
-        const int row = 32 * qd + lane;
-        const int64_t o = o0 + row;
-        const uint32_t lane_off = (uint32_t)(32 * qd) << 16;
-        bool bad = false;
-        bool ok = true;
-        for (int k = 0; k < nch; ++k) {
-            const int zb = k & 1;
-            const uint32_t par = (k >> 1) & 1;
-            ok = wait_phase(&bar[K_ZFULL + zb], par, abort);
-            ok = ok && wait_phase(&bar[K_VFULL + zb], par, abort);
-            if (!(ok = __all_sync(0xffffffffu, ok))) break;
-            tc_fence_after();
-            uint32_t zr[32];
-            tmem_ld32(tmem + zb * SCH + lane_off + 32 * hf, zr);
-            tmem_ld_wait();
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&bar[K_ZEMPTY + zb]);
-            const float* Vs = reinterpret_cast<const float*>(sm + L::VR + zb * L::V_BYTES) +
-                              32 * hf * OBLK + row;
-            uint32_t qp[16], qbp[16];
-#pragma unroll
-            for (int j = 0; j < 32; j += 2) {
-                float q[2], qb[2];
-#pragma unroll
-                for (int t = 0; t < 2; ++t) {
-                    const float v = Vs[(j + t) * OBLK];
-                    const float z = __uint_as_float(zr[j + t]);
-                    const float rz = __fdividef(1.0f, z);
-                    const bool pos = v > 0.f;
-                    bad |= pos && !(z > 0.f);
-                    q[t] = pos ? v * rz : 0.f;
-                    qb[t] = pos ? q[t] * rz : 0.f;
-                }
-                qp[j / 2] = pack_bf16x2(q[0], q[1]);
-                qbp[j / 2] = pack_bf16x2(qb[0], qb[1]);
-            }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&bar[K_VEMPTY + zb]);
-            ok = wait_phase(&bar[K_QEMPTY], (k & 1) ^ 1, abort);
-            if (!(ok = __all_sync(0xffffffffu, ok))) break;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const uint32_t off = sw128_offset(row, 4 * hf + c, OBLK);
-                asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(sbase + L::Q + off),
-                             "r"(qp[4 * c]), "r"(qp[4 * c + 1]), "r"(qp[4 * c + 2]),
-                             "r"(qp[4 * c + 3])
-                             : "memory");
-                if (WITH_B)
-                    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(
-                                     sbase + L::QB + off),
-                                 "r"(qbp[4 * c]), "r"(qbp[4 * c + 1]), "r"(qbp[4 * c + 2]),
-                                 "r"(qbp[4 * c + 3])
-                                 : "memory");
-            }
-            fence_proxy_async_smem();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&bar[K_QFULL]);
-        }
-        if (bad) atomicOr(a.status, STATUS_NONFINITE);
-        if (ok && nch > 0) ok = __all_sync(0xffffffffu, wait_phase(&bar[K_ACC], 0, abort));
-        if (ok && nch > 0) {
-            tc_fence_after();
-            const int64_t base = (int64_t)blockIdx.z * a.R;
-#pragma unroll 1
-            for (int g = hf; g < 4; g += 2) {
-                uint32_t r32[32];
-                tmem_ld32(tA + lane_off + 32 * g, r32);
-                tmem_ld_wait();
-                if (o < a.O)
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        const int64_t r = 128 * rb + 32 * g + i;
-                        if (r < a.R) a.Apart[(base + r) * a.O + o] = __uint_as_float(r32[i]);
-                    }
-                if (WITH_B) {
-                    tmem_ld32(tB + lane_off + 32 * g, r32);
-                    tmem_ld_wait();
-                    if (o < a.O)
-#pragma unroll
-                        for (int i = 0; i < 32; ++i) {
-                            const int64_t r = 128 * rb + 32 * g + i;
-                            if (r < a.R) a.Bpart[(base + r) * a.O + o] = __uint_as_float(r32[i]);
-                        }
-                }
-            }
-        }
-    }
-    tc_fence_before();
-    __syncthreads();
-    if (tid == 0 && *abort) atomicOr(a.status, STATUS_TIMEOUT);
-    if (warp == 0) tmem_dealloc(tmem, L::NCOLS);
-}
 
 struct KsLayout2 {
     static constexpr uint32_t XS = OBLK * 64 * 2;
@@ -866,18 +612,6 @@ int launch_pass1(const P1Args& a, const TcMaps& m, int64_t O_pad, int splits, cu
     return after_launch();
 }
 
-template <int RP, bool WITH_B>
-int launch_pass1_ks(const P1Args& a, const TcMaps& m, int64_t O_pad, int splits, cudaStream_t st) {
-    const uint32_t smem = KsLayout1::TOTAL + 1024;
-    auto k = k_tc_pass1_ks<RP, WITH_B>;
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-        return DNA_ERR_CUDA;
-    dim3 grid((unsigned)(O_pad / OBLK), (unsigned)(RP / 128), (unsigned)splits);
-    k<<<grid, NTHREADS, smem, st>>>(a, m.x, m.y, m.yt, m.y2t, m.v);
-    return after_launch();
-}
-
 template <int RP>
 int launch_pass2_ks(const P2Args& a, const TcMaps& m, int64_t O_pad, int splits, cudaStream_t st) {
     const uint32_t smem = KsLayout2::TOTAL + 1024;
@@ -963,12 +697,8 @@ int TcBf16::pass1(const TcOperands& op, const TcMaps& maps, float* Apart, float*
     if (rp == 128)
         return with_b ? tc::launch_pass1<128, true>(a, maps, op.O_pad, splits, st)
                       : tc::launch_pass1<128, false>(a, maps, op.O_pad, splits, st);
-    if (rp == 256)
-        return with_b ? tc::launch_pass1_ks<256, true>(a, maps, op.O_pad, splits, st)
-                      : tc::launch_pass1_ks<256, false>(a, maps, op.O_pad, splits, st);
-    if (rp == 512)
-        return with_b ? tc::launch_pass1_ks<512, true>(a, maps, op.O_pad, splits, st)
-                      : tc::launch_pass1_ks<512, false>(a, maps, op.O_pad, splits, st);
+    if (rp == 256 || rp == 512)
+        return pass1_large(op, maps, Apart, Bpart, splits, s_per, with_b, status, st);
     return DNA_ERR_UNSUPPORTED;
 }
 

@@ -81,6 +81,15 @@ def test_bf16_half_steps(shape):
     _bf16_steps(p, 2)
 
 
+@pytest.mark.parametrize("shape", [(1500, 3000, 300), (2100, 1700, 256)],
+                         ids=lambda s: "x".join(map(str, s)))
+def test_bf16_large_rank_persistent_tiles(shape):
+    """Ranks above 128 at sizes where the persistent pass 1 gives a CTA several
+    (r-block, o-block, split) tiles and splits s into several 128-wide-chunk ranges."""
+    N, T, R = shape
+    _bf16_steps(workloads.custom(N, T, R, seed=N + T + R), 1)
+
+
 def test_bf16_plain_small_trajectory():
     """N=256 T=512 R=16: a free-running 5-iteration trajectory stays within the tolerance."""
     errs = _bf16_steps(workloads.plain_small(0), 5, restart=False)

@@ -11,12 +11,18 @@
 //     of 128 columns, A and B of the r-block (512 columns);
 //   * GEMM2 / GEMM3 A[o, r] += sum_s Q[o, s] Yt[r, s], B[o, r] += sum_s Qbar[o, s] Y2t[r, s]
 //     take Q from tensor memory and the r-block's rows of Y^t and (Y o Y)^t from a ring of
-//     half chunks (64 values of s).
+//     half chunks (64 values of s);
+//   * the epilogue reads V straight from global memory into registers, a half chunk ahead
+//     of its use, so that shared memory holds five K-slice stages: the K-slice ring is
+//     bound by the latency of its TMA round trip (about 2500 cycles from a stage's release
+//     to its next use), and each stage feeds only four MMAs.
 // Warp roles as in the split FP32 kernels (tc_split.cu): sixteen epilogue warps, a TMA
 // producer warp, one MMA-issuing warp for GEMM1 and one for GEMM2 / GEMM3.  Persistent:
 // CTA i takes the tiles [i T / G, (i + 1) T / G), numbered r-block-major so that the
 // r-block CTAs of one (split, o-block) stream the same V, X and Y tiles at the same time.
 #include <algorithm>
+#include <cfloat>
+#include <type_traits>
 
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -33,7 +39,7 @@ namespace ks {
 constexpr int SC = 128;   // values of s per chunk
 
 struct Layout {
-    static constexpr int KST = 3, HST = 2, VST = 2;
+    static constexpr int KST = 5, HST = 2;
     // K-slice stage: X [128 o][64 r] and Y [128 s][64 r], bf16, K-major 128-byte swizzled
     static constexpr uint32_t X_SLICE = OBLK * 64 * 2;
     static constexpr uint32_t Y_SLICE = SC * 64 * 2;
@@ -41,23 +47,20 @@ struct Layout {
     // H stage: the r-block's rows of Y^t and (Y o Y)^t for 64 values of s, [128 r][64 s]
     static constexpr uint32_t H_PLANE = 128 * SCH * 2;
     static constexpr uint32_t H_STAGE = 2 * H_PLANE;
-    // V stage: 64 values of s, [64 s][128 o] float32
-    static constexpr uint32_t V_STAGE = SCH * OBLK * 4;
     static constexpr uint32_t KR = 0;
     static constexpr uint32_t HR = KR + KST * K_STAGE;
-    static constexpr uint32_t VR = HR + HST * H_STAGE;
-    static constexpr uint32_t BAR = VR + VST * V_STAGE;
+    static constexpr uint32_t BAR = HR + HST * H_STAGE;
     static constexpr uint32_t TOTAL = BAR + 256;
     static constexpr uint32_t NCOLS = 512;
     // tensor memory: ZQ x 2 | A of the r-block | B of the r-block
     static constexpr uint32_t TA = 2 * SC, TB = TA + 128;
     static_assert(TB + 128 <= NCOLS, "tensor memory budget");
-    static_assert(K_STAGE % 1024 == 0 && HR % 1024 == 0 && VR % 1024 == 0, "alignment");
+    static_assert(K_STAGE % 1024 == 0 && HR % 1024 == 0, "alignment");
     static_assert(TOTAL + 1024 <= 232448, "shared memory budget");
 };
 
-enum { B_KFULL = 0, B_KEMPTY = 3, B_HFULL = 6, B_HEMPTY = 8, B_VFULL = 10, B_VEMPTY = 12,
-       B_ZFULL = 14, B_QFULL = 16, B_QEMPTY = 20, B_DRAIN = 22, B_COUNT = 24 };
+enum { B_KFULL = 0, B_KEMPTY = 5, B_HFULL = 10, B_HEMPTY = 12, B_ZFULL = 14, B_QFULL = 16,
+       B_QEMPTY = 20, B_DRAIN = 22, B_COUNT = 24 };
 
 // One tile: the 128 values of r of r-block rb, one o-block, one split of s.
 struct Tile {
@@ -103,11 +106,10 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
     k_tc_pass1_kt(P1Args a, int nob, int nsplit, int ntiles,
                   const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY,
                   const __grid_constant__ CUtensorMap tmYt,
-                  const __grid_constant__ CUtensorMap tmY2t,
-                  const __grid_constant__ CUtensorMap tmV) {
+                  const __grid_constant__ CUtensorMap tmY2t) {
     using L = ks::Layout;
     using namespace ks;
-    constexpr int KST = L::KST, HST = L::HST, VST = L::VST, KS = RP / 64;
+    constexpr int KST = L::KST, HST = L::HST, KS = RP / 64;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* sm = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -129,8 +131,6 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
         for (int i = 0; i < 2; ++i) {
             mbar_init(&bar[B_HFULL + i], 1);
             mbar_init(&bar[B_HEMPTY + i], 1);
-            mbar_init(&bar[B_VFULL + i], 1);
-            mbar_init(&bar[B_VEMPTY + i], W_EPI);
             mbar_init(&bar[B_ZFULL + i], 1);
             mbar_init(&bar[B_QEMPTY + i], 1);
             mbar_init(&bar[B_DRAIN + i], 1);
@@ -145,29 +145,17 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
     const uint32_t tmem = *tslot;
 
     if (warp == W_PRODUCER) {
-        // one thread services the three rings in whatever order their slots free up
+        // one thread services both rings in whatever order their slots free up
         if (lane == 0 && t_begin < t_end) {
             tma_prefetch_desc(&tmX); tma_prefetch_desc(&tmY); tma_prefetch_desc(&tmYt);
-            tma_prefetch_desc(&tmV);
             if (WITH_B) tma_prefetch_desc(&tmY2t);
-            Cursor ck_, ch_, cv_;
+            Cursor ck_, ch_;
             ck_.start(t_begin, nob, nsplit, a);
             ch_.start(t_begin, nob, nsplit, a);
-            cv_.start(t_begin, nob, nsplit, a);
-            int kk_ = 0, kh = 0, kv = 0;   // units issued per ring
+            int kk_ = 0, kh = 0;   // units issued per ring
             long long t0 = clock64();
-            while (ck_.t < t_end || ch_.t < t_end || cv_.t < t_end) {
+            while (ck_.t < t_end || ch_.t < t_end) {
                 bool prog = false;
-                if (cv_.t < t_end && mbar_test(&bar[B_VEMPTY + kv % VST], ((kv / VST) & 1) ^ 1)) {
-                    const int st = kv % VST;
-                    mbar_arrive_expect_tx(&bar[B_VFULL + st], L::V_STAGE);
-                    tma_load_2d(sbase + L::VR + st * L::V_STAGE, &tmV, (int32_t)cv_.x.o0,
-                                (int32_t)(cv_.x.s_begin + (int64_t)cv_.k * SC + SCH * cv_.sub),
-                                &bar[B_VFULL + st]);
-                    ++kv;
-                    cv_.next(2, nob, nsplit, a);
-                    prog = true;
-                }
                 if (ck_.t < t_end && mbar_test(&bar[B_KEMPTY + kk_ % KST], ((kk_ / KST) & 1) ^ 1)) {
                     // K-slice sub of the chunk: X [128 o][64 r] and Y [128 s][64 r]
                     const int st = kk_ % KST;
@@ -206,8 +194,6 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
                 }
             }
             if (*abort) {  // let the copies already issued land before the CTA exits
-                for (int k = max(0, kv - VST); k < kv; ++k)
-                    drain_phase(&bar[B_VFULL + k % VST], (k / VST) & 1);
                 for (int k = max(0, kk_ - KST); k < kk_; ++k)
                     drain_phase(&bar[B_KFULL + k % KST], (k / KST) & 1);
                 for (int k = max(0, kh - HST); k < kh; ++k)
@@ -300,7 +286,27 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
         const int qd = warp & 3, cg = warp >> 2;
         const int row = 32 * qd + lane;
         const uint32_t lane_off = (uint32_t)(32 * qd) << 16;
-        float zmin = 1.f;   // min over v > 0 of z (a non-positive z there: infinite cost)
+        // this thread's 16 values of v for half h of chunk k of tile x are p[j * vs] for
+        // j < n (0 for j >= n, outside the problem); each load instruction of the warp
+        // reads 128 contiguous bytes of a row of V
+        auto v_src = [&](const Tile& x, int k, int h, const float*& p, int& n) {
+            const int64_t o = x.o0 + row;
+            const int64_t s0 = x.s_begin + (int64_t)k * SC + 64 * h + 16 * cg;
+            const int64_t left = a.S - s0;
+            p = a.V + s0 * a.vs + o;
+            n = o < a.O ? (left < 16 ? (int)left : 16) : 0;
+        };
+        // v of the half chunk being processed; each value is replaced by the next half
+        // chunk's as soon as it has been used, so the loads fly for a whole half chunk
+        float vn[16];
+        if (t_begin < t_end) {
+            const float* p;
+            int n;
+            v_src(tile_of(t_begin, nob, nsplit, a), 0, 0, p, n);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) vn[j] = j < n ? __ldg(p + j * a.vs) : 0.f;
+        }
+        float qbmax = 0.f;   // an infinite qbar: z = 0 where v > 0 (infinite cost)
         bool ok = true;
         int m = 0;
         for (int t = t_begin; ok && t < t_end; ++t) {
@@ -312,38 +318,49 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
                 tc_fence_after();
 #pragma unroll 1
                 for (int h = 0; h < 2; ++h) {
-                    const int kv = 2 * m + h, vs = kv % VST;
-                    ok = wait_phase(&bar[B_VFULL + vs], (kv / VST) & 1, abort);
-                    if (!(ok = __all_sync(0xffffffffu, ok))) break;
                     const uint32_t col = tmem + b * SC + 64 * h + 16 * cg + lane_off;
                     uint32_t zr[16];
                     tmem_ld16(col, zr);
-                    // V rows s = 16 cg + j of this half; TMA zero-fills v outside the problem
-                    const float* Vs = reinterpret_cast<const float*>(sm + L::VR + vs * L::V_STAGE) +
-                                      16 * cg * OBLK + row;
-                    float vv[16];
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) vv[j] = Vs[j * OBLK];
+                    const float* pn = a.V;   // the next half chunk's v
+                    int nn = 0;
+                    if (h == 0)
+                        v_src(x, k, 1, pn, nn);
+                    else if (k + 1 < x.nch)
+                        v_src(x, k + 1, 0, pn, nn);
+                    else if (t + 1 < t_end)
+                        v_src(tile_of(t + 1, nob, nsplit, a), 0, 0, pn, nn);
                     tmem_ld_wait();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&bar[B_VEMPTY + vs]);
+                    // z >= 0 (a sum of products of non-negative operands); with v' = max(v, 0)
+                    // and z' = max(z, FLT_MIN), q = v' / z' and qbar = q / z' are 0 where
+                    // v = 0 (z = 0 there too) and equal v / z, v / z^2 elsewhere, unless
+                    // z = 0 where v > 0, which makes qbar infinite
                     uint32_t qp[8], qbp[8];
+                    auto make_q = [&](auto all_in) {
 #pragma unroll
-                    for (int j = 0; j < 16; j += 2) {
-                        float q[2], qb[2];
+                        for (int j = 0; j < 16; j += 2) {
+                            float q[2], qb[2];
 #pragma unroll
-                        for (int tt = 0; tt < 2; ++tt) {
-                            const float v = vv[j + tt];
-                            const float z = __uint_as_float(zr[j + tt]);
-                            const float rz = __fdividef(1.0f, z);
-                            const bool pos = v > 0.f;
-                            zmin = fminf(zmin, pos ? z : 1.f);
-                            q[tt] = pos ? v * rz : 0.f;
-                            qb[tt] = pos ? q[tt] * rz : 0.f;
+                            for (int tt = 0; tt < 2; ++tt) {
+                                const float v = fmaxf(vn[j + tt], 0.f);
+                                if (decltype(all_in)::value)
+                                    vn[j + tt] = __ldg(pn + (j + tt) * a.vs);
+                                else
+                                    vn[j + tt] =
+                                        j + tt < nn ? __ldg(pn + (j + tt) * a.vs) : 0.f;
+                                const float z = fmaxf(__uint_as_float(zr[j + tt]), FLT_MIN);
+                                const float rz = __fdividef(1.0f, z);
+                                q[tt] = v * rz;
+                                qb[tt] = q[tt] * rz;
+                                qbmax = fmaxf(qbmax, qb[tt]);
+                            }
+                            qp[j / 2] = pack_bf16x2(q[0], q[1]);
+                            qbp[j / 2] = pack_bf16x2(qb[0], qb[1]);
                         }
-                        qp[j / 2] = pack_bf16x2(q[0], q[1]);
-                        qbp[j / 2] = pack_bf16x2(qb[0], qb[1]);
-                    }
+                    };
+                    if (nn == 16)
+                        make_q(std::true_type{});
+                    else
+                        make_q(std::false_type{});
                     tmem_st8(col, qp);
                     if (WITH_B) tmem_st8(col + 8, qbp);
                     tmem_st_wait();
@@ -351,7 +368,6 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&bar[B_QFULL + 2 * b + h]);
                 }
-                if (!ok) break;
             }
             if (!ok) break;
             // GEMM2 / GEMM3 of the tile's last chunk done: its A and B rows of the r-block
@@ -377,7 +393,7 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
             }
             tc_fence_before();
         }
-        if (!(zmin > 0.f)) atomicOr(a.status, STATUS_NONFINITE);
+        if (!(qbmax <= FLT_MAX)) atomicOr(a.status, STATUS_NONFINITE);
     }
     tc_fence_before();
     __syncthreads();
@@ -397,7 +413,7 @@ int launch_pass1_kt(const P1Args& a, const TcMaps& m, int64_t O_pad, int splits,
     const int ntiles = (RP / 128) * nob * splits;
     if (ntiles == 0) return DNA_OK;
     const int grid = ctas > 0 ? std::min(ctas, ntiles) : ntiles;
-    k<<<grid, P1_THREADS, smem, st>>>(a, nob, splits, ntiles, m.x, m.y, m.yt, m.y2t, m.v);
+    k<<<grid, P1_THREADS, smem, st>>>(a, nob, splits, ntiles, m.x, m.y, m.yt, m.y2t);
     return after_launch();
 }
 

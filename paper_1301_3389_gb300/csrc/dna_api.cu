@@ -185,9 +185,9 @@ void plan_all(dna_ctx* c) {
                        &c->tper1[w], part, c->split ? SPLIT_MAX_CHUNKS : 0);
             plan_split(Sdim, c->pad_o[w] / tob, c->num_sms, sch, &c->tsp2[w], &c->tper2[w],
                        2.0 / (double)Sdim);
-            // pass 2 of the split form and of the BF16 form at R <= 128 balances (o-block,
+            // pass 2 of the split form and of the BF16 form at R <= 256 balances (o-block,
             // chunk) units over the SMs instead
-            if (c->split || c->rp <= 128)
+            if (c->split || c->rp <= 256)
                 c->tsp2[w] = dna::TcBf16::pass2_split_slots(c->pad_o[w], Sdim, c->num_sms);
         }
     }
@@ -447,7 +447,7 @@ int half_step(dna_ctx* c, int w, bool mu_only, bool prepared, bool next) {
     e = phase(c, DNA_PHASE_PASS2, 1, [&] {
         if constexpr (sizeof(Tp) == 4)
             if (tc)
-                return c->split || c->rp <= 128
+                return c->split || c->rp <= 256
                            ? dna::TcBf16::pass2_split(tc_operands(c, w), c->maps[w], c->dpart,
                                                       sp2, c->status, st)
                                 : dna::TcBf16::pass2(tc_operands(c, w), c->maps[w], c->dpart,

@@ -179,6 +179,7 @@ struct TcBf16 {
     static int pass1_split(const TcOperands& op, const TcMaps& maps, float* Apart,
                            float* Bpart, int splits, int64_t s_per, bool with_b, int* status,
                            cudaStream_t st);
+    // pass 2 of the split form (RP <= 128) and of the BF16 form (RP <= 256)
     static int pass2_split(const TcOperands& op, const TcMaps& maps, double* dpart, int slots,
                            int* status, cudaStream_t st);
     // cost slots per column that pass2_split writes (4 per CTA that an o-block spans)

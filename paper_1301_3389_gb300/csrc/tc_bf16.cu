@@ -1,7 +1,8 @@
 // tcgen05 tensor-core kernels of the DNA half-step, BF16 operands with FP32 accumulation
 // in TMEM (the precision form): pass 1 for padded rank RP in {64, 128}, and the K-streamed
-// passes 1 and 2 for RP in {256, 512} near the end of the file.  Pass 2 at RP <= 128 is
-// the balanced kernel of tc_split.cu, which takes the BF16 form with one operand plane.
+// pass 2 for RP = 512 near the end of the file.  Pass 1 at RP in {256, 512} is in
+// tc_ks.cu; pass 2 at RP <= 256 is the balanced kernel of tc_split.cu, which takes the
+// BF16 form with one operand plane.
 //
 // Pass 1 (Algorithm 1 steps 2-5 and 10), per CTA = 128 values of o (the TMEM lanes) and
 // an s-range streamed in chunks of 64:
@@ -319,7 +320,7 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
 }
 
 // ------------------------------------------------------------ large rank (RP > 128)
-// Pass 2 for RP in {256, 512}: the candidates' operand tiles do not fit in shared memory
+// Pass 2 for RP = 512: the candidates' operand tiles do not fit in shared memory
 // beside the rings, so X_mu, X_dna and Y stream through a ring of 64-wide K-slices for
 // every s-chunk (pass 1 at these ranks is in tc_ks.cu).
 
@@ -709,8 +710,7 @@ int TcBf16::pass2(const TcOperands& op, const TcMaps& maps, double* dpart, int s
     a.dpart = dpart; a.status = status;
     a.V = op.V; a.vs = op.vs; a.Xm = op.Xmk; a.Xd = op.Xdk; a.rp = rank_pad(op.R);
     const int rp = rank_pad(op.R);
-    // RP <= 128: pass2_split (tc_split.cu) takes both forms
-    if (rp == 256) return tc::launch_pass2_ks<256>(a, maps, op.O_pad, splits, st);
+    // RP <= 256: pass2_split (tc_split.cu)
     if (rp == 512) return tc::launch_pass2_ks<512>(a, maps, op.O_pad, splits, st);
     return DNA_ERR_UNSUPPORTED;
 }

@@ -891,6 +891,7 @@ int TcBf16::pass2_split(const TcOperands& op, const TcMaps& maps, double* dpart,
     } else {          // BF16 form
         if (a.rp == 64) return tc::launch_pass2s<64, 1, false>(a, maps, Op, slots, op.ctas, st);
         if (a.rp == 128) return tc::launch_pass2s<128, 1, false>(a, maps, Op, slots, op.ctas, st);
+        if (a.rp == 256) return tc::launch_pass2s<256, 1, false>(a, maps, Op, slots, op.ctas, st);
     }
     return DNA_ERR_UNSUPPORTED;
 }

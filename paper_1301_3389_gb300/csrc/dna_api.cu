@@ -183,12 +183,15 @@ void plan_all(dna_ctx* c) {
             const int sch1 = c->split || c->rp > 128 ? (int)SPLIT_CHUNK : tch;
             plan_split(Sdim, c->pad_o[w] / tob * rblocks, c->num_sms, sch1, &c->tsp1[w],
                        &c->tper1[w], part, c->split ? SPLIT_MAX_CHUNKS : 0);
-            plan_split(Sdim, c->pad_o[w] / tob, c->num_sms, sch, &c->tsp2[w], &c->tper2[w],
-                       2.0 / (double)Sdim);
+            plan_split(Sdim, c->pad_o[w] / tob, c->num_sms, c->rp > 256 ? (int)SPLIT_CHUNK : sch,
+                       &c->tsp2[w], &c->tper2[w], 2.0 / (double)Sdim);
             // pass 2 of the split form and of the BF16 form at R <= 256 balances (o-block,
-            // chunk) units over the SMs instead
+            // chunk) units over the SMs instead; at R > 256 each split has four cost slots
+            // (one per column group of the epilogue warps)
             if (c->split || c->rp <= 256)
                 c->tsp2[w] = dna::TcBf16::pass2_split_slots(c->pad_o[w], Sdim, c->num_sms);
+            else
+                c->tsp2[w] *= 4;
         }
     }
 }
@@ -450,8 +453,9 @@ int half_step(dna_ctx* c, int w, bool mu_only, bool prepared, bool next) {
                 return c->split || c->rp <= 256
                            ? dna::TcBf16::pass2_split(tc_operands(c, w), c->maps[w], c->dpart,
                                                       sp2, c->status, st)
-                                : dna::TcBf16::pass2(tc_operands(c, w), c->maps[w], c->dpart,
-                                                     sp2, c->tper2[w], c->status, st);
+                           : dna::TcBf16::pass2_large(tc_operands(c, w), c->maps[w],
+                                                      c->dpart, sp2, c->tper2[w], c->status,
+                                                      st);
         return S::pass2(v, Xmu, Xdna, c->dpart, sp2, c->per2[w], c->status, st);
     });
     if (e) return e;

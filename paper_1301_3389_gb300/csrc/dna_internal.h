@@ -171,8 +171,10 @@ struct TcBf16 {
     static int pass1_large(const TcOperands& op, const TcMaps& maps, float* Apart,
                            float* Bpart, int splits, int64_t s_per, bool with_b, int* status,
                            cudaStream_t st);
-    static int pass2(const TcOperands& op, const TcMaps& maps, double* dpart, int splits,
-                     int64_t s_per, int* status, cudaStream_t st);
+    // pass 2 at padded rank 512 (tc_ks.cu): persistent CTAs over (o-block, split) tiles,
+    // s_per a multiple of 128, cost slots dpart[4 splits][2][O]
+    static int pass2_large(const TcOperands& op, const TcMaps& maps, double* dpart, int slots,
+                           int64_t s_per, int* status, cudaStream_t st);
     // The FP32 form on the tensor cores (tc_split.cu): the same passes with every operand
     // split into hi + lo bf16 planes and three MMAs per product.  Pass 1 runs 2 x splits
     // CTA rows (A and B accumulated by separate CTAs; with_b = false: A only).

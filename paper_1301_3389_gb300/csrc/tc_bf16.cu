@@ -1,8 +1,7 @@
 // tcgen05 tensor-core kernels of the DNA half-step, BF16 operands with FP32 accumulation
-// in TMEM (the precision form): pass 1 for padded rank RP in {64, 128}, and the K-streamed
-// pass 2 for RP = 512 near the end of the file.  Pass 1 at RP in {256, 512} is in
-// tc_ks.cu; pass 2 at RP <= 256 is the balanced kernel of tc_split.cu, which takes the
-// BF16 form with one operand plane.
+// in TMEM (the precision form): pass 1 for padded rank RP in {64, 128}.  Both passes at
+// RP = 512, and pass 1 at RP = 256, are in tc_ks.cu; pass 2 at RP <= 256 is the balanced
+// kernel of tc_split.cu, which takes the BF16 form with one operand plane.
 //
 // Pass 1 (Algorithm 1 steps 2-5 and 10), per CTA = 128 values of o (the TMEM lanes) and
 // an s-range streamed in chunks of 64:
@@ -319,195 +318,6 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
     if (warp == 0) tmem_dealloc(tmem, L::NCOLS);
 }
 
-// ------------------------------------------------------------ large rank (RP > 128)
-// Pass 2 for RP = 512: the candidates' operand tiles do not fit in shared memory
-// beside the rings, so X_mu, X_dna and Y stream through a ring of 64-wide K-slices for
-// every s-chunk (pass 1 at these ranks is in tc_ks.cu).
-
-constexpr int KS_STAGES = 3;
-
-enum { K_KFULL = 0, K_KEMPTY = 3, K_VFULL = 6, K_VEMPTY = 8, K_BFULL = 10, K_BEMPTY = 11,
-       K_ZFULL = 12, K_ZEMPTY = 14, K_QFULL = 16, K_QEMPTY = 17, K_ACC = 18, K_DRAIN = 19,
-       K_COUNT = 20 };
-
-struct KsLayout2 {
-    static constexpr uint32_t XS = OBLK * 64 * 2;
-    static constexpr uint32_t YS = SCH * 64 * 2;
-    static constexpr uint32_t KSTAGE = 2 * XS + YS;        // Xmu, Xdna, Y slices
-    static constexpr uint32_t KR = 0;
-    static constexpr uint32_t V_BYTES = SCH * OBLK * 4;
-    static constexpr uint32_t VR = KR + KS_STAGES * KSTAGE;
-    static constexpr uint32_t RED = VR + 2 * V_BYTES;
-    static constexpr uint32_t BAR = RED + 2 * OBLK * 8;
-    static constexpr uint32_t TOTAL = BAR + 256;
-    static constexpr uint32_t NCOLS = 4 * SCH;
-    static_assert(KSTAGE % 1024 == 0 && VR % 1024 == 0, "");
-    static_assert(TOTAL + 1024 <= 232448, "shared memory budget");
-};
-
-template <int RP>
-__global__ void __launch_bounds__(NTHREADS, 1)
-    k_tc_pass2_ks(P2Args a, const __grid_constant__ CUtensorMap tmXm,
-                  const __grid_constant__ CUtensorMap tmXd, const __grid_constant__ CUtensorMap tmY,
-                  const __grid_constant__ CUtensorMap tmV) {
-    using L = KsLayout2;
-    constexpr int KS = RP / 64;
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char* sm = reinterpret_cast<unsigned char*>(
-        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    const uint32_t sbase = smem_u32(sm);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + L::BAR);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L::BAR + K_COUNT * 8);
-    volatile int* abort = reinterpret_cast<volatile int*>(sm + L::BAR + K_COUNT * 8 + 8);
-
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int64_t o0 = (int64_t)blockIdx.x * OBLK;
-    const int64_t s_begin = (int64_t)blockIdx.y * a.s_per;
-    const int64_t s_end = min(a.S, s_begin + a.s_per);
-    const int nch = s_end > s_begin ? (int)((s_end - s_begin + SCH - 1) / SCH) : 0;
-
-    if (warp == 0) { tmem_alloc(tslot, L::NCOLS); tmem_relinquish(); }
-    if (tid == MMA_WARP * 32) {
-        for (int i = 0; i < KS_STAGES; ++i) {
-            mbar_init(&bar[K_KFULL + i], 1);
-            mbar_init(&bar[K_KEMPTY + i], 1);
-        }
-        for (int i = 0; i < 2; ++i) {
-            mbar_init(&bar[K_VFULL + i], 1);
-            mbar_init(&bar[K_VEMPTY + i], NEPI_WARPS);
-            mbar_init(&bar[K_ZFULL + i], 1);
-            mbar_init(&bar[K_ZEMPTY + i], NEPI_WARPS);
-        }
-        mbar_init(&bar[K_DRAIN], 1);
-        *abort = 0;
-        fence_mbar_init();
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = *tslot;
-
-    if (warp == PRODUCER_WARP) {
-        if (lane == 0 && nch > 0) {
-            tma_prefetch_desc(&tmXm); tma_prefetch_desc(&tmXd); tma_prefetch_desc(&tmY);
-            tma_prefetch_desc(&tmV);
-            int lastK[KS_STAGES] = {-1, -1, -1}, lastV[2] = {-1, -1};
-            bool ok = true;
-            for (int k = 0; k < nch && ok; ++k) {
-                const int32_t s0 = (int32_t)(s_begin + (int64_t)k * SCH);
-                const int vs = k & 1;
-                if (!(ok = wait_phase(&bar[K_VEMPTY + vs], ((k >> 1) & 1) ^ 1, abort))) break;
-                mbar_arrive_expect_tx(&bar[K_VFULL + vs], L::V_BYTES);
-                tma_load_2d(sbase + L::VR + vs * L::V_BYTES, &tmV, (int32_t)o0, s0, &bar[K_VFULL + vs]);
-                lastV[vs] = k;
-                for (int ks = 0; ks < KS; ++ks) {
-                    const int j = k * KS + ks, st = j % KS_STAGES;
-                    if (!(ok = wait_phase(&bar[K_KEMPTY + st], ((j / KS_STAGES) & 1) ^ 1, abort))) break;
-                    const uint32_t kb = sbase + L::KR + st * L::KSTAGE;
-                    mbar_arrive_expect_tx(&bar[K_KFULL + st], L::KSTAGE);
-                    tma_load_2d(kb, &tmXm, 64 * ks, (int32_t)o0, &bar[K_KFULL + st]);
-                    tma_load_2d(kb + L::XS, &tmXd, 64 * ks, (int32_t)o0, &bar[K_KFULL + st]);
-                    tma_load_2d(kb + 2 * L::XS, &tmY, 64 * ks, s0, &bar[K_KFULL + st]);
-                    lastK[st] = j;
-                }
-            }
-            if (*abort) {
-                for (int st = 0; st < KS_STAGES; ++st)
-                    if (lastK[st] >= 0) drain_phase(&bar[K_KFULL + st], (lastK[st] / KS_STAGES) & 1);
-                for (int vs = 0; vs < 2; ++vs)
-                    if (lastV[vs] >= 0) drain_phase(&bar[K_VFULL + vs], (lastV[vs] >> 1) & 1);
-            }
-        }
-    } else if (warp == MMA_WARP) {
-        if (lane == 0 && nch > 0) {
-            bool ok = true;
-            for (int k = 0; ok && k < nch; ++k) {
-                const int zb = k & 1;
-                if (!(ok = wait_phase(&bar[K_ZEMPTY + zb], ((k >> 1) & 1) ^ 1, abort))) break;
-                tc_fence_after();
-                const uint32_t tz = tmem + zb * 2 * SCH;
-                for (int ks = 0; ks < KS && ok; ++ks) {
-                    const int j = k * KS + ks, st = j % KS_STAGES;
-                    if (!(ok = wait_phase(&bar[K_KFULL + st], (j / KS_STAGES) & 1, abort))) break;
-                    tc_fence_after();
-                    const uint32_t kb = sbase + L::KR + st * L::KSTAGE;
-#pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {
-                        const uint64_t yd = desc_sw128(kb + 2 * L::XS + 32u * kk);
-                        const uint32_t acc = (ks > 0 || kk > 0) ? 1u : 0u;
-                        mma_bf16(tz, desc_sw128(kb + 32u * kk), yd, idesc_bf16(OBLK, SCH), acc);
-                        mma_bf16(tz + SCH, desc_sw128(kb + L::XS + 32u * kk), yd,
-                                 idesc_bf16(OBLK, SCH), acc);
-                    }
-                    mma_commit(&bar[K_KEMPTY + st]);
-                }
-                if (!ok) break;
-                mma_commit(&bar[K_ZFULL + zb]);
-            }
-            if (!ok) {
-                mma_commit(&bar[K_DRAIN]);
-                drain_phase(&bar[K_DRAIN], 0);
-            }
-        }
-    } else {
-        const int qd = warp & 3, hf = warp >> 2;
-        const int row = 32 * qd + lane;
-        const int64_t o = o0 + row;
-        const uint32_t lane_off = (uint32_t)(32 * qd) << 16;
-        double acc_m = 0.0, acc_d = 0.0;
-        bool bad = false;
-        bool ok = true;
-        for (int k = 0; k < nch; ++k) {
-            const int zb = k & 1;
-            const uint32_t par = (k >> 1) & 1;
-            ok = wait_phase(&bar[K_ZFULL + zb], par, abort);
-            ok = ok && wait_phase(&bar[K_VFULL + zb], par, abort);
-            if (!(ok = __all_sync(0xffffffffu, ok))) break;
-            tc_fence_after();
-            const uint32_t tz = tmem + zb * 2 * SCH + lane_off + 32 * hf;
-            uint32_t zm[32], zd[32];
-            tmem_ld32(tz, zm);
-            tmem_ld32(tz + SCH, zd);
-            tmem_ld_wait();
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&bar[K_ZEMPTY + zb]);
-            const float* Vs = reinterpret_cast<const float*>(sm + L::VR + zb * L::V_BYTES) +
-                              32 * hf * OBLK + row;
-            float run_m = 0.f, run_d = 0.f;
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const float v = Vs[j * OBLK];
-                const float z1 = __uint_as_float(zm[j]), z2 = __uint_as_float(zd[j]);
-                const bool pos = v > 0.f;
-                bad |= pos && !(z1 > 0.f && z2 > 0.f);
-                const float l1 = __logf(z1), l2 = __logf(z2);
-                run_m += pos ? z1 - v * l1 : z1;
-                run_d += pos ? z2 - v * l2 : z2;
-            }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&bar[K_VEMPTY + zb]);
-            acc_m += (double)run_m;
-            acc_d += (double)run_d;
-        }
-        if (bad) atomicOr(a.status, STATUS_NONFINITE);
-        double* red = reinterpret_cast<double*>(sm + L::RED);
-        if (hf == 1) {
-            red[row] = acc_m;
-            red[OBLK + row] = acc_d;
-        }
-        asm volatile("bar.sync 1, %0;" ::"r"(NEPI_WARPS * 32) : "memory");
-        if (hf == 0 && ok && nch > 0 && !*abort && o < a.O) {
-            a.dpart[((int64_t)blockIdx.y * 2 + 0) * a.O + o] = acc_m + red[row];
-            a.dpart[((int64_t)blockIdx.y * 2 + 1) * a.O + o] = acc_d + red[OBLK + row];
-        }
-    }
-    tc_fence_before();
-    __syncthreads();
-    if (tid == 0 && *abort) atomicOr(a.status, STATUS_TIMEOUT);
-    if (warp == 0) tmem_dealloc(tmem, L::NCOLS);
-}
-
 // dst[i][j] (leading dimension ld, padded to rows_pad x cols_pad with zeros) =
 // bf16(src(i, j)) (squared first when `square`), where src(i, j) = src[i * si + j * sj]
 // for i < rows, j < cols, and one of si, sj is 1.  32 x 32 tiles through shared memory.
@@ -613,18 +423,6 @@ int launch_pass1(const P1Args& a, const TcMaps& m, int64_t O_pad, int splits, cu
     return after_launch();
 }
 
-template <int RP>
-int launch_pass2_ks(const P2Args& a, const TcMaps& m, int64_t O_pad, int splits, cudaStream_t st) {
-    const uint32_t smem = KsLayout2::TOTAL + 1024;
-    auto k = k_tc_pass2_ks<RP>;
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-        return DNA_ERR_CUDA;
-    dim3 grid((unsigned)(O_pad / OBLK), (unsigned)splits);
-    k<<<grid, NTHREADS, smem, st>>>(a, m.xm, m.xd, m.y, m.v);
-    return after_launch();
-}
-
 }  // namespace tc
 
 int TcBf16::rank_pad(int64_t R) {
@@ -700,18 +498,6 @@ int TcBf16::pass1(const TcOperands& op, const TcMaps& maps, float* Apart, float*
                       : tc::launch_pass1<128, false>(a, maps, op.O_pad, splits, st);
     if (rp == 256 || rp == 512)
         return pass1_large(op, maps, Apart, Bpart, splits, s_per, with_b, status, st);
-    return DNA_ERR_UNSUPPORTED;
-}
-
-int TcBf16::pass2(const TcOperands& op, const TcMaps& maps, double* dpart, int splits,
-                  int64_t s_per, int* status, cudaStream_t st) {
-    tc::P2Args a{};
-    a.S = op.S; a.O = op.O; a.R = op.R; a.s_per = s_per;
-    a.dpart = dpart; a.status = status;
-    a.V = op.V; a.vs = op.vs; a.Xm = op.Xmk; a.Xd = op.Xdk; a.rp = rank_pad(op.R);
-    const int rp = rank_pad(op.R);
-    // RP <= 256: pass2_split (tc_split.cu)
-    if (rp == 512) return tc::launch_pass2_ks<512>(a, maps, op.O_pad, splits, st);
     return DNA_ERR_UNSUPPORTED;
 }
 

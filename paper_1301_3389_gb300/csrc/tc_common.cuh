@@ -14,9 +14,6 @@ namespace tc {
 
 constexpr int OBLK = 128;      // o per CTA (MMA M, TMEM lanes)
 constexpr int SCH = 64;        // s per chunk (GEMM1 N, GEMM2 K)
-constexpr int NEPI_WARPS = 8;  // epilogue: two warps per TMEM lane quadrant
-constexpr int NTHREADS = 320;  // warps 0-7 epilogue, 8 TMA producer, 9 MMA issuer
-constexpr int PRODUCER_WARP = 8, MMA_WARP = 9;
 constexpr long long WAIT_LIMIT = 4000000000LL;  // SM cycles (about 2 s) per wait
 
 using bf16 = __nv_bfloat16;

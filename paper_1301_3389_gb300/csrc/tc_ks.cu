@@ -1,5 +1,7 @@
-// tcgen05 pass 1 of the BF16 form for padded rank RP in {256, 512} (Algorithm 1 steps 2-5
-// and 10).  Tensor memory cannot hold X (the A operand of GEMM1) beside Z and both
+// tcgen05 passes of the BF16 form at large padded rank: pass 1 for RP in {256, 512}
+// (Algorithm 1 steps 2-5 and 10) and pass 2 for RP = 512 (after it in this file).
+//
+// Pass 1.  Tensor memory cannot hold X (the A operand of GEMM1) beside Z and both
 // accumulators at these ranks, so
 //   * GEMM1 Z[o, s] = sum_r X[o, r] Y[s, r] takes both operands from shared memory: X and
 //     Y stream together through a ring of 64-wide K-slices (M = 128, N = 128, K = 16 per
@@ -67,7 +69,8 @@ struct Tile {
     int64_t o0, s_begin;
     int nch, rb, split;
 };
-__device__ __forceinline__ Tile tile_of(int t, int nob, int nsplit, const P1Args& a) {
+template <typename Args>
+__device__ __forceinline__ Tile tile_of(int t, int nob, int nsplit, const Args& a) {
     Tile x;
     const int per_rb = nob * nsplit;
     x.rb = t / per_rb;
@@ -85,11 +88,13 @@ __device__ __forceinline__ Tile tile_of(int t, int nob, int nsplit, const P1Args
 struct Cursor {
     int t, k, sub;
     Tile x;
-    __device__ __forceinline__ void start(int t0, int nob, int nsplit, const P1Args& a) {
+    template <typename Args>
+    __device__ __forceinline__ void start(int t0, int nob, int nsplit, const Args& a) {
         t = t0; k = 0; sub = 0;
         x = tile_of(t, nob, nsplit, a);
     }
-    __device__ __forceinline__ void next(int per_chunk, int nob, int nsplit, const P1Args& a) {
+    template <typename Args>
+    __device__ __forceinline__ void next(int per_chunk, int nob, int nsplit, const Args& a) {
         if (++sub < per_chunk) return;
         sub = 0;
         if (++k < x.nch) return;
@@ -417,6 +422,235 @@ int launch_pass1_kt(const P1Args& a, const TcMaps& m, int64_t O_pad, int splits,
     return after_launch();
 }
 
+// ---------------------------------------------------------------- pass 2, RP = 512
+// Candidate costs (Algorithm 1 steps 6-9 and 19-22): Z_mu = X_mu Y^t and Z_dna = X_dna
+// Y^t per chunk of 128 values of s, both operands from shared memory (tensor memory holds
+// two Z pairs, 4 x 128 columns, and no X), X_mu, X_dna and Y streaming together through a
+// ring of 64-wide K-slices (eight MMAs per slice, alternating between the candidates);
+// the epilogue reads V from global memory a half chunk ahead, as in pass 1, and sums
+// d' = sum_s (z - v log z) (v > 0; z where v = 0) per column and candidate in float32
+// over a chunk, then in float64.  Persistent over (o-block, split) tiles, o-block fastest,
+// so CTAs that run at the same time share the Y slices in L2.  Each epilogue warp writes
+// its own sums: cost slot 4 split + w / 4 of dpart[slot][2][O].
+namespace ks {
+struct Layout2 {
+    static constexpr int KST = 4;
+    static constexpr uint32_t X_SLICE = OBLK * 64 * 2;   // [128 o][64 r]
+    static constexpr uint32_t Y_SLICE = SC * 64 * 2;     // [128 s][64 r]
+    static constexpr uint32_t K_STAGE = 2 * X_SLICE + Y_SLICE;
+    static constexpr uint32_t BAR = KST * K_STAGE;
+    static constexpr uint32_t TOTAL = BAR + 256;
+    static constexpr uint32_t NCOLS = 512;   // (Z_mu, Z_dna) x 2, 128 columns each
+    static_assert(K_STAGE % 1024 == 0, "alignment");
+    static_assert(TOTAL + 1024 <= 232448, "shared memory budget");
+};
+enum { C_KFULL = 0, C_KEMPTY = 4, C_ZFULL = 8, C_ZEMPTY = 10, C_DRAIN = 12, C_COUNT = 14 };
+constexpr int P2K_THREADS = (W_EPI + 2) * 32;   // epilogue warps, producer, MMA issuer
+}  // namespace ks
+
+template <int RP>
+__global__ void __launch_bounds__(ks::P2K_THREADS, 1)
+    k_tc_pass2_kt(P2Args a, int nob, int nsplit, int ntiles,
+                  const __grid_constant__ CUtensorMap tmXm, const __grid_constant__ CUtensorMap tmXd,
+                  const __grid_constant__ CUtensorMap tmY) {
+    using L = ks::Layout2;
+    using namespace ks;
+    constexpr int KST = L::KST, KS = RP / 64;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* sm = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const uint32_t sbase = smem_u32(sm);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + L::BAR);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L::BAR + C_COUNT * 8);
+    volatile int* abort = reinterpret_cast<volatile int*>(sm + L::BAR + C_COUNT * 8 + 8);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int t_begin = (int)((int64_t)blockIdx.x * ntiles / gridDim.x);
+    const int t_end = (int)((int64_t)(blockIdx.x + 1) * ntiles / gridDim.x);
+
+    if (warp == 0) { tmem_alloc(tslot, L::NCOLS); tmem_relinquish(); }
+    if (tid == W_PRODUCER * 32) {
+        for (int i = 0; i < KST; ++i) {
+            mbar_init(&bar[C_KFULL + i], 1);
+            mbar_init(&bar[C_KEMPTY + i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&bar[C_ZFULL + i], 1);
+            mbar_init(&bar[C_ZEMPTY + i], W_EPI);
+            mbar_init(&bar[C_DRAIN + i], 1);
+        }
+        *abort = 0;
+        fence_mbar_init();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    if (warp == W_PRODUCER) {
+        if (lane == 0 && t_begin < t_end) {
+            tma_prefetch_desc(&tmXm); tma_prefetch_desc(&tmXd); tma_prefetch_desc(&tmY);
+            Cursor ck_;
+            ck_.start(t_begin, nob, nsplit, a);
+            int kk_ = 0;
+            bool ok = true;
+            for (; ok && ck_.t < t_end; ++kk_, ck_.next(KS, nob, nsplit, a)) {
+                const int st = kk_ % KST;
+                if (!(ok = wait_phase(&bar[C_KEMPTY + st], ((kk_ / KST) & 1) ^ 1, abort))) break;
+                // K-slice sub of the chunk: X_mu, X_dna [128 o][64 r], Y [128 s][64 r]
+                const uint32_t dst = sbase + st * L::K_STAGE;
+                const int32_t r0 = 64 * ck_.sub;
+                const int32_t s0 = (int32_t)(ck_.x.s_begin + (int64_t)ck_.k * SC);
+                mbar_arrive_expect_tx(&bar[C_KFULL + st], L::K_STAGE);
+                tma_load_2d(dst, &tmXm, r0, (int32_t)ck_.x.o0, &bar[C_KFULL + st]);
+                tma_load_2d(dst + L::X_SLICE, &tmXd, r0, (int32_t)ck_.x.o0, &bar[C_KFULL + st]);
+                tma_load_2d(dst + 2 * L::X_SLICE, &tmY, r0, s0, &bar[C_KFULL + st]);
+                tma_load_2d(dst + 2 * L::X_SLICE + SCH * 128, &tmY, r0, s0 + SCH,
+                            &bar[C_KFULL + st]);
+            }
+            if (*abort)   // let the copies already issued land before the CTA exits
+                for (int k = max(0, kk_ - KST); k < kk_; ++k)
+                    drain_phase(&bar[C_KFULL + k % KST], (k / KST) & 1);
+        }
+    } else if (warp == W_EPI + 1) {
+        // Z_mu(m), Z_dna(m) into pair buffer m & 1, K-slice by K-slice
+        if (lane == 0) {
+            bool ok = true;
+            int m = 0, j = 0;
+            constexpr uint32_t idesc = idesc_bf16(OBLK, SC);
+            for (int t = t_begin; ok && t < t_end; ++t) {
+                const int nch = tile_of(t, nob, nsplit, a).nch;
+                for (int k = 0; ok && k < nch; ++k, ++m) {
+                    const int b = m & 1;
+                    // the epilogue has read chunk m - 2 out of this buffer pair
+                    if (m >= 2 &&
+                        !(ok = wait_phase(&bar[C_ZEMPTY + b], ((m - 2) >> 1) & 1, abort)))
+                        break;
+                    tc_fence_after();
+                    const uint32_t zm = tmem + b * 2 * SC, zd = zm + SC;
+#pragma unroll 1
+                    for (int ks = 0; ks < KS; ++ks, ++j) {
+                        if (!(ok = wait_phase(&bar[C_KFULL + j % KST], (j / KST) & 1, abort)))
+                            break;
+                        const uint32_t xs = sbase + (j % KST) * L::K_STAGE;
+                        const uint32_t ys = xs + 2 * L::X_SLICE;
+#pragma unroll
+                        for (int kq = 0; kq < 4; ++kq) {
+                            const uint64_t yd = desc_sw128(ys + 32u * kq);
+                            const uint32_t acc = (ks > 0 || kq > 0) ? 1u : 0u;
+                            mma_bf16(zm, desc_sw128(xs + 32u * kq), yd, idesc, acc);
+                            mma_bf16(zd, desc_sw128(xs + L::X_SLICE + 32u * kq), yd, idesc, acc);
+                        }
+                        mma_commit(&bar[C_KEMPTY + j % KST]);
+                    }
+                    if (ok) mma_commit(&bar[C_ZFULL + b]);
+                }
+            }
+            if (!ok) {
+                mma_commit(&bar[C_DRAIN + 0]);
+                drain_phase(&bar[C_DRAIN + 0], 0);
+            }
+        }
+    } else if (warp < W_EPI) {
+        // epilogue warp: lanes o = o0 + 32 qd + lane; in half h of a chunk the 16 values
+        // s = 64 h + 16 cg .. + 15
+        const int qd = warp & 3, cg = warp >> 2;
+        const int row = 32 * qd + lane;
+        const uint32_t lane_off = (uint32_t)(32 * qd) << 16;
+        auto v_src = [&](const Tile& x, int k, int h, const float*& p, int& n) {
+            const int64_t o = x.o0 + row;
+            const int64_t s0 = x.s_begin + (int64_t)k * SC + 64 * h + 16 * cg;
+            const int64_t left = a.S - s0;
+            p = a.V + s0 * a.vs + o;
+            n = o < a.O ? (left < 16 ? (int)left : 16) : 0;
+        };
+        float vn[16];   // v of the half chunk being processed, then of the next one
+        if (t_begin < t_end) {
+            const float* p;
+            int n;
+            v_src(tile_of(t_begin, nob, nsplit, a), 0, 0, p, n);
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) vn[jj] = jj < n ? __ldg(p + jj * a.vs) : 0.f;
+        }
+        bool ok = true, bad = false;
+        int m = 0;
+        for (int t = t_begin; ok && t < t_end; ++t) {
+            const Tile x = tile_of(t, nob, nsplit, a);
+            double acc_m = 0.0, acc_d = 0.0;
+            for (int k = 0; k < x.nch; ++k, ++m) {
+                const int b = m & 1;
+                ok = wait_phase(&bar[C_ZFULL + b], (m >> 1) & 1, abort);
+                if (!(ok = __all_sync(0xffffffffu, ok))) break;   // keep the warp converged
+                tc_fence_after();
+                float run_m = 0.f, run_d = 0.f;
+#pragma unroll 1
+                for (int h = 0; h < 2; ++h) {
+                    const uint32_t col = tmem + b * 2 * SC + 64 * h + 16 * cg + lane_off;
+                    uint32_t zm[16], zd[16];
+                    tmem_ld16(col, zm);
+                    tmem_ld16(col + SC, zd);
+                    const float* pn = a.V;   // the next half chunk's v
+                    int nn = 0;
+                    if (h == 0)
+                        v_src(x, k, 1, pn, nn);
+                    else if (k + 1 < x.nch)
+                        v_src(x, k + 1, 0, pn, nn);
+                    else if (t + 1 < t_end)
+                        v_src(tile_of(t + 1, nob, nsplit, a), 0, 0, pn, nn);
+                    tmem_ld_wait();
+                    if (h == 1) {   // both halves of the pair read: buffer free for chunk m + 2
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&bar[C_ZEMPTY + b]);
+                    }
+#pragma unroll
+                    for (int jj = 0; jj < 16; ++jj) {
+                        const float v = vn[jj];
+                        vn[jj] = jj < nn ? __ldg(pn + jj * a.vs) : 0.f;
+                        const float z1 = __uint_as_float(zm[jj]), z2 = __uint_as_float(zd[jj]);
+                        const bool pos = v > 0.f;
+                        bad |= pos && !(z1 > 0.f && z2 > 0.f);
+                        // the hardware logarithm (absolute error near 2^-21 around 1,
+                        // relative 2^-21 elsewhere), far below the bf16 operand rounding
+                        run_m += pos ? z1 - v * __logf(z1) : z1;
+                        run_d += pos ? z2 - v * __logf(z2) : z2;
+                    }
+                }
+                acc_m += (double)run_m;
+                acc_d += (double)run_d;
+            }
+            if (!ok) break;
+            const int64_t o = x.o0 + row;
+            if (o < a.O) {
+                const int64_t slot = 4 * (int64_t)x.split + cg;
+                a.dpart[(slot * 2 + 0) * a.O + o] = acc_m;
+                a.dpart[(slot * 2 + 1) * a.O + o] = acc_d;
+            }
+        }
+        if (bad) atomicOr(a.status, STATUS_NONFINITE);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0 && *abort) atomicOr(a.status, STATUS_TIMEOUT);
+    if (warp == 0) tmem_dealloc(tmem, L::NCOLS);
+}
+
+template <int RP>
+int launch_pass2_kt(const P2Args& a, const TcMaps& m, int64_t O_pad, int splits, int ctas,
+                    cudaStream_t st) {
+    const uint32_t smem = ks::Layout2::TOTAL + 1024;
+    auto k = k_tc_pass2_kt<RP>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return DNA_ERR_CUDA;
+    const int nob = (int)(O_pad / OBLK);
+    const int ntiles = nob * splits;
+    if (ntiles == 0) return DNA_OK;
+    const int grid = ctas > 0 ? std::min(ctas, ntiles) : ntiles;
+    k<<<grid, ks::P2K_THREADS, smem, st>>>(a, nob, splits, ntiles, m.xm, m.xd, m.y);
+    return after_launch();
+}
+
 }  // namespace tc
 
 int TcBf16::pass1_large(const TcOperands& op, const TcMaps& maps, float* Apart, float* Bpart,
@@ -432,6 +666,19 @@ int TcBf16::pass1_large(const TcOperands& op, const TcMaps& maps, float* Apart, 
     if (a.rp == 512)
         return with_b ? tc::launch_pass1_kt<512, true>(a, maps, op.O_pad, splits, op.ctas, st)
                       : tc::launch_pass1_kt<512, false>(a, maps, op.O_pad, splits, op.ctas, st);
+    return DNA_ERR_UNSUPPORTED;
+}
+
+int TcBf16::pass2_large(const TcOperands& op, const TcMaps& maps, double* dpart, int slots,
+                        int64_t s_per, int* status, cudaStream_t st) {
+    tc::P2Args a{};
+    a.S = op.S; a.O = op.O; a.R = op.R; a.s_per = s_per;
+    a.dpart = dpart; a.status = status;
+    a.V = op.V; a.vs = op.vs; a.Xm = op.Xmk; a.Xd = op.Xdk; a.rp = rank_pad(op.R);
+    if (s_per % tc::ks::SC != 0 || slots % 4 != 0) return DNA_ERR_ARG;
+    const int splits = slots / 4;
+    if (splits != (int)((op.S + s_per - 1) / s_per)) return DNA_ERR_ARG;
+    if (a.rp == 512) return tc::launch_pass2_kt<512>(a, maps, op.O_pad, splits, op.ctas, st);
     return DNA_ERR_UNSUPPORTED;
 }
 

@@ -15,9 +15,10 @@
 //     take Q from tensor memory and the r-block's rows of Y^t and (Y o Y)^t from a ring of
 //     half chunks (64 values of s);
 //   * the epilogue reads V straight from global memory into registers, a half chunk ahead
-//     of its use, so that shared memory holds five K-slice stages: the K-slice ring is
-//     bound by the latency of its TMA round trip (about 2500 cycles from a stage's release
-//     to its next use), and each stage feeds only four MMAs.
+//     of its use, so shared memory carries only the MMA operands: per chunk RP / 2 KB of X
+//     and Y slices (written by TMA, read by GEMM1; five K-slice stages) and 64 KB of the
+//     r-block's Y^t and (Y o Y)^t rows.  That traffic and the chain GEMM1(m) -> epilogue(m)
+//     -> GEMM2/3(m) -> GEMM1(m + 2) through the two ZQ buffers bound the kernel.
 // Warp roles as in the split FP32 kernels (tc_split.cu): sixteen epilogue warps, a TMA
 // producer warp, one MMA-issuing warp for GEMM1 and one for GEMM2 / GEMM3.  Persistent:
 // CTA i takes the tiles [i T / G, (i + 1) T / G), numbered r-block-major so that the

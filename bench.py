@@ -199,7 +199,8 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["dna", "reference"], default="dna")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched"], default="plain_large")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched", "unrolled"],
+                    default="plain_large")
     ap.add_argument("--dtype", choices=["f32", "f64", "bf16"], default="f32")
     ap.add_argument("--engine", choices=["auto", "simt", "tensor"], default=None,
                     help="default: tensor for f32 with R <= 128 (split bf16 products), else auto")
@@ -219,6 +220,8 @@ def main(argv=None):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.workload == "batched":
         return run_batched(args, world, rank, local)
+    if args.workload == "unrolled":
+        return run_unrolled(args, world, rank, local)
     spec = WORKLOADS[args.workload]
 
     if args.impl == "reference":
@@ -556,6 +559,101 @@ def run_batched(args, world, rank, local):
                                      f"flop x {sm_max:.0f} MHz")},
         "clocks": clk,
         "kl_sum_start": float(np.sum(kl0)), "kl_sum_end": float(np.sum(kl1)),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+UNROLLED_K, UNROLLED_EVERY = 20, 5
+
+
+def run_unrolled(args, world, rank, local):
+    """The differentiation form: one step = the K = 20 unrolled DNA H-solve at fixed W
+    (checkpoints every 5 steps), the loss d_KL(V, W H_K) + (mu / 2) |H_K|^2 and its
+    backward pass to V and H0, through the autograd wrappers (N=1024 T=4096 R=64)."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_1301_3389_gb300.autograd import KLDiv, UnrolledDNAH
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    prob = workloads.diff_form(rank)
+    dev = torch.device("cuda", local)
+    dt = torch.float64 if args.dtype == "f64" else torch.float32
+    N, T = prob.V.shape
+    R = prob.W.shape[1]
+    mu = 1e-3 * float(prob.V.mean()) / float(prob.H.mean()) ** 2
+    V = torch.from_numpy(prob.V).to(dev, dt).requires_grad_(True)
+    W = torch.from_numpy(prob.W).to(dev, dt)
+    H0 = torch.from_numpy(prob.H).to(dev, dt).requires_grad_(True)
+
+    def step():
+        V.grad = None
+        H0.grad = None
+        HK = UnrolledDNAH.apply(V, W, H0, UNROLLED_K, UNROLLED_EVERY)
+        loss = KLDiv.apply(V, W, HK) + 0.5 * mu * (HK.double() ** 2).sum()
+        loss.backward()
+        return loss
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    # V is 16 MB: L2 is flushed (a 256 MB write) before every step, outside its events
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        loss = step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms += ev0.elapsed_time(ev1)
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms_max = max_over_ranks(torch, dist, ms, dev) if world > 1 else ms
+    if world > 1:
+        dist.destroy_process_group()
+    value = job_rate(world, args.steps, ms_max)
+    # forward: K H half-steps of about 10 R N T flop; backward: the segments' recomputed
+    # steps (K - K / every) plus K adjoint steps of about 10 R N T each (z recomputed, the
+    # two z-tiles P1, P2 and H-bar's product), and d_KL's backward (4 R N T)
+    K, ev = UNROLLED_K, UNROLLED_EVERY
+    flops = (K + (K - K // ev) + K) * 10 * R * N * T + 4 * R * N * T
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    if dt == torch.float64:
+        alu, alu_src = 1.25, "nominal GB300 FP64 rate (1.25 TFLOP/s)"
+    else:
+        alu = SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+        alu_src = f"derived: {SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {sm_max:.0f} MHz"
+    step_s = ms_max / args.steps / 1e3
+    achieved = flops / step_s / 1e12
+    line = {
+        "metric": METRIC, "value": value,
+        "unit": "unrolled-solve forward + backward steps/s (K = 20 H half-steps)",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if dt == torch.float64 else "f32",
+        "data": "synthetic",
+        "config": {"workload": "unrolled", "N": N, "T": T, "R": R, "K": K, "every": ev,
+                   "mu": mu, "engine": "CUDA cores (F32 / F64 forms)",
+                   "l2": "L2 flushed (256 MB write) before each step, outside the timed events"},
+        "roofline": {"bound": "alu", "kernel": "whole forward + backward step",
+                     "achieved": achieved, "peak": alu, "unit": "TFLOP/s",
+                     "frac": achieved / alu, "traffic": None,
+                     "algorithmic_flops_per_step": flops, "peak_source": alu_src},
+        "clocks": clk, "loss": float(loss),
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -34,14 +34,15 @@ struct GProb {
     uint8_t* choice[2];        // O per view
     int64_t per1[2], per2[2];  // rows of s per split
     int sp1[2], sp2[2];
-    int rclass;                // 0: R <= 32, 1: R <= 64
+    int rclass;                // rank class: 0: R <= 16, 1: R <= 32, 2: R <= 64
 };
 
 struct GTile {
     int32_t prob, a, b, pad;
 };
 
-constexpr int NCLASS = 2;
+constexpr int NCLASS = 3;   // r-blocks of 16, 32 and 64 (rank padding at most 2x past R = 8)
+constexpr int class_of_rb(int rb) { return rb == 16 ? 0 : rb == 32 ? 1 : 2; }
 constexpr int64_t MIN_SPLIT_ROWS = 256;   // smallest s-range per split (bounds the workspace)
 
 template <int RB, bool WITH_B>
@@ -193,7 +194,7 @@ struct dna_group {
     // tile lists [view][class] for the passes, [view] for the rest
     TileList p1[2][dna::grp::NCLASS], p2[2][dna::grp::NCLASS], kl[dna::grp::NCLASS];
     TileList cand[2], sums_y[2], sums_x[2], resc[2];
-    int slots1[dna::grp::NCLASS] = {1, 1}, slots2[dna::grp::NCLASS] = {1, 1};
+    int slots1[dna::grp::NCLASS] = {1, 1, 1}, slots2[dna::grp::NCLASS] = {1, 1, 1};
     int64_t split_rows = 1024;  // rows of s per split (autotuned)
     bool bound = false, use_graph = false;
     cudaGraphExec_t gexec = nullptr;
@@ -268,7 +269,8 @@ int build_tiles(dna_group* g) {
             p.sp1[w] = p.sp2[w] = (int)((S + per - 1) / per);
         }
     }
-    std::vector<GTile> t1[2][2], t2[2][2], tk[2], tc[2], ty[2], tx[2], tr[2];
+    constexpr int NC = dna::grp::NCLASS;
+    std::vector<GTile> t1[2][NC], t2[2][NC], tk[NC], tc[2], ty[2], tx[2], tr[2];
     for (int q = 0; q < g->count; ++q) {
         const GProb& p = g->hp[q];
         for (int w = 0; w < 2; ++w) {
@@ -291,7 +293,7 @@ int build_tiles(dna_group* g) {
     }
     int e = DNA_OK;
     for (int w = 0; w < 2; ++w) {
-        for (int k = 0; k < 2; ++k) {
+        for (int k = 0; k < NC; ++k) {
             e |= upload(g, t1[w][k], &g->p1[w][k]);
             e |= upload(g, t2[w][k], &g->p2[w][k]);
         }
@@ -300,7 +302,7 @@ int build_tiles(dna_group* g) {
         e |= upload(g, tx[w], &g->sums_x[w]);
         e |= upload(g, tr[w], &g->resc[w]);
     }
-    for (int k = 0; k < 2; ++k) e |= upload(g, tk[k], &g->kl[k]);
+    for (int k = 0; k < NC; ++k) e |= upload(g, tk[k], &g->kl[k]);
     if (e) return e;
     if (cudaMemcpy(g->dp, g->hp.data(), sizeof(GProb) * g->count, cudaMemcpyHostToDevice) !=
         cudaSuccess)
@@ -318,7 +320,7 @@ template <int RB>
 int launch_p1(dna_group* g, const TileList& t, int w, bool with_b) {
     using namespace dna::grp;
     if (!t.n) return DNA_OK;
-    const int grid = grid_for(t.n, g->slots1[RB == 32 ? 0 : 1]);
+    const int grid = grid_for(t.n, g->slots1[dna::grp::class_of_rb(RB)]);
     if (with_b)
         k_g_pass1<RB, true><<<grid, simt::NT, p1_smem<RB>(), g->gs>>>(g->dp, t.d, t.n, w, g->status);
     else
@@ -330,7 +332,7 @@ template <int RB, bool FULL>
 int launch_p2(dna_group* g, const TileList& t, int w) {
     using namespace dna::grp;
     if (!t.n) return DNA_OK;
-    const int grid = grid_for(t.n, g->slots2[RB == 32 ? 0 : 1]);
+    const int grid = grid_for(t.n, g->slots2[dna::grp::class_of_rb(RB)]);
     k_g_pass2<RB, 2, FULL><<<grid, simt::NT, p2_smem<RB>(), g->gs>>>(g->dp, t.d, t.n, w, g->status);
     return after_launch();
 }
@@ -362,13 +364,15 @@ int g_normalize(dna_group* g, int which) {
 int g_half(dna_group* g, int w, bool mu_only) {
     const double reg_den = w ? g->o.rho : g->o.lambda;
     int e = launch_small(g, 0, g->sums_y[w], w, reg_den);
-    if (!e) e = launch_p1<32>(g, g->p1[w][0], w, !mu_only);
-    if (!e) e = launch_p1<64>(g, g->p1[w][1], w, !mu_only);
+    if (!e) e = launch_p1<16>(g, g->p1[w][0], w, !mu_only);
+    if (!e) e = launch_p1<32>(g, g->p1[w][1], w, !mu_only);
+    if (!e) e = launch_p1<64>(g, g->p1[w][2], w, !mu_only);
     if (e) return e;
     if (mu_only) return DNA_ERR_UNSUPPORTED;
     e = launch_small(g, 3, g->cand[w], w);
-    if (!e) e = launch_p2<32, false>(g, g->p2[w][0], w);
-    if (!e) e = launch_p2<64, false>(g, g->p2[w][1], w);
+    if (!e) e = launch_p2<16, false>(g, g->p2[w][0], w);
+    if (!e) e = launch_p2<32, false>(g, g->p2[w][1], w);
+    if (!e) e = launch_p2<64, false>(g, g->p2[w][2], w);
     if (!e) e = launch_small(g, 4, g->cand[w], w);
     if (!e) e = g_normalize(g, w == 1 ? 1 : 0);
     return e;
@@ -438,8 +442,9 @@ int dna_group_create(int count, const int64_t* N, const int64_t* T, const int64_
         cudaEventCreateWithFlags(&g->ev_in, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&g->ev_out, cudaEventDisableTiming) != cudaSuccess)
         e = DNA_ERR_CUDA;
-    if (!e) e = prep_class<32>(g, 0);
-    if (!e) e = prep_class<64>(g, 1);
+    if (!e) e = prep_class<16>(g, 0);
+    if (!e) e = prep_class<32>(g, 1);
+    if (!e) e = prep_class<64>(g, 2);
     // arena: per problem Vt, V sums, factor sums, A/B partials (worst split count), candidates,
     // cost partials, final costs, choices
     // the largest split counts any plan can use (splits of at least MIN_SPLIT_ROWS rows)
@@ -489,7 +494,7 @@ int dna_group_create(int count, const int64_t* N, const int64_t* T, const int64_
         p.dfin[0] = reinterpret_cast<double*>(b); p.dfin[1] = p.dfin[0] + 2 * t;
         b += al(8 * 2 * (n + t));
         p.choice[0] = b; p.choice[1] = b + t;
-        p.rclass = r <= 32 ? 0 : 1;
+        p.rclass = r <= 16 ? 0 : r <= 32 ? 1 : 2;
         // views without the caller's buffers yet
         View& vh = p.v[0];
         vh.S = n; vh.O = t; vh.R = r; vh.vsum = colsum;
@@ -654,8 +659,9 @@ int dna_group_kl(dna_group* g, double* out) {
     {
         Handoff h(g);
         if (h.err) return h.err;
-        e = launch_p2<32, true>(g, g->kl[0], 0);
-        if (!e) e = launch_p2<64, true>(g, g->kl[1], 0);
+        e = launch_p2<16, true>(g, g->kl[0], 0);
+        if (!e) e = launch_p2<32, true>(g, g->kl[1], 0);
+        if (!e) e = launch_p2<64, true>(g, g->kl[2], 0);
         if (!e) {
             k_g_kl_reduce<<<std::min(g->count, 1024), 256, 0, g->gs>>>(g->dp, g->count, g->kl_dev);
             e = dna::after_launch();
@@ -678,7 +684,7 @@ int64_t dna_group_launches_per_iteration(dna_group* g) {
     int64_t n = 0;
     for (int w = 0; w < 2; ++w) {
         n += 5;  // sums, candidates, select, normaliser sums, rescale
-        for (int k = 0; k < 2; ++k) n += (g->p1[w][k].n > 0) + (g->p2[w][k].n > 0);
+        for (int k = 0; k < dna::grp::NCLASS; ++k) n += (g->p1[w][k].n > 0) + (g->p2[w][k].n > 0);
     }
     return n;
 }

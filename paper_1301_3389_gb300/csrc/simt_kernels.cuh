@@ -283,7 +283,6 @@ __device__ __forceinline__ void pass2_tile(const View& v, const Tp* __restrict__
         }
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const int64_t o = o0 + zo + j;
             Tp run[NC];
 #pragma unroll
             for (int c = 0; c < NC; ++c) run[c] = Tp(0);

@@ -70,8 +70,10 @@ def _bf16_steps(p, iters, check_costs=True, restart=True):
 
 SHAPES = [(200, 300, 16), (130, 257, 64), (256, 512, 100), (70, 1000, 128), (1000, 70, 128),
           (129, 131, 65), (1, 1, 1),
-          # ranks above 128: the K-streamed kernels (RP = 256, 512)
-          (300, 500, 200), (257, 300, 512), (640, 130, 300)]
+          # ranks above 128: the large-rank kernels (RP = 256, 512), including the
+          # smallest rank of each padding class and ragged o-blocks and chunks
+          (300, 500, 200), (257, 300, 512), (640, 130, 300), (150, 700, 129), (700, 150, 257),
+          (333, 1025, 256)]
 
 
 @pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(map(str, s)))

@@ -283,6 +283,22 @@ def main(argv=None):
                                       "ms_per_step": sm["ms_max"] / sargs.steps,
                                       "roofline": sm["roofline"], "gpu_launches": sm["launches"]}
         line["time_to_target"] = time_to_target(dna, torch, prob, args.target_iters, args.engine)
+        if args.workload == "plain_large":
+            # the BF16 form at its own headline size (N=8192 T=32768 R=512), 20 iterations
+            pspec = WORKLOADS["precision_large"]
+            pprob = pspec["fn"](rank)
+            pargs = argparse.Namespace(**vars(args))
+            pargs.steps = max(3, min(args.steps, 20))
+            pargs.workload = "precision_large"   # the traffic record of that workload
+            pr = measure(dna, torch, dist, pprob, "bf16", pargs, world, local, peaks,
+                         clocks=False)
+            line["precision_form"] = {
+                "value": pr["value"], "unit": UNIT, "steps": pargs.steps,
+                "ms_per_step": pr["ms_max"] / pargs.steps, "roofline": pr["roofline"],
+                "gpu_launches": pr["launches"],
+                "config": {"workload": "precision_large", "desc": pspec["desc"],
+                           "N": pspec["N"], "T": pspec["T"], "R": pspec["R"], "form": "BF16"}}
+            del pprob
 
     if rank == 0 and not args.no_e2e:
         code = {"f32": dna.DNA_F32, "f64": dna.DNA_F64, "bf16": dna.DNA_BF16}[args.dtype]

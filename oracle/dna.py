@@ -22,11 +22,15 @@ Readings taken where the paper is silent, ambiguous or garbled (each is tested):
 * The floor [x]_eps = max(x, eps) applies to the gain of the a < 0 branch only.
 * "EM" in steps 15 and 28 is the MU candidate.
 * Selection: the Newton candidate is kept iff d_DNA < d_MU; ties keep MU (step 15).
-* The per-column (per-row) cost compared in steps 9, 14, 22, 27 is
-  d' = sum_{v>0} (-v log z) + sum z, i.e. eq. 1 restricted to that column (row) minus
-  the candidate-independent constant sum v log v - sum v.  Under eq. 9 the sum-z term
-  is the same for both candidates, so this orders them exactly as steps 9/14 do, and it
-  stays a true cost comparison when eq. 9 holds only up to rounding.
+* The per-column cost compared in steps 9 and 14 is the eq. 5 sub-problem cost of that
+  column minus a candidate-independent constant:
+  d' = sum_{v>0} (-v log z) + sum z + lambda sum_r h_r, i.e. eq. 1 restricted to the
+  column, plus the eq. 5 penalty lambda 1^t h, minus sum v log v - sum v.  Per row of W
+  (steps 22, 27) the penalty is rho sum_r w_r (eq. 4).  Under eq. 9,
+  sum z + lambda sum h = sum v for both candidates, so this orders them exactly as
+  steps 9/14 do (1^t (V log Q)), and it stays a true cost comparison when eq. 9 holds only
+  up to rounding.  (At lambda > 0, sum z alone differs between the candidates by
+  -lambda sum h, so the penalty term cannot be dropped.)
 * Zeros in V (note after Algorithm 1): q = v/z and v/z^2 are 0 where v = 0, and such
   entries add only z to the cost.
 * z <= 0 where v > 0 cannot happen with positive factors; it raises NonFiniteError.
@@ -158,8 +162,8 @@ class HalfStep:
     A: np.ndarray        # eq. 7 a, for every entry
     B: np.ndarray        # eq. 14 b, for every entry
     c: np.ndarray        # denominators (W^t 1 + lambda) or (H 1 + rho)
-    d_mu: np.ndarray     # per-column (row) cost of the MU candidate
-    d_dna: np.ndarray    # per-column (row) cost of the Newton candidate
+    d_mu: np.ndarray     # per-column (row) eq. 5 (eq. 4) cost of the MU candidate, less a constant
+    d_dna: np.ndarray    # the same for the Newton candidate
     choice: np.ndarray   # True where the Newton candidate is kept
     margin: np.ndarray   # |d_dna - d_mu| / max(|d_mu|, tiny)
 
@@ -179,7 +183,7 @@ def h_half_step(V, W, H, eps: float = EPS, alpha: float = ALPHA, lam: float = 0.
     A = (W.T @ Q) / c[:, None] - 1.0              # step 5 (eq. 7)
     H_mu = H + A * H                              # step 6 (eq. 11)
     Z_mu = W @ H_mu                               # step 7
-    d_mu = column_cost(V, Z_mu)                   # steps 8-9
+    d_mu = column_cost(V, Z_mu) + lam * H_mu.sum(axis=0)     # steps 8-9, eq. 5 cost
     Qb = ratio(V, Z, 2)                           # step 10
     B = (W2.T @ Qb) / c[:, None]                  #         (eq. 14)
     H_dna = newton_candidate(H, A, B, eps, alpha)  # step 11 (eq. 15, 17)
@@ -190,7 +194,7 @@ def h_half_step(V, W, H, eps: float = EPS, alpha: float = ALPHA, lam: float = 0.
     scale[ok] = s[ok] / den[ok]
     H_dna = H_dna * scale[None, :]
     Z_dna = W @ H_dna                             # step 12
-    d_dna = column_cost(V, Z_dna)                 # steps 13-14
+    d_dna = column_cost(V, Z_dna) + lam * H_dna.sum(axis=0)  # steps 13-14, eq. 5 cost
     if choice is None:
         choice = d_dna < d_mu                     # step 15, ties keep MU
     choice = np.asarray(choice, dtype=bool)
@@ -210,7 +214,7 @@ def w_half_step(V, W, H, eps: float = EPS, alpha: float = ALPHA, rho: float = 0.
     A = (Q @ H.T) / c[None, :] - 1.0              # step 18
     W_mu = W + A * W                              # step 19
     Z_mu = W_mu @ H                               # step 20
-    d_mu = row_cost(V, Z_mu)                      # steps 21-22
+    d_mu = row_cost(V, Z_mu) + rho * W_mu.sum(axis=1)        # steps 21-22, eq. 4 cost
     Qb = ratio(V, Z, 2)                           # step 23
     B = (Qb @ H2.T) / c[None, :]
     W_dna = newton_candidate(W, A, B, eps, alpha)  # step 24
@@ -221,7 +225,7 @@ def w_half_step(V, W, H, eps: float = EPS, alpha: float = ALPHA, rho: float = 0.
     scale[ok] = s[ok] / den[ok]
     W_dna = W_dna * scale[:, None]
     Z_dna = W_dna @ H                             # step 25
-    d_dna = row_cost(V, Z_dna)                    # steps 26-27
+    d_dna = row_cost(V, Z_dna) + rho * W_dna.sum(axis=1)     # steps 26-27, eq. 4 cost
     if choice is None:
         choice = d_dna < d_mu                     # step 28, ties keep MU
     choice = np.asarray(choice, dtype=bool)

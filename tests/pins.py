@@ -211,6 +211,46 @@ def check_monotone(iters=25):
         assert np.all(o.row_cost(V, Wm @ Hm) <= before + 1e-12 * np.abs(before)), "MU W"
 
 
+def _eq5_cost_columns(V, W, X, lam):
+    """Eq. 5 per column, evaluated directly: sum kl_div(v, W h) + lambda 1^t h."""
+    return np.array([float(np.sum(special.kl_div(V[:, t], W @ X[:, t]))) + lam * X[:, t].sum()
+                     for t in range(V.shape[1])])
+
+
+def check_regularised_selection(reg=2.0, seeds=range(8), iters=3):
+    """At lambda, rho > 0 the selection orders the candidates by the eq. 5 (eq. 4) cost.
+
+    For every column (row) of several H (W) half-steps, the Newton candidate is kept iff
+    its sub-problem cost d_KL + lambda 1^t h (per row: + rho 1^t w), evaluated here directly
+    with SciPy's kl_div, is below the MU candidate's (Section 2.4; ties and rounding-level
+    margins are skipped), and the kept candidate's cost is not above that of the factor the
+    half-step started from (MU never increases it, [20])."""
+    for seed in seeds:
+        V, W, H = rand_problem(12, 30, 4, 100 + seed)
+        W, H = o.normalize_w_columns(W, H, reg)
+        for _ in range(iters):
+            hs = o.h_half_step(V, W, H, lam=reg)
+            e_mu = _eq5_cost_columns(V, W, hs.X_mu, reg)
+            e_dna = _eq5_cost_columns(V, W, hs.X_dna, reg)
+            clear = np.abs(e_dna - e_mu) > 1e-10 * np.abs(e_mu)
+            assert np.array_equal(hs.choice[clear], (e_dna < e_mu)[clear]), \
+                f"H-step selection disagrees with the eq. 5 cost (seed {seed})"
+            e_old = _eq5_cost_columns(V, W, H, reg)
+            e_new = _eq5_cost_columns(V, W, hs.X, reg)
+            assert np.all(e_new <= e_old + 1e-10 * np.abs(e_old)), "eq. 5 cost increased"
+            W, H, _ = o.dna_step_h(V, W, H, rho=reg, lam=reg)
+            ws = o.w_half_step(V, W, H, rho=reg)
+            e_mu = _eq5_cost_columns(V.T, H.T, ws.X_mu.T, reg)
+            e_dna = _eq5_cost_columns(V.T, H.T, ws.X_dna.T, reg)
+            clear = np.abs(e_dna - e_mu) > 1e-10 * np.abs(e_mu)
+            assert np.array_equal(ws.choice[clear], (e_dna < e_mu)[clear]), \
+                f"W-step selection disagrees with the eq. 4 cost (seed {seed})"
+            e_old = _eq5_cost_columns(V.T, H.T, W.T, reg)
+            e_new = _eq5_cost_columns(V.T, H.T, ws.X.T, reg)
+            assert np.all(e_new <= e_old + 1e-10 * np.abs(e_old)), "eq. 4 cost increased"
+            W, H, _ = o.dna_step_w(V, W, H, rho=reg, lam=reg)
+
+
 def check_fixed_point():
     """At an exact factorisation a = 0, so MU and DNA leave W and H unchanged (Section 2.1-2.2)."""
     g = np.random.default_rng(10)
@@ -312,4 +352,4 @@ ALL = [check_kl_definition, check_costs_sum_to_kl, check_a_b_finite_differences,
        check_w_a_b_finite_differences, check_r1_golden, check_r1_random,
        check_step_limits_golden, check_eq9_invariant, check_monotone, check_fixed_point,
        check_transpose_symmetry, check_scale_equivariance, check_normalisation_steps,
-       check_brute_force_tiny]
+       check_brute_force_tiny, check_regularised_selection]

@@ -39,6 +39,14 @@ MUTATIONS = {
                            "choice = d_dna > d_mu                     # step 15"),
     "renorm_uses_row_sums": ("s = V.sum(axis=0)                             # 1^t V",
                              "s = V.sum()                             # 1^t V"),
+    "h_cost_without_lambda_term": ("column_cost(V, Z_mu) + lam * H_mu.sum(axis=0)",
+                                   "column_cost(V, Z_mu)"),
+    "h_dna_cost_without_lambda_term": ("column_cost(V, Z_dna) + lam * H_dna.sum(axis=0)",
+                                       "column_cost(V, Z_dna)"),
+    "w_cost_without_rho_term": ("row_cost(V, Z_mu) + rho * W_mu.sum(axis=1)",
+                                "row_cost(V, Z_mu)"),
+    "w_dna_cost_without_rho_term": ("row_cost(V, Z_dna) + rho * W_dna.sum(axis=1)",
+                                    "row_cost(V, Z_dna)"),
 }
 
 EXTRA = [lambda: pins.check_a_b_finite_differences(lam=0.3),

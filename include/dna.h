@@ -160,8 +160,10 @@ int dna_get_choice(dna_ctx* ctx, int which, uint8_t* out, int64_t len);
 
 /* Copy the per-column (which = 0, T values) or per-row (which = 1, N values) costs of
  * the two candidates of the last DNA half-step to host memory:
- * d = sum_{v>0} (-v log z) + sum z over that column (row) (Algorithm 1 steps 9, 14, 22,
- * 27, with the candidate-independent constant dropped).  Synchronises. */
+ * d = sum_{v>0} (-v log z) + sum z + lambda sum_r h_r over that column (per row:
+ * + rho sum_r w_r), i.e. the eq. 5 (eq. 4) sub-problem cost with the
+ * candidate-independent constant sum v log v - sum v dropped (Algorithm 1 steps 9, 14,
+ * 22, 27).  The selection keeps the Newton candidate iff its d is lower.  Synchronises. */
 int dna_get_costs(dna_ctx* ctx, int which, double* d_mu, double* d_dna, int64_t len);
 
 /* Synchronise the stream and return the sticky device status (DNA_OK or an error). */
@@ -250,6 +252,12 @@ int dna_group_kl(dna_group* g, double* out);
 /* Synchronise and return the sticky status of the group's kernels. */
 int dna_group_get_status(dna_group* g);
 
+/* dna_get_choice for problem q of the group: the selection (Section 2.4, Algorithm 1
+ * steps 15 / 28) of its last DNA half-step, 1 = Newton, per column of H (which = 0,
+ * len = T[q]) or per row of W (which = 1, len = N[q]), copied to host memory.
+ * Synchronises. */
+int dna_group_get_choice(dna_group* g, int q, int which, uint8_t* out, int64_t len);
+
 /* Kernel launches of one grouped iteration (both half-steps). */
 int64_t dna_group_launches_per_iteration(dna_group* g);
 
@@ -259,9 +267,9 @@ void dna_group_destroy(dna_group* g);
 /* Capacity, in float64 partial sums, of the static scratch of dna_kl_noalloc. */
 #define DNA_KL_NOALLOC_MAX_PARTIALS (1 << 20)
 
-/* d_KL(V, W H) (eq. 1), like dna_kl, for callers that cannot allocate device memory:
- * code whose device memory is all owned by another framework's pool allocator, and
- * latency-critical code that cannot pay for cudaMalloc or the implicit device
+/* d_KL(V, W H), the value dna_kl returns, for callers that cannot allocate device
+ * memory: code whose device memory is all owned by another framework's pool allocator,
+ * and latency-critical code that cannot pay for cudaMalloc or the implicit device
  * synchronisation of cudaFree.  The paper has no counterpart of this entry point.
  *
  * Needs no context and allocates nothing: it calls no cudaMalloc, cudaFree or
@@ -276,9 +284,15 @@ void dna_group_destroy(dna_group* g);
  * returned before any work is queued.
  *
  * The first call on a device looks up the device address of the static array (with that
- * device current); make that first call before any stream capture.  All calls share the
- * one array: calls that overlap on the GPU (for example on two unordered streams) race
- * and give wrong results, so order them, e.g. on one stream. */
+ * device current) and keeps it for later calls on that device; make that first call
+ * before any stream capture.  The kept address belongs to the CUDA context current at
+ * that first call (the device's primary context when the runtime API is used): callers
+ * that switch that device to another driver context, or reset it, must not call this
+ * entry point afterwards.  All calls share the one array: calls that overlap on the GPU
+ * (for example on two unordered streams) race and give wrong results, so order them,
+ * e.g. on one stream.  The partial sums (splits x T of them, splits <= 32) are added by a
+ * single 1024-thread block at the end, a few microseconds for T in the thousands and up
+ * to tens of microseconds near the capacity. */
 int dna_kl_noalloc(const float* V, int64_t ldv, const float* W, const float* H, int64_t N,
                    int64_t T, int64_t R, double* kl_out, void* stream);
 

@@ -79,6 +79,7 @@ def _load() -> ctypes.CDLL:
         "dna_group_autotune": (I, [P, I, P]),
         "dna_group_kl": (I, [P, P]),
         "dna_group_get_status": (I, [P]),
+        "dna_group_get_choice": (I, [P, I, I, P, I64]),
         "dna_group_launches_per_iteration": (I64, [P]),
         "dna_group_destroy": (None, [P]),
         "dna_destroy": (None, [P]),
@@ -252,8 +253,18 @@ def dna_kl_noalloc(V, W, H, out, stream=None, ldv: int | None = None) -> None:
 
     Allocates nothing (static scratch inside the library); calls that overlap on the GPU
     race, so keep them ordered on one stream."""
+    import torch
     N, T = V.shape
     R = W.shape[1]
+    for name, t in (("V", V), ("W", W), ("H", H)):
+        if t.dtype != torch.float32 or not t.is_cuda:
+            raise DNAError(DNA_ERR_ARG, f"dna_kl_noalloc: {name} must be a float32 CUDA tensor")
+    if W.shape[0] != N or tuple(H.shape) != (R, T):
+        raise DNAError(DNA_ERR_ARG, "dna_kl_noalloc: shapes must be V (N, T), W (N, R), H (R, T)")
+    if not (W.is_contiguous() and H.is_contiguous()) or V.stride(1) != 1:
+        raise DNAError(DNA_ERR_ARG, "dna_kl_noalloc: W, H contiguous and V rows contiguous")
+    if out.dtype != torch.float64 or not out.is_cuda or out.numel() < 1:
+        raise DNAError(DNA_ERR_ARG, "dna_kl_noalloc: out must be a float64 CUDA tensor")
     if ldv is None:
         ldv = V.stride(0)
     _check(LIB.dna_kl_noalloc(_ptr(V), ldv, _ptr(W), _ptr(H), N, T, R, _ptr(out),
@@ -325,6 +336,13 @@ def dna_group_kl(g: int, count: int):
 
 def dna_group_get_status(g: int) -> int:
     return LIB.dna_group_get_status(g)
+
+
+def dna_group_get_choice(g: int, q: int, which: int, n: int):
+    import numpy as np
+    out = np.zeros(n, dtype=np.uint8)
+    _check(LIB.dna_group_get_choice(g, q, which, out.ctypes.data, n), "dna_group_get_choice")
+    return out.astype(bool)
 
 
 def dna_group_launches_per_iteration(g: int) -> int:

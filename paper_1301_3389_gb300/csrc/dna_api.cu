@@ -340,7 +340,8 @@ int step_h_fixed(dna_ctx* c, uint8_t* choice_out) {
         return S::pass2(v, Xmu, Xdna, c->dpart, c->sp2[0], c->per2[0], c->status, st);
     });
     if (!e) e = phase(c, DNA_PHASE_SELECT, 1, [&] {
-        return S::select(v, Xmu, Xdna, c->dpart, c->sp2[0], c->choice_h, c->dfin_h, st);
+        return S::select(v, Xmu, Xdna, c->dpart, c->sp2[0], c->choice_h, c->dfin_h, c->o.lambda,
+                         st);
     });
     if (!e && choice_out &&
         cudaMemcpyAsync(choice_out, c->choice_h, (size_t)c->T, cudaMemcpyDeviceToDevice, st) !=
@@ -461,7 +462,8 @@ int half_step(dna_ctx* c, int w, bool mu_only, bool prepared, bool next) {
     if (e) return e;
     e = phase(c, DNA_PHASE_SELECT, 1, [&] {
         return S::select_fused(v, Xmu, Xdna, c->dpart, sp2, w ? c->choice_w : c->choice_h,
-                               w ? c->dfin_w : c->dfin_h, c->gpart, st);
+                               w ? c->dfin_w : c->dfin_h, c->gpart, w ? c->o.rho : c->o.lambda,
+                               st);
     });
     if (e) return e;
     // steps 16 / 29: f_r = sum over o of the new x(r, o) + (rho | lambda)

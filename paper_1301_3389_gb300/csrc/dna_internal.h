@@ -66,9 +66,11 @@ template <typename Tp> struct Simt {
     // pass 2: per-column costs of the two candidates, float64 partials [splits][2][O]
     static int pass2(const View& v, const Tp* Xmu, const Tp* Xdna, double* dpart, int splits,
                      int64_t s_per, int* status, cudaStream_t st);
-    // selection: x(r, o) <- Newton if d_dna < d_mu else MU; choice and final costs
+    // selection: x(r, o) <- Newton if d_dna < d_mu else MU, each d being the pass-2 sum
+    // plus reg * sum_r x (the eq. 5 penalty; reg = lambda for H, rho for W); choice and
+    // final costs
     static int select(const View& v, const Tp* Xmu, const Tp* Xdna, const double* dpart,
-                      int splits, uint8_t* choice, double* dfin, cudaStream_t st);
+                      int splits, uint8_t* choice, double* dfin, double reg, cudaStream_t st);
     // per-column full KL terms of eq. 1 for x = the view's X, partials [splits][O]
     static int kl_columns(const View& v, double* dpart, int splits, int64_t s_per,
                           int* status, cudaStream_t st);
@@ -100,7 +102,7 @@ template <typename Tp> struct Simt {
     // Selection as above, plus fpart[glue_parts(O)][R]: per-block sums of the new X.
     static int select_fused(const View& v, const Tp* Xmu, const Tp* Xdna, const double* dpart,
                             int splits, uint8_t* choice, double* dfin, double* fpart,
-                            cudaStream_t st);
+                            double reg, cudaStream_t st);
     // out[r] = sum over k < nparts of part[k * R + r] + reg (fixed order; an exact zero
     // sum is replaced by 1)
     static int part_sums(const double* part, int64_t nparts, int64_t R, double reg, double* out,

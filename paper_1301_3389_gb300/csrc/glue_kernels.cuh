@@ -327,14 +327,16 @@ constexpr size_t select_smem(int64_t R) {
 
 // Selection: x(r, o) <- Newton candidate iff d_dna < d_mu (ties keep MU), the choice and
 // the final costs per column, and fpart[blk][r] = sum over this CTA's 32 columns of the
-// new x(r, o) (float64), the first level of the normalisation sums.
+// new x(r, o) (float64), the first level of the normalisation sums.  Each cost is the
+// column's eq. 5 sub-problem cost less a constant: the pass-2 slots plus
+// reg * sum_r x(r, o) of that candidate (reg = lambda for H, rho for W; eq. 5 and eq. 4).
 template <typename Tp>
 __global__ void __launch_bounds__(256) k_select_fused(View v, const Tp* __restrict__ Xmu,
                                                       const Tp* __restrict__ Xdna,
                                                       const double* __restrict__ dpart,
                                                       int splits, uint8_t* __restrict__ choice,
                                                       double* __restrict__ dfin,
-                                                      double* __restrict__ fpart) {
+                                                      double* __restrict__ fpart, double reg) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int64_t R = v.R, O = v.O;
     Tp* xs = reinterpret_cast<Tp*>(smem_raw);                   // [R][TO + 1]
@@ -356,6 +358,18 @@ __global__ void __launch_bounds__(256) k_select_fused(View v, const Tp* __restri
         dsum[0][ty][tx] = dm;
         dsum[1][ty][tx] = dd;
     }
+    // the eq. 5 penalty: warp ty sums r = ty, ty + 8, ... of both candidates (float64)
+    __shared__ double psum[2][8][TO];
+    if (reg != 0.0) {
+        double pm = 0.0, pd = 0.0;
+        if (live)
+            for (int64_t r = ty; r < R; r += 8) {
+                pm += (double)Xmu[r * O + o];
+                pd += (double)Xdna[r * O + o];
+            }
+        psum[0][ty][tx] = pm;
+        psum[1][ty][tx] = pd;
+    }
     __syncthreads();
     if (ty == 0) {
         int newton = 0;
@@ -364,6 +378,15 @@ __global__ void __launch_bounds__(256) k_select_fused(View v, const Tp* __restri
             for (int g = 1; g < 8; ++g) {
                 dm += dsum[0][g][tx];
                 dd += dsum[1][g][tx];
+            }
+            if (reg != 0.0) {
+                double pm = psum[0][0][tx], pd = psum[1][0][tx];
+                for (int g = 1; g < 8; ++g) {
+                    pm += psum[0][g][tx];
+                    pd += psum[1][g][tx];
+                }
+                dm += reg * pm;
+                dd += reg * pd;
             }
             newton = dd < dm;
             choice[o] = (uint8_t)newton;

@@ -91,13 +91,14 @@ __global__ void __launch_bounds__(256)
 }
 
 __global__ void __launch_bounds__(256)
-    k_g_select(const GProb* __restrict__ P, const GTile* __restrict__ tl, int n, int w) {
+    k_g_select(const GProb* __restrict__ P, const GTile* __restrict__ tl, int n, int w,
+               double reg) {
     for (int t = blockIdx.x; t < n; t += gridDim.x) {
         const GTile tt = tl[t];
         const GProb& p = P[tt.prob];
         const View v = p.v[w];
         simt::select_tile<float>(v, p.Xmu, p.Xdna, p.dpart, p.sp2[w], p.choice[w], p.dfin[w],
-                                 tt.a);
+                                 tt.a, reg);
     }
 }
 
@@ -348,7 +349,7 @@ int launch_small(dna_group* g, int which, const TileList& t, int w, double reg =
         case 2: k_g_rescale<<<grid, blk, 0, g->gs>>>(g->dp, t.d, t.n, w); break;
         case 3: k_g_candidates<<<grid, blk, 0, g->gs>>>(g->dp, t.d, t.n, w, (float)g->o.eps,
                                                         (float)g->o.alpha); break;
-        case 4: k_g_select<<<grid, blk, 0, g->gs>>>(g->dp, t.d, t.n, w); break;
+        case 4: k_g_select<<<grid, blk, 0, g->gs>>>(g->dp, t.d, t.n, w, reg); break;
         default: return DNA_ERR_ARG;
     }
     return after_launch();
@@ -373,7 +374,7 @@ int g_half(dna_group* g, int w, bool mu_only) {
     if (!e) e = launch_p2<16, false>(g, g->p2[w][0], w);
     if (!e) e = launch_p2<32, false>(g, g->p2[w][1], w);
     if (!e) e = launch_p2<64, false>(g, g->p2[w][2], w);
-    if (!e) e = launch_small(g, 4, g->cand[w], w);
+    if (!e) e = launch_small(g, 4, g->cand[w], w, w ? g->o.rho : g->o.lambda);
     if (!e) e = g_normalize(g, w == 1 ? 1 : 0);
     return e;
 }
@@ -676,6 +677,21 @@ int dna_group_kl(dna_group* g, double* out) {
 
 int dna_group_get_status(dna_group* g) {
     if (!g) return DNA_ERR_ARG;
+    return sync_status(g);
+}
+
+int dna_group_get_choice(dna_group* g, int q, int which, uint8_t* out, int64_t len) {
+    if (!g || !g->bound || q < 0 || q >= g->count || (which != 0 && which != 1) || !out)
+        return DNA_ERR_ARG;
+    if (len != (which ? g->N[q] : g->T[q])) return DNA_ERR_ARG;
+    if (cudaSetDevice(g->device) != cudaSuccess) return DNA_ERR_CUDA;
+    {
+        Handoff h(g);   // ordered after the caller's stream
+        if (h.err) return h.err;
+        if (cudaMemcpyAsync(out, g->hp[q].choice[which], (size_t)len, cudaMemcpyDeviceToHost,
+                            g->gs) != cudaSuccess)
+            return DNA_ERR_CUDA;
+    }
     return sync_status(g);
 }
 

@@ -1,4 +1,5 @@
-// dna_kl_noalloc: d_KL(V, WH) of eq. 1 for callers that cannot allocate device memory.
+// dna_kl_noalloc: d_KL(V, WH), the value of dna_kl, for callers that cannot allocate
+// device memory (the paper has no counterpart of this entry point).
 //
 // Some callers cannot call cudaMalloc: code whose device memory is all owned by another
 // framework's pool allocator, and latency-critical code that cannot afford cudaMalloc's

@@ -415,14 +415,17 @@ __global__ void k_mu_apply(View v, const double* __restrict__ c, const Tp* __res
     }
 }
 
-// Selection (step 15 / 28): keep the Newton candidate iff d_dna < d_mu (ties keep MU).
+// Selection (step 15 / 28): keep the Newton candidate iff d_dna < d_mu (ties keep MU),
+// each cost being the column's eq. 5 sub-problem cost less a constant: the pass-2 sum
+// plus reg * sum_r x(r, o) (reg = lambda for H, rho for W; eq. 5 and its mirror eq. 4).
 // CTA = 32 columns o x 8 groups of r.
 template <typename Tp>
 __device__ __forceinline__ void select_tile(const View& v, const Tp* __restrict__ Xmu,
                                             const Tp* __restrict__ Xdna,
                                             const double* __restrict__ dpart, int splits,
                                             uint8_t* __restrict__ choice,
-                                            double* __restrict__ dfin, int64_t tile_o) {
+                                            double* __restrict__ dfin, int64_t tile_o,
+                                            double reg) {
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int64_t o = tile_o * 32 + tx;
     if (o >= v.O) return;
@@ -430,6 +433,15 @@ __device__ __forceinline__ void select_tile(const View& v, const Tp* __restrict_
     for (int sp = 0; sp < splits; ++sp) {
         dm += dpart[((int64_t)sp * 2 + 0) * v.O + o];
         dd += dpart[((int64_t)sp * 2 + 1) * v.O + o];
+    }
+    if (reg != 0.0) {   // the penalty of eq. 5, summed over r in ascending order
+        double sm = 0.0, sd = 0.0;
+        for (int64_t r = 0; r < v.R; ++r) {
+            sm += (double)Xmu[r * v.O + o];
+            sd += (double)Xdna[r * v.O + o];
+        }
+        dm += reg * sm;
+        dd += reg * sd;
     }
     const bool newton = dd < dm;
     if (ty == 0) {
@@ -447,8 +459,8 @@ __global__ void __launch_bounds__(256) k_select(View v, const Tp* __restrict__ X
                                                 const Tp* __restrict__ Xdna,
                                                 const double* __restrict__ dpart, int splits,
                                                 uint8_t* __restrict__ choice,
-                                                double* __restrict__ dfin) {
-    select_tile<Tp>(v, Xmu, Xdna, dpart, splits, choice, dfin, blockIdx.x);
+                                                double* __restrict__ dfin, double reg) {
+    select_tile<Tp>(v, Xmu, Xdna, dpart, splits, choice, dfin, blockIdx.x, reg);
 }
 
 // Gradient of eq. 1 with respect to the view's X from the raw pass-1 sums:

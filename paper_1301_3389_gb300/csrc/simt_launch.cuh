@@ -174,9 +174,9 @@ int Simt<Tp>::pass2(const View& v, const Tp* Xmu, const Tp* Xdna, double* dpart,
 
 template <typename Tp>
 int Simt<Tp>::select(const View& v, const Tp* Xmu, const Tp* Xdna, const double* dpart,
-                     int splits, uint8_t* choice, double* dfin, cudaStream_t st) {
-    simt::k_select<Tp><<<(unsigned)((v.O + 31) / 32), dim3(32, 8), 0, st>>>(v, Xmu, Xdna, dpart,
-                                                                              splits, choice, dfin);
+                     int splits, uint8_t* choice, double* dfin, double reg, cudaStream_t st) {
+    simt::k_select<Tp><<<(unsigned)((v.O + 31) / 32), dim3(32, 8), 0, st>>>(
+        v, Xmu, Xdna, dpart, splits, choice, dfin, reg);
     return simt::launch_status();
 }
 
@@ -330,12 +330,12 @@ int Simt<Tp>::split_sum(Tp* A, Tp* B, int64_t R, int64_t O, int splits, cudaStre
 template <typename Tp>
 int Simt<Tp>::select_fused(const View& v, const Tp* Xmu, const Tp* Xdna, const double* dpart,
                            int splits, uint8_t* choice, double* dfin, double* fpart,
-                           cudaStream_t st) {
+                           double reg, cudaStream_t st) {
     const size_t smem = glue::select_smem<Tp>(v.R);
     auto k = glue::k_select_fused<Tp>;
     if (simt::prep_smem(k, smem)) return DNA_ERR_CUDA;
     k<<<(unsigned)glue_parts(v.O), dim3(32, 8), smem, st>>>(v, Xmu, Xdna, dpart, splits, choice,
-                                                           dfin, fpart);
+                                                           dfin, fpart, reg);
     return simt::launch_status();
 }
 

@@ -2,6 +2,8 @@
 with the FP64 oracle."""
 from __future__ import annotations
 
+import os
+
 import numpy as np
 
 from oracle import dna as o
@@ -17,12 +19,40 @@ from oracle import dna as o
 #    near ties up to 1e-4.
 NEAR_TIE = {"f32": 1e-5, "f32t": 1e-4, "f64": 1e-12}
 
+# Element-wise check beside every Frobenius one: the largest |x - x_ref| / |x_ref| over
+# the entries with |x_ref| > ELEM_FLOOR * max |x_ref| (smaller entries carry no relative
+# accuracy worth testing: they are the ones an eps floor or a strong MU decrease has
+# driven towards zero, and their absolute error is already bounded by the Frobenius
+# check).  ELEM_TOL per form; derivation in the module docstring of test_gpu_parity.py.
+ELEM_FLOOR = 1e-6
+ELEM_TOL = {"f32": 2e-3, "f32t": 5e-3, "f64": 1e-8}
+
 
 def rel_fro(a, b) -> float:
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
     den = np.linalg.norm(b)
     return float(np.linalg.norm(a - b) / den) if den > 0 else float(np.linalg.norm(a - b))
+
+
+def rel_elem(a, b, label: str = "", floor: float = ELEM_FLOOR) -> float:
+    """max |a - b| / |b| over the entries of b above floor * max |b| (see ELEM_FLOOR).
+
+    With DNA_PARITY_LOG set, each value is also appended to that file (label, value), so a
+    run can report the measured element-wise errors."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    m = float(np.abs(b).max()) if b.size else 0.0
+    if m == 0.0:
+        val = float(np.abs(a).max()) if a.size else 0.0
+    else:
+        sel = np.abs(b) > floor * m
+        val = float((np.abs(a[sel] - b[sel]) / np.abs(b[sel])).max())
+    path = os.environ.get("DNA_PARITY_LOG")
+    if path:
+        with open(path, "a") as f:
+            f.write(f"{os.environ.get('PYTEST_CURRENT_TEST', '?').split(' ')[0]} {label} {val:.3e}\n")
+    return val
 
 
 class GpuProblem:

@@ -16,12 +16,13 @@ import numpy as np
 import pytest
 
 import workloads
-from gpu_helpers import GpuProblem, rel_fro
+from gpu_helpers import GpuProblem, rel_elem, rel_fro
 from oracle import dna as o
 
 pytestmark = pytest.mark.gpu
 
 TOL_BF16 = 2e-2
+ELEM_BF16 = 1e-1    # element-wise, entries above 1e-6 of the largest (gpu_helpers.ELEM_FLOOR)
 TOL_COST = 1e-2
 MARGIN_BF16 = 1e-2
 
@@ -62,6 +63,8 @@ def _bf16_steps(p, iters, check_costs=True, restart=True):
                 Wg, Hg = gp.WH()
                 errs.append((rel_fro(Wg, W), rel_fro(Hg, H)))
                 assert errs[-1][0] < TOL_BF16 and errs[-1][1] < TOL_BF16, errs[-1]
+                xw, xh = rel_elem(Wg, W, "bf16 W"), rel_elem(Hg, H, "bf16 H")
+                assert xw < ELEM_BF16 and xh < ELEM_BF16, (xw, xh)
         kl = gp.dna.dna_kl(gp.ctx)
         Wg, Hg = gp.WH()
         assert abs(kl - o.kl_divergence(V, Wg @ Hg)) <= 1e-4 * kl
@@ -122,6 +125,7 @@ def test_bf16_mu_steps():
             W, H = (o.mu_step_h if which == 0 else o.mu_step_w)(V, W, H)
             Wg, Hg = gp.WH()
             assert rel_fro(Wg, W) < TOL_BF16 and rel_fro(Hg, H) < TOL_BF16
+            assert rel_elem(Wg, W, "bf16 mu W") < ELEM_BF16 and rel_elem(Hg, H, "bf16 mu H") < ELEM_BF16
 
 
 def test_bf16_unaligned_leading_dimension():
@@ -147,6 +151,7 @@ def test_bf16_plain_large_sampled():
         X = np.where(mask[None, :], half.X_dna, half.X_mu)
         sigma = W1.sum(axis=0) / W0.sum(axis=0)
         assert rel_fro(H1[:, cols], X / sigma[:, None]) < TOL_BF16
+        assert rel_elem(H1[:, cols], X / sigma[:, None], "bf16 H sampled") < ELEM_BF16
         gp.dna.dna_step_W(gp.ctx)
         W2, H2 = gp.WH()
         half = o.w_half_step(big.V[rows, :].astype(np.float64), W1[rows, :], H1)
@@ -154,6 +159,7 @@ def test_bf16_plain_large_sampled():
         X = np.where(mask[:, None], half.X_dna, half.X_mu)
         sigma = H2.sum(axis=1) / H1.sum(axis=1)
         assert rel_fro(W2[rows, :], X / sigma[None, :]) < TOL_BF16
+        assert rel_elem(W2[rows, :], X / sigma[None, :], "bf16 W sampled") < ELEM_BF16
 
 
 def test_bf16_precision_large_sampled():
@@ -173,6 +179,7 @@ def test_bf16_precision_large_sampled():
         X = np.where(mask[None, :], half.X_dna, half.X_mu)
         sigma = W1.sum(axis=0) / W0.sum(axis=0)
         assert rel_fro(H1[:, cols], X / sigma[:, None]) < TOL_BF16
+        assert rel_elem(H1[:, cols], X / sigma[:, None], "bf16 H sampled") < ELEM_BF16
         gp.dna.dna_step_W(gp.ctx)
         W2, H2 = gp.WH()
         half = o.w_half_step(big.V[rows, :].astype(np.float64), W1[rows, :], H1)
@@ -180,3 +187,4 @@ def test_bf16_precision_large_sampled():
         X = np.where(mask[:, None], half.X_dna, half.X_mu)
         sigma = H2.sum(axis=1) / H1.sum(axis=1)
         assert rel_fro(W2[rows, :], X / sigma[None, :]) < TOL_BF16
+        assert rel_elem(W2[rows, :], X / sigma[None, :], "bf16 W sampled") < ELEM_BF16

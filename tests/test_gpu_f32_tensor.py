@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 import workloads
-from gpu_helpers import GpuProblem, rel_fro, step_pair
+from gpu_helpers import ELEM_TOL, GpuProblem, rel_elem, rel_fro, step_pair
 from oracle import dna as o
 
 pytestmark = pytest.mark.gpu
@@ -31,6 +31,8 @@ def test_split_half_steps(shape):
                 W, H, _ = step_pair(gp, W, H, which)
                 Wg, Hg = gp.WH()
                 worst = max(worst, rel_fro(Wg, W), rel_fro(Hg, H))
+                assert rel_elem(Wg, W, "f32t W") < ELEM_TOL["f32t"]
+                assert rel_elem(Hg, H, "f32t H") < ELEM_TOL["f32t"]
         print(f"\n{shape}: worst W/H error over 2 iterations {worst:.2e}")
         assert worst < 1e-4
 
@@ -50,6 +52,8 @@ def test_split_persistent_tiles_and_segments():
             W, H, _ = step_pair(gp, W, H, which)
             Wg, Hg = gp.WH()
             worst = max(worst, rel_fro(Wg, W), rel_fro(Hg, H))
+            assert rel_elem(Wg, W, "f32t W") < ELEM_TOL["f32t"]
+            assert rel_elem(Hg, H, "f32t H") < ELEM_TOL["f32t"]
         kl_gpu = gp.dna.dna_kl(gp.ctx)
         kl_ref = o.kl_divergence(p.V.astype(np.float64), W @ H)
         print(f"\n{(N, T, R)}: worst W/H error {worst:.2e}, d_KL {kl_gpu:.6e} vs {kl_ref:.6e}")

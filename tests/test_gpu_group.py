@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 import workloads
-from gpu_helpers import GpuProblem, rel_fro
+from gpu_helpers import ELEM_TOL, GpuProblem, rel_elem, rel_fro, replay_choice
 from oracle import dna as o
 
 pytestmark = pytest.mark.gpu
@@ -64,6 +64,48 @@ def test_group_matches_single_path():
             assert rel_fro(W[q].double().cpu().numpy(), Ws) < 5e-5, q
             assert rel_fro(H[q].double().cpu().numpy(), Hs) < 5e-5, q
             assert abs(kl[q] - kls) <= 1e-5 * max(abs(kls), 1.0), (q, kl[q], kls)
+    finally:
+        dna.dna_group_destroy(g)
+
+
+def test_group_matches_oracle_per_half_step():
+    """Every problem of the group against the FP64 oracle, half-step by half-step, with the
+    oracle replaying the group's selections where they differ at near ties: W and H within
+    the FP32 form's 1e-4 relative (Frobenius) and element-wise tolerance after each of two
+    iterations, and d_KL within 1e-4."""
+    import torch
+    probs = _problems(3)
+    dna, g, V, W, H = _group(probs)
+    try:
+        dna.dna_group_normalize(g, 1)
+        ref = [o.normalize_w_columns(p.W, p.H) for p in probs]
+        V64 = [p.V.astype(np.float64) for p in probs]
+        for it in range(2):
+            for which in (0, 1):
+                (dna.dna_group_step_H if which == 0 else dna.dna_group_step_W)(g)
+                torch.cuda.synchronize()
+                for q, p in enumerate(probs):
+                    Wr, Hr = ref[q]
+                    n = p.V.shape[1] if which == 0 else p.V.shape[0]
+                    ch = dna.dna_group_get_choice(g, q, which, n)
+                    if which == 0:
+                        half = o.h_half_step(V64[q], Wr, Hr)
+                        mask, _ = replay_choice(half, ch, "f32")
+                        Wr, Hr, _ = o.dna_step_h(V64[q], Wr, Hr, choice=mask)
+                    else:
+                        half = o.w_half_step(V64[q], Wr, Hr)
+                        mask, _ = replay_choice(half, ch, "f32")
+                        Wr, Hr, _ = o.dna_step_w(V64[q], Wr, Hr, choice=mask)
+                    ref[q] = (Wr, Hr)
+                    Wg = W[q].double().cpu().numpy()
+                    Hg = H[q].double().cpu().numpy()
+                    assert rel_fro(Wg, Wr) < 1e-4 and rel_fro(Hg, Hr) < 1e-4, (q, it, which)
+                    assert rel_elem(Wg, Wr, "group W") < ELEM_TOL["f32"], (q, it, which)
+                    assert rel_elem(Hg, Hr, "group H") < ELEM_TOL["f32"], (q, it, which)
+        kl = dna.dna_group_kl(g, len(probs))
+        for q, (Wr, Hr) in enumerate(ref):
+            kr = o.kl_divergence(V64[q], Wr @ Hr)
+            assert abs(kl[q] - kr) <= 1e-4 * max(kr, 1.0), (q, kl[q], kr)
     finally:
         dna.dna_group_destroy(g)
 

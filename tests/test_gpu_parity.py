@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 import workloads
-from gpu_helpers import GpuProblem, rel_fro, step_pair
+from gpu_helpers import ELEM_TOL, GpuProblem, rel_elem, rel_fro, step_pair
 from oracle import dna as o
 
 pytestmark = pytest.mark.gpu
@@ -37,6 +37,9 @@ def _trajectory(p, kind, iters, mu=False, **opts):
                 Wg, Hg = gp.WH()
                 ew, eh = rel_fro(Wg, W), rel_fro(Hg, H)
                 assert ew < TOL[kind] and eh < TOL[kind], (it, which, ew, eh)
+                xw = rel_elem(Wg, W, f"{kind} W it{it}.{which}")
+                xh = rel_elem(Hg, H, f"{kind} H it{it}.{which}")
+                assert xw < ELEM_TOL[kind] and xh < ELEM_TOL[kind], (it, which, xw, xh)
         kl_gpu = gp.dna.dna_kl(gp.ctx)
         kl_ref = o.kl_divergence(V, W @ H)
         assert abs(kl_gpu - kl_ref) <= TOL[kind] * abs(kl_ref), (kl_gpu, kl_ref)
@@ -168,3 +171,34 @@ def test_deterministic():
             outs.append(gp.WH())
     np.testing.assert_array_equal(outs[0][0], outs[1][0])
     np.testing.assert_array_equal(outs[0][1], outs[1][1])
+
+
+COST_RTOL = {"f32": 1e-5, "f32t": 1e-4, "f64": 1e-11}
+
+
+@pytest.mark.parametrize("kind", ["f32", "f32t", "f64"])
+def test_regularised_selection_costs(kind):
+    """lambda = rho = 2 (eq. 2-5): from the GPU's own state at each half-step, the costs the
+    GPU compares are the oracle's eq. 5 (eq. 4) costs d' + lambda sum_r h (rho sum_r w), and
+    its selections are the oracle's except at near ties."""
+    from gpu_helpers import NEAR_TIE
+    p = workloads.custom(60, 140, 6, seed=21)
+    V = p.V.astype(np.float64)
+    reg = 2.0
+    with GpuProblem(p.V, p.W, p.H, kind, rho=reg, lam=reg) as gp:
+        gp.dna.dna_normalize(gp.ctx, 1)
+        for _ in range(3):
+            for which in (0, 1):
+                W, H = gp.WH()
+                if which == 0:
+                    half = o.h_half_step(V, W, H, lam=reg)
+                    gp.dna.dna_step_H(gp.ctx)
+                else:
+                    half = o.w_half_step(V, W, H, rho=reg)
+                    gp.dna.dna_step_W(gp.ctx)
+                dm, dd = gp.costs(which)
+                np.testing.assert_allclose(dm, half.d_mu, rtol=COST_RTOL[kind])
+                np.testing.assert_allclose(dd, half.d_dna, rtol=COST_RTOL[kind])
+                diff = np.asarray(gp.choice(which), bool) != half.choice
+                if diff.any():
+                    assert half.margin[diff].max() < NEAR_TIE[kind]

@@ -38,6 +38,16 @@ UNIT = "DNA iterations/s"
 SMS = 152
 FP32_LANES_PER_SM = 128
 
+ARITHMETIC = {
+    ("f32", "tensor"): "float32 masters and element-wise work; each tensor-core product is "
+                       "three bf16 products of hi/lo splits (x_hi y_hi + x_hi y_lo + x_lo y_hi, "
+                       "about 16 significant bits per operand), float32 accumulation; float64 "
+                       "cost sums",
+    "f32": "float32 (CUDA-core FMA), float64 cost sums",
+    "f64": "float64",
+    "bf16": "bf16 tensor-core operands, float32 accumulation and masters, float64 cost sums",
+}
+
 BATCHED_DESC = ("512 problems, N ~ logU[64,2048], T ~ logU[128,8192], R ~ U{8,16,32,64}, "
                 "Gamma(0.5) truth, Poisson V")
 
@@ -182,7 +192,11 @@ def run_reference(args, spec, prob):
               f"{cols} of {spec['T']} columns; rate scaled by {cols}/{spec['T']}")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3 / scale,
+        "steps": args.steps, "warmup": args.warmup,
+        # the measured duration of one timed step (one iteration on the column sample); the
+        # full-workload figure it scales to is beside it
+        "ms_per_step": el / args.steps * 1e3,
+        "ms_per_step_scaled_to_full_workload": el / args.steps * 1e3 / scale,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": args.workload, "desc": spec["desc"],
                                         "sample_columns": cols},
@@ -211,6 +225,11 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the BF16 line and time-to-target")
     ap.add_argument("--target-iters", type=int, default=200)
+    ap.add_argument("--c3-iters", type=int, default=100,
+                    help="FP32 iterations that set the target at N=8192 T=32768 R=512")
+    ap.add_argument("--no-c3-target", action="store_true")
+    ap.add_argument("--no-mu-log", action="store_true")
+    ap.add_argument("--log-file", default=None, help="per-iteration DNA/MU log (text)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -260,6 +279,7 @@ def main(argv=None):
         "config": {"workload": args.workload, "desc": spec["desc"], "N": N, "T": T, "R": R,
                    "form": args.dtype.upper(),
                    "engine": engine_name,
+                   "arithmetic": ARITHMETIC.get((args.dtype, args.engine), ARITHMETIC.get(args.dtype)),
                    "l2": "inputs larger than L2 (V is %d MB)" % (N * T * 4 // 2**20),
                    "parallelism": "independent problem per GPU" if world > 1 else "single GPU",
                    "zero_fraction": prob.meta.get("zero_fraction")},
@@ -282,7 +302,11 @@ def main(argv=None):
             line["fp32_simt_form"] = {"value": sm["value"], "unit": UNIT, "steps": sargs.steps,
                                       "ms_per_step": sm["ms_max"] / sargs.steps,
                                       "roofline": sm["roofline"], "gpu_launches": sm["launches"]}
-        line["time_to_target"] = time_to_target(dna, torch, prob, args.target_iters, args.engine)
+        line["time_to_target"] = time_to_target(dna, torch, prob, args.target_iters, args.engine,
+                                                args.workload)
+        if args.workload == "plain_large" and not args.no_mu_log:
+            line["dna_vs_mu"] = convergence_log(dna, torch, prob, args.target_iters, args.engine,
+                                                args.log_file)
         if args.workload == "plain_large":
             # the BF16 form at its own headline size (N=8192 T=32768 R=512), 20 iterations
             pspec = WORKLOADS["precision_large"]
@@ -298,6 +322,12 @@ def main(argv=None):
                 "gpu_launches": pr["launches"],
                 "config": {"workload": "precision_large", "desc": pspec["desc"],
                            "N": pspec["N"], "T": pspec["T"], "R": pspec["R"], "form": "BF16"}}
+            if not args.no_c3_target:
+                # the metric at the precision form's own size: FP32 (its fastest engine at
+                # R = 512) against BF16, to the FP32 form's d_KL after c3_iters iterations
+                eng = "tensor" if pspec["R"] <= 128 else "simt"
+                line["precision_form"]["time_to_target"] = time_to_target(
+                    dna, torch, pprob, args.c3_iters, eng, "precision_large")
             del pprob
 
     if rank == 0 and not args.no_e2e:
@@ -418,18 +448,18 @@ def measure(dna, torch, dist, prob, dtype, args, world, local, peaks, clocks, en
         # to them is a third of the bf16 peak.  Executed bf16 work per launch: pass 1 runs
         # GEMM1 in both its A and B halves (2 x 3 x 2RNT) plus GEMM2/3 (2 x 3 x 2RNT);
         # pass 2 runs 2 x 3 x 2RNT.
-        bf16_peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
+        bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
         fp32_peak = bf16_peak / 3.0
         executed = (24 if dom == "pass1" else 12) * R * N * T
         roof = {"bound": "tensor", "achieved": flops / per_launch_s / 1e12, "peak": fp32_peak,
                 "unit": "TFLOP/s",
-                "peak_source": "measured sustained dense bf16 (MEASURED_PEAKS.json) / 3: "
-                               "three bf16 products per FP32-accurate product"}
+                "peak_source": "measured burst dense bf16 (MEASURED_PEAKS.json) / 3: three bf16 "
+                               "products per FP32-accurate product (timed region well under 1 s)"}
         roof["executed_bf16_flops_per_launch"] = executed
         roof["tensor_frac_executed"] = executed / per_launch_s / 1e12 / bf16_peak
         roof["hbm_frac"] = alg_bytes / per_launch_s / 1e9 / hbm
     elif dtype == "bf16":
-        tensor_peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
+        tensor_peak = float(peaks.get("bf16_tflops", 1900.0))
         t_tensor = flops / (tensor_peak * 1e12)
         t_hbm = alg_bytes / (hbm * 1e9)
         if t_hbm >= t_tensor:   # the binding floor of this kernel at this size
@@ -438,7 +468,8 @@ def measure(dna, torch, dist, prob, dtype, args, world, local, peaks, clocks, en
         else:
             roof = {"bound": "tensor", "achieved": flops / per_launch_s / 1e12, "peak": tensor_peak,
                     "unit": "TFLOP/s",
-                    "peak_source": "measured sustained dense bf16 (MEASURED_PEAKS.json)"}
+                    "peak_source": "measured burst dense bf16 (MEASURED_PEAKS.json; timed region "
+                                   "well under 1 s)"}
         roof["tensor_frac"] = flops / per_launch_s / 1e12 / tensor_peak
         roof["hbm_frac"] = alg_bytes / per_launch_s / 1e9 / hbm
     else:
@@ -448,6 +479,17 @@ def measure(dna, torch, dist, prob, dtype, args, world, local, peaks, clocks, en
                 "peak_source": (f"derived: {SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x "
                                 f"{sm_max:.0f} MHz (max SM clock of measured)")}
     roof["frac"] = roof["achieved"] / roof["peak"] if roof.get("peak") else None
+    # the whole iteration: the paper's 16 N R T useful flops (four O(NRT) products per
+    # half-step) over the measured time per iteration, against the same peak
+    iter_s = ms_max / args.steps / 1e3
+    if split:
+        iter_peak = float(peaks.get("bf16_tflops", 1900.0)) / 3.0
+    elif dtype == "bf16":
+        iter_peak = float(peaks.get("bf16_tflops", 1900.0))
+    else:
+        iter_peak = roof.get("peak") if roof["unit"] == "TFLOP/s" else None
+    roof["iteration_tflops"] = 16 * R * N * T / iter_s / 1e12
+    roof["iteration_frac"] = roof["iteration_tflops"] / iter_peak if iter_peak else None
     roof["kernel"] = dom
     roof["traffic"] = recorded_traffic(dom + ("_tc" if dtype == "bf16" else "_split" if split else ""),
                                        args.workload)
@@ -463,42 +505,99 @@ def measure(dna, torch, dist, prob, dtype, args, world, local, peaks, clocks, en
             "kl_end": kl_end}
 
 
-def time_to_target(dna, torch, prob, iters, engine="auto"):
-    """Seconds of DNA iterations (CUDA events, d_KL evaluations excluded) for the FP32 form
-    to run `iters` iterations, whose final d_KL is the target, and for the BF16 form to come
-    within 1e-2 relative of it (checked every 5 iterations, at most 2 x iters)."""
+def run_logged(dna, torch, prob, dtype, engine, max_iters, target=None, algo="dna"):
+    """Up to max_iters iterations of one form (DNA, or MU with algo="mu"), d_KL after every
+    iteration.  Each iteration is timed with CUDA events on the library's stream; the d_KL
+    evaluations (and the selection read-back) are outside the events.  Stops early once
+    d_KL <= target.  Returns d_KL per iteration (index 0 = start), cumulative seconds, and
+    for DNA the fraction of columns (H step) and rows (W step) that kept the Newton
+    candidate."""
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
-    out = {"iterations_fp32": iters, "fp32_engine": engine}
-    ctx, keep = _bind(dna, torch, prob, "f32", dev, engine)
+    ctx, keep = _bind(dna, torch, prob, dtype, dev, engine)
+    N, T = prob.V.shape
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    dna.dna_iterate(ctx, iters)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    out["sec_fp32"] = e0.elapsed_time(e1) / 1e3
-    target = dna.dna_kl(ctx)
-    dna.dna_destroy(ctx)
-    out["target_kl"] = target
-    ctx, keep2 = _bind(dna, torch, prob, "bf16", dev)
-    sec, it, kl = 0.0, 0, float("inf")
-    while it < 2 * iters:
-        torch.cuda.synchronize()
-        e0.record(stream)
-        dna.dna_iterate(ctx, 5)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        sec += e0.elapsed_time(e1) / 1e3
-        it += 5
-        kl = dna.dna_kl(ctx)
-        if kl <= target * (1 + 1e-2):
-            break
-    dna.dna_destroy(ctx)
-    out.update({"sec_bf16": sec, "iterations_bf16": it, "kl_bf16": kl,
-                "bf16_reached": bool(kl <= target * (1 + 1e-2)),
-                "speedup": out["sec_fp32"] / sec if sec > 0 else None})
-    return out
+    kls, secs, newton = [dna.dna_kl(ctx)], [0.0], []
+    try:
+        for _ in range(max_iters):
+            torch.cuda.synchronize()
+            e0.record(stream)
+            if algo == "dna":
+                dna.dna_iterate(ctx, 1)
+            else:
+                dna.mu_step(ctx, 0)
+                dna.mu_step(ctx, 1)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            secs.append(secs[-1] + e0.elapsed_time(e1) / 1e3)
+            kls.append(dna.dna_kl(ctx))
+            if algo == "dna":
+                newton.append((float(dna.dna_get_choice(ctx, 0, T).mean()),
+                               float(dna.dna_get_choice(ctx, 1, N).mean())))
+            if target is not None and kls[-1] <= target:
+                break
+    finally:
+        dna.dna_destroy(ctx)
+        del keep
+    return kls, secs, newton
+
+
+def first_reach(kls, secs, target):
+    for i, k in enumerate(kls):
+        if k <= target:
+            return i, secs[i]
+    return None, None
+
+
+def time_to_target(dna, torch, prob, iters, fp32_engine, workload):
+    """Seconds and iterations for the FP32 and the BF16 form to reach the same d_KL target:
+    the FP32 form's d_KL after `iters` iterations, times (1 + 1e-2).  Each form runs from
+    the same start, checks d_KL after every iteration (outside the timing) and reports the
+    first iteration at or below the target (the BF16 form runs at most 2 x iters)."""
+    k32, s32, _ = run_logged(dna, torch, prob, "f32", fp32_engine, iters)
+    target = k32[-1] * (1 + 1e-2)
+    i32, t32 = first_reach(k32, s32, target)
+    kb, sb, _ = run_logged(dna, torch, prob, "bf16", "auto", 2 * iters, target=target)
+    ib, tb = first_reach(kb, sb, target)
+    return {
+        "workload": workload, "target_kl": target,
+        "target_rule": f"FP32 form's d_KL after {iters} iterations x (1 + 1e-2)",
+        "check": "d_KL after every iteration, outside the timed events",
+        "fp32": {"engine": fp32_engine, "iterations": i32, "sec": t32,
+                 "ms_per_iteration": s32[-1] / iters * 1e3, "kl_final": k32[-1]},
+        "bf16": {"iterations": ib, "sec": tb, "reached": ib is not None,
+                 "ms_per_iteration": sb[-1] / max(len(sb) - 1, 1) * 1e3, "kl_last": kb[-1]},
+        "speedup": (t32 / tb) if (t32 and tb) else None,
+    }
+
+
+def convergence_log(dna, torch, prob, iters, engine, log_file=None):
+    """DNA and MU (eq. 11, no cost evaluation) in the FP32 form, `iters` iterations each from
+    the same start, d_KL after every iteration; the iterations and seconds DNA needs to
+    reach MU's final d_KL (the paper's comparison in Section 4.1), and the fraction of
+    columns / rows that kept the Newton candidate."""
+    kd, sd, nw = run_logged(dna, torch, prob, "f32", engine, iters, algo="dna")
+    km, sm, _ = run_logged(dna, torch, prob, "f32", engine, iters, algo="mu")
+    target = km[-1]
+    i_d, t_d = first_reach(kd, sd, target)
+    marks = [i for i in (0, 1, 2, 3, 5, 10, 20, 50, 100, 150, 200, 300, 500) if i <= iters]
+    if log_file:
+        with open(log_file, "w") as f:
+            f.write("iteration kl_dna sec_dna kl_mu sec_mu newton_frac_H newton_frac_W\n")
+            for i in range(iters + 1):
+                nh, nww = nw[i - 1] if i > 0 else (float("nan"), float("nan"))
+                f.write(f"{i} {kd[i]:.10e} {sd[i]:.6e} {km[i]:.10e} {sm[i]:.6e} {nh:.4f} {nww:.4f}\n")
+    return {
+        "iterations": iters, "engine": engine,
+        "target": "MU's d_KL after %d iterations" % iters,
+        "dna_iterations_to_mu_final": i_d, "dna_sec_to_mu_final": t_d, "mu_sec": sm[-1],
+        "iteration_ratio": (iters / i_d) if i_d else None,
+        "time_ratio": (sm[-1] / t_d) if t_d else None,
+        "ms_per_iteration": {"dna": sd[-1] / iters * 1e3, "mu": sm[-1] / iters * 1e3},
+        "kl_at": {str(i): {"dna": kd[i], "mu": km[i]} for i in marks},
+        "newton_fraction_at": {str(i): {"H": nw[i - 1][0], "W": nw[i - 1][1]}
+                               for i in marks if i > 0},
+    }
 
 
 def run_batched(args, world, rank, local):

@@ -525,8 +525,7 @@ def run_logged(dna, torch, prob, dtype, engine, max_iters, target=None, algo="dn
             if algo == "dna":
                 dna.dna_iterate(ctx, 1)
             else:
-                dna.mu_step(ctx, 0)
-                dna.mu_step(ctx, 1)
+                dna.mu_iterate(ctx, 1)
             e1.record(stream)
             torch.cuda.synchronize()
             secs.append(secs[-1] + e0.elapsed_time(e1) / 1e3)

@@ -117,6 +117,10 @@ int dna_iterate(dna_ctx* ctx, int iters);
  * Asynchronous. */
 int mu_step(dna_ctx* ctx, int which);
 
+/* iters MU iterations: iters times (mu_step(ctx, 0), mu_step(ctx, 1)), each half-step
+ * leaving the operands of the next one ready (as dna_iterate does).  Asynchronous. */
+int mu_iterate(dna_ctx* ctx, int iters);
+
 /* d_KL(V, W H) of eq. 1 in float64, written to *out (host memory): per element
  * z + v log(v / z) - v (z where v = 0), summed in float32 over short runs and in float64
  * beyond.  Z is formed by the context's engine (for F32 with ENGINE_TENSOR: the split

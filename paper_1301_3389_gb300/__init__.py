@@ -9,7 +9,7 @@ from ._lib import (  # noqa: F401
     DNA_OK, LIB, LIB_PATH, DNAError, dna_bind, dna_create, dna_default_opts, dna_destroy,
     dna_get_choice, dna_get_costs, dna_get_status, dna_iterate, dna_kl, dna_kl_backward, dna_kl_noalloc, dna_step_H_fixed, dna_step_H_adjoint, dna_normalize,
     dna_opts, dna_phase_times, dna_profile, dna_profile_phases, dna_run_host, PHASES, dna_set_stream, dna_step_H, dna_step_W, dna_strerror, make_opts,
-    mu_step, dna_group_create, dna_group_bind, dna_group_set_stream,
+    mu_step, mu_iterate, dna_group_create, dna_group_bind, dna_group_set_stream,
     dna_group_normalize, dna_group_step_H, dna_group_step_W, dna_group_iterate,
     dna_group_use_graph, dna_group_autotune, dna_group_kl, dna_group_get_status, dna_group_get_choice,
     dna_group_launches_per_iteration, dna_group_destroy)

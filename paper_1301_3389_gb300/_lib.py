@@ -56,6 +56,7 @@ def _load() -> ctypes.CDLL:
         "dna_step_W": (I, [P]),
         "dna_iterate": (I, [P, I]),
         "mu_step": (I, [P, I]),
+        "mu_iterate": (I, [P, I]),
         "dna_kl": (I, [P, ctypes.POINTER(D)]),
         "dna_get_choice": (I, [P, I, P, I64]),
         "dna_get_costs": (I, [P, I, P, P, I64]),
@@ -176,6 +177,10 @@ def dna_iterate(ctx: int, iters: int) -> None:
 
 def mu_step(ctx: int, which: int) -> None:
     _check(LIB.mu_step(ctx, which), "mu_step")
+
+
+def mu_iterate(ctx: int, iters: int) -> None:
+    _check(LIB.mu_iterate(ctx, iters), "mu_iterate")
 
 
 def dna_kl(ctx: int) -> float:

@@ -403,6 +403,9 @@ int prep_step(dna_ctx* c, int w, bool with_sq) {
     });
 }
 
+template <typename Tp>
+int finish_step(dna_ctx* c, int w, bool next);
+
 // One half-step (w = 0: Algorithm 1 steps 4-16, w = 1: steps 17-29).  mu_only: the
 // multiplicative update of eq. 11 instead of DNA.  prepared: the operands and c of this
 // half-step were left by the previous one (inside one dna_iterate call); next: leave them
@@ -419,7 +422,7 @@ int half_step(dna_ctx* c, int w, bool mu_only, bool prepared, bool next) {
     const bool tc = c->tc;
     const int sp1 = tc ? c->tsp1[w] : c->sp1[w], sp2 = tc ? c->tsp2[w] : c->sp2[w];
     int e = DNA_OK;
-    if (!prepared || mu_only)
+    if (!prepared)
         if ((e = prep_step<Tp>(c, w, !mu_only))) return e;
     e = phase(c, DNA_PHASE_PASS1, 1, [&] {
         if constexpr (sizeof(Tp) == 4)
@@ -432,9 +435,10 @@ int half_step(dna_ctx* c, int w, bool mu_only, bool prepared, bool next) {
         return S::pass1(v, A, B, sp1, c->per1[w], !mu_only, c->status, st);
     });
     if (e) return e;
-    if (mu_only) {
-        e = phase(c, DNA_PHASE_CANDIDATES, 1, [&] { return S::mu_apply(v, c->c, A, sp1, st); });
-        return e ? e : normalize<Tp>(c, w == 1 ? 1 : 0);
+    if (mu_only) {   // eq. 11 in place, with the first level of the step 16 / 29 sums
+        e = phase(c, DNA_PHASE_CANDIDATES, 1, [&] { return S::mu_fused(v, c->c, A, sp1, c->gpart, st); });
+        if (e) return e;
+        return finish_step<Tp>(c, w, next);
     }
     // many split partials: one streaming pass sums them into split 0 first (the candidates
     // kernel streams up to 4 itself when the rank allows its register form)
@@ -466,6 +470,18 @@ int half_step(dna_ctx* c, int w, bool mu_only, bool prepared, bool next) {
                                st);
     });
     if (e) return e;
+    return finish_step<Tp>(c, w, next);
+}
+
+// Steps 16 / 29 after the new factor and its per-block sums (gpart) are written: f_r = sum
+// over o of the new x(r, o) + (rho | lambda), then the rescale, fused (next) with the
+// preparation of half-step 1 - w.
+template <typename Tp>
+int finish_step(dna_ctx* c, int w, bool next) {
+    using S = dna::Simt<Tp>;
+    const View v = make_view(c, w == 1);
+    cudaStream_t st = c->stream;
+    int e = DNA_OK;
     // steps 16 / 29: f_r = sum over o of the new x(r, o) + (rho | lambda)
     e = phase(c, DNA_PHASE_SUMS, 1, [&] {
         return S::part_sums(c->gpart, S::glue_parts(v.O), c->R, w ? c->o.lambda : c->o.rho,
@@ -760,6 +776,21 @@ int mu_step(dna_ctx* c, int which) {
     if (set_device(c)) return DNA_ERR_CUDA;
     return is_f64(c) ? half_step<double>(c, which, true, false, false)
                      : half_step<float>(c, which, true, false, false);
+}
+
+int mu_iterate(dna_ctx* c, int iters) {
+    if (int e = check_ready(c)) return e;
+    if (iters < 0) return DNA_ERR_ARG;
+    if (set_device(c)) return DNA_ERR_CUDA;
+    for (int i = 0; i < iters; ++i) {
+        const bool more = i + 1 < iters;
+        int e = is_f64(c) ? half_step<double>(c, 0, true, i > 0, true)
+                          : half_step<float>(c, 0, true, i > 0, true);
+        if (!e) e = is_f64(c) ? half_step<double>(c, 1, true, true, more)
+                              : half_step<float>(c, 1, true, true, more);
+        if (e) return e;
+    }
+    return DNA_OK;
 }
 
 int dna_kl(dna_ctx* c, double* out) {

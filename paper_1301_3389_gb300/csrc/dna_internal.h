@@ -103,6 +103,9 @@ template <typename Tp> struct Simt {
     static int select_fused(const View& v, const Tp* Xmu, const Tp* Xdna, const double* dpart,
                             int splits, uint8_t* choice, double* dfin, double* fpart,
                             double reg, cudaStream_t st);
+    // MU (eq. 11) in place from the pass-1 split partials, plus fpart as select_fused
+    static int mu_fused(const View& v, const double* c, const Tp* Apart, int splits,
+                        double* fpart, cudaStream_t st);
     // out[r] = sum over k < nparts of part[k * R + r] + reg (fixed order; an exact zero
     // sum is replaced by 1)
     static int part_sums(const double* part, int64_t nparts, int64_t R, double reg, double* out,

@@ -422,6 +422,59 @@ __global__ void __launch_bounds__(256) k_select_fused(View v, const Tp* __restri
     }
 }
 
+// The multiplicative update (eq. 11) fused with the first level of the step 16 / 29 sums:
+// x(r, o) <- x(r, o) * (sum over splits of Apart(r, o)) / c_r, written in place, and
+// fpart[blk][r] = sum over this CTA's 32 columns of the new x(r, o) (float64).  The same
+// CTA shape, grid and fpart layout as k_select_fused, so the normalisation that follows is
+// shared with the DNA half-step.
+template <typename Tp>
+__global__ void __launch_bounds__(256) k_mu_fused(View v, const double* __restrict__ c,
+                                                  const Tp* __restrict__ Apart, int splits,
+                                                  double* __restrict__ fpart) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int64_t R = v.R, O = v.O;
+    Tp* xs = reinterpret_cast<Tp*>(smem_raw);                   // [R][TO + 1]
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+    const int64_t o0 = (int64_t)blockIdx.x * TO, o = o0 + tx;
+    const bool live = o < O;
+    Tp* __restrict__ X = static_cast<Tp*>(v.X);
+    const bool direct = v.xo == 1;
+    if (!direct) {   // columns of X contiguous along r: read the tile with lanes along r
+        for (int i = ty; i < TO; i += 8) {
+            const int64_t oi = o0 + i;
+#pragma unroll 4
+            for (int64_t r = tx; r < R; r += 32)
+                xs[r * (TO + 1) + i] = oi < O ? X[r * v.xr + oi * v.xo] : Tp(0);
+        }
+        __syncthreads();
+    }
+#pragma unroll 4
+    for (int64_t r = ty; r < R; r += 8) {
+        Tp ra = Tp(0);
+        if (live)
+            for (int sp = 0; sp < splits; ++sp) ra += Apart[((int64_t)sp * R + r) * O + o];
+        const Tp x = direct ? (live ? X[r * v.xr + o] : Tp(0)) : xs[r * (TO + 1) + tx];
+        const Tp xm = live ? x * (ra / (Tp)c[r]) : Tp(0);   // eq. 11
+        xs[r * (TO + 1) + tx] = xm;
+        if (direct && live) X[r * v.xr + o] = xm;
+    }
+    __syncthreads();
+    if (!direct) {
+        for (int i = ty; i < TO; i += 8) {
+            const int64_t oi = o0 + i;
+            if (oi >= O) break;
+#pragma unroll 4
+            for (int64_t r = tx; r < R; r += 32) X[r * v.xr + oi * v.xo] = xs[r * (TO + 1) + i];
+        }
+    }
+    for (int64_t r = tid; r < R; r += 256) {
+        Tp s = Tp(0);
+#pragma unroll 8
+        for (int i = 0; i < TO; ++i) s += xs[r * (TO + 1) + i];
+        fpart[(int64_t)blockIdx.x * R + r] = (double)s;
+    }
+}
+
 // One tile job of k_scale_ops.
 struct OpsArgs {
     // the target half-step's X (element (r, o) at X[r * xr + o * xo]) and Y ((s, r) at

@@ -340,6 +340,16 @@ int Simt<Tp>::select_fused(const View& v, const Tp* Xmu, const Tp* Xdna, const d
 }
 
 template <typename Tp>
+int Simt<Tp>::mu_fused(const View& v, const double* c, const Tp* A, int splits, double* fpart,
+                       cudaStream_t st) {
+    const size_t smem = glue::select_smem<Tp>(v.R);
+    auto k = glue::k_mu_fused<Tp>;
+    if (simt::prep_smem(k, smem)) return DNA_ERR_CUDA;
+    k<<<(unsigned)glue_parts(v.O), dim3(32, 8), smem, st>>>(v, c, A, splits, fpart);
+    return simt::launch_status();
+}
+
+template <typename Tp>
 int Simt<Tp>::part_sums(const double* part, int64_t nparts, int64_t R, double reg, double* out,
                         cudaStream_t st) {
     if (R <= 1024)   // a CTA per r: latency of one load round and a tree, not of nparts / 32

@@ -11,7 +11,10 @@ import numpy as np
 import pytest
 
 import workloads
-from gpu_helpers import ELEM_TOL, GpuProblem, rel_elem, rel_fro, replay_choice
+import dataclasses
+
+from gpu_helpers import (ELEM_TOL, GpuProblem, rel_elem, rel_fro, replay_choice,
+                         step_elementwise)
 from oracle import dna as o
 
 pytestmark = pytest.mark.gpu
@@ -82,12 +85,22 @@ def test_group_matches_oracle_per_half_step():
         V64 = [p.V.astype(np.float64) for p in probs]
         for it in range(2):
             for which in (0, 1):
+                torch.cuda.synchronize()
+                before = [(w.double().cpu().numpy(), h.double().cpu().numpy()) for w, h in zip(W, H)]
                 (dna.dna_group_step_H if which == 0 else dna.dna_group_step_W)(g)
                 torch.cuda.synchronize()
                 for q, p in enumerate(probs):
                     Wr, Hr = ref[q]
                     n = p.V.shape[1] if which == 0 else p.V.shape[0]
                     ch = dna.dna_group_get_choice(g, q, which, n)
+                    # element-wise, one step from the group's own state (gpu_helpers bound)
+                    W0, H0 = before[q]
+                    one = (o.h_half_step if which == 0 else o.w_half_step)(V64[q], W0, H0)
+                    m1, _ = replay_choice(one, ch, "f32")
+                    assert step_elementwise(dataclasses.replace(one, choice=m1), which, W0, H0,
+                                            W[q].double().cpu().numpy(),
+                                            H[q].double().cpu().numpy(), "f32",
+                                            label="group") <= 1.0, (q, it, which)
                     if which == 0:
                         half = o.h_half_step(V64[q], Wr, Hr)
                         mask, _ = replay_choice(half, ch, "f32")

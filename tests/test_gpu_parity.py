@@ -58,6 +58,33 @@ def test_plain_small_mu_iterations(kind):
 
 
 @pytest.mark.parametrize("kind", ["f32", "f32t", "f64"])
+def test_mu_iterate_matches_oracle(kind):
+    """mu_iterate (MU iterations with each half-step preparing the next) against the oracle's
+    MU (eq. 11 then steps 16 / 29), and bit-identical to the same iterations by mu_step."""
+    p = workloads.custom(150, 333, 12, seed=31)
+    V = p.V.astype(np.float64)
+    W, H = o.normalize_w_columns(p.W, p.H)
+    for _ in range(4):
+        W, H = o.mu_iteration(V, W, H)
+    outs = []
+    for chained in (True, False):
+        with GpuProblem(p.V, p.W, p.H, kind) as gp:
+            gp.dna.dna_normalize(gp.ctx, 1)
+            if chained:
+                gp.dna.mu_iterate(gp.ctx, 4)
+            else:
+                for _ in range(4):
+                    gp.dna.mu_step(gp.ctx, 0)
+                    gp.dna.mu_step(gp.ctx, 1)
+            outs.append(gp.WH())
+    Wg, Hg = outs[0]
+    assert rel_fro(Wg, W) < TOL[kind] and rel_fro(Hg, H) < TOL[kind]
+    assert rel_elem(Wg, W, "mu W") < ELEM_TOL[kind] and rel_elem(Hg, H, "mu H") < ELEM_TOL[kind]
+    np.testing.assert_array_equal(outs[0][0], outs[1][0])
+    np.testing.assert_array_equal(outs[0][1], outs[1][1])
+
+
+@pytest.mark.parametrize("kind", ["f32", "f32t", "f64"])
 def test_plain_small_final_kl_free_running(kind):
     """50 free-running DNA iterations: final d_KL within 1e-3 relative (FP32)."""
     p = workloads.plain_small(0)

@@ -213,7 +213,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["dna", "reference"], default="dna")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched", "unrolled"],
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched", "unrolled"] + sorted(SPARSE),
                     default="plain_large")
     ap.add_argument("--dtype", choices=["f32", "f64", "bf16"], default="f32")
     ap.add_argument("--engine", choices=["auto", "simt", "tensor"], default=None,
@@ -229,6 +229,7 @@ def main(argv=None):
                     help="FP32 iterations that set the target at N=8192 T=32768 R=512")
     ap.add_argument("--no-c3-target", action="store_true")
     ap.add_argument("--no-mu-log", action="store_true")
+    ap.add_argument("--no-sparse", action="store_true")
     ap.add_argument("--log-file", default=None, help="per-iteration DNA/MU log (text)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
@@ -241,6 +242,8 @@ def main(argv=None):
         return run_batched(args, world, rank, local)
     if args.workload == "unrolled":
         return run_unrolled(args, world, rank, local)
+    if args.workload in SPARSE:
+        return run_sparse(args, world, rank, local)
     spec = WORKLOADS[args.workload]
 
     if args.impl == "reference":
@@ -329,6 +332,11 @@ def main(argv=None):
                 line["precision_form"]["time_to_target"] = time_to_target(
                     dna, torch, pprob, args.c3_iters, eng, "precision_large")
             del pprob
+        if args.workload == "plain_large" and not args.no_sparse:
+            sp = workloads.sparse_tdt2(rank)
+            line["sparse_form"] = measure_sparse(dna, torch, sp, max(3, min(args.steps, 50)),
+                                                 args.warmup, peaks)
+            line["sparse_form"]["config"]["workload"] = "sparse_tdt2"
 
     if rank == 0 and not args.no_e2e:
         code = {"f32": dna.DNA_F32, "f64": dna.DNA_F64, "bf16": dna.DNA_BF16}[args.dtype]
@@ -597,6 +605,101 @@ def convergence_log(dna, torch, prob, iters, engine, log_file=None):
         "newton_fraction_at": {str(i): {"H": nw[i - 1][0], "W": nw[i - 1][1]}
                                for i in marks if i > 0},
     }
+
+
+SPARSE = {
+    "sparse_tdt2": (workloads.sparse_tdt2, "36771 x 10212 term counts, 0.35 % non-zeros, R=64 "
+                    "(TDT2's shape), synthetic"),
+    "sparse_newsgroup": (workloads.sparse_newsgroup, "61188 x 18774 term counts, 0.2 % "
+                         "non-zeros, R=64 (Newsgroup's shape), synthetic"),
+}
+
+
+def measure_sparse(dna, torch, sp, steps, warmup, peaks, dtype="f32"):
+    """DNA iterations of the sparse-V form (CSR V, passes over the non-zeros only): CUDA
+    events around `steps` iterations in one dna_iterate call, events around the two passes
+    for the dominant kernel's roofline (algorithmic bytes: the index and value of every
+    non-zero, the column pointers and each factor once, per pass)."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    rp = torch.from_numpy(sp.row_ptr).to(dev)
+    ci = torch.from_numpy(sp.col_idx).to(dev)
+    vals = torch.from_numpy(sp.vals).to(dev, tdt)
+    W = torch.from_numpy(sp.W).to(dev, tdt)
+    H = torch.from_numpy(sp.H).to(dev, tdt)
+    R = sp.W.shape[1]
+    code = dna.DNA_F64 if dtype == "f64" else dna.DNA_F32
+    ctx = dna.dna_create_sparse(sp.N, sp.T, R, sp.nnz, dna.make_opts(dtype=code))
+    stream = torch.cuda.current_stream()
+    try:
+        dna.dna_set_stream(ctx, stream)
+        dna.dna_bind_csr(ctx, rp, ci, vals, W, H)
+        dna.dna_normalize(ctx, 1)
+        kl0 = dna.dna_kl(ctx)
+        dna.dna_iterate(ctx, warmup)
+        dna.dna_profile_phases(ctx, ["pass1", "pass2"])
+        dna.dna_phase_times(ctx)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        dna.dna_iterate(ctx, steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        ph = dna.dna_phase_times(ctx)
+        dna.dna_profile(ctx, False)
+        kl1 = dna.dna_kl(ctx)
+    finally:
+        dna.dna_destroy(ctx)
+    es = 8 if dtype == "f64" else 4
+    # per pass: each non-zero's index (4 B) and value, the O + 1 pointers, both factors once
+    bytes_h = sp.nnz * (4 + es) + (sp.T + 1) * 8 + es * R * (sp.N + sp.T)
+    bytes_w = sp.nnz * (4 + es) + (sp.N + 1) * 8 + es * R * (sp.N + sp.T)
+    dom = max(("pass1", "pass2"), key=lambda p: ph[p][0])
+    dom_ms, dom_n = ph[dom]
+    per_launch = dom_ms / max(dom_n, 1) / 1e3
+    alg = (bytes_h + bytes_w) / 2                  # average over the H and W views
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    it_bytes = 2 * (bytes_h + bytes_w)             # two passes per view
+    return {
+        "value": steps / (ms / 1e3), "unit": UNIT, "steps": steps, "ms_per_step": ms / steps,
+        "config": {"N": sp.N, "T": sp.T, "R": R, "nnz": sp.nnz, "density": sp.nnz / (sp.N * sp.T),
+                   "form": dtype.upper(), "engine": "simt sparse (warp per column / row)"},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": alg / per_launch / 1e9,
+                     "peak": hbm, "unit": "GB/s", "frac": alg / per_launch / 1e9 / hbm,
+                     "traffic": None, "algorithmic_bytes_per_launch": alg,
+                     "launch_ms": per_launch * 1e3,
+                     "iteration_hbm_frac": it_bytes / (ms / steps / 1e3) / 1e9 / hbm,
+                     "note": "the rows of the fixed factor gathered per non-zero are served "
+                             "by L2 and not counted; the passes are bound by those gathers"},
+        "kl_start": kl0, "kl_end": kl1,
+    }
+
+
+def run_sparse(args, world, rank, local):
+    """The sparse-V form on a synthetic term-count workload (one line)."""
+    import torch
+
+    import paper_1301_3389_gb300 as dna
+    torch.cuda.set_device(local)
+    fn, desc = SPARSE[args.workload]
+    sp = fn(rank)
+    peaks = measured_peaks()
+    clocks = ClockSampler(local)
+    time.sleep(0.3)
+    res = measure_sparse(dna, torch, sp, args.steps, args.warmup, peaks, args.dtype)
+    clk = clocks.stop()
+    line = {"metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": args.dtype, "data": "synthetic",
+            "config": dict(res["config"], workload=args.workload, desc=desc,
+                           l2="factors and indices fit L2; no flush (steady-state iterations)"),
+            "roofline": res["roofline"], "clocks": clk,
+            "kl_start": res["kl_start"], "kl_end": res["kl_end"]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
 
 
 def run_batched(args, world, rank, local):

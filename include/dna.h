@@ -91,6 +91,35 @@ int dna_create(int64_t N, int64_t T, int64_t R, const dna_opts* opts, dna_ctx** 
  * V, and the transposed copy used by the W half-step).  V must not change while bound. */
 int dna_bind(dna_ctx* ctx, const void* V, int64_t ldv, void* W, void* H);
 
+/* ---------------------------------------------------------------- sparse-V form
+ * The paper's sparse workloads (Section 4.2; the note after Algorithm 1 on zeros in V):
+ * V is given in CSR and every O(NRT) step touches only its non-zeros.  z is formed at the
+ * non-zeros only; q = v / z and v / z^2 vanish at the zeros, so A and B (eq. 7, 14) and the
+ * -v log z part of the candidates' costs (steps 9, 14) are sums over the non-zeros, and
+ * sum_n z_nt = sum_r (sum_n w_nr) h_rt needs no zeros either.  Candidates, selection and
+ * normalisation are those of the dense form.  F32 and F64 forms on the CUDA cores,
+ * R <= 128.  A context made by dna_create_sparse is bound with dna_bind_csr (not
+ * dna_bind) and takes dna_normalize, dna_step_H, dna_step_W, dna_iterate, mu_step,
+ * mu_iterate, dna_kl, dna_get_choice, dna_get_costs, dna_get_status; the other calls
+ * return DNA_ERR_UNSUPPORTED. */
+
+/* Create a sparse-V context for an N x T matrix V with nnz stored entries, rank R
+ * (1 <= R <= 128), F32 or F64 (BF16 or the tensor engine: DNA_ERR_UNSUPPORTED).
+ * Allocates O(nnz + (N + T) R) of workspace. */
+int dna_create_sparse(int64_t N, int64_t T, int64_t R, int64_t nnz, const dna_opts* opts,
+                      dna_ctx** out);
+
+/* Attach V in CSR form and the factors, all device memory owned by the caller and kept
+ * unchanged while bound: row_ptr (N + 1 int64, row_ptr[0] = 0, non-decreasing,
+ * row_ptr[N] = nnz), col_idx (nnz int32 in [0, T), any order within a row), vals (nnz
+ * values >= 0 of the context's element type; explicit zeros allowed), W (N x R) and H
+ * (R x T).  Copies the structure to the host once, checks it (DNA_ERR_ARG if it is not a
+ * valid CSR of an N x T matrix with non-negative values), builds the library's CSC copy
+ * (the H half-step's view, rows ascending within a column) and the row and column sums of
+ * V.  Synchronises the context's stream. */
+int dna_bind_csr(dna_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
+                 const void* vals, void* W, void* H);
+
 /* Set the CUDA stream (a cudaStream_t; NULL = legacy default stream) for later calls. */
 int dna_set_stream(dna_ctx* ctx, void* stream);
 

@@ -57,6 +57,8 @@ def _load() -> ctypes.CDLL:
         "dna_iterate": (I, [P, I]),
         "mu_step": (I, [P, I]),
         "mu_iterate": (I, [P, I]),
+        "dna_create_sparse": (I, [I64, I64, I64, I64, ctypes.POINTER(dna_opts), ctypes.POINTER(P)]),
+        "dna_bind_csr": (I, [P, P, P, P, P, P]),
         "dna_kl": (I, [P, ctypes.POINTER(D)]),
         "dna_get_choice": (I, [P, I, P, I64]),
         "dna_get_costs": (I, [P, I, P, P, I64]),
@@ -147,6 +149,19 @@ def dna_create(N: int, T: int, R: int, opts: dna_opts | None = None) -> int:
     _check(LIB.dna_create(N, T, R, ctypes.byref(opts) if opts is not None else None,
                           ctypes.byref(h)), "dna_create")
     return h.value
+
+
+def dna_create_sparse(N: int, T: int, R: int, nnz: int, opts: dna_opts | None = None) -> int:
+    h = ctypes.c_void_p()
+    _check(LIB.dna_create_sparse(N, T, R, nnz, ctypes.byref(opts) if opts is not None else None,
+                                 ctypes.byref(h)), "dna_create_sparse")
+    return h.value
+
+
+def dna_bind_csr(ctx: int, row_ptr, col_idx, vals, W, H) -> None:
+    """row_ptr int64 (N + 1), col_idx int32 (nnz), vals (nnz), W, H: device tensors."""
+    _check(LIB.dna_bind_csr(ctx, _ptr(row_ptr), _ptr(col_idx), _ptr(vals), _ptr(W), _ptr(H)),
+           "dna_bind_csr")
 
 
 def dna_bind(ctx: int, V, W, H, ldv: int | None = None) -> None:

@@ -73,6 +73,19 @@ struct dna_ctx {
     dna::TcMaps maps[2];             // TMA descriptors of the H view (0) and W view (1)
     int tsp1[2] = {1, 1}, tsp2[2] = {1, 1};
     int64_t tper1[2] = {0, 0}, tper2[2] = {0, 0};
+    // sparse-V form: the caller's CSR of V (the W half-step's view), the library's CSC (the
+    // H half-step's view), a transposed copy of H (gathered by the W half-step) and the
+    // column sums c0 of the fixed factor without regularisation (sum_s z = sum_r c0_r x_r)
+    bool sparse = false;
+    int64_t nnz = 0;
+    const int64_t* rptr = nullptr;
+    const int32_t* cidx = nullptr;
+    const void* rval = nullptr;
+    int64_t* cptr = nullptr;
+    int32_t* ridx = nullptr;
+    void* cval = nullptr;
+    void* Yt = nullptr;
+    double* c0 = nullptr;
     // profiling: event pairs around phases, launch counts
     unsigned prof_mask = 0;          // phases whose instances get an event pair
     std::vector<cudaEvent_t> ev_pool;
@@ -200,7 +213,7 @@ void free_all(dna_ctx* c) {
     void* ptrs[] = {c->own_V, c->own_W, c->own_H, c->Vt, c->colsum_v, c->rowsum_v, c->c, c->sig,
                     c->fwork, c->gpart, c->vpart, c->Apart, c->Bpart, c->Xmu, c->Xdna, c->dpart, c->dfin_h, c->dfin_w,
                     c->choice_h, c->choice_w, c->kl_dev, c->kl_part, c->status, c->Xk, c->Yk, c->Ytk,
-                    c->Y2tk, c->Xmk, c->Xdk, c->Vp};
+                    c->Y2tk, c->Xmk, c->Xdk, c->Vp, c->cptr, c->ridx, c->cval, c->Yt, c->c0};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t ev : c->ev_pool) cudaEventDestroy(ev);
@@ -263,6 +276,91 @@ int alloc_workspace(dna_ctx* c) {
     if (cudaMemset(c->choice_w, 0, (size_t)N) != cudaSuccess) return DNA_ERR_CUDA;
     if (cudaMemset(c->dfin_h, 0, sizeof(double) * 2 * T) != cudaSuccess) return DNA_ERR_CUDA;
     if (cudaMemset(c->dfin_w, 0, sizeof(double) * 2 * N) != cudaSuccess) return DNA_ERR_CUDA;
+    return DNA_OK;
+}
+
+// Workspace of the sparse-V form: no transposed copy of V (the CSC copy has nnz entries)
+// and one split (each view column is reduced by one warp).
+template <typename Tp>
+int alloc_sparse_workspace(dna_ctx* c) {
+    const int64_t N = c->N, T = c->T, R = c->R, M = std::max(N, T);
+    int e = DNA_OK;
+    e |= dmalloc(&c->colsum_v, sizeof(double) * T);
+    e |= dmalloc(&c->rowsum_v, sizeof(double) * N);
+    e |= dmalloc(&c->c, sizeof(double) * R);
+    e |= dmalloc(&c->c0, sizeof(double) * R);
+    e |= dmalloc(&c->sig, sizeof(double) * R);
+    e |= dmalloc(&c->fwork, sizeof(double) * dna::FSUM_SPLITS * R);
+    e |= dmalloc(&c->gpart, sizeof(double) * (size_t)(dna::Simt<Tp>::glue_parts(M) * R));
+    e |= dmalloc(&c->Apart, sizeof(Tp) * (size_t)(R * M));
+    e |= dmalloc(&c->Bpart, sizeof(Tp) * (size_t)(R * M));
+    e |= dmalloc(&c->Xmu, sizeof(Tp) * (size_t)(R * M));
+    e |= dmalloc(&c->Xdna, sizeof(Tp) * (size_t)(R * M));
+    e |= dmalloc(&c->dpart, sizeof(double) * (size_t)(2 * M));
+    e |= dmalloc(&c->dfin_h, sizeof(double) * 2 * T);
+    e |= dmalloc(&c->dfin_w, sizeof(double) * 2 * N);
+    e |= dmalloc(&c->choice_h, (size_t)T);
+    e |= dmalloc(&c->choice_w, (size_t)N);
+    e |= dmalloc(&c->kl_dev, sizeof(double));
+    e |= dmalloc(&c->kl_part, sizeof(double) * (size_t)dna::REDUCE_PARTS);
+    e |= dmalloc(&c->status, sizeof(int));
+    e |= dmalloc(&c->cptr, sizeof(int64_t) * (size_t)(T + 1));
+    e |= dmalloc(&c->ridx, sizeof(int32_t) * (size_t)std::max<int64_t>(c->nnz, 1));
+    e |= dmalloc(&c->cval, sizeof(Tp) * (size_t)std::max<int64_t>(c->nnz, 1));
+    e |= dmalloc(&c->Yt, sizeof(Tp) * (size_t)(T * R));
+    if (e != DNA_OK) return DNA_ERR_ALLOC;
+    if (cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess ||
+        cudaMemset(c->choice_h, 0, (size_t)T) != cudaSuccess ||
+        cudaMemset(c->choice_w, 0, (size_t)N) != cudaSuccess ||
+        cudaMemset(c->dfin_h, 0, sizeof(double) * 2 * T) != cudaSuccess ||
+        cudaMemset(c->dfin_w, 0, sizeof(double) * 2 * N) != cudaSuccess)
+        return DNA_ERR_CUDA;
+    return DNA_OK;
+}
+
+// The CSC copy of V and the row and column sums of V (eq. 10 targets), built on the host
+// from the caller's CSR (copied in once): the structure is validated first, so no kernel
+// can index outside V, W or H.  Within a column the non-zeros keep ascending row order.
+template <typename Tp>
+int bind_csr(dna_ctx* c, const int64_t* rptr, const int32_t* cidx, const Tp* vals) {
+    const int64_t N = c->N, T = c->T, nnz = c->nnz;
+    std::vector<int64_t> rp((size_t)N + 1);
+    std::vector<int32_t> ci((size_t)nnz);
+    std::vector<Tp> vv((size_t)nnz);
+    cudaStream_t st = c->stream;
+    if (cudaMemcpyAsync(rp.data(), rptr, sizeof(int64_t) * (N + 1), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        (nnz && cudaMemcpyAsync(ci.data(), cidx, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost, st) != cudaSuccess) ||
+        (nnz && cudaMemcpyAsync(vv.data(), vals, sizeof(Tp) * nnz, cudaMemcpyDeviceToHost, st) != cudaSuccess) ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return DNA_ERR_CUDA;
+    if (rp[0] != 0 || rp[N] != nnz) return DNA_ERR_ARG;
+    for (int64_t n = 0; n < N; ++n)
+        if (rp[n + 1] < rp[n]) return DNA_ERR_ARG;
+    for (int64_t k = 0; k < nnz; ++k)
+        if (ci[k] < 0 || ci[k] >= T || !(vv[k] >= Tp(0))) return DNA_ERR_ARG;
+    std::vector<int64_t> cp((size_t)T + 1, 0);
+    for (int64_t k = 0; k < nnz; ++k) ++cp[ci[k] + 1];
+    for (int64_t t = 0; t < T; ++t) cp[t + 1] += cp[t];
+    std::vector<int64_t> fill(cp.begin(), cp.end() - 1);
+    std::vector<int32_t> ri((size_t)nnz);
+    std::vector<Tp> cv((size_t)nnz);
+    std::vector<double> rs((size_t)N, 0.0), cs((size_t)T, 0.0);
+    for (int64_t n = 0; n < N; ++n)
+        for (int64_t k = rp[n]; k < rp[n + 1]; ++k) {
+            const int64_t at = fill[ci[k]]++;
+            ri[at] = (int32_t)n;
+            cv[at] = vv[k];
+            rs[n] += (double)vv[k];
+        }
+    for (int64_t t = 0; t < T; ++t)
+        for (int64_t k = cp[t]; k < cp[t + 1]; ++k) cs[t] += (double)cv[k];
+    if (cudaMemcpyAsync(c->cptr, cp.data(), sizeof(int64_t) * (T + 1), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        (nnz && cudaMemcpyAsync(c->ridx, ri.data(), sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, st) != cudaSuccess) ||
+        (nnz && cudaMemcpyAsync(c->cval, cv.data(), sizeof(Tp) * nnz, cudaMemcpyHostToDevice, st) != cudaSuccess) ||
+        cudaMemcpyAsync(c->rowsum_v, rs.data(), sizeof(double) * N, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(c->colsum_v, cs.data(), sizeof(double) * T, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)   // the host vectors go out of scope
+        return DNA_ERR_CUDA;
     return DNA_OK;
 }
 
@@ -405,6 +503,8 @@ int prep_step(dna_ctx* c, int w, bool with_sq) {
 
 template <typename Tp>
 int finish_step(dna_ctx* c, int w, bool next);
+template <typename Tp>
+int sparse_half_step(dna_ctx* c, int w, bool mu_only, bool prepared, bool next);
 
 // One half-step (w = 0: Algorithm 1 steps 4-16, w = 1: steps 17-29).  mu_only: the
 // multiplicative update of eq. 11 instead of DNA.  prepared: the operands and c of this
@@ -412,6 +512,7 @@ int finish_step(dna_ctx* c, int w, bool next);
 // for half-step 1 - w (the step 16 / 29 normalisation writes them in the same pass).
 template <typename Tp>
 int half_step(dna_ctx* c, int w, bool mu_only, bool prepared, bool next) {
+    if (c->sparse) return sparse_half_step<Tp>(c, w, mu_only, prepared, next);
     using S = dna::Simt<Tp>;
     const View v = make_view(c, w == 1);
     Tp* A = static_cast<Tp*>(c->Apart);
@@ -508,6 +609,80 @@ int finish_step(dna_ctx* c, int w, bool next) {
     });
 }
 
+// One half-step of the sparse-V form: the same steps as half_step with the two O(NRT)
+// passes replaced by passes over the non-zeros (sparse_kernels.cuh); candidates, selection
+// and normalisation are the dense glue kernels (they touch only W, H and O-vectors).
+template <typename Tp>
+int sparse_half_step(dna_ctx* c, int w, bool mu_only, bool prepared, bool next) {
+    using S = dna::Simt<Tp>;
+    const View v = make_view(c, w == 1);
+    Tp* A = static_cast<Tp*>(c->Apart);
+    Tp* B = static_cast<Tp*>(c->Bpart);
+    Tp* Xmu = static_cast<Tp*>(c->Xmu);
+    Tp* Xdna = static_cast<Tp*>(c->Xdna);
+    cudaStream_t st = c->stream;
+    int e = DNA_OK;
+    if (!prepared)
+        if ((e = prep_step<Tp>(c, w, false))) return e;
+    // c0 from the per-block column sums of Y that the preparation left in gpart
+    e = phase(c, DNA_PHASE_SUMS, 1, [&] {
+        return S::raw_sums(c->gpart, S::glue_parts(v.S), c->R, c->c0, st);
+    });
+    if (e) return e;
+    const Tp* Yg = static_cast<const Tp*>(c->W);   // H-step: W is already S x R
+    if (w == 1) {                                   // W-step: gather rows of H^t
+        e = phase(c, DNA_PHASE_OPERANDS, 1, [&] {
+            return S::transpose(static_cast<const Tp*>(c->H), c->R, c->T, static_cast<Tp*>(c->Yt), st);
+        });
+        if (e) return e;
+        Yg = static_cast<const Tp*>(c->Yt);
+    }
+    const int64_t* ptr = w ? c->rptr : c->cptr;
+    const int32_t* idx = w ? c->cidx : c->ridx;
+    const Tp* val = static_cast<const Tp*>(w ? c->rval : c->cval);
+    e = phase(c, DNA_PHASE_PASS1, 1, [&] {
+        return S::sp_pass1(v, ptr, idx, val, Yg, A, B, !mu_only, c->status, st);
+    });
+    if (e) return e;
+    if (mu_only) {
+        e = phase(c, DNA_PHASE_CANDIDATES, 1, [&] { return S::mu_fused(v, c->c, A, 1, c->gpart, st); });
+        return e ? e : finish_step<Tp>(c, w, next);
+    }
+    e = phase(c, DNA_PHASE_CANDIDATES, 1, [&] {
+        return S::cand_fused(v, c->c, A, B, 1, Xmu, Xdna, c->o.eps, c->o.alpha, nullptr, nullptr,
+                             0, 0, 0, st);
+    });
+    if (e) return e;
+    e = phase(c, DNA_PHASE_PASS2, 1, [&] {
+        return S::sp_pass2(v, ptr, idx, val, Yg, Xmu, Xdna, c->c0, c->dpart, c->status, st);
+    });
+    if (e) return e;
+    e = phase(c, DNA_PHASE_SELECT, 1, [&] {
+        return S::select_fused(v, Xmu, Xdna, c->dpart, 1, w ? c->choice_w : c->choice_h,
+                               w ? c->dfin_w : c->dfin_h, c->gpart, w ? c->o.rho : c->o.lambda,
+                               st);
+    });
+    if (e) return e;
+    return finish_step<Tp>(c, w, next);
+}
+
+// d_KL of the sparse-V form: per column of V the non-zeros' v log(v / z) - v plus
+// sum_r c0_r h(r, t) (c0 = column sums of W), then the fixed-order total.
+template <typename Tp>
+int sparse_kl(dna_ctx* c) {
+    using S = dna::Simt<Tp>;
+    const View v = make_view(c, false);
+    cudaStream_t st = c->stream;
+    return phase(c, DNA_PHASE_KL, 4, [&] {
+        int e = S::scale_ops(v, nullptr, false, nullptr, nullptr, nullptr, nullptr, 0, 0, 0, 0,
+                             c->gpart, st);
+        if (!e) e = S::raw_sums(c->gpart, S::glue_parts(v.S), c->R, c->c0, st);
+        if (!e) e = S::sp_kl(v, c->cptr, c->ridx, static_cast<const Tp*>(c->cval),
+                             static_cast<const Tp*>(c->W), c->c0, c->dpart, c->status, st);
+        return e ? e : dna::reduce_sum(c->dpart, c->T, c->kl_dev, c->kl_part, st);
+    });
+}
+
 // Gradient of eq. 1 (no regularisation) with respect to W, H and V, scaled by `scale`:
 // dH = W^t (1 - Q) = (W^t 1) - W^t Q, dW = (1 - Q) H^t = (H 1)^t - Q H^t, dV = log(V / Z).
 // The raw W^t Q and Q H^t are pass 1 of the H and W views without the Qbar half.
@@ -532,6 +707,7 @@ int kl_backward(dna_ctx* c, double scale, Tp* dW, Tp* dH, Tp* dV) {
 
 template <typename Tp>
 int kl_async(dna_ctx* c) {
+    if (c->sparse) return sparse_kl<Tp>(c);
     const View v = make_view(c, false);
     if constexpr (sizeof(Tp) == 4)
         if (c->split) {   // the split tensor-core pass 2 on the H view's current operands
@@ -703,9 +879,58 @@ int dna_create(int64_t N, int64_t T, int64_t R, const dna_opts* opts, dna_ctx** 
     return DNA_OK;
 }
 
+int dna_create_sparse(int64_t N, int64_t T, int64_t R, int64_t nnz, const dna_opts* opts,
+                      dna_ctx** out) {
+    if (!out) return DNA_ERR_ARG;
+    *out = nullptr;
+    if (N < 1 || T < 1 || R < 1 || nnz < 0) return DNA_ERR_ARG;
+    if (N > ((int64_t)1 << 31) - 1 || T > ((int64_t)1 << 31) - 1 || nnz > ((int64_t)1 << 40))
+        return DNA_ERR_ARG;
+    dna_opts o;
+    dna_default_opts(&o);
+    if (opts) o = *opts;
+    if (!valid_opts(o)) return DNA_ERR_ARG;
+    if (R > 128 || o.dtype == DNA_BF16 || o.engine == DNA_ENGINE_TENSOR) return DNA_ERR_UNSUPPORTED;
+    dna_ctx* c = new (std::nothrow) dna_ctx();
+    if (!c) return DNA_ERR_ALLOC;
+    c->N = N; c->T = T; c->R = R; c->o = o;
+    c->sparse = true;
+    c->nnz = nnz;
+    c->esz = o.dtype == DNA_F64 ? 8 : 4;
+    if (cudaGetDevice(&c->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return DNA_ERR_CUDA;
+    }
+    const int e = is_f64(c) ? alloc_sparse_workspace<double>(c) : alloc_sparse_workspace<float>(c);
+    if (e != DNA_OK) {
+        free_all(c);
+        delete c;
+        return e;
+    }
+    *out = c;
+    return DNA_OK;
+}
+
+int dna_bind_csr(dna_ctx* c, const int64_t* row_ptr, const int32_t* col_idx, const void* vals,
+                 void* W, void* H) {
+    if (!c || !c->sparse || !row_ptr || (c->nnz && (!col_idx || !vals)) || !W || !H)
+        return DNA_ERR_ARG;
+    if (set_device(c)) return DNA_ERR_CUDA;
+    const int e = is_f64(c) ? bind_csr<double>(c, row_ptr, col_idx, static_cast<const double*>(vals))
+                            : bind_csr<float>(c, row_ptr, col_idx, static_cast<const float*>(vals));
+    if (e) return e;
+    c->rptr = row_ptr; c->cidx = col_idx; c->rval = vals;
+    c->W = W; c->H = H;
+    c->bound = true;
+    return DNA_OK;
+}
+
 int dna_bind(dna_ctx* c, const void* V, int64_t ldv, void* W, void* H) {
     if (!c || !V || !W || !H || ldv < c->T) return DNA_ERR_ARG;
-    if (c->host_mode) return DNA_ERR_ARG;
+    if (c->host_mode || c->sparse) return DNA_ERR_ARG;
     if (set_device(c)) return DNA_ERR_CUDA;
     c->V = V; c->ldv = ldv; c->W = W; c->H = H;
     c->bound = true;
@@ -807,7 +1032,7 @@ int dna_kl(dna_ctx* c, double* out) {
 
 int dna_step_H_fixed(dna_ctx* c, uint8_t* choice_out) {
     if (int e = check_ready(c)) return e;
-    if (c->tc) return DNA_ERR_UNSUPPORTED;
+    if (c->tc || c->sparse) return DNA_ERR_UNSUPPORTED;
     if (set_device(c)) return DNA_ERR_CUDA;
     return is_f64(c) ? step_h_fixed<double>(c, choice_out) : step_h_fixed<float>(c, choice_out);
 }
@@ -816,7 +1041,7 @@ int dna_step_H_adjoint(dna_ctx* c, const void* Hk, const uint8_t* choice, const 
                        void* Hbar_out, void* Vbar) {
     if (int e = check_ready(c)) return e;
     if (!Hk || !choice || !Hbar_next || !Hbar_out || !Vbar) return DNA_ERR_ARG;
-    if (c->tc || (is_f64(c) ? c->R > 64 : c->R > 128)) return DNA_ERR_UNSUPPORTED;
+    if (c->tc || c->sparse || (is_f64(c) ? c->R > 64 : c->R > 128)) return DNA_ERR_UNSUPPORTED;
     if (set_device(c)) return DNA_ERR_CUDA;
     if (is_f64(c))
         return step_h_adjoint<double>(c, static_cast<const double*>(Hk), choice,
@@ -829,7 +1054,7 @@ int dna_step_H_adjoint(dna_ctx* c, const void* Hk, const uint8_t* choice, const 
 
 int dna_kl_backward(dna_ctx* c, double scale, void* dW, void* dH, void* dV) {
     if (int e = check_ready(c)) return e;
-    if (c->tc) return DNA_ERR_UNSUPPORTED;
+    if (c->tc || c->sparse) return DNA_ERR_UNSUPPORTED;
     if (set_device(c)) return DNA_ERR_CUDA;
     if (is_f64(c))
         return kl_backward<double>(c, scale, static_cast<double*>(dW), static_cast<double*>(dH),
@@ -870,6 +1095,7 @@ int dna_get_status(dna_ctx* c) {
 
 int dna_run_host(dna_ctx* c, const void* V, void* W, void* H, int iters, double* kl_out) {
     if (!c || !V || !W || !H || iters < 0) return DNA_ERR_ARG;
+    if (c->sparse) return DNA_ERR_UNSUPPORTED;
     if (c->bound && !c->host_mode) return DNA_ERR_ARG;
     if (set_device(c)) return DNA_ERR_CUDA;
     const size_t es = c->esz;

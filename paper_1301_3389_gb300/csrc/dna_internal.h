@@ -118,6 +118,22 @@ template <typename Tp> struct Simt {
                          void* Ytk, void* Y2tk, int64_t rp, int64_t O_pad, int64_t S_pad,
                          int64_t plane, double* cpart, cudaStream_t st);
     static int64_t glue_parts(int64_t n);   // partial sums per R of the fused glue
+    // out[r] = sum over k < nparts of part[k * R + r] (fixed order; no regularisation and
+    // no replacement of a zero sum: the column sums c0 of Y that sum_s z needs)
+    static int raw_sums(const double* part, int64_t nparts, int64_t R, double* out,
+                        cudaStream_t st);
+    // Sparse-V form (sparse_kernels.cuh): the view's non-zeros of column o are
+    // k in [ptr[o], ptr[o + 1]) at s = idx[k] with value val[k]; Yg is Y as S x R row-major.
+    // R <= 128.
+    static int sp_pass1(const View& v, const int64_t* ptr, const int32_t* idx, const Tp* val,
+                        const Tp* Yg, Tp* A, Tp* B, bool with_b, int* status, cudaStream_t st);
+    static int sp_pass2(const View& v, const int64_t* ptr, const int32_t* idx, const Tp* val,
+                        const Tp* Yg, const Tp* Xmu, const Tp* Xdna, const double* c0,
+                        double* dpart, int* status, cudaStream_t st);
+    static int sp_kl(const View& v, const int64_t* ptr, const int32_t* idx, const Tp* val,
+                     const Tp* Yg, const double* c0, double* part, int* status, cudaStream_t st);
+    // out (cols x rows) = in^t (rows x cols), both row-major
+    static int transpose(const Tp* in, int64_t rows, int64_t cols, Tp* out, cudaStream_t st);
     // one-time: row and column sums of V (float64) and the transposed copy
     static int prepare_v(const Tp* V, int64_t N, int64_t T, int64_t ldv, Tp* Vt, int64_t ldvt,
                          double* colsum, double* rowsum, cudaStream_t st,

@@ -5,6 +5,7 @@
 
 #include "glue_kernels.cuh"
 #include "simt_kernels.cuh"
+#include "sparse_kernels.cuh"
 
 namespace dna {
 
@@ -439,5 +440,79 @@ int Simt<Tp>::pass2_blocks_per_sm(int64_t R) {
 template <typename Tp> int Simt<Tp>::chunk() { return simt::SB; }
 template <typename Tp> int Simt<Tp>::oblock() { return simt::OB; }
 template <typename Tp> int Simt<Tp>::rblock(int64_t R) { return simt::rblock_for<Tp>(R); }
+
+template <typename Tp>
+int Simt<Tp>::raw_sums(const double* part, int64_t nparts, int64_t R, double* out,
+                       cudaStream_t st) {
+    if (R <= 1024)
+        simt::k_colsum_small<0><<<(unsigned)R, 256, 0, st>>>(part, (int)nparts, R, 0.0, out, false);
+    else
+        simt::k_colsum_final<<<(unsigned)((R + 31) / 32), dim3(32, 32), 0, st>>>(
+            part, (int)nparts, R, 0.0, out, false);
+    return simt::launch_status();
+}
+
+namespace simt {
+template <typename Tp, int RPL>
+int sp_pass1_r(const View& v, const int64_t* ptr, const int32_t* idx, const Tp* val,
+               const Tp* Yg, Tp* A, Tp* B, bool with_b, int* status, cudaStream_t st) {
+    const unsigned grid = (unsigned)((v.O + sparse::WARPS - 1) / sparse::WARPS);
+    sparse::k_sp_pass1<Tp, RPL><<<grid, sparse::WARPS * 32, 0, st>>>(v, ptr, idx, val, Yg, A, B,
+                                                                      with_b, status);
+    return launch_status();
+}
+template <typename Tp, int RPL>
+int sp_pass2_r(const View& v, const int64_t* ptr, const int32_t* idx, const Tp* val,
+               const Tp* Yg, const Tp* Xmu, const Tp* Xdna, const double* c0, double* dpart,
+               int* status, cudaStream_t st) {
+    const unsigned grid = (unsigned)((v.O + sparse::WARPS - 1) / sparse::WARPS);
+    sparse::k_sp_pass2<Tp, RPL><<<grid, sparse::WARPS * 32, 0, st>>>(v, ptr, idx, val, Yg, Xmu,
+                                                                      Xdna, c0, dpart, status);
+    return launch_status();
+}
+template <typename Tp, int RPL>
+int sp_kl_r(const View& v, const int64_t* ptr, const int32_t* idx, const Tp* val, const Tp* Yg,
+            const double* c0, double* part, int* status, cudaStream_t st) {
+    const unsigned grid = (unsigned)((v.O + sparse::WARPS - 1) / sparse::WARPS);
+    sparse::k_sp_kl<Tp, RPL><<<grid, sparse::WARPS * 32, 0, st>>>(v, ptr, idx, val, Yg, c0, part,
+                                                                   status);
+    return launch_status();
+}
+}  // namespace simt
+
+template <typename Tp>
+int Simt<Tp>::sp_pass1(const View& v, const int64_t* ptr, const int32_t* idx, const Tp* val,
+                       const Tp* Yg, Tp* A, Tp* B, bool with_b, int* status, cudaStream_t st) {
+    if (v.R <= 32) return simt::sp_pass1_r<Tp, 1>(v, ptr, idx, val, Yg, A, B, with_b, status, st);
+    if (v.R <= 64) return simt::sp_pass1_r<Tp, 2>(v, ptr, idx, val, Yg, A, B, with_b, status, st);
+    if (v.R <= 128) return simt::sp_pass1_r<Tp, 4>(v, ptr, idx, val, Yg, A, B, with_b, status, st);
+    return DNA_ERR_UNSUPPORTED;
+}
+
+template <typename Tp>
+int Simt<Tp>::sp_pass2(const View& v, const int64_t* ptr, const int32_t* idx, const Tp* val,
+                       const Tp* Yg, const Tp* Xmu, const Tp* Xdna, const double* c0,
+                       double* dpart, int* status, cudaStream_t st) {
+    if (v.R <= 32) return simt::sp_pass2_r<Tp, 1>(v, ptr, idx, val, Yg, Xmu, Xdna, c0, dpart, status, st);
+    if (v.R <= 64) return simt::sp_pass2_r<Tp, 2>(v, ptr, idx, val, Yg, Xmu, Xdna, c0, dpart, status, st);
+    if (v.R <= 128) return simt::sp_pass2_r<Tp, 4>(v, ptr, idx, val, Yg, Xmu, Xdna, c0, dpart, status, st);
+    return DNA_ERR_UNSUPPORTED;
+}
+
+template <typename Tp>
+int Simt<Tp>::sp_kl(const View& v, const int64_t* ptr, const int32_t* idx, const Tp* val,
+                    const Tp* Yg, const double* c0, double* part, int* status, cudaStream_t st) {
+    if (v.R <= 32) return simt::sp_kl_r<Tp, 1>(v, ptr, idx, val, Yg, c0, part, status, st);
+    if (v.R <= 64) return simt::sp_kl_r<Tp, 2>(v, ptr, idx, val, Yg, c0, part, status, st);
+    if (v.R <= 128) return simt::sp_kl_r<Tp, 4>(v, ptr, idx, val, Yg, c0, part, status, st);
+    return DNA_ERR_UNSUPPORTED;
+}
+
+template <typename Tp>
+int Simt<Tp>::transpose(const Tp* in, int64_t rows, int64_t cols, Tp* out, cudaStream_t st) {
+    const dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
+    sparse::k_transpose<Tp><<<grid, dim3(32, 8), 0, st>>>(in, rows, cols, out);
+    return simt::launch_status();
+}
 
 }  // namespace dna

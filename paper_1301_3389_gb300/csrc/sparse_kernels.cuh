@@ -1,0 +1,250 @@
+// Kernels of the sparse-V form (a DNA half-step that touches only the non-zeros of V).
+//
+// A half-step over the (s, o) view of Section 2 (H-step: o = column t, s = row n; W-step:
+// o = row n, s = column t) needs z = (W H)_so only where v_so != 0: the ratios q = v/z and
+// qbar = v/z^2 (steps 3, 10) are 0 elsewhere (the note after Algorithm 1), so A and B
+// (eq. 7, 14) are sums over the non-zeros of the column, and so is the -v log z part of the
+// candidates' costs (steps 9, 14).  The sum z part needs no zeros either:
+// sum_s z_so = sum_r (sum_s y_sr) x_ro = sum_r c0_r x_ro with c0 the column sums of Y.
+//
+// Storage: the non-zeros of view column o are k in [ptr[o], ptr[o + 1]), at s = idx[k] with
+// value val[k] (CSC of V for the H-step, CSR of V for the W-step); Yg is the fixed factor
+// as an S x R row-major array (W for the H-step, a transposed copy of H for the W-step),
+// so the R values of y(s, .) are one contiguous, coalesced row.
+//
+// One warp per view column o; lane l holds r = l + 32 j (j < RPL).  Dot products over r are
+// reduced with a fixed xor butterfly, so every result is bit-reproducible.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "dna_internal.h"
+
+namespace dna {
+namespace sparse {
+
+constexpr int WARPS = 8;   // warps (view columns) per CTA
+constexpr int U = 4;       // non-zeros whose loads are issued together
+
+template <typename Tp>
+__device__ __forceinline__ Tp warp_sum(Tp x) {
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) x += __shfl_xor_sync(0xffffffffu, x, m);
+    return x;
+}
+
+// Pass 1 (Algorithm 1 steps 2-5 and 10 on the non-zeros): raw sums
+// A(r, o) = sum_k y(s_k, r) q_k and B(r, o) = sum_k y(s_k, r)^2 qbar_k, written [R][O]
+// (the layout of split 0 of the dense pass), with q = v / z, qbar = q / z.  Sets
+// STATUS_NONFINITE when z <= 0 (or is not a number) at a positive v.
+template <typename Tp, int RPL>
+__global__ void __launch_bounds__(WARPS * 32)
+    k_sp_pass1(View v, const int64_t* __restrict__ ptr, const int32_t* __restrict__ idx,
+               const Tp* __restrict__ val, const Tp* __restrict__ Yg, Tp* __restrict__ A,
+               Tp* __restrict__ B, bool with_b, int* __restrict__ status) {
+    const int lane = threadIdx.x & 31;
+    const int64_t o = (int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5);
+    if (o >= v.O) return;
+    const int64_t R = v.R;
+    const Tp* __restrict__ X = static_cast<const Tp*>(v.X);
+    Tp x[RPL], a[RPL], b[RPL];
+#pragma unroll
+    for (int j = 0; j < RPL; ++j) {
+        const int64_t r = lane + 32 * j;
+        x[j] = r < R ? X[r * v.xr + o * v.xo] : Tp(0);
+        a[j] = Tp(0);
+        b[j] = Tp(0);
+    }
+    bool bad = false;
+    const int64_t k0 = ptr[o], k1 = ptr[o + 1];
+    for (int64_t k = k0; k < k1; k += U) {
+        Tp vv[U], y[U][RPL], z[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const bool in = k + u < k1;
+            const int64_t s = in ? idx[k + u] : 0;
+            vv[u] = in ? val[k + u] : Tp(0);
+#pragma unroll
+            for (int j = 0; j < RPL; ++j) {
+                const int64_t r = lane + 32 * j;
+                y[u][j] = (in && r < R) ? Yg[s * R + r] : Tp(0);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            Tp p = Tp(0);
+#pragma unroll
+            for (int j = 0; j < RPL; ++j) p += y[u][j] * x[j];
+            z[u] = warp_sum(p);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (!(vv[u] > Tp(0))) continue;        // v = 0 (or padding): q = qbar = 0
+            if (!(z[u] > Tp(0))) { bad = true; continue; }
+            const Tp q = vv[u] / z[u];
+            const Tp qb = q / z[u];
+#pragma unroll
+            for (int j = 0; j < RPL; ++j) {
+                a[j] += y[u][j] * q;
+                b[j] += y[u][j] * y[u][j] * qb;
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < RPL; ++j) {
+        const int64_t r = lane + 32 * j;
+        if (r < R) {
+            A[r * v.O + o] = a[j];
+            if (with_b) B[r * v.O + o] = b[j];
+        }
+    }
+    if (bad && status) atomicOr(status, STATUS_NONFINITE);
+}
+
+// Pass 2 (steps 7-9, 12-14 on the non-zeros): per view column o, the cost of each candidate
+// sum_{v>0} (-v log z) + sum_s z with sum_s z = sum_r c0_r x(r, o), into
+// dpart[0 * O + o] (MU) and dpart[1 * O + o] (Newton) in float64.  The -v log z terms of
+// non-zero k are accumulated by lane (k - k0) mod U, then the lanes' float64 sums are
+// added by the fixed butterfly.
+template <typename Tp, int RPL>
+__global__ void __launch_bounds__(WARPS * 32)
+    k_sp_pass2(View v, const int64_t* __restrict__ ptr, const int32_t* __restrict__ idx,
+               const Tp* __restrict__ val, const Tp* __restrict__ Yg,
+               const Tp* __restrict__ Xmu, const Tp* __restrict__ Xdna,
+               const double* __restrict__ c0, double* __restrict__ dpart,
+               int* __restrict__ status) {
+    const int lane = threadIdx.x & 31;
+    const int64_t o = (int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5);
+    if (o >= v.O) return;
+    const int64_t R = v.R, O = v.O;
+    Tp xm[RPL], xd[RPL];
+    double zm_sum = 0.0, zd_sum = 0.0;
+#pragma unroll
+    for (int j = 0; j < RPL; ++j) {
+        const int64_t r = lane + 32 * j;
+        xm[j] = r < R ? Xmu[r * O + o] : Tp(0);
+        xd[j] = r < R ? Xdna[r * O + o] : Tp(0);
+        if (r < R) {
+            zm_sum += c0[r] * (double)xm[j];
+            zd_sum += c0[r] * (double)xd[j];
+        }
+    }
+    double lm = 0.0, ld = 0.0;   // this lane's -v log z sums
+    const int64_t k0 = ptr[o], k1 = ptr[o + 1];
+    for (int64_t k = k0; k < k1; k += U) {
+        Tp vv[U], y[U][RPL];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const bool in = k + u < k1;
+            const int64_t s = in ? idx[k + u] : 0;
+            vv[u] = in ? val[k + u] : Tp(0);
+#pragma unroll
+            for (int j = 0; j < RPL; ++j) {
+                const int64_t r = lane + 32 * j;
+                y[u][j] = (in && r < R) ? Yg[s * R + r] : Tp(0);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            Tp pm = Tp(0), pd = Tp(0);
+#pragma unroll
+            for (int j = 0; j < RPL; ++j) {
+                pm += y[u][j] * xm[j];
+                pd += y[u][j] * xd[j];
+            }
+            pm = warp_sum(pm);
+            pd = warp_sum(pd);
+            if (lane == u && vv[u] > Tp(0)) {   // log of a non-positive z gives NaN / -inf
+                lm -= (double)(vv[u] * log(pm));
+                ld -= (double)(vv[u] * log(pd));
+            }
+        }
+    }
+    lm = warp_sum(lm);
+    ld = warp_sum(ld);
+    zm_sum = warp_sum(zm_sum);
+    zd_sum = warp_sum(zd_sum);
+    if (lane == 0) {
+        const double dm = lm + zm_sum, dd = ld + zd_sum;
+        dpart[o] = dm;
+        dpart[O + o] = dd;
+        if (!isfinite(dm) || !isfinite(dd)) atomicOr(status, STATUS_NONFINITE);
+    }
+}
+
+// d_KL (eq. 1) per view column o of the H view: sum over the non-zeros of
+// v log(v / z) - v, plus sum_n z_nt = sum_r c0_r h(r, t), into part[o] (float64).
+template <typename Tp, int RPL>
+__global__ void __launch_bounds__(WARPS * 32)
+    k_sp_kl(View v, const int64_t* __restrict__ ptr, const int32_t* __restrict__ idx,
+            const Tp* __restrict__ val, const Tp* __restrict__ Yg, const double* __restrict__ c0,
+            double* __restrict__ part, int* __restrict__ status) {
+    const int lane = threadIdx.x & 31;
+    const int64_t o = (int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5);
+    if (o >= v.O) return;
+    const int64_t R = v.R;
+    const Tp* __restrict__ X = static_cast<const Tp*>(v.X);
+    Tp x[RPL];
+    double zsum = 0.0;
+#pragma unroll
+    for (int j = 0; j < RPL; ++j) {
+        const int64_t r = lane + 32 * j;
+        x[j] = r < R ? X[r * v.xr + o * v.xo] : Tp(0);
+        if (r < R) zsum += c0[r] * (double)x[j];
+    }
+    double acc = 0.0;
+    const int64_t k0 = ptr[o], k1 = ptr[o + 1];
+    for (int64_t k = k0; k < k1; k += U) {
+        Tp vv[U], y[U][RPL];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const bool in = k + u < k1;
+            const int64_t s = in ? idx[k + u] : 0;
+            vv[u] = in ? val[k + u] : Tp(0);
+#pragma unroll
+            for (int j = 0; j < RPL; ++j) {
+                const int64_t r = lane + 32 * j;
+                y[u][j] = (in && r < R) ? Yg[s * R + r] : Tp(0);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            Tp p = Tp(0);
+#pragma unroll
+            for (int j = 0; j < RPL; ++j) p += y[u][j] * x[j];
+            p = warp_sum(p);
+            if (lane == u && vv[u] > Tp(0))
+                acc += (double)(vv[u] * log(vv[u] / p)) - (double)vv[u];
+        }
+    }
+    acc = warp_sum(acc);
+    zsum = warp_sum(zsum);
+    if (lane == 0) {
+        const double d = acc + zsum;
+        part[o] = d;
+        if (!isfinite(d)) atomicOr(status, STATUS_NONFINITE);
+    }
+}
+
+// Y^t: out[t * R + r] = H[r * T + t] (R x T row-major in, T x R row-major out), through
+// 32 x 32 shared-memory tiles so both sides stay coalesced.  CTA (32, 8).
+template <typename Tp>
+__global__ void __launch_bounds__(256) k_transpose(const Tp* __restrict__ in, int64_t rows,
+                                                   int64_t cols, Tp* __restrict__ out) {
+    __shared__ Tp tile[32][33];
+    const int64_t c0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int64_t r = r0 + i, c = c0 + threadIdx.x;
+        tile[i][threadIdx.x] = (r < rows && c < cols) ? in[r * cols + c] : Tp(0);
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int64_t c = c0 + i, r = r0 + threadIdx.x;
+        if (c < cols && r < rows) out[c * rows + r] = tile[threadIdx.x][i];
+    }
+}
+
+}  // namespace sparse
+}  // namespace dna

@@ -261,3 +261,31 @@ def gp_V(gp):
     if not hasattr(gp, "_V64"):
         gp._V64 = gp.V.double().cpu().numpy()
     return gp._V64
+
+
+class SparseGpuProblem(GpuProblem):
+    """A sparse-V problem (workloads.SparseProblem, CSR) bound to a dna_create_sparse context;
+    the same interface as GpuProblem, with the dense V kept for the oracle."""
+
+    def __init__(self, sp, dtype="f32", V_dense=None, **opts):
+        import torch
+
+        import paper_1301_3389_gb300 as dna
+        self.dna = dna
+        self.torch = torch
+        self.kind = dtype
+        code = {"f64": dna.DNA_F64, "f32": dna.DNA_F32}[dtype]
+        self.tdt = torch.float64 if dtype == "f64" else torch.float32
+        self.N, self.T = sp.N, sp.T
+        self.R = sp.W.shape[1]
+        self.rp = torch.from_numpy(sp.row_ptr).cuda()
+        self.ci = torch.from_numpy(sp.col_idx).cuda()
+        self.vals = torch.from_numpy(sp.vals).to("cuda", self.tdt)
+        self.W = torch.from_numpy(np.ascontiguousarray(sp.W)).to("cuda", self.tdt)
+        self.H = torch.from_numpy(np.ascontiguousarray(sp.H)).to("cuda", self.tdt)
+        self.ctx = dna.dna_create_sparse(self.N, self.T, self.R, sp.nnz,
+                                         dna.make_opts(dtype=code, **opts))
+        dna.dna_set_stream(self.ctx)
+        dna.dna_bind_csr(self.ctx, self.rp, self.ci, self.vals, self.W, self.H)
+        if V_dense is not None:
+            self._V64 = np.asarray(V_dense, dtype=np.float64)

@@ -251,6 +251,32 @@ def check_regularised_selection(reg=2.0, seeds=range(8), iters=3):
             W, H, _ = o.dna_step_w(V, W, H, rho=reg, lam=reg)
 
 
+def check_sparse_identities():
+    """On a sparse term-count V (the paper's second workload, Section 4.2), the oracle's
+    quantities are sums over the stored non-zeros only (the note after Algorithm 1): A and
+    B of eq. 7 / 14 recomputed entry by entry over the non-zeros of each column, and each
+    column cost over the non-zeros plus sum_n z = sum_r (sum_n w_nr) h_r."""
+    import workloads
+    sp = workloads.sparse_custom(40, 60, 3, 0.08, seed=4)
+    V = sp.dense().astype(np.float64)
+    W, H = sp.W.astype(np.float64), sp.H.astype(np.float64)
+    hs = o.h_half_step(V, W, H)
+    c = W.sum(axis=0)
+    rows = np.repeat(np.arange(sp.N), np.diff(sp.row_ptr))
+    A = np.zeros_like(H)
+    B = np.zeros_like(H)
+    cost = (c @ hs.X_mu).copy()                   # sum_n z of the MU candidate
+    for k in range(sp.nnz):
+        n, t, v = rows[k], sp.col_idx[k], float(sp.vals[k])
+        z = float(W[n] @ H[:, t])
+        A[:, t] += W[n] * v / z
+        B[:, t] += W[n] ** 2 * v / z ** 2
+        cost[t] -= v * np.log(float(W[n] @ hs.X_mu[:, t]))
+    np.testing.assert_allclose(hs.A, A / c[:, None] - 1.0, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(hs.B, B / c[:, None], rtol=1e-12)
+    np.testing.assert_allclose(hs.d_mu, cost, rtol=1e-12)
+
+
 def check_fixed_point():
     """At an exact factorisation a = 0, so MU and DNA leave W and H unchanged (Section 2.1-2.2)."""
     g = np.random.default_rng(10)
@@ -352,4 +378,4 @@ ALL = [check_kl_definition, check_costs_sum_to_kl, check_a_b_finite_differences,
        check_w_a_b_finite_differences, check_r1_golden, check_r1_random,
        check_step_limits_golden, check_eq9_invariant, check_monotone, check_fixed_point,
        check_transpose_symmetry, check_scale_equivariance, check_normalisation_steps,
-       check_brute_force_tiny, check_regularised_selection]
+       check_brute_force_tiny, check_regularised_selection, check_sparse_identities]

@@ -39,3 +39,18 @@ def test_batched_shapes():
     assert N.min() >= 64 and N.max() <= 2048
     assert T.min() >= 128 and T.max() <= 8192
     assert set(np.unique(R)) <= {8, 16, 32, 64}
+
+
+def test_sparse_generators_shape_density_and_csr():
+    import numpy as np
+    for fn, (N, T, dens) in ((workloads.sparse_tdt2, (36771, 10212, 0.0035)),
+                             (workloads.sparse_newsgroup, (61188, 18774, 0.002))):
+        sp = fn(0)
+        assert (sp.N, sp.T) == (N, T)
+        assert abs(sp.nnz / (N * T) - dens) < 0.1 * dens
+        assert sp.row_ptr[0] == 0 and sp.row_ptr[-1] == sp.nnz
+        assert np.all(np.diff(sp.row_ptr) >= 0)
+        assert sp.col_idx.min() >= 0 and sp.col_idx.max() < T
+        assert np.all(sp.vals >= 1)
+    a, b = workloads.sparse_custom(50, 70, 4, 0.1, seed=2), workloads.sparse_custom(50, 70, 4, 0.1, seed=2)
+    assert np.array_equal(a.col_idx, b.col_idx) and np.array_equal(a.vals, b.vals)

@@ -18,8 +18,16 @@ datasets not available here.  The recipes:
 * ``batched``          512 problems, N ~ logU[64, 2048], T ~ logU[128, 8192],
                        R ~ U{8, 16, 32, 64}, each V ~ Poisson(W0 H0), Gamma(0.5) truth.
 
+* ``sparse_tdt2``      36771 terms x 10212 documents, 0.35 % non-zeros, R=64 (the shape
+                       of the TDT2 term counts of Section 4.2);
+* ``sparse_newsgroup`` 61188 x 18774, 0.2 % non-zeros, R=64 (the Newsgroup counts):
+                       synthetic term-document counts, one dominant topic per document
+                       (70 % of its tokens from the topic's Zipf(1.1) vocabulary, the rest
+                       from a background Zipf(1.1)), log-normal document lengths tuned to
+                       the target density, returned as CSR (rows = terms).
+
 The starting guess is W, H ~ U(0.1, 1) in every case.  ``custom`` builds the same
-kind of problem at any (N, T, R) for tests.
+kind of problem at any (N, T, R) for tests, ``sparse_custom`` the sparse kind.
 """
 from __future__ import annotations
 
@@ -28,7 +36,8 @@ from dataclasses import dataclass, field
 import numpy as np
 
 _CONFIG_IDS = {"plain_small": 1, "plain_large": 2, "precision_large": 3,
-               "diff_form": 4, "batched": 5, "custom": 99}
+               "diff_form": 4, "batched": 5, "sparse_tdt2": 6, "sparse_newsgroup": 7,
+               "sparse_custom": 8, "custom": 99}
 
 
 @dataclass
@@ -150,3 +159,76 @@ def batched(count: int = 512, seed: int = 0, **kw) -> list[Problem]:
         p = custom(n, t, r, seed=seed * 100003 + i, shape=0.5, name="batched")
         out.append(p)
     return out
+
+
+@dataclass
+class SparseProblem:
+    """A term-document count matrix V (N x T) in CSR and a starting guess."""
+    name: str
+    N: int
+    T: int
+    row_ptr: np.ndarray    # int64 N + 1
+    col_idx: np.ndarray    # int32 nnz, ascending within a row
+    vals: np.ndarray       # float32 nnz (counts >= 1)
+    W: np.ndarray          # float32 N x R starting guess
+    H: np.ndarray          # float32 R x T starting guess
+    seed: int
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def nnz(self) -> int:
+        return int(self.vals.size)
+
+    def dense(self) -> np.ndarray:
+        """V as a dense float32 array (small cases only)."""
+        V = np.zeros((self.N, self.T), dtype=np.float32)
+        rows = np.repeat(np.arange(self.N), np.diff(self.row_ptr))
+        V[rows, self.col_idx] = self.vals
+        return V
+
+
+def _zipf_cdf(n: int, exponent: float) -> np.ndarray:
+    p = (np.arange(n, dtype=np.float64) + 1.0) ** -exponent
+    return np.cumsum(p / p.sum())
+
+
+def _draw_counts(g: np.random.Generator, N: int, T: int, R: int, mean_len: float):
+    """Token draws -> (term, doc) count pairs, sorted by term then document."""
+    lens = np.maximum(1, np.round(g.lognormal(np.log(mean_len), 0.8, size=T))).astype(np.int64)
+    doc = np.repeat(np.arange(T, dtype=np.int64), lens)
+    topic = g.integers(0, R, size=T)[doc]
+    cdf = _zipf_cdf(N, 1.1)
+    rank = np.minimum(np.searchsorted(cdf, g.random(doc.size)), N - 1)
+    perms = np.stack([g.permutation(N) for _ in range(R + 1)])     # row R: background
+    from_topic = g.random(doc.size) < 0.7
+    term = np.where(from_topic, perms[topic, rank], perms[R, rank])
+    key, cnt = np.unique(term * T + doc, return_counts=True)
+    return key // T, key % T, cnt
+
+
+def sparse_custom(N: int, T: int, R: int, density: float, seed: int = 0,
+                  name: str = "sparse_custom") -> SparseProblem:
+    """Synthetic term-document counts with about density * N * T non-zeros (module doc)."""
+    target = density * N * T
+    mean_len = 1.3 * target / T
+    for _ in range(2):                   # one correction of the length scale for repeats
+        rows, cols, cnt = _draw_counts(_rng(seed, name, 0), N, T, R, mean_len)
+        mean_len *= target / max(1, rows.size)
+    row_ptr = np.zeros(N + 1, dtype=np.int64)
+    np.add.at(row_ptr, rows + 1, 1)
+    row_ptr = np.cumsum(row_ptr)
+    W, H = _init(_rng(seed, name, 2), N, T, R)
+    meta = {"density": rows.size / (N * T), "nnz": int(rows.size),
+            "mean_count": float(cnt.mean())}
+    return SparseProblem(name, N, T, row_ptr, cols.astype(np.int32), cnt.astype(np.float32),
+                         W, H, seed, meta)
+
+
+def sparse_tdt2(seed: int = 0, R: int = 64) -> SparseProblem:
+    """36771 x 10212 term counts at 0.35 % non-zeros (TDT2's shape, Section 4.2)."""
+    return sparse_custom(36771, 10212, R, 0.0035, seed, name="sparse_tdt2")
+
+
+def sparse_newsgroup(seed: int = 0, R: int = 64) -> SparseProblem:
+    """61188 x 18774 term counts at 0.2 % non-zeros (Newsgroup's shape, Section 4.2)."""
+    return sparse_custom(61188, 18774, R, 0.002, seed, name="sparse_newsgroup")

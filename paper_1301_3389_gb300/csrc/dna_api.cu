@@ -86,6 +86,16 @@ struct dna_ctx {
     void* cval = nullptr;
     void* Yt = nullptr;
     double* c0 = nullptr;
+    // segments of at most sparse::SEG non-zeros per view (0: columns of V, 1: rows), built
+    // at bind, with their partial sums
+    int32_t* seg_col[2] = {nullptr, nullptr};
+    int64_t* seg_k0[2] = {nullptr, nullptr};
+    int64_t* seg_k1[2] = {nullptr, nullptr};
+    int64_t* seg_ptr[2] = {nullptr, nullptr};
+    int64_t nseg[2] = {0, 0};
+    void* Aseg = nullptr;
+    void* Bseg = nullptr;
+    double* dseg = nullptr;
     // profiling: event pairs around phases, launch counts
     unsigned prof_mask = 0;          // phases whose instances get an event pair
     std::vector<cudaEvent_t> ev_pool;
@@ -213,7 +223,9 @@ void free_all(dna_ctx* c) {
     void* ptrs[] = {c->own_V, c->own_W, c->own_H, c->Vt, c->colsum_v, c->rowsum_v, c->c, c->sig,
                     c->fwork, c->gpart, c->vpart, c->Apart, c->Bpart, c->Xmu, c->Xdna, c->dpart, c->dfin_h, c->dfin_w,
                     c->choice_h, c->choice_w, c->kl_dev, c->kl_part, c->status, c->Xk, c->Yk, c->Ytk,
-                    c->Y2tk, c->Xmk, c->Xdk, c->Vp, c->cptr, c->ridx, c->cval, c->Yt, c->c0};
+                    c->Y2tk, c->Xmk, c->Xdk, c->Vp, c->cptr, c->ridx, c->cval, c->Yt, c->c0,
+                    c->seg_col[0], c->seg_col[1], c->seg_k0[0], c->seg_k0[1], c->seg_k1[0],
+                    c->seg_k1[1], c->seg_ptr[0], c->seg_ptr[1], c->Aseg, c->Bseg, c->dseg};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t ev : c->ev_pool) cudaEventDestroy(ev);
@@ -354,6 +366,51 @@ int bind_csr(dna_ctx* c, const int64_t* rptr, const int32_t* cidx, const Tp* val
         }
     for (int64_t t = 0; t < T; ++t)
         for (int64_t k = cp[t]; k < cp[t + 1]; ++k) cs[t] += (double)cv[k];
+    // segment tables: view 0 cuts the columns (CSC), view 1 the rows (CSR)
+    std::vector<int32_t> scol[2];
+    std::vector<int64_t> sk0[2], sk1[2], sptr[2];
+    for (int w = 0; w < 2; ++w) {
+        const std::vector<int64_t>& p = w ? rp : cp;
+        const int64_t O = w ? N : T;
+        sptr[w].assign((size_t)O + 1, 0);
+        for (int64_t o = 0; o < O; ++o) {
+            for (int64_t k = p[o]; k < p[o + 1]; k += dna::SPARSE_SEG) {
+                scol[w].push_back((int32_t)o);
+                sk0[w].push_back(k);
+                sk1[w].push_back(std::min<int64_t>(k + dna::SPARSE_SEG, p[o + 1]));
+            }
+            sptr[w][o + 1] = (int64_t)scol[w].size();
+        }
+    }
+    const int64_t maxseg = std::max<int64_t>(1, std::max(scol[0].size(), scol[1].size()));
+    for (int w = 0; w < 2; ++w) {
+        for (void* q : {(void*)c->seg_col[w], (void*)c->seg_k0[w], (void*)c->seg_k1[w],
+                        (void*)c->seg_ptr[w]})
+            if (q) cudaFree(q);
+        const int64_t n = std::max<int64_t>(1, (int64_t)scol[w].size());
+        const int64_t O = w ? N : T;
+        int e = dmalloc(&c->seg_col[w], sizeof(int32_t) * n);
+        e |= dmalloc(&c->seg_k0[w], sizeof(int64_t) * n);
+        e |= dmalloc(&c->seg_k1[w], sizeof(int64_t) * n);
+        e |= dmalloc(&c->seg_ptr[w], sizeof(int64_t) * (O + 1));
+        if (e) return DNA_ERR_ALLOC;
+        c->nseg[w] = (int64_t)scol[w].size();
+    }
+    for (void* q : {c->Aseg, c->Bseg, (void*)c->dseg})
+        if (q) cudaFree(q);
+    if (dmalloc(&c->Aseg, sizeof(Tp) * (size_t)(maxseg * c->R)) ||
+        dmalloc(&c->Bseg, sizeof(Tp) * (size_t)(maxseg * c->R)) ||
+        dmalloc(&c->dseg, sizeof(double) * (size_t)(2 * maxseg)))
+        return DNA_ERR_ALLOC;
+    for (int w = 0; w < 2; ++w) {
+        const int64_t O = w ? N : T;
+        if ((c->nseg[w] &&
+             (cudaMemcpyAsync(c->seg_col[w], scol[w].data(), sizeof(int32_t) * c->nseg[w], cudaMemcpyHostToDevice, st) != cudaSuccess ||
+              cudaMemcpyAsync(c->seg_k0[w], sk0[w].data(), sizeof(int64_t) * c->nseg[w], cudaMemcpyHostToDevice, st) != cudaSuccess ||
+              cudaMemcpyAsync(c->seg_k1[w], sk1[w].data(), sizeof(int64_t) * c->nseg[w], cudaMemcpyHostToDevice, st) != cudaSuccess)) ||
+            cudaMemcpyAsync(c->seg_ptr[w], sptr[w].data(), sizeof(int64_t) * (O + 1), cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return DNA_ERR_CUDA;
+    }
     if (cudaMemcpyAsync(c->cptr, cp.data(), sizeof(int64_t) * (T + 1), cudaMemcpyHostToDevice, st) != cudaSuccess ||
         (nnz && cudaMemcpyAsync(c->ridx, ri.data(), sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, st) != cudaSuccess) ||
         (nnz && cudaMemcpyAsync(c->cval, cv.data(), sizeof(Tp) * nnz, cudaMemcpyHostToDevice, st) != cudaSuccess) ||
@@ -609,6 +666,10 @@ int finish_step(dna_ctx* c, int w, bool next) {
     });
 }
 
+dna::SparseSegs segs(const dna_ctx* c, int w) {
+    return dna::SparseSegs{c->seg_col[w], c->seg_k0[w], c->seg_k1[w], c->seg_ptr[w], c->nseg[w]};
+}
+
 // One half-step of the sparse-V form: the same steps as half_step with the two O(NRT)
 // passes replaced by passes over the non-zeros (sparse_kernels.cuh); candidates, selection
 // and normalisation are the dense glue kernels (they touch only W, H and O-vectors).
@@ -637,11 +698,13 @@ int sparse_half_step(dna_ctx* c, int w, bool mu_only, bool prepared, bool next) 
         if (e) return e;
         Yg = static_cast<const Tp*>(c->Yt);
     }
-    const int64_t* ptr = w ? c->rptr : c->cptr;
+    const dna::SparseSegs sg = segs(c, w);
     const int32_t* idx = w ? c->cidx : c->ridx;
     const Tp* val = static_cast<const Tp*>(w ? c->rval : c->cval);
-    e = phase(c, DNA_PHASE_PASS1, 1, [&] {
-        return S::sp_pass1(v, ptr, idx, val, Yg, A, B, !mu_only, c->status, st);
+    Tp* Aseg = static_cast<Tp*>(c->Aseg);
+    Tp* Bseg = static_cast<Tp*>(c->Bseg);
+    e = phase(c, DNA_PHASE_PASS1, 2, [&] {
+        return S::sp_pass1(v, sg, idx, val, Yg, Aseg, Bseg, A, B, !mu_only, c->status, st);
     });
     if (e) return e;
     if (mu_only) {
@@ -653,8 +716,8 @@ int sparse_half_step(dna_ctx* c, int w, bool mu_only, bool prepared, bool next) 
                              0, 0, 0, st);
     });
     if (e) return e;
-    e = phase(c, DNA_PHASE_PASS2, 1, [&] {
-        return S::sp_pass2(v, ptr, idx, val, Yg, Xmu, Xdna, c->c0, c->dpart, c->status, st);
+    e = phase(c, DNA_PHASE_PASS2, 2, [&] {
+        return S::sp_pass2(v, sg, idx, val, Yg, Xmu, Xdna, c->c0, c->dseg, c->dpart, c->status, st);
     });
     if (e) return e;
     e = phase(c, DNA_PHASE_SELECT, 1, [&] {
@@ -673,12 +736,13 @@ int sparse_kl(dna_ctx* c) {
     using S = dna::Simt<Tp>;
     const View v = make_view(c, false);
     cudaStream_t st = c->stream;
-    return phase(c, DNA_PHASE_KL, 4, [&] {
+    return phase(c, DNA_PHASE_KL, 5, [&] {
         int e = S::scale_ops(v, nullptr, false, nullptr, nullptr, nullptr, nullptr, 0, 0, 0, 0,
                              c->gpart, st);
         if (!e) e = S::raw_sums(c->gpart, S::glue_parts(v.S), c->R, c->c0, st);
-        if (!e) e = S::sp_kl(v, c->cptr, c->ridx, static_cast<const Tp*>(c->cval),
-                             static_cast<const Tp*>(c->W), c->c0, c->dpart, c->status, st);
+        if (!e) e = S::sp_kl(v, segs(c, 0), c->ridx, static_cast<const Tp*>(c->cval),
+                             static_cast<const Tp*>(c->W), c->c0, c->dseg, c->dpart, c->status,
+                             st);
         return e ? e : dna::reduce_sum(c->dpart, c->T, c->kl_dev, c->kl_part, st);
     });
 }

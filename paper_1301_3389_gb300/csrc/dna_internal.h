@@ -41,6 +41,18 @@ struct View {
     const double* vsum; // sum_s v(s, o), length O (the eq. 10 target)
 };
 
+// Segment table of one view of a sparse V: segment g covers the non-zeros [k0[g], k1[g])
+// of view column col[g]; the segments of column o are [sptr[o], sptr[o + 1]).
+constexpr int SPARSE_SEG = 128;   // non-zeros per segment at most
+
+struct SparseSegs {
+    const int32_t* col;
+    const int64_t* k0;
+    const int64_t* k1;
+    const int64_t* sptr;
+    int64_t n;
+};
+
 // Launchers, one instantiation per element type (float, double).  Each returns a
 // DNA_* status (launch errors only; device-side errors go to *status).
 template <typename Tp> struct Simt {
@@ -122,16 +134,18 @@ template <typename Tp> struct Simt {
     // no replacement of a zero sum: the column sums c0 of Y that sum_s z needs)
     static int raw_sums(const double* part, int64_t nparts, int64_t R, double* out,
                         cudaStream_t st);
-    // Sparse-V form (sparse_kernels.cuh): the view's non-zeros of column o are
-    // k in [ptr[o], ptr[o + 1]) at s = idx[k] with value val[k]; Yg is Y as S x R row-major.
-    // R <= 128.
-    static int sp_pass1(const View& v, const int64_t* ptr, const int32_t* idx, const Tp* val,
-                        const Tp* Yg, Tp* A, Tp* B, bool with_b, int* status, cudaStream_t st);
-    static int sp_pass2(const View& v, const int64_t* ptr, const int32_t* idx, const Tp* val,
+    // Sparse-V form (sparse_kernels.cuh): the view's non-zero k is at s = idx[k] with value
+    // val[k], grouped in segments `sg`; Yg is Y as S x R row-major; R <= 128.  Each call is a
+    // segment kernel (partials Aseg, Bseg [nseg][R] or dseg) and a per-column reduction.
+    static int sp_pass1(const View& v, const SparseSegs& sg, const int32_t* idx, const Tp* val,
+                        const Tp* Yg, Tp* Aseg, Tp* Bseg, Tp* A, Tp* B, bool with_b,
+                        int* status, cudaStream_t st);
+    static int sp_pass2(const View& v, const SparseSegs& sg, const int32_t* idx, const Tp* val,
                         const Tp* Yg, const Tp* Xmu, const Tp* Xdna, const double* c0,
-                        double* dpart, int* status, cudaStream_t st);
-    static int sp_kl(const View& v, const int64_t* ptr, const int32_t* idx, const Tp* val,
-                     const Tp* Yg, const double* c0, double* part, int* status, cudaStream_t st);
+                        double* dseg, double* dpart, int* status, cudaStream_t st);
+    static int sp_kl(const View& v, const SparseSegs& sg, const int32_t* idx, const Tp* val,
+                     const Tp* Yg, const double* c0, double* dseg, double* part, int* status,
+                     cudaStream_t st);
     // out (cols x rows) = in^t (rows x cols), both row-major
     static int transpose(const Tp* in, int64_t rows, int64_t cols, Tp* out, cudaStream_t st);
     // one-time: row and column sums of V (float64) and the transposed copy

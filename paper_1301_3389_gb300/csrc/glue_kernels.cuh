@@ -107,7 +107,8 @@ __global__ void __launch_bounds__(1024) k_cand_fused(View v, const double* __res
             const Tp x = xs[r * (TO + 1) + tx];
             const Tp a = ra[u] * ics[r] - Tp(1);   // eq. 7
             const Tp b = rb[u] * ics[r];           // eq. 14
-            const Tp xmu = x + a * x;              // eq. 11
+            // eq. 11 as x (W^t q)_r / c_r: no cancellation where 1 + a is small
+            const Tp xmu = x * (ra[u] * ics[r]);
             Tp xd;
             if (a < Tp(0)) {                       // eq. 15, gain floored at eps
                 const Tp xb = x * b;
@@ -227,7 +228,7 @@ __global__ void __launch_bounds__(512) k_cand_reg(View v, const double* __restri
         const Tp a = ra[i] * ic - Tp(1);   // eq. 7
         const Tp b = rb[i] * ic;           // eq. 14
         const Tp xr = x[i];
-        xm[i] = xr + a * xr;               // eq. 11
+        xm[i] = xr * (ra[i] * ic);         // eq. 11 as x (W^t q)_r / c_r (no cancellation)
         if (a < Tp(0)) {                   // eq. 15, gain floored at eps
             const Tp xb = xr * b;
             const Tp g = simt::dev_div(xb, xb - a);

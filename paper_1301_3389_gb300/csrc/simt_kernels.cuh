@@ -365,7 +365,8 @@ __device__ __forceinline__ void candidates_tile(const View& v, const double* __r
             const Tp a = ra * ic - Tp(1);         // eq. 7
             const Tp b = rb * ic;                 // eq. 14
             const Tp x = X[r * v.xr + o * v.xo];
-            const Tp xmu = x + a * x;             // eq. 11 (step 6)
+            // eq. 11 (step 6) as x (W^t q)_r / c_r: no cancellation where 1 + a is small
+            const Tp xmu = x * (ra * ic);
             Tp xd;
             if (a < Tp(0)) {                      // eq. 15 with the eps floor on the gain
                 const Tp xb = x * b;

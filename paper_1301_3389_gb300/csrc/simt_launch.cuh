@@ -453,58 +453,76 @@ int Simt<Tp>::raw_sums(const double* part, int64_t nparts, int64_t R, double* ou
 }
 
 namespace simt {
+inline unsigned sp_grid(int64_t n) { return (unsigned)((n + sparse::WARPS - 1) / sparse::WARPS); }
+
 template <typename Tp, int RPL>
-int sp_pass1_r(const View& v, const int64_t* ptr, const int32_t* idx, const Tp* val,
-               const Tp* Yg, Tp* A, Tp* B, bool with_b, int* status, cudaStream_t st) {
-    const unsigned grid = (unsigned)((v.O + sparse::WARPS - 1) / sparse::WARPS);
-    sparse::k_sp_pass1<Tp, RPL><<<grid, sparse::WARPS * 32, 0, st>>>(v, ptr, idx, val, Yg, A, B,
-                                                                      with_b, status);
+int sp_pass1_r(const View& v, const SparseSegs& sg, const int32_t* idx, const Tp* val,
+               const Tp* Yg, Tp* Aseg, Tp* Bseg, Tp* A, Tp* B, bool with_b, int* status,
+               cudaStream_t st) {
+    if (sg.n > 0) {
+        sparse::k_sp_pass1<Tp, RPL><<<sp_grid(sg.n), sparse::WARPS * 32, 0, st>>>(
+            v, sg, idx, val, Yg, Aseg, Bseg, with_b, status);
+        if (launch_status()) return DNA_ERR_CUDA;
+    }
+    sparse::k_sp_reduce_ab<Tp, RPL><<<sp_grid(v.O), sparse::WARPS * 32, 0, st>>>(
+        v.O, v.R, sg.sptr, Aseg, Bseg, A, B, with_b);
     return launch_status();
 }
 template <typename Tp, int RPL>
-int sp_pass2_r(const View& v, const int64_t* ptr, const int32_t* idx, const Tp* val,
-               const Tp* Yg, const Tp* Xmu, const Tp* Xdna, const double* c0, double* dpart,
-               int* status, cudaStream_t st) {
-    const unsigned grid = (unsigned)((v.O + sparse::WARPS - 1) / sparse::WARPS);
-    sparse::k_sp_pass2<Tp, RPL><<<grid, sparse::WARPS * 32, 0, st>>>(v, ptr, idx, val, Yg, Xmu,
-                                                                      Xdna, c0, dpart, status);
+int sp_pass2_r(const View& v, const SparseSegs& sg, const int32_t* idx, const Tp* val,
+               const Tp* Yg, const Tp* Xmu, const Tp* Xdna, const double* c0, double* dseg,
+               double* dpart, int* status, cudaStream_t st) {
+    if (sg.n > 0) {
+        sparse::k_sp_pass2<Tp, RPL><<<sp_grid(sg.n), sparse::WARPS * 32, 0, st>>>(
+            v, sg, idx, val, Yg, Xmu, Xdna, dseg);
+        if (launch_status()) return DNA_ERR_CUDA;
+    }
+    sparse::k_sp_reduce_cost<Tp, RPL><<<sp_grid(v.O), sparse::WARPS * 32, 0, st>>>(
+        v.O, v.R, sg.sptr, dseg, Xmu, Xdna, c0, dpart, status);
     return launch_status();
 }
 template <typename Tp, int RPL>
-int sp_kl_r(const View& v, const int64_t* ptr, const int32_t* idx, const Tp* val, const Tp* Yg,
-            const double* c0, double* part, int* status, cudaStream_t st) {
-    const unsigned grid = (unsigned)((v.O + sparse::WARPS - 1) / sparse::WARPS);
-    sparse::k_sp_kl<Tp, RPL><<<grid, sparse::WARPS * 32, 0, st>>>(v, ptr, idx, val, Yg, c0, part,
-                                                                   status);
+int sp_kl_r(const View& v, const SparseSegs& sg, const int32_t* idx, const Tp* val,
+            const Tp* Yg, const double* c0, double* dseg, double* part, int* status,
+            cudaStream_t st) {
+    if (sg.n > 0) {
+        sparse::k_sp_kl<Tp, RPL><<<sp_grid(sg.n), sparse::WARPS * 32, 0, st>>>(v, sg, idx, val,
+                                                                               Yg, dseg);
+        if (launch_status()) return DNA_ERR_CUDA;
+    }
+    sparse::k_sp_reduce_kl<Tp, RPL><<<sp_grid(v.O), sparse::WARPS * 32, 0, st>>>(
+        v, sg.sptr, dseg, c0, part, status);
     return launch_status();
 }
 }  // namespace simt
 
 template <typename Tp>
-int Simt<Tp>::sp_pass1(const View& v, const int64_t* ptr, const int32_t* idx, const Tp* val,
-                       const Tp* Yg, Tp* A, Tp* B, bool with_b, int* status, cudaStream_t st) {
-    if (v.R <= 32) return simt::sp_pass1_r<Tp, 1>(v, ptr, idx, val, Yg, A, B, with_b, status, st);
-    if (v.R <= 64) return simt::sp_pass1_r<Tp, 2>(v, ptr, idx, val, Yg, A, B, with_b, status, st);
-    if (v.R <= 128) return simt::sp_pass1_r<Tp, 4>(v, ptr, idx, val, Yg, A, B, with_b, status, st);
+int Simt<Tp>::sp_pass1(const View& v, const SparseSegs& sg, const int32_t* idx, const Tp* val,
+                       const Tp* Yg, Tp* Aseg, Tp* Bseg, Tp* A, Tp* B, bool with_b, int* status,
+                       cudaStream_t st) {
+    if (v.R <= 32) return simt::sp_pass1_r<Tp, 1>(v, sg, idx, val, Yg, Aseg, Bseg, A, B, with_b, status, st);
+    if (v.R <= 64) return simt::sp_pass1_r<Tp, 2>(v, sg, idx, val, Yg, Aseg, Bseg, A, B, with_b, status, st);
+    if (v.R <= 128) return simt::sp_pass1_r<Tp, 4>(v, sg, idx, val, Yg, Aseg, Bseg, A, B, with_b, status, st);
     return DNA_ERR_UNSUPPORTED;
 }
 
 template <typename Tp>
-int Simt<Tp>::sp_pass2(const View& v, const int64_t* ptr, const int32_t* idx, const Tp* val,
+int Simt<Tp>::sp_pass2(const View& v, const SparseSegs& sg, const int32_t* idx, const Tp* val,
                        const Tp* Yg, const Tp* Xmu, const Tp* Xdna, const double* c0,
-                       double* dpart, int* status, cudaStream_t st) {
-    if (v.R <= 32) return simt::sp_pass2_r<Tp, 1>(v, ptr, idx, val, Yg, Xmu, Xdna, c0, dpart, status, st);
-    if (v.R <= 64) return simt::sp_pass2_r<Tp, 2>(v, ptr, idx, val, Yg, Xmu, Xdna, c0, dpart, status, st);
-    if (v.R <= 128) return simt::sp_pass2_r<Tp, 4>(v, ptr, idx, val, Yg, Xmu, Xdna, c0, dpart, status, st);
+                       double* dseg, double* dpart, int* status, cudaStream_t st) {
+    if (v.R <= 32) return simt::sp_pass2_r<Tp, 1>(v, sg, idx, val, Yg, Xmu, Xdna, c0, dseg, dpart, status, st);
+    if (v.R <= 64) return simt::sp_pass2_r<Tp, 2>(v, sg, idx, val, Yg, Xmu, Xdna, c0, dseg, dpart, status, st);
+    if (v.R <= 128) return simt::sp_pass2_r<Tp, 4>(v, sg, idx, val, Yg, Xmu, Xdna, c0, dseg, dpart, status, st);
     return DNA_ERR_UNSUPPORTED;
 }
 
 template <typename Tp>
-int Simt<Tp>::sp_kl(const View& v, const int64_t* ptr, const int32_t* idx, const Tp* val,
-                    const Tp* Yg, const double* c0, double* part, int* status, cudaStream_t st) {
-    if (v.R <= 32) return simt::sp_kl_r<Tp, 1>(v, ptr, idx, val, Yg, c0, part, status, st);
-    if (v.R <= 64) return simt::sp_kl_r<Tp, 2>(v, ptr, idx, val, Yg, c0, part, status, st);
-    if (v.R <= 128) return simt::sp_kl_r<Tp, 4>(v, ptr, idx, val, Yg, c0, part, status, st);
+int Simt<Tp>::sp_kl(const View& v, const SparseSegs& sg, const int32_t* idx, const Tp* val,
+                    const Tp* Yg, const double* c0, double* dseg, double* part, int* status,
+                    cudaStream_t st) {
+    if (v.R <= 32) return simt::sp_kl_r<Tp, 1>(v, sg, idx, val, Yg, c0, dseg, part, status, st);
+    if (v.R <= 64) return simt::sp_kl_r<Tp, 2>(v, sg, idx, val, Yg, c0, dseg, part, status, st);
+    if (v.R <= 128) return simt::sp_kl_r<Tp, 4>(v, sg, idx, val, Yg, c0, dseg, part, status, st);
     return DNA_ERR_UNSUPPORTED;
 }
 

@@ -12,8 +12,11 @@
 // as an S x R row-major array (W for the H-step, a transposed copy of H for the W-step),
 // so the R values of y(s, .) are one contiguous, coalesced row.
 //
-// One warp per view column o; lane l holds r = l + 32 j (j < RPL).  Dot products over r are
-// reduced with a fixed xor butterfly, so every result is bit-reproducible.
+// Work is split into segments of at most SEG non-zeros of one view column (term rows of
+// count data follow a Zipf law: one row can hold thousands of non-zeros), one warp per
+// segment; lane l holds r = l + 32 j (j < RPL).  Each segment writes its partial sums
+// [seg][R], and a warp per view column then adds its segments in order.  Dot products over
+// r are reduced with a fixed xor butterfly, so every result is bit-reproducible.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -25,8 +28,9 @@
 namespace dna {
 namespace sparse {
 
-constexpr int WARPS = 8;   // warps (view columns) per CTA
-constexpr int U = 4;       // non-zeros whose loads are issued together
+constexpr int WARPS = 8;   // warps (segments or view columns) per CTA
+constexpr int U = 8;       // non-zeros whose loads are issued together
+constexpr int SEG = SPARSE_SEG;
 
 template <typename Tp>
 __device__ __forceinline__ Tp warp_sum(Tp x) {
@@ -35,19 +39,39 @@ __device__ __forceinline__ Tp warp_sum(Tp x) {
     return x;
 }
 
-// Pass 1 (Algorithm 1 steps 2-5 and 10 on the non-zeros): raw sums
-// A(r, o) = sum_k y(s_k, r) q_k and B(r, o) = sum_k y(s_k, r)^2 qbar_k, written [R][O]
-// (the layout of split 0 of the dense pass), with q = v / z, qbar = q / z.  Sets
-// STATUS_NONFINITE when z <= 0 (or is not a number) at a positive v.
+// Loads of U non-zeros of a segment: values, and the rows y(s, .) they gather.
+template <typename Tp, int RPL>
+__device__ __forceinline__ void load_batch(int64_t k, int64_t k1, int lane, int64_t R,
+                                           const int32_t* __restrict__ idx,
+                                           const Tp* __restrict__ val, const Tp* __restrict__ Yg,
+                                           Tp (&vv)[U], Tp (&y)[U][RPL]) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const bool in = k + u < k1;
+        const int64_t s = in ? idx[k + u] : 0;
+        vv[u] = in ? val[k + u] : Tp(0);
+#pragma unroll
+        for (int j = 0; j < RPL; ++j) {
+            const int64_t r = lane + 32 * j;
+            y[u][j] = (in && r < R) ? Yg[s * R + r] : Tp(0);
+        }
+    }
+}
+
+using Segs = SparseSegs;
+
+// Pass 1 (Algorithm 1 steps 2-5 and 10 on the non-zeros of one segment): partial raw sums
+// Aseg[g][r] = sum_k y(s_k, r) q_k and Bseg[g][r] = sum_k y(s_k, r)^2 qbar_k with q = v / z,
+// qbar = q / z.  Sets STATUS_NONFINITE when z <= 0 (or is not a number) at a positive v.
 template <typename Tp, int RPL>
 __global__ void __launch_bounds__(WARPS * 32)
-    k_sp_pass1(View v, const int64_t* __restrict__ ptr, const int32_t* __restrict__ idx,
-               const Tp* __restrict__ val, const Tp* __restrict__ Yg, Tp* __restrict__ A,
-               Tp* __restrict__ B, bool with_b, int* __restrict__ status) {
+    k_sp_pass1(View v, Segs sg, const int32_t* __restrict__ idx, const Tp* __restrict__ val,
+               const Tp* __restrict__ Yg, Tp* __restrict__ Aseg, Tp* __restrict__ Bseg,
+               bool with_b, int* __restrict__ status) {
     const int lane = threadIdx.x & 31;
-    const int64_t o = (int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5);
-    if (o >= v.O) return;
-    const int64_t R = v.R;
+    const int64_t g = (int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5);
+    if (g >= sg.n) return;
+    const int64_t R = v.R, o = sg.col[g];
     const Tp* __restrict__ X = static_cast<const Tp*>(v.X);
     Tp x[RPL], a[RPL], b[RPL];
 #pragma unroll
@@ -58,20 +82,10 @@ __global__ void __launch_bounds__(WARPS * 32)
         b[j] = Tp(0);
     }
     bool bad = false;
-    const int64_t k0 = ptr[o], k1 = ptr[o + 1];
+    const int64_t k0 = sg.k0[g], k1 = sg.k1[g];
     for (int64_t k = k0; k < k1; k += U) {
         Tp vv[U], y[U][RPL], z[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const bool in = k + u < k1;
-            const int64_t s = in ? idx[k + u] : 0;
-            vv[u] = in ? val[k + u] : Tp(0);
-#pragma unroll
-            for (int j = 0; j < RPL; ++j) {
-                const int64_t r = lane + 32 * j;
-                y[u][j] = (in && r < R) ? Yg[s * R + r] : Tp(0);
-            }
-        }
+        load_batch<Tp, RPL>(k, k1, lane, R, idx, val, Yg, vv, y);
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             Tp p = Tp(0);
@@ -96,56 +110,71 @@ __global__ void __launch_bounds__(WARPS * 32)
     for (int j = 0; j < RPL; ++j) {
         const int64_t r = lane + 32 * j;
         if (r < R) {
-            A[r * v.O + o] = a[j];
-            if (with_b) B[r * v.O + o] = b[j];
+            Aseg[g * R + r] = a[j];
+            if (with_b) Bseg[g * R + r] = b[j];
         }
     }
     if (bad && status) atomicOr(status, STATUS_NONFINITE);
 }
 
-// Pass 2 (steps 7-9, 12-14 on the non-zeros): per view column o, the cost of each candidate
-// sum_{v>0} (-v log z) + sum_s z with sum_s z = sum_r c0_r x(r, o), into
-// dpart[0 * O + o] (MU) and dpart[1 * O + o] (Newton) in float64.  The -v log z terms of
-// non-zero k are accumulated by lane (k - k0) mod U, then the lanes' float64 sums are
-// added by the fixed butterfly.
+// A(r, o) = sum over the segments of column o of Aseg (in segment order), written [R][O]
+// (split 0 of the dense layout); the same for B.  A warp per view column.
 template <typename Tp, int RPL>
 __global__ void __launch_bounds__(WARPS * 32)
-    k_sp_pass2(View v, const int64_t* __restrict__ ptr, const int32_t* __restrict__ idx,
-               const Tp* __restrict__ val, const Tp* __restrict__ Yg,
-               const Tp* __restrict__ Xmu, const Tp* __restrict__ Xdna,
-               const double* __restrict__ c0, double* __restrict__ dpart,
-               int* __restrict__ status) {
+    k_sp_reduce_ab(int64_t O, int64_t R, const int64_t* __restrict__ sptr,
+                   const Tp* __restrict__ Aseg, const Tp* __restrict__ Bseg, Tp* __restrict__ A,
+                   Tp* __restrict__ B, bool with_b) {
     const int lane = threadIdx.x & 31;
     const int64_t o = (int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5);
-    if (o >= v.O) return;
-    const int64_t R = v.R, O = v.O;
+    if (o >= O) return;
+    Tp a[RPL], b[RPL];
+#pragma unroll
+    for (int j = 0; j < RPL; ++j) { a[j] = Tp(0); b[j] = Tp(0); }
+    for (int64_t g = sptr[o]; g < sptr[o + 1]; ++g) {
+#pragma unroll
+        for (int j = 0; j < RPL; ++j) {
+            const int64_t r = lane + 32 * j;
+            if (r < R) {
+                a[j] += Aseg[g * R + r];
+                if (with_b) b[j] += Bseg[g * R + r];
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < RPL; ++j) {
+        const int64_t r = lane + 32 * j;
+        if (r < R) {
+            A[r * O + o] = a[j];
+            if (with_b) B[r * O + o] = b[j];
+        }
+    }
+}
+
+// Pass 2 (steps 7-9, 12-14 on the non-zeros of one segment): the partial sums
+// dseg[2 g] = sum_{v>0} -v log z_MU and dseg[2 g + 1] = sum_{v>0} -v log z_DNA (float64).
+// The terms of non-zero k are accumulated by lane (k - k0) mod U, then the lanes' float64
+// sums are added by the fixed butterfly.
+template <typename Tp, int RPL>
+__global__ void __launch_bounds__(WARPS * 32)
+    k_sp_pass2(View v, Segs sg, const int32_t* __restrict__ idx, const Tp* __restrict__ val,
+               const Tp* __restrict__ Yg, const Tp* __restrict__ Xmu,
+               const Tp* __restrict__ Xdna, double* __restrict__ dseg) {
+    const int lane = threadIdx.x & 31;
+    const int64_t g = (int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5);
+    if (g >= sg.n) return;
+    const int64_t R = v.R, O = v.O, o = sg.col[g];
     Tp xm[RPL], xd[RPL];
-    double zm_sum = 0.0, zd_sum = 0.0;
 #pragma unroll
     for (int j = 0; j < RPL; ++j) {
         const int64_t r = lane + 32 * j;
         xm[j] = r < R ? Xmu[r * O + o] : Tp(0);
         xd[j] = r < R ? Xdna[r * O + o] : Tp(0);
-        if (r < R) {
-            zm_sum += c0[r] * (double)xm[j];
-            zd_sum += c0[r] * (double)xd[j];
-        }
     }
-    double lm = 0.0, ld = 0.0;   // this lane's -v log z sums
-    const int64_t k0 = ptr[o], k1 = ptr[o + 1];
+    double lm = 0.0, ld = 0.0;
+    const int64_t k0 = sg.k0[g], k1 = sg.k1[g];
     for (int64_t k = k0; k < k1; k += U) {
         Tp vv[U], y[U][RPL];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const bool in = k + u < k1;
-            const int64_t s = in ? idx[k + u] : 0;
-            vv[u] = in ? val[k + u] : Tp(0);
-#pragma unroll
-            for (int j = 0; j < RPL; ++j) {
-                const int64_t r = lane + 32 * j;
-                y[u][j] = (in && r < R) ? Yg[s * R + r] : Tp(0);
-            }
-        }
+        load_batch<Tp, RPL>(k, k1, lane, R, idx, val, Yg, vv, y);
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             Tp pm = Tp(0), pd = Tp(0);
@@ -164,51 +193,69 @@ __global__ void __launch_bounds__(WARPS * 32)
     }
     lm = warp_sum(lm);
     ld = warp_sum(ld);
-    zm_sum = warp_sum(zm_sum);
-    zd_sum = warp_sum(zd_sum);
     if (lane == 0) {
-        const double dm = lm + zm_sum, dd = ld + zd_sum;
+        dseg[2 * g] = lm;
+        dseg[2 * g + 1] = ld;
+    }
+}
+
+// Per view column o: the segments' partial costs in order, plus sum_s z = sum_r c0_r x(r, o)
+// of each candidate, into dpart[o] (MU) and dpart[O + o] (Newton).
+template <typename Tp, int RPL>
+__global__ void __launch_bounds__(WARPS * 32)
+    k_sp_reduce_cost(int64_t O, int64_t R, const int64_t* __restrict__ sptr,
+                     const double* __restrict__ dseg, const Tp* __restrict__ Xmu,
+                     const Tp* __restrict__ Xdna, const double* __restrict__ c0,
+                     double* __restrict__ dpart, int* __restrict__ status) {
+    const int lane = threadIdx.x & 31;
+    const int64_t o = (int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5);
+    if (o >= O) return;
+    double zm = 0.0, zd = 0.0;
+#pragma unroll
+    for (int j = 0; j < RPL; ++j) {
+        const int64_t r = lane + 32 * j;
+        if (r < R) {
+            zm += c0[r] * (double)Xmu[r * O + o];
+            zd += c0[r] * (double)Xdna[r * O + o];
+        }
+    }
+    zm = warp_sum(zm);
+    zd = warp_sum(zd);
+    if (lane == 0) {
+        double lm = 0.0, ld = 0.0;
+        for (int64_t g = sptr[o]; g < sptr[o + 1]; ++g) {
+            lm += dseg[2 * g];
+            ld += dseg[2 * g + 1];
+        }
+        const double dm = lm + zm, dd = ld + zd;
         dpart[o] = dm;
         dpart[O + o] = dd;
         if (!isfinite(dm) || !isfinite(dd)) atomicOr(status, STATUS_NONFINITE);
     }
 }
 
-// d_KL (eq. 1) per view column o of the H view: sum over the non-zeros of
-// v log(v / z) - v, plus sum_n z_nt = sum_r c0_r h(r, t), into part[o] (float64).
+// d_KL (eq. 1) of the H view, per segment: sum over its non-zeros of v log(v / z) - v into
+// dseg[g] (float64).
 template <typename Tp, int RPL>
 __global__ void __launch_bounds__(WARPS * 32)
-    k_sp_kl(View v, const int64_t* __restrict__ ptr, const int32_t* __restrict__ idx,
-            const Tp* __restrict__ val, const Tp* __restrict__ Yg, const double* __restrict__ c0,
-            double* __restrict__ part, int* __restrict__ status) {
+    k_sp_kl(View v, Segs sg, const int32_t* __restrict__ idx, const Tp* __restrict__ val,
+            const Tp* __restrict__ Yg, double* __restrict__ dseg) {
     const int lane = threadIdx.x & 31;
-    const int64_t o = (int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5);
-    if (o >= v.O) return;
-    const int64_t R = v.R;
+    const int64_t g = (int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5);
+    if (g >= sg.n) return;
+    const int64_t R = v.R, o = sg.col[g];
     const Tp* __restrict__ X = static_cast<const Tp*>(v.X);
     Tp x[RPL];
-    double zsum = 0.0;
 #pragma unroll
     for (int j = 0; j < RPL; ++j) {
         const int64_t r = lane + 32 * j;
         x[j] = r < R ? X[r * v.xr + o * v.xo] : Tp(0);
-        if (r < R) zsum += c0[r] * (double)x[j];
     }
     double acc = 0.0;
-    const int64_t k0 = ptr[o], k1 = ptr[o + 1];
+    const int64_t k0 = sg.k0[g], k1 = sg.k1[g];
     for (int64_t k = k0; k < k1; k += U) {
         Tp vv[U], y[U][RPL];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const bool in = k + u < k1;
-            const int64_t s = in ? idx[k + u] : 0;
-            vv[u] = in ? val[k + u] : Tp(0);
-#pragma unroll
-            for (int j = 0; j < RPL; ++j) {
-                const int64_t r = lane + 32 * j;
-                y[u][j] = (in && r < R) ? Yg[s * R + r] : Tp(0);
-            }
-        }
+        load_batch<Tp, RPL>(k, k1, lane, R, idx, val, Yg, vv, y);
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             Tp p = Tp(0);
@@ -220,9 +267,31 @@ __global__ void __launch_bounds__(WARPS * 32)
         }
     }
     acc = warp_sum(acc);
-    zsum = warp_sum(zsum);
+    if (lane == 0) dseg[g] = acc;
+}
+
+// Per column t of the H view: its segments' d_KL terms plus sum_n z_nt = sum_r c0_r h(r, t)
+// into part[t].
+template <typename Tp, int RPL>
+__global__ void __launch_bounds__(WARPS * 32)
+    k_sp_reduce_kl(View v, const int64_t* __restrict__ sptr, const double* __restrict__ dseg,
+                   const double* __restrict__ c0, double* __restrict__ part,
+                   int* __restrict__ status) {
+    const int lane = threadIdx.x & 31;
+    const int64_t o = (int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5);
+    if (o >= v.O) return;
+    const Tp* __restrict__ X = static_cast<const Tp*>(v.X);
+    double zs = 0.0;
+#pragma unroll
+    for (int j = 0; j < RPL; ++j) {
+        const int64_t r = lane + 32 * j;
+        if (r < v.R) zs += c0[r] * (double)X[r * v.xr + o * v.xo];
+    }
+    zs = warp_sum(zs);
     if (lane == 0) {
-        const double d = acc + zsum;
+        double acc = 0.0;
+        for (int64_t g = sptr[o]; g < sptr[o + 1]; ++g) acc += dseg[g];
+        const double d = acc + zs;
         part[o] = d;
         if (!isfinite(d)) atomicOr(status, STATUS_NONFINITE);
     }

@@ -647,6 +647,15 @@ def measure_sparse(dna, torch, sp, steps, warmup, peaks, dtype="f32"):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
         ph = dna.dna_phase_times(ctx)
+        # phase shares from a separate, untimed pass with every phase bracketed
+        dna.dna_profile(ctx, True)
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        dna.dna_iterate(ctx, 10)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        pms = f0.elapsed_time(f1)
+        pph = dna.dna_phase_times(ctx)
         dna.dna_profile(ctx, False)
         kl1 = dna.dna_kl(ctx)
     finally:
@@ -671,7 +680,9 @@ def measure_sparse(dna, torch, sp, steps, warmup, peaks, dtype="f32"):
                      "launch_ms": per_launch * 1e3,
                      "iteration_hbm_frac": it_bytes / (ms / steps / 1e3) / 1e9 / hbm,
                      "note": "the rows of the fixed factor gathered per non-zero are served "
-                             "by L2 and not counted; the passes are bound by those gathers"},
+                             "by L2 and not counted; the passes are bound by those gathers",
+                     "phase_share": {p: round(pph[p][0] / pms, 4) for p in
+                                     ("pass1", "candidates", "pass2", "select", "sums", "operands")}},
         "kl_start": kl0, "kl_end": kl1,
     }
 

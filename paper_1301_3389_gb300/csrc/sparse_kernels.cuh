@@ -39,22 +39,61 @@ __device__ __forceinline__ Tp warp_sum(Tp x) {
     return x;
 }
 
-// Loads of U non-zeros of a segment: values, and the rows y(s, .) they gather.
+// The non-zeros of a segment are read 32 at a time with one coalesced load (lane l holds
+// the index and value of non-zero k + l) and handed to the whole warp by shuffles; the
+// next 32 are loaded while the current ones are used, so each batch of U non-zeros waits
+// only for its gathered rows y(s, .).
+template <typename Tp>
+struct Chunk {
+    int32_t s;
+    Tp v;
+};
+
+template <typename Tp>
+__device__ __forceinline__ Chunk<Tp> load_chunk(int64_t k, int64_t k1, int lane,
+                                                const int32_t* __restrict__ idx,
+                                                const Tp* __restrict__ val) {
+    Chunk<Tp> c;
+    const bool in = k + lane < k1;
+    c.s = in ? idx[k + lane] : 0;
+    c.v = in ? val[k + lane] : Tp(0);
+    return c;
+}
+
+// The U non-zeros base .. base + U - 1 of chunk c (lanes of c): values, and the rows they
+// gather (zeros past the segment's end, where the chunk holds v = 0 and s = 0).
 template <typename Tp, int RPL>
-__device__ __forceinline__ void load_batch(int64_t k, int64_t k1, int lane, int64_t R,
-                                           const int32_t* __restrict__ idx,
-                                           const Tp* __restrict__ val, const Tp* __restrict__ Yg,
-                                           Tp (&vv)[U], Tp (&y)[U][RPL]) {
+__device__ __forceinline__ void gather_batch(const Chunk<Tp>& c, int base, int lane, int64_t R,
+                                             const Tp* __restrict__ Yg, Tp (&vv)[U],
+                                             Tp (&y)[U][RPL]) {
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-        const bool in = k + u < k1;
-        const int64_t s = in ? idx[k + u] : 0;
-        vv[u] = in ? val[k + u] : Tp(0);
+        const int64_t s = __shfl_sync(0xffffffffu, c.s, base + u);
+        vv[u] = __shfl_sync(0xffffffffu, c.v, base + u);
 #pragma unroll
         for (int j = 0; j < RPL; ++j) {
             const int64_t r = lane + 32 * j;
-            y[u][j] = (in && r < R) ? Yg[s * R + r] : Tp(0);
+            y[u][j] = r < R ? Yg[s * R + r] : Tp(0);
         }
+    }
+}
+
+// Runs body(vv, y) over the non-zeros [k0, k1) in batches of U.
+template <typename Tp, int RPL, class F>
+__device__ __forceinline__ void for_nonzeros(int64_t k0, int64_t k1, int lane, int64_t R,
+                                             const int32_t* __restrict__ idx,
+                                             const Tp* __restrict__ val,
+                                             const Tp* __restrict__ Yg, F&& body) {
+    Chunk<Tp> cur = load_chunk<Tp>(k0, k1, lane, idx, val);
+    for (int64_t k = k0; k < k1; k += 32) {
+        const Chunk<Tp> nxt = load_chunk<Tp>(k + 32, k1, lane, idx, val);
+        const int n = (int)(k1 - k < 32 ? k1 - k : 32);
+        for (int base = 0; base < n; base += U) {
+            Tp vv[U], y[U][RPL];
+            gather_batch<Tp, RPL>(cur, base, lane, R, Yg, vv, y);
+            body(vv, y);
+        }
+        cur = nxt;
     }
 }
 
@@ -82,10 +121,8 @@ __global__ void __launch_bounds__(WARPS * 32)
         b[j] = Tp(0);
     }
     bool bad = false;
-    const int64_t k0 = sg.k0[g], k1 = sg.k1[g];
-    for (int64_t k = k0; k < k1; k += U) {
-        Tp vv[U], y[U][RPL], z[U];
-        load_batch<Tp, RPL>(k, k1, lane, R, idx, val, Yg, vv, y);
+    for_nonzeros<Tp, RPL>(sg.k0[g], sg.k1[g], lane, R, idx, val, Yg, [&](Tp (&vv)[U], Tp (&y)[U][RPL]) {
+        Tp z[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             Tp p = Tp(0);
@@ -105,7 +142,7 @@ __global__ void __launch_bounds__(WARPS * 32)
                 b[j] += y[u][j] * y[u][j] * qb;
             }
         }
-    }
+    });
 #pragma unroll
     for (int j = 0; j < RPL; ++j) {
         const int64_t r = lane + 32 * j;
@@ -171,10 +208,7 @@ __global__ void __launch_bounds__(WARPS * 32)
         xd[j] = r < R ? Xdna[r * O + o] : Tp(0);
     }
     double lm = 0.0, ld = 0.0;
-    const int64_t k0 = sg.k0[g], k1 = sg.k1[g];
-    for (int64_t k = k0; k < k1; k += U) {
-        Tp vv[U], y[U][RPL];
-        load_batch<Tp, RPL>(k, k1, lane, R, idx, val, Yg, vv, y);
+    for_nonzeros<Tp, RPL>(sg.k0[g], sg.k1[g], lane, R, idx, val, Yg, [&](Tp (&vv)[U], Tp (&y)[U][RPL]) {
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             Tp pm = Tp(0), pd = Tp(0);
@@ -190,7 +224,7 @@ __global__ void __launch_bounds__(WARPS * 32)
                 ld -= (double)(vv[u] * log(pd));
             }
         }
-    }
+    });
     lm = warp_sum(lm);
     ld = warp_sum(ld);
     if (lane == 0) {
@@ -252,10 +286,7 @@ __global__ void __launch_bounds__(WARPS * 32)
         x[j] = r < R ? X[r * v.xr + o * v.xo] : Tp(0);
     }
     double acc = 0.0;
-    const int64_t k0 = sg.k0[g], k1 = sg.k1[g];
-    for (int64_t k = k0; k < k1; k += U) {
-        Tp vv[U], y[U][RPL];
-        load_batch<Tp, RPL>(k, k1, lane, R, idx, val, Yg, vv, y);
+    for_nonzeros<Tp, RPL>(sg.k0[g], sg.k1[g], lane, R, idx, val, Yg, [&](Tp (&vv)[U], Tp (&y)[U][RPL]) {
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             Tp p = Tp(0);
@@ -265,7 +296,7 @@ __global__ void __launch_bounds__(WARPS * 32)
             if (lane == u && vv[u] > Tp(0))
                 acc += (double)(vv[u] * log(vv[u] / p)) - (double)vv[u];
         }
-    }
+    });
     acc = warp_sum(acc);
     if (lane == 0) dseg[g] = acc;
 }

@@ -560,6 +560,7 @@ int prep_step(dna_ctx* c, int w, bool with_sq) {
 
 template <typename Tp>
 int finish_step(dna_ctx* c, int w, bool next);
+enum { STOP_NONE = 0, STOP_PASS1 = 1, STOP_PASS2 = 2, STOP_SELECT = 3 };
 template <typename Tp>
 int sparse_half_step(dna_ctx* c, int w, bool mu_only, bool prepared, bool next);
 
@@ -568,8 +569,22 @@ int sparse_half_step(dna_ctx* c, int w, bool mu_only, bool prepared, bool next);
 // half-step were left by the previous one (inside one dna_iterate call); next: leave them
 // for half-step 1 - w (the step 16 / 29 normalisation writes them in the same pass).
 template <typename Tp>
+int step_core(dna_ctx* c, int w, bool mu_only, bool prepared, int stop);
+
+template <typename Tp>
 int half_step(dna_ctx* c, int w, bool mu_only, bool prepared, bool next) {
     if (c->sparse) return sparse_half_step<Tp>(c, w, mu_only, prepared, next);
+    if (int e = step_core<Tp>(c, w, mu_only, prepared, STOP_NONE)) return e;
+    return finish_step<Tp>(c, w, next);
+}
+
+// Steps of half_step up to and including the selection (the MU update with mu_only), which
+// leaves the new factor and its per-block sums (gpart).  stop: STOP_PASS1 returns after
+// pass 1 (the split partials of A, B in Apart, Bpart); STOP_PASS2 starts from A, B already
+// summed into split 0 and returns after pass 2 (the cost slots in dpart); STOP_SELECT
+// starts from the costs summed into slot 0 and runs the selection only.
+template <typename Tp>
+int step_core(dna_ctx* c, int w, bool mu_only, bool prepared, int stop) {
     using S = dna::Simt<Tp>;
     const View v = make_view(c, w == 1);
     Tp* A = static_cast<Tp*>(c->Apart);
@@ -580,55 +595,59 @@ int half_step(dna_ctx* c, int w, bool mu_only, bool prepared, bool next) {
     const bool tc = c->tc;
     const int sp1 = tc ? c->tsp1[w] : c->sp1[w], sp2 = tc ? c->tsp2[w] : c->sp2[w];
     int e = DNA_OK;
-    if (!prepared)
-        if ((e = prep_step<Tp>(c, w, !mu_only))) return e;
-    e = phase(c, DNA_PHASE_PASS1, 1, [&] {
-        if constexpr (sizeof(Tp) == 4)
-            if (tc)
-                return c->split
-                           ? dna::TcBf16::pass1_split(tc_operands(c, w), c->maps[w], A, B, sp1,
-                                                      c->tper1[w], !mu_only, c->status, st)
-                           : dna::TcBf16::pass1(tc_operands(c, w), c->maps[w], A, B, sp1,
-                                                c->tper1[w], !mu_only, c->status, st);
-        return S::pass1(v, A, B, sp1, c->per1[w], !mu_only, c->status, st);
-    });
-    if (e) return e;
-    if (mu_only) {   // eq. 11 in place, with the first level of the step 16 / 29 sums
-        e = phase(c, DNA_PHASE_CANDIDATES, 1, [&] { return S::mu_fused(v, c->c, A, sp1, c->gpart, st); });
-        if (e) return e;
-        return finish_step<Tp>(c, w, next);
+    if (stop <= STOP_PASS1) {
+        if (!prepared)
+            if ((e = prep_step<Tp>(c, w, !mu_only))) return e;
+        e = phase(c, DNA_PHASE_PASS1, 1, [&] {
+            if constexpr (sizeof(Tp) == 4)
+                if (tc)
+                    return c->split
+                               ? dna::TcBf16::pass1_split(tc_operands(c, w), c->maps[w], A, B, sp1,
+                                                          c->tper1[w], !mu_only, c->status, st)
+                               : dna::TcBf16::pass1(tc_operands(c, w), c->maps[w], A, B, sp1,
+                                                    c->tper1[w], !mu_only, c->status, st);
+            return S::pass1(v, A, B, sp1, c->per1[w], !mu_only, c->status, st);
+        });
+        if (e || stop == STOP_PASS1) return e;
+        if (mu_only)   // eq. 11 in place, with the first level of the step 16 / 29 sums
+            return phase(c, DNA_PHASE_CANDIDATES, 1,
+                         [&] { return S::mu_fused(v, c->c, A, sp1, c->gpart, st); });
     }
-    // many split partials: one streaming pass sums them into split 0 first (the candidates
-    // kernel streams up to 4 itself when the rank allows its register form)
-    const bool presum =
-        (int64_t)sp1 * v.O >= 32768 && (sp1 > 4 || !S::cand_in_registers(c->R));
-    e = phase(c, DNA_PHASE_CANDIDATES, presum ? 2 : 1, [&] {
-        if (presum)
-            if (int r = S::split_sum(A, B, c->R, v.O, sp1, st)) return r;
-        return S::cand_fused(v, c->c, A, B, presum ? 1 : sp1, Xmu, Xdna, c->o.eps, c->o.alpha,
-                             tc ? c->Xmk : nullptr, tc ? c->Xdk : nullptr, c->rp, c->pad_o[w],
-                             c->plane, st);
-    });
-    if (e) return e;
-    e = phase(c, DNA_PHASE_PASS2, 1, [&] {
-        if constexpr (sizeof(Tp) == 4)
-            if (tc)
-                return c->split || c->rp <= 256
-                           ? dna::TcBf16::pass2_split(tc_operands(c, w), c->maps[w], c->dpart,
-                                                      sp2, c->status, st)
-                           : dna::TcBf16::pass2_large(tc_operands(c, w), c->maps[w],
-                                                      c->dpart, sp2, c->tper2[w], c->status,
-                                                      st);
-        return S::pass2(v, Xmu, Xdna, c->dpart, sp2, c->per2[w], c->status, st);
-    });
-    if (e) return e;
-    e = phase(c, DNA_PHASE_SELECT, 1, [&] {
-        return S::select_fused(v, Xmu, Xdna, c->dpart, sp2, w ? c->choice_w : c->choice_h,
+    int slots = sp2;
+    if (stop <= STOP_PASS2) {
+        // many split partials: one streaming pass sums them into split 0 first (the
+        // candidates kernel streams up to 4 itself when the rank allows its register form)
+        const int parts = stop == STOP_PASS2 ? 1 : sp1;
+        const bool presum =
+            (int64_t)parts * v.O >= 32768 && (parts > 4 || !S::cand_in_registers(c->R));
+        e = phase(c, DNA_PHASE_CANDIDATES, presum ? 2 : 1, [&] {
+            if (presum)
+                if (int r = S::split_sum(A, B, c->R, v.O, parts, st)) return r;
+            return S::cand_fused(v, c->c, A, B, presum ? 1 : parts, Xmu, Xdna, c->o.eps,
+                                 c->o.alpha, tc ? c->Xmk : nullptr, tc ? c->Xdk : nullptr, c->rp,
+                                 c->pad_o[w], c->plane, st);
+        });
+        if (e) return e;
+        e = phase(c, DNA_PHASE_PASS2, 1, [&] {
+            if constexpr (sizeof(Tp) == 4)
+                if (tc)
+                    return c->split || c->rp <= 256
+                               ? dna::TcBf16::pass2_split(tc_operands(c, w), c->maps[w], c->dpart,
+                                                          sp2, c->status, st)
+                               : dna::TcBf16::pass2_large(tc_operands(c, w), c->maps[w],
+                                                          c->dpart, sp2, c->tper2[w], c->status,
+                                                          st);
+            return S::pass2(v, Xmu, Xdna, c->dpart, sp2, c->per2[w], c->status, st);
+        });
+        if (e || stop == STOP_PASS2) return e;
+    } else {
+        slots = 1;
+    }
+    return phase(c, DNA_PHASE_SELECT, 1, [&] {
+        return S::select_fused(v, Xmu, Xdna, c->dpart, slots, w ? c->choice_w : c->choice_h,
                                w ? c->dfin_w : c->dfin_h, c->gpart, w ? c->o.rho : c->o.lambda,
                                st);
     });
-    if (e) return e;
-    return finish_step<Tp>(c, w, next);
 }
 
 // Steps 16 / 29 after the new factor and its per-block sums (gpart) are written: f_r = sum

@@ -60,16 +60,14 @@ __device__ __forceinline__ Chunk<Tp> load_chunk(int64_t k, int64_t k1, int lane,
     return c;
 }
 
-// The U non-zeros base .. base + U - 1 of chunk c (lanes of c): values, and the rows they
-// gather (zeros past the segment's end, where the chunk holds v = 0 and s = 0).
+// The rows y(s, .) gathered by the U non-zeros base .. base + U - 1 of chunk c (row 0 past
+// the segment's end, where the chunk holds s = 0 and v = 0).
 template <typename Tp, int RPL>
 __device__ __forceinline__ void gather_batch(const Chunk<Tp>& c, int base, int lane, int64_t R,
-                                             const Tp* __restrict__ Yg, Tp (&vv)[U],
-                                             Tp (&y)[U][RPL]) {
+                                             const Tp* __restrict__ Yg, Tp (&y)[U][RPL]) {
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         const int64_t s = __shfl_sync(0xffffffffu, c.s, base + u);
-        vv[u] = __shfl_sync(0xffffffffu, c.v, base + u);
 #pragma unroll
         for (int j = 0; j < RPL; ++j) {
             const int64_t r = lane + 32 * j;
@@ -78,7 +76,33 @@ __device__ __forceinline__ void gather_batch(const Chunk<Tp>& c, int base, int l
     }
 }
 
-// Runs body(vv, y) over the non-zeros [k0, k1) in batches of U.
+// Sums each of the NV per-lane values p[i] over the warp (NV a power of two <= 32) with a
+// fixed reduce-scatter: at the step with xor mask m the lanes with bit m set keep the upper
+// half of the remaining values and the others the lower half, each adding its partner's
+// copy of the half it keeps; after log2(NV) steps a lane holds one value, index
+// lane >> (5 - log2(NV)), and the remaining xor steps complete its sum over all 32 lanes.
+// NV + 5 - log2(NV) - 1 shuffles for NV values instead of 5 NV.
+template <typename Tp, int NV>
+__device__ __forceinline__ Tp scatter_sum(Tp (&p)[NV], int lane) {
+    static_assert(NV >= 1 && NV <= 32 && (NV & (NV - 1)) == 0, "NV: a power of two <= 32");
+    int m = 16;
+#pragma unroll
+    for (int cnt = NV; cnt > 1; cnt >>= 1, m >>= 1) {
+        const bool hi = (lane & m) != 0;
+#pragma unroll
+        for (int i = 0; i < cnt / 2; ++i) {
+            const Tp keep = hi ? p[i + cnt / 2] : p[i];
+            const Tp send = hi ? p[i] : p[i + cnt / 2];
+            p[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+        }
+    }
+    Tp t = p[0];
+#pragma unroll
+    for (; m > 0; m >>= 1) t += __shfl_xor_sync(0xffffffffu, t, m);
+    return t;
+}
+
+// Runs body(chunk, base, y) over the non-zeros [k0, k1) in batches of U.
 template <typename Tp, int RPL, class F>
 __device__ __forceinline__ void for_nonzeros(int64_t k0, int64_t k1, int lane, int64_t R,
                                              const int32_t* __restrict__ idx,
@@ -89,9 +113,9 @@ __device__ __forceinline__ void for_nonzeros(int64_t k0, int64_t k1, int lane, i
         const Chunk<Tp> nxt = load_chunk<Tp>(k + 32, k1, lane, idx, val);
         const int n = (int)(k1 - k < 32 ? k1 - k : 32);
         for (int base = 0; base < n; base += U) {
-            Tp vv[U], y[U][RPL];
-            gather_batch<Tp, RPL>(cur, base, lane, R, Yg, vv, y);
-            body(vv, y);
+            Tp y[U][RPL];
+            gather_batch<Tp, RPL>(cur, base, lane, R, Yg, y);
+            body(cur, base, y);
         }
         cur = nxt;
     }
@@ -121,28 +145,42 @@ __global__ void __launch_bounds__(WARPS * 32)
         b[j] = Tp(0);
     }
     bool bad = false;
-    for_nonzeros<Tp, RPL>(sg.k0[g], sg.k1[g], lane, R, idx, val, Yg, [&](Tp (&vv)[U], Tp (&y)[U][RPL]) {
-        Tp z[U];
+    constexpr int LOGU = U == 8 ? 3 : (U == 4 ? 2 : (U == 16 ? 4 : -1));
+    static_assert(LOGU > 0, "U: 4, 8 or 16");
+    const int ul = lane >> (5 - LOGU);   // the non-zero of the batch this lane finishes
+    for_nonzeros<Tp, RPL>(sg.k0[g], sg.k1[g], lane, R, idx, val, Yg,
+                          [&](const Chunk<Tp>& c, int base, Tp (&y)[U][RPL]) {
+        Tp p[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            Tp p = Tp(0);
+            p[u] = Tp(0);
 #pragma unroll
-            for (int j = 0; j < RPL; ++j) p += y[u][j] * x[j];
-            z[u] = warp_sum(p);
+            for (int j = 0; j < RPL; ++j) p[u] += y[u][j] * x[j];
+        }
+        const Tp z = scatter_sum<Tp, U>(p, lane);             // z of non-zero ul
+        const Tp vl = __shfl_sync(0xffffffffu, c.v, base + ul);
+        Tp q = Tp(0), qb = Tp(0);
+        if (vl > Tp(0)) {                                      // v = 0: q = qbar = 0
+            if (z > Tp(0)) {
+                const Tp rz = Tp(1) / z;                       // q = v / z, qbar = q / z
+                q = vl * rz;
+                qb = q * rz;
+            } else {
+                bad = true;
+            }
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            if (!(vv[u] > Tp(0))) continue;        // v = 0 (or padding): q = qbar = 0
-            if (!(z[u] > Tp(0))) { bad = true; continue; }
-            const Tp q = vv[u] / z[u];
-            const Tp qb = q / z[u];
+            const Tp qu = __shfl_sync(0xffffffffu, q, u << (5 - LOGU));
+            const Tp qbu = __shfl_sync(0xffffffffu, qb, u << (5 - LOGU));
 #pragma unroll
             for (int j = 0; j < RPL; ++j) {
-                a[j] += y[u][j] * q;
-                b[j] += y[u][j] * y[u][j] * qb;
+                a[j] += y[u][j] * qu;
+                b[j] += y[u][j] * y[u][j] * qbu;
             }
         }
     });
+    bad = __any_sync(0xffffffffu, bad);
 #pragma unroll
     for (int j = 0; j < RPL; ++j) {
         const int64_t r = lane + 32 * j;
@@ -188,9 +226,10 @@ __global__ void __launch_bounds__(WARPS * 32)
 }
 
 // Pass 2 (steps 7-9, 12-14 on the non-zeros of one segment): the partial sums
-// dseg[2 g] = sum_{v>0} -v log z_MU and dseg[2 g + 1] = sum_{v>0} -v log z_DNA (float64).
-// The terms of non-zero k are accumulated by lane (k - k0) mod U, then the lanes' float64
-// sums are added by the fixed butterfly.
+// dseg[2 g] = sum_{v>0} -v log z_MU and dseg[2 g + 1] = sum_{v>0} -v log z_DNA.  The term
+// of non-zero k is added by lane (k - k0) mod U in the element type (at most SEG / U terms
+// per lane: float64 arithmetic is slow on this GPU), then the lanes' sums are added in
+// float64 by the fixed butterfly.
 template <typename Tp, int RPL>
 __global__ void __launch_bounds__(WARPS * 32)
     k_sp_pass2(View v, Segs sg, const int32_t* __restrict__ idx, const Tp* __restrict__ val,
@@ -207,26 +246,35 @@ __global__ void __launch_bounds__(WARPS * 32)
         xm[j] = r < R ? Xmu[r * O + o] : Tp(0);
         xd[j] = r < R ? Xdna[r * O + o] : Tp(0);
     }
-    double lm = 0.0, ld = 0.0;
-    for_nonzeros<Tp, RPL>(sg.k0[g], sg.k1[g], lane, R, idx, val, Yg, [&](Tp (&vv)[U], Tp (&y)[U][RPL]) {
+    Tp lm_t = Tp(0), ld_t = Tp(0);
+    constexpr int LOG2U = U == 8 ? 4 : (U == 4 ? 3 : (U == 16 ? 5 : -1));
+    static_assert(LOG2U > 0, "U: 4, 8 or 16");
+    // lane l finishes value l >> (5 - LOG2U) of the 2U: the MU z of non-zero u (values
+    // 0 .. U - 1) or the Newton z (U .. 2U - 1); one lane of each value adds its term
+    const int vi = lane >> (5 - LOG2U), ul = vi & (U - 1);
+    const bool adds = (lane & ((1 << (5 - LOG2U)) - 1)) == 0;
+    for_nonzeros<Tp, RPL>(sg.k0[g], sg.k1[g], lane, R, idx, val, Yg,
+                          [&](const Chunk<Tp>& c, int base, Tp (&y)[U][RPL]) {
+        Tp p[2 * U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            Tp pm = Tp(0), pd = Tp(0);
+            p[u] = Tp(0);
+            p[U + u] = Tp(0);
 #pragma unroll
             for (int j = 0; j < RPL; ++j) {
-                pm += y[u][j] * xm[j];
-                pd += y[u][j] * xd[j];
-            }
-            pm = warp_sum(pm);
-            pd = warp_sum(pd);
-            if (lane == u && vv[u] > Tp(0)) {   // log of a non-positive z gives NaN / -inf
-                lm -= (double)(vv[u] * log(pm));
-                ld -= (double)(vv[u] * log(pd));
+                p[u] += y[u][j] * xm[j];
+                p[U + u] += y[u][j] * xd[j];
             }
         }
+        const Tp z = scatter_sum<Tp, 2 * U>(p, lane);
+        const Tp vl = __shfl_sync(0xffffffffu, c.v, base + ul);
+        if (adds && vl > Tp(0)) {   // log of a non-positive z gives NaN / -inf
+            const Tp t = vl * log(z);
+            if (vi < U) lm_t -= t; else ld_t -= t;
+        }
     });
-    lm = warp_sum(lm);
-    ld = warp_sum(ld);
+    const double lm = warp_sum((double)lm_t);
+    const double ld = warp_sum((double)ld_t);
     if (lane == 0) {
         dseg[2 * g] = lm;
         dseg[2 * g + 1] = ld;
@@ -285,19 +333,24 @@ __global__ void __launch_bounds__(WARPS * 32)
         const int64_t r = lane + 32 * j;
         x[j] = r < R ? X[r * v.xr + o * v.xo] : Tp(0);
     }
-    double acc = 0.0;
-    for_nonzeros<Tp, RPL>(sg.k0[g], sg.k1[g], lane, R, idx, val, Yg, [&](Tp (&vv)[U], Tp (&y)[U][RPL]) {
+    Tp acc_t = Tp(0);   // the element type within the segment, float64 across lanes
+    constexpr int LOGU = U == 8 ? 3 : (U == 4 ? 2 : (U == 16 ? 4 : -1));
+    const int ul = lane >> (5 - LOGU);
+    const bool adds = (lane & ((1 << (5 - LOGU)) - 1)) == 0;
+    for_nonzeros<Tp, RPL>(sg.k0[g], sg.k1[g], lane, R, idx, val, Yg,
+                          [&](const Chunk<Tp>& c, int base, Tp (&y)[U][RPL]) {
+        Tp p[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            Tp p = Tp(0);
+            p[u] = Tp(0);
 #pragma unroll
-            for (int j = 0; j < RPL; ++j) p += y[u][j] * x[j];
-            p = warp_sum(p);
-            if (lane == u && vv[u] > Tp(0))
-                acc += (double)(vv[u] * log(vv[u] / p)) - (double)vv[u];
+            for (int j = 0; j < RPL; ++j) p[u] += y[u][j] * x[j];
         }
+        const Tp z = scatter_sum<Tp, U>(p, lane);
+        const Tp vl = __shfl_sync(0xffffffffu, c.v, base + ul);
+        if (adds && vl > Tp(0)) acc_t += vl * log(vl / z) - vl;
     });
-    acc = warp_sum(acc);
+    const double acc = warp_sum((double)acc_t);
     if (lane == 0) dseg[g] = acc;
 }
 

@@ -230,6 +230,8 @@ def main(argv=None):
     ap.add_argument("--no-c3-target", action="store_true")
     ap.add_argument("--no-mu-log", action="store_true")
     ap.add_argument("--no-sparse", action="store_true")
+    ap.add_argument("--sharded", action="store_true",
+                    help="one problem split by columns over the ranks (strong scaling)")
     ap.add_argument("--log-file", default=None, help="per-iteration DNA/MU log (text)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
@@ -244,6 +246,8 @@ def main(argv=None):
         return run_unrolled(args, world, rank, local)
     if args.workload in SPARSE:
         return run_sparse(args, world, rank, local)
+    if args.sharded:
+        return run_sharded(args, world, rank, local)
     spec = WORKLOADS[args.workload]
 
     if args.impl == "reference":
@@ -708,6 +712,71 @@ def run_sparse(args, world, rank, local):
                            l2="factors and indices fit L2; no flush (steady-state iterations)"),
             "roofline": res["roofline"], "clocks": clk,
             "kl_start": res["kl_start"], "kl_end": res["kl_end"]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_sharded(args, world, rank, local):
+    """One problem (the workload) split by columns over the ranks (strong scaling): each
+    rank's GPU holds V[:, block], H[:, block] and a copy of W; the exchanges of the W
+    half-step and of the normalisations are NCCL all-reduces (paper_1301_3389_gb300.sharded).
+    A step is one DNA iteration of the whole problem."""
+    import torch
+    import torch.distributed as dist
+
+    import paper_1301_3389_gb300 as dna
+    from paper_1301_3389_gb300.sharded import ShardedDNA
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    spec = WORKLOADS[args.workload]
+    prob = spec["fn"](0)                                # the same problem on every rank
+    N, T, R = spec["N"], spec["T"], spec["R"]
+    cuts = np.linspace(0, T, world + 1).astype(int)
+    a, b = int(cuts[rank]), int(cuts[rank + 1])
+    V = torch.from_numpy(np.ascontiguousarray(prob.V[:, a:b])).to(dev)
+    W = torch.from_numpy(prob.W).to(dev)
+    H = torch.from_numpy(np.ascontiguousarray(prob.H[:, a:b])).to(dev)
+    del prob
+    engine = args.engine or ("tensor" if R <= 128 else "auto")
+    ctx = dna.dna_create(N, b - a, R, dna.make_opts(dtype=dna.DNA_F32, engine=engine_code(dna, engine)))
+    stream = torch.cuda.current_stream()
+    dna.dna_set_stream(ctx, stream)
+    dna.dna_bind(ctx, V, W, H)
+    dna.dna_normalize(ctx, 1)
+    sh = ShardedDNA([ctx], N, R, torch.float32, all_reduce=dist.all_reduce if world > 1 else None)
+    kl0 = sh.kl()
+    sh.iterate(args.warmup)
+    clocks = ClockSampler(local) if rank == 0 else None
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sh.iterate(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop() if clocks else None
+    ms_max = max_over_ranks(torch, dist, ms, dev) if world > 1 else ms
+    kl1 = sh.kl()
+    dna.dna_destroy(ctx)
+    if world > 1:
+        dist.destroy_process_group()
+    line = {"metric": METRIC, "value": args.steps / (ms_max / 1e3), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "strong",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": spec["desc"], "N": N, "T": T, "R": R,
+                       "parallelism": f"columns split over {world} GPUs, W replicated, NCCL "
+                                      "all-reduce of the W half-step's sums",
+                       "engine": engine, "l2": "inputs larger than L2"},
+            "clocks": clk, "kl_start": kl0, "kl_end": kl1}
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0

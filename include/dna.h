@@ -329,6 +329,54 @@ void dna_group_destroy(dna_group* g);
 int dna_kl_noalloc(const float* V, int64_t ldv, const float* W, const float* H, int64_t N,
                    int64_t T, int64_t R, double* kl_out, void* stream);
 
+/* ---------------------------------------------------------------- column shards
+ * One DNA iteration of a problem whose columns are split over G ranks (one GPU each): rank
+ * g holds V[:, T_g] and H[:, T_g] (a column block) and a full copy of W, in an ordinary
+ * dense context of size N x T_g (any form and engine; dna_normalize(ctx, 1) for step 1 as
+ * usual, and dna_kl gives this block's share of d_KL, to be summed over the ranks).
+ * The H half-step separates over columns (eq. 5); the W half-step and the normalisations
+ * need sums over all columns.  The calls below run every step on this rank's block and
+ * stop at each such sum: the caller adds the buffer a call wrote over the G ranks (an
+ * all-reduce, e.g. NCCL through torch.distributed) and passes the total to the next call.
+ * Every buffer is caller-owned device memory; float64 unless stated; every call is
+ * asynchronous on the context's stream.  With G = 1 (no reduction) the sequence equals
+ * dna_step_H then dna_step_W.
+ *
+ * Once after dna_bind:
+ *   dna_shard_rowsums(out[N]) -> all-reduce -> dna_shard_set_rowsums(total)
+ *   (the row sums of V, the eq. 10 targets of the W half-step)
+ * H half-step (Algorithm 1 steps 4-16):
+ *   dna_shard_H_begin(rsum[R]) -> all-reduce -> dna_shard_H_end(rsum)
+ * W half-step (steps 17-29):
+ *   dna_shard_W_begin(hsum[R]) -> all-reduce -> dna_shard_W_pass1(hsum, AB[2][R][N], the
+ *   context's element type) -> all-reduce AB -> dna_shard_W_pass2(AB, cost[2][N]) ->
+ *   all-reduce -> dna_shard_W_end(cost)
+ * Sparse and host-buffer contexts: DNA_ERR_UNSUPPORTED. */
+
+/* out[n] = sum over this block's columns of v_nt. */
+int dna_shard_rowsums(dna_ctx* ctx, double* out);
+/* Set the row sums of V over all columns (the eq. 10 targets of the W half-step). */
+int dna_shard_set_rowsums(dna_ctx* ctx, const double* in);
+/* Steps 4-15 on this block's columns (each column's selection is local, eq. 5), then
+ * rsum[r] = sum over this block of the new h_rt (step 16's sums before rho). */
+int dna_shard_H_begin(dna_ctx* ctx, double* rsum);
+/* Step 16 with the all-reduced rsum: row r of H divided, column r of W multiplied, by
+ * rsum[r] + rho (identical on every rank). */
+int dna_shard_H_end(dna_ctx* ctx, const double* rsum);
+/* Operands of the W half-step; hsum[r] = sum over this block of h_rt (the eq. 7 / 14
+ * denominators of the W half-step before rho). */
+int dna_shard_W_begin(dna_ctx* ctx, double* hsum);
+/* With the all-reduced hsum: the raw sums over this block's columns of eq. 7 and 14,
+ * AB[0][r][n] = sum_t q_nt h_rt and AB[1][r][n] = sum_t qbar_nt h_rt^2 (steps 18, 23). */
+int dna_shard_W_pass1(dna_ctx* ctx, const double* hsum, void* AB);
+/* With the all-reduced AB: both candidates per row of W (steps 19, 24; identical on every
+ * rank) and their costs over this block's columns, cost[0][n] (MU) and cost[1][n]
+ * (Newton), each sum_t (-v log z + z) (steps 20-22, 25-27). */
+int dna_shard_W_pass2(dna_ctx* ctx, const void* AB, double* cost);
+/* With the all-reduced costs: the selection per row (step 28, the rho penalty added as in
+ * dna_step_W) and step 29 (W's column sums are local: W is replicated). */
+int dna_shard_W_end(dna_ctx* ctx, const double* cost);
+
 /* Release the context and its workspace (not the caller's buffers). */
 void dna_destroy(dna_ctx* ctx);
 

@@ -59,6 +59,14 @@ def _load() -> ctypes.CDLL:
         "mu_iterate": (I, [P, I]),
         "dna_create_sparse": (I, [I64, I64, I64, I64, ctypes.POINTER(dna_opts), ctypes.POINTER(P)]),
         "dna_bind_csr": (I, [P, P, P, P, P, P]),
+        "dna_shard_rowsums": (I, [P, P]),
+        "dna_shard_set_rowsums": (I, [P, P]),
+        "dna_shard_H_begin": (I, [P, P]),
+        "dna_shard_H_end": (I, [P, P]),
+        "dna_shard_W_begin": (I, [P, P]),
+        "dna_shard_W_pass1": (I, [P, P, P]),
+        "dna_shard_W_pass2": (I, [P, P, P]),
+        "dna_shard_W_end": (I, [P, P]),
         "dna_kl": (I, [P, ctypes.POINTER(D)]),
         "dna_get_choice": (I, [P, I, P, I64]),
         "dna_get_costs": (I, [P, I, P, P, I64]),
@@ -375,3 +383,20 @@ def dna_group_destroy(g: int) -> None:
 
 def dna_destroy(ctx: int) -> None:
     LIB.dna_destroy(ctx)
+
+
+def _shard_call(name):
+    def f(ctx: int, *bufs) -> None:
+        _check(getattr(LIB, name)(ctx, *[_ptr(b) for b in bufs]), name)
+    f.__name__ = name
+    return f
+
+
+dna_shard_rowsums = _shard_call("dna_shard_rowsums")
+dna_shard_set_rowsums = _shard_call("dna_shard_set_rowsums")
+dna_shard_H_begin = _shard_call("dna_shard_H_begin")
+dna_shard_H_end = _shard_call("dna_shard_H_end")
+dna_shard_W_begin = _shard_call("dna_shard_W_begin")
+dna_shard_W_pass1 = _shard_call("dna_shard_W_pass1")
+dna_shard_W_pass2 = _shard_call("dna_shard_W_pass2")
+dna_shard_W_end = _shard_call("dna_shard_W_end")

@@ -854,6 +854,77 @@ int phase(dna_ctx* c, int ph, int nlaunch, F&& f) {
     return e;
 }
 
+// ---------------------------------------------------------------- column shards
+int shard_ready(dna_ctx* c) {
+    if (int e = check_ready(c)) return e;
+    if (c->sparse || c->host_mode) return DNA_ERR_UNSUPPORTED;
+    return set_device(c) ? DNA_ERR_CUDA : DNA_OK;
+}
+
+int d2d(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, st) == cudaSuccess
+               ? DNA_OK
+               : DNA_ERR_CUDA;
+}
+
+template <typename Tp>
+int shard_H_begin(dna_ctx* c, double* rsum) {
+    using S = dna::Simt<Tp>;
+    if (int e = step_core<Tp>(c, 0, false, false, STOP_NONE)) return e;
+    if (int e = S::raw_sums(c->gpart, S::glue_parts(c->T), c->R, c->sig, c->stream)) return e;
+    return d2d(rsum, c->sig, sizeof(double) * c->R, c->stream);
+}
+
+template <typename Tp>
+int shard_H_end(dna_ctx* c, const double* rsum) {
+    using S = dna::Simt<Tp>;
+    if (int e = S::add_reg(rsum, c->R, c->o.rho, c->sig, c->stream)) return e;
+    return S::scale_ops(make_view(c, false), c->sig, false, nullptr, nullptr, nullptr, nullptr, 0,
+                        0, 0, 0, nullptr, c->stream);
+}
+
+template <typename Tp>
+int shard_W_begin(dna_ctx* c, double* hsum) {
+    using S = dna::Simt<Tp>;
+    if (int e = prep_step<Tp>(c, 1, true)) return e;
+    if (int e = S::raw_sums(c->gpart, S::glue_parts(c->T), c->R, c->sig, c->stream)) return e;
+    return d2d(hsum, c->sig, sizeof(double) * c->R, c->stream);
+}
+
+template <typename Tp>
+int shard_W_pass1(dna_ctx* c, const double* hsum, void* AB) {
+    using S = dna::Simt<Tp>;
+    if (int e = S::add_reg(hsum, c->R, c->o.rho, c->c, c->stream)) return e;
+    if (int e = step_core<Tp>(c, 1, false, true, STOP_PASS1)) return e;
+    const int sp1 = c->tc ? c->tsp1[1] : c->sp1[1];
+    Tp* A = static_cast<Tp*>(c->Apart);
+    Tp* B = static_cast<Tp*>(c->Bpart);
+    if (int e = S::split_sum(A, B, c->R, c->N, sp1, c->stream)) return e;
+    const size_t n = sizeof(Tp) * (size_t)(c->R * c->N);
+    if (int e = d2d(AB, A, n, c->stream)) return e;
+    return d2d(static_cast<char*>(AB) + n, B, n, c->stream);
+}
+
+template <typename Tp>
+int shard_W_pass2(dna_ctx* c, const void* AB, double* cost) {
+    const size_t n = sizeof(Tp) * (size_t)(c->R * c->N);
+    if (int e = d2d(c->Apart, AB, n, c->stream)) return e;
+    if (int e = d2d(c->Bpart, static_cast<const char*>(AB) + n, n, c->stream)) return e;
+    if (int e = step_core<Tp>(c, 1, false, true, STOP_PASS2)) return e;
+    const int sp2 = c->tc ? c->tsp2[1] : c->sp2[1];
+    // the cost slots [sp2][2][N] summed into slot 0 (float64, ascending slot order)
+    if (int e = dna::Simt<double>::split_sum(c->dpart, nullptr, 1, 2 * c->N, sp2, c->stream))
+        return e;
+    return d2d(cost, c->dpart, sizeof(double) * 2 * c->N, c->stream);
+}
+
+template <typename Tp>
+int shard_W_end(dna_ctx* c, const double* cost) {
+    if (int e = d2d(c->dpart, cost, sizeof(double) * 2 * c->N, c->stream)) return e;
+    if (int e = step_core<Tp>(c, 1, false, true, STOP_SELECT)) return e;
+    return finish_step<Tp>(c, 1, false);
+}
+
 }  // namespace
 
 namespace dna {
@@ -1099,6 +1170,54 @@ int mu_iterate(dna_ctx* c, int iters) {
         if (e) return e;
     }
     return DNA_OK;
+}
+
+int dna_shard_rowsums(dna_ctx* c, double* out) {
+    if (!out) return DNA_ERR_ARG;
+    if (int e = shard_ready(c)) return e;
+    return d2d(out, c->rowsum_v, sizeof(double) * c->N, c->stream);
+}
+
+int dna_shard_set_rowsums(dna_ctx* c, const double* in) {
+    if (!in) return DNA_ERR_ARG;
+    if (int e = shard_ready(c)) return e;
+    return d2d(c->rowsum_v, in, sizeof(double) * c->N, c->stream);
+}
+
+int dna_shard_H_begin(dna_ctx* c, double* rsum) {
+    if (!rsum) return DNA_ERR_ARG;
+    if (int e = shard_ready(c)) return e;
+    return is_f64(c) ? shard_H_begin<double>(c, rsum) : shard_H_begin<float>(c, rsum);
+}
+
+int dna_shard_H_end(dna_ctx* c, const double* rsum) {
+    if (!rsum) return DNA_ERR_ARG;
+    if (int e = shard_ready(c)) return e;
+    return is_f64(c) ? shard_H_end<double>(c, rsum) : shard_H_end<float>(c, rsum);
+}
+
+int dna_shard_W_begin(dna_ctx* c, double* hsum) {
+    if (!hsum) return DNA_ERR_ARG;
+    if (int e = shard_ready(c)) return e;
+    return is_f64(c) ? shard_W_begin<double>(c, hsum) : shard_W_begin<float>(c, hsum);
+}
+
+int dna_shard_W_pass1(dna_ctx* c, const double* hsum, void* AB) {
+    if (!hsum || !AB) return DNA_ERR_ARG;
+    if (int e = shard_ready(c)) return e;
+    return is_f64(c) ? shard_W_pass1<double>(c, hsum, AB) : shard_W_pass1<float>(c, hsum, AB);
+}
+
+int dna_shard_W_pass2(dna_ctx* c, const void* AB, double* cost) {
+    if (!AB || !cost) return DNA_ERR_ARG;
+    if (int e = shard_ready(c)) return e;
+    return is_f64(c) ? shard_W_pass2<double>(c, AB, cost) : shard_W_pass2<float>(c, AB, cost);
+}
+
+int dna_shard_W_end(dna_ctx* c, const double* cost) {
+    if (!cost) return DNA_ERR_ARG;
+    if (int e = shard_ready(c)) return e;
+    return is_f64(c) ? shard_W_end<double>(c, cost) : shard_W_end<float>(c, cost);
 }
 
 int dna_kl(dna_ctx* c, double* out) {

@@ -115,6 +115,8 @@ template <typename Tp> struct Simt {
     static int select_fused(const View& v, const Tp* Xmu, const Tp* Xdna, const double* dpart,
                             int splits, uint8_t* choice, double* dfin, double* fpart,
                             double reg, cudaStream_t st);
+    // out[r] = in[r] + reg (an exact zero replaced by 1)
+    static int add_reg(const double* in, int64_t R, double reg, double* out, cudaStream_t st);
     // MU (eq. 11) in place from the pass-1 split partials, plus fpart as select_fused
     static int mu_fused(const View& v, const double* c, const Tp* Apart, int splits,
                         double* fpart, cudaStream_t st);

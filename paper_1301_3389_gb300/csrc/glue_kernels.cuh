@@ -476,6 +476,18 @@ __global__ void __launch_bounds__(256) k_mu_fused(View v, const double* __restri
     }
 }
 
+// out[r] = in[r] + reg, an exact zero replaced by 1 (the factor sums of Algorithm 1 from
+// sums that other ranks helped form).
+template <int UNUSED = 0>
+__global__ void k_add_reg(const double* __restrict__ in, int64_t R, double reg,
+                          double* __restrict__ out) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < R) {
+        const double s = in[r] + reg;
+        out[r] = s == 0.0 ? 1.0 : s;
+    }
+}
+
 // One tile job of k_scale_ops.
 struct OpsArgs {
     // the target half-step's X (element (r, o) at X[r * xr + o * xo]) and Y ((s, r) at

@@ -442,6 +442,12 @@ template <typename Tp> int Simt<Tp>::oblock() { return simt::OB; }
 template <typename Tp> int Simt<Tp>::rblock(int64_t R) { return simt::rblock_for<Tp>(R); }
 
 template <typename Tp>
+int Simt<Tp>::add_reg(const double* in, int64_t R, double reg, double* out, cudaStream_t st) {
+    glue::k_add_reg<0><<<(unsigned)((R + 255) / 256), 256, 0, st>>>(in, R, reg, out);
+    return simt::launch_status();
+}
+
+template <typename Tp>
 int Simt<Tp>::raw_sums(const double* part, int64_t nparts, int64_t R, double* out,
                        cudaStream_t st) {
     if (R <= 1024)

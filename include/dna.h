@@ -377,6 +377,17 @@ int dna_shard_W_pass2(dna_ctx* ctx, const void* AB, double* cost);
  * dna_step_W) and step 29 (W's column sums are local: W is replicated). */
 int dna_shard_W_end(dna_ctx* ctx, const double* cost);
 
+/* Failure detection of the device-side waits: every barrier wait of the tensor-core kernels
+ * is bounded (about 2 s of SM cycles); when one gives up, the kernel raises an abort flag
+ * that its other warps see, waits (bounded) for its own copies and MMAs in flight, frees
+ * its tensor memory and returns, and the next synchronising call reports
+ * DNA_ERR_TIMEOUT.  This call runs that path on one CTA whose wait, limited to
+ * limit_cycles (1 .. 2^32) SM cycles, is on a barrier phase that nothing completes (no
+ * copy or MMA is in flight), on the legacy default stream, and returns DNA_ERR_TIMEOUT
+ * when the timeout was detected and reported (DNA_OK would mean it was not).
+ * Synchronises; allocates and frees one int of device memory. */
+int dna_check_wait_timeout(int64_t limit_cycles);
+
 /* Release the context and its workspace (not the caller's buffers). */
 void dna_destroy(dna_ctx* ctx);
 

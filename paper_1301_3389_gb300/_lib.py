@@ -60,6 +60,7 @@ def _load() -> ctypes.CDLL:
         "dna_create_sparse": (I, [I64, I64, I64, I64, ctypes.POINTER(dna_opts), ctypes.POINTER(P)]),
         "dna_bind_csr": (I, [P, P, P, P, P, P]),
         "dna_shard_rowsums": (I, [P, P]),
+        "dna_check_wait_timeout": (I, [I64]),
         "dna_shard_set_rowsums": (I, [P, P]),
         "dna_shard_H_begin": (I, [P, P]),
         "dna_shard_H_end": (I, [P, P]),

@@ -1172,6 +1172,20 @@ int mu_iterate(dna_ctx* c, int iters) {
     return DNA_OK;
 }
 
+int dna_check_wait_timeout(int64_t limit_cycles) {
+    if (limit_cycles < 1 || limit_cycles > ((int64_t)1 << 32)) return DNA_ERR_ARG;
+    int* status = nullptr;
+    if (dmalloc(&status, sizeof(int))) return DNA_ERR_ALLOC;
+    int st = 0;
+    int e = cudaMemset(status, 0, sizeof(int)) == cudaSuccess ? DNA_OK : DNA_ERR_CUDA;
+    if (!e) e = dna::TcBf16::check_wait_timeout(limit_cycles, status, nullptr);
+    if (!e && (cudaMemcpy(&st, status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess))
+        e = DNA_ERR_CUDA;
+    cudaFree(status);
+    if (e) return e;
+    return (st & dna::STATUS_TIMEOUT) ? DNA_ERR_TIMEOUT : DNA_OK;
+}
+
 int dna_shard_rowsums(dna_ctx* c, double* out) {
     if (!out) return DNA_ERR_ARG;
     if (int e = shard_ready(c)) return e;

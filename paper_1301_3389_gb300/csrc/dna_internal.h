@@ -229,6 +229,9 @@ struct TcBf16 {
                         int* status, cudaStream_t st);
     static int chunk();
     static int oblock();
+    // one CTA whose bounded wait on a barrier that nothing completes gives up after
+    // `limit` SM cycles and sets STATUS_TIMEOUT in *status
+    static int check_wait_timeout(long long limit, int* status, cudaStream_t st);
 };
 
 // sum of part[0 .. n) into *out in a fixed order (work: REDUCE_PARTS doubles)

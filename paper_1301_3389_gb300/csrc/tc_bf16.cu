@@ -504,4 +504,37 @@ int TcBf16::pass1(const TcOperands& op, const TcMaps& maps, float* Apart, float*
 int TcBf16::chunk() { return tc::SCH; }
 int TcBf16::oblock() { return tc::OBLK; }
 
+namespace tc {
+// The timeout path of the bounded barrier waits (wait_phase_limit, the wait of every
+// tcgen05 kernel here), with no asynchronous copy or MMA in flight: warp 0 waits on a
+// barrier phase that nothing completes and gives up after `limit` cycles, raising the
+// CTA's abort flag; warp 1, waiting on another such phase, leaves on the flag (or after
+// 1000 x limit); the CTA then reports STATUS_TIMEOUT as the tcgen05 kernels do.
+__global__ void k_wait_timeout_check(long long limit, int* status) {
+    __shared__ uint64_t bar[2];
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        abort_flag = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+    volatile int* abort = &abort_flag;
+    if ((threadIdx.x & 31) == 0) {
+        if (threadIdx.x == 0)
+            wait_phase_limit(&bar[0], 0, abort, limit);
+        else
+            wait_phase_limit(&bar[1], 0, abort, 1000 * limit);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && *abort) atomicOr(status, STATUS_TIMEOUT);
+}
+}  // namespace tc
+
+int TcBf16::check_wait_timeout(long long limit, int* status, cudaStream_t st) {
+    tc::k_wait_timeout_check<<<1, 64, 0, st>>>(limit, status);
+    return after_launch();
+}
+
 }  // namespace dna

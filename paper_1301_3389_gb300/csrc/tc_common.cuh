@@ -22,17 +22,21 @@ using bf16 = __nv_bfloat16;
 // WAIT_LIMIT cycles (then abort the CTA).
 // A phase that has already completed costs only the non-blocking test: the suspending
 // try_wait costs a couple of hundred cycles even then.
-__device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity, volatile int* abort) {
+__device__ __forceinline__ bool wait_phase_limit(uint64_t* bar, uint32_t parity,
+                                                 volatile int* abort, long long limit) {
     if (mbar_test(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
         if (*abort) return false;
-        if (clock64() - t0 > WAIT_LIMIT) {
+        if (clock64() - t0 > limit) {
             *abort = 1;
             return false;
         }
     }
     return true;
+}
+__device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity, volatile int* abort) {
+    return wait_phase_limit(bar, parity, abort, WAIT_LIMIT);
 }
 
 // After an abort: wait (bounded, ignoring the abort flag) for a phase that was armed, so

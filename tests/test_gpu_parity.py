@@ -229,3 +229,16 @@ def test_regularised_selection_costs(kind):
                 diff = np.asarray(gp.choice(which), bool) != half.choice
                 if diff.any():
                     assert half.margin[diff].max() < NEAR_TIE[kind]
+
+
+def test_wait_timeout_reported_and_context_usable():
+    """A bounded device wait that runs out (on a barrier nothing completes, nothing else in
+    flight) is reported as DNA_ERR_TIMEOUT; the CUDA context stays usable and a context made
+    afterwards runs a tensor-core iteration with a clean status."""
+    import paper_1301_3389_gb300 as dna
+    assert dna.LIB.dna_check_wait_timeout(2_000_000) == dna.DNA_ERR_TIMEOUT
+    p = workloads.custom(120, 200, 16, seed=12)
+    with GpuProblem(p.V, p.W, p.H, "f32t") as gp:
+        gp.dna.dna_iterate(gp.ctx, 2)
+        assert gp.dna.dna_get_status(gp.ctx) == dna.DNA_OK
+    assert dna.LIB.dna_check_wait_timeout(0) == dna.DNA_ERR_ARG

@@ -35,6 +35,11 @@ Readings taken where the paper is silent, ambiguous or garbled (each is tested):
   entries add only z to the cost.
 * z <= 0 where v > 0 cannot happen with positive factors; it raises NonFiniteError.
 * Eq. 10 renormalisation with a zero denominator leaves the column unscaled.
+* Descent selection (an optional variant; the paper's closing remark that refined step
+  damping could avoid cost evaluations): keep the Newton candidate iff its eq. 5 cost is
+  below that of the column the half-step starts from, else the MU candidate.  MU never
+  increases the eq. 5 cost ([20], Section 2.1), so the kept candidate never does either
+  (the guarantee of Section 2.4), and only the Newton candidate's cost is evaluated.
 * The denominators of eq. 7 and eq. 14 are always the explicit (W^t 1)_r + lambda
   (H-step) and (H 1)_r + rho (W-step); steps 1, 16 and 29 normalise as written.
 * A factor sum that is exactly zero (an all-zero column of W or row of H with no
@@ -165,15 +170,18 @@ class HalfStep:
     d_mu: np.ndarray     # per-column (row) eq. 5 (eq. 4) cost of the MU candidate, less a constant
     d_dna: np.ndarray    # the same for the Newton candidate
     choice: np.ndarray   # True where the Newton candidate is kept
-    margin: np.ndarray   # |d_dna - d_mu| / max(|d_mu|, tiny)
+    margin: np.ndarray   # |d_dna - d_ref| / max(|d_ref|, tiny), d_ref the compared cost
+    d_cur: np.ndarray = None   # eq. 5 cost of the starting factor (descent selection)
 
 
 def h_half_step(V, W, H, eps: float = EPS, alpha: float = ALPHA, lam: float = 0.0,
-                choice=None) -> HalfStep:
+                choice=None, selection: str = "paper") -> HalfStep:
     """Algorithm 1 steps 2-15 for H (W fixed).
 
     ``choice`` (bool per column) replaces the step-15 comparison when given: it lets a
-    test replay another implementation's selection near ties.
+    test replay another implementation's selection near ties.  ``selection="descent"``
+    compares the Newton candidate with the starting column instead of with the MU
+    candidate (module docstring).
     """
     V, W, H = f64(V), f64(W), f64(H)
     c = nonzero_sum(W.sum(axis=0) + lam)          # (W^t 1)_r + lambda   (eq. 7, 14)
@@ -195,16 +203,18 @@ def h_half_step(V, W, H, eps: float = EPS, alpha: float = ALPHA, lam: float = 0.
     H_dna = H_dna * scale[None, :]
     Z_dna = W @ H_dna                             # step 12
     d_dna = column_cost(V, Z_dna) + lam * H_dna.sum(axis=0)  # steps 13-14, eq. 5 cost
+    d_cur = column_cost(V, Z) + lam * H.sum(axis=0)          # starting column, eq. 5 cost
+    d_ref = d_cur if selection == "descent" else d_mu
     if choice is None:
-        choice = d_dna < d_mu                     # step 15, ties keep MU
+        choice = d_dna < d_ref                    # step 15, ties keep MU
     choice = np.asarray(choice, dtype=bool)
     H_new = np.where(choice[None, :], H_dna, H_mu)
-    margin = np.abs(d_dna - d_mu) / np.maximum(np.abs(d_mu), 1e-300)
-    return HalfStep(H_new, H_mu, H_dna, A, B, c, d_mu, d_dna, choice, margin)
+    margin = np.abs(d_dna - d_ref) / np.maximum(np.abs(d_ref), 1e-300)
+    return HalfStep(H_new, H_mu, H_dna, A, B, c, d_mu, d_dna, choice, margin, d_cur)
 
 
 def w_half_step(V, W, H, eps: float = EPS, alpha: float = ALPHA, rho: float = 0.0,
-                choice=None) -> HalfStep:
+                choice=None, selection: str = "paper") -> HalfStep:
     """Algorithm 1 steps 17-28 for W (H fixed); selection per row of W."""
     V, W, H = f64(V), f64(W), f64(H)
     c = nonzero_sum(H.sum(axis=1) + rho)          # (H 1)_r + rho
@@ -226,34 +236,38 @@ def w_half_step(V, W, H, eps: float = EPS, alpha: float = ALPHA, rho: float = 0.
     W_dna = W_dna * scale[:, None]
     Z_dna = W_dna @ H                             # step 25
     d_dna = row_cost(V, Z_dna) + rho * W_dna.sum(axis=1)     # steps 26-27, eq. 4 cost
+    d_cur = row_cost(V, Z) + rho * W.sum(axis=1)             # starting row, eq. 4 cost
+    d_ref = d_cur if selection == "descent" else d_mu
     if choice is None:
-        choice = d_dna < d_mu                     # step 28, ties keep MU
+        choice = d_dna < d_ref                    # step 28, ties keep MU
     choice = np.asarray(choice, dtype=bool)
     W_new = np.where(choice[:, None], W_dna, W_mu)
-    margin = np.abs(d_dna - d_mu) / np.maximum(np.abs(d_mu), 1e-300)
-    return HalfStep(W_new, W_mu, W_dna, A, B, c, d_mu, d_dna, choice, margin)
+    margin = np.abs(d_dna - d_ref) / np.maximum(np.abs(d_ref), 1e-300)
+    return HalfStep(W_new, W_mu, W_dna, A, B, c, d_mu, d_dna, choice, margin, d_cur)
 
 
 # ----------------------------------------------------------------------- full steps
-def dna_step_h(V, W, H, eps=EPS, alpha=ALPHA, rho=0.0, lam=0.0, choice=None):
+def dna_step_h(V, W, H, eps=EPS, alpha=ALPHA, rho=0.0, lam=0.0, choice=None,
+               selection="paper"):
     """Steps 4-16: H half-step then the step-16 normalisation.  Returns (W, H, HalfStep)."""
-    hs = h_half_step(V, W, H, eps, alpha, lam, choice)
+    hs = h_half_step(V, W, H, eps, alpha, lam, choice, selection)
     W2, H2 = normalize_h_rows(W, hs.X, rho)
     return W2, H2, hs
 
 
-def dna_step_w(V, W, H, eps=EPS, alpha=ALPHA, rho=0.0, lam=0.0, choice=None):
+def dna_step_w(V, W, H, eps=EPS, alpha=ALPHA, rho=0.0, lam=0.0, choice=None,
+               selection="paper"):
     """Steps 17-29: W half-step then the step-29 normalisation.  Returns (W, H, HalfStep)."""
-    ws = w_half_step(V, W, H, eps, alpha, rho, choice)
+    ws = w_half_step(V, W, H, eps, alpha, rho, choice, selection)
     W2, H2 = normalize_w_columns(ws.X, H, lam)
     return W2, H2, ws
 
 
 def dna_iteration(V, W, H, eps=EPS, alpha=ALPHA, rho=0.0, lam=0.0,
-                  choice_h=None, choice_w=None):
+                  choice_h=None, choice_w=None, selection="paper"):
     """One DNA iteration (steps 4-29).  Returns (W, H, HalfStep_H, HalfStep_W)."""
-    W, H, hs = dna_step_h(V, W, H, eps, alpha, rho, lam, choice_h)
-    W, H, ws = dna_step_w(V, W, H, eps, alpha, rho, lam, choice_w)
+    W, H, hs = dna_step_h(V, W, H, eps, alpha, rho, lam, choice_h, selection)
+    W, H, ws = dna_step_w(V, W, H, eps, alpha, rho, lam, choice_w, selection)
     return W, H, hs, ws
 
 
@@ -290,12 +304,15 @@ def mu_iteration(V, W, H, rho=0.0, lam=0.0):
 
 def run(V, W, H, iters: int, algo: str = "dna", eps=EPS, alpha=ALPHA, rho=0.0, lam=0.0,
         log_cost: bool = True):
-    """Step 1 then ``iters`` iterations of DNA or MU.  Returns (W, H, costs)."""
+    """Step 1 then ``iters`` iterations of DNA, DNA with descent selection ("dna_descent")
+    or MU.  Returns (W, H, costs)."""
     W, H = normalize_w_columns(W, H, lam)
     costs = [kl_divergence(V, W @ H)] if log_cost else []
     for _ in range(iters):
         if algo == "dna":
             W, H, _, _ = dna_iteration(V, W, H, eps, alpha, rho, lam)
+        elif algo == "dna_descent":
+            W, H, _, _ = dna_iteration(V, W, H, eps, alpha, rho, lam, selection="descent")
         elif algo == "mu":
             W, H = mu_iteration(V, W, H, rho, lam)
         else:

@@ -251,6 +251,34 @@ def check_regularised_selection(reg=2.0, seeds=range(8), iters=3):
             W, H, _ = o.dna_step_w(V, W, H, rho=reg, lam=reg)
 
 
+def check_descent_selection(reg_values=(0.0, 1.5), seeds=range(6), iters=3):
+    """Descent selection: the Newton candidate is kept iff its eq. 5 (eq. 4) cost, evaluated
+    directly with SciPy, is below that of the starting column (row), so the kept candidate
+    never raises it; and every column the paper's rule gives to Newton, descent does too
+    (d_DNA < d_MU <= d_start, MU being non-increasing)."""
+    for reg in reg_values:
+        for seed in seeds:
+            V, W, H = rand_problem(12, 30, 4, 300 + seed)
+            W, H = o.normalize_w_columns(W, H, reg)
+            for _ in range(iters):
+                hs = o.h_half_step(V, W, H, lam=reg, selection="descent")
+                paper = o.h_half_step(V, W, H, lam=reg)
+                e_cur = _eq5_cost_columns(V, W, H, reg)
+                e_dna = _eq5_cost_columns(V, W, hs.X_dna, reg)
+                clear = np.abs(e_dna - e_cur) > 1e-10 * np.abs(e_cur)
+                assert np.array_equal(hs.choice[clear], (e_dna < e_cur)[clear]), "H descent"
+                e_new = _eq5_cost_columns(V, W, hs.X, reg)
+                assert np.all(e_new <= e_cur + 1e-10 * np.abs(e_cur)), "descent raised a cost"
+                assert np.all(hs.choice[paper.choice]), "paper's Newton columns must stay Newton"
+                W, H, _ = o.dna_step_h(V, W, H, rho=reg, lam=reg, selection="descent")
+                ws = o.w_half_step(V, W, H, rho=reg, selection="descent")
+                e_cur = _eq5_cost_columns(V.T, H.T, W.T, reg)
+                e_dna = _eq5_cost_columns(V.T, H.T, ws.X_dna.T, reg)
+                clear = np.abs(e_dna - e_cur) > 1e-10 * np.abs(e_cur)
+                assert np.array_equal(ws.choice[clear], (e_dna < e_cur)[clear]), "W descent"
+                W, H, _ = o.dna_step_w(V, W, H, rho=reg, lam=reg, selection="descent")
+
+
 def check_sparse_identities():
     """On a sparse term-count V (the paper's second workload, Section 4.2), the oracle's
     quantities are sums over the stored non-zeros only (the note after Algorithm 1): A and
@@ -378,4 +406,5 @@ ALL = [check_kl_definition, check_costs_sum_to_kl, check_a_b_finite_differences,
        check_w_a_b_finite_differences, check_r1_golden, check_r1_random,
        check_step_limits_golden, check_eq9_invariant, check_monotone, check_fixed_point,
        check_transpose_symmetry, check_scale_equivariance, check_normalisation_steps,
-       check_brute_force_tiny, check_regularised_selection, check_sparse_identities]
+       check_brute_force_tiny, check_regularised_selection, check_sparse_identities,
+       check_descent_selection]

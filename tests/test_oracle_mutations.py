@@ -35,8 +35,14 @@ MUTATIONS = {
                                      "c = nonzero_sum(W.sum(axis=0))          # (W^t 1)_r"),
     "step16_multiplies_h": ("return W * s[None, :], H / s[:, None]",
                             "return W / s[None, :], H * s[:, None]"),
-    "selection_inverted": ("choice = d_dna < d_mu                     # step 15",
-                           "choice = d_dna > d_mu                     # step 15"),
+    "selection_inverted": ("choice = d_dna < d_ref                    # step 15",
+                           "choice = d_dna > d_ref                    # step 15"),
+    "descent_compares_mu": ("d_ref = d_cur if selection == \"descent\" else d_mu\n    if choice is None:\n        choice = d_dna < d_ref                    # step 15",
+                            "d_ref = d_mu\n    if choice is None:\n        choice = d_dna < d_ref                    # step 15"),
+    "descent_cost_without_lambda": ("d_cur = column_cost(V, Z) + lam * H.sum(axis=0)",
+                                    "d_cur = column_cost(V, Z)"),
+    "descent_w_cost_without_rho": ("d_cur = row_cost(V, Z) + rho * W.sum(axis=1)",
+                                   "d_cur = row_cost(V, Z)"),
     "renorm_uses_row_sums": ("s = V.sum(axis=0)                             # 1^t V",
                              "s = V.sum()                             # 1^t V"),
     "h_cost_without_lambda_term": ("column_cost(V, Z_mu) + lam * H_mu.sum(axis=0)",

@@ -314,6 +314,7 @@ def main(argv=None):
         if args.workload == "plain_large" and not args.no_mu_log:
             line["dna_vs_mu"] = convergence_log(dna, torch, prob, args.target_iters, args.engine,
                                                 args.log_file)
+            line["selection_forms"] = selection_forms(dna, torch, prob, 30)
         if args.workload == "plain_large":
             # the BF16 form at its own headline size (N=8192 T=32768 R=512), 20 iterations
             pspec = WORKLOADS["precision_large"]
@@ -379,7 +380,7 @@ def engine_code(dna, engine):
             "tensor": dna.DNA_ENGINE_TENSOR}[engine or "auto"]
 
 
-def _bind(dna, torch, prob, dtype, dev, engine="auto"):
+def _bind(dna, torch, prob, dtype, dev, engine="auto", selection="paper"):
     code = {"f32": dna.DNA_F32, "f64": dna.DNA_F64, "bf16": dna.DNA_BF16}[dtype]
     tdt = torch.float64 if dtype == "f64" else torch.float32
     V = torch.from_numpy(prob.V).to(dev, tdt)
@@ -392,6 +393,8 @@ def _bind(dna, torch, prob, dtype, dev, engine="auto"):
                          dna.make_opts(dtype=code, engine=engine_code(dna, engine)))
     dna.dna_set_stream(ctx, torch.cuda.current_stream())
     dna.dna_bind(ctx, V, W, H)
+    if selection == "descent":
+        dna.dna_set_selection(ctx, dna.DNA_SELECT_DESCENT)
     dna.dna_normalize(ctx, 1)                    # Algorithm 1 step 1
     return ctx, (V, W, H)
 
@@ -517,7 +520,8 @@ def measure(dna, torch, dist, prob, dtype, args, world, local, peaks, clocks, en
             "kl_end": kl_end}
 
 
-def run_logged(dna, torch, prob, dtype, engine, max_iters, target=None, algo="dna"):
+def run_logged(dna, torch, prob, dtype, engine, max_iters, target=None, algo="dna",
+               selection="paper"):
     """Up to max_iters iterations of one form (DNA, or MU with algo="mu"), d_KL after every
     iteration.  Each iteration is timed with CUDA events on the library's stream; the d_KL
     evaluations (and the selection read-back) are outside the events.  Stops early once
@@ -526,7 +530,7 @@ def run_logged(dna, torch, prob, dtype, engine, max_iters, target=None, algo="dn
     candidate."""
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
-    ctx, keep = _bind(dna, torch, prob, dtype, dev, engine)
+    ctx, keep = _bind(dna, torch, prob, dtype, dev, engine, selection)
     N, T = prob.V.shape
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     kls, secs, newton = [dna.dna_kl(ctx)], [0.0], []
@@ -580,6 +584,24 @@ def time_to_target(dna, torch, prob, iters, fp32_engine, workload):
                  "ms_per_iteration": sb[-1] / max(len(sb) - 1, 1) * 1e3, "kl_last": kb[-1]},
         "speedup": (t32 / tb) if (t32 and tb) else None,
     }
+
+
+def selection_forms(dna, torch, prob, iters):
+    """The paper's selection against descent selection (the Newton candidate against the
+    starting column; one candidate's cost per half-step) in the FP32 form on the CUDA-core
+    engine: time per iteration, d_KL after `iters` iterations, and the iterations and
+    seconds descent needs to reach the paper rule's final d_KL."""
+    kp, sp_, _ = run_logged(dna, torch, prob, "f32", "simt", iters)
+    kd, sd, nd = run_logged(dna, torch, prob, "f32", "simt", 2 * iters, target=kp[-1],
+                            selection="descent")
+    i_d, t_d = first_reach(kd, sd, kp[-1])
+    return {"engine": "simt (FP32 CUDA cores)", "iterations": iters,
+            "paper": {"ms_per_iteration": sp_[-1] / iters * 1e3, "kl_final": kp[-1],
+                      "sec": sp_[-1]},
+            "descent": {"ms_per_iteration": sd[-1] / max(len(sd) - 1, 1) * 1e3,
+                        "iterations_to_paper_final": i_d, "sec_to_paper_final": t_d,
+                        "newton_fraction_last": nd[-1] if nd else None},
+            "speedup_to_target": (sp_[-1] / t_d) if t_d else None}
 
 
 def convergence_log(dna, torch, prob, iters, engine, log_file=None):

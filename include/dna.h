@@ -186,6 +186,23 @@ int dna_step_H_fixed(dna_ctx* ctx, uint8_t* choice_out);
 int dna_step_H_adjoint(dna_ctx* ctx, const void* Hk, const uint8_t* choice,
                        const void* Hbar_next, void* Hbar_out, void* Vbar);
 
+/* Selection rules (dna_set_selection).  PAPER: Section 2.4 and Algorithm 1 steps 15 / 28,
+ * the Newton candidate is kept iff its cost is below the MU candidate's (both costs are
+ * evaluated).  DESCENT: the Newton candidate is kept iff its eq. 5 (eq. 4) cost is below
+ * that of the column (row) the half-step starts from, else the MU candidate.  MU never
+ * increases the eq. 5 cost (Section 2.1), so the cost still never increases, but only the
+ * Newton candidate's cost is evaluated: pass 1 accumulates the starting column's cost from
+ * the z it forms anyway, and pass 2 forms one candidate's z instead of two (Section 5
+ * names step damping that avoids cost evaluations as a way to speed DNA up).  Every column
+ * that PAPER gives to Newton, DESCENT does too. */
+#define DNA_SELECT_PAPER   0
+#define DNA_SELECT_DESCENT 1
+
+/* Choose the selection rule of later DNA half-steps (default PAPER).  DESCENT needs the
+ * CUDA-core engine (F32 or F64, dense V; else DNA_ERR_UNSUPPORTED) and allocates its cost
+ * buffer on first use.  With DESCENT, dna_get_costs gives (starting cost, Newton cost). */
+int dna_set_selection(dna_ctx* ctx, int mode);
+
 /* Copy the selection of the last DNA half-step to host memory: which = 0 gives T bytes
  * (column t of H took the Newton candidate iff out[t] = 1), which = 1 gives N bytes (per
  * row of W).  len must equal T (N).  Synchronises. */

@@ -61,6 +61,7 @@ def _load() -> ctypes.CDLL:
         "dna_bind_csr": (I, [P, P, P, P, P, P]),
         "dna_shard_rowsums": (I, [P, P]),
         "dna_check_wait_timeout": (I, [I64]),
+        "dna_set_selection": (I, [P, I]),
         "dna_shard_set_rowsums": (I, [P, P]),
         "dna_shard_H_begin": (I, [P, P]),
         "dna_shard_H_end": (I, [P, P]),
@@ -401,3 +402,11 @@ dna_shard_W_begin = _shard_call("dna_shard_W_begin")
 dna_shard_W_pass1 = _shard_call("dna_shard_W_pass1")
 dna_shard_W_pass2 = _shard_call("dna_shard_W_pass2")
 dna_shard_W_end = _shard_call("dna_shard_W_end")
+
+
+DNA_SELECT_PAPER = 0
+DNA_SELECT_DESCENT = 1
+
+
+def dna_set_selection(ctx: int, mode: int) -> None:
+    _check(LIB.dna_set_selection(ctx, mode), "dna_set_selection")

@@ -96,6 +96,10 @@ struct dna_ctx {
     void* Aseg = nullptr;
     void* Bseg = nullptr;
     double* dseg = nullptr;
+    // selection rule: DNA_SELECT_PAPER or DNA_SELECT_DESCENT (with the starting factor's
+    // per-column costs from pass 1, [splits][max(N, T)])
+    int selection = DNA_SELECT_PAPER;
+    double* dcur = nullptr;
     // profiling: event pairs around phases, launch counts
     unsigned prof_mask = 0;          // phases whose instances get an event pair
     std::vector<cudaEvent_t> ev_pool;
@@ -225,7 +229,8 @@ void free_all(dna_ctx* c) {
                     c->choice_h, c->choice_w, c->kl_dev, c->kl_part, c->status, c->Xk, c->Yk, c->Ytk,
                     c->Y2tk, c->Xmk, c->Xdk, c->Vp, c->cptr, c->ridx, c->cval, c->Yt, c->c0,
                     c->seg_col[0], c->seg_col[1], c->seg_k0[0], c->seg_k0[1], c->seg_k1[0],
-                    c->seg_k1[1], c->seg_ptr[0], c->seg_ptr[1], c->Aseg, c->Bseg, c->dseg};
+                    c->seg_k1[1], c->seg_ptr[0], c->seg_ptr[1], c->Aseg, c->Bseg, c->dseg,
+                    c->dcur};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t ev : c->ev_pool) cudaEventDestroy(ev);
@@ -595,6 +600,9 @@ int step_core(dna_ctx* c, int w, bool mu_only, bool prepared, int stop) {
     const bool tc = c->tc;
     const int sp1 = tc ? c->tsp1[w] : c->sp1[w], sp2 = tc ? c->tsp2[w] : c->sp2[w];
     int e = DNA_OK;
+    // descent selection (CUDA-core engine): pass 1 also gives the starting factor's costs,
+    // pass 2 evaluates the Newton candidate only
+    const bool descent = c->selection == DNA_SELECT_DESCENT && !mu_only && !tc;
     if (stop <= STOP_PASS1) {
         if (!prepared)
             if ((e = prep_step<Tp>(c, w, !mu_only))) return e;
@@ -606,7 +614,8 @@ int step_core(dna_ctx* c, int w, bool mu_only, bool prepared, int stop) {
                                                           c->tper1[w], !mu_only, c->status, st)
                                : dna::TcBf16::pass1(tc_operands(c, w), c->maps[w], A, B, sp1,
                                                     c->tper1[w], !mu_only, c->status, st);
-            return S::pass1(v, A, B, sp1, c->per1[w], !mu_only, c->status, st);
+            return S::pass1(v, A, B, sp1, c->per1[w], !mu_only, c->status, st,
+                            descent ? c->dcur : nullptr);
         });
         if (e || stop == STOP_PASS1) return e;
         if (mu_only)   // eq. 11 in place, with the first level of the step 16 / 29 sums
@@ -637,6 +646,7 @@ int step_core(dna_ctx* c, int w, bool mu_only, bool prepared, int stop) {
                                : dna::TcBf16::pass2_large(tc_operands(c, w), c->maps[w],
                                                           c->dpart, sp2, c->tper2[w], c->status,
                                                           st);
+            if (descent) return S::pass2_one(v, Xdna, c->dpart, sp2, c->per2[w], c->status, st);
             return S::pass2(v, Xmu, Xdna, c->dpart, sp2, c->per2[w], c->status, st);
         });
         if (e || stop == STOP_PASS2) return e;
@@ -646,7 +656,7 @@ int step_core(dna_ctx* c, int w, bool mu_only, bool prepared, int stop) {
     return phase(c, DNA_PHASE_SELECT, 1, [&] {
         return S::select_fused(v, Xmu, Xdna, c->dpart, slots, w ? c->choice_w : c->choice_h,
                                w ? c->dfin_w : c->dfin_h, c->gpart, w ? c->o.rho : c->o.lambda,
-                               st);
+                               st, descent ? c->dcur : nullptr, sp1);
     });
 }
 
@@ -857,7 +867,7 @@ int phase(dna_ctx* c, int ph, int nlaunch, F&& f) {
 // ---------------------------------------------------------------- column shards
 int shard_ready(dna_ctx* c) {
     if (int e = check_ready(c)) return e;
-    if (c->sparse || c->host_mode) return DNA_ERR_UNSUPPORTED;
+    if (c->sparse || c->host_mode || c->selection != DNA_SELECT_PAPER) return DNA_ERR_UNSUPPORTED;
     return set_device(c) ? DNA_ERR_CUDA : DNA_OK;
 }
 
@@ -1169,6 +1179,19 @@ int mu_iterate(dna_ctx* c, int iters) {
                               : half_step<float>(c, 1, true, true, more);
         if (e) return e;
     }
+    return DNA_OK;
+}
+
+int dna_set_selection(dna_ctx* c, int mode) {
+    if (!c || (mode != DNA_SELECT_PAPER && mode != DNA_SELECT_DESCENT)) return DNA_ERR_ARG;
+    if (mode == DNA_SELECT_DESCENT && (c->tc || c->sparse)) return DNA_ERR_UNSUPPORTED;
+    if (set_device(c)) return DNA_ERR_CUDA;
+    if (mode == DNA_SELECT_DESCENT && !c->dcur) {
+        const int sp = std::max(c->sp1[0], c->sp1[1]);
+        if (dmalloc(&c->dcur, sizeof(double) * (size_t)sp * std::max(c->N, c->T)))
+            return DNA_ERR_ALLOC;
+    }
+    c->selection = mode;
     return DNA_OK;
 }
 

@@ -65,9 +65,10 @@ template <typename Tp> struct Simt {
                              cudaStream_t st);
     // x(r, o) *= f_r^-1 ... : X scaled by 1/f_r, Y scaled by f_r (steps 1, 16, 29)
     static int rescale(const View& v, const double* f, cudaStream_t st);
-    // pass 1: raw sums Apart = sum_s y q, Bpart = sum_s y^2 qbar (split over s)
+    // pass 1: raw sums Apart = sum_s y q, Bpart = sum_s y^2 qbar (split over s); with dcur,
+    // also the starting factor's per-column costs [splits][O] (descent selection)
     static int pass1(const View& v, Tp* Apart, Tp* Bpart, int splits, int64_t s_per,
-                     bool with_b, int* status, cudaStream_t st);
+                     bool with_b, int* status, cudaStream_t st, double* dcur = nullptr);
     // candidates: MU and renormalised Newton candidates, laid out [R][O]
     static int candidates(const View& v, const double* c, const Tp* Apart, const Tp* Bpart,
                           int splits, Tp* Xmu, Tp* Xdna, double eps, double alpha,
@@ -78,6 +79,9 @@ template <typename Tp> struct Simt {
     // pass 2: per-column costs of the two candidates, float64 partials [splits][2][O]
     static int pass2(const View& v, const Tp* Xmu, const Tp* Xdna, double* dpart, int splits,
                      int64_t s_per, int* status, cudaStream_t st);
+    // pass 2 for one candidate X ([R][O]): its per-column costs, dpart [splits][O]
+    static int pass2_one(const View& v, const Tp* X, double* dpart, int splits, int64_t s_per,
+                         int* status, cudaStream_t st);
     // selection: x(r, o) <- Newton if d_dna < d_mu else MU, each d being the pass-2 sum
     // plus reg * sum_r x (the eq. 5 penalty; reg = lambda for H, rho for W); choice and
     // final costs
@@ -112,9 +116,12 @@ template <typename Tp> struct Simt {
     // they stream in (no split_sum pass needed)
     static bool cand_in_registers(int64_t R);
     // Selection as above, plus fpart[glue_parts(O)][R]: per-block sums of the new X.
+    // With dcur: descent selection (dpart = Newton costs [splits][O], dcur = the starting
+    // factor's [cur_splits][O]).
     static int select_fused(const View& v, const Tp* Xmu, const Tp* Xdna, const double* dpart,
                             int splits, uint8_t* choice, double* dfin, double* fpart,
-                            double reg, cudaStream_t st);
+                            double reg, cudaStream_t st, const double* dcur = nullptr,
+                            int cur_splits = 0);
     // out[r] = in[r] + reg (an exact zero replaced by 1)
     static int add_reg(const double* in, int64_t R, double reg, double* out, cudaStream_t st);
     // MU (eq. 11) in place from the pass-1 split partials, plus fpart as select_fused

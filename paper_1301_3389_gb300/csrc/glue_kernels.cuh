@@ -331,13 +331,20 @@ constexpr size_t select_smem(int64_t R) {
 // new x(r, o) (float64), the first level of the normalisation sums.  Each cost is the
 // column's eq. 5 sub-problem cost less a constant: the pass-2 slots plus
 // reg * sum_r x(r, o) of that candidate (reg = lambda for H, rho for W; eq. 5 and eq. 4).
+//
+// Descent selection (dcur given): the Newton candidate is compared with the starting column
+// instead of the MU candidate: dpart holds the Newton costs only ([splits][O]), dcur the
+// starting column's ([cur_splits][O]), and the penalty of the starting column is
+// reg * sum_r x(r, o) of the current X.  dfin receives (d_start, d_dna).
 template <typename Tp>
 __global__ void __launch_bounds__(256) k_select_fused(View v, const Tp* __restrict__ Xmu,
                                                       const Tp* __restrict__ Xdna,
                                                       const double* __restrict__ dpart,
                                                       int splits, uint8_t* __restrict__ choice,
                                                       double* __restrict__ dfin,
-                                                      double* __restrict__ fpart, double reg) {
+                                                      double* __restrict__ fpart, double reg,
+                                                      const double* __restrict__ dcur,
+                                                      int cur_splits) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int64_t R = v.R, O = v.O;
     Tp* xs = reinterpret_cast<Tp*>(smem_raw);                   // [R][TO + 1]
@@ -348,7 +355,8 @@ __global__ void __launch_bounds__(256) k_select_fused(View v, const Tp* __restri
     // the cost slots of column o: warp ty adds the contiguous range [ty k, (ty + 1) k)
     // (k = ceil(splits / 8)), warp 0 the eight range sums in order
     __shared__ double dsum[2][8][TO];
-    {
+    const Tp* __restrict__ Xcur = static_cast<const Tp*>(v.X);
+    if (dcur == nullptr) {
         const int per = (splits + 7) / 8, sp0 = ty * per, sp1 = min(splits, sp0 + per);
         double dm = 0.0, dd = 0.0;
         if (live)
@@ -358,6 +366,16 @@ __global__ void __launch_bounds__(256) k_select_fused(View v, const Tp* __restri
             }
         dsum[0][ty][tx] = dm;
         dsum[1][ty][tx] = dd;
+    } else {
+        const int per = (splits + 7) / 8, sp0 = ty * per, sp1 = min(splits, sp0 + per);
+        const int pc = (cur_splits + 7) / 8, c0 = ty * pc, c1 = min(cur_splits, c0 + pc);
+        double dm = 0.0, dd = 0.0;
+        if (live) {
+            for (int sp = c0; sp < c1; ++sp) dm += dcur[(int64_t)sp * O + o];
+            for (int sp = sp0; sp < sp1; ++sp) dd += dpart[(int64_t)sp * O + o];
+        }
+        dsum[0][ty][tx] = dm;
+        dsum[1][ty][tx] = dd;
     }
     // the eq. 5 penalty: warp ty sums r = ty, ty + 8, ... of both candidates (float64)
     __shared__ double psum[2][8][TO];
@@ -365,7 +383,7 @@ __global__ void __launch_bounds__(256) k_select_fused(View v, const Tp* __restri
         double pm = 0.0, pd = 0.0;
         if (live)
             for (int64_t r = ty; r < R; r += 8) {
-                pm += (double)Xmu[r * O + o];
+                pm += dcur ? (double)Xcur[r * v.xr + o * v.xo] : (double)Xmu[r * O + o];
                 pd += (double)Xdna[r * O + o];
             }
         psum[0][ty][tx] = pm;

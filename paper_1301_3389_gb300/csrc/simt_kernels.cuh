@@ -96,11 +96,15 @@ struct Pass1Cfg {
 
 // Pass 1: raw A and B sums for one (o-block, r-block, s-split).
 // grid = (ceil(O / OB), ceil(R / RB), splits); Apart/Bpart are [splits][R][O].
+// dcur (may be null): the r-block-0 tiles also write the starting factor's per-column cost
+// d'(o) = sum_{v>0} (-v log z) + sum z over their split of s into dcur[split][O] (float64;
+// the terms summed in the element type within a chunk), for descent selection.
 template <typename Tp, int RB, bool WITH_B>
 __device__ __forceinline__ void pass1_tile(const View& v, Tp* __restrict__ Apart,
                                            Tp* __restrict__ Bpart, int64_t s_per,
                                            int* __restrict__ status, int64_t tile_o, int64_t tile_r,
-                                           int64_t tile_s, unsigned char* smem_raw) {
+                                           int64_t tile_s, unsigned char* smem_raw,
+                                           double* __restrict__ dcur = nullptr) {
     using C = Pass1Cfg<Tp, RB>;
     Tp* Xs = reinterpret_cast<Tp*>(smem_raw);  // [RB][LD]  x(r, o) of the current r-piece
     Tp* Yt = Xs + RB * LD;                     // [RB][LD]  y(s, r) transposed: Yt[r][s]
@@ -128,6 +132,8 @@ __device__ __forceinline__ void pass1_tile(const View& v, Tp* __restrict__ Apart
 
     if (npieces == 1) load_tile<Tp, RB, OB>(Xs, X, v.xr, v.xo, 0, o0, v.R, v.O);
     int bad = 0;
+    const bool want_cur = dcur != nullptr && tile_r == 0;
+    double dsum[4] = {0.0, 0.0, 0.0, 0.0};   // this thread's columns zo .. zo + 3
 
     for (int64_t s0 = s_begin; s0 < s_end; s0 += SB) {
         Tp z[4][4], vpre[4][4];
@@ -146,6 +152,19 @@ __device__ __forceinline__ void pass1_tile(const View& v, Tp* __restrict__ Apart
             __syncthreads();
             z_tile<Tp, RB>(Yt, Xs, zs, zo, z);
             __syncthreads();
+        }
+        if (want_cur) {   // the starting column's cost terms (steps 9 / 14 at the current x)
+            Tp t[4] = {Tp(0), Tp(0), Tp(0), Tp(0)};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const Tp vv = vpre[i][j], zz = z[i][j];
+                    if (s0 + zs + i < s_end)
+                        t[j] += vv > Tp(0) ? zz - vv * dev_log(zz) : zz;
+                }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) dsum[j] += (double)t[j];
         }
         // q = v / z and qbar = v / z^2, zero where v = 0 (note after Algorithm 1): one
         // reciprocal per element, branch-free, rows stored as vectors (no bank conflicts)
@@ -188,6 +207,21 @@ __device__ __forceinline__ void pass1_tile(const View& v, Tp* __restrict__ Apart
         __syncthreads();
     }
     if (bad) atomicOr(status, STATUS_NONFINITE);
+    if (want_cur) {   // the 16 threads of each column group, added in a fixed order
+        double* red = reinterpret_cast<double*>(smem_raw);   // [16][OB], over Xs / Yt
+#pragma unroll
+        for (int j = 0; j < 4; ++j) red[(tid / 16) * OB + zo + j] = dsum[j];
+        __syncthreads();
+        if (tid < OB) {
+            double d = 0.0;
+            for (int g = 0; g < 16; ++g) d += red[g * OB + tid];
+            const int64_t o = o0 + tid;
+            if (o < v.O) {
+                dcur[tile_s * v.O + o] = d;
+                if (!isfinite(d)) atomicOr(status, STATUS_NONFINITE);
+            }
+        }
+    }
 
     const int64_t base = tile_s * v.R;
 #pragma unroll
@@ -209,10 +243,10 @@ __device__ __forceinline__ void pass1_tile(const View& v, Tp* __restrict__ Apart
 template <typename Tp, int RB, bool WITH_B>
 __global__ void __launch_bounds__(NT, sizeof(Tp) == 4 ? 2 : 1)
     k_pass1(View v, Tp* __restrict__ Apart, Tp* __restrict__ Bpart, int64_t s_per,
-            int* __restrict__ status) {
+            int* __restrict__ status, double* __restrict__ dcur) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     pass1_tile<Tp, RB, WITH_B>(v, Apart, Bpart, s_per, status, blockIdx.x, blockIdx.y, blockIdx.z,
-                               smem_raw);
+                               smem_raw, dcur);
 }
 
 template <typename Tp, int RB, int NC>

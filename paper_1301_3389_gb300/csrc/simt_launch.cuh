@@ -30,17 +30,17 @@ inline int prep_smem(Kern k, size_t bytes) {
 
 template <typename Tp, int RB>
 int pass1_rb(const View& v, Tp* A, Tp* B, int splits, int64_t s_per, bool with_b, int* status,
-             cudaStream_t st) {
+             cudaStream_t st, double* dcur) {
     const size_t smem = Pass1Cfg<Tp, RB>::smem;
     dim3 grid((unsigned)((v.O + OB - 1) / OB), (unsigned)((v.R + RB - 1) / RB), (unsigned)splits);
     if (with_b) {
         auto k = k_pass1<Tp, RB, true>;
         if (prep_smem(k, smem)) return DNA_ERR_CUDA;
-        k<<<grid, NT, smem, st>>>(v, A, B, s_per, status);
+        k<<<grid, NT, smem, st>>>(v, A, B, s_per, status, dcur);
     } else {
         auto k = k_pass1<Tp, RB, false>;
         if (prep_smem(k, smem)) return DNA_ERR_CUDA;
-        k<<<grid, NT, smem, st>>>(v, A, B, s_per, status);
+        k<<<grid, NT, smem, st>>>(v, A, B, s_per, status, dcur);
     }
     return launch_status();
 }
@@ -142,13 +142,13 @@ int Simt<Tp>::rescale(const View& v, const double* f, cudaStream_t st) {
 
 template <typename Tp>
 int Simt<Tp>::pass1(const View& v, Tp* A, Tp* B, int splits, int64_t s_per, bool with_b,
-                    int* status, cudaStream_t st) {
+                    int* status, cudaStream_t st, double* dcur) {
     switch (simt::rblock_for<Tp>(v.R)) {
-        case 32: return simt::pass1_rb<Tp, 32>(v, A, B, splits, s_per, with_b, status, st);
-        case 64: return simt::pass1_rb<Tp, 64>(v, A, B, splits, s_per, with_b, status, st);
+        case 32: return simt::pass1_rb<Tp, 32>(v, A, B, splits, s_per, with_b, status, st, dcur);
+        case 64: return simt::pass1_rb<Tp, 64>(v, A, B, splits, s_per, with_b, status, st, dcur);
         default:
             if constexpr (sizeof(Tp) == 4)
-                return simt::pass1_rb<Tp, 128>(v, A, B, splits, s_per, with_b, status, st);
+                return simt::pass1_rb<Tp, 128>(v, A, B, splits, s_per, with_b, status, st, dcur);
             return DNA_ERR_UNSUPPORTED;
     }
 }
@@ -171,6 +171,12 @@ template <typename Tp>
 int Simt<Tp>::pass2(const View& v, const Tp* Xmu, const Tp* Xdna, double* dpart, int splits,
                     int64_t s_per, int* status, cudaStream_t st) {
     return simt::pass2_any<Tp, 2, false>(v, Xmu, Xdna, v.O, 1, dpart, splits, s_per, status, st);
+}
+
+template <typename Tp>
+int Simt<Tp>::pass2_one(const View& v, const Tp* X, double* dpart, int splits, int64_t s_per,
+                        int* status, cudaStream_t st) {
+    return simt::pass2_any<Tp, 1, false>(v, X, X, v.O, 1, dpart, splits, s_per, status, st);
 }
 
 template <typename Tp>
@@ -331,12 +337,12 @@ int Simt<Tp>::split_sum(Tp* A, Tp* B, int64_t R, int64_t O, int splits, cudaStre
 template <typename Tp>
 int Simt<Tp>::select_fused(const View& v, const Tp* Xmu, const Tp* Xdna, const double* dpart,
                            int splits, uint8_t* choice, double* dfin, double* fpart,
-                           double reg, cudaStream_t st) {
+                           double reg, cudaStream_t st, const double* dcur, int cur_splits) {
     const size_t smem = glue::select_smem<Tp>(v.R);
     auto k = glue::k_select_fused<Tp>;
     if (simt::prep_smem(k, smem)) return DNA_ERR_CUDA;
     k<<<(unsigned)glue_parts(v.O), dim3(32, 8), smem, st>>>(v, Xmu, Xdna, dpart, splits, choice,
-                                                           dfin, fpart, reg);
+                                                           dfin, fpart, reg, dcur, cur_splits);
     return simt::launch_status();
 }
 

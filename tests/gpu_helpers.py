@@ -156,6 +156,7 @@ class GpuProblem:
                 "bf16": dna.DNA_BF16}[dtype]
         if dtype == "f32t":
             opts.setdefault("engine", dna.DNA_ENGINE_TENSOR)
+        selection = opts.pop("selection", None)
         self.tdt = torch.float64 if dtype == "f64" else torch.float32
         self.N, self.T = V.shape
         self.R = W.shape[1]
@@ -165,6 +166,8 @@ class GpuProblem:
         self.ctx = dna.dna_create(self.N, self.T, self.R, dna.make_opts(dtype=code, **opts))
         dna.dna_set_stream(self.ctx)
         dna.dna_bind(self.ctx, self.V, self.W, self.H)
+        if selection == "descent":
+            dna.dna_set_selection(self.ctx, dna.DNA_SELECT_DESCENT)
 
     def WH(self):
         self.torch.cuda.synchronize()
@@ -213,10 +216,11 @@ def one_step_check(gp: GpuProblem, which, W0, H0, opts=None, label=""):
     rho = opts.get("rho", 0.0)
     lam = opts.get("lam", 0.0)
     V = gp_V(gp)
+    sel = opts.get("selection", "paper")
     if which == 0:
-        half = o.h_half_step(V, W0, H0, eps, alpha, lam)
+        half = o.h_half_step(V, W0, H0, eps, alpha, lam, selection=sel)
     else:
-        half = o.w_half_step(V, W0, H0, eps, alpha, rho)
+        half = o.w_half_step(V, W0, H0, eps, alpha, rho, selection=sel)
     mask, _ = replay_choice(half, gp.choice(which), gp.kind)
     half = dataclasses.replace(half, choice=mask)
     Wg, Hg = gp.WH()
@@ -241,15 +245,16 @@ def step_pair(gp: GpuProblem, W, H, which, mu=False, opts=None):
             W2, H2 = o.mu_step_w(gp_V(gp), W, H, rho, lam)
         return W2, H2, 0
     V = gp_V(gp)
+    sel = opts.get("selection", "paper")
     Wg0, Hg0 = gp.WH()            # the GPU's state before the step, for the one-step check
     if which == 0:
         dna.dna_step_H(gp.ctx)
-        half = o.h_half_step(V, W, H, eps, alpha, lam)
+        half = o.h_half_step(V, W, H, eps, alpha, lam, selection=sel)
         mask, nflip = replay_choice(half, gp.choice(0), gp.kind)
         W2, H2, _ = o.dna_step_h(V, W, H, eps, alpha, rho, lam, choice=mask)
     else:
         dna.dna_step_W(gp.ctx)
-        half = o.w_half_step(V, W, H, eps, alpha, rho)
+        half = o.w_half_step(V, W, H, eps, alpha, rho, selection=sel)
         mask, nflip = replay_choice(half, gp.choice(1), gp.kind)
         W2, H2, _ = o.dna_step_w(V, W, H, eps, alpha, rho, lam, choice=mask)
     ratio = one_step_check(gp, which, Wg0, Hg0, opts, "step")

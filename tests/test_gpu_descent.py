@@ -36,9 +36,12 @@ def test_descent_matches_oracle(kind, reg):
                 # the two costs the GPU compared, from its own starting state
                 half = (o.h_half_step(V, Wg0, Hg0, lam=reg, selection="descent") if which == 0
                         else o.w_half_step(V, Wg0, Hg0, rho=reg, selection="descent"))
+                # d' sums terms of size ~ v (|log z| + 1) and can cross zero: its error scales
+                # with |d'| + sum v of the column (row), not with d'
                 dc, dd = gp.costs(which)
-                np.testing.assert_allclose(dc, half.d_cur, rtol=COST_RTOL[kind])
-                np.testing.assert_allclose(dd, half.d_dna, rtol=COST_RTOL[kind])
+                scale = V.sum(axis=0 if which == 0 else 1) + 1.0
+                for got, ref in ((dc, half.d_cur), (dd, half.d_dna)):
+                    assert np.all(np.abs(got - ref) <= COST_RTOL[kind] * (np.abs(ref) + scale))
             if reg == 0.0:
                 kl = gp.dna.dna_kl(gp.ctx)
                 assert kl <= prev * (1 + 1e-7), (kl, prev)          # never increases

@@ -452,7 +452,10 @@ def measure(dna, torch, dist, prob, dtype, args, world, local, peaks, clocks, en
     # roofline of the dominant kernel (largest share of the timed region)
     dom = max(("pass1", "pass2"), key=lambda p: phases[p][0])
     dom_ms, dom_launches = phases[dom]
-    per_launch_s = dom_ms / max(dom_launches, 1) / 1e3
+    # one instance of each pass per half-step (an instance may be several kernel launches:
+    # pass 1 of the BF16 form at R > 128 is the ratios and the contraction kernels)
+    instances = 2 * args.steps
+    per_launch_s = dom_ms / instances / 1e3
     flops = (6 if dom == "pass1" else 4) * R * N * T    # per launch (H or W half-step)
     alg_bytes = 4 * N * T + (8 * R * max(N, T) if dom == "pass1" else 16 * max(N, T))
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
@@ -511,6 +514,7 @@ def measure(dna, torch, dist, prob, dtype, args, world, local, peaks, clocks, en
     roof["algorithmic_flops_per_launch"] = flops
     roof["algorithmic_bytes_per_launch"] = alg_bytes
     roof["launch_ms"] = per_launch_s * 1e3
+    roof["kernels_per_pass"] = dom_launches / instances
     roof["phase_share"] = {p: round(prof_phases[p][0] / prof_ms, 4)
                            for p in ("pass1", "candidates", "pass2", "select", "sums", "operands")}
     roof["phase_share_note"] = (f"separate pass of {prof_iters} iterations with every phase "

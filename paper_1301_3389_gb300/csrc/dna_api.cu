@@ -68,6 +68,9 @@ struct dna_ctx {
     void* Y2tk = nullptr;
     void* Xmk = nullptr;             // bf16 [max O_pad][rp]
     void* Xdk = nullptr;
+    void* Qg = nullptr;              // BF16 form at RP > 128: Q, Qbar rows [max O_pad][ldq]
+    void* Qbg = nullptr;
+    int64_t ldq[2] = {0, 0};         // of the H view (0) and W view (1)
     void* Vp = nullptr;              // aligned copy of V when V's rows are not 16-byte aligned
     int64_t ldvp = 0;
     dna::TcMaps maps[2];             // TMA descriptors of the H view (0) and W view (1)
@@ -202,9 +205,9 @@ void plan_all(dna_ctx* c) {
             c->pad_s[w] = (Sdim + tch - 1) / tch * tch;
             // partial A, B sums per split relative to V's bytes: 2 R / S
             const double part = 2.0 * (double)c->R / (double)Sdim;
-            // CTA rows per o-block of pass 1: r-blocks of the K-streamed kernels, or the A and
-            // B halves of the split FP32 kernel
-            const int64_t rblocks = c->split ? 2 : (c->rp > 128 ? c->rp / 128 : 1);
+            // CTA rows per o-block of pass 1: the 256-wide r-blocks of the contraction kernel
+            // (RP > 128), or the A and B halves of the split FP32 kernel
+            const int64_t rblocks = c->split ? 2 : (c->rp > 128 ? c->rp / 256 : 1);
             // the split form, and pass 1 at ranks above 128, stream s in chunks of 128
             const int sch = c->split ? (int)SPLIT_CHUNK : tch;
             const int sch1 = c->split || c->rp > 128 ? (int)SPLIT_CHUNK : tch;
@@ -227,7 +230,7 @@ void free_all(dna_ctx* c) {
     void* ptrs[] = {c->own_V, c->own_W, c->own_H, c->Vt, c->colsum_v, c->rowsum_v, c->c, c->sig,
                     c->fwork, c->gpart, c->vpart, c->Apart, c->Bpart, c->Xmu, c->Xdna, c->dpart, c->dfin_h, c->dfin_w,
                     c->choice_h, c->choice_w, c->kl_dev, c->kl_part, c->status, c->Xk, c->Yk, c->Ytk,
-                    c->Y2tk, c->Xmk, c->Xdk, c->Vp, c->cptr, c->ridx, c->cval, c->Yt, c->c0,
+                    c->Y2tk, c->Xmk, c->Xdk, c->Vp, c->Qg, c->Qbg, c->cptr, c->ridx, c->cval, c->Yt, c->c0,
                     c->seg_col[0], c->seg_col[1], c->seg_k0[0], c->seg_k0[1], c->seg_k1[0],
                     c->seg_k1[1], c->seg_ptr[0], c->seg_ptr[1], c->Aseg, c->Bseg, c->dseg,
                     c->dcur};
@@ -284,6 +287,15 @@ int alloc_workspace(dna_ctx* c) {
         e |= dmalloc(&c->Y2tk, b * np * (size_t)ps);
         e |= dmalloc(&c->Xmk, b * np * (size_t)po);
         e |= dmalloc(&c->Xdk, b * np * (size_t)po);
+        if (!c->split && c->rp > 128) {   // pass 1 in two kernels: the Q, Qbar workspace
+            size_t q = 0;
+            for (int w = 0; w < 2; ++w) {
+                c->ldq[w] = ((w ? T : N) + 127) / 128 * 128;
+                q = std::max(q, (size_t)(c->pad_o[w] * c->ldq[w]));
+            }
+            e |= dmalloc(&c->Qg, b * q);
+            e |= dmalloc(&c->Qbg, b * q);
+        }
     }
     if (e != DNA_OK) return DNA_ERR_ALLOC;
     // the padding columns of the transposed copy of V are read by 16-byte copies: zero them
@@ -463,6 +475,7 @@ dna::TcOperands tc_operands(const dna_ctx* c, int wstep) {
     op.Xmk = c->Xmk; op.Xdk = c->Xdk;
     op.plane = c->plane;
     op.ctas = c->num_sms;
+    op.Qg = c->Qg; op.Qbg = c->Qbg; op.ldq = c->ldq[wstep];
     tc_v(c, wstep, &op.V, &op.vs);
     return op;
 }

@@ -186,11 +186,18 @@ struct TcOperands {
     // elements after it, a lo plane (x = hi + lo, both bf16); 0 in the BF16 form
     int64_t plane;
     int ctas;   // CTAs of the persistent kernels (the SM count)
+    // BF16 form at RP > 128: bf16 workspace rows Q[o][s], Qbar[o][s] ([O_pad][ldq], ldq a
+    // multiple of 128) written by the ratios kernel of pass 1 and read by its contraction
+    void* Qg;
+    void* Qbg;
+    int64_t ldq;
 };
 
 // TMA descriptors of one half-step view (built once per bound problem).
 struct TcMaps {
     CUtensorMap x, y, yt, y2t, v, xm, xd;
+    CUtensorMap q, qb;                                 // Q, Qbar workspace (RP > 128)
+    CUtensorMap y128, yt256, y2t256;                   // larger boxes of Y, Yt, Y2t (RP > 128)
     CUtensorMap x_l, y_l, yt_l, y2t_l, xm_l, xd_l;   // lo planes (FP32 form, tensor cores)
 };
 
@@ -212,9 +219,11 @@ struct TcBf16 {
                      int splits, int64_t s_per, bool with_b, int* status, cudaStream_t st);
     // pass 1 at padded rank 256 or 512 (tc_ks.cu): persistent CTAs over (r-block of 128,
     // o-block, split) tiles; s_per must be a multiple of 128
-    static int pass1_large(const TcOperands& op, const TcMaps& maps, float* Apart,
-                           float* Bpart, int splits, int64_t s_per, bool with_b, int* status,
-                           cudaStream_t st);
+    // pass 1 at RP in {256, 512} as two kernels (tc_mat.cu): Z once per (o-block, chunk) with
+    // q, qbar written to the Q, Qbar workspace, then the dual GEMM over 256-wide r-blocks;
+    // Apart/Bpart [splits][R][O] with splits = ceil(S / s_per), s_per a multiple of 64
+    static int pass1_mat(const TcOperands& op, const TcMaps& maps, float* Apart, float* Bpart,
+                         int splits, int64_t s_per, bool with_b, int* status, cudaStream_t st);
     // pass 2 at padded rank 512 (tc_ks.cu): persistent CTAs over (o-block, split) tiles,
     // s_per a multiple of 128, cost slots dpart[4 splits][2][O]
     static int pass2_large(const TcOperands& op, const TcMaps& maps, double* dpart, int slots,

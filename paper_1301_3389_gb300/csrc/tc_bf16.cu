@@ -445,6 +445,14 @@ int TcBf16::make_maps(TcMaps* m, const TcOperands& op, const float* V, int64_t v
     if (!e)
         e = make_map(&m->v, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, V, (uint64_t)op.O, (uint64_t)op.S,
                      (uint64_t)vs * 4, OBLK, SCH, CU_TENSOR_MAP_SWIZZLE_NONE);
+    if (!e && op.Qg) {      // the Q, Qbar workspace of pass 1 at RP > 128, and larger boxes
+        e = make_map(&m->q, BF, op.Qg, (uint64_t)op.ldq, op.O_pad, (uint64_t)op.ldq * 2, 64, OBLK, SW);
+        if (!e) e = make_map(&m->qb, BF, op.Qbg, (uint64_t)op.ldq, op.O_pad, (uint64_t)op.ldq * 2, 64,
+                             OBLK, SW);
+        if (!e) e = make_map(&m->y128, BF, op.Yk, rp, op.S_pad, rp * 2, 64, 128, SW);
+        if (!e) e = make_map(&m->yt256, BF, op.Ytk, op.S_pad, rp, op.S_pad * 2, SCH, 256, SW);
+        if (!e) e = make_map(&m->y2t256, BF, op.Y2tk, op.S_pad, rp, op.S_pad * 2, SCH, 256, SW);
+    }
     if (!e && op.plane) {   // lo planes of the split FP32 form
         const bf16* yl = static_cast<const bf16*>(op.Yk) + op.plane;
         const bf16* ytl = static_cast<const bf16*>(op.Ytk) + op.plane;
@@ -497,7 +505,7 @@ int TcBf16::pass1(const TcOperands& op, const TcMaps& maps, float* Apart, float*
         return with_b ? tc::launch_pass1<128, true>(a, maps, op.O_pad, splits, st)
                       : tc::launch_pass1<128, false>(a, maps, op.O_pad, splits, st);
     if (rp == 256 || rp == 512)
-        return pass1_large(op, maps, Apart, Bpart, splits, s_per, with_b, status, st);
+        return pass1_mat(op, maps, Apart, Bpart, splits, s_per, with_b, status, st);
     return DNA_ERR_UNSUPPORTED;
 }
 

@@ -230,6 +230,7 @@ def main(argv=None):
     ap.add_argument("--no-c3-target", action="store_true")
     ap.add_argument("--no-mu-log", action="store_true")
     ap.add_argument("--no-sparse", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--sharded", action="store_true",
                     help="one problem split by columns over the ranks (strong scaling)")
     ap.add_argument("--log-file", default=None, help="per-iteration DNA/MU log (text)")
@@ -337,6 +338,18 @@ def main(argv=None):
                 line["precision_form"]["time_to_target"] = time_to_target(
                     dna, torch, pprob, args.c3_iters, eng, "precision_large")
             del pprob
+        if args.workload == "plain_large" and not args.no_batched:
+            # the batching form: 512 uneven problems, one grouped launch per phase, CUDA graph
+            bres = measure_batched(dna, torch, workloads.batched(512, seed=rank),
+                                   max(3, min(args.steps, 10)), args.warmup, peaks)
+            line["batched_form"] = {
+                "value": max(3, min(args.steps, 10)) / (bres["ms"] / 1e3),
+                "unit": "grouped DNA iterations/s (all 512 problems)",
+                "ms_per_step": bres["ms"] / max(3, min(args.steps, 10)),
+                "split_rows": bres["rows"], "gpu_launches": bres["launches"],
+                "roofline": bres["roofline"],
+                "config": {"workload": "batched", "desc": BATCHED_DESC, "sum_NT": bres["nt"],
+                           "engine": "simt grouped + CUDA graph"}}
         if args.workload == "plain_large" and not args.no_sparse:
             sp = workloads.sparse_tdt2(rank)
             line["sparse_form"] = measure_sparse(dna, torch, sp, max(3, min(args.steps, 50)),
@@ -808,6 +821,55 @@ def run_sharded(args, world, rank, local):
     return 0
 
 
+def measure_batched(dna, torch, probs, steps, warmup, peaks):
+    """Grouped DNA iterations of all problems (every phase one persistent grouped launch,
+    the iteration replayed as a CUDA graph, split sizes autotuned), timed with CUDA events."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    V = [torch.from_numpy(p.V).to(dev) for p in probs]
+    W = [torch.from_numpy(p.W).to(dev) for p in probs]
+    H = [torch.from_numpy(p.H).to(dev) for p in probs]
+    shapes = [p.shape for p in probs]
+    g = dna.dna_group_create([s[0] for s in shapes], [s[1] for s in shapes], [s[2] for s in shapes])
+    stream = torch.cuda.current_stream()
+    try:
+        dna.dna_group_set_stream(g, stream)
+        dna.dna_group_bind(g, V, W, H)
+        dna.dna_group_normalize(g, 1)
+        rows = dna.dna_group_autotune(g, 2)
+        dna.dna_group_use_graph(g, True)
+        kl0 = dna.dna_group_kl(g, len(probs))
+        dna.dna_group_iterate(g, warmup)
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        dna.dna_group_iterate(g, steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        kl1 = dna.dna_group_kl(g, len(probs))
+        launches = dna.dna_group_launches_per_iteration(g) * steps
+    finally:
+        dna.dna_group_destroy(g)
+    nt = sum(s[0] * s[1] for s in shapes)
+    alg_bytes = 4 * 4 * nt          # V read by both passes of both half-steps, float32
+    flops = sum(20 * s[2] * s[0] * s[1] for s in shapes)   # 10 R flop per element per half-step
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    alu = SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    step_s = ms / steps / 1e3
+    achieved = flops / step_s / 1e12
+    return {"ms": ms, "rows": rows, "launches": launches, "kl0": kl0, "kl1": kl1, "nt": nt,
+            "roofline": {"bound": "alu", "kernel": "whole grouped iteration",
+                         "achieved": achieved, "peak": alu, "unit": "TFLOP/s",
+                         "frac": achieved / alu, "traffic": None,
+                         "algorithmic_flops_per_step": flops,
+                         "algorithmic_bytes_per_step": alg_bytes,
+                         "hbm_frac": alg_bytes / step_s / 1e9 / hbm,
+                         "peak_source": (f"derived: {SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes "
+                                         f"x 2 flop x {sm_max:.0f} MHz")}}
+
+
 def run_batched(args, world, rank, local):
     """The batching form: one step = one DNA iteration of all 512 problems, every phase one
     grouped launch, the iteration replayed as a CUDA graph, split sizes autotuned."""
@@ -820,68 +882,31 @@ def run_batched(args, world, rank, local):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     probs = workloads.batched(512, seed=rank)
     dev = torch.device("cuda", local)
-    V = [torch.from_numpy(p.V).to(dev) for p in probs]
-    W = [torch.from_numpy(p.W).to(dev) for p in probs]
-    H = [torch.from_numpy(p.H).to(dev) for p in probs]
-    shapes = [p.shape for p in probs]
-    g = dna.dna_group_create([s[0] for s in shapes], [s[1] for s in shapes], [s[2] for s in shapes])
-    stream = torch.cuda.current_stream()
-    dna.dna_group_set_stream(g, stream)
-    dna.dna_group_bind(g, V, W, H)
-    dna.dna_group_normalize(g, 1)
-    rows = dna.dna_group_autotune(g, 2)
-    dna.dna_group_use_graph(g, True)
-    kl0 = dna.dna_group_kl(g, len(probs))
-    dna.dna_group_iterate(g, args.warmup)
-    torch.cuda.synchronize()
     clocks = ClockSampler(local)
     time.sleep(0.3)
     if world > 1:
         dist.barrier()
-    torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    dna.dna_group_iterate(g, args.steps)
-    ev1.record(stream)
-    torch.cuda.synchronize()
+    res = measure_batched(dna, torch, probs, args.steps, args.warmup, measured_peaks())
     if world > 1:
         dist.barrier()
-    ms = ev0.elapsed_time(ev1)
     clk = clocks.stop()
-    kl1 = dna.dna_group_kl(g, len(probs))
-    launches = dna.dna_group_launches_per_iteration(g) * args.steps
-    dna.dna_group_destroy(g)
-    ms_max = max_over_ranks(torch, dist, ms, dev) if world > 1 else ms
+    ms_max = max_over_ranks(torch, dist, res["ms"], dev) if world > 1 else res["ms"]
     if world > 1:
         dist.destroy_process_group()
     value = job_rate(world, args.steps, ms_max)
-    nt = sum(s[0] * s[1] for s in shapes)
-    alg_bytes = 4 * 4 * nt          # V read by both passes of both half-steps, float32
-    flops = sum(20 * s[2] * s[0] * s[1] for s in shapes)   # 10 R flop per element per half-step
-    peaks = measured_peaks()
-    hbm = float(peaks.get("hbm_gbs", 6800.0))
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    alu = SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    step_s = ms_max / args.steps / 1e3
-    achieved = flops / step_s / 1e12
     line = {
         "metric": METRIC, "value": value, "unit": "grouped DNA iterations/s (all 512 problems)",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "batched", "desc": BATCHED_DESC, "problems": len(probs),
-                   "sum_NT": nt, "form": "F32", "engine": "simt grouped + CUDA graph",
-                   "split_rows": rows, "l2": "inputs larger than L2 (V totals %d MB)" % (nt * 4 >> 20)},
-        "gpu_launches": launches,
-        "roofline": {"bound": "alu", "kernel": "whole grouped iteration", "achieved": achieved,
-                     "peak": alu, "unit": "TFLOP/s", "frac": achieved / alu, "traffic": None,
-                     "algorithmic_flops_per_step": flops, "algorithmic_bytes_per_step": alg_bytes,
-                     "hbm_frac": alg_bytes / step_s / 1e9 / hbm,
-                     "peak_source": (f"derived: {SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 "
-                                     f"flop x {sm_max:.0f} MHz")},
+                   "sum_NT": res["nt"], "form": "F32", "engine": "simt grouped + CUDA graph",
+                   "split_rows": res["rows"],
+                   "l2": "inputs larger than L2 (V totals %d MB)" % (res["nt"] * 4 >> 20)},
+        "gpu_launches": res["launches"],
+        "roofline": res["roofline"],
         "clocks": clk,
-        "kl_sum_start": float(np.sum(kl0)), "kl_sum_end": float(np.sum(kl1)),
+        "kl_sum_start": float(np.sum(res["kl0"])), "kl_sum_end": float(np.sum(res["kl1"])),
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -917,9 +917,11 @@ UNROLLED_K, UNROLLED_EVERY = 20, 5
 
 
 def run_unrolled(args, world, rank, local):
-    """The differentiation form: one step = the K = 20 unrolled DNA H-solve at fixed W
-    (checkpoints every 5 steps), the loss d_KL(V, W H_K) + (mu / 2) |H_K|^2 and its
-    backward pass to V and H0, through the autograd wrappers (N=1024 T=4096 R=64)."""
+    """The differentiation form: one step = the K = 20 unrolled DNA H-solve with W held by
+    the solve (checkpoints every 5 steps), the loss d_KL(V, W H_K) + (mu / 2) |H_K|^2 and
+    its backward pass to V, W and H0, through the autograd wrappers (N=1024 T=4096 R=64).
+    With the F32 form the line also gives the relative error of each gradient against the
+    F64 form's (the F64 form is tested against the FP64 reference to 1e-8)."""
     import torch
     import torch.distributed as dist
 
@@ -933,13 +935,14 @@ def run_unrolled(args, world, rank, local):
     N, T = prob.V.shape
     R = prob.W.shape[1]
     mu = 1e-3 * float(prob.V.mean()) / float(prob.H.mean()) ** 2
-    V = torch.from_numpy(prob.V).to(dev, dt).requires_grad_(True)
-    W = torch.from_numpy(prob.W).to(dev, dt)
-    H0 = torch.from_numpy(prob.H).to(dev, dt).requires_grad_(True)
+    def leaves(dtype):
+        return tuple(torch.from_numpy(x).to(dev, dtype).requires_grad_(True)
+                     for x in (prob.V, prob.W, prob.H))
 
-    def step():
-        V.grad = None
-        H0.grad = None
+    V, W, H0 = leaves(dt)
+
+    def step(V=V, W=W, H0=H0):
+        V.grad = W.grad = H0.grad = None
         HK = UnrolledDNAH.apply(V, W, H0, UNROLLED_K, UNROLLED_EVERY)
         loss = KLDiv.apply(V, W, HK) + 0.5 * mu * (HK.double() ** 2).sum()
         loss.backward()
@@ -973,11 +976,23 @@ def run_unrolled(args, world, rank, local):
     if world > 1:
         dist.destroy_process_group()
     value = job_rate(world, args.steps, ms_max)
+    accuracy = None
+    if dt == torch.float32:
+        # the F32 gradients of the last timed step against the F64 form's, same inputs
+        g32 = [x.grad.double() for x in (V, W, H0)]
+        V64, W64, H64 = leaves(torch.float64)
+        step(V64, W64, H64)
+        torch.cuda.synchronize()
+        accuracy = {"reference": "F64 form of the same solve and loss",
+                    "K": UNROLLED_K}
+        for name, g, x in zip(("dL/dV", "dL/dW", "dL/dH0"), g32, (V64, W64, H64)):
+            accuracy[name] = float(torch.linalg.norm(g - x.grad) / torch.linalg.norm(x.grad))
     # forward: K H half-steps of about 10 R N T flop; backward: the segments' recomputed
     # steps (K - K / every) plus K adjoint steps of about 10 R N T each (z recomputed, the
-    # two z-tiles P1, P2 and H-bar's product), and d_KL's backward (4 R N T)
+    # two z-tiles P1, P2 and H-bar's product) and K W-gradient steps of about 12 R N T (z,
+    # P1, P2 recomputed, then the three sums over o), and d_KL's backward (4 R N T)
     K, ev = UNROLLED_K, UNROLLED_EVERY
-    flops = (K + (K - K // ev) + K) * 10 * R * N * T + 4 * R * N * T
+    flops = (K + (K - K // ev) + K) * 10 * R * N * T + K * 12 * R * N * T + 4 * R * N * T
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     if dt == torch.float64:
@@ -1002,7 +1017,10 @@ def run_unrolled(args, world, rank, local):
                      "frac": achieved / alu, "traffic": None,
                      "algorithmic_flops_per_step": flops, "peak_source": alu_src},
         "clocks": clk, "loss": float(loss),
+        "gradients": "V, W and H0",
     }
+    if accuracy is not None:
+        line["accuracy_rel_fro"] = accuracy
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0

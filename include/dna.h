@@ -186,6 +186,21 @@ int dna_step_H_fixed(dna_ctx* ctx, uint8_t* choice_out);
 int dna_step_H_adjoint(dna_ctx* ctx, const void* Hk, const uint8_t* choice,
                        const void* Hbar_next, void* Hbar_out, void* Vbar);
 
+/* dna_step_H_adjoint with W a variable of the step as well: as above, and ADDS dL/dW of the
+ * step into Wbar (N x R, row-major like W): the paths through Z = W H (hence Q = V / Z and
+ * Qbar = V / Z^2), through A = W^t Q and B = (W o W)^t Qbar of eq. 7 and 14, and through
+ * the column sums c = W^t 1 + lambda that divide them (eq. 7) and weight the eq. 10
+ * renormalisation.  Summed over the steps of an unrolled solve (plus the loss's own
+ * derivative in W, e.g. dna_kl_backward's dW) this is the gradient of the loss with
+ * respect to W.  Vbar and Wbar may each be NULL (the other outputs are still written).
+ * The first call with Wbar allocates the context's W-gradient workspace (at most
+ * 32 x R x N values of the element type and ceil(T / 32) x R float64); later calls
+ * allocate nothing.  Same limits on R as dna_step_H_adjoint. Returns DNA_ERR_ALLOC if the
+ * workspace cannot be allocated.
+ * Asynchronous. */
+int dna_step_H_adjoint_w(dna_ctx* ctx, const void* Hk, const uint8_t* choice,
+                         const void* Hbar_next, void* Hbar_out, void* Vbar, void* Wbar);
+
 /* Selection rules (dna_set_selection).  PAPER: Section 2.4 and Algorithm 1 steps 15 / 28,
  * the Newton candidate is kept iff its cost is below the MU candidate's (both costs are
  * evaluated).  DESCENT: the Newton candidate is kept iff its eq. 5 (eq. 4) cost is below

@@ -75,6 +75,20 @@ def kl(V, Z):
     return torch.where(pos, V * torch.log(Vp / Zp) - V, torch.zeros_like(Z)).sum() + Z.sum()
 
 
+def loss_and_grads_vwh(V, W, H0, K, mu, choices=None, lam=0.0):
+    """As loss_and_grads, with W a variable of the solve too (and lambda >= 0 in eq. 7):
+    (loss, dL/dV, dL/dW, dL/dH0, choices).  dL/dW collects every path by which W enters:
+    the loss's Z = W H_K and, in every step, Z = W H, A = W^t Q, B = (W o W)^t Qbar and the
+    column sums c = W^t 1 + lambda (eq. 7, 10, 14)."""
+    V = torch.as_tensor(V, dtype=torch.float64).clone().requires_grad_(True)
+    W = torch.as_tensor(W, dtype=torch.float64).clone().requires_grad_(True)
+    H0 = torch.as_tensor(H0, dtype=torch.float64).clone().requires_grad_(True)
+    HK, used = unrolled(V, W, H0, K, lam=lam, choices=choices)
+    loss = kl(V, W @ HK) + 0.5 * mu * (HK * HK).sum()
+    gV, gW, gH = torch.autograd.grad(loss, (V, W, H0))
+    return float(loss.detach()), gV.numpy(), gW.numpy(), gH.numpy(), [u.numpy() for u in used]
+
+
 def loss_and_grads(V, W, H0, K, mu, choices=None):
     """Loss d_KL(V, W H_K) + (mu / 2) |H_K|^2 and its gradients w.r.t. V and H0 (float64)."""
     V = torch.as_tensor(V, dtype=torch.float64).clone().requires_grad_(True)

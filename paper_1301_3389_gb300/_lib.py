@@ -81,6 +81,7 @@ def _load() -> ctypes.CDLL:
         "dna_kl_backward": (I, [P, D, P, P, P]),
         "dna_step_H_fixed": (I, [P, P]),
         "dna_step_H_adjoint": (I, [P, P, P, P, P, P]),
+        "dna_step_H_adjoint_w": (I, [P, P, P, P, P, P, P]),
         "dna_group_create": (I, [I, P, P, P, ctypes.POINTER(dna_opts), ctypes.POINTER(P)]),
         "dna_group_bind": (I, [P, P, P, P, P]),
         "dna_group_set_stream": (I, [P, P]),
@@ -228,6 +229,14 @@ def dna_step_H_fixed(ctx: int, choice_out=None) -> None:
 def dna_step_H_adjoint(ctx: int, Hk, choice, Hbar_next, Hbar_out, Vbar) -> None:
     _check(LIB.dna_step_H_adjoint(ctx, _ptr(Hk), _ptr(choice), _ptr(Hbar_next), _ptr(Hbar_out),
                                   _ptr(Vbar)), "dna_step_H_adjoint")
+
+
+def dna_step_H_adjoint_w(ctx: int, Hk, choice, Hbar_next, Hbar_out, Vbar=None,
+                         Wbar=None) -> None:
+    _check(LIB.dna_step_H_adjoint_w(ctx, _ptr(Hk), _ptr(choice), _ptr(Hbar_next),
+                                    _ptr(Hbar_out), _ptr(Vbar) if Vbar is not None else None,
+                                    _ptr(Wbar) if Wbar is not None else None),
+           "dna_step_H_adjoint_w")
 
 
 def dna_get_choice(ctx: int, which: int, n: int):

@@ -2,10 +2,12 @@
 
 * ``KLDiv.apply(V, W, H)``: d_KL(V, W H) of eq. 1; the backward pass is
   ``dna_kl_backward`` (dW = (1 - Q) H^t, dH = W^t (1 - Q), dV = log(V / Z)).
-* ``UnrolledDNAH.apply(V, W, H0, K, every)``: K DNA H half-steps at fixed W
-  (``dna_step_H_fixed``), returning H_K; the backward pass runs ``dna_step_H_adjoint`` in
-  reverse, recomputing the states of each segment from checkpoints kept every ``every``
-  steps.  Gradients flow to V and H0; W is treated as a constant of the solve.
+* ``UnrolledDNAH.apply(V, W, H0, K, every)``: K DNA H half-steps with W held fixed by the
+  solve (``dna_step_H_fixed``), returning H_K; the backward pass runs
+  ``dna_step_H_adjoint_w`` in reverse, recomputing the states of each segment from
+  checkpoints kept every ``every`` steps.  Gradients flow to V, H0 and, when W requires
+  one, to W (through every step's Z = W H, A = W^t Q, B = (W o W)^t Qbar and the column
+  sums W^t 1 + lambda).
 
 Tensors are CUDA float32 (F32 form) or float64 (F64 form), contiguous, row-major.
 
@@ -116,8 +118,10 @@ class UnrolledDNAH(torch.autograd.Function):
     def backward(fctx, grad_HK):
         V, W, choices, *ckpts = fctx.saved_tensors
         K, every = fctx.K, fctx.every
+        need_v, need_w = fctx.needs_input_grad[0], fctx.needs_input_grad[1]
         Hbar = grad_HK.contiguous().clone()
-        Vbar = torch.zeros_like(V)
+        Vbar = torch.zeros_like(V) if need_v else None
+        Wbar = torch.zeros_like(W) if need_w else None
         Hrun = ckpts[0].clone()
         with _Ctx(V, W, Hrun) as ctx:
             for seg in reversed(range(len(ckpts))):
@@ -129,8 +133,8 @@ class UnrolledDNAH(torch.autograd.Function):
                     states.append(Hrun.clone())
                 for k in reversed(range(k0, k1)):
                     out = torch.empty_like(Hbar)
-                    L.dna_step_H_adjoint(ctx, states[k - k0], choices[k], Hbar, out, Vbar)
+                    L.dna_step_H_adjoint_w(ctx, states[k - k0], choices[k], Hbar, out, Vbar,
+                                           Wbar)
                     Hbar = out
             torch.cuda.current_stream().synchronize()
-        need_v = fctx.needs_input_grad[0]
-        return (Vbar if need_v else None), None, Hbar, None, None
+        return Vbar, Wbar, Hbar, None, None

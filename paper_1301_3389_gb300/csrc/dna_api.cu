@@ -103,6 +103,12 @@ struct dna_ctx {
     // per-column costs from pass 1, [splits][max(N, T)])
     int selection = DNA_SELECT_PAPER;
     double* dcur = nullptr;
+    // W-gradient of the H-step adjoint (allocated on first use): partial sums over splits
+    // of o [wsp][R][N] and the column-sum terms per block of 32 columns [ceil(T / 32)][R]
+    void* wg_part = nullptr;
+    double* wg_cpart = nullptr;
+    int wsp = 0;
+    int64_t wper = 0;
     // profiling: event pairs around phases, launch counts
     unsigned prof_mask = 0;          // phases whose instances get an event pair
     std::vector<cudaEvent_t> ev_pool;
@@ -233,7 +239,7 @@ void free_all(dna_ctx* c) {
                     c->Y2tk, c->Xmk, c->Xdk, c->Vp, c->Qg, c->Qbg, c->cptr, c->ridx, c->cval, c->Yt, c->c0,
                     c->seg_col[0], c->seg_col[1], c->seg_k0[0], c->seg_k0[1], c->seg_k1[0],
                     c->seg_k1[1], c->seg_ptr[0], c->seg_ptr[1], c->Aseg, c->Bseg, c->dseg,
-                    c->dcur};
+                    c->dcur, c->wg_part, c->wg_cpart};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t ev : c->ev_pool) cudaEventDestroy(ev);
@@ -524,22 +530,34 @@ int step_h_fixed(dna_ctx* c, uint8_t* choice_out) {
 }
 
 // Adjoint of step_h_fixed at state Hk with the recorded choices: Hbar_out = dL/dH_k from
-// Hbar_next = dL/dH_{k+1}; Vbar += dL/dV.
+// Hbar_next = dL/dH_{k+1}; Vbar += dL/dV and Wbar += dL/dW (either may be null).
 template <typename Tp>
 int step_h_adjoint(dna_ctx* c, const Tp* Hk, const uint8_t* choice, const Tp* Hbar_next,
-                   Tp* Hbar_out, Tp* Vbar) {
+                   Tp* Hbar_out, Tp* Vbar, Tp* Wbar) {
     using S = dna::Simt<Tp>;
     View v = make_view(c, false);
     v.X = const_cast<Tp*>(Hk);
     cudaStream_t st = c->stream;
+    if (Wbar && !c->wg_part) {
+        // o split so that the s-blocks x splits fill the SMs (one CTA per SM)
+        plan_split(c->T, (c->N + 63) / 64, c->num_sms, 64, &c->wsp, &c->wper);
+        if (dmalloc(&c->wg_part, sizeof(Tp) * (size_t)c->wsp * (size_t)c->R * (size_t)c->N) ||
+            dmalloc(&c->wg_cpart, sizeof(double) * (size_t)((c->T + 31) / 32) * (size_t)c->R))
+            return DNA_ERR_ALLOC;
+    }
     Tp* A = static_cast<Tp*>(c->Apart);
     Tp* B = static_cast<Tp*>(c->Bpart);
+    Tp* Abar = static_cast<Tp*>(c->Xmu);
+    Tp* Bbar = static_cast<Tp*>(c->Xdna);
     int e = S::factor_sums_y(v, c->o.lambda, c->c, c->fwork, st);
     if (!e) e = S::pass1(v, A, B, c->sp1[0], c->per1[0], true, c->status, st);
     if (!e)
-        e = S::adjoint_h(v, c->c, A, B, c->sp1[0], choice, Hbar_next, Hbar_out,
-                         static_cast<Tp*>(c->Xmu), static_cast<Tp*>(c->Xdna), c->dpart, A,
-                         c->sp1[0], c->per1[0], Vbar, c->T, c->o.eps, c->o.alpha, c->status, st);
+        e = S::adjoint_h(v, c->c, A, B, c->sp1[0], choice, Hbar_next, Hbar_out, Abar, Bbar,
+                         c->dpart, A, c->sp1[0], c->per1[0], Vbar, c->T, c->o.eps, c->o.alpha,
+                         c->status, st, Wbar ? c->wg_cpart : nullptr);
+    if (!e && Wbar)
+        e = S::adjoint_w(v, Abar, Bbar, c->wg_cpart, static_cast<Tp*>(c->wg_part), c->wsp,
+                         c->wper, Wbar, c->status, st);
     return e;
 }
 
@@ -1289,19 +1307,26 @@ int dna_step_H_fixed(dna_ctx* c, uint8_t* choice_out) {
     return is_f64(c) ? step_h_fixed<double>(c, choice_out) : step_h_fixed<float>(c, choice_out);
 }
 
-int dna_step_H_adjoint(dna_ctx* c, const void* Hk, const uint8_t* choice, const void* Hbar_next,
-                       void* Hbar_out, void* Vbar) {
+int dna_step_H_adjoint_w(dna_ctx* c, const void* Hk, const uint8_t* choice,
+                         const void* Hbar_next, void* Hbar_out, void* Vbar, void* Wbar) {
     if (int e = check_ready(c)) return e;
-    if (!Hk || !choice || !Hbar_next || !Hbar_out || !Vbar) return DNA_ERR_ARG;
+    if (!Hk || !choice || !Hbar_next || !Hbar_out) return DNA_ERR_ARG;
     if (c->tc || c->sparse || (is_f64(c) ? c->R > 64 : c->R > 128)) return DNA_ERR_UNSUPPORTED;
     if (set_device(c)) return DNA_ERR_CUDA;
     if (is_f64(c))
         return step_h_adjoint<double>(c, static_cast<const double*>(Hk), choice,
                                       static_cast<const double*>(Hbar_next),
-                                      static_cast<double*>(Hbar_out), static_cast<double*>(Vbar));
+                                      static_cast<double*>(Hbar_out), static_cast<double*>(Vbar),
+                                      static_cast<double*>(Wbar));
     return step_h_adjoint<float>(c, static_cast<const float*>(Hk), choice,
                                  static_cast<const float*>(Hbar_next), static_cast<float*>(Hbar_out),
-                                 static_cast<float*>(Vbar));
+                                 static_cast<float*>(Vbar), static_cast<float*>(Wbar));
+}
+
+int dna_step_H_adjoint(dna_ctx* c, const void* Hk, const uint8_t* choice, const void* Hbar_next,
+                       void* Hbar_out, void* Vbar) {
+    if (!Vbar) return DNA_ERR_ARG;
+    return dna_step_H_adjoint_w(c, Hk, choice, Hbar_next, Hbar_out, Vbar, nullptr);
 }
 
 int dna_kl_backward(dna_ctx* c, double scale, void* dW, void* dH, void* dV) {

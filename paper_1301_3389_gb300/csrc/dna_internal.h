@@ -96,12 +96,19 @@ template <typename Tp> struct Simt {
     // gradient of eq. 1 w.r.t. V: dV(s, o) = scale log(v / z) (0 where v = 0)
     static int grad_v(const View& v, double scale, Tp* dV, int64_t ldd, int* status,
                       cudaStream_t st);
-    // adjoint of one H step at fixed W (see k_adj_elem / k_adj_gemm): Hbar0 = dL/dH_k given
-    // Hbar1 = dL/dH_{k+1}; Vbar += dL/dV.  Uses A, B (pass 1 of H_k) and the column choices.
+    // adjoint of one H step (see k_adj_elem / k_adj_gemm): Hbar0 = dL/dH_k given
+    // Hbar1 = dL/dH_{k+1}; Vbar += dL/dV (Vbar may be null).  Uses A, B (pass 1 of H_k) and
+    // the column choices.  With cpart ([ceil(O / 32)][R] float64) also the column-sum part
+    // of dL/dW, per block of 32 columns.
     static int adjoint_h(const View& v, const double* c, const Tp* Apart, const Tp* Bpart,
                          int splits1, const uint8_t* choice, const Tp* Hbar1, Tp* Hbar0,
                          Tp* Abar, Tp* Bbar, double* vs, Tp* Hpart, int splits2, int64_t s_per2,
                          Tp* Vbar, int64_t ldvb, double eps, double alpha, int* status,
+                         cudaStream_t st, double* cpart = nullptr);
+    // after adjoint_h (its Abar, Bbar, cpart): Wbar += dL/dW of the step (k_adj_wgrad),
+    // through Wpart [wsplits][R][S], o split in ranges of o_per (a multiple of 64)
+    static int adjoint_w(const View& v, const Tp* Abar, const Tp* Bbar, const double* cpart,
+                         Tp* Wpart, int wsplits, int64_t o_per, Tp* Wbar, int* status,
                          cudaStream_t st);
     // Fused glue of the single-problem path (glue_kernels.cuh).
     // Candidates as above; with Xmk, Xdk (float only) also their bf16 copies [O_pad][rp]

@@ -572,13 +572,21 @@ __global__ void __launch_bounds__(NT) k_grad_v(View v, double scale, Tp* __restr
 // with a = A / c - 1, b = B / c, A = W^t (V / Z), B = (W o W)^t (V / Z^2), Z = W H.  The
 // selection (which column took which candidate) is held fixed.  Given hb' = dL/dh', this
 // kernel forms, per column, the direct part of dL/dh, the adjoints Abar = dL/dA and
-// Bbar = dL/dB (raw sums), and vs = dL/ds.  CTA = 32 columns x 8 groups of r.
+// Bbar = dL/dB (raw sums), and vs = dL/ds.  With cpart it also forms the part of dL/dW
+// that flows through the column sums c_r = sum_n w_nr + lambda (every w_nr of column r
+// receives it):
+//   dL/dc_r = -(abar (a + 1) + bbar b) / c_r - [Newton] (s hg / D^2) g_r
+// (a = A / c - 1 and b = B / c, so da/dc = -(a + 1) / c and db/dc = -b / c; the eq. 10
+// denominator D = sum_l c_l g_l gives dD/dc_r = g_r, and dL/dD = -s hg / D^2 with
+// hg = sum_r hb'_r g_r), summed over the CTA's 32 columns into cpart[blockIdx.x][r].
+// CTA = 32 columns x 8 groups of r (one warp per group).
 template <typename Tp>
 __global__ void __launch_bounds__(256)
     k_adj_elem(View v, const double* __restrict__ c, const Tp* __restrict__ Apart,
                const Tp* __restrict__ Bpart, int splits, const uint8_t* __restrict__ choice,
                const Tp* __restrict__ Hbar1, Tp* __restrict__ Hbar0, Tp* __restrict__ Abar,
-               Tp* __restrict__ Bbar, double* __restrict__ vs, Tp eps, Tp alpha) {
+               Tp* __restrict__ Bbar, double* __restrict__ vs, Tp eps, Tp alpha,
+               double* __restrict__ cpart) {
     __shared__ double red[2][8][32];
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int64_t o = (int64_t)blockIdx.x * 32 + tx;
@@ -611,52 +619,67 @@ __global__ void __launch_bounds__(256)
     red[0][ty][tx] = dsum;
     red[1][ty][tx] = hg;
     __syncthreads();
-    if (!live) return;
     double D = 0.0, HG = 0.0;
     for (int k = 0; k < 8; ++k) { D += red[0][k][tx]; HG += red[1][k][tx]; }
-    const double s_o = v.vsum[o];
+    const double s_o = live ? v.vsum[o] : 0.0;
     const bool renorm = D > 0.0;
     const Tp f1 = (Tp)(renorm ? s_o / D : 1.0);            // d h' / d g (diagonal part)
     const Tp f2 = (Tp)(renorm ? s_o * HG / (D * D) : 0.0); // weight of the D coupling
-    if (ty == 0) vs[o] = (newton && renorm) ? HG / D : 0.0;
+    if (ty == 0 && live) vs[o] = (newton && renorm) ? HG / D : 0.0;
+    // the loop bound is uniform over the warp (one warp per ty), so every lane takes part
+    // in the cpart shuffle; lanes past the last column contribute 0
     for (int64_t r = ty; r < v.R; r += 8) {
-        Tp ra = Tp(0), rb = Tp(0);
-        for (int sp = 0; sp < splits; ++sp) {
-            ra += Apart[((int64_t)sp * v.R + r) * v.O + o];
-            rb += Bpart[((int64_t)sp * v.R + r) * v.O + o];
-        }
-        const Tp cr = (Tp)c[r], x = X[r * v.xr + o * v.xo];
-        const Tp hb1 = Hbar1[r * v.xr + o * v.xo];
-        const Tp a = ra / cr - Tp(1), b = rb / cr;
-        Tp hx, ab = Tp(0), bb = Tp(0);   // dL/dh (direct), dL/da, dL/db
-        if (!newton) {                   // h' = h (1 + a)
-            hx = hb1 * (Tp(1) + a);
-            ab = hb1 * x;
-        } else {
-            const Tp gb = f1 * hb1 - cr * f2;   // dL/dg_r
-            if (a < Tp(0)) {
-                const Tp xb = x * b, den = xb - a, gain = xb / den;
-                if (gain > eps) {                // g = x^2 b / (x b - a)
-                    const Tp d2 = den * den;
-                    hx = gb * xb * (xb - Tp(2) * a) / d2;
-                    ab = gb * x * xb / d2;
-                    bb = -gb * a * x * x / d2;
-                } else {                         // floor: g = eps x
-                    hx = gb * eps;
-                }
+        double cb = 0.0;
+        if (live) {
+            Tp ra = Tp(0), rb = Tp(0);
+            for (int sp = 0; sp < splits; ++sp) {
+                ra += Apart[((int64_t)sp * v.R + r) * v.O + o];
+                rb += Bpart[((int64_t)sp * v.R + r) * v.O + o];
+            }
+            const Tp cr = (Tp)c[r], x = X[r * v.xr + o * v.xo];
+            const Tp hb1 = Hbar1[r * v.xr + o * v.xo];
+            const Tp a = ra / cr - Tp(1), b = rb / cr;
+            Tp hx, ab = Tp(0), bb = Tp(0);   // dL/dh (direct), dL/da, dL/db
+            Tp g = Tp(0);                    // the Newton column's g_r (for dL/dc)
+            if (!newton) {                   // h' = h (1 + a)
+                hx = hb1 * (Tp(1) + a);
+                ab = hb1 * x;
             } else {
-                const Tp st = b > Tp(0) ? a / b : Tp(0), cap = alpha * x;
-                if (st < cap) {                  // g = x + a / b
-                    hx = gb;
-                    if (b > Tp(0)) { ab = gb / b; bb = -gb * a / (b * b); }
-                } else {                         // cap: g = (1 + alpha) x
-                    hx = gb * (Tp(1) + alpha);
+                const Tp gb = f1 * hb1 - cr * f2;   // dL/dg_r
+                if (a < Tp(0)) {
+                    const Tp xb = x * b, den = xb - a, gain = xb / den;
+                    if (gain > eps) {                // g = x^2 b / (x b - a)
+                        const Tp d2 = den * den;
+                        hx = gb * xb * (xb - Tp(2) * a) / d2;
+                        ab = gb * x * xb / d2;
+                        bb = -gb * a * x * x / d2;
+                        g = x * gain;
+                    } else {                         // floor: g = eps x
+                        hx = gb * eps;
+                        g = eps * x;
+                    }
+                } else {
+                    const Tp st = b > Tp(0) ? a / b : Tp(0), cap = alpha * x;
+                    if (st < cap) {                  // g = x + a / b
+                        hx = gb;
+                        if (b > Tp(0)) { ab = gb / b; bb = -gb * a / (b * b); }
+                        g = x + st;
+                    } else {                         // cap: g = (1 + alpha) x
+                        hx = gb * (Tp(1) + alpha);
+                        g = x + cap;
+                    }
                 }
             }
+            Hbar0[r * v.xr + o * v.xo] = hx;
+            Abar[r * v.O + o] = ab / cr;     // a = A / c - 1
+            Bbar[r * v.O + o] = bb / cr;     // b = B / c
+            cb = -(double)(ab * (a + Tp(1)) + bb * b) / (double)cr - (double)(f2 * g);
         }
-        Hbar0[r * v.xr + o * v.xo] = hx;
-        Abar[r * v.O + o] = ab / cr;     // a = A / c - 1
-        Bbar[r * v.O + o] = bb / cr;     // b = B / c
+        if (cpart) {
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) cb += __shfl_xor_sync(0xffffffffu, cb, off);
+            if (tx == 0) cpart[(int64_t)blockIdx.x * v.R + r] = cb;
+        }
     }
 }
 
@@ -744,7 +767,7 @@ __global__ void __launch_bounds__(NT)
                         const Tp iz = Tp(1) / zz;
                         vb += p1[i][j] * iz + p2[i][j] * iz * iz;
                     }
-                    Vbar[s * ldvb + o] += vb;
+                    if (Vbar) Vbar[s * ldvb + o] += vb;
                 }
                 Zb[(zs + i) * LD + zo + j] = zb;
             }
@@ -775,6 +798,160 @@ __global__ void __launch_bounds__(NT)
             const int64_t o = o0 + go + j;
             if (o < v.O) Hpart[(base + r) * v.O + o] = acc[i][j];
         }
+    }
+}
+
+// The part of dL/dW of one H step that flows through A, B and Z (W held as a variable):
+//   A = W^t Q, B = (W o W)^t Qbar, Z = W H, Q = V / Z, Qbar = V / Z^2 give
+//   dL/dw_sr = sum_o [ q(s,o) Abar(r,o) + 2 w_sr qbar(s,o) Bbar(r,o) + zbar(s,o) x(r,o) ]
+// with zbar = -qbar P1 - 2 (qbar / z) P2, P1 = W Abar, P2 = (W o W) Bbar as in k_adj_gemm.
+// Each CTA owns a 64-row s-block and every r <= RB, walks its split of o in 64-wide chunks
+// (z, P1, P2 as 4 x 4 register tiles, then q, qbar, zbar as shared tiles [o][s]) and
+// accumulates the two sums of the (r, s) tile in registers; Wpart is [splits][R][S].
+// The y^t tile and the zbar tile share one region (y^t is reloaded per chunk).
+template <typename Tp, int RB>
+struct WgradCfg {
+    static constexpr int RPT = RB / 16;            // r rows per thread of the (r, s) tile
+    static constexpr int UR = RB > SB ? RB : SB;   // rows of the y^t / zbar region
+    static constexpr size_t smem = (size_t)((3 * RB + UR + 2 * OB) * LD) * sizeof(Tp);
+};
+
+template <typename Tp, int RB>
+__global__ void __launch_bounds__(NT)
+    k_adj_wgrad(View v, const Tp* __restrict__ Abar, const Tp* __restrict__ Bbar,
+                Tp* __restrict__ Wpart, int64_t o_per, int* __restrict__ status) {
+    using C = WgradCfg<Tp, RB>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Tp* Xs = reinterpret_cast<Tp*>(smem_raw);  // [RB][LD] x(r, o)
+    Tp* As = Xs + RB * LD;                     // [RB][LD] Abar(r, o)
+    Tp* Bs = As + RB * LD;                     // [RB][LD] Bbar(r, o)
+    Tp* Yt = Bs + RB * LD;                     // [RB][LD] y(s, r) transposed, or
+    Tp* Zb = Yt;                               // [OB][LD] zbar(s, o) transposed
+    Tp* Qs = Yt + C::UR * LD;                  // [OB][LD] q(s, o) transposed
+    Tp* Qb = Qs + OB * LD;                     // [OB][LD] qbar(s, o) transposed
+    const Tp* __restrict__ V = static_cast<const Tp*>(v.V);
+    const Tp* __restrict__ X = static_cast<const Tp*>(v.X);
+    const Tp* __restrict__ Y = static_cast<const Tp*>(v.Y);
+    const int tid = threadIdx.x;
+    const int64_t s0 = (int64_t)blockIdx.x * SB;
+    const int64_t o_begin = (int64_t)blockIdx.y * o_per;
+    const int64_t o_end = min(v.O, o_begin + o_per);
+    const int zo = (tid % 16) * 4, zs = (tid / 16) * 4;   // (s, o) tile of the GEMM phase
+    const int gs = (tid % 16) * 4, gr = tid / 16;         // (r, s) tile of the sums
+    Tp acc1[C::RPT][4], acc2[C::RPT][4];
+#pragma unroll
+    for (int i = 0; i < C::RPT; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) { acc1[i][j] = Tp(0); acc2[i][j] = Tp(0); }
+    int bad = 0;
+    for (int64_t oc = o_begin; oc < o_end; oc += OB) {
+        load_tile<Tp, RB, SB>(Yt, Y, v.yr, v.ys, 0, s0, v.R, v.S);
+        load_tile<Tp, RB, OB>(Xs, X, v.xr, v.xo, 0, oc, v.R, o_end);
+        load_tile<Tp, RB, OB>(As, Abar, v.O, 1, 0, oc, v.R, o_end);
+        load_tile<Tp, RB, OB>(Bs, Bbar, v.O, 1, 0, oc, v.R, o_end);
+        __syncthreads();
+        Tp z[4][4], p1[4][4], p2[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) { z[i][j] = Tp(0); p1[i][j] = Tp(0); p2[i][j] = Tp(0); }
+        z_tile<Tp, RB>(Yt, Xs, zs, zo, z);
+        z_tile<Tp, RB>(Yt, As, zs, zo, p1);
+#pragma unroll 4
+        for (int r = 0; r < RB; ++r) {   // P2 = (Y o Y) Bbar
+            Tp ba[4], ya[4];
+            ld4(Bs + r * LD + zo, ba);
+            ld4(Yt + r * LD + zs, ya);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) p2[i][j] = fma(ya[i] * ya[i], ba[j], p2[i][j]);
+        }
+        __syncthreads();   // every read of the y^t tile is done: the region becomes zbar
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int64_t s = s0 + zs + i;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int64_t o = oc + zo + j;
+                Tp q = Tp(0), qb = Tp(0), zb = Tp(0);
+                if (s < v.S && o < o_end) {
+                    const Tp vv = V[s * v.vs + o], zz = z[i][j];
+                    if (vv > Tp(0)) {
+                        if (zz > Tp(0)) {
+                            const Tp iz = Tp(1) / zz;
+                            q = vv * iz;
+                            qb = q * iz;
+                            zb = -qb * p1[i][j] - Tp(2) * qb * iz * p2[i][j];
+                        } else {
+                            bad = 1;
+                        }
+                    }
+                }
+                Qs[(zo + j) * LD + zs + i] = q;
+                Qb[(zo + j) * LD + zs + i] = qb;
+                Zb[(zo + j) * LD + zs + i] = zb;
+            }
+        }
+        __syncthreads();
+        // acc1(r, s) += sum_o Abar(r, o) q(s, o) + x(r, o) zbar(s, o);
+        // acc2(r, s) += sum_o Bbar(r, o) qbar(s, o)
+#pragma unroll 2
+        for (int o = 0; o < OB; ++o) {
+            Tp qv[4], qbv[4], zbv[4];
+            ld4(Qs + o * LD + gs, qv);
+            ld4(Qb + o * LD + gs, qbv);
+            ld4(Zb + o * LD + gs, zbv);
+#pragma unroll
+            for (int i = 0; i < C::RPT; ++i) {
+                const int r = gr + 16 * i;
+                const Tp a = As[r * LD + o], x = Xs[r * LD + o], b = Bs[r * LD + o];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    acc1[i][j] = fma(a, qv[j], fma(x, zbv[j], acc1[i][j]));
+                    acc2[i][j] = fma(b, qbv[j], acc2[i][j]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (bad) atomicOr(status, STATUS_NONFINITE);
+    const int64_t base = (int64_t)blockIdx.y * v.R;
+#pragma unroll
+    for (int i = 0; i < C::RPT; ++i) {
+        const int64_t r = gr + 16 * i;
+        if (r >= v.R) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t s = s0 + gs + j;
+            if (s >= v.S) continue;
+            const Tp w = Y[s * v.ys + r * v.yr];
+            Wpart[(base + r) * v.S + s] = acc1[i][j] + Tp(2) * w * acc2[i][j];
+        }
+    }
+}
+
+// Wbar(s, r) += sum over splits of Wpart(r, s) + sum over parts of cpart(r) (the column-sum
+// term of k_adj_elem), Wbar laid out like the view's Y.  CTA = 32 values of s x 8 of r.
+template <typename Tp>
+__global__ void __launch_bounds__(256)
+    k_adj_wcombine(View v, const Tp* __restrict__ Wpart, int splits,
+                   const double* __restrict__ cpart, int64_t nparts, Tp* __restrict__ Wbar) {
+    __shared__ double cb[128];
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+    for (int64_t r = tid; r < v.R; r += 256) {
+        double t = 0.0;
+        for (int64_t k = 0; k < nparts; ++k) t += cpart[k * v.R + r];
+        cb[r] = t;
+    }
+    __syncthreads();
+    const int64_t s = (int64_t)blockIdx.x * 32 + tx;
+    if (s >= v.S) return;
+    for (int64_t r = ty; r < v.R; r += 8) {
+        double t = cb[r];
+        for (int sp = 0; sp < splits; ++sp) t += (double)Wpart[((int64_t)sp * v.R + r) * v.S + s];
+        Tp* w = Wbar + s * v.ys + r * v.yr;
+        *w = (Tp)((double)*w + t);
     }
 }
 

@@ -243,9 +243,11 @@ template <typename Tp>
 int Simt<Tp>::adjoint_h(const View& v, const double* c, const Tp* Apart, const Tp* Bpart,
                         int splits1, const uint8_t* choice, const Tp* Hbar1, Tp* Hbar0, Tp* Abar,
                         Tp* Bbar, double* vs, Tp* Hpart, int splits2, int64_t s_per2, Tp* Vbar,
-                        int64_t ldvb, double eps, double alpha, int* status, cudaStream_t st) {
+                        int64_t ldvb, double eps, double alpha, int* status, cudaStream_t st,
+                        double* cpart) {
     simt::k_adj_elem<Tp><<<(unsigned)((v.O + 31) / 32), dim3(32, 8), 0, st>>>(
-        v, c, Apart, Bpart, splits1, choice, Hbar1, Hbar0, Abar, Bbar, vs, (Tp)eps, (Tp)alpha);
+        v, c, Apart, Bpart, splits1, choice, Hbar1, Hbar0, Abar, Bbar, vs, (Tp)eps, (Tp)alpha,
+        cpart);
     if (simt::launch_status()) return DNA_ERR_CUDA;
     int e;
     switch (simt::rblock_for<Tp>(v.R)) {
@@ -263,6 +265,41 @@ int Simt<Tp>::adjoint_h(const View& v, const double* c, const Tp* Apart, const T
     if (e) return e;
     simt::k_adj_combine<Tp><<<(unsigned)((v.O + 31) / 32), dim3(32, 8), 0, st>>>(v, Hpart, splits2,
                                                                                  Hbar0);
+    return simt::launch_status();
+}
+
+namespace simt {
+template <typename Tp, int RB>
+int adj_wgrad_rb(const View& v, const Tp* Abar, const Tp* Bbar, Tp* Wpart, int wsplits,
+                 int64_t o_per, int* status, cudaStream_t st) {
+    const size_t smem = WgradCfg<Tp, RB>::smem;
+    auto k = k_adj_wgrad<Tp, RB>;
+    if (prep_smem(k, smem)) return DNA_ERR_CUDA;
+    dim3 grid((unsigned)((v.S + SB - 1) / SB), (unsigned)wsplits);
+    k<<<grid, NT, smem, st>>>(v, Abar, Bbar, Wpart, o_per, status);
+    return launch_status();
+}
+}  // namespace simt
+
+template <typename Tp>
+int Simt<Tp>::adjoint_w(const View& v, const Tp* Abar, const Tp* Bbar, const double* cpart,
+                        Tp* Wpart, int wsplits, int64_t o_per, Tp* Wbar, int* status,
+                        cudaStream_t st) {
+    if (v.R > 128 || o_per % simt::OB) return DNA_ERR_UNSUPPORTED;
+    int e;
+    switch (simt::rblock_for<Tp>(v.R)) {
+        case 32: e = simt::adj_wgrad_rb<Tp, 32>(v, Abar, Bbar, Wpart, wsplits, o_per, status, st); break;
+        case 64: e = simt::adj_wgrad_rb<Tp, 64>(v, Abar, Bbar, Wpart, wsplits, o_per, status, st); break;
+        default:
+            if constexpr (sizeof(Tp) == 4) {
+                e = simt::adj_wgrad_rb<Tp, 128>(v, Abar, Bbar, Wpart, wsplits, o_per, status, st);
+                break;
+            }
+            return DNA_ERR_UNSUPPORTED;
+    }
+    if (e) return e;
+    simt::k_adj_wcombine<Tp><<<(unsigned)((v.S + 31) / 32), dim3(32, 8), 0, st>>>(
+        v, Wpart, wsplits, cpart, (v.O + 31) / 32, Wbar);
     return simt::launch_status();
 }
 

@@ -122,6 +122,15 @@ def step_elementwise(half, which, W0, H0, Wg, Hg, kind, eps=o.EPS, alpha=o.ALPHA
     return worst
 
 
+def log_value(label: str, val: float) -> float:
+    """Append (test, label, value) to the DNA_PARITY_LOG file, if that variable is set."""
+    path = os.environ.get("DNA_PARITY_LOG")
+    if path:
+        with open(path, "a") as f:
+            f.write(f"{os.environ.get('PYTEST_CURRENT_TEST', '?').split(' ')[0]} {label} {val:.3e}\n")
+    return val
+
+
 def rel_elem(a, b, label: str = "", floor: float = ELEM_FLOOR) -> float:
     """max |a - b| / |b| over the entries of b above floor * max |b| (see ELEM_FLOOR).
 

@@ -2,16 +2,18 @@
 
 * KLDiv: torch.autograd.gradcheck in FP64 (finite differences of the library's own d_KL),
   and dW, dH, dV against the oracle's analytic gradient (FP64 1e-10, FP32 1e-4 relative).
-* UnrolledDNAH (K H steps at fixed W) composed with KLDiv and an L2 penalty on H_K:
-  gradients with respect to V and H0 against torch.autograd of the FP64 reference in
-  oracle/unrolled.py, replaying the GPU's selections (FP64 1e-8; FP32 2e-3 relative for
-  short unrolls; for K = 20 the FP32 dL/dH0 is bounded by the problem's gradient scale).
+* UnrolledDNAH (K H steps with W held by the solve) composed with KLDiv and an L2 penalty
+  on H_K: gradients with respect to V, H0 and W against torch.autograd of the FP64
+  reference in oracle/unrolled.py, replaying the GPU's selections (FP64 1e-8; FP32 2e-3
+  relative for short unrolls; for K = 20 the FP32 dL/dH0 is bounded by the problem's
+  gradient scale, and its relative error is logged).
+* dna_step_H_adjoint_w called directly with lambda > 0 (eq. 7's denominators).
 """
 import numpy as np
 import pytest
 
 import workloads
-from gpu_helpers import rel_fro
+from gpu_helpers import log_value, rel_fro
 from oracle import dna as o
 from oracle import unrolled as u
 
@@ -72,26 +74,30 @@ def _gpu_choices(V, W, H0, K):
     return [torch.from_numpy(c.cpu().numpy().astype(bool)) for c in ch], H
 
 
-def _unrolled_case(p, K, every, kind, tol, h0_scale_tol=None):
+def _unrolled_case(p, K, every, kind, tol, h0_scale_tol=None, w_tol=None):
+    """Loss d_KL(V, W H_K) + (mu / 2) |H_K|^2 through UnrolledDNAH and KLDiv, gradients to
+    V, W and H0 against the FP64 reference.  Returns the relative Frobenius errors."""
     import torch
 
     from paper_1301_3389_gb300.autograd import KLDiv, UnrolledDNAH
     dt = torch.float64 if kind == "f64" else torch.float32
     mu = 1e-3 * float(p.V.mean()) / float(p.H.mean()) ** 2
     V = _t(p.V, dt).requires_grad_(True)
-    W = _t(p.W, dt)
+    W = _t(p.W, dt).requires_grad_(True)
     H0 = _t(p.H, dt).requires_grad_(True)
     choices, HK_ref_gpu = _gpu_choices(V, W, H0, K)
     HK = UnrolledDNAH.apply(V, W, H0, K, every)
     assert torch.equal(HK.detach(), HK_ref_gpu)              # the Function's forward is the solve
     loss = KLDiv.apply(V, W, HK) + 0.5 * mu * (HK.double() ** 2).sum()
     loss.backward()
-    ref_loss, gV, gH, used = u.loss_and_grads(p.V, p.W, p.H, K, mu, choices=choices)
+    ref_loss, gV, gW, gH, used = u.loss_and_grads_vwh(p.V, p.W, p.H, K, mu, choices=choices)
     assert abs(float(loss) - ref_loss) <= max(tol, 1e-6) * abs(ref_loss)
-    ev = rel_fro(V.grad.double().cpu().numpy(), gV)
-    eh = rel_fro(H0.grad.double().cpu().numpy(), gH)
+    ev = log_value(f"unrolled-K{K}-{kind} rel_fro dL/dV", rel_fro(V.grad.double().cpu().numpy(), gV))
+    eh = log_value(f"unrolled-K{K}-{kind} rel_fro dL/dH0", rel_fro(H0.grad.double().cpu().numpy(), gH))
+    ew = log_value(f"unrolled-K{K}-{kind} rel_fro dL/dW", rel_fro(W.grad.double().cpu().numpy(), gW))
     print(f"\n{p.shape} K={K} {kind}: |gV|={np.linalg.norm(gV):.3e} |gH0|={np.linalg.norm(gH):.3e} "
-          f"rel err V {ev:.2e} H0 {eh:.2e}")
+          f"|gW|={np.linalg.norm(gW):.3e} rel err V {ev:.2e} H0 {eh:.2e} W {ew:.2e}")
+    assert ew < (tol if w_tol is None else w_tol), ew
     if h0_scale_tol is None:
         assert ev < tol and eh < tol, (ev, eh)
     else:
@@ -100,7 +106,7 @@ def _unrolled_case(p, K, every, kind, tol, h0_scale_tol=None):
         # problem's gradient scale instead (the F64 form is checked to 1e-8 relative)
         err_h = np.linalg.norm(H0.grad.double().cpu().numpy() - gH)
         assert ev < tol and err_h <= h0_scale_tol * np.linalg.norm(gV), (ev, err_h)
-    return ev, eh
+    return ev, eh, ew
 
 
 @pytest.mark.parametrize("kind", ["f64", "f32"])
@@ -123,3 +129,44 @@ def test_unrolled_diff_form_config(kind):
         _unrolled_case(p, K=20, every=5, kind=kind, tol=1e-8)
     else:
         _unrolled_case(p, K=20, every=5, kind=kind, tol=2e-2, h0_scale_tol=1e-2)
+
+
+@pytest.mark.parametrize("kind", ["f64", "f32"])
+def test_adjoint_w_with_lambda(kind):
+    """The C call directly, lambda = 0.3: K forward steps, then the adjoint in reverse with
+    dL/dW accumulated from every step plus dna_kl_backward's dW of the loss."""
+    import torch
+
+    import paper_1301_3389_gb300 as dna
+    dt = torch.float64 if kind == "f64" else torch.float32
+    p = workloads.custom(96, 200, 12, seed=41)
+    K, lam = 5, 0.3
+    V, W, H = (_t(x, dt) for x in (p.V, p.W, p.H))
+    T = p.V.shape[1]
+    ctx = dna.dna_create(*p.shape, dna.make_opts(
+        dtype=dna.DNA_F64 if kind == "f64" else dna.DNA_F32, lam=lam))
+    try:
+        dna.dna_set_stream(ctx)
+        states = [H.clone()]
+        ch = torch.empty((K, T), dtype=torch.uint8, device="cuda")
+        dna.dna_bind(ctx, V, W, H)
+        for k in range(K):
+            dna.dna_step_H_fixed(ctx, ch[k])
+            states.append(H.clone())
+        # loss = d_KL(V, W H_K): its own gradients at H_K
+        dW = torch.zeros_like(W)
+        Hbar = torch.empty_like(H)
+        dna.dna_kl_backward(ctx, 1.0, dW, Hbar, None)
+        for k in reversed(range(K)):
+            out = torch.empty_like(H)
+            dna.dna_step_H_adjoint_w(ctx, states[k], ch[k], Hbar, out, None, dW)
+            Hbar = out
+        torch.cuda.synchronize()
+    finally:
+        dna.dna_destroy(ctx)
+    choices = [torch.from_numpy(c.cpu().numpy().astype(bool)) for c in ch]
+    _, _, gW, gH, _ = u.loss_and_grads_vwh(p.V, p.W, p.H, K, 0.0, choices=choices, lam=lam)
+    tol = 1e-8 if kind == "f64" else 2e-3
+    ew = log_value(f"adjoint-w-lambda-{kind} rel_fro dL/dW", rel_fro(dW.double().cpu().numpy(), gW))
+    eh = log_value(f"adjoint-w-lambda-{kind} rel_fro dL/dH0", rel_fro(Hbar.double().cpu().numpy(), gH))
+    assert ew < tol and eh < tol, (ew, eh)

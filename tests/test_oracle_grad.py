@@ -60,3 +60,33 @@ def test_unrolled_gradient_finite_differences():
             assert abs(G[idx] - fd) <= 1e-5 * max(1.0, abs(fd)), (which, idx, G[idx], fd)
             checked += 1
     assert checked >= 5
+
+
+def test_unrolled_w_gradient_finite_differences():
+    """dL/dW through the unrolled solve (every step's Z, A, B and column sums, plus the
+    loss's own Z = W H_K) against central differences of the forward, with lambda = 0 and
+    lambda > 0 (eq. 7's denominators), at points where no selection, floor or cap flips."""
+    checked = 0
+    for lam, seed in ((0.0, 24), (0.3, 25)):
+        V, W, H0 = pins.rand_problem(9, 7, 3, seed)
+        K, mu = 4, 1e-2
+        loss, gV, gW, gH, used = u.loss_and_grads_vwh(V, W, H0, K, mu, lam=lam)
+        # the V and H0 gradients are those of loss_and_grads (W's being a variable adds
+        # nothing to them)
+        if lam == 0.0:
+            _, gV2, gH2, _ = u.loss_and_grads(V, W, H0, K, mu)
+            np.testing.assert_allclose(gV, gV2, rtol=1e-12, atol=1e-14)
+            np.testing.assert_allclose(gH, gH2, rtol=1e-12, atol=1e-14)
+        d = 1e-6
+        for idx in [(0, 0), (1, 2), (4, 1), (8, 2), (6, 0), (3, 1)]:
+            Wp, Wm = W.copy(), W.copy()
+            Wp[idx] += d
+            Wm[idx] -= d
+            lp, _, _, _, up = u.loss_and_grads_vwh(V, Wp, H0, K, mu, lam=lam)
+            lm, _, _, _, um = u.loss_and_grads_vwh(V, Wm, H0, K, mu, lam=lam)
+            if any((a != b).any() for a, b in zip(up, used)) or any((a != b).any() for a, b in zip(um, used)):
+                continue
+            fd = (lp - lm) / (2 * d)
+            assert abs(gW[idx] - fd) <= 1e-5 * max(1.0, abs(fd)), (lam, idx, gW[idx], fd)
+            checked += 1
+    assert checked >= 8

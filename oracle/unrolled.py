@@ -89,6 +89,21 @@ def loss_and_grads_vwh(V, W, H0, K, mu, choices=None, lam=0.0):
     return float(loss.detach()), gV.numpy(), gW.numpy(), gH.numpy(), [u.numpy() for u in used]
 
 
+def step_vjp(V, W, Hk, choice, Hbar_next, lam=0.0):
+    """Vector-Jacobian product of one step at a GIVEN state Hk (with the selection held):
+    (dL/dH_k, the step's share of dL/dV, the step's share of dL/dW) for
+    dL/dH_{k+1} = Hbar_next, by autograd of h_step in float64.  Chaining these over the
+    states of another run (e.g. a float32 solve) gives the exact gradient along that run's
+    own trajectory, which separates the accuracy of an adjoint from that of the forward."""
+    V = torch.as_tensor(V, dtype=torch.float64).clone().requires_grad_(True)
+    W = torch.as_tensor(W, dtype=torch.float64).clone().requires_grad_(True)
+    Hk = torch.as_tensor(Hk, dtype=torch.float64).clone().requires_grad_(True)
+    Hn, _ = h_step(V, W, Hk, lam=lam, choice=torch.as_tensor(choice, dtype=torch.bool))
+    gH, gV, gW = torch.autograd.grad(Hn, (Hk, V, W),
+                                     grad_outputs=torch.as_tensor(Hbar_next, dtype=torch.float64))
+    return gH.numpy(), gV.numpy(), gW.numpy()
+
+
 def loss_and_grads(V, W, H0, K, mu, choices=None):
     """Loss d_KL(V, W H_K) + (mu / 2) |H_K|^2 and its gradients w.r.t. V and H0 (float64)."""
     V = torch.as_tensor(V, dtype=torch.float64).clone().requires_grad_(True)

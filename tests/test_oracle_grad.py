@@ -90,3 +90,26 @@ def test_unrolled_w_gradient_finite_differences():
             assert abs(gW[idx] - fd) <= 1e-5 * max(1.0, abs(fd)), (lam, idx, gW[idx], fd)
             checked += 1
     assert checked >= 8
+
+
+def test_step_vjp_chain_matches_unrolled_autograd():
+    """Chaining step_vjp over the oracle's own states gives loss_and_grads_vwh's gradients."""
+    V, W, H0 = pins.rand_problem(9, 7, 3, 26)
+    K, mu = 4, 1e-2
+    loss, gV, gW, gH, used = u.loss_and_grads_vwh(V, W, H0, K, mu)
+    Vt, Wt = torch.tensor(V, dtype=torch.float64), torch.tensor(W, dtype=torch.float64)
+    states = [torch.tensor(H0, dtype=torch.float64)]
+    for k in range(K):
+        states.append(u.h_step(Vt, Wt, states[-1], choice=torch.tensor(used[k]))[0])
+    # the loss's own gradients at H_K
+    Vl = Vt.clone().requires_grad_(True)
+    Wl = Wt.clone().requires_grad_(True)
+    HK = states[-1].clone().requires_grad_(True)
+    lk = u.kl(Vl, Wl @ HK) + 0.5 * mu * (HK * HK).sum()
+    hb, vb, wb = (g.numpy() for g in torch.autograd.grad(lk, (HK, Vl, Wl)))
+    for k in reversed(range(K)):
+        hb, dv, dw = u.step_vjp(V, W, states[k].numpy(), used[k], hb)
+        vb, wb = vb + dv, wb + dw
+    np.testing.assert_allclose(hb, gH, rtol=1e-10, atol=1e-12 * np.abs(gH).max())
+    np.testing.assert_allclose(vb, gV, rtol=1e-10, atol=1e-12 * np.abs(gV).max())
+    np.testing.assert_allclose(wb, gW, rtol=1e-10, atol=1e-12 * np.abs(gW).max())

@@ -217,7 +217,7 @@ def main(argv=None):
                     default="plain_large")
     ap.add_argument("--dtype", choices=["f32", "f64", "bf16"], default="f32")
     ap.add_argument("--engine", choices=["auto", "simt", "tensor"], default=None,
-                    help="default: tensor for f32 with R <= 128 (split bf16 products), else auto")
+                    help="default: tensor for f32 with R <= 512 (split bf16 products), else auto")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work")
     ap.add_argument("--ref-cols", type=int, default=512)
@@ -272,7 +272,7 @@ def main(argv=None):
     dev = torch.device("cuda", local)
     peaks = measured_peaks()
     if args.engine is None:
-        args.engine = "tensor" if (args.dtype == "f32" and R <= 128) else "auto"
+        args.engine = "tensor" if (args.dtype == "f32" and R <= 512) else "auto"
     engine_name = {"bf16": "tcgen05 (bf16 operands)", "f64": "simt"}.get(
         args.dtype, "tcgen05 (split bf16 operands, 3 products)" if args.engine == "tensor"
         else "simt")
@@ -332,9 +332,9 @@ def main(argv=None):
                 "config": {"workload": "precision_large", "desc": pspec["desc"],
                            "N": pspec["N"], "T": pspec["T"], "R": pspec["R"], "form": "BF16"}}
             if not args.no_c3_target:
-                # the metric at the precision form's own size: FP32 (its fastest engine at
-                # R = 512) against BF16, to the FP32 form's d_KL after c3_iters iterations
-                eng = "tensor" if pspec["R"] <= 128 else "simt"
+                # the metric at the precision form's own size: FP32 (the split tensor-core
+                # form) against BF16, to the FP32 form's d_KL after c3_iters iterations
+                eng = "tensor" if pspec["R"] <= 512 else "simt"
                 line["precision_form"]["time_to_target"] = time_to_target(
                     dna, torch, pprob, args.c3_iters, eng, "precision_large")
             del pprob
@@ -779,7 +779,7 @@ def run_sharded(args, world, rank, local):
     W = torch.from_numpy(prob.W).to(dev)
     H = torch.from_numpy(np.ascontiguousarray(prob.H[:, a:b])).to(dev)
     del prob
-    engine = args.engine or ("tensor" if R <= 128 else "auto")
+    engine = args.engine or ("tensor" if R <= 512 else "auto")
     ctx = dna.dna_create(N, b - a, R, dna.make_opts(dtype=dna.DNA_F32, engine=engine_code(dna, engine)))
     stream = torch.cuda.current_stream()
     dna.dna_set_stream(ctx, stream)

@@ -54,7 +54,7 @@ extern "C" {
                        float64 per-column cost sums                                      */
 
 /* Engines for the O(NRT) contractions.  AUTO: BF16 on the tensor cores, F32 and F64 on
- * the CUDA cores.  TENSOR with F32 (R <= 128): every float32 operand x is split into
+ * the CUDA cores.  TENSOR with F32 (R <= 512): every float32 operand x is split into
  * bf16 x_hi = bf16(x) and x_lo = bf16(x - x_hi) and every product is formed as
  * x_hi y_hi + x_hi y_lo + x_lo y_hi with float32 accumulation (relative error per product
  * below about 2^-15); dna_step_H_fixed, dna_step_H_adjoint and dna_kl_backward need the

@@ -58,6 +58,7 @@ struct dna_ctx {
     // tensor-core (BF16) path
     bool tc = false;
     bool split = false;              // FP32 form on the tensor cores (hi + lo bf16 operands)
+    int64_t qplane = 0;              // lo plane offset of the Q, Qbar workspace (split, RP > 128)
     int64_t plane = 0;               // elements between the hi and lo planes of each operand
     int rp = 0;                      // padded rank
     int64_t pad_o[2] = {0, 0};       // O_pad of the H view (0) and W view (1)
@@ -193,6 +194,11 @@ void plan_split(int64_t S, int64_t nblocks_os, int slots, int chunk, int* splits
 constexpr int64_t SPLIT_CHUNK = 128;
 constexpr int64_t SPLIT_MAX_CHUNKS = 8;
 
+// Pass 2 on the tensor cores balances (o-block, chunk) units over the SMs (pass2_split)
+// in the split form at RP <= 128 and the BF16 form at RP <= 256; else it streams the X
+// operands by K-slices over (o-block, split) tiles (pass2_large).
+bool balanced_pass2(const dna_ctx* c) { return c->split ? c->rp <= 128 : c->rp <= 256; }
+
 template <typename Tp>
 void plan_all(dna_ctx* c) {
     using S = dna::Simt<Tp>;
@@ -212,8 +218,9 @@ void plan_all(dna_ctx* c) {
             // partial A, B sums per split relative to V's bytes: 2 R / S
             const double part = 2.0 * (double)c->R / (double)Sdim;
             // CTA rows per o-block of pass 1: the 256-wide r-blocks of the contraction kernel
-            // (RP > 128), or the A and B halves of the split FP32 kernel
-            const int64_t rblocks = c->split ? 2 : (c->rp > 128 ? c->rp / 256 : 1);
+            // (RP > 128; in the split form each for A and for B), or the A and B halves of
+            // the split FP32 kernel
+            const int64_t rblocks = (c->split ? 2 : 1) * (c->rp > 128 ? c->rp / 256 : 1);
             // the split form, and pass 1 at ranks above 128, stream s in chunks of 128
             const int sch = c->split ? (int)SPLIT_CHUNK : tch;
             const int sch1 = c->split || c->rp > 128 ? (int)SPLIT_CHUNK : tch;
@@ -221,10 +228,10 @@ void plan_all(dna_ctx* c) {
                        &c->tper1[w], part, c->split ? SPLIT_MAX_CHUNKS : 0);
             plan_split(Sdim, c->pad_o[w] / tob, c->num_sms, c->rp > 256 ? (int)SPLIT_CHUNK : sch,
                        &c->tsp2[w], &c->tper2[w], 2.0 / (double)Sdim);
-            // pass 2 of the split form and of the BF16 form at R <= 256 balances (o-block,
-            // chunk) units over the SMs instead; at R > 256 each split has four cost slots
-            // (one per column group of the epilogue warps)
-            if (c->split || c->rp <= 256)
+            // pass 2 of the split form at R <= 128 and of the BF16 form at R <= 256 balances
+            // (o-block, chunk) units over the SMs instead; otherwise each split has four
+            // cost slots (one per column group of the epilogue warps)
+            if (balanced_pass2(c))
                 c->tsp2[w] = dna::TcBf16::pass2_split_slots(c->pad_o[w], Sdim, c->num_sms);
             else
                 c->tsp2[w] *= 4;
@@ -293,14 +300,15 @@ int alloc_workspace(dna_ctx* c) {
         e |= dmalloc(&c->Y2tk, b * np * (size_t)ps);
         e |= dmalloc(&c->Xmk, b * np * (size_t)po);
         e |= dmalloc(&c->Xdk, b * np * (size_t)po);
-        if (!c->split && c->rp > 128) {   // pass 1 in two kernels: the Q, Qbar workspace
+        if (c->rp > 128) {   // pass 1 in two kernels: the Q, Qbar workspace (hi, lo planes)
             size_t q = 0;
             for (int w = 0; w < 2; ++w) {
                 c->ldq[w] = ((w ? T : N) + 127) / 128 * 128;
                 q = std::max(q, (size_t)(c->pad_o[w] * c->ldq[w]));
             }
-            e |= dmalloc(&c->Qg, b * q);
-            e |= dmalloc(&c->Qbg, b * q);
+            c->qplane = c->split ? (int64_t)q : 0;
+            e |= dmalloc(&c->Qg, b * np * q);
+            e |= dmalloc(&c->Qbg, b * np * q);
         }
     }
     if (e != DNA_OK) return DNA_ERR_ALLOC;
@@ -481,7 +489,7 @@ dna::TcOperands tc_operands(const dna_ctx* c, int wstep) {
     op.Xmk = c->Xmk; op.Xdk = c->Xdk;
     op.plane = c->plane;
     op.ctas = c->num_sms;
-    op.Qg = c->Qg; op.Qbg = c->Qbg; op.ldq = c->ldq[wstep];
+    op.Qg = c->Qg; op.Qbg = c->Qbg; op.ldq = c->ldq[wstep]; op.qplane = c->qplane;
     tc_v(c, wstep, &op.V, &op.vs);
     return op;
 }
@@ -671,7 +679,7 @@ int step_core(dna_ctx* c, int w, bool mu_only, bool prepared, int stop) {
         e = phase(c, DNA_PHASE_PASS2, 1, [&] {
             if constexpr (sizeof(Tp) == 4)
                 if (tc)
-                    return c->split || c->rp <= 256
+                    return balanced_pass2(c)
                                ? dna::TcBf16::pass2_split(tc_operands(c, w), c->maps[w], c->dpart,
                                                           sp2, c->status, st)
                                : dna::TcBf16::pass2_large(tc_operands(c, w), c->maps[w],
@@ -834,7 +842,7 @@ int kl_async(dna_ctx* c) {
     if (c->sparse) return sparse_kl<Tp>(c);
     const View v = make_view(c, false);
     if constexpr (sizeof(Tp) == 4)
-        if (c->split) {   // the split tensor-core pass 2 on the H view's current operands
+        if (c->split && c->rp <= 128) {   // the split tensor-core pass 2 on the H view's operands
             if (int e = prep_step<Tp>(c, 0, false)) return e;
             return phase(c, DNA_PHASE_KL, 2, [&] {
                 int e = dna::TcBf16::kl_split(tc_operands(c, 0), c->maps[0], c->dpart,
@@ -1041,14 +1049,13 @@ int dna_create(int64_t N, int64_t T, int64_t R, const dna_opts* opts, dna_ctx** 
     if (opts) o = *opts;
     if (!valid_opts(o)) return DNA_ERR_ARG;
     // Engines: BF16 runs on the tensor cores (R <= 512).  F32 runs on the CUDA cores by
-    // default and on the tensor cores (split hi + lo bf16 operands, R <= 128) when the
+    // default and on the tensor cores (split hi + lo bf16 operands, R <= 512) when the
     // tensor engine is asked for.  F64 runs on the CUDA cores.
     const bool split = o.dtype == DNA_F32 && o.engine == DNA_ENGINE_TENSOR;
     const bool tc = o.dtype == DNA_BF16 || split;
     if (o.dtype == DNA_BF16 && (o.engine == DNA_ENGINE_SIMT || dna::TcBf16::rank_pad(R) == 0))
         return DNA_ERR_UNSUPPORTED;
-    if (split && (dna::TcBf16::rank_pad(R) == 0 || dna::TcBf16::rank_pad(R) > 128))
-        return DNA_ERR_UNSUPPORTED;
+    if (split && dna::TcBf16::rank_pad(R) == 0) return DNA_ERR_UNSUPPORTED;
     if (o.dtype == DNA_F64 && o.engine == DNA_ENGINE_TENSOR) return DNA_ERR_UNSUPPORTED;
     dna_ctx* c = new (std::nothrow) dna_ctx();
     if (!c) return DNA_ERR_ALLOC;

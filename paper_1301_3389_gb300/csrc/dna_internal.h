@@ -193,11 +193,13 @@ struct TcOperands {
     // elements after it, a lo plane (x = hi + lo, both bf16); 0 in the BF16 form
     int64_t plane;
     int ctas;   // CTAs of the persistent kernels (the SM count)
-    // BF16 form at RP > 128: bf16 workspace rows Q[o][s], Qbar[o][s] ([O_pad][ldq], ldq a
-    // multiple of 128) written by the ratios kernel of pass 1 and read by its contraction
+    // pass 1 at RP > 128: bf16 workspace rows Q[o][s], Qbar[o][s] ([O_pad][ldq], ldq a
+    // multiple of 128) written by the ratios kernel of pass 1 and read by its contraction;
+    // in the FP32 form a lo plane follows each, qplane elements after its hi plane
     void* Qg;
     void* Qbg;
     int64_t ldq;
+    int64_t qplane;
 };
 
 // TMA descriptors of one half-step view (built once per bound problem).
@@ -206,6 +208,7 @@ struct TcMaps {
     CUtensorMap q, qb;                                 // Q, Qbar workspace (RP > 128)
     CUtensorMap y128, yt256, y2t256;                   // larger boxes of Y, Yt, Y2t (RP > 128)
     CUtensorMap x_l, y_l, yt_l, y2t_l, xm_l, xd_l;   // lo planes (FP32 form, tensor cores)
+    CUtensorMap q_l, qb_l, y128_l, yt256_l, y2t256_l;  // lo planes, FP32 form at RP > 128
 };
 
 struct TcBf16 {
@@ -231,8 +234,9 @@ struct TcBf16 {
     // Apart/Bpart [splits][R][O] with splits = ceil(S / s_per), s_per a multiple of 64
     static int pass1_mat(const TcOperands& op, const TcMaps& maps, float* Apart, float* Bpart,
                          int splits, int64_t s_per, bool with_b, int* status, cudaStream_t st);
-    // pass 2 at padded rank 512 (tc_ks.cu): persistent CTAs over (o-block, split) tiles,
-    // s_per a multiple of 128, cost slots dpart[4 splits][2][O]
+    // pass 2 at padded rank 512, and of the split form at 256 and 512 (tc_ks.cu):
+    // persistent CTAs over (o-block, split) tiles, s_per a multiple of 128, cost slots
+    // dpart[4 splits][2][O]
     static int pass2_large(const TcOperands& op, const TcMaps& maps, double* dpart, int slots,
                            int64_t s_per, int* status, cudaStream_t st);
     // The FP32 form on the tensor cores (tc_split.cu): the same passes with every operand
@@ -241,6 +245,11 @@ struct TcBf16 {
     static int pass1_split(const TcOperands& op, const TcMaps& maps, float* Apart,
                            float* Bpart, int splits, int64_t s_per, bool with_b, int* status,
                            cudaStream_t st);
+    // pass 1 of the split form at RP in {256, 512} (tc_mats.cu): the ratios kernel writes
+    // the hi / lo planes of Q, Qbar, then the contraction accumulates A (and B) per split;
+    // s_per a multiple of 64 and at most 1024
+    static int pass1_mats(const TcOperands& op, const TcMaps& maps, float* Apart, float* Bpart,
+                          int splits, int64_t s_per, bool with_b, int* status, cudaStream_t st);
     // pass 2 of the split form (RP <= 128) and of the BF16 form (RP <= 256)
     static int pass2_split(const TcOperands& op, const TcMaps& maps, double* dpart, int slots,
                            int* status, cudaStream_t st);

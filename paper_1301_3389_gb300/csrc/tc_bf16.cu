@@ -453,6 +453,19 @@ int TcBf16::make_maps(TcMaps* m, const TcOperands& op, const float* V, int64_t v
         if (!e) e = make_map(&m->yt256, BF, op.Ytk, op.S_pad, rp, op.S_pad * 2, SCH, 256, SW);
         if (!e) e = make_map(&m->y2t256, BF, op.Y2tk, op.S_pad, rp, op.S_pad * 2, SCH, 256, SW);
     }
+    if (!e && op.Qg && op.plane) {   // lo planes of pass 1 of the split form at RP > 128
+        const bf16* ql = static_cast<const bf16*>(op.Qg) + op.qplane;
+        const bf16* qbl = static_cast<const bf16*>(op.Qbg) + op.qplane;
+        e = make_map(&m->q_l, BF, ql, (uint64_t)op.ldq, op.O_pad, (uint64_t)op.ldq * 2, 64, OBLK, SW);
+        if (!e) e = make_map(&m->qb_l, BF, qbl, (uint64_t)op.ldq, op.O_pad, (uint64_t)op.ldq * 2, 64,
+                             OBLK, SW);
+        if (!e) e = make_map(&m->y128_l, BF, static_cast<const bf16*>(op.Yk) + op.plane, rp, op.S_pad,
+                             rp * 2, 64, 128, SW);
+        if (!e) e = make_map(&m->yt256_l, BF, static_cast<const bf16*>(op.Ytk) + op.plane, op.S_pad,
+                             rp, op.S_pad * 2, SCH, 256, SW);
+        if (!e) e = make_map(&m->y2t256_l, BF, static_cast<const bf16*>(op.Y2tk) + op.plane,
+                             op.S_pad, rp, op.S_pad * 2, SCH, 256, SW);
+    }
     if (!e && op.plane) {   // lo planes of the split FP32 form
         const bf16* yl = static_cast<const bf16*>(op.Yk) + op.plane;
         const bf16* ytl = static_cast<const bf16*>(op.Ytk) + op.plane;

@@ -84,6 +84,14 @@ constexpr int W_PRODUCER = W_EPI;
 constexpr int P1_THREADS = (W_EPI + 3) * 32;      // producer + two MMA warps
 constexpr int W_MMA_Z = W_EPI + 1, W_MMA_AB = W_EPI + 2;
 
+// v -> (hi, lo) bf16 pairs of two values: hi = bf16(v), lo = bf16(v - hi) (the operand
+// split of the FP32 form on the tensor cores).
+__device__ __forceinline__ void split2(float v0, float v1, uint32_t& hi, uint32_t& lo) {
+    hi = pack_bf16x2(v0, v1);
+    const float h0 = __uint_as_float(hi << 16), h1 = __uint_as_float(hi & 0xffff0000u);
+    lo = pack_bf16x2(v0 - h0, v1 - h1);
+}
+
 // X rows [o][rp] (bf16, global) -> tensor memory, 16-column unit `unit` (32 values of r)
 // of the lane quadrant addressed by taddr.
 __device__ __forceinline__ void x_to_tmem(const bf16* __restrict__ X, int64_t rp, int64_t o,

@@ -60,7 +60,7 @@ struct Cursor {
 
 }  // namespace ks
 
-// ---------------------------------------------------------------- pass 2, RP = 512
+// ---------------------------------------------------------------- pass 2, RP = 512 (and split)
 // Candidate costs (Algorithm 1 steps 6-9 and 19-22): Z_mu = X_mu Y^t and Z_dna = X_dna
 // Y^t per chunk of 128 values of s, both operands from shared memory (tensor memory holds
 // two Z pairs, 4 x 128 columns, and no X), X_mu, X_dna and Y streaming together through a
@@ -70,12 +70,19 @@ struct Cursor {
 // over a chunk, then in float64.  Persistent over (o-block, split) tiles, o-block fastest,
 // so CTAs that run at the same time share the Y slices in L2.  Each epilogue warp writes
 // its own sums: cost slot 4 split + w / 4 of dpart[slot][2][O].
+//
+// SPLIT: the FP32 form on the tensor cores (RP in {256, 512}): every operand as hi and lo
+// bf16 planes, a K-slice holds X_mu, X_dna hi / lo and Y hi / lo (96 KB, two stages), and
+// each Z takes the three products hi hi, hi lo, lo hi.
 namespace ks {
+template <bool SPLIT>
 struct Layout2 {
-    static constexpr int KST = 4;
+    static constexpr int NP = SPLIT ? 2 : 1;               // planes per operand
+    static constexpr int KST = SPLIT ? 2 : 4;
     static constexpr uint32_t X_SLICE = OBLK * 64 * 2;   // [128 o][64 r]
     static constexpr uint32_t Y_SLICE = SC * 64 * 2;     // [128 s][64 r]
-    static constexpr uint32_t K_STAGE = 2 * X_SLICE + Y_SLICE;
+    // X_mu hi (lo), X_dna hi (lo), Y hi (lo)
+    static constexpr uint32_t K_STAGE = NP * (2 * X_SLICE + Y_SLICE);
     static constexpr uint32_t BAR = KST * K_STAGE;
     static constexpr uint32_t TOTAL = BAR + 256;
     static constexpr uint32_t NCOLS = 512;   // (Z_mu, Z_dna) x 2, 128 columns each
@@ -86,12 +93,13 @@ enum { C_KFULL = 0, C_KEMPTY = 4, C_ZFULL = 8, C_ZEMPTY = 10, C_DRAIN = 12, C_CO
 constexpr int P2K_THREADS = (W_EPI + 2) * 32;   // epilogue warps, producer, MMA issuer
 }  // namespace ks
 
-template <int RP>
+template <int RP, bool SPLIT>
 __global__ void __launch_bounds__(ks::P2K_THREADS, 1)
     k_tc_pass2_kt(P2Args a, int nob, int nsplit, int ntiles,
                   const __grid_constant__ CUtensorMap tmXm, const __grid_constant__ CUtensorMap tmXd,
-                  const __grid_constant__ CUtensorMap tmY) {
-    using L = ks::Layout2;
+                  const __grid_constant__ CUtensorMap tmY, const __grid_constant__ CUtensorMap tmXml,
+                  const __grid_constant__ CUtensorMap tmXdl, const __grid_constant__ CUtensorMap tmYl) {
+    using L = ks::Layout2<SPLIT>;
     using namespace ks;
     constexpr int KST = L::KST, KS = RP / 64;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -128,6 +136,9 @@ __global__ void __launch_bounds__(ks::P2K_THREADS, 1)
     if (warp == W_PRODUCER) {
         if (lane == 0 && t_begin < t_end) {
             tma_prefetch_desc(&tmXm); tma_prefetch_desc(&tmXd); tma_prefetch_desc(&tmY);
+            if (SPLIT) {
+                tma_prefetch_desc(&tmXml); tma_prefetch_desc(&tmXdl); tma_prefetch_desc(&tmYl);
+            }
             Cursor ck_;
             ck_.start(t_begin, nob, nsplit, a);
             int kk_ = 0;
@@ -140,11 +151,19 @@ __global__ void __launch_bounds__(ks::P2K_THREADS, 1)
                 const int32_t r0 = 64 * ck_.sub;
                 const int32_t s0 = (int32_t)(ck_.x.s_begin + (int64_t)ck_.k * SC);
                 mbar_arrive_expect_tx(&bar[C_KFULL + st], L::K_STAGE);
-                tma_load_2d(dst, &tmXm, r0, (int32_t)ck_.x.o0, &bar[C_KFULL + st]);
-                tma_load_2d(dst + L::X_SLICE, &tmXd, r0, (int32_t)ck_.x.o0, &bar[C_KFULL + st]);
-                tma_load_2d(dst + 2 * L::X_SLICE, &tmY, r0, s0, &bar[C_KFULL + st]);
-                tma_load_2d(dst + 2 * L::X_SLICE + SCH * 128, &tmY, r0, s0 + SCH,
-                            &bar[C_KFULL + st]);
+                // plane p of the stage: X_mu, X_dna, Y (p = 1: the lo planes)
+#pragma unroll
+                for (int p = 0; p < L::NP; ++p) {
+                    const uint32_t d = dst + (uint32_t)p * (2 * L::X_SLICE + L::Y_SLICE);
+                    const CUtensorMap* mxm = p ? &tmXml : &tmXm;
+                    const CUtensorMap* mxd = p ? &tmXdl : &tmXd;
+                    const CUtensorMap* my = p ? &tmYl : &tmY;
+                    tma_load_2d(d, mxm, r0, (int32_t)ck_.x.o0, &bar[C_KFULL + st]);
+                    tma_load_2d(d + L::X_SLICE, mxd, r0, (int32_t)ck_.x.o0, &bar[C_KFULL + st]);
+                    tma_load_2d(d + 2 * L::X_SLICE, my, r0, s0, &bar[C_KFULL + st]);
+                    tma_load_2d(d + 2 * L::X_SLICE + SCH * 128, my, r0, s0 + SCH,
+                                &bar[C_KFULL + st]);
+                }
             }
             if (*abort)   // let the copies already issued land before the CTA exits
                 for (int k = max(0, kk_ - KST); k < kk_; ++k)
@@ -171,13 +190,20 @@ __global__ void __launch_bounds__(ks::P2K_THREADS, 1)
                         if (!(ok = wait_phase(&bar[C_KFULL + j % KST], (j / KST) & 1, abort)))
                             break;
                         const uint32_t xs = sbase + (j % KST) * L::K_STAGE;
-                        const uint32_t ys = xs + 2 * L::X_SLICE;
+                        // product p: (X hi, Y hi), (X hi, Y lo), (X lo, Y hi); one in BF16
+                        constexpr uint32_t PL = 2 * L::X_SLICE + L::Y_SLICE;
 #pragma unroll
-                        for (int kq = 0; kq < 4; ++kq) {
-                            const uint64_t yd = desc_sw128(ys + 32u * kq);
-                            const uint32_t acc = (ks > 0 || kq > 0) ? 1u : 0u;
-                            mma_bf16(zm, desc_sw128(xs + 32u * kq), yd, idesc, acc);
-                            mma_bf16(zd, desc_sw128(xs + L::X_SLICE + 32u * kq), yd, idesc, acc);
+                        for (int p = 0; p < (SPLIT ? 3 : 1); ++p) {
+                            const uint32_t xp = xs + (p == 2 ? PL : 0u);
+                            const uint32_t ys = xs + (p == 1 ? PL : 0u) + 2 * L::X_SLICE;
+#pragma unroll
+                            for (int kq = 0; kq < 4; ++kq) {
+                                const uint64_t yd = desc_sw128(ys + 32u * kq);
+                                const uint32_t acc = (ks > 0 || p > 0 || kq > 0) ? 1u : 0u;
+                                mma_bf16(zm, desc_sw128(xp + 32u * kq), yd, idesc, acc);
+                                mma_bf16(zd, desc_sw128(xp + L::X_SLICE + 32u * kq), yd, idesc,
+                                         acc);
+                            }
                         }
                         mma_commit(&bar[C_KEMPTY + j % KST]);
                     }
@@ -273,11 +299,11 @@ __global__ void __launch_bounds__(ks::P2K_THREADS, 1)
     if (warp == 0) tmem_dealloc(tmem, L::NCOLS);
 }
 
-template <int RP>
+template <int RP, bool SPLIT>
 int launch_pass2_kt(const P2Args& a, const TcMaps& m, int64_t O_pad, int splits, int ctas,
                     cudaStream_t st) {
-    const uint32_t smem = ks::Layout2::TOTAL + 1024;
-    auto k = k_tc_pass2_kt<RP>;
+    const uint32_t smem = ks::Layout2<SPLIT>::TOTAL + 1024;
+    auto k = k_tc_pass2_kt<RP, SPLIT>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return DNA_ERR_CUDA;
@@ -285,7 +311,12 @@ int launch_pass2_kt(const P2Args& a, const TcMaps& m, int64_t O_pad, int splits,
     const int ntiles = nob * splits;
     if (ntiles == 0) return DNA_OK;
     const int grid = ctas > 0 ? std::min(ctas, ntiles) : ntiles;
-    k<<<grid, ks::P2K_THREADS, smem, st>>>(a, nob, splits, ntiles, m.xm, m.xd, m.y);
+    if (SPLIT)
+        k<<<grid, ks::P2K_THREADS, smem, st>>>(a, nob, splits, ntiles, m.xm, m.xd, m.y, m.xm_l,
+                                               m.xd_l, m.y_l);
+    else   // the lo maps are not read
+        k<<<grid, ks::P2K_THREADS, smem, st>>>(a, nob, splits, ntiles, m.xm, m.xd, m.y, m.xm,
+                                               m.xd, m.y);
     return after_launch();
 }
 
@@ -300,7 +331,12 @@ int TcBf16::pass2_large(const TcOperands& op, const TcMaps& maps, double* dpart,
     if (s_per % tc::ks::SC != 0 || slots % 4 != 0) return DNA_ERR_ARG;
     const int splits = slots / 4;
     if (splits != (int)((op.S + s_per - 1) / s_per)) return DNA_ERR_ARG;
-    if (a.rp == 512) return tc::launch_pass2_kt<512>(a, maps, op.O_pad, splits, op.ctas, st);
+    if (op.plane) {   // the FP32 form on the tensor cores
+        if (a.rp == 256) return tc::launch_pass2_kt<256, true>(a, maps, op.O_pad, splits, op.ctas, st);
+        if (a.rp == 512) return tc::launch_pass2_kt<512, true>(a, maps, op.O_pad, splits, op.ctas, st);
+        return DNA_ERR_UNSUPPORTED;
+    }
+    if (a.rp == 512) return tc::launch_pass2_kt<512, false>(a, maps, op.O_pad, splits, op.ctas, st);
     return DNA_ERR_UNSUPPORTED;
 }
 

@@ -29,13 +29,6 @@
 namespace dna {
 namespace tc {
 
-// v -> (hi, lo) bf16 pairs of two values: hi = bf16(v), lo = bf16(v - hi).
-__device__ __forceinline__ void split2(float v0, float v1, uint32_t& hi, uint32_t& lo) {
-    hi = pack_bf16x2(v0, v1);
-    const float h0 = __uint_as_float(hi << 16), h1 = __uint_as_float(hi & 0xffff0000u);
-    lo = pack_bf16x2(v0 - h0, v1 - h1);
-}
-
 constexpr int SC2 = 128;   // values of s per chunk
 
 template <int RP>
@@ -874,6 +867,8 @@ int TcBf16::pass1_split(const TcOperands& op, const TcMaps& maps, float* Apart, 
         return tc::launch_pass1s<64>(a, with_b, maps, op.O_pad, splits, op.ctas, st);
     if (a.rp == 128)
         return tc::launch_pass1s<128>(a, with_b, maps, op.O_pad, splits, op.ctas, st);
+    if (a.rp == 256 || a.rp == 512)   // ratios + contraction kernels (tc_mats.cu)
+        return pass1_mats(op, maps, Apart, Bpart, splits, s_per, with_b, status, st);
     return DNA_ERR_UNSUPPORTED;
 }
 

@@ -61,10 +61,64 @@ def test_split_persistent_tiles_and_segments():
         assert abs(kl_gpu - kl_ref) <= 1e-5 * abs(kl_ref)
 
 
+LARGE = [(300, 700, 129), (257, 500, 300), (520, 640, 512)]
+
+
+@pytest.mark.parametrize("shape", LARGE, ids=lambda s: "x".join(map(str, s)))
+def test_split_large_rank_half_steps(shape):
+    """Padded ranks 256 and 512 (the ratios + contraction pass 1 and the K-sliced pass 2 of
+    the split form): two DNA iterations from the oracle's state, each half-step within 1e-4
+    relative (Frobenius) and the element-wise bound."""
+    N, T, R = shape
+    p = workloads.custom(N, T, R, seed=N + 3 * T + 7 * R)
+    with GpuProblem(p.V, p.W, p.H, "f32t") as gp:
+        gp.dna.dna_normalize(gp.ctx, 1)
+        W, H = o.normalize_w_columns(p.W, p.H)
+        worst = 0.0
+        for _ in range(2):
+            for which in (0, 1):
+                W, H, _ = step_pair(gp, W, H, which)
+                Wg, Hg = gp.WH()
+                worst = max(worst, rel_fro(Wg, W), rel_fro(Hg, H))
+                assert rel_elem(Wg, W, "f32t-large W") < ELEM_TOL["f32t"]
+                assert rel_elem(Hg, H, "f32t-large H") < ELEM_TOL["f32t"]
+        kl_gpu = gp.dna.dna_kl(gp.ctx)
+        kl_ref = o.kl_divergence(p.V.astype(np.float64), W @ H)
+        print(f"\n{shape}: worst W/H error over 2 iterations {worst:.2e}")
+        assert worst < 1e-4
+        assert abs(kl_gpu - kl_ref) <= 1e-5 * abs(kl_ref)
+
+
+def test_split_large_rank_many_tiles():
+    """R = 300 (padded 512) at a size where each kernel's CTAs run several tiles: the
+    contraction has two (H step) and three (W step) splits of s, the ratios kernel several
+    chunks per tile, pass 2 several (o-block, split) tiles per CTA.  One iteration from the
+    oracle's state, then four MU iterations (the ratios kernel without Qbar)."""
+    N, T, R = 2100, 2600, 300
+    p = workloads.custom(N, T, R, seed=77)
+    with GpuProblem(p.V, p.W, p.H, "f32t") as gp:
+        gp.dna.dna_normalize(gp.ctx, 1)
+        W, H = o.normalize_w_columns(p.W, p.H)
+        for which in (0, 1):
+            W, H, _ = step_pair(gp, W, H, which)
+            Wg, Hg = gp.WH()
+            assert rel_fro(Wg, W) < 1e-4 and rel_fro(Hg, H) < 1e-4
+            assert rel_elem(Wg, W, "f32t-tiles W") < ELEM_TOL["f32t"]
+            assert rel_elem(Hg, H, "f32t-tiles H") < ELEM_TOL["f32t"]
+        gp.dna.mu_iterate(gp.ctx, 4)
+        V = p.V.astype(np.float64)
+        for _ in range(4):
+            W, H = o.mu_iteration(V, W, H)
+        Wg, Hg = gp.WH()
+        assert rel_fro(Wg, W) < 1e-4 and rel_fro(Hg, H) < 1e-4
+        assert rel_elem(Wg, W, "f32t-tiles mu W") < ELEM_TOL["f32t"]
+        assert rel_elem(Hg, H, "f32t-tiles mu H") < ELEM_TOL["f32t"]
+
+
 def test_split_unsupported_rank():
     import paper_1301_3389_gb300 as dna
     with pytest.raises(dna.DNAError) as e:
-        dna.dna_create(64, 64, 200, dna.make_opts(dtype=dna.DNA_F32, engine=dna.DNA_ENGINE_TENSOR))
+        dna.dna_create(64, 64, 513, dna.make_opts(dtype=dna.DNA_F32, engine=dna.DNA_ENGINE_TENSOR))
     assert e.value.code == dna.DNA_ERR_UNSUPPORTED
 
 

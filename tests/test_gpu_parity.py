@@ -110,11 +110,9 @@ SHAPES = [(1, 1, 1), (3, 5, 2), (67, 131, 17), (130, 70, 33), (129, 200, 64),
 @pytest.mark.parametrize("kind", ["f32", "f32t", "f64"])
 @pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(map(str, s)))
 def test_ragged_shapes(shape, kind):
-    """Odd sizes: several tiles plus ragged tails in N, T and R (R up to 512; the
-    tensor-core FP32 form takes R up to 128)."""
+    """Odd sizes: several tiles plus ragged tails in N, T and R (R up to 512, padded to 64,
+    128, 256 or 512 on the tensor cores)."""
     N, T, R = shape
-    if kind == "f32t" and R > 128:
-        pytest.skip("the split FP32 tensor-core form takes R <= 128")
     p = workloads.custom(N, T, R, seed=N * 7 + T * 3 + R)
     _trajectory(p, kind, 2)
 

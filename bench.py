@@ -476,12 +476,14 @@ def measure(dna, torch, dist, prob, dtype, args, world, local, peaks, clocks, en
     split = dtype == "f32" and engine == "tensor"
     if split:
         # FP32-accurate products from three bf16 products each: the tensor peak available
-        # to them is a third of the bf16 peak.  Executed bf16 work per launch: pass 1 runs
-        # GEMM1 in both its A and B halves (2 x 3 x 2RNT) plus GEMM2/3 (2 x 3 x 2RNT);
-        # pass 2 runs 2 x 3 x 2RNT.
+        # to them is a third of the bf16 peak.  Executed bf16 work per launch: at R <= 128
+        # pass 1 runs GEMM1 in both its A and B halves (2 x 3 x 2RNT) plus GEMM2/3
+        # (2 x 3 x 2RNT); at R > 128 its ratios kernel forms Z once (3 x 2RNT) and its
+        # contraction A and B (2 x 3 x 2RNT); pass 2 runs 2 x 3 x 2RNT.
         bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
         fp32_peak = bf16_peak / 3.0
-        executed = (24 if dom == "pass1" else 12) * R * N * T
+        p1_exec = 24 if R <= 128 else 18
+        executed = (p1_exec if dom == "pass1" else 12) * R * N * T
         roof = {"bound": "tensor", "achieved": flops / per_launch_s / 1e12, "peak": fp32_peak,
                 "unit": "TFLOP/s",
                 "peak_source": "measured burst dense bf16 (MEASURED_PEAKS.json) / 3: three bf16 "

@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 import workloads
-from gpu_helpers import ELEM_TOL, GpuProblem, rel_elem, rel_fro, step_pair
+from gpu_helpers import ELEM_TOL, SPLIT_LARGE_R_TOL, GpuProblem, rel_elem, rel_fro, step_pair
 from oracle import dna as o
 
 pytestmark = pytest.mark.gpu
@@ -22,11 +22,12 @@ TOL = {"f32": 1e-4, "f32t": 1e-4, "f64": 1e-10}
 
 def _trajectory(p, kind, iters, mu=False, **opts):
     V = p.V.astype(np.float64)
+    tol = SPLIT_LARGE_R_TOL if (kind == "f32t" and p.W.shape[1] > 300) else TOL[kind]
     with GpuProblem(p.V, p.W, p.H, kind, **{k: v for k, v in opts.items()}) as gp:
         gp.dna.dna_normalize(gp.ctx, 1)
         W, H = o.normalize_w_columns(p.W, p.H, opts.get("lam", 0.0))
         Wg, Hg = gp.WH()
-        assert rel_fro(Wg, W) < TOL[kind] and rel_fro(Hg, H) < TOL[kind]
+        assert rel_fro(Wg, W) < tol and rel_fro(Hg, H) < tol
         flips = 0
         oopts = {"eps": opts.get("eps", o.EPS), "alpha": opts.get("alpha", o.ALPHA),
                  "rho": opts.get("rho", 0.0), "lam": opts.get("lam", 0.0)}
@@ -36,13 +37,13 @@ def _trajectory(p, kind, iters, mu=False, **opts):
                 flips += nf
                 Wg, Hg = gp.WH()
                 ew, eh = rel_fro(Wg, W), rel_fro(Hg, H)
-                assert ew < TOL[kind] and eh < TOL[kind], (it, which, ew, eh)
+                assert ew < tol and eh < tol, (it, which, ew, eh)
                 xw = rel_elem(Wg, W, f"{kind} W it{it}.{which}")
                 xh = rel_elem(Hg, H, f"{kind} H it{it}.{which}")
                 assert xw < ELEM_TOL[kind] and xh < ELEM_TOL[kind], (it, which, xw, xh)
         kl_gpu = gp.dna.dna_kl(gp.ctx)
         kl_ref = o.kl_divergence(V, W @ H)
-        assert abs(kl_gpu - kl_ref) <= TOL[kind] * abs(kl_ref), (kl_gpu, kl_ref)
+        assert abs(kl_gpu - kl_ref) <= tol * abs(kl_ref), (kl_gpu, kl_ref)
     return flips
 
 

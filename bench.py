@@ -340,16 +340,26 @@ def main(argv=None):
             del pprob
         if args.workload == "plain_large" and not args.no_batched:
             # the batching form: 512 uneven problems, one grouped launch per phase, CUDA graph
-            bres = measure_batched(dna, torch, workloads.batched(512, seed=rank),
-                                   max(3, min(args.steps, 10)), args.warmup, peaks)
+            bprobs = workloads.batched(512, seed=rank)
+            bsteps = max(3, min(args.steps, 10))
+            bres = measure_batched(dna, torch, bprobs, bsteps, args.warmup, peaks)
             line["batched_form"] = {
-                "value": max(3, min(args.steps, 10)) / (bres["ms"] / 1e3),
+                "value": bsteps / (bres["ms"] / 1e3),
                 "unit": "grouped DNA iterations/s (all 512 problems)",
-                "ms_per_step": bres["ms"] / max(3, min(args.steps, 10)),
+                "ms_per_step": bres["ms"] / bsteps,
                 "split_rows": bres["rows"], "gpu_launches": bres["launches"],
                 "roofline": bres["roofline"],
                 "config": {"workload": "batched", "desc": BATCHED_DESC, "sum_NT": bres["nt"],
-                           "engine": "simt grouped + CUDA graph"}}
+                           "form": "F32", "engine": "simt grouped + CUDA graph"}}
+            bb = measure_batched(dna, torch, bprobs, bsteps, args.warmup, peaks, bf16=True)
+            line["batched_form"]["bf16"] = {
+                "value": bsteps / (bb["ms"] / 1e3),
+                "unit": "grouped DNA iterations/s (all 512 problems)",
+                "ms_per_step": bb["ms"] / bsteps, "split_rows": bb["rows"],
+                "pass2_units_per_cta": bb["units"], "gpu_launches": bb["launches"],
+                "roofline": bb["roofline"],
+                "config": {"form": "BF16", "engine": "tcgen05 grouped passes + CUDA graph"}}
+            del bprobs
         if args.workload == "plain_large" and not args.no_sparse:
             sp = workloads.sparse_tdt2(rank)
             line["sparse_form"] = measure_sparse(dna, torch, sp, max(3, min(args.steps, 50)),
@@ -823,21 +833,25 @@ def run_sharded(args, world, rank, local):
     return 0
 
 
-def measure_batched(dna, torch, probs, steps, warmup, peaks):
-    """Grouped DNA iterations of all problems (every phase one persistent grouped launch,
-    the iteration replayed as a CUDA graph, split sizes autotuned), timed with CUDA events."""
+def measure_batched(dna, torch, probs, steps, warmup, peaks, bf16=False):
+    """Grouped DNA iterations of all problems (every phase one grouped launch, the
+    iteration replayed as a CUDA graph, tile sizes autotuned), timed with CUDA events.
+    bf16: the BF16 form (passes on the tensor cores), else FP32 on the CUDA cores."""
     dev = torch.device("cuda", torch.cuda.current_device())
     V = [torch.from_numpy(p.V).to(dev) for p in probs]
     W = [torch.from_numpy(p.W).to(dev) for p in probs]
     H = [torch.from_numpy(p.H).to(dev) for p in probs]
     shapes = [p.shape for p in probs]
-    g = dna.dna_group_create([s[0] for s in shapes], [s[1] for s in shapes], [s[2] for s in shapes])
+    opts = dna.make_opts(dtype=dna.DNA_BF16) if bf16 else None
+    g = dna.dna_group_create([s[0] for s in shapes], [s[1] for s in shapes], [s[2] for s in shapes],
+                             opts)
     stream = torch.cuda.current_stream()
     try:
         dna.dna_group_set_stream(g, stream)
         dna.dna_group_bind(g, V, W, H)
         dna.dna_group_normalize(g, 1)
         rows = dna.dna_group_autotune(g, 2)
+        _, units = dna.dna_group_tile_config(g)
         dna.dna_group_use_graph(g, True)
         kl0 = dna.dna_group_kl(g, len(probs))
         dna.dna_group_iterate(g, warmup)
@@ -858,18 +872,32 @@ def measure_batched(dna, torch, probs, steps, warmup, peaks):
     flops = sum(20 * s[2] * s[0] * s[1] for s in shapes)   # 10 R flop per element per half-step
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    alu = SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     step_s = ms / steps / 1e3
     achieved = flops / step_s / 1e12
-    return {"ms": ms, "rows": rows, "launches": launches, "kl0": kl0, "kl1": kl1, "nt": nt,
-            "roofline": {"bound": "alu", "kernel": "whole grouped iteration",
-                         "achieved": achieved, "peak": alu, "unit": "TFLOP/s",
-                         "frac": achieved / alu, "traffic": None,
-                         "algorithmic_flops_per_step": flops,
-                         "algorithmic_bytes_per_step": alg_bytes,
-                         "hbm_frac": alg_bytes / step_s / 1e9 / hbm,
-                         "peak_source": (f"derived: {SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes "
-                                         f"x 2 flop x {sm_max:.0f} MHz")}}
+    out = {"ms": ms, "rows": rows, "units": units, "launches": launches, "kl0": kl0, "kl1": kl1,
+           "nt": nt}
+    if bf16:
+        # at R <= 64 the grouped passes read far more bytes than the tensor pipe needs time
+        # for: HBM bound (V, float32, 16 bytes per element per iteration)
+        tensor = float(peaks.get("bf16_tflops", 1900.0))
+        out["roofline"] = {"bound": "hbm", "kernel": "whole grouped iteration",
+                           "achieved": alg_bytes / step_s / 1e9, "peak": hbm, "unit": "GB/s",
+                           "frac": alg_bytes / step_s / 1e9 / hbm, "traffic": None,
+                           "algorithmic_flops_per_step": flops,
+                           "algorithmic_bytes_per_step": alg_bytes,
+                           "tensor_frac": achieved / tensor,
+                           "peak_source": "measured HBM copy (MEASURED_PEAKS.json)"}
+    else:
+        alu = SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+        out["roofline"] = {"bound": "alu", "kernel": "whole grouped iteration",
+                           "achieved": achieved, "peak": alu, "unit": "TFLOP/s",
+                           "frac": achieved / alu, "traffic": None,
+                           "algorithmic_flops_per_step": flops,
+                           "algorithmic_bytes_per_step": alg_bytes,
+                           "hbm_frac": alg_bytes / step_s / 1e9 / hbm,
+                           "peak_source": (f"derived: {SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes "
+                                           f"x 2 flop x {sm_max:.0f} MHz")}
+    return out
 
 
 def run_batched(args, world, rank, local):
@@ -888,7 +916,8 @@ def run_batched(args, world, rank, local):
     time.sleep(0.3)
     if world > 1:
         dist.barrier()
-    res = measure_batched(dna, torch, probs, args.steps, args.warmup, measured_peaks())
+    bf16 = args.dtype == "bf16"
+    res = measure_batched(dna, torch, probs, args.steps, args.warmup, measured_peaks(), bf16=bf16)
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
@@ -900,10 +929,12 @@ def run_batched(args, world, rank, local):
         "metric": METRIC, "value": value, "unit": "grouped DNA iterations/s (all 512 problems)",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": "bf16" if bf16 else "f32", "data": "synthetic",
         "config": {"workload": "batched", "desc": BATCHED_DESC, "problems": len(probs),
-                   "sum_NT": res["nt"], "form": "F32", "engine": "simt grouped + CUDA graph",
-                   "split_rows": res["rows"],
+                   "sum_NT": res["nt"], "form": "BF16" if bf16 else "F32",
+                   "engine": ("tcgen05 grouped passes + CUDA graph" if bf16
+                              else "simt grouped + CUDA graph"),
+                   "split_rows": res["rows"], "pass2_units_per_cta": res["units"],
                    "l2": "inputs larger than L2 (V totals %d MB)" % (res["nt"] * 4 >> 20)},
         "gpu_launches": res["launches"],
         "roofline": res["roofline"],

@@ -270,17 +270,22 @@ int dna_phase_times(dna_ctx* ctx, double* ms, int64_t* launches, int n);
 
 /* ---------------------------------------------------------------- batching form
  * Many independent KL-NMF problems of uneven sizes (count of them; problem q is
- * N[q] x T[q] of rank R[q] <= 64), FP32 form.  Each phase of a DNA half-step runs for all
- * problems in one persistent grouped launch (a tile list over (problem, block, split)),
- * and dna_group_iterate can replay one whole iteration as a captured CUDA graph.  Every
- * problem follows exactly the single-problem algorithm above (Algorithm 1); only the
- * order of the split sums may differ.  The group owns a private stream that is ordered
- * after and before the caller's stream on every call. */
+ * N[q] x T[q] of rank R[q] <= 64), FP32 or BF16 form.  Each phase of a DNA half-step runs
+ * for all problems in one grouped launch (a tile list over (problem, block, split)), and
+ * dna_group_iterate can replay one whole iteration as a captured CUDA graph.  FP32: every
+ * phase on the CUDA cores.  BF16: the two O(NRT) passes on the tensor cores (the
+ * single-problem BF16 kernels at padded rank 64, each problem's operands and tensor maps
+ * in a device table), bf16 operands written by grouped conversion kernels, the rest as in
+ * FP32.  Every problem follows exactly the single-problem algorithm above (Algorithm 1);
+ * only the order of the split sums may differ.  The group owns a private stream that is
+ * ordered after and before the caller's stream on every call. */
 typedef struct dna_group dna_group;
 
 /* Create a group of `count` problems with sizes N[q], T[q], R[q] (host arrays); opts may
- * be NULL.  Only DNA_F32 is supported (R[q] > 64 or another dtype: DNA_ERR_UNSUPPORTED).
- * Allocates the whole workspace at once. */
+ * be NULL.  DNA_F32 (CUDA-core engine) and DNA_BF16 (tensor-core passes) are supported;
+ * R[q] > 64, DNA_F64, F32 on the tensor engine or BF16 on the SIMT engine give
+ * DNA_ERR_UNSUPPORTED.  Allocates the whole workspace at once (BF16 adds an aligned copy
+ * of each V and the bf16 operands). */
 int dna_group_create(int count, const int64_t* N, const int64_t* T, const int64_t* R,
                      const dna_opts* opts, dna_group** out);
 
@@ -306,10 +311,16 @@ int dna_group_step_W(dna_group* g);
 int dna_group_iterate(dna_group* g, int iters);
 int dna_group_use_graph(dna_group* g, int enable);
 
-/* Autotuner: time `reps` iterations for each candidate split size (rows of s per tile of
- * the reduction) and keep the fastest; W and H are restored afterwards.  The chosen
- * size is written to *rows_out (may be NULL).  Synchronises. */
+/* Autotuner: time `reps` iterations for each candidate tile configuration and keep the
+ * fastest; W and H are restored afterwards.  Candidates: the split size (rows of s per
+ * tile of the reductions) and, in the BF16 form, the pass-2 tile size ((o-block, chunk)
+ * units per CTA, 2 to 32).  The chosen split size is written to *rows_out (may be NULL).
+ * Synchronises. */
 int dna_group_autotune(dna_group* g, int reps, int64_t* rows_out);
+
+/* The tile configuration in use: rows of s per split and (BF16 form; 0 in FP32) pass-2
+ * units per CTA.  Either pointer may be NULL. */
+int dna_group_tile_config(dna_group* g, int64_t* split_rows, int64_t* p2_units);
 
 /* d_KL (eq. 1) of every problem into out[0 .. count) (host).  Synchronises. */
 int dna_group_kl(dna_group* g, double* out);

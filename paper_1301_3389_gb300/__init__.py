@@ -11,7 +11,7 @@ from ._lib import (  # noqa: F401
     dna_opts, dna_phase_times, dna_profile, dna_profile_phases, dna_run_host, PHASES, dna_set_stream, dna_step_H, dna_step_W, dna_strerror, make_opts,
     mu_step, mu_iterate, dna_group_create, dna_group_bind, dna_group_set_stream,
     dna_group_normalize, dna_group_step_H, dna_group_step_W, dna_group_iterate,
-    dna_group_use_graph, dna_group_autotune, dna_group_kl, dna_group_get_status, dna_group_get_choice,
+    dna_group_use_graph, dna_group_autotune, dna_group_tile_config, dna_group_kl, dna_group_get_status, dna_group_get_choice,
     dna_group_launches_per_iteration, dna_group_destroy, dna_shard_rowsums,
     dna_shard_set_rowsums, dna_shard_H_begin, dna_shard_H_end, dna_shard_W_begin,
     dna_shard_W_pass1, dna_shard_W_pass2, dna_shard_W_end, DNA_SELECT_PAPER, DNA_SELECT_DESCENT,

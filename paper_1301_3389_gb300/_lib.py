@@ -91,6 +91,7 @@ def _load() -> ctypes.CDLL:
         "dna_group_iterate": (I, [P, I]),
         "dna_group_use_graph": (I, [P, I]),
         "dna_group_autotune": (I, [P, I, P]),
+        "dna_group_tile_config": (I, [P, P, P]),
         "dna_group_kl": (I, [P, P]),
         "dna_group_get_status": (I, [P]),
         "dna_group_get_choice": (I, [P, I, I, P, I64]),
@@ -364,6 +365,14 @@ def dna_group_autotune(g: int, reps: int = 2) -> int:
     rows = ctypes.c_int64()
     _check(LIB.dna_group_autotune(g, reps, ctypes.byref(rows)), "dna_group_autotune")
     return rows.value
+
+
+def dna_group_tile_config(g: int):
+    """(rows of s per split, pass-2 units per CTA (0 in the FP32 form))."""
+    rows, units = ctypes.c_int64(), ctypes.c_int64()
+    _check(LIB.dna_group_tile_config(g, ctypes.byref(rows), ctypes.byref(units)),
+           "dna_group_tile_config")
+    return rows.value, units.value
 
 
 def dna_group_kl(g: int, count: int):

@@ -211,6 +211,31 @@ struct TcMaps {
     CUtensorMap q_l, qb_l, y128_l, yt256_l, y2t256_l;  // lo planes, FP32 form at RP > 128
 };
 
+// One view (0: H step, 1: W step) of one problem of the grouped BF16 form on the tensor
+// cores: the device table the grouped kernels read (tensor maps in global memory).
+struct alignas(64) TcGView {
+    CUtensorMap y, yt, y2t, v, xm, xd;
+    int64_t S, O, R, S_pad, O_pad;
+    const float* X;                 // the view's factors (float32 masters): x(r, o) at
+    int64_t xr, xo;                 // X[r xr + o xo], y(s, r) at Y[s ys + r yr]
+    const float* Y;
+    int64_t ys, yr;
+    void* Xk;                       // bf16 operands: Xk, Xmk, Xdk [O_pad][64],
+    void* Yk;                       // Yk [S_pad][64], Ytk, Y2tk [64][S_pad]
+    void* Ytk;
+    void* Y2tk;
+    void* Xmk;
+    void* Xdk;
+    const float* Xmu;               // candidates [R][O] (float32)
+    const float* Xdna;
+    float* A;                       // pass-1 partials [splits][R][O]
+    float* B;
+    double* dpart;                  // pass-2 cost slots [slots][2][O]
+    int64_t s_per1;                 // rows of s per pass-1 split (a multiple of 64)
+    int64_t nch2, U2;               // pass 2: chunks of 128 per o-block, (o-block, chunk) units
+    int slots2;                     // pass-2 cost slots per column
+};
+
 struct TcBf16 {
     // padded rank for the tensor-core kernels (64, 128, 256 or 512), 0 if unsupported
     static int rank_pad(int64_t R);
@@ -261,6 +286,19 @@ struct TcBf16 {
                         int* status, cudaStream_t st);
     static int chunk();
     static int oblock();
+    // The grouped BF16 form (R <= 64, padded rank 64), tables in device memory.
+    // Operands of view w: tiles (problem, what, bx, by) of k_g_operands.
+    static int group_operands(const TcGView* gv, const void* tiles, int n, int w, int grid,
+                              cudaStream_t st);
+    // pass 1: one CTA per tile (problem, o-block, split)
+    static int group_pass1(const TcGView* gv, const void* tiles, int n, int w, bool with_b,
+                           int* status, cudaStream_t st);
+    // pass 2: one CTA per entry (problem, rank, CTAs of that problem)
+    static int group_pass2(const TcGView* gv, const void* ctas, int n, int w, int* status,
+                           cudaStream_t st);
+    // once per group, before any launch (and outside graph capture): kernel attributes
+    static int group_prepare();
+    static int group_prepare_pass2();
     // one CTA whose bounded wait on a barrier that nothing completes gives up after
     // `limit` SM cycles and sets STATUS_TIMEOUT in *status
     static int check_wait_timeout(long long limit, int* status, cudaStream_t st);

@@ -1,6 +1,9 @@
 // Grouped (batched) DNA: many independent KL-NMF problems of uneven sizes, each phase of a
-// half-step run for all problems in one persistent launch, optionally replayed as a CUDA
-// graph.  FP32 form on the CUDA cores, R <= 64.
+// half-step run for all problems in one launch, optionally replayed as a CUDA graph, R <= 64.
+// FP32 form: every phase on the CUDA cores.  BF16 form: the two O(NRT) passes on the tensor
+// cores (the tcgen05 pass kernels of the single-problem BF16 form at padded rank 64, run
+// over a tile table with each problem's operands and TMA descriptors in a device table),
+// the rest on the CUDA cores as in the FP32 form.
 //
 // The problems live in one device arena; a device table holds each problem's (s, o, r)
 // views and workspace pointers; each phase has a tile list (problem, block, split) that a
@@ -34,6 +37,7 @@ struct GProb {
     uint8_t* choice[2];        // O per view
     int64_t per1[2], per2[2];  // rows of s per split
     int sp1[2], sp2[2];
+    int nslot[2];              // cost slots per column that the selection adds
     int rclass;                // rank class: 0: R <= 16, 1: R <= 32, 2: R <= 64
 };
 
@@ -97,7 +101,7 @@ __global__ void __launch_bounds__(256)
         const GTile tt = tl[t];
         const GProb& p = P[tt.prob];
         const View v = p.v[w];
-        simt::select_tile<float>(v, p.Xmu, p.Xdna, p.dpart, p.sp2[w], p.choice[w], p.dfin[w],
+        simt::select_tile<float>(v, p.Xmu, p.Xdna, p.dpart, p.nslot[w], p.choice[w], p.dfin[w],
                                  tt.a, reg);
     }
 }
@@ -198,6 +202,14 @@ struct dna_group {
     int slots1[dna::grp::NCLASS] = {1, 1, 1}, slots2[dna::grp::NCLASS] = {1, 1, 1};
     int64_t split_rows = 1024;  // rows of s per split (autotuned)
     bool bound = false, use_graph = false;
+    // BF16 form: the tensor-core passes
+    bool tc = false;
+    int64_t p2_units = 8;       // pass-2 (o-block, chunk) units per CTA (autotuned)
+    dna::TcGView* gv = nullptr; // device table [count][2]
+    std::vector<dna::TcGView> hgv;
+    struct TcBufs { float* Vp; int64_t ldp; void *Xk, *Yk, *Ytk, *Y2tk, *Xmk, *Xdk; };
+    std::vector<TcBufs> tcb;
+    TileList ops_in[2], ops_cand[2], tp1[2], tp2[2];
     cudaGraphExec_t gexec = nullptr;
     int64_t graph_launches = 0;
     std::vector<void*> tile_allocs;
@@ -292,7 +304,44 @@ int build_tiles(dna_group* g) {
         for (int64_t b = 0; b < (v.O + ob - 1) / ob; ++b)
             for (int s = 0; s < p.sp2[0]; ++s) tk[p.rclass].push_back({q, (int)b, s, 0});
     }
+    std::vector<GTile> ti[2], tcn[2], tq1[2], tq2[2];
+    for (int q = 0; q < g->count; ++q)
+        for (int w = 0; w < 2; ++w) {
+            GProb& p = g->hp[q];
+            p.nslot[w] = p.sp2[w];
+            if (!g->tc) continue;
+            dna::TcGView& t = g->hgv[2 * q + w];
+            const int64_t S = t.S, nob = t.O_pad / 128, nch = (S + 127) / 128, U = nob * nch;
+            t.s_per1 = p.per1[w];   // a multiple of 64, at least MIN_SPLIT_ROWS
+            for (int64_t b = 0; b < nob; ++b)
+                for (int sp = 0; sp < p.sp1[w]; ++sp) tq1[w].push_back({q, (int)b, sp, 0});
+            const int64_t G = std::max<int64_t>(1, std::min<int64_t>(U, (U + g->p2_units - 1) / g->p2_units));
+            t.nch2 = nch;
+            t.U2 = U;
+            t.slots2 = dna::TcBf16::pass2_split_slots(t.O_pad, S, (int)G);
+            p.nslot[w] = t.slots2;
+            for (int64_t me = 0; me < G; ++me) tq2[w].push_back({q, (int)me, (int)G, 0});
+            for (int64_t by = 0; by < t.O_pad / 32; ++by)
+                for (int bx = 0; bx < 2; ++bx) {
+                    ti[w].push_back({q, 0, bx, (int)by});
+                    tcn[w].push_back({q, 2, bx, (int)by});
+                    tcn[w].push_back({q, 3, bx, (int)by});
+                }
+            for (int64_t bx = 0; bx < t.S_pad / 32; ++bx)
+                for (int by = 0; by < 2; ++by) ti[w].push_back({q, 1, (int)bx, by});
+        }
     int e = DNA_OK;
+    if (g->tc) {
+        for (int w = 0; w < 2; ++w) {
+            e |= upload(g, ti[w], &g->ops_in[w]);
+            e |= upload(g, tcn[w], &g->ops_cand[w]);
+            e |= upload(g, tq1[w], &g->tp1[w]);
+            e |= upload(g, tq2[w], &g->tp2[w]);
+        }
+        if (!e && cudaMemcpy(g->gv, g->hgv.data(), sizeof(dna::TcGView) * g->hgv.size(),
+                             cudaMemcpyHostToDevice) != cudaSuccess)
+            e = DNA_ERR_CUDA;
+    }
     for (int w = 0; w < 2; ++w) {
         for (int k = 0; k < NC; ++k) {
             e |= upload(g, t1[w][k], &g->p1[w][k]);
@@ -364,16 +413,26 @@ int g_normalize(dna_group* g, int which) {
 
 int g_half(dna_group* g, int w, bool mu_only) {
     const double reg_den = w ? g->o.rho : g->o.lambda;
-    int e = launch_small(g, 0, g->sums_y[w], w, reg_den);
-    if (!e) e = launch_p1<16>(g, g->p1[w][0], w, !mu_only);
-    if (!e) e = launch_p1<32>(g, g->p1[w][1], w, !mu_only);
-    if (!e) e = launch_p1<64>(g, g->p1[w][2], w, !mu_only);
-    if (e) return e;
     if (mu_only) return DNA_ERR_UNSUPPORTED;
-    e = launch_small(g, 3, g->cand[w], w);
-    if (!e) e = launch_p2<16, false>(g, g->p2[w][0], w);
-    if (!e) e = launch_p2<32, false>(g, g->p2[w][1], w);
-    if (!e) e = launch_p2<64, false>(g, g->p2[w][2], w);
+    int e = launch_small(g, 0, g->sums_y[w], w, reg_den);
+    if (g->tc) {   // bf16 operands, pass 1 on the tensor cores, candidates, their bf16 copies
+        if (!e) e = dna::TcBf16::group_operands(g->gv, g->ops_in[w].d, g->ops_in[w].n, w,
+                                                8 * g->num_sms, g->gs);
+        if (!e) e = dna::TcBf16::group_pass1(g->gv, g->tp1[w].d, g->tp1[w].n, w, true, g->status,
+                                             g->gs);
+        if (!e) e = launch_small(g, 3, g->cand[w], w);
+        if (!e) e = dna::TcBf16::group_operands(g->gv, g->ops_cand[w].d, g->ops_cand[w].n, w,
+                                                8 * g->num_sms, g->gs);
+        if (!e) e = dna::TcBf16::group_pass2(g->gv, g->tp2[w].d, g->tp2[w].n, w, g->status, g->gs);
+    } else {
+        if (!e) e = launch_p1<16>(g, g->p1[w][0], w, true);
+        if (!e) e = launch_p1<32>(g, g->p1[w][1], w, true);
+        if (!e) e = launch_p1<64>(g, g->p1[w][2], w, true);
+        if (!e) e = launch_small(g, 3, g->cand[w], w);
+        if (!e) e = launch_p2<16, false>(g, g->p2[w][0], w);
+        if (!e) e = launch_p2<32, false>(g, g->p2[w][1], w);
+        if (!e) e = launch_p2<64, false>(g, g->p2[w][2], w);
+    }
     if (!e) e = launch_small(g, 4, g->cand[w], w, w ? g->o.rho : g->o.lambda);
     if (!e) e = g_normalize(g, w == 1 ? 1 : 0);
     return e;
@@ -421,7 +480,10 @@ int dna_group_create(int count, const int64_t* N, const int64_t* T, const int64_
     dna_opts o;
     dna_default_opts(&o);
     if (opts) o = *opts;
-    if (o.dtype != DNA_F32 || o.engine == DNA_ENGINE_TENSOR) return DNA_ERR_UNSUPPORTED;
+    // FP32 on the CUDA cores; BF16 with its passes on the tensor cores
+    const bool tc = o.dtype == DNA_BF16;
+    if (tc ? o.engine == DNA_ENGINE_SIMT : (o.dtype != DNA_F32 || o.engine == DNA_ENGINE_TENSOR))
+        return DNA_ERR_UNSUPPORTED;
     if (!(o.eps > 0.0 && o.eps <= 1.0) || !(o.alpha >= 0.0) || !(o.rho >= 0.0) ||
         !(o.lambda >= 0.0))
         return DNA_ERR_ARG;
@@ -432,6 +494,7 @@ int dna_group_create(int count, const int64_t* N, const int64_t* T, const int64_
     if (!g) return DNA_ERR_ALLOC;
     g->count = count;
     g->o = o;
+    g->tc = tc;
     g->N.assign(N, N + count);
     g->T.assign(T, T + count);
     g->R.assign(R, R + count);
@@ -446,11 +509,29 @@ int dna_group_create(int count, const int64_t* N, const int64_t* T, const int64_
     if (!e) e = prep_class<16>(g, 0);
     if (!e) e = prep_class<32>(g, 1);
     if (!e) e = prep_class<64>(g, 2);
+    if (!e && tc) e = dna::TcBf16::group_prepare();
     // arena: per problem Vt, V sums, factor sums, A/B partials (worst split count), candidates,
-    // cost partials, final costs, choices
+    // cost partials, final costs, choices; in the BF16 form also an aligned copy of V and
+    // the bf16 operands
     // the largest split counts any plan can use (splits of at least MIN_SPLIT_ROWS rows)
     auto nsplit = [](int64_t S) {
         return (S + dna::grp::MIN_SPLIT_ROWS - 1) / dna::grp::MIN_SPLIT_ROWS;
+    };
+    // cost slots of the tensor-core pass 2: 4 per CTA spanning an o-block, at most
+    // (chunks of 128 per o-block) + 1 CTAs with at least one unit each
+    auto tc_slots = [](int64_t S) { return 4 * ((S + 127) / 128 + 2); };
+    auto r128 = [](int64_t x) { return (x + 127) / 128 * 128; };
+    auto r64 = [](int64_t x) { return (x + 63) / 64 * 64; };
+    auto dp_of = [&](int64_t n, int64_t t) {
+        int64_t d = std::max(nsplit(n) * 2 * t, nsplit(t) * 2 * n);
+        if (tc) d = std::max(d, std::max(tc_slots(n) * 2 * t, tc_slots(t) * 2 * n));
+        return d;
+    };
+    auto tc_bytes = [&](int64_t n, int64_t t) -> size_t {
+        if (!tc) return 0;
+        const int64_t opad = std::max(r128(t), r128(n)), spad = std::max(r64(n), r64(t));
+        const int64_t ldp = (t + 3) / 4 * 4;
+        return al(4 * n * ldp) + 3 * al(2 * 64 * opad) + 3 * al(2 * 64 * spad);
     };
     std::vector<size_t> off(count);
     size_t total = 0;
@@ -458,15 +539,18 @@ int dna_group_create(int count, const int64_t* N, const int64_t* T, const int64_
         const int64_t n = N[q], t = T[q], r = R[q], m = std::max(n, t);
         const int64_t ldvt = (n + 3) / 4 * 4;
         const int64_t ab = std::max(nsplit(n) * r * t, nsplit(t) * r * n);   // A/B partials
-        const int64_t dp = std::max(nsplit(n) * 2 * t, nsplit(t) * 2 * n);   // cost partials
+        const int64_t dp = dp_of(n, t);                                       // cost partials
         off[q] = total;
         total += al(4 * t * ldvt) + al(8 * (n + t)) + al(16 * r) + 2 * al(4 * ab) +
-                 2 * al(4 * r * m) + al(8 * dp) + al(8 * 2 * (n + t)) + al(n + t);
+                 2 * al(4 * r * m) + al(8 * dp) + al(8 * 2 * (n + t)) + al(n + t) +
+                 tc_bytes(n, t);
     }
     if (!e && cudaMalloc(&g->arena, total + 256) != cudaSuccess) e = DNA_ERR_ALLOC;
     if (!e && (cudaMalloc(&g->dp, sizeof(GProb) * count) != cudaSuccess ||
                cudaMalloc(&g->kl_dev, sizeof(double) * count) != cudaSuccess ||
                cudaMalloc(&g->status, sizeof(int)) != cudaSuccess))
+        e = DNA_ERR_ALLOC;
+    if (!e && tc && cudaMalloc(&g->gv, sizeof(dna::TcGView) * 2 * (size_t)count) != cudaSuccess)
         e = DNA_ERR_ALLOC;
     if (!e && cudaMemset(g->status, 0, sizeof(int)) != cudaSuccess) e = DNA_ERR_CUDA;
     if (e) {
@@ -486,7 +570,7 @@ int dna_group_create(int count, const int64_t* N, const int64_t* T, const int64_
         double* rowsum = colsum + t; b += al(8 * (n + t));
         p.c = reinterpret_cast<double*>(b); p.sig = p.c + r; b += al(16 * r);
         const int64_t ab = std::max(nsplit(n) * r * t, nsplit(t) * r * n);
-        const int64_t dp = std::max(nsplit(n) * 2 * t, nsplit(t) * 2 * n);
+        const int64_t dp = dp_of(n, t);
         p.A = reinterpret_cast<float*>(b); b += al(4 * ab);
         p.B = reinterpret_cast<float*>(b); b += al(4 * ab);
         p.Xmu = reinterpret_cast<float*>(b); b += al(4 * r * m);
@@ -495,6 +579,20 @@ int dna_group_create(int count, const int64_t* N, const int64_t* T, const int64_
         p.dfin[0] = reinterpret_cast<double*>(b); p.dfin[1] = p.dfin[0] + 2 * t;
         b += al(8 * 2 * (n + t));
         p.choice[0] = b; p.choice[1] = b + t;
+        b += al(n + t);
+        if (tc) {
+            dna_group::TcBufs tb{};
+            const int64_t opad = std::max(r128(t), r128(n)), spad = std::max(r64(n), r64(t));
+            tb.ldp = (t + 3) / 4 * 4;
+            tb.Vp = reinterpret_cast<float*>(b); b += al(4 * n * tb.ldp);
+            tb.Xk = b; b += al(2 * 64 * opad);
+            tb.Xmk = b; b += al(2 * 64 * opad);
+            tb.Xdk = b; b += al(2 * 64 * opad);
+            tb.Yk = b; b += al(2 * 64 * spad);
+            tb.Ytk = b; b += al(2 * 64 * spad);
+            tb.Y2tk = b; b += al(2 * 64 * spad);
+            g->tcb.push_back(tb);
+        }
         p.rclass = r <= 16 ? 0 : r <= 32 ? 1 : 2;
         // views without the caller's buffers yet
         View& vh = p.v[0];
@@ -502,6 +600,7 @@ int dna_group_create(int count, const int64_t* N, const int64_t* T, const int64_
         View& vw = p.v[1];
         vw.S = t; vw.O = n; vw.R = r; vw.V = Vt; vw.vs = ldvt; vw.vsum = rowsum;
     }
+    if (tc) g->hgv.resize(2 * (size_t)count);
     *out = g;
     return DNA_OK;
 }
@@ -534,6 +633,37 @@ int dna_group_bind(dna_group* g, const void* const* V, const int64_t* ldv, void*
                                            const_cast<double*>(vh.vsum),
                                            const_cast<double*>(vw.vsum), g->gs))
             return e;
+        if (g->tc) {
+            // V with 16-byte aligned rows for the tensor maps of the H view (the W view reads
+            // the transposed copy, whose rows are aligned), and the problem's view table
+            const dna_group::TcBufs& tb = g->tcb[q];
+            if (cudaMemcpy2DAsync(tb.Vp, sizeof(float) * tb.ldp, V[q], sizeof(float) * ld,
+                                  sizeof(float) * t, n, cudaMemcpyDeviceToDevice, g->gs) !=
+                cudaSuccess)
+                return DNA_ERR_CUDA;
+            for (int w = 0; w < 2; ++w) {
+                const View& v = p.v[w];
+                dna::TcGView& tv = g->hgv[2 * q + w];
+                tv = dna::TcGView{};
+                tv.S = v.S; tv.O = v.O; tv.R = v.R;
+                tv.S_pad = (v.S + 63) / 64 * 64; tv.O_pad = (v.O + 127) / 128 * 128;
+                tv.X = static_cast<const float*>(v.X); tv.xr = v.xr; tv.xo = v.xo;
+                tv.Y = static_cast<const float*>(v.Y); tv.ys = v.ys; tv.yr = v.yr;
+                tv.Xk = tb.Xk; tv.Yk = tb.Yk; tv.Ytk = tb.Ytk; tv.Y2tk = tb.Y2tk;
+                tv.Xmk = tb.Xmk; tv.Xdk = tb.Xdk;
+                tv.Xmu = p.Xmu; tv.Xdna = p.Xdna; tv.A = p.A; tv.B = p.B; tv.dpart = p.dpart;
+                dna::TcOperands op{};
+                op.S = v.S; op.O = v.O; op.R = v.R; op.S_pad = tv.S_pad; op.O_pad = tv.O_pad;
+                op.Xk = tb.Xk; op.Yk = tb.Yk; op.Ytk = tb.Ytk; op.Y2tk = tb.Y2tk;
+                op.Xmk = tb.Xmk; op.Xdk = tb.Xdk;
+                op.ctas = g->num_sms;
+                op.V = w ? static_cast<const float*>(v.V) : tb.Vp;
+                op.vs = w ? v.vs : tb.ldp;
+                dna::TcMaps m{};
+                if (int e = dna::TcBf16::make_maps(&m, op, op.V, op.vs, tb.Xmk, tb.Xdk)) return e;
+                tv.y = m.y; tv.yt = m.yt; tv.y2t = m.y2t; tv.v = m.v; tv.xm = m.xm; tv.xd = m.xd;
+            }
+        }
     }
     g->bound = true;
     return build_tiles(g);
@@ -624,19 +754,28 @@ int dna_group_autotune(dna_group* g, int reps, int64_t* rows_out) {
     }
     if (cudaStreamSynchronize(g->gs) != cudaSuccess) return DNA_ERR_CUDA;
     double best = 1e300;
-    int64_t best_rows = g->split_rows;
+    int64_t best_rows = g->split_rows, best_units = g->p2_units;
     int e = DNA_OK;
+    // the BF16 form also tunes the pass-2 tile size: (o-block, chunk) units per CTA
+    const int64_t units_tc[] = {2, 4, 8, 16, 32};
+    const int64_t units_simt[] = {8};
+    const int64_t* units = g->tc ? units_tc : units_simt;
+    const int nunits = g->tc ? 5 : 1;
     for (int64_t rows : cands) {
-        g->split_rows = rows;
-        if ((e = build_tiles(g))) break;
-        if ((e = g_iteration(g))) break;   // warm-up
-        cudaEventRecord(a, g->gs);
-        for (int i = 0; i < reps && !e; ++i) e = g_iteration(g);
-        cudaEventRecord(b, g->gs);
-        if (e || cudaEventSynchronize(b) != cudaSuccess) { e = e ? e : DNA_ERR_CUDA; break; }
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, a, b);
-        if (ms < best) { best = ms; best_rows = rows; }
+        for (int ui = 0; ui < nunits && !e; ++ui) {
+            g->split_rows = rows;
+            g->p2_units = units[ui];
+            if ((e = build_tiles(g))) break;
+            if ((e = g_iteration(g))) break;   // warm-up
+            cudaEventRecord(a, g->gs);
+            for (int i = 0; i < reps && !e; ++i) e = g_iteration(g);
+            cudaEventRecord(b, g->gs);
+            if (e || cudaEventSynchronize(b) != cudaSuccess) { e = e ? e : DNA_ERR_CUDA; break; }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, a, b);
+            if (ms < best) { best = ms; best_rows = rows; best_units = units[ui]; }
+        }
+        if (e) break;
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
@@ -649,8 +788,16 @@ int dna_group_autotune(dna_group* g, int reps, int64_t* rows_out) {
     if (cudaStreamSynchronize(g->gs) != cudaSuccess) return DNA_ERR_CUDA;
     if (e) return e;
     g->split_rows = best_rows;
+    g->p2_units = best_units;
     if (rows_out) *rows_out = best_rows;
     return build_tiles(g);
+}
+
+int dna_group_tile_config(dna_group* g, int64_t* split_rows, int64_t* p2_units) {
+    if (!g) return DNA_ERR_ARG;
+    if (split_rows) *split_rows = g->split_rows;
+    if (p2_units) *p2_units = g->tc ? g->p2_units : 0;
+    return DNA_OK;
 }
 
 int dna_group_kl(dna_group* g, double* out) {
@@ -700,7 +847,12 @@ int64_t dna_group_launches_per_iteration(dna_group* g) {
     int64_t n = 0;
     for (int w = 0; w < 2; ++w) {
         n += 5;  // sums, candidates, select, normaliser sums, rescale
-        for (int k = 0; k < dna::grp::NCLASS; ++k) n += (g->p1[w][k].n > 0) + (g->p2[w][k].n > 0);
+        if (g->tc)   // operands, pass 1, candidate operands, pass 2
+            n += (g->ops_in[w].n > 0) + (g->tp1[w].n > 0) + (g->ops_cand[w].n > 0) +
+                 (g->tp2[w].n > 0);
+        else
+            for (int k = 0; k < dna::grp::NCLASS; ++k)
+                n += (g->p1[w][k].n > 0) + (g->p2[w][k].n > 0);
     }
     return n;
 }
@@ -713,6 +865,7 @@ void dna_group_destroy(dna_group* g) {
     free_lists(g);
     if (g->arena) cudaFree(g->arena);
     if (g->dp) cudaFree(g->dp);
+    if (g->gv) cudaFree(g->gv);
     if (g->kl_dev) cudaFree(g->kl_dev);
     if (g->status) cudaFree(g->status);
     if (g->ev_in) cudaEventDestroy(g->ev_in);

@@ -19,6 +19,8 @@
 // GEMM1 of the next chunk overlaps the epilogue of this one.  Every hand-off is an
 // mbarrier; every wait is bounded and aborts the CTA (with DNA_ERR_TIMEOUT reported)
 // instead of hanging.
+#include <algorithm>
+
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -60,11 +62,12 @@ struct P1Layout {
 enum { B_XFULL = 0, B_VFULL = 1, B_VEMPTY = 5, B_YFULL = 9, B_TFULL = 11, B_ZFULL = 13,
        B_ZEMPTY = 15, B_QFULL = 17, B_QEMPTY = 18, B_DRAIN = 20, B_COUNT = 22 };
 
+// The tile (o-block bx, split by of s) of pass 1; the tensor maps may live in kernel
+// parameters or in global memory (the grouped form keeps one set per problem there).
 template <int RP, bool WITH_B>
-__global__ void __launch_bounds__(P1_THREADS, 1)
-    k_tc_pass1(P1Args a, const __grid_constant__ CUtensorMap tmY,
-               const __grid_constant__ CUtensorMap tmYt, const __grid_constant__ CUtensorMap tmY2t,
-               const __grid_constant__ CUtensorMap tmV) {
+__device__ __forceinline__ void pass1_body(const P1Args& a, int64_t bx, int64_t by,
+                                           const CUtensorMap* tmY, const CUtensorMap* tmYt,
+                                           const CUtensorMap* tmY2t, const CUtensorMap* tmV) {
     using L = P1Layout<RP>;
     constexpr int VST = L::VST, YST = L::YST, TST = L::TST;
     static_assert(YST == 2 && TST == 2, "stage reuse is signalled by the 2-deep commit barriers");
@@ -77,8 +80,8 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
     volatile int* abort = reinterpret_cast<volatile int*>(sm + L::BAR + B_COUNT * 8 + 8);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int64_t o0 = (int64_t)blockIdx.x * OBLK;
-    const int64_t s_begin = (int64_t)blockIdx.y * a.s_per;
+    const int64_t o0 = bx * OBLK;
+    const int64_t s_begin = by * a.s_per;
     const int64_t s_end = min(a.S, s_begin + a.s_per);
     const int nch = s_end > s_begin ? (int)((s_end - s_begin + SCH - 1) / SCH) : 0;
 
@@ -109,8 +112,8 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
     if (warp == W_PRODUCER) {
         // One thread services the three rings in whatever order their slots free up.
         if (lane == 0 && nch > 0) {
-            tma_prefetch_desc(&tmY); tma_prefetch_desc(&tmYt); tma_prefetch_desc(&tmY2t);
-            tma_prefetch_desc(&tmV);
+            tma_prefetch_desc(tmY); tma_prefetch_desc(tmYt); tma_prefetch_desc(tmY2t);
+            tma_prefetch_desc(tmV);
             int kv = 0, ky = 0, kt = 0;
             long long t0 = clock64();
             while (kv < nch || ky < nch || kt < nch) {
@@ -118,7 +121,7 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
                 if (kv < nch && mbar_test(&bar[B_VEMPTY + kv % VST], ((kv / VST) & 1) ^ 1)) {
                     const int st = kv % VST;
                     mbar_arrive_expect_tx(&bar[B_VFULL + st], L::V_BYTES);
-                    tma_load_2d(sbase + L::VR + st * L::V_BYTES, &tmV, (int32_t)o0,
+                    tma_load_2d(sbase + L::VR + st * L::V_BYTES, tmV, (int32_t)o0,
                                 (int32_t)(s_begin + (int64_t)kv * SCH), &bar[B_VFULL + st]);
                     ++kv;
                     prog = true;
@@ -130,7 +133,7 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
                     const uint32_t dst = sbase + L::YR + st * L::Y_BYTES;
                     mbar_arrive_expect_tx(&bar[B_YFULL + st], L::Y_BYTES);
                     for (int at = 0; at < RP / 64; ++at)
-                        tma_load_2d(dst + at * SCH * 128, &tmY, 64 * at,
+                        tma_load_2d(dst + at * SCH * 128, tmY, 64 * at,
                                     (int32_t)(s_begin + (int64_t)ky * SCH), &bar[B_YFULL + st]);
                     ++ky;
                     prog = true;
@@ -142,8 +145,8 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
                     const uint32_t dst = sbase + L::TR + st * L::T_STAGE;
                     const int32_t s0 = (int32_t)(s_begin + (int64_t)kt * SCH);
                     mbar_arrive_expect_tx(&bar[B_TFULL + st], (WITH_B ? 2 : 1) * L::YT_BYTES);
-                    tma_load_2d(dst, &tmYt, s0, 0, &bar[B_TFULL + st]);
-                    if (WITH_B) tma_load_2d(dst + L::YT_BYTES, &tmY2t, s0, 0, &bar[B_TFULL + st]);
+                    tma_load_2d(dst, tmYt, s0, 0, &bar[B_TFULL + st]);
+                    if (WITH_B) tma_load_2d(dst + L::YT_BYTES, tmY2t, s0, 0, &bar[B_TFULL + st]);
                     ++kt;
                     prog = true;
                 }
@@ -293,7 +296,7 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
         }
         if (ok && nch > 0) {
             tc_fence_after();
-            const int64_t base = (int64_t)blockIdx.y * a.R;
+            const int64_t base = by * a.R;
             constexpr int G = RP / 32;   // 32-column groups of A (then of B)
 #pragma unroll 1
             for (int u = cg; u < (WITH_B ? 2 : 1) * G; u += 4) {
@@ -318,13 +321,37 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
     if (warp == 0) tmem_dealloc(tmem, L::NCOLS);
 }
 
+template <int RP, bool WITH_B>
+__global__ void __launch_bounds__(P1_THREADS, 1)
+    k_tc_pass1(P1Args a, const __grid_constant__ CUtensorMap tmY,
+               const __grid_constant__ CUtensorMap tmYt, const __grid_constant__ CUtensorMap tmY2t,
+               const __grid_constant__ CUtensorMap tmV) {
+    pass1_body<RP, WITH_B>(a, blockIdx.x, blockIdx.y, &tmY, &tmYt, &tmY2t, &tmV);
+}
+
+// Grouped pass 1: CTA i runs tile tiles[i] = (problem, o-block, split) of view w with that
+// problem's operands and tensor maps (gv[2 problem + w], global memory).
+template <int RP, bool WITH_B>
+__global__ void __launch_bounds__(P1_THREADS, 1)
+    k_tc_gpass1(const TcGView* __restrict__ gv, const int4* __restrict__ tiles, int w,
+                int* status) {
+    const int4 t = tiles[blockIdx.x];
+    const TcGView& v = gv[2 * t.x + w];
+    P1Args a{};
+    a.S = v.S; a.O = v.O; a.R = v.R; a.s_per = v.s_per1;
+    a.Apart = v.A; a.Bpart = v.B; a.status = status;
+    a.X = v.Xk; a.rp = RP;
+    pass1_body<RP, WITH_B>(a, t.y, t.z, &v.y, &v.yt, &v.y2t, &v.v);
+}
+
 // dst[i][j] (leading dimension ld, padded to rows_pad x cols_pad with zeros) =
 // bf16(src(i, j)) (squared first when `square`), where src(i, j) = src[i * si + j * sj]
 // for i < rows, j < cols, and one of si, sj is 1.  32 x 32 tiles through shared memory.
-__global__ void k_to_bf16(const float* __restrict__ src, int64_t si, int64_t sj, int64_t rows,
-                          int64_t cols, bf16* __restrict__ dst, int64_t ld, bool square) {
+__device__ __forceinline__ void to_bf16_tile(const float* __restrict__ src, int64_t si, int64_t sj,
+                                             int64_t rows, int64_t cols, bf16* __restrict__ dst,
+                                             int64_t ld, bool square, int64_t bx, int64_t by) {
     __shared__ float tile[32][33];
-    const int64_t i0 = (int64_t)blockIdx.y * 32, j0 = (int64_t)blockIdx.x * 32;
+    const int64_t i0 = by * 32, j0 = bx * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;
     if (sj == 1) {
         for (int k = ty; k < 32; k += 8) {
@@ -345,16 +372,21 @@ __global__ void k_to_bf16(const float* __restrict__ src, int64_t si, int64_t sj,
         dst[i * ld + j] = __float2bfloat16_rn(x);
     }
 }
+__global__ void k_to_bf16(const float* __restrict__ src, int64_t si, int64_t sj, int64_t rows,
+                          int64_t cols, bf16* __restrict__ dst, int64_t ld, bool square) {
+    to_bf16_tile(src, si, sj, rows, cols, dst, ld, square, blockIdx.x, blockIdx.y);
+}
 
 // The three operands derived from Y in one pass over a 32 x 32 tile of y(s, r):
 //   Yk[s][r] = bf16(y), Ytk[r][s] = bf16(y), Y2tk[r][s] = bf16(y * y), zero-padded.
 // y(s, r) at Y[s * ys + r * yr] with ys == 1 or yr == 1.  Grid covers S_pad x RP.
-__global__ void k_y_operands(const float* __restrict__ Y, int64_t ys, int64_t yr, int64_t S,
-                             int64_t R, bf16* __restrict__ Yk, int64_t rp,
-                             bf16* __restrict__ Ytk, bf16* __restrict__ Y2tk, int64_t s_pad,
-                             bool with_sq) {
+__device__ __forceinline__ void y_operands_tile(const float* __restrict__ Y, int64_t ys, int64_t yr,
+                                                int64_t S, int64_t R, bf16* __restrict__ Yk,
+                                                int64_t rp, bf16* __restrict__ Ytk,
+                                                bf16* __restrict__ Y2tk, int64_t s_pad,
+                                                bool with_sq, int64_t bx, int64_t by) {
     __shared__ float tile[32][33];   // tile[s][r]
-    const int64_t s0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
+    const int64_t s0 = bx * 32, r0 = by * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;
     if (yr == 1) {   // rows of Y contiguous along r
         for (int k = ty; k < 32; k += 8) {
@@ -375,6 +407,37 @@ __global__ void k_y_operands(const float* __restrict__ Y, int64_t ys, int64_t yr
         const float y = tile[tx][k];
         Ytk[r2 * s_pad + s2] = __float2bfloat16_rn(y);
         if (with_sq) Y2tk[r2 * s_pad + s2] = __float2bfloat16_rn(y * y);
+    }
+}
+__global__ void k_y_operands(const float* __restrict__ Y, int64_t ys, int64_t yr, int64_t S,
+                             int64_t R, bf16* __restrict__ Yk, int64_t rp,
+                             bf16* __restrict__ Ytk, bf16* __restrict__ Y2tk, int64_t s_pad,
+                             bool with_sq) {
+    y_operands_tile(Y, ys, yr, S, R, Yk, rp, Ytk, Y2tk, s_pad, with_sq, blockIdx.x, blockIdx.y);
+}
+
+// Grouped operands of view w, one 32 x 32 tile per CTA step (tiles[t] = (problem, what,
+// bx, by)): what = 0: X -> Xk [O_pad][64] (x(r, o) at X[r xr + o xo]); 1: Y -> Yk, Ytk,
+// Y2tk; 2: the candidates Xmu, Xdna ([R][O] float32) -> Xmk, Xdk.
+__global__ void __launch_bounds__(256)
+    k_g_operands(const TcGView* __restrict__ gv, const int4* __restrict__ tiles, int n, int w) {
+    for (int i = blockIdx.x; i < n; i += gridDim.x) {
+        const int4 t = tiles[i];
+        const TcGView& v = gv[2 * t.x + w];
+        bf16* const Xmk = static_cast<bf16*>(v.Xmk);
+        bf16* const Xdk = static_cast<bf16*>(v.Xdk);
+        if (t.y == 0)
+            to_bf16_tile(v.X, v.xo, v.xr, v.O, v.R, static_cast<bf16*>(v.Xk), 64, false, t.z,
+                         t.w);
+        else if (t.y == 1)
+            y_operands_tile(v.Y, v.ys, v.yr, v.S, v.R, static_cast<bf16*>(v.Yk), 64,
+                            static_cast<bf16*>(v.Ytk), static_cast<bf16*>(v.Y2tk), v.S_pad, true,
+                            t.z, t.w);
+        else if (t.y == 2)
+            to_bf16_tile(v.Xmu, 1, v.O, v.O, v.R, Xmk, 64, false, t.z, t.w);
+        else
+            to_bf16_tile(v.Xdna, 1, v.O, v.O, v.R, Xdk, 64, false, t.z, t.w);
+        __syncthreads();   // the tile buffer is reused by the next step
     }
 }
 
@@ -502,6 +565,33 @@ int TcBf16::y_operands(const float* Y, int64_t ys, int64_t yr, const TcOperands&
         static_cast<tc::bf16*>(const_cast<void*>(op.Ytk)),
         static_cast<tc::bf16*>(const_cast<void*>(op.Y2tk)), op.S_pad, with_sq);
     return after_launch();
+}
+
+int TcBf16::group_operands(const TcGView* gv, const void* tiles, int n, int w, int grid,
+                           cudaStream_t st) {
+    if (n <= 0) return DNA_OK;
+    tc::k_g_operands<<<std::max(1, std::min(n, grid)), dim3(32, 8), 0, st>>>(
+        gv, static_cast<const int4*>(tiles), n, w);
+    return after_launch();
+}
+
+int TcBf16::group_pass1(const TcGView* gv, const void* tiles, int n, int w, bool with_b,
+                        int* status, cudaStream_t st) {
+    if (n <= 0) return DNA_OK;
+    const uint32_t smem = tc::P1Layout<64>::TOTAL + 1024;
+    auto k = with_b ? tc::k_tc_gpass1<64, true> : tc::k_tc_gpass1<64, false>;
+    k<<<n, tc::P1_THREADS, smem, st>>>(gv, static_cast<const int4*>(tiles), w, status);
+    return after_launch();
+}
+
+int TcBf16::group_prepare() {
+    const int s1 = (int)(tc::P1Layout<64>::TOTAL + 1024);
+    if (cudaFuncSetAttribute(tc::k_tc_gpass1<64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             s1) != cudaSuccess ||
+        cudaFuncSetAttribute(tc::k_tc_gpass1<64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             s1) != cudaSuccess)
+        return DNA_ERR_CUDA;
+    return group_prepare_pass2();
 }
 
 int TcBf16::pass1(const TcOperands& op, const TcMaps& maps, float* Apart, float* Bpart,

@@ -547,13 +547,14 @@ struct P2SGCursor {
 // NP: operand planes, 2 for the split FP32 form (three products), 1 for the BF16 form.
 // FULL: d_KL per column instead (eq. 1 terms z + v log(v / z) - v with the accurate
 // logarithm), both candidates = the current factor, slot layout [slot][O] of candidate 0.
+// The work of CTA `me` of the G CTAs that share one problem's units; the tensor maps may
+// live in kernel parameters or in global memory (the grouped form).
 template <int RP, int NP, bool FULL>
-__global__ void __launch_bounds__(P1_THREADS, 1)
-    k_tc_pass2s(P2Args a, int64_t nch, int64_t U, int slots,
-                const __grid_constant__ CUtensorMap tmXm, const __grid_constant__ CUtensorMap tmXml,
-                const __grid_constant__ CUtensorMap tmXd, const __grid_constant__ CUtensorMap tmXdl,
-                const __grid_constant__ CUtensorMap tmY, const __grid_constant__ CUtensorMap tmYl,
-                const __grid_constant__ CUtensorMap tmV) {
+__device__ __forceinline__ void pass2s_body(const P2Args& a, int64_t nch, int64_t U, int slots,
+                                            int me, int G, const CUtensorMap* pXm,
+                                            const CUtensorMap* pXml, const CUtensorMap* pXd,
+                                            const CUtensorMap* pXdl, const CUtensorMap* pY,
+                                            const CUtensorMap* pYl, const CUtensorMap* pV) {
     using L = P2SLayout<RP, NP>;
     constexpr int GST = L::GST, VST = L::VST;
     static_assert(NP == 2 || !FULL, "the d_KL mode runs in the split form");
@@ -566,7 +567,6 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
     volatile int* abort = reinterpret_cast<volatile int*>(sm + L::BAR + T_COUNT * 8 + 8);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int G = (int)gridDim.x, me = (int)blockIdx.x;
     const int64_t u0 = (int64_t)me * U / G, u1 = (int64_t)(me + 1) * U / G;
 
     if (warp == 0) { tmem_alloc(tslot, L::NCOLS); tmem_relinquish(); }
@@ -592,9 +592,9 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
 
     if (warp == W_PRODUCER) {
         if (lane == 0 && u0 < u1) {
-            tma_prefetch_desc(&tmXm); tma_prefetch_desc(&tmXml); tma_prefetch_desc(&tmXd);
-            tma_prefetch_desc(&tmXdl); tma_prefetch_desc(&tmY); tma_prefetch_desc(&tmYl);
-            tma_prefetch_desc(&tmV);
+            tma_prefetch_desc(pXm); tma_prefetch_desc(pXml); tma_prefetch_desc(pXd);
+            tma_prefetch_desc(pXdl); tma_prefetch_desc(pY); tma_prefetch_desc(pYl);
+            tma_prefetch_desc(pV);
             P2SGCursor cg_{u0, u1, nch, 0};
             int64_t uv = u0;   // V: half h of unit uv
             int hv = 0, kg = 0, kv = 0;
@@ -605,7 +605,7 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
                     const int st = kv % VST;
                     const int64_t ob = uv / nch, ck = uv % nch;
                     mbar_arrive_expect_tx(&bar[T_VFULL + st], L::V_STAGE);
-                    tma_load_2d(sbase + L::VR + st * L::V_STAGE, &tmV, (int32_t)(ob * OBLK),
+                    tma_load_2d(sbase + L::VR + st * L::V_STAGE, pV, (int32_t)(ob * OBLK),
                                 (int32_t)(ck * SC2 + SCH * hv), &bar[T_VFULL + st]);
                     ++kv;
                     if (++hv == 2) { hv = 0; ++uv; }
@@ -616,8 +616,8 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
                     const uint32_t dst = sbase + L::GR + st * L::G_STAGE;
                     const int64_t ob = cg_.u / nch, ck = cg_.u % nch;
                     if (cg_.xu < 2) {   // X hi (and lo) of candidate xu, [NA][128 o][64 r] each
-                        const CUtensorMap* mh = cg_.xu ? &tmXd : &tmXm;
-                        const CUtensorMap* ml = cg_.xu ? &tmXdl : &tmXml;
+                        const CUtensorMap* mh = cg_.xu ? pXd : pXm;
+                        const CUtensorMap* ml = cg_.xu ? pXdl : pXml;
                         mbar_arrive_expect_tx(&bar[T_GFULL + st], NP * L::X_PLANE);
                         for (int at = 0; at < RP / 64; ++at) {
                             tma_load_2d(dst + at * OBLK * 128, mh, 64 * at, (int32_t)(ob * OBLK),
@@ -632,10 +632,10 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
                         for (int at = 0; at < RP / 64; ++at)
                             for (int hs = 0; hs < 2; ++hs) {
                                 const uint32_t off = at * SC2 * 128 + hs * SCH * 128;
-                                tma_load_2d(dst + off, &tmY, 64 * at, s0 + SCH * hs,
+                                tma_load_2d(dst + off, pY, 64 * at, s0 + SCH * hs,
                                             &bar[T_GFULL + st]);
                                 if (NP == 2)
-                                    tma_load_2d(dst + L::G_PLANE + off, &tmYl, 64 * at,
+                                    tma_load_2d(dst + L::G_PLANE + off, pYl, 64 * at,
                                                 s0 + SCH * hs, &bar[T_GFULL + st]);
                             }
                     }
@@ -834,6 +834,33 @@ int launch_pass1s(const P1Args& a, bool with_b, const TcMaps& m, int64_t O_pad, 
 }
 
 template <int RP, int NP, bool FULL>
+__global__ void __launch_bounds__(P1_THREADS, 1)
+    k_tc_pass2s(P2Args a, int64_t nch, int64_t U, int slots,
+                const __grid_constant__ CUtensorMap tmXm, const __grid_constant__ CUtensorMap tmXml,
+                const __grid_constant__ CUtensorMap tmXd, const __grid_constant__ CUtensorMap tmXdl,
+                const __grid_constant__ CUtensorMap tmY, const __grid_constant__ CUtensorMap tmYl,
+                const __grid_constant__ CUtensorMap tmV) {
+    pass2s_body<RP, NP, FULL>(a, nch, U, slots, (int)blockIdx.x, (int)gridDim.x, &tmXm, &tmXml,
+                              &tmXd, &tmXdl, &tmY, &tmYl, &tmV);
+}
+
+// Grouped pass 2 of the BF16 form: CTA i is rank ctas[i].y of the ctas[i].z CTAs that
+// share problem ctas[i].x's units (view w), with that problem's tensor maps (global memory).
+template <int RP>
+__global__ void __launch_bounds__(P1_THREADS, 1)
+    k_tc_gpass2(const TcGView* __restrict__ gv, const int4* __restrict__ ctas, int w,
+                int* status) {
+    const int4 c = ctas[blockIdx.x];
+    const TcGView& v = gv[2 * c.x + w];
+    P2Args a{};
+    a.S = v.S; a.O = v.O; a.R = v.R; a.s_per = 0;
+    a.dpart = v.dpart; a.status = status;
+    a.Xm = v.Xmk; a.Xd = v.Xdk; a.rp = RP;
+    pass2s_body<RP, 1, false>(a, v.nch2, v.U2, v.slots2, c.y, c.z, &v.xm, &v.xm, &v.xd, &v.xd,
+                              &v.y, &v.y, &v.v);
+}
+
+template <int RP, int NP, bool FULL>
 int launch_pass2s(const P2Args& a, const TcMaps& m, int64_t O_pad, int slots, int ctas,
                   cudaStream_t st) {
     const uint32_t smem = P2SLayout<RP, NP>::TOTAL + 1024;
@@ -902,6 +929,23 @@ int TcBf16::kl_split(const TcOperands& op, const TcMaps& maps, double* dpart, in
     if (a.rp == 64) return tc::launch_pass2s<64, 2, true>(a, maps, op.O_pad, slots, op.ctas, st);
     if (a.rp == 128) return tc::launch_pass2s<128, 2, true>(a, maps, op.O_pad, slots, op.ctas, st);
     return DNA_ERR_UNSUPPORTED;
+}
+
+int TcBf16::group_pass2(const TcGView* gv, const void* ctas, int n, int w, int* status,
+                        cudaStream_t st) {
+    if (n <= 0) return DNA_OK;
+    const uint32_t smem = tc::P2SLayout<64, 1>::TOTAL + 1024;
+    tc::k_tc_gpass2<64><<<n, tc::P1_THREADS, smem, st>>>(gv, static_cast<const int4*>(ctas), w,
+                                                         status);
+    return after_launch();
+}
+
+int TcBf16::group_prepare_pass2() {
+    const int smem = (int)(tc::P2SLayout<64, 1>::TOTAL + 1024);
+    return cudaFuncSetAttribute(tc::k_tc_gpass2<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                smem) == cudaSuccess
+               ? DNA_OK
+               : DNA_ERR_CUDA;
 }
 
 int TcBf16::pass2_split_slots(int64_t O_pad, int64_t S, int ctas) {

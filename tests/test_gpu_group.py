@@ -1,7 +1,9 @@
 """The batching form: many uneven problems, one grouped launch per phase, CUDA graph.
 
-Each problem of a group must follow the single-problem FP32 path and its d_KL must match
-the FP64 oracle's to 1e-4 after the same iterations.  The two paths share the pass tiles
+FP32 form (CUDA cores): each problem of a group must follow the single-problem FP32 path
+and its d_KL must match the FP64 oracle's to 1e-4 after the same iterations.  BF16 form
+(tensor-core passes): every problem against the FP64 oracle half-step by half-step with the
+BF16 form's bounds (test_gpu_bf16.py).  The two paths share the pass tiles
 but not the reductions between them (split sums, the eq. 10 denominator and the step
 16 / 29 sums are taken in different fixed orders), so their float32 trajectories agree
 to rounding amplified by two DNA iterations: 5e-5 relative.  Graph replay must equal
@@ -23,7 +25,7 @@ SHAPES = [(64, 128, 8), (700, 300, 16), (150, 900, 32), (333, 129, 64), (90, 517
           (257, 257, 33), (1, 200, 4), (400, 1, 12), (128, 640, 64), (77, 77, 7)]
 
 
-def _group(problems):
+def _group(problems, bf16=False):
     import torch
 
     import paper_1301_3389_gb300 as dna
@@ -31,8 +33,9 @@ def _group(problems):
     V = [torch.from_numpy(p.V).to(dev) for p in problems]
     W = [torch.from_numpy(p.W).to(dev) for p in problems]
     H = [torch.from_numpy(p.H).to(dev) for p in problems]
+    opts = dna.make_opts(dtype=dna.DNA_BF16) if bf16 else None
     g = dna.dna_group_create([p.V.shape[0] for p in problems], [p.V.shape[1] for p in problems],
-                             [p.W.shape[1] for p in problems])
+                             [p.W.shape[1] for p in problems], opts)
     dna.dna_group_set_stream(g)
     dna.dna_group_bind(g, V, W, H)
     return dna, g, V, W, H
@@ -168,6 +171,86 @@ def test_group_rejects_unsupported():
     with pytest.raises(dna.DNAError) as e:
         dna.dna_group_create([10], [10], [65])
     assert e.value.code == dna.DNA_ERR_UNSUPPORTED
-    with pytest.raises(dna.DNAError) as e:
-        dna.dna_group_create([10], [10], [8], dna.make_opts(dtype=dna.DNA_BF16))
-    assert e.value.code == dna.DNA_ERR_UNSUPPORTED
+    for opts in (dna.make_opts(dtype=dna.DNA_F64),
+                 dna.make_opts(dtype=dna.DNA_BF16, engine=dna.DNA_ENGINE_SIMT),
+                 dna.make_opts(dtype=dna.DNA_F32, engine=dna.DNA_ENGINE_TENSOR)):
+        with pytest.raises(dna.DNAError) as e:
+            dna.dna_group_create([10], [10], [8], opts)
+        assert e.value.code == dna.DNA_ERR_UNSUPPORTED
+
+
+BF16_TOL = 2e-2   # one BF16 half-step against the oracle from the same state (test_gpu_bf16)
+
+
+def test_group_bf16_matches_oracle_per_half_step():
+    """The BF16 form of the group (tcgen05 passes over the tile table): every problem, after
+    each half-step of two iterations, against the FP64 oracle's half-step from the group's
+    own state with the group's selections replayed where they differ at near ties: W and H
+    within the BF16 form's 2e-2 relative (Frobenius) and its element-wise bound; d_KL of the
+    final factors within 1e-4."""
+    import torch
+    probs = _problems(5)
+    dna, g, V, W, H = _group(probs, bf16=True)
+    try:
+        dna.dna_group_normalize(g, 1)
+        V64 = [p.V.astype(np.float64) for p in probs]
+        for it in range(2):
+            for which in (0, 1):
+                torch.cuda.synchronize()
+                before = [(w.double().cpu().numpy(), h.double().cpu().numpy()) for w, h in zip(W, H)]
+                (dna.dna_group_step_H if which == 0 else dna.dna_group_step_W)(g)
+                torch.cuda.synchronize()
+                assert dna.dna_group_get_status(g) == 0
+                for q, p in enumerate(probs):
+                    n = p.V.shape[1] if which == 0 else p.V.shape[0]
+                    ch = dna.dna_group_get_choice(g, q, which, n)
+                    W0, H0 = before[q]
+                    one = (o.h_half_step if which == 0 else o.w_half_step)(V64[q], W0, H0)
+                    m1, _ = replay_choice(one, ch, "bf16")
+                    Wg = W[q].double().cpu().numpy()
+                    Hg = H[q].double().cpu().numpy()
+                    assert step_elementwise(dataclasses.replace(one, choice=m1), which, W0, H0,
+                                            Wg, Hg, "bf16", label="group-bf16") <= 1.0, (q, it, which)
+                    step = o.dna_step_h if which == 0 else o.dna_step_w
+                    Wr, Hr, _ = step(V64[q], W0, H0, choice=m1)
+                    assert rel_fro(Wg, Wr) < BF16_TOL and rel_fro(Hg, Hr) < BF16_TOL, (q, it, which)
+        kl = dna.dna_group_kl(g, len(probs))
+        for q, p in enumerate(probs):
+            kr = o.kl_divergence(V64[q], W[q].double().cpu().numpy() @ H[q].double().cpu().numpy())
+            assert abs(kl[q] - kr) <= 1e-4 * max(kr, 1.0), (q, kl[q], kr)
+    finally:
+        dna.dna_group_destroy(g)
+
+
+def test_group_bf16_graph_autotune():
+    """BF16 group: graph replay equals direct launches bit for bit; the autotuner picks a
+    split size and a pass-2 tile size, restores W and H, and the group keeps iterating."""
+    import torch
+    outs = []
+    for graph in (False, True):
+        probs = _problems(6)
+        dna, g, V, W, H = _group(probs, bf16=True)
+        try:
+            dna.dna_group_use_graph(g, graph)
+            dna.dna_group_normalize(g, 1)
+            dna.dna_group_iterate(g, 3)
+            torch.cuda.synchronize()
+            outs.append([(w.cpu().numpy().copy(), h.cpu().numpy().copy()) for w, h in zip(W, H)])
+            assert dna.dna_group_get_status(g) == 0
+            if graph:
+                before = outs[-1]
+                rows = dna.dna_group_autotune(g, 1)
+                r2, units = dna.dna_group_tile_config(g)
+                assert rows == r2 and rows in (256, 512, 1024, 2048, 4096, 1 << 30)
+                assert units in (2, 4, 8, 16, 32)
+                torch.cuda.synchronize()
+                for (w0, h0), w, h in zip(before, W, H):
+                    np.testing.assert_array_equal(w0, w.cpu().numpy())
+                    np.testing.assert_array_equal(h0, h.cpu().numpy())
+                dna.dna_group_iterate(g, 1)
+                assert dna.dna_group_get_status(g) == 0
+        finally:
+            dna.dna_group_destroy(g)
+    for (w0, h0), (w1, h1) in zip(*outs):
+        np.testing.assert_array_equal(w0, w1)
+        np.testing.assert_array_equal(h0, h1)

@@ -180,20 +180,21 @@ __global__ void __launch_bounds__(1024) k_cand_fused(View v, const double* __res
 // ascending split order while they stream in (no separate pass over them); all loads of
 // a thread are issued before their results are used.  With BF the grid covers O_pad and
 // the bf16 operand rows [o][rp] are written with 16-byte stores (zeros in the padding).
+// The 32 columns of block bx (the kernel below; the grouped form runs it per problem).
 template <typename Tp, bool BF, int RS>
-__global__ void __launch_bounds__(512) k_cand_reg(View v, const double* __restrict__ c,
-                                                  const Tp* __restrict__ Apart,
-                                                  const Tp* __restrict__ Bpart, int splits,
-                                                  Tp* __restrict__ Xmu, Tp* __restrict__ Xdna,
-                                                  Tp eps, Tp alpha, bf16* __restrict__ Xmk,
-                                                  bf16* __restrict__ Xdk, int64_t rp,
-                                                  int64_t plane) {
+__device__ __forceinline__ void cand_reg_tile(const View& v, const double* __restrict__ c,
+                                              const Tp* __restrict__ Apart,
+                                              const Tp* __restrict__ Bpart, int splits,
+                                              Tp* __restrict__ Xmu, Tp* __restrict__ Xdna,
+                                              Tp eps, Tp alpha, bf16* __restrict__ Xmk,
+                                              bf16* __restrict__ Xdk, int64_t rp, int64_t plane,
+                                              int64_t bx) {
     static_assert(RS % 8 == 0, "operand rows are written 8 values at a time");
     __shared__ Tp red[16][33];
     __shared__ Tp scl[32];
     const int64_t R = v.R, O = v.O;
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int64_t o = (int64_t)blockIdx.x * 32 + tx;
+    const int64_t o = bx * 32 + tx;
     const bool live = o < O;
     const int64_t r0 = (int64_t)ty * RS;
     const Tp* __restrict__ X = static_cast<const Tp*>(v.X);
@@ -279,6 +280,18 @@ __global__ void __launch_bounds__(512) k_cand_reg(View v, const double* __restri
             }
         }
     }
+}
+
+template <typename Tp, bool BF, int RS>
+__global__ void __launch_bounds__(512) k_cand_reg(View v, const double* __restrict__ c,
+                                                  const Tp* __restrict__ Apart,
+                                                  const Tp* __restrict__ Bpart, int splits,
+                                                  Tp* __restrict__ Xmu, Tp* __restrict__ Xdna,
+                                                  Tp eps, Tp alpha, bf16* __restrict__ Xmk,
+                                                  bf16* __restrict__ Xdk, int64_t rp,
+                                                  int64_t plane) {
+    cand_reg_tile<Tp, BF, RS>(v, c, Apart, Bpart, splits, Xmu, Xdna, eps, alpha, Xmk, Xdk, rp,
+                              plane, blockIdx.x);
 }
 
 // A[0][i] = A[0][i] + A[1][i] + ... + A[splits-1][i] (ascending, the order the candidates

@@ -19,6 +19,7 @@
 
 #include "dna.h"
 #include "dna_internal.h"
+#include "glue_kernels.cuh"
 #include "simt_kernels.cuh"
 
 namespace dna {
@@ -94,61 +95,168 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// BF16 form: the candidates and their bf16 operand rows [O_pad][64] (the single-problem
+// register candidates kernel per tile (problem, 32-column block); blocks cover O_pad so
+// the padding rows are written as zeros).  CTA = 32 columns x 8 groups of 8 r.
 __global__ void __launch_bounds__(256)
-    k_g_select(const GProb* __restrict__ P, const GTile* __restrict__ tl, int n, int w,
-               double reg) {
+    k_g_candidates_bf(const GProb* __restrict__ P, const TcGView* __restrict__ gv,
+                      const GTile* __restrict__ tl, int n, int w, float eps, float alpha) {
     for (int t = blockIdx.x; t < n; t += gridDim.x) {
         const GTile tt = tl[t];
         const GProb& p = P[tt.prob];
-        const View v = p.v[w];
-        simt::select_tile<float>(v, p.Xmu, p.Xdna, p.dpart, p.nslot[w], p.choice[w], p.dfin[w],
-                                 tt.a, reg);
+        const TcGView& g = gv[2 * tt.prob + w];
+        glue::cand_reg_tile<float, true, 8>(p.v[w], p.c, p.A, p.B, p.sp1[w], p.Xmu, p.Xdna, eps,
+                                            alpha, static_cast<glue::bf16*>(g.Xmk),
+                                            static_cast<glue::bf16*>(g.Xdk), 64, 0, tt.a);
+        __syncthreads();   // the body's shared arrays are reused by the next tile
     }
 }
 
-// Factor sums for 32 values of r of one problem: of y over s (which = 0, into c) or of x
-// over o (which = 1, into sig), plus the regularisation weight; an exact zero becomes 1.
+// Selection for 32 columns o of one problem (tile (problem, block)): the costs (pass-2
+// slots plus reg * sum_r x of each candidate, eq. 5) by the first warp, then the chosen
+// candidate's 32 columns staged in shared memory and written to X along its contiguous
+// index (o for H, r for W), so both views' stores coalesce.  CTA = 32 x 8 threads.
 __global__ void __launch_bounds__(256)
-    k_g_sums(const GProb* __restrict__ P, const GTile* __restrict__ tl, int n, int w, int which,
-             double reg) {
-    __shared__ double red[8][33];
-    const int lane = threadIdx.x, ty = threadIdx.y;
+    k_g_select(const GProb* __restrict__ P, const GTile* __restrict__ tl, int n, int w,
+               double reg) {
+    __shared__ float xs[64][33];   // [r][o]
+    __shared__ int nw[32];
+    const int tx = threadIdx.x, ty = threadIdx.y;
     for (int t = blockIdx.x; t < n; t += gridDim.x) {
         const GTile tt = tl[t];
         const GProb& p = P[tt.prob];
-        const View v = p.v[w];
-        const int64_t r = (int64_t)tt.a * 32 + lane;
-        const float* M = static_cast<const float*>(which ? v.X : v.Y);
-        const int64_t cnt = which ? v.O : v.S;
-        const int64_t si = which ? v.xo : v.ys, sr = which ? v.xr : v.yr;
-        float s = 0.f;
-        if (r < v.R)
-            for (int64_t i = ty; i < cnt; i += 8) s += M[i * si + r * sr];
-        red[ty][lane] = (double)s;
+        const View& v = p.v[w];
+        const int64_t o0 = (int64_t)tt.a * 32, o = o0 + tx;
+        const int64_t O = v.O, R = v.R;
+        if (ty == 0) {
+            int newton = 0;
+            if (o < O) {
+                double dm = 0.0, dd = 0.0;
+                for (int sp = 0; sp < p.nslot[w]; ++sp) {
+                    dm += p.dpart[((int64_t)sp * 2 + 0) * O + o];
+                    dd += p.dpart[((int64_t)sp * 2 + 1) * O + o];
+                }
+                if (reg != 0.0) {   // the penalty of eq. 5, summed over r in ascending order
+                    double sm = 0.0, sd = 0.0;
+                    for (int64_t r = 0; r < R; ++r) {
+                        sm += (double)p.Xmu[r * O + o];
+                        sd += (double)p.Xdna[r * O + o];
+                    }
+                    dm += reg * sm;
+                    dd += reg * sd;
+                }
+                newton = dd < dm;
+                p.choice[w][o] = newton ? 1 : 0;
+                p.dfin[w][o] = dm;
+                p.dfin[w][O + o] = dd;
+            }
+            nw[tx] = newton;
+        }
         __syncthreads();
-        if (ty == 0 && r < v.R) {
-            double tot = 0.0;
-            for (int k = 0; k < 8; ++k) tot += red[k][lane];
-            (which ? p.sig : p.c)[r] = simt::nonzero_sum(tot + reg, true);
+        for (int64_t r = ty; r < R; r += 8)
+            xs[r][tx] = o < O ? (nw[tx] ? p.Xdna : p.Xmu)[r * O + o] : 0.f;
+        __syncthreads();
+        float* X = static_cast<float*>(v.X);
+        if (v.xo == 1) {
+            if (o < O)
+                for (int64_t r = ty; r < R; r += 8) X[r * v.xr + o] = xs[r][tx];
+        } else {
+            for (int k = ty; k < 32; k += 8) {
+                const int64_t oo = o0 + k;
+                if (oo < O)
+                    for (int64_t r = tx; r < R; r += 32) X[oo * v.xo + r * v.xr] = xs[r][k];
+            }
         }
         __syncthreads();
     }
 }
 
-// Steps 1, 16, 29 for 8 values of r of one problem: X(r, .) /= sig_r, Y(., r) *= sig_r.
+// Factor sums of one problem per CTA step (tile (problem, -)): of y over s (which = 0,
+// into c) or of x over o (which = 1, into sig), plus the regularisation weight; an exact
+// zero becomes 1.  The matrix is read along its contiguous index: lanes over i with the
+// 8 thread rows over r (i contiguous), or lanes over r with the thread rows over i (r
+// contiguous); each r's sum is formed in a fixed order (per thread, then over the lanes or
+// the thread rows in ascending order).
+__global__ void __launch_bounds__(256)
+    k_g_sums(const GProb* __restrict__ P, const GTile* __restrict__ tl, int n, int w, int which,
+             double reg) {
+    __shared__ double red[8][65];
+    const int lane = threadIdx.x, ty = threadIdx.y;
+    for (int t = blockIdx.x; t < n; t += gridDim.x) {
+        const GProb& p = P[tl[t].prob];
+        const View& v = p.v[w];
+        const float* M = static_cast<const float*>(which ? v.X : v.Y);
+        const int64_t cnt = which ? v.O : v.S;
+        const int64_t si = which ? v.xo : v.ys, sr = which ? v.xr : v.yr;
+        const int64_t R = v.R;
+        double* out = which ? p.sig : p.c;
+        if (si == 1) {
+            for (int64_t r = ty; r < R; r += 8) {
+                float s = 0.f;
+                for (int64_t i = lane; i < cnt; i += 32) s += M[r * sr + i];
+                double d = (double)s;
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) d += __shfl_down_sync(0xffffffffu, d, off);
+                if (lane == 0) out[r] = simt::nonzero_sum(d + reg, true);
+            }
+        } else {
+            for (int64_t r0 = 0; r0 < R; r0 += 64) {
+                float s0 = 0.f, s1 = 0.f;
+                const int64_t ra = r0 + lane, rb = r0 + 32 + lane;
+                for (int64_t i = ty; i < cnt; i += 8) {
+                    if (ra < R) s0 += M[i * si + ra];
+                    if (rb < R) s1 += M[i * si + rb];
+                }
+                red[ty][lane] = (double)s0;
+                red[ty][32 + lane] = (double)s1;
+                __syncthreads();
+                if (ty == 0)
+                    for (int h = 0; h < 2; ++h) {
+                        const int64_t r = r0 + 32 * h + lane;
+                        if (r < R) {
+                            double d = 0.0;
+                            for (int k = 0; k < 8; ++k) d += red[k][32 * h + lane];
+                            out[r] = simt::nonzero_sum(d + reg, true);
+                        }
+                    }
+                __syncthreads();
+            }
+        }
+    }
+}
+
+// Steps 1, 16, 29: X(r, .) /= sig_r and Y(., r) *= sig_r for a block of 32 values of i
+// (o of X or s of Y) of one problem: tiles (problem, 0 | 1 (X | Y), block).  Lanes walk
+// the matrix's contiguous index.
 __global__ void __launch_bounds__(256)
     k_g_rescale(const GProb* __restrict__ P, const GTile* __restrict__ tl, int n, int w) {
+    const int lane = threadIdx.x, ty = threadIdx.y;
     for (int t = blockIdx.x; t < n; t += gridDim.x) {
         const GTile tt = tl[t];
         const GProb& p = P[tt.prob];
-        const View v = p.v[w];
-        const int64_t r = (int64_t)tt.a * 8 + threadIdx.y;
-        if (r >= v.R) continue;
-        const float f = (float)p.sig[r], inv = 1.0f / f;
-        float* X = static_cast<float*>(v.X);
-        float* Y = const_cast<float*>(static_cast<const float*>(v.Y));
-        for (int64_t i = threadIdx.x; i < v.O; i += 32) X[r * v.xr + i * v.xo] *= inv;
-        for (int64_t i = threadIdx.x; i < v.S; i += 32) Y[i * v.ys + r * v.yr] *= f;
+        const View& v = p.v[w];
+        const bool isx = tt.a == 0;
+        float* M = static_cast<float*>(isx ? v.X : const_cast<void*>(v.Y));
+        const int64_t cnt = isx ? v.O : v.S;
+        const int64_t si = isx ? v.xo : v.ys, sr = isx ? v.xr : v.yr;
+        const int64_t R = v.R, i0 = (int64_t)tt.b * 32;
+        if (si == 1) {
+            const int64_t i = i0 + lane;
+            if (i < cnt)
+                for (int64_t r = ty; r < R; r += 8) {
+                    const float f = (float)p.sig[r];
+                    M[r * sr + i] = isx ? M[r * sr + i] * (1.0f / f) : M[r * sr + i] * f;
+                }
+        } else {
+            for (int k = ty; k < 32; k += 8) {
+                const int64_t i = i0 + k;
+                if (i >= cnt) break;
+                for (int64_t r = lane; r < R; r += 32) {
+                    const float f = (float)p.sig[r];
+                    M[i * si + r] = isx ? M[i * si + r] * (1.0f / f) : M[i * si + r] * f;
+                }
+            }
+        }
     }
 }
 
@@ -209,7 +317,7 @@ struct dna_group {
     std::vector<dna::TcGView> hgv;
     struct TcBufs { float* Vp; int64_t ldp; void *Xk, *Yk, *Ytk, *Y2tk, *Xmk, *Xdk; };
     std::vector<TcBufs> tcb;
-    TileList ops_in[2], ops_cand[2], tp1[2], tp2[2];
+    TileList ops_in[2], cand_bf[2], tp1[2], tp2[2];
     cudaGraphExec_t gexec = nullptr;
     int64_t graph_launches = 0;
     std::vector<void*> tile_allocs;
@@ -294,17 +402,16 @@ int build_tiles(dna_group* g) {
             for (int64_t b = 0; b < nob; ++b)
                 for (int s = 0; s < p.sp2[w]; ++s) t2[w][p.rclass].push_back({q, (int)b, s, 0});
             for (int64_t b = 0; b < (v.O + 31) / 32; ++b) tc[w].push_back({q, (int)b, 0, 0});
-            for (int64_t b = 0; b < (v.R + 31) / 32; ++b) {
-                ty[w].push_back({q, (int)b, 0, 0});
-                tx[w].push_back({q, (int)b, 0, 0});
-            }
-            for (int64_t b = 0; b < (v.R + 7) / 8; ++b) tr[w].push_back({q, (int)b, 0, 0});
+            ty[w].push_back({q, 0, 0, 0});
+            tx[w].push_back({q, 0, 0, 0});
+            for (int64_t b = 0; b < (v.O + 31) / 32; ++b) tr[w].push_back({q, 0, (int)b, 0});
+            for (int64_t b = 0; b < (v.S + 31) / 32; ++b) tr[w].push_back({q, 1, (int)b, 0});
         }
         const View& v = p.v[0];
         for (int64_t b = 0; b < (v.O + ob - 1) / ob; ++b)
             for (int s = 0; s < p.sp2[0]; ++s) tk[p.rclass].push_back({q, (int)b, s, 0});
     }
-    std::vector<GTile> ti[2], tcn[2], tq1[2], tq2[2];
+    std::vector<GTile> ti[2], tcb[2], tq1[2], tq2[2];
     for (int q = 0; q < g->count; ++q)
         for (int w = 0; w < 2; ++w) {
             GProb& p = g->hp[q];
@@ -321,12 +428,10 @@ int build_tiles(dna_group* g) {
             t.slots2 = dna::TcBf16::pass2_split_slots(t.O_pad, S, (int)G);
             p.nslot[w] = t.slots2;
             for (int64_t me = 0; me < G; ++me) tq2[w].push_back({q, (int)me, (int)G, 0});
-            for (int64_t by = 0; by < t.O_pad / 32; ++by)
-                for (int bx = 0; bx < 2; ++bx) {
-                    ti[w].push_back({q, 0, bx, (int)by});
-                    tcn[w].push_back({q, 2, bx, (int)by});
-                    tcn[w].push_back({q, 3, bx, (int)by});
-                }
+            for (int64_t by = 0; by < t.O_pad / 32; ++by) {
+                for (int bx = 0; bx < 2; ++bx) ti[w].push_back({q, 0, bx, (int)by});
+                tcb[w].push_back({q, (int)by, 0, 0});
+            }
             for (int64_t bx = 0; bx < t.S_pad / 32; ++bx)
                 for (int by = 0; by < 2; ++by) ti[w].push_back({q, 1, (int)bx, by});
         }
@@ -334,7 +439,7 @@ int build_tiles(dna_group* g) {
     if (g->tc) {
         for (int w = 0; w < 2; ++w) {
             e |= upload(g, ti[w], &g->ops_in[w]);
-            e |= upload(g, tcn[w], &g->ops_cand[w]);
+            e |= upload(g, tcb[w], &g->cand_bf[w]);
             e |= upload(g, tq1[w], &g->tp1[w]);
             e |= upload(g, tq2[w], &g->tp2[w]);
         }
@@ -420,9 +525,13 @@ int g_half(dna_group* g, int w, bool mu_only) {
                                                 8 * g->num_sms, g->gs);
         if (!e) e = dna::TcBf16::group_pass1(g->gv, g->tp1[w].d, g->tp1[w].n, w, true, g->status,
                                              g->gs);
-        if (!e) e = launch_small(g, 3, g->cand[w], w);
-        if (!e) e = dna::TcBf16::group_operands(g->gv, g->ops_cand[w].d, g->ops_cand[w].n, w,
-                                                8 * g->num_sms, g->gs);
+        if (!e && g->cand_bf[w].n) {
+            const int grid = std::max(1, std::min(g->cand_bf[w].n, 8 * g->num_sms));
+            dna::grp::k_g_candidates_bf<<<grid, dim3(32, 8), 0, g->gs>>>(
+                g->dp, g->gv, g->cand_bf[w].d, g->cand_bf[w].n, w, (float)g->o.eps,
+                (float)g->o.alpha);
+            e = after_launch();
+        }
         if (!e) e = dna::TcBf16::group_pass2(g->gv, g->tp2[w].d, g->tp2[w].n, w, g->status, g->gs);
     } else {
         if (!e) e = launch_p1<16>(g, g->p1[w][0], w, true);
@@ -847,9 +956,8 @@ int64_t dna_group_launches_per_iteration(dna_group* g) {
     int64_t n = 0;
     for (int w = 0; w < 2; ++w) {
         n += 5;  // sums, candidates, select, normaliser sums, rescale
-        if (g->tc)   // operands, pass 1, candidate operands, pass 2
-            n += (g->ops_in[w].n > 0) + (g->tp1[w].n > 0) + (g->ops_cand[w].n > 0) +
-                 (g->tp2[w].n > 0);
+        if (g->tc)   // operands, pass 1, pass 2 (the candidates write their bf16 rows)
+            n += (g->ops_in[w].n > 0) + (g->tp1[w].n > 0) + (g->tp2[w].n > 0);
         else
             for (int k = 0; k < dna::grp::NCLASS; ++k)
                 n += (g->p1[w][k].n > 0) + (g->p2[w][k].n > 0);

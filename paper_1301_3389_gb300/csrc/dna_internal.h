@@ -287,7 +287,7 @@ struct TcBf16 {
     static int chunk();
     static int oblock();
     // The grouped BF16 form (R <= 64, padded rank 64), tables in device memory.
-    // Operands of view w: tiles (problem, what, bx, by) of k_g_operands.
+    // Operands of view w: tiles (problem, 0 | 1 (X | Y), block of 64, -) of k_g_operands.
     static int group_operands(const TcGView* gv, const void* tiles, int n, int w, int grid,
                               cudaStream_t st);
     // pass 1: one CTA per tile (problem, o-block, split)

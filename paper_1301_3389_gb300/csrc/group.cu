@@ -428,12 +428,9 @@ int build_tiles(dna_group* g) {
             t.slots2 = dna::TcBf16::pass2_split_slots(t.O_pad, S, (int)G);
             p.nslot[w] = t.slots2;
             for (int64_t me = 0; me < G; ++me) tq2[w].push_back({q, (int)me, (int)G, 0});
-            for (int64_t by = 0; by < t.O_pad / 32; ++by) {
-                for (int bx = 0; bx < 2; ++bx) ti[w].push_back({q, 0, bx, (int)by});
-                tcb[w].push_back({q, (int)by, 0, 0});
-            }
-            for (int64_t bx = 0; bx < t.S_pad / 32; ++bx)
-                for (int by = 0; by < 2; ++by) ti[w].push_back({q, 1, (int)bx, by});
+            for (int64_t by = 0; by < t.O_pad / 32; ++by) tcb[w].push_back({q, (int)by, 0, 0});
+            for (int64_t b = 0; b < t.O_pad / 64; ++b) ti[w].push_back({q, 0, (int)b, 0});
+            for (int64_t b = 0; b < t.S_pad / 64; ++b) ti[w].push_back({q, 1, (int)b, 0});
         }
     int e = DNA_OK;
     if (g->tc) {

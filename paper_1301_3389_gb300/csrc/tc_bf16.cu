@@ -416,28 +416,63 @@ __global__ void k_y_operands(const float* __restrict__ Y, int64_t ys, int64_t yr
     y_operands_tile(Y, ys, yr, S, R, Yk, rp, Ytk, Y2tk, s_pad, with_sq, blockIdx.x, blockIdx.y);
 }
 
-// Grouped operands of view w, one 32 x 32 tile per CTA step (tiles[t] = (problem, what,
-// bx, by)): what = 0: X -> Xk [O_pad][64] (x(r, o) at X[r xr + o xo]); 1: Y -> Yk, Ytk,
-// Y2tk; 2: the candidates Xmu, Xdna ([R][O] float32) -> Xmk, Xdk.
+// Grouped bf16 operands of view w, one 64 x 64 tile per CTA step: tiles[t] = (problem,
+// what, block, -), what = 0: X -> Xk [O_pad][64] rows o of the block (x(r, o) at
+// X[r xr + o xo]); what = 1: Y -> Yk [S_pad][64], Ytk and Y2tk [64][S_pad] for the block's
+// 64 values of s (y(s, r) at Y[s ys + r yr]).  The tile is read along the matrix's
+// contiguous index and written as bf16 pairs, 128 bytes per row and warp; entries past R
+// or past O (S) are zeros.  CTA = 32 x 8 threads.
 __global__ void __launch_bounds__(256)
     k_g_operands(const TcGView* __restrict__ gv, const int4* __restrict__ tiles, int n, int w) {
-    for (int i = blockIdx.x; i < n; i += gridDim.x) {
-        const int4 t = tiles[i];
-        const TcGView& v = gv[2 * t.x + w];
-        bf16* const Xmk = static_cast<bf16*>(v.Xmk);
-        bf16* const Xdk = static_cast<bf16*>(v.Xdk);
-        if (t.y == 0)
-            to_bf16_tile(v.X, v.xo, v.xr, v.O, v.R, static_cast<bf16*>(v.Xk), 64, false, t.z,
-                         t.w);
-        else if (t.y == 1)
-            y_operands_tile(v.Y, v.ys, v.yr, v.S, v.R, static_cast<bf16*>(v.Yk), 64,
-                            static_cast<bf16*>(v.Ytk), static_cast<bf16*>(v.Y2tk), v.S_pad, true,
-                            t.z, t.w);
-        else if (t.y == 2)
-            to_bf16_tile(v.Xmu, 1, v.O, v.O, v.R, Xmk, 64, false, t.z, t.w);
-        else
-            to_bf16_tile(v.Xdna, 1, v.O, v.O, v.R, Xdk, 64, false, t.z, t.w);
-        __syncthreads();   // the tile buffer is reused by the next step
+    __shared__ float tile[64][65];   // [r][i]
+    const int lane = threadIdx.x, ty = threadIdx.y;
+    for (int t = blockIdx.x; t < n; t += gridDim.x) {
+        const int4 tt = tiles[t];
+        const TcGView& v = gv[2 * tt.x + w];
+        const bool isx = tt.y == 0;
+        const float* M = isx ? v.X : v.Y;
+        const int64_t cnt = isx ? v.O : v.S;
+        const int64_t si = isx ? v.xo : v.ys, sr = isx ? v.xr : v.yr;
+        const int64_t R = v.R, i0 = (int64_t)tt.z * 64;
+        if (si == 1) {   // contiguous along i: lanes walk i
+            for (int r = ty; r < 64; r += 8)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int64_t i = i0 + 32 * h + lane;
+                    tile[r][32 * h + lane] = (r < R && i < cnt) ? M[r * sr + i] : 0.f;
+                }
+        } else {         // contiguous along r: lanes walk r
+            for (int k = ty; k < 64; k += 8)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int64_t i = i0 + k, r = 32 * h + lane;
+                    tile[r][k] = (r < R && i < cnt) ? M[i * si + r * sr] : 0.f;
+                }
+        }
+        __syncthreads();
+        // rows [i][64] with r contiguous: Xk (X) or Yk (Y); lanes walk pairs of r
+        bf16* RM = static_cast<bf16*>(isx ? v.Xk : v.Yk);
+        const int64_t ipad = isx ? v.O_pad : v.S_pad;
+        for (int k = ty; k < 64; k += 8) {
+            const int64_t i = i0 + k;
+            if (i < ipad)
+                *reinterpret_cast<uint32_t*>(RM + i * 64 + 2 * lane) =
+                    pack_bf16x2(tile[2 * lane][k], tile[2 * lane + 1][k]);
+        }
+        if (!isx) {   // Ytk, Y2tk [64][S_pad] with s contiguous; lanes walk pairs of s
+            bf16* Yt = static_cast<bf16*>(v.Ytk);
+            bf16* Y2t = static_cast<bf16*>(v.Y2tk);
+            for (int r = ty; r < 64; r += 8) {
+                const int64_t i = i0 + 2 * lane;
+                if (i < v.S_pad) {
+                    const float y0 = tile[r][2 * lane], y1 = tile[r][2 * lane + 1];
+                    *reinterpret_cast<uint32_t*>(Yt + r * v.S_pad + i) = pack_bf16x2(y0, y1);
+                    *reinterpret_cast<uint32_t*>(Y2t + r * v.S_pad + i) =
+                        pack_bf16x2(y0 * y0, y1 * y1);
+                }
+            }
+        }
+        __syncthreads();   // the tile is reused by the next step
     }
 }
 

@@ -8,15 +8,16 @@
 //             qbar = q / z (one reciprocal) and writes both as bf16 rows Q[o][s], Qbar[o][s]
 //             to a workspace (the operands GEMM2 / GEMM3 take in bf16 anyway);
 //   contract  A[o, r] += sum_s Q[o, s] Yt[r, s] and B[o, r] += sum_s Qbar[o, s] Y2t[r, s]:
-//             a plain dual GEMM over (o-block, 256-wide r-block, split of s) tiles, both
-//             128 x 256 accumulators in tensor memory, Q, Qbar, Yt, Y2t K-slices (64 values
-//             of s) brought in by TMA, the accumulators written out per split as in the
-//             other pass-1 kernels ([split][R][O]).
+//             a plain GEMM over (A or B, pair of o-blocks, 256-wide r-block, split of s)
+//             tiles, two 128 x 256 accumulators in tensor memory sharing each Yt (Y2t)
+//             K-slice of 64 values of s, the Q (Qbar) slices of both o-blocks brought in by
+//             TMA beside it, the accumulators written out per split as in the other pass-1
+//             kernels ([split][R][O]).
 //
 // Against one fused kernel per r-block (which forms Z once per r-block of 128) this forms
 // Z once, and each SM brings in about half the bytes per unit of useful work: the ratios
 // kernel brings in Y (64 bytes per MAC row of 128) and V and writes Q, Qbar; the contract
-// kernel brings in 96 KB per 64-value slice for 2 x 128 x 256 x 64 MACs.  The price is the
+// kernel brings in 64 KB per 64-value slice for 2 x 128 x 256 x 64 MACs.  The price is the
 // Q, Qbar round trip through HBM (4 bytes per element of V, written once and read once per
 // r-block, the second read mostly from L2).
 //
@@ -93,18 +94,23 @@ constexpr int W_PROD_B = B_EPI, W_MMA_B = B_EPI + 1;
 constexpr int B_THREADS = (B_EPI + 2) * 32;
 constexpr int RB = 256;                      // r per tile of the contract kernel
 
+// A tile covers two o-blocks (M = 256 as two 128-row MMAs that share each Yt slice), one
+// 256-wide r-block, one split of s and one accumulator kind (A, or B): shared-memory
+// bytes per MAC are 2 (1/256 + 1/256), two thirds of what a 128 x 256 tile of both kinds
+// takes, for the same tensor work.  Tensor memory holds the two 128 x 256 accumulators.
 struct LayoutB {
-    static constexpr int KST = 2;
+    static constexpr int KST = 3;
     static constexpr uint32_t Q_TILE = OBLK * 64 * 2;    // [128 o][64 s]
     static constexpr uint32_t Y_TILE = RB * 64 * 2;      // [256 r][64 s]
-    static constexpr uint32_t STAGE = 2 * Q_TILE + 2 * Y_TILE;
+    // Q (or Qbar) of the two o-blocks, then Yt (or Y2t)
+    static constexpr uint32_t STAGE = 2 * Q_TILE + Y_TILE;
     static constexpr uint32_t BAR = KST * STAGE;
     static constexpr uint32_t TOTAL = BAR + 256;
-    static constexpr uint32_t NCOLS = 512;               // A 256 | B 256
+    static constexpr uint32_t NCOLS = 512;               // o-block 0: 256 | o-block 1: 256
     static_assert(STAGE % 1024 == 0, "alignment");
     static_assert(TOTAL + 1024 <= 232448, "shared memory budget");
 };
-enum { C_KFULL = 0, C_KEMPTY = 2, C_ACCFULL = 4, C_ACCEMPTY = 5, C_DRAIN = 6, C_COUNT = 7 };
+enum { C_KFULL = 0, C_KEMPTY = 3, C_ACCFULL = 6, C_ACCEMPTY = 7, C_DRAIN = 8, C_COUNT = 9 };
 
 struct ContractArgs {
     int64_t S, O, R, s_per;    // s_per: a multiple of 64
@@ -113,16 +119,20 @@ struct ContractArgs {
 };
 
 struct BTile {
-    int64_t o0, s_begin;
-    int nsl, rb, split;
+    int64_t o0, s_begin;       // o0: the first of the tile's two o-blocks
+    int nsl, rb, split, which;
 };
-__device__ __forceinline__ BTile b_tile(int t, int nob, int nsplit, const ContractArgs& a) {
+// tiles: which slowest, then the r-block, then the split, o-block pair fastest
+__device__ __forceinline__ BTile b_tile(int t, int nop, int nrb, int nsplit,
+                                        const ContractArgs& a) {
     BTile x;
-    const int per_rb = nob * nsplit;
-    x.rb = t / per_rb;
-    const int rest = t % per_rb;
-    x.o0 = (int64_t)(rest % nob) * OBLK;
-    x.split = rest / nob;
+    const int per_rb = nop * nsplit, per_which = nrb * per_rb;
+    x.which = t / per_which;
+    const int u = t % per_which;
+    x.rb = u / per_rb;
+    const int rest = u % per_rb;
+    x.o0 = (int64_t)(rest % nop) * 2 * OBLK;
+    x.split = rest / nop;
     x.s_begin = (int64_t)x.split * a.s_per;
     const int64_t s_end = min(a.S, x.s_begin + a.s_per);
     x.nsl = s_end > x.s_begin ? (int)((s_end - x.s_begin + 63) / 64) : 0;
@@ -404,7 +414,8 @@ __global__ void __launch_bounds__(mat::A_THREADS, 1)
 // ---------------------------------------------------------------- contract kernel
 template <bool WITH_B>
 __global__ void __launch_bounds__(mat::B_THREADS, 1)
-    k_tc_contract(mat::ContractArgs a, int nob, int nsplit, int ntiles, int* status,
+    k_tc_contract(mat::ContractArgs a, int nob, int nop, int nrb, int nsplit, int ntiles,
+                  int* status,
                   const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmQb,
                   const __grid_constant__ CUtensorMap tmYt,
                   const __grid_constant__ CUtensorMap tmY2t) {
@@ -439,7 +450,6 @@ __global__ void __launch_bounds__(mat::B_THREADS, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
-    constexpr uint32_t STAGE_BYTES = WITH_B ? L::STAGE : L::Q_TILE + L::Y_TILE;
 
     if (warp == W_PROD_B) {
         if (lane == 0 && t_begin < t_end) {
@@ -448,8 +458,12 @@ __global__ void __launch_bounds__(mat::B_THREADS, 1)
             int kk = 0;
             bool ok = true;
             for (int t = t_begin; ok && t < t_end; ++t) {
-                const BTile x = b_tile(t, nob, nsplit, a);
-                for (int sl = 0; sl < x.nsl; ++sl) {
+                const BTile x = b_tile(t, nop, nrb, nsplit, a);
+                const CUtensorMap* mq = x.which ? &tmQb : &tmQ;
+                const CUtensorMap* my = x.which ? &tmY2t : &tmYt;
+                // the pair's second o-block exists unless the o-block count is odd
+                const bool two = x.o0 / OBLK + 1 < nob;
+                for (int sl = 0; sl < x.nsl; ++sl, ++kk) {
                     const int st = kk % KST;
                     if (!(ok = wait_phase(&bar[C_KEMPTY + st], ((kk / KST) & 1) ^ 1, abort)))
                         break;
@@ -457,14 +471,10 @@ __global__ void __launch_bounds__(mat::B_THREADS, 1)
                     const int32_t s0 = (int32_t)(x.s_begin + 64 * (int64_t)sl);
                     const int32_t r0 = RB * x.rb, o0 = (int32_t)x.o0;
                     uint64_t* fb = &bar[C_KFULL + st];
-                    mbar_arrive_expect_tx(fb, STAGE_BYTES);
-                    tma_load_2d(dst, &tmQ, s0, o0, fb);
-                    tma_load_2d(dst + 2 * L::Q_TILE, &tmYt, s0, r0, fb);   // [256 r][64 s]
-                    if (WITH_B) {
-                        tma_load_2d(dst + L::Q_TILE, &tmQb, s0, o0, fb);
-                        tma_load_2d(dst + 2 * L::Q_TILE + L::Y_TILE, &tmY2t, s0, r0, fb);
-                    }
-                    ++kk;
+                    mbar_arrive_expect_tx(fb, L::STAGE - (two ? 0u : L::Q_TILE));
+                    tma_load_2d(dst, mq, s0, o0, fb);                              // [128 o][64 s]
+                    if (two) tma_load_2d(dst + L::Q_TILE, mq, s0, o0 + OBLK, fb);
+                    tma_load_2d(dst + 2 * L::Q_TILE, my, s0, r0, fb);              // [256 r][64 s]
                 }
             }
             if (*abort)
@@ -477,7 +487,9 @@ __global__ void __launch_bounds__(mat::B_THREADS, 1)
             int j = 0, tt = 0;
             constexpr uint32_t idesc = idesc_bf16(OBLK, RB);
             for (int t = t_begin; ok && t < t_end; ++t, ++tt) {
-                const int nsl = b_tile(t, nob, nsplit, a).nsl;
+                const BTile x = b_tile(t, nop, nrb, nsplit, a);
+                const int nsl = x.nsl;
+                const bool two = x.o0 / OBLK + 1 < nob;
                 // the epilogue has copied the previous tile's accumulators out
                 if (tt > 0 && !(ok = wait_phase(&bar[C_ACCEMPTY], (tt - 1) & 1, abort))) break;
                 tc_fence_after();
@@ -485,16 +497,14 @@ __global__ void __launch_bounds__(mat::B_THREADS, 1)
                 for (int sl = 0; sl < nsl; ++sl, ++j) {
                     if (!(ok = wait_phase(&bar[C_KFULL + j % KST], (j / KST) & 1, abort))) break;
                     tc_fence_after();
-                    const uint32_t qs = sbase + (j % KST) * L::STAGE;
-                    const uint32_t ys = qs + 2 * L::Q_TILE;
+                    const uint32_t q0 = sbase + (j % KST) * L::STAGE, q1 = q0 + L::Q_TILE;
+                    const uint32_t ys = q0 + 2 * L::Q_TILE;
 #pragma unroll
                     for (int kq = 0; kq < 4; ++kq) {
                         const uint32_t acc = (sl > 0 || kq > 0) ? 1u : 0u;
-                        mma_bf16(tmem, desc_sw128(qs + 32u * kq), desc_sw128(ys + 32u * kq),
-                                 idesc, acc);
-                        if (WITH_B)
-                            mma_bf16(tmem + RB, desc_sw128(qs + L::Q_TILE + 32u * kq),
-                                     desc_sw128(ys + L::Y_TILE + 32u * kq), idesc, acc);
+                        const uint64_t yd = desc_sw128(ys + 32u * kq);
+                        mma_bf16(tmem, desc_sw128(q0 + 32u * kq), yd, idesc, acc);
+                        if (two) mma_bf16(tmem + RB, desc_sw128(q1 + 32u * kq), yd, idesc, acc);
                     }
                     mma_commit(&bar[C_KEMPTY + j % KST]);
                 }
@@ -506,23 +516,24 @@ __global__ void __launch_bounds__(mat::B_THREADS, 1)
             }
         }
     } else {
-        // epilogue warps: lane quadrant qd, matrix mat (0: A, 1: B); rows o = o0 + 32 qd + lane
-        const int qd = warp & 3, mat_ = warp >> 2;
+        // epilogue warps: lane quadrant qd, o-block h of the pair; rows
+        // o = o0 + 128 h + 32 qd + lane, the accumulator's 256 columns in eight loads
+        const int qd = warp & 3, h = warp >> 2;
         const uint32_t lane_off = (uint32_t)(32 * qd) << 16;
         int tt = 0;
         for (int t = t_begin; t < t_end; ++t, ++tt) {
-            const BTile x = b_tile(t, nob, nsplit, a);
+            const BTile x = b_tile(t, nop, nrb, nsplit, a);
             bool ok = wait_phase(&bar[C_ACCFULL], tt & 1, abort);
             if (!__all_sync(0xffffffffu, ok)) break;
             tc_fence_after();
-            const int64_t o = x.o0 + 32 * qd + lane;
-            if (WITH_B || mat_ == 0) {
-                float* dst = mat_ ? a.Bpart : a.Apart;
+            const int64_t o = x.o0 + OBLK * h + 32 * qd + lane;
+            if (WITH_B || x.which == 0) {
+                float* dst = x.which ? a.Bpart : a.Apart;
                 const int64_t base = (int64_t)x.split * a.R;
 #pragma unroll 1
                 for (int c = 0; c < RB / 32; ++c) {
                     uint32_t r32[32];
-                    tmem_ld32(tmem + mat_ * RB + 32 * c + lane_off, r32);
+                    tmem_ld32(tmem + (uint32_t)(RB * h + 32 * c) + lane_off, r32);
                     tmem_ld_wait();
                     if (o < a.O)
 #pragma unroll
@@ -581,9 +592,11 @@ int launch_mat(const TcOperands& op, const TcMaps& m, float* Apart, float* Bpart
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return DNA_ERR_CUDA;
-    const int ntiles = (RP / RB) * nob * splits;
+    const int nop = (nob + 1) / 2, nrb = RP / RB;
+    const int ntiles = (WITH_B ? 2 : 1) * nrb * nop * splits;
     const int grid = op.ctas > 0 ? std::min(op.ctas, ntiles) : ntiles;
-    k<<<grid, B_THREADS, smem, st>>>(ca, nob, splits, ntiles, status, m.q, m.qb, m.yt256, m.y2t256);
+    k<<<grid, B_THREADS, smem, st>>>(ca, nob, nop, nrb, splits, ntiles, status, m.q, m.qb,
+                                     m.yt256, m.y2t256);
     return after_launch();
 }
 

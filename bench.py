@@ -59,6 +59,11 @@ WORKLOADS = {
     "precision_large": dict(fn=workloads.precision_large, N=8192, T=32768, R=512,
                             desc="N=8192 T=32768 R=512, Gamma(0.5) W0, 70%-sparse Gamma(0.5) H0, "
                                  "V = W0 H0 + |N(0,0.01)|"),
+    # the same recipe at a quarter of the size (V 268 MB, larger than L2): the case for
+    # multi-pass ncu captures of the rank-512 kernels
+    "precision_scaled": dict(fn=lambda seed=0: workloads.precision_large(seed, 4096, 16384, 512),
+                             N=4096, T=16384, R=512,
+                             desc="N=4096 T=16384 R=512, the precision_large recipe at 1/4 size"),
 }
 
 

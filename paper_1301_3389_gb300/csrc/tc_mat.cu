@@ -122,15 +122,17 @@ struct BTile {
     int64_t o0, s_begin;       // o0: the first of the tile's two o-blocks
     int nsl, rb, split, which;
 };
-// tiles: which slowest, then the r-block, then the split, o-block pair fastest
+// tiles: which slowest, then the split, then the o-block pair, r-block fastest: a CTA
+// runs the r-blocks of one (pair, split) back to back, so the second reads the Q slices
+// from L2 (CTAs running together share the Yt slices of one split)
 __device__ __forceinline__ BTile b_tile(int t, int nop, int nrb, int nsplit,
                                         const ContractArgs& a) {
     BTile x;
-    const int per_rb = nop * nsplit, per_which = nrb * per_rb;
+    const int per_which = nrb * nop * nsplit;
     x.which = t / per_which;
     const int u = t % per_which;
-    x.rb = u / per_rb;
-    const int rest = u % per_rb;
+    x.rb = u % nrb;
+    const int rest = u / nrb;
     x.o0 = (int64_t)(rest % nop) * 2 * OBLK;
     x.split = rest / nop;
     x.s_begin = (int64_t)x.split * a.s_per;

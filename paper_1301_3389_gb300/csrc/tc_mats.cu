@@ -128,16 +128,17 @@ struct BTile {
     int64_t o0, s_begin;
     int nsl, rb, split, which;
 };
-// tiles: which slowest, then the r-block, then the split, o-block fastest (CTAs that run
-// together share the Yt slices in L2)
+// tiles: which slowest, then the split, then the o-block, r-block fastest: a CTA runs the
+// r-blocks of one (o-block, split) back to back, so the second reads the Q planes from L2
+// (CTAs running together share the Yt slices of one split)
 __device__ __forceinline__ BTile b_tile(int t, int nob, int nrb, int nsplit,
                                         const ContractArgs& a) {
     BTile x;
-    const int per_rb = nob * nsplit, per_which = nrb * per_rb;
+    const int per_which = nrb * nob * nsplit;
     x.which = t / per_which;
     const int u = t % per_which;
-    x.rb = u / per_rb;
-    const int rest = u % per_rb;
+    x.rb = u % nrb;
+    const int rest = u / nrb;
     x.o0 = (int64_t)(rest % nob) * OBLK;
     x.split = rest / nob;
     x.s_begin = (int64_t)x.split * a.s_per;

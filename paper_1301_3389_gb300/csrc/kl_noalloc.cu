@@ -27,29 +27,29 @@ static __device__ __align__(256) unsigned char g_kl_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
-void* g_base[kMaxDevices] = {};
 int g_sms[kMaxDevices] = {};
 
-// Device address of g_kl_scratch on the current device (looked up once per device, with
-// that device current).  The host-side name of the array is not a device address.
+// Device address of g_kl_scratch in the current context, looked up on every call (a
+// lookup, no allocation): an address cached per device would go stale under another
+// context or after a device reset.  The host-side name of the array is not a device
+// address.  The SM count is cached per device.
 int scratch_base(int dev, void** base, int* sms) {
     if (dev < 0 || dev >= kMaxDevices) return DNA_ERR_UNSUPPORTED;
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_kl_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return DNA_ERR_CUDA;
+    }
     std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_base[dev]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_kl_scratch) != cudaSuccess || !p) {
-            cudaGetLastError();
-            return DNA_ERR_CUDA;
-        }
+    if (!g_sms[dev]) {
         int n = 0;
         if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
             cudaGetLastError();
             return DNA_ERR_CUDA;
         }
-        g_base[dev] = p;
         g_sms[dev] = n;
     }
-    *base = g_base[dev];
+    *base = p;
     *sms = g_sms[dev];
     return DNA_OK;
 }

@@ -314,7 +314,7 @@ int dna_group_use_graph(dna_group* g, int enable);
 /* Autotuner: time `reps` iterations for each candidate tile configuration and keep the
  * fastest; W and H are restored afterwards.  Candidates: the split size (rows of s per
  * tile of the reductions) and, in the BF16 form, the pass-2 tile size ((o-block, chunk)
- * units per CTA, 2 to 32).  The chosen split size is written to *rows_out (may be NULL).
+ * units per CTA, 4 to 128).  The chosen split size is written to *rows_out (may be NULL).
  * Synchronises. */
 int dna_group_autotune(dna_group* g, int reps, int64_t* rows_out);
 

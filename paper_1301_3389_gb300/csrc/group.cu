@@ -432,6 +432,26 @@ int build_tiles(dna_group* g) {
             for (int64_t b = 0; b < t.O_pad / 64; ++b) ti[w].push_back({q, 0, (int)b, 0});
             for (int64_t b = 0; b < t.S_pad / 64; ++b) ti[w].push_back({q, 1, (int)b, 0});
         }
+    if (g->tc)
+        // longest tiles first (pass 1: rows of s in the tile; pass 2: units of the CTA), so
+        // the short ones fill the end of the grid instead of a long one trailing alone
+        for (int w = 0; w < 2; ++w) {
+            auto rows1 = [&](const GTile& x) {
+                const GProb& p = g->hp[x.prob];
+                const int64_t s0 = (int64_t)x.b * p.per1[w];
+                return std::min<int64_t>(p.per1[w], p.v[w].S - s0);
+            };
+            std::stable_sort(tq1[w].begin(), tq1[w].end(), [&](const GTile& a, const GTile& b) {
+                return rows1(a) > rows1(b);
+            });
+            auto units2 = [&](const GTile& x) {
+                const dna::TcGView& t = g->hgv[2 * x.prob + w];
+                return (int64_t)(x.a + 1) * t.U2 / x.b - (int64_t)x.a * t.U2 / x.b;
+            };
+            std::stable_sort(tq2[w].begin(), tq2[w].end(), [&](const GTile& a, const GTile& b) {
+                return units2(a) > units2(b);
+            });
+        }
     int e = DNA_OK;
     if (g->tc) {
         for (int w = 0; w < 2; ++w) {
@@ -863,10 +883,10 @@ int dna_group_autotune(dna_group* g, int reps, int64_t* rows_out) {
     int64_t best_rows = g->split_rows, best_units = g->p2_units;
     int e = DNA_OK;
     // the BF16 form also tunes the pass-2 tile size: (o-block, chunk) units per CTA
-    const int64_t units_tc[] = {2, 4, 8, 16, 32};
+    const int64_t units_tc[] = {4, 8, 16, 32, 64, 128};
     const int64_t units_simt[] = {8};
     const int64_t* units = g->tc ? units_tc : units_simt;
-    const int nunits = g->tc ? 5 : 1;
+    const int nunits = g->tc ? 6 : 1;
     for (int64_t rows : cands) {
         for (int ui = 0; ui < nunits && !e; ++ui) {
             g->split_rows = rows;

@@ -334,7 +334,8 @@ int dna_group_get_status(dna_group* g);
  * Synchronises. */
 int dna_group_get_choice(dna_group* g, int q, int which, uint8_t* out, int64_t len);
 
-/* Kernel launches of one grouped iteration (both half-steps). */
+/* Kernel launches of one grouped iteration (both half-steps, as dna_group_iterate runs
+ * them). */
 int64_t dna_group_launches_per_iteration(dna_group* g);
 
 /* Release the group and its workspace. */

@@ -260,6 +260,71 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// BF16 form: the rescale of half-step w (X_w(r, .) /= sig_r, Y_w(., r) *= sig_r) fused with
+// the bf16 operands of half-step wn = 1 - w, whose X is Y_w and whose Y is X_w: tiles
+// (problem, 0 | 1 (X | Y of view wn), block of 64) of that view's operand list, each
+// element scaled once, written back in float32 and as bf16 operand rows (the layout of
+// k_g_operands).  CTA = 32 x 8 threads.
+__global__ void __launch_bounds__(256)
+    k_g_rescale_ops(const GProb* __restrict__ P, const TcGView* __restrict__ gv,
+                    const GTile* __restrict__ tl, int n, int wn) {
+    __shared__ float tile[64][65];   // [r][i]
+    const int lane = threadIdx.x, ty = threadIdx.y;
+    for (int t = blockIdx.x; t < n; t += gridDim.x) {
+        const GTile tt = tl[t];
+        const GProb& p = P[tt.prob];
+        const TcGView& v = gv[2 * tt.prob + wn];
+        const bool isx = tt.a == 0;   // X of view wn = Y_w (times sig); else Y of wn = X_w
+        float* M = const_cast<float*>(isx ? v.X : v.Y);
+        const int64_t cnt = isx ? v.O : v.S;
+        const int64_t si = isx ? v.xo : v.ys, sr = isx ? v.xr : v.yr;
+        const int64_t R = v.R, i0 = (int64_t)tt.b * 64;
+        auto scaled = [&](int64_t r, int64_t at) {
+            const float f = (float)p.sig[r];
+            const float x = isx ? M[at] * f : M[at] * (1.0f / f);
+            M[at] = x;
+            return x;
+        };
+        if (si == 1) {
+            for (int r = ty; r < 64; r += 8)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int64_t i = i0 + 32 * h + lane;
+                    tile[r][32 * h + lane] = (r < R && i < cnt) ? scaled(r, r * sr + i) : 0.f;
+                }
+        } else {
+            for (int k = ty; k < 64; k += 8)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int64_t i = i0 + k, r = 32 * h + lane;
+                    tile[r][k] = (r < R && i < cnt) ? scaled(r, i * si + r * sr) : 0.f;
+                }
+        }
+        __syncthreads();
+        glue::bf16* RM = static_cast<glue::bf16*>(isx ? v.Xk : v.Yk);
+        const int64_t ipad = isx ? v.O_pad : v.S_pad;
+        for (int k = ty; k < 64; k += 8) {
+            const int64_t i = i0 + k;
+            if (i < ipad)
+                *reinterpret_cast<uint32_t*>(RM + i * 64 + 2 * lane) =
+                    glue::pack2(tile[2 * lane][k], tile[2 * lane + 1][k]);
+        }
+        if (!isx) {
+            glue::bf16* Yt = static_cast<glue::bf16*>(v.Ytk);
+            glue::bf16* Y2t = static_cast<glue::bf16*>(v.Y2tk);
+            for (int r = ty; r < 64; r += 8) {
+                const int64_t i = i0 + 2 * lane;
+                if (i < v.S_pad) {
+                    const float y0 = tile[r][2 * lane], y1 = tile[r][2 * lane + 1];
+                    *reinterpret_cast<uint32_t*>(Yt + r * v.S_pad + i) = glue::pack2(y0, y1);
+                    *reinterpret_cast<uint32_t*>(Y2t + r * v.S_pad + i) = glue::pack2(y0 * y0, y1 * y1);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // d_KL of each problem: sum of its per-column partials, fixed order.
 __global__ void k_g_kl_reduce(const GProb* __restrict__ P, int count, double* __restrict__ out) {
     __shared__ double red[256];
@@ -533,13 +598,17 @@ int g_normalize(dna_group* g, int which) {
     return e ? e : launch_small(g, 2, g->resc[which], which);
 }
 
-int g_half(dna_group* g, int w, bool mu_only) {
+// One half-step of every problem.  BF16 form: ops_ready says the bf16 operands of view w
+// are current (written by the previous half-step's fused rescale); fuse_next makes this
+// half-step's rescale write the operands of view 1 - w.
+int g_half(dna_group* g, int w, bool mu_only, bool ops_ready = false, bool fuse_next = false) {
     const double reg_den = w ? g->o.rho : g->o.lambda;
     if (mu_only) return DNA_ERR_UNSUPPORTED;
     int e = launch_small(g, 0, g->sums_y[w], w, reg_den);
     if (g->tc) {   // bf16 operands, pass 1 on the tensor cores, candidates, their bf16 copies
-        if (!e) e = dna::TcBf16::group_operands(g->gv, g->ops_in[w].d, g->ops_in[w].n, w,
-                                                8 * g->num_sms, g->gs);
+        if (!e && !ops_ready)
+            e = dna::TcBf16::group_operands(g->gv, g->ops_in[w].d, g->ops_in[w].n, w,
+                                            8 * g->num_sms, g->gs);
         if (!e) e = dna::TcBf16::group_pass1(g->gv, g->tp1[w].d, g->tp1[w].n, w, true, g->status,
                                              g->gs);
         if (!e && g->cand_bf[w].n) {
@@ -560,13 +629,25 @@ int g_half(dna_group* g, int w, bool mu_only) {
         if (!e) e = launch_p2<64, false>(g, g->p2[w][2], w);
     }
     if (!e) e = launch_small(g, 4, g->cand[w], w, w ? g->o.rho : g->o.lambda);
-    if (!e) e = g_normalize(g, w == 1 ? 1 : 0);
-    return e;
+    if (e) return e;
+    if (g->tc && fuse_next) {   // steps 16 / 29 fused with the next view's operands
+        const int wn = 1 - w;
+        e = launch_small(g, 1, g->sums_x[w], w, w ? g->o.lambda : g->o.rho);
+        if (!e && g->ops_in[wn].n) {
+            const int grid = std::max(1, std::min(g->ops_in[wn].n, 8 * g->num_sms));
+            dna::grp::k_g_rescale_ops<<<grid, dim3(32, 8), 0, g->gs>>>(
+                g->dp, g->gv, g->ops_in[wn].d, g->ops_in[wn].n, wn);
+            e = after_launch();
+        }
+        return e;
+    }
+    return g_normalize(g, w == 1 ? 1 : 0);
 }
 
 int g_iteration(dna_group* g) {
-    int e = g_half(g, 0, false);
-    return e ? e : g_half(g, 1, false);
+    // the H half-step's rescale writes the W half-step's bf16 operands (BF16 form)
+    int e = g_half(g, 0, false, false, true);
+    return e ? e : g_half(g, 1, false, true, false);
 }
 
 struct Handoff {   // order the group's private stream after, and before, the caller's
@@ -973,8 +1054,9 @@ int64_t dna_group_launches_per_iteration(dna_group* g) {
     int64_t n = 0;
     for (int w = 0; w < 2; ++w) {
         n += 5;  // sums, candidates, select, normaliser sums, rescale
-        if (g->tc)   // operands, pass 1, pass 2 (the candidates write their bf16 rows)
-            n += (g->ops_in[w].n > 0) + (g->tp1[w].n > 0) + (g->tp2[w].n > 0);
+        if (g->tc)   // pass 1, pass 2 and, for the H half-step only, the operands (the W
+                     // half-step's come from the H half-step's rescale)
+            n += (w == 0 && g->ops_in[w].n > 0) + (g->tp1[w].n > 0) + (g->tp2[w].n > 0);
         else
             for (int k = 0; k < dna::grp::NCLASS; ++k)
                 n += (g->p1[w][k].n > 0) + (g->p2[w][k].n > 0);

@@ -254,3 +254,29 @@ def test_group_bf16_graph_autotune():
     for (w0, h0), (w1, h1) in zip(*outs):
         np.testing.assert_array_equal(w0, w1)
         np.testing.assert_array_equal(h0, h1)
+
+
+def test_group_bf16_fused_rescale_equals_half_steps():
+    """dna_group_iterate (whose H half-step rescale also writes the W half-step's bf16
+    operands) equals separate dna_group_step_H / dna_group_step_W calls bit for bit."""
+    import torch
+    outs = []
+    for fused in (True, False):
+        probs = _problems(7)
+        dna, g, V, W, H = _group(probs, bf16=True)
+        try:
+            dna.dna_group_normalize(g, 1)
+            for _ in range(2):
+                if fused:
+                    dna.dna_group_iterate(g, 1)
+                else:
+                    dna.dna_group_step_H(g)
+                    dna.dna_group_step_W(g)
+            torch.cuda.synchronize()
+            assert dna.dna_group_get_status(g) == 0
+            outs.append([(w.cpu().numpy().copy(), h.cpu().numpy().copy()) for w, h in zip(W, H)])
+        finally:
+            dna.dna_group_destroy(g)
+    for (w0, h0), (w1, h1) in zip(*outs):
+        np.testing.assert_array_equal(w0, w1)
+        np.testing.assert_array_equal(h0, h1)

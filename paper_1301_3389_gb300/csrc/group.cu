@@ -95,20 +95,97 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-// BF16 form: the candidates and their bf16 operand rows [O_pad][64] (the single-problem
-// register candidates kernel per tile (problem, 32-column block); blocks cover O_pad so
-// the padding rows are written as zeros).  CTA = 32 columns x 8 groups of 8 r.
+// BF16 form: the candidates (eq. 11, eq. 15 / 17 and the eq. 10 renormalisation, the
+// arithmetic of the single-problem candidates kernels) and their bf16 operand rows
+// [O_pad][64], one warp per tile (problem, 32 columns; blocks cover O_pad, so padding rows
+// are written as zeros).  Each lane owns a column: it walks r in groups of 8, keeps its
+// Newton candidates in registers for the eq. 10 sum (no cross-thread reduction), and writes
+// each group of 8 bf16 values as one 16-byte store.  CTA = 8 warps, each on its own tile.
 __global__ void __launch_bounds__(256)
     k_g_candidates_bf(const GProb* __restrict__ P, const TcGView* __restrict__ gv,
                       const GTile* __restrict__ tl, int n, int w, float eps, float alpha) {
-    for (int t = blockIdx.x; t < n; t += gridDim.x) {
+    const int lane = threadIdx.x;
+    for (int t = blockIdx.x * 8 + threadIdx.y; t < n; t += gridDim.x * 8) {
         const GTile tt = tl[t];
         const GProb& p = P[tt.prob];
+        const View& v = p.v[w];
         const TcGView& g = gv[2 * tt.prob + w];
-        glue::cand_reg_tile<float, true, 8>(p.v[w], p.c, p.A, p.B, p.sp1[w], p.Xmu, p.Xdna, eps,
-                                            alpha, static_cast<glue::bf16*>(g.Xmk),
-                                            static_cast<glue::bf16*>(g.Xdk), 64, 0, tt.a);
-        __syncthreads();   // the body's shared arrays are reused by the next tile
+        const int64_t R = v.R, O = v.O, o = (int64_t)tt.a * 32 + lane;
+        const bool live = o < O;
+        const int sp1 = p.sp1[w];
+        const float* __restrict__ X = static_cast<const float*>(v.X);
+        glue::bf16* Xmk = static_cast<glue::bf16*>(g.Xmk) + o * 64;
+        glue::bf16* Xdk = static_cast<glue::bf16*>(g.Xdk) + o * 64;
+        float xd[64];
+        float den = 0.f;
+#pragma unroll
+        for (int rc = 0; rc < 8; ++rc) {
+            // the group's loads first (split partials in ascending split order, then x)
+            float ra[8], rb[8], xv[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) { ra[i] = 0.f; rb[i] = 0.f; xv[i] = 0.f; }
+            if (live && 8 * rc < R) {
+                for (int sp = 0; sp < sp1; ++sp)
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int64_t r = 8 * rc + i;
+                        if (r < R) {
+                            ra[i] += p.A[((int64_t)sp * R + r) * O + o];
+                            rb[i] += p.B[((int64_t)sp * R + r) * O + o];
+                        }
+                    }
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int64_t r = 8 * rc + i;
+                    if (r < R) xv[i] = X[r * v.xr + o * v.xo];
+                }
+            }
+            float xm[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int64_t r = 8 * rc + i;
+                xm[i] = 0.f;
+                xd[8 * rc + i] = 0.f;
+                if (live && r < R) {
+                    const float cr = (float)p.c[r], ic = 1.0f / cr;
+                    const float a = ra[i] * ic - 1.0f;   // eq. 7
+                    const float b = rb[i] * ic;          // eq. 14
+                    const float xr = xv[i];
+                    xm[i] = xr * (ra[i] * ic);           // eq. 11
+                    float d;
+                    if (a < 0.f) {                    // eq. 15, gain floored at eps
+                        const float xb = xr * b;
+                        const float gn = simt::dev_div(xb, xb - a);
+                        d = xr * (gn > eps ? gn : eps);
+                    } else {                          // eq. 17, step capped at alpha x
+                        const float stp = b > 0.f ? simt::dev_div(a, b) : 0.f;
+                        const float cap = alpha * xr;
+                        d = xr + (stp < cap ? stp : cap);
+                    }
+                    p.Xmu[r * O + o] = xm[i];
+                    xd[8 * rc + i] = d;
+                    den += cr * d;
+                }
+            }
+            *reinterpret_cast<uint4*>(Xmk + 8 * rc) =
+                make_uint4(glue::pack2(xm[0], xm[1]), glue::pack2(xm[2], xm[3]),
+                           glue::pack2(xm[4], xm[5]), glue::pack2(xm[6], xm[7]));
+        }
+        // eq. 10: column scale s_o / sum_r c_r g_r (1 when that sum is not positive)
+        const float sc = live ? (den > 0.f ? (float)v.vsum[o] / den : 1.0f) : 0.f;
+#pragma unroll
+        for (int rc = 0; rc < 8; ++rc) {
+            float d[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int64_t r = 8 * rc + i;
+                d[i] = xd[8 * rc + i] * sc;
+                if (live && r < R) p.Xdna[r * O + o] = d[i];
+            }
+            *reinterpret_cast<uint4*>(Xdk + 8 * rc) =
+                make_uint4(glue::pack2(d[0], d[1]), glue::pack2(d[2], d[3]),
+                           glue::pack2(d[4], d[5]), glue::pack2(d[6], d[7]));
+        }
     }
 }
 
@@ -612,7 +689,7 @@ int g_half(dna_group* g, int w, bool mu_only, bool ops_ready = false, bool fuse_
         if (!e) e = dna::TcBf16::group_pass1(g->gv, g->tp1[w].d, g->tp1[w].n, w, true, g->status,
                                              g->gs);
         if (!e && g->cand_bf[w].n) {
-            const int grid = std::max(1, std::min(g->cand_bf[w].n, 8 * g->num_sms));
+            const int grid = std::max(1, std::min((g->cand_bf[w].n + 7) / 8, 8 * g->num_sms));
             dna::grp::k_g_candidates_bf<<<grid, dim3(32, 8), 0, g->gs>>>(
                 g->dp, g->gv, g->cand_bf[w].d, g->cand_bf[w].n, w, (float)g->o.eps,
                 (float)g->o.alpha);

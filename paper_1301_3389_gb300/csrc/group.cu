@@ -189,78 +189,80 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-// Selection for 32 columns o of one problem (tile (problem, block)): the costs (pass-2
-// slots plus reg * sum_r x of each candidate, eq. 5) by the first warp, then the chosen
-// candidate's 32 columns staged in shared memory and written to X along its contiguous
-// index (o for H, r for W), so both views' stores coalesce.  CTA = 32 x 8 threads.
+// Selection for 32 columns o of one problem per warp (tile (problem, block); CTA = 8
+// warps on 8 tiles): each lane sums its column's costs (pass-2 slots plus reg * sum_r x of
+// each candidate, eq. 5), then the warp stages the chosen candidate's 32 columns in its own
+// shared-memory tile and writes X along its contiguous index (o for H, r for W), so both
+// views' stores coalesce.
 __global__ void __launch_bounds__(256)
     k_g_select(const GProb* __restrict__ P, const GTile* __restrict__ tl, int n, int w,
                double reg) {
-    __shared__ float xs[64][33];   // [r][o]
-    __shared__ int nw[32];
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    for (int t = blockIdx.x; t < n; t += gridDim.x) {
+    __shared__ float xs_all[8][32][33];   // per warp [r][o], 32 values of r at a time
+    const int lane = threadIdx.x, wid = threadIdx.y;
+    float (*xs)[33] = xs_all[wid];
+    for (int t = blockIdx.x * 8 + wid; t < n; t += gridDim.x * 8) {
         const GTile tt = tl[t];
         const GProb& p = P[tt.prob];
         const View& v = p.v[w];
-        const int64_t o0 = (int64_t)tt.a * 32, o = o0 + tx;
+        const int64_t o0 = (int64_t)tt.a * 32, o = o0 + lane;
         const int64_t O = v.O, R = v.R;
-        if (ty == 0) {
-            int newton = 0;
-            if (o < O) {
-                double dm = 0.0, dd = 0.0;
-                for (int sp = 0; sp < p.nslot[w]; ++sp) {
-                    dm += p.dpart[((int64_t)sp * 2 + 0) * O + o];
-                    dd += p.dpart[((int64_t)sp * 2 + 1) * O + o];
-                }
-                if (reg != 0.0) {   // the penalty of eq. 5, summed over r in ascending order
-                    double sm = 0.0, sd = 0.0;
-                    for (int64_t r = 0; r < R; ++r) {
-                        sm += (double)p.Xmu[r * O + o];
-                        sd += (double)p.Xdna[r * O + o];
-                    }
-                    dm += reg * sm;
-                    dd += reg * sd;
-                }
-                newton = dd < dm;
-                p.choice[w][o] = newton ? 1 : 0;
-                p.dfin[w][o] = dm;
-                p.dfin[w][O + o] = dd;
+        bool newton = false;
+        if (o < O) {
+            double dm = 0.0, dd = 0.0;
+            for (int sp = 0; sp < p.nslot[w]; ++sp) {
+                dm += p.dpart[((int64_t)sp * 2 + 0) * O + o];
+                dd += p.dpart[((int64_t)sp * 2 + 1) * O + o];
             }
-            nw[tx] = newton;
+            if (reg != 0.0) {   // the penalty of eq. 5, summed over r in ascending order
+                double sm = 0.0, sd = 0.0;
+                for (int64_t r = 0; r < R; ++r) {
+                    sm += (double)p.Xmu[r * O + o];
+                    sd += (double)p.Xdna[r * O + o];
+                }
+                dm += reg * sm;
+                dd += reg * sd;
+            }
+            newton = dd < dm;
+            p.choice[w][o] = newton ? 1 : 0;
+            p.dfin[w][o] = dm;
+            p.dfin[w][O + o] = dd;
         }
-        __syncthreads();
-        for (int64_t r = ty; r < R; r += 8)
-            xs[r][tx] = o < O ? (nw[tx] ? p.Xdna : p.Xmu)[r * O + o] : 0.f;
-        __syncthreads();
         float* X = static_cast<float*>(v.X);
-        if (v.xo == 1) {
-            if (o < O)
-                for (int64_t r = ty; r < R; r += 8) X[r * v.xr + o] = xs[r][tx];
-        } else {
-            for (int k = ty; k < 32; k += 8) {
-                const int64_t oo = o0 + k;
-                if (oo < O)
-                    for (int64_t r = tx; r < R; r += 32) X[oo * v.xo + r * v.xr] = xs[r][k];
+        if (v.xo == 1) {   // X rows contiguous along o: lanes write their own column
+            if (o < O) {
+                const float* src = newton ? p.Xdna : p.Xmu;
+                for (int64_t r = 0; r < R; ++r) X[r * v.xr + o] = src[r * O + o];
+            }
+        } else {           // contiguous along r: stage the 32 columns, lanes walk r
+            const float* src = newton ? p.Xdna : p.Xmu;
+            for (int64_t r0 = 0; r0 < R; r0 += 32) {
+                const int64_t nr = R - r0 < 32 ? R - r0 : 32;
+                for (int64_t r = 0; r < nr; ++r) xs[r][lane] = o < O ? src[(r0 + r) * O + o] : 0.f;
+                __syncwarp();
+                for (int k = 0; k < 32; ++k) {
+                    const int64_t oo = o0 + k;
+                    if (oo >= O) break;
+                    if (lane < nr) X[oo * v.xo + (r0 + lane) * v.xr] = xs[lane][k];
+                }
+                __syncwarp();
             }
         }
-        __syncthreads();
     }
 }
 
-// Factor sums of one problem per CTA step (tile (problem, -)): of y over s (which = 0,
-// into c) or of x over o (which = 1, into sig), plus the regularisation weight; an exact
-// zero becomes 1.  The matrix is read along its contiguous index: lanes over i with the
-// 8 thread rows over r (i contiguous), or lanes over r with the thread rows over i (r
-// contiguous); each r's sum is formed in a fixed order (per thread, then over the lanes or
-// the thread rows in ascending order).
+// Factor sums of one problem: of y over s (which = 0, into c) or of x over o (which = 1,
+// into sig), plus the regularisation weight; an exact zero becomes 1.  The matrix is read
+// along its contiguous index.  i contiguous: tile (problem, rb) covers rows r = 8 rb + ty,
+// one warp per row (lanes over i, then a shuffle sum); r contiguous: tile (problem, 0)
+// covers every r, lanes over r and the 8 thread rows over i (added in ascending order).
 __global__ void __launch_bounds__(256)
     k_g_sums(const GProb* __restrict__ P, const GTile* __restrict__ tl, int n, int w, int which,
              double reg) {
     __shared__ double red[8][65];
     const int lane = threadIdx.x, ty = threadIdx.y;
     for (int t = blockIdx.x; t < n; t += gridDim.x) {
-        const GProb& p = P[tl[t].prob];
+        const GTile tt = tl[t];
+        const GProb& p = P[tt.prob];
         const View& v = p.v[w];
         const float* M = static_cast<const float*>(which ? v.X : v.Y);
         const int64_t cnt = which ? v.O : v.S;
@@ -268,7 +270,8 @@ __global__ void __launch_bounds__(256)
         const int64_t R = v.R;
         double* out = which ? p.sig : p.c;
         if (si == 1) {
-            for (int64_t r = ty; r < R; r += 8) {
+            const int64_t r = 8 * (int64_t)tt.a + ty;
+            if (r < R) {
                 float s = 0.f;
                 for (int64_t i = lane; i < cnt; i += 32) s += M[r * sr + i];
                 double d = (double)s;
@@ -544,8 +547,11 @@ int build_tiles(dna_group* g) {
             for (int64_t b = 0; b < nob; ++b)
                 for (int s = 0; s < p.sp2[w]; ++s) t2[w][p.rclass].push_back({q, (int)b, s, 0});
             for (int64_t b = 0; b < (v.O + 31) / 32; ++b) tc[w].push_back({q, (int)b, 0, 0});
-            ty[w].push_back({q, 0, 0, 0});
-            tx[w].push_back({q, 0, 0, 0});
+            // factor sums: blocks of 8 rows where the matrix is contiguous along i (the
+            // long sums over T), else one tile per problem
+            const int64_t nrb = (v.R + 7) / 8;
+            for (int64_t b = 0; b < (v.ys == 1 ? nrb : 1); ++b) ty[w].push_back({q, (int)b, 0, 0});
+            for (int64_t b = 0; b < (v.xo == 1 ? nrb : 1); ++b) tx[w].push_back({q, (int)b, 0, 0});
             for (int64_t b = 0; b < (v.O + 31) / 32; ++b) tr[w].push_back({q, 0, (int)b, 0});
             for (int64_t b = 0; b < (v.S + 31) / 32; ++b) tr[w].push_back({q, 1, (int)b, 0});
         }
@@ -662,7 +668,10 @@ int launch_small(dna_group* g, int which, const TileList& t, int w, double reg =
         case 2: k_g_rescale<<<grid, blk, 0, g->gs>>>(g->dp, t.d, t.n, w); break;
         case 3: k_g_candidates<<<grid, blk, 0, g->gs>>>(g->dp, t.d, t.n, w, (float)g->o.eps,
                                                         (float)g->o.alpha); break;
-        case 4: k_g_select<<<grid, blk, 0, g->gs>>>(g->dp, t.d, t.n, w, reg); break;
+        case 4:
+            k_g_select<<<std::max(1, std::min((t.n + 7) / 8, 8 * g->num_sms)), blk, 0, g->gs>>>(
+                g->dp, t.d, t.n, w, reg);
+            break;
         default: return DNA_ERR_ARG;
     }
     return after_launch();

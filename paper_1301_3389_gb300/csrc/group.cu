@@ -231,12 +231,14 @@ __global__ void __launch_bounds__(256)
         if (v.xo == 1) {   // X rows contiguous along o: lanes write their own column
             if (o < O) {
                 const float* src = newton ? p.Xdna : p.Xmu;
+#pragma unroll 8
                 for (int64_t r = 0; r < R; ++r) X[r * v.xr + o] = src[r * O + o];
             }
         } else {           // contiguous along r: stage the 32 columns, lanes walk r
             const float* src = newton ? p.Xdna : p.Xmu;
             for (int64_t r0 = 0; r0 < R; r0 += 32) {
                 const int64_t nr = R - r0 < 32 ? R - r0 : 32;
+#pragma unroll 8
                 for (int64_t r = 0; r < nr; ++r) xs[r][lane] = o < O ? src[(r0 + r) * O + o] : 0.f;
                 __syncwarp();
                 for (int k = 0; k < 32; ++k) {

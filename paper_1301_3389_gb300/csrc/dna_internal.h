@@ -290,9 +290,10 @@ struct TcBf16 {
     // Operands of view w: tiles (problem, 0 | 1 (X | Y), block of 64, -) of k_g_operands.
     static int group_operands(const TcGView* gv, const void* tiles, int n, int w, int grid,
                               cudaStream_t st);
-    // pass 1: one CTA per tile (problem, o-block, split)
+    // pass 1: `ctas` persistent CTAs over the tiles (problem, o-block, split), CTA i taking
+    // tiles i, i + ctas, ...
     static int group_pass1(const TcGView* gv, const void* tiles, int n, int w, bool with_b,
-                           int* status, cudaStream_t st);
+                           int ctas, int* status, cudaStream_t st);
     // pass 2: one CTA per entry (problem, rank, CTAs of that problem)
     static int group_pass2(const TcGView* gv, const void* ctas, int n, int w, int* status,
                            cudaStream_t st);

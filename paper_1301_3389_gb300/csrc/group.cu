@@ -697,8 +697,8 @@ int g_half(dna_group* g, int w, bool mu_only, bool ops_ready = false, bool fuse_
         if (!e && !ops_ready)
             e = dna::TcBf16::group_operands(g->gv, g->ops_in[w].d, g->ops_in[w].n, w,
                                             8 * g->num_sms, g->gs);
-        if (!e) e = dna::TcBf16::group_pass1(g->gv, g->tp1[w].d, g->tp1[w].n, w, true, g->status,
-                                             g->gs);
+        if (!e) e = dna::TcBf16::group_pass1(g->gv, g->tp1[w].d, g->tp1[w].n, w, true,
+                                             g->num_sms, g->status, g->gs);
         if (!e && g->cand_bf[w].n) {
             const int grid = std::max(1, std::min((g->cand_bf[w].n + 7) / 8, 8 * g->num_sms));
             dna::grp::k_g_candidates_bf<<<grid, dim3(32, 8), 0, g->gs>>>(

@@ -329,19 +329,334 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
     pass1_body<RP, WITH_B>(a, blockIdx.x, blockIdx.y, &tmY, &tmYt, &tmY2t, &tmV);
 }
 
-// Grouped pass 1: CTA i runs tile tiles[i] = (problem, o-block, split) of view w with that
-// problem's operands and tensor maps (gv[2 problem + w], global memory).
-template <int RP, bool WITH_B>
+// Persistent grouped pass 1 (padded rank 64): CTA i runs tiles i, i + G, i + 2G, ... of
+// the list (problem, o-block, split) (G CTAs; the host sorts the list longest first), with
+// the rings, the Z and Q buffers and every barrier phase running on across tiles, so a
+// tile's start (its X into tensor memory, the first copies) overlaps the previous tile's
+// last chunks.  Per tile the epilogue loads the next tile's X once it has read the last Z
+// of this one (GEMM1 no longer reads X), then drains A and B once the last GEMM2/3 is done
+// and releases them (ACCEMPTY) for the next tile's first GEMM2/3.  The chunk work is that
+// of pass1_body, with Q and Qbar double-buffered in tensor memory.
+struct GP1Tile {
+    const TcGView* v;
+    int64_t o0, s_begin, split;
+    int nch;
+};
+__device__ __forceinline__ GP1Tile gp1_tile(const TcGView* gv, const int4* tiles, int ti,
+                                            int w) {
+    const int4 t = tiles[ti];
+    GP1Tile x;
+    x.v = &gv[2 * t.x + w];
+    x.o0 = (int64_t)t.y * OBLK;
+    x.split = t.z;
+    x.s_begin = x.split * x.v->s_per1;
+    const int64_t s_end = min(x.v->S, x.s_begin + x.v->s_per1);
+    x.nch = s_end > x.s_begin ? (int)((s_end - x.s_begin + SCH - 1) / SCH) : 0;
+    return x;
+}
+
+template <bool WITH_B>
 __global__ void __launch_bounds__(P1_THREADS, 1)
-    k_tc_gpass1(const TcGView* __restrict__ gv, const int4* __restrict__ tiles, int w,
-                int* status) {
-    const int4 t = tiles[blockIdx.x];
-    const TcGView& v = gv[2 * t.x + w];
-    P1Args a{};
-    a.S = v.S; a.O = v.O; a.R = v.R; a.s_per = v.s_per1;
-    a.Apart = v.A; a.Bpart = v.B; a.status = status;
-    a.X = v.Xk; a.rp = RP;
-    pass1_body<RP, WITH_B>(a, t.y, t.z, &v.y, &v.yt, &v.y2t, &v.v);
+    k_tc_gpass1p(const TcGView* __restrict__ gv, const int4* __restrict__ tiles, int n, int w,
+                 int* status) {
+    constexpr int RP = 64;
+    using L = P1Layout<RP>;
+    constexpr int VST = L::VST, YST = L::YST, TST = L::TST;
+    // two Q / Qbar buffers in tensor memory (chunk g uses buffer g & 1), each with its own
+    // QFULL barrier, so the epilogue writes chunk g + 1's Q while GEMM2/3 read chunk g's
+    constexpr int B_ACCEMPTY = B_COUNT, B_QFULL1 = B_COUNT + 1, NBAR = B_COUNT + 2;
+    static_assert(NBAR * 8 + 16 <= 256, "barrier area");
+    constexpr uint32_t TQ2 = L::TQB + SCH / 2;   // second Q buffer, then second Qbar buffer
+    static_assert(TQ2 + SCH <= L::NCOLS, "tensor memory budget");
+    auto tq = [](int b) { return b ? TQ2 : L::TQ; };
+    auto tqb = [](int b) { return b ? TQ2 + SCH / 2 : L::TQB; };
+    auto qfull = [](int b) { return b ? B_QFULL1 : B_QFULL; };
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* sm = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const uint32_t sbase = smem_u32(sm);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + L::BAR);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L::BAR + NBAR * 8);
+    volatile int* abort = reinterpret_cast<volatile int*>(sm + L::BAR + NBAR * 8 + 8);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int G = (int)gridDim.x, t0 = (int)blockIdx.x;   // tiles t0, t0 + G, ...
+
+    if (warp == 0) { tmem_alloc(tslot, L::NCOLS); tmem_relinquish(); }
+    if (tid == W_PRODUCER * 32) {
+        mbar_init(&bar[B_XFULL], W_EPI);
+        mbar_init(&bar[B_ACCEMPTY], W_EPI);
+        for (int i = 0; i < VST; ++i) {
+            mbar_init(&bar[B_VFULL + i], 1);
+            mbar_init(&bar[B_VEMPTY + i], W_EPI);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&bar[B_YFULL + i], 1);
+            mbar_init(&bar[B_TFULL + i], 1);
+            mbar_init(&bar[B_ZFULL + i], 1);
+            mbar_init(&bar[B_ZEMPTY + i], W_EPI);
+            mbar_init(&bar[B_QEMPTY + i], 1);
+            mbar_init(&bar[B_DRAIN + i], 1);
+        }
+        mbar_init(&bar[B_QFULL], W_EPI);
+        mbar_init(&bar[B_QFULL1], W_EPI);
+        *abort = 0;
+        fence_mbar_init();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    if (warp == W_PRODUCER) {
+        // three ring cursors, each over (tile, chunk) of this CTA's tiles
+        if (lane == 0 && t0 < n) {
+            struct Cur {
+                int ti, k, g;
+                GP1Tile x;
+            };
+            auto start = [&](Cur& c) {
+                c.ti = t0; c.k = 0; c.g = 0;
+                c.x = gp1_tile(gv, tiles, c.ti, w);
+            };
+            auto next = [&](Cur& c) {
+                ++c.g;
+                if (++c.k < c.x.nch) return;
+                c.k = 0;
+                c.ti += G;
+                if (c.ti < n) c.x = gp1_tile(gv, tiles, c.ti, w);
+            };
+            Cur cv, cy, ct;
+            start(cv); start(cy); start(ct);
+            long long tw = clock64();
+            while (cv.ti < n || cy.ti < n || ct.ti < n) {
+                bool prog = false;
+                if (cv.ti < n && mbar_test(&bar[B_VEMPTY + cv.g % VST], ((cv.g / VST) & 1) ^ 1)) {
+                    const int st = cv.g % VST;
+                    mbar_arrive_expect_tx(&bar[B_VFULL + st], L::V_BYTES);
+                    tma_load_2d(sbase + L::VR + st * L::V_BYTES, &cv.x.v->v, (int32_t)cv.x.o0,
+                                (int32_t)(cv.x.s_begin + (int64_t)cv.k * SCH), &bar[B_VFULL + st]);
+                    next(cv);
+                    prog = true;
+                }
+                // Y(g) reuses the stage of chunk g - 2, free once its GEMM1 is done
+                if (cy.ti < n && (cy.g < YST || mbar_test(&bar[B_ZFULL + (cy.g & 1)],
+                                                          ((cy.g - 2) >> 1) & 1))) {
+                    const int st = cy.g % YST;
+                    const uint32_t dst = sbase + L::YR + st * L::Y_BYTES;
+                    mbar_arrive_expect_tx(&bar[B_YFULL + st], L::Y_BYTES);
+                    tma_load_2d(dst, &cy.x.v->y, 0, (int32_t)(cy.x.s_begin + (int64_t)cy.k * SCH),
+                                &bar[B_YFULL + st]);
+                    next(cy);
+                    prog = true;
+                }
+                // Y^t(g) reuses the stage of chunk g - 2, free once its GEMM2/3 are done
+                if (ct.ti < n && (ct.g < TST || mbar_test(&bar[B_QEMPTY + (ct.g & 1)],
+                                                          ((ct.g - 2) >> 1) & 1))) {
+                    const int st = ct.g % TST;
+                    const uint32_t dst = sbase + L::TR + st * L::T_STAGE;
+                    const int32_t s0 = (int32_t)(ct.x.s_begin + (int64_t)ct.k * SCH);
+                    mbar_arrive_expect_tx(&bar[B_TFULL + st], (WITH_B ? 2 : 1) * L::YT_BYTES);
+                    tma_load_2d(dst, &ct.x.v->yt, s0, 0, &bar[B_TFULL + st]);
+                    if (WITH_B) tma_load_2d(dst + L::YT_BYTES, &ct.x.v->y2t, s0, 0, &bar[B_TFULL + st]);
+                    next(ct);
+                    prog = true;
+                }
+                if (prog) {
+                    tw = clock64();
+                } else {
+                    if (*abort) break;
+                    if (clock64() - tw > WAIT_LIMIT) { *abort = 1; break; }
+                    __nanosleep(20);
+                }
+            }
+            if (*abort) {  // let the copies already issued land before the CTA exits
+                for (int k = max(0, cv.g - VST); k < cv.g; ++k)
+                    drain_phase(&bar[B_VFULL + k % VST], (k / VST) & 1);
+                for (int k = max(0, cy.g - YST); k < cy.g; ++k)
+                    drain_phase(&bar[B_YFULL + k % YST], (k / YST) & 1);
+                for (int k = max(0, ct.g - TST); k < ct.g; ++k)
+                    drain_phase(&bar[B_TFULL + k % TST], (k / TST) & 1);
+            }
+        }
+    } else if (warp == W_MMA_Z) {
+        // GEMM1 of every chunk (global index m) into Z buffer m & 1, A = the tile's X
+        if (lane == 0 && t0 < n) {
+            bool ok = true;
+            int m = 0, j = 0;
+            for (int ti = t0; ok && ti < n; ti += G, ++j) {
+                const int nch = gp1_tile(gv, tiles, ti, w).nch;
+                if (!(ok = wait_phase(&bar[B_XFULL], j & 1, abort))) break;
+                for (int k = 0; ok && k < nch; ++k, ++m) {
+                    const int zb = m & 1;
+                    if (!(ok = wait_phase(&bar[B_YFULL + m % YST], (m / YST) & 1, abort))) break;
+                    if (m >= 2 &&
+                        !(ok = wait_phase(&bar[B_ZEMPTY + zb], ((m >> 1) & 1) ^ 1, abort)))
+                        break;
+                    tc_fence_after();
+                    const uint32_t yb = sbase + L::YR + (m % YST) * L::Y_BYTES;
+#pragma unroll
+                    for (int kk = 0; kk < RP / 16; ++kk)
+                        mma_bf16_tmem_a(tmem + zb * SCH, tmem + L::TX + 8 * kk,
+                                        desc_sw128(yb + 32u * kk), idesc_bf16(OBLK, SCH), kk > 0);
+                    mma_commit(&bar[B_ZFULL + zb]);
+                }
+            }
+            if (!ok) {
+                mma_commit(&bar[B_DRAIN + 0]);
+                drain_phase(&bar[B_DRAIN + 0], 0);
+            }
+        }
+    } else if (warp == W_MMA_AB) {
+        // GEMM2 / GEMM3 of every chunk; a tile's first overwrites A and B once the
+        // epilogue has drained the previous tile's
+        if (lane == 0 && t0 < n) {
+            bool ok = true;
+            int m = 0, j = 0;
+            for (int ti = t0; ok && ti < n; ti += G, ++j) {
+                const int nch = gp1_tile(gv, tiles, ti, w).nch;
+                if (j > 0 && !(ok = wait_phase(&bar[B_ACCEMPTY], (j - 1) & 1, abort))) break;
+                for (int k = 0; ok && k < nch; ++k, ++m) {
+                    const int qb = m & 1;
+                    if (!(ok = wait_phase(&bar[qfull(qb)], (m >> 1) & 1, abort))) break;
+                    if (!(ok = wait_phase(&bar[B_TFULL + m % TST], (m / TST) & 1, abort))) break;
+                    tc_fence_after();
+                    const uint32_t tb = sbase + L::TR + (m % TST) * L::T_STAGE;
+#pragma unroll
+                    for (int kk = 0; kk < SCH / 16; ++kk) {
+                        const uint32_t acc = (k > 0 || kk > 0) ? 1u : 0u;
+                        mma_bf16_tmem_a(tmem + L::TA, tmem + tq(qb) + 8 * kk,
+                                        desc_sw128(tb + 32u * kk), idesc_bf16(OBLK, RP), acc);
+                        if (WITH_B)
+                            mma_bf16_tmem_a(tmem + L::TB, tmem + tqb(qb) + 8 * kk,
+                                            desc_sw128(tb + L::YT_BYTES + 32u * kk),
+                                            idesc_bf16(OBLK, RP), acc);
+                    }
+                    mma_commit(&bar[B_QEMPTY + (m & 1)]);
+                }
+            }
+            if (!ok) {
+                mma_commit(&bar[B_DRAIN + 1]);
+                drain_phase(&bar[B_DRAIN + 1], 0);
+            }
+        }
+    } else {
+        // epilogue warps 0-15: lane quadrant qd = warp % 4, chunk columns 16 cg .. + 15
+        const int qd = warp & 3, cg = warp >> 2;
+        const int row = 32 * qd + lane;
+        const uint32_t lane_off = (uint32_t)(32 * qd) << 16;
+        auto load_x = [&](const GP1Tile& x) {   // the tile's X into tensor memory
+            for (int u = cg; u < RP / 32; u += 4)
+                x_to_tmem(static_cast<const bf16*>(x.v->Xk), RP, x.o0 + row, u,
+                          tmem + L::TX + lane_off);
+            tmem_st_wait();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bar[B_XFULL]);
+        };
+        float zmin = 1.f;
+        bool ok = true;
+        int g = 0;   // global chunk index
+        GP1Tile x = {};
+        if (t0 < n) {
+            x = gp1_tile(gv, tiles, t0, w);
+            load_x(x);
+        }
+        for (int ti = t0; ok && ti < n; ti += G) {
+            const int64_t o = x.o0 + row;
+            for (int k = 0; k < x.nch; ++k, ++g) {
+                const int zb = g & 1, vs = g % VST;
+                ok = wait_phase(&bar[B_ZFULL + zb], (g >> 1) & 1, abort);
+                ok = ok && wait_phase(&bar[B_VFULL + vs], (g / VST) & 1, abort);
+                if (!(ok = __all_sync(0xffffffffu, ok))) break;
+                tc_fence_after();
+                uint32_t zr[16];
+                tmem_ld16(tmem + zb * SCH + lane_off + 16 * cg, zr);
+                const float* Vs = reinterpret_cast<const float*>(sm + L::VR + vs * L::V_BYTES) +
+                                  16 * cg * OBLK + row;
+                float vv[16];
+#pragma unroll
+                for (int jj = 0; jj < 16; ++jj) vv[jj] = Vs[jj * OBLK];
+                tmem_ld_wait();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&bar[B_ZEMPTY + zb]);
+                uint32_t qp[8], qbp[8];
+#pragma unroll
+                for (int jj = 0; jj < 16; jj += 2) {
+                    float q[2], qb[2];
+#pragma unroll
+                    for (int t = 0; t < 2; ++t) {
+                        const float v = vv[jj + t];
+                        const float z = __uint_as_float(zr[jj + t]);
+                        const float rz = __fdividef(1.0f, z);
+                        const bool pos = v > 0.f;
+                        zmin = fminf(zmin, pos ? z : 1.f);
+                        q[t] = pos ? v * rz : 0.f;
+                        qb[t] = pos ? q[t] * rz : 0.f;
+                    }
+                    qp[jj / 2] = pack_bf16x2(q[0], q[1]);
+                    qbp[jj / 2] = pack_bf16x2(qb[0], qb[1]);
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&bar[B_VEMPTY + vs]);
+                const int qb = g & 1;
+                if (g >= 2) {   // GEMM2/3 of chunk g - 2 have read Q buffer g & 1
+                    const int gp = g - 2;
+                    ok = wait_phase(&bar[B_QEMPTY + qb], (gp >> 1) & 1, abort);
+                    if (!(ok = __all_sync(0xffffffffu, ok))) break;
+                    tc_fence_after();
+                }
+                tmem_st8(tmem + tq(qb) + 8 * cg + lane_off, qp);
+                if (WITH_B) tmem_st8(tmem + tqb(qb) + 8 * cg + lane_off, qbp);
+                tmem_st_wait();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&bar[qfull(qb)]);
+            }
+            if (!ok) break;
+            // every Z of this tile has been read, so GEMM1 is done with X: the next tile's
+            // X goes in now, while the last GEMM2/3 of this one runs
+            const GP1Tile cur = x;
+            if (ti + G < n) {
+                x = gp1_tile(gv, tiles, ti + G, w);
+                load_x(x);
+            }
+            if (cur.nch > 0) {   // GEMM2/3 of the last chunk done: A and B are final
+                const int gl = g - 1;
+                ok = __all_sync(0xffffffffu,
+                                wait_phase(&bar[B_QEMPTY + (gl & 1)], (gl >> 1) & 1, abort));
+                if (!ok) break;
+                tc_fence_after();
+                const TcGView& v = *cur.v;
+                const int64_t base = cur.split * v.R;
+                constexpr int GR = RP / 32;
+#pragma unroll 1
+                for (int u = cg; u < (WITH_B ? 2 : 1) * GR; u += 4) {
+                    const bool isb = u >= GR;
+                    const int gg = isb ? u - GR : u;
+                    uint32_t r32[32];
+                    tmem_ld32(tmem + (isb ? L::TB : L::TA) + lane_off + 32 * gg, r32);
+                    tmem_ld_wait();
+                    float* dst = isb ? v.B : v.A;
+                    if (o < v.O)
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) {
+                            const int64_t r = 32 * gg + i;
+                            if (r < v.R) dst[(base + r) * v.O + o] = __uint_as_float(r32[i]);
+                        }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bar[B_ACCEMPTY]);
+        }
+        if (!(zmin > 0.f)) atomicOr(status, STATUS_NONFINITE);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0 && *abort) atomicOr(status, STATUS_TIMEOUT);
+    if (warp == 0) tmem_dealloc(tmem, L::NCOLS);
 }
 
 // dst[i][j] (leading dimension ld, padded to rows_pad x cols_pad with zeros) =
@@ -611,19 +926,20 @@ int TcBf16::group_operands(const TcGView* gv, const void* tiles, int n, int w, i
 }
 
 int TcBf16::group_pass1(const TcGView* gv, const void* tiles, int n, int w, bool with_b,
-                        int* status, cudaStream_t st) {
+                        int ctas, int* status, cudaStream_t st) {
     if (n <= 0) return DNA_OK;
     const uint32_t smem = tc::P1Layout<64>::TOTAL + 1024;
-    auto k = with_b ? tc::k_tc_gpass1<64, true> : tc::k_tc_gpass1<64, false>;
-    k<<<n, tc::P1_THREADS, smem, st>>>(gv, static_cast<const int4*>(tiles), w, status);
+    auto k = with_b ? tc::k_tc_gpass1p<true> : tc::k_tc_gpass1p<false>;
+    const int grid = std::max(1, std::min(n, ctas));
+    k<<<grid, tc::P1_THREADS, smem, st>>>(gv, static_cast<const int4*>(tiles), n, w, status);
     return after_launch();
 }
 
 int TcBf16::group_prepare() {
     const int s1 = (int)(tc::P1Layout<64>::TOTAL + 1024);
-    if (cudaFuncSetAttribute(tc::k_tc_gpass1<64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(tc::k_tc_gpass1p<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              s1) != cudaSuccess ||
-        cudaFuncSetAttribute(tc::k_tc_gpass1<64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(tc::k_tc_gpass1p<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              s1) != cudaSuccess)
         return DNA_ERR_CUDA;
     return group_prepare_pass2();

@@ -25,7 +25,7 @@ SHAPES = [(64, 128, 8), (700, 300, 16), (150, 900, 32), (333, 129, 64), (90, 517
           (257, 257, 33), (1, 200, 4), (400, 1, 12), (128, 640, 64), (77, 77, 7)]
 
 
-def _group(problems, bf16=False):
+def _group(problems, bf16=False, **opts):
     import torch
 
     import paper_1301_3389_gb300 as dna
@@ -33,7 +33,9 @@ def _group(problems, bf16=False):
     V = [torch.from_numpy(p.V).to(dev) for p in problems]
     W = [torch.from_numpy(p.W).to(dev) for p in problems]
     H = [torch.from_numpy(p.H).to(dev) for p in problems]
-    opts = dna.make_opts(dtype=dna.DNA_BF16) if bf16 else None
+    if bf16:
+        opts["dtype"] = dna.DNA_BF16
+    opts = dna.make_opts(**opts) if opts else None
     g = dna.dna_group_create([p.V.shape[0] for p in problems], [p.V.shape[1] for p in problems],
                              [p.W.shape[1] for p in problems], opts)
     dna.dna_group_set_stream(g)
@@ -280,3 +282,46 @@ def test_group_bf16_fused_rescale_equals_half_steps():
     for (w0, h0), (w1, h1) in zip(*outs):
         np.testing.assert_array_equal(w0, w1)
         np.testing.assert_array_equal(h0, h1)
+
+
+@pytest.mark.parametrize("kind", ["f32", "bf16"])
+def test_group_regularised(kind):
+    """The group with lambda, rho > 0 and non-default eps, alpha (eq. 2, Section 2.3), in both
+    forms: every problem's half-steps against the oracle's from the group's own state, the
+    group's selections replayed at near ties; the element-wise bound of the form, and its
+    Frobenius tolerance (FP32 1e-4, BF16 2e-2)."""
+    import torch
+    probs = _problems(8)[:6]
+    reg = dict(eps=0.05, alpha=1.5, rho=0.2, lam=0.3)
+    tol = BF16_TOL if kind == "bf16" else 1e-4
+    dna, g, V, W, H = _group(probs, bf16=(kind == "bf16"), **reg)
+    try:
+        dna.dna_group_normalize(g, 1)
+        V64 = [p.V.astype(np.float64) for p in probs]
+        for which in (0, 1, 0, 1):
+            torch.cuda.synchronize()
+            before = [(w.double().cpu().numpy(), h.double().cpu().numpy()) for w, h in zip(W, H)]
+            (dna.dna_group_step_H if which == 0 else dna.dna_group_step_W)(g)
+            torch.cuda.synchronize()
+            assert dna.dna_group_get_status(g) == 0
+            for q, p in enumerate(probs):
+                n = p.V.shape[1] if which == 0 else p.V.shape[0]
+                ch = dna.dna_group_get_choice(g, q, which, n)
+                W0, H0 = before[q]
+                if which == 0:
+                    one = o.h_half_step(V64[q], W0, H0, reg["eps"], reg["alpha"], reg["lam"])
+                else:
+                    one = o.w_half_step(V64[q], W0, H0, reg["eps"], reg["alpha"], reg["rho"])
+                m1, _ = replay_choice(one, ch, kind)
+                Wg = W[q].double().cpu().numpy()
+                Hg = H[q].double().cpu().numpy()
+                assert step_elementwise(dataclasses.replace(one, choice=m1), which, W0, H0, Wg, Hg,
+                                        kind, reg["eps"], reg["alpha"],
+                                        reg["rho"] if which == 0 else reg["lam"],
+                                        label=f"group-{kind}-reg") <= 1.0, (q, which)
+                step = o.dna_step_h if which == 0 else o.dna_step_w
+                Wr, Hr, _ = step(V64[q], W0, H0, reg["eps"], reg["alpha"], reg["rho"], reg["lam"],
+                                 choice=m1)
+                assert rel_fro(Wg, Wr) < tol and rel_fro(Hg, Hr) < tol, (q, which)
+    finally:
+        dna.dna_group_destroy(g)

@@ -125,6 +125,13 @@ def test_regularised_and_limits(kind):
     _trajectory(p, kind, 3, eps=0.05, alpha=1.5, rho=0.2, lam=0.3)
 
 
+def test_regularised_large_rank_split():
+    """lambda, rho > 0 and non-default eps, alpha through the split form's rank-512 kernels
+    (R = 300: ratios + contraction pass 1, K-sliced pass 2)."""
+    p = workloads.custom(257, 400, 300, seed=15)
+    _trajectory(p, "f32t", 2, eps=0.05, alpha=1.5, rho=0.2, lam=0.3)
+
+
 def test_costs_match_oracle():
     """Per-column and per-row candidate costs (steps 9, 14, 22, 27) against the oracle."""
     p = workloads.custom(100, 180, 10, seed=9)

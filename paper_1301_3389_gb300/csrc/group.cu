@@ -96,96 +96,133 @@ __global__ void __launch_bounds__(256)
 }
 
 // BF16 form: the candidates (eq. 11, eq. 15 / 17 and the eq. 10 renormalisation, the
-// arithmetic of the single-problem candidates kernels) and their bf16 operand rows
-// [O_pad][64], one warp per tile (problem, 32 columns; blocks cover O_pad, so padding rows
-// are written as zeros).  Each lane owns a column: it walks r in groups of 8, keeps its
-// Newton candidates in registers for the eq. 10 sum (no cross-thread reduction), and writes
-// each group of 8 bf16 values as one 16-byte store.  CTA = 8 warps, each on its own tile.
-__global__ void __launch_bounds__(256)
+// arithmetic of the single-problem register candidates kernel) and their bf16 operand rows
+// [O_pad][64].  A job is one warp on (problem, 32 columns, group g of 8 values of r): lane
+// = column, so every load and store of [R][O] data coalesces, and each thread issues all
+// of a split's loads (with x for the first) before using them.  The
+// jobs of one 32-column tile (ng = a power of two >= ceil(R / 8) warps) sit in one CTA of
+// 8 warps: the eq. 10 sum over r adds the groups' partials in ascending order through
+// shared memory (the order of the single-problem kernel), and the tile's bf16 rows, a
+// contiguous 4 KB per candidate with zeros past r = 8 ng, are staged in shared memory and
+// stored 512 bytes per warp instruction.  Tiles wholly past O (padding up to O_pad) are one
+// job writing zero rows.  Job lists are padded to whole CTAs with empty jobs (prob < 0).
+__global__ void __launch_bounds__(256, 4)
     k_g_candidates_bf(const GProb* __restrict__ P, const TcGView* __restrict__ gv,
-                      const GTile* __restrict__ tl, int n, int w, float eps, float alpha) {
-    const int lane = threadIdx.x;
-    for (int t = blockIdx.x * 8 + threadIdx.y; t < n; t += gridDim.x * 8) {
-        const GTile tt = tl[t];
-        const GProb& p = P[tt.prob];
-        const View& v = p.v[w];
-        const TcGView& g = gv[2 * tt.prob + w];
-        const int64_t R = v.R, O = v.O, o = (int64_t)tt.a * 32 + lane;
-        const bool live = o < O;
-        const int sp1 = p.sp1[w];
-        const float* __restrict__ X = static_cast<const float*>(v.X);
-        glue::bf16* Xmk = static_cast<glue::bf16*>(g.Xmk) + o * 64;
-        glue::bf16* Xdk = static_cast<glue::bf16*>(g.Xdk) + o * 64;
-        float xd[64];
+                      const GTile* __restrict__ jobs, int nblk, int w, float eps, float alpha) {
+    __shared__ float red[8][32];
+    __shared__ uint4 stm[8][33], std_[8][33];   // per warp, per column: 8 bf16 values
+    const int lane = threadIdx.x, wid = threadIdx.y;
+    for (int jb = blockIdx.x; jb < nblk; jb += gridDim.x) {
+        const GTile jt = jobs[jb * 8 + wid];
+        const int ng = jt.pad > 0 ? jt.pad : 1, g = jt.b;
+        const int lead = wid & ~(ng - 1);
+        float xm[8], xd[8];
         float den = 0.f;
+        bool live = false;
+        int64_t o = 0, R = 0, O = 0;
 #pragma unroll
-        for (int rc = 0; rc < 8; ++rc) {
-            // the group's loads first (split partials in ascending split order, then x)
-            float ra[8], rb[8], xv[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) { ra[i] = 0.f; rb[i] = 0.f; xv[i] = 0.f; }
-            if (live && 8 * rc < R) {
-                for (int sp = 0; sp < sp1; ++sp)
+        for (int i = 0; i < 8; ++i) { xm[i] = 0.f; xd[i] = 0.f; }
+        if (jt.prob >= 0) {
+            const GProb& p = P[jt.prob];
+            const View& v = p.v[w];
+            R = v.R;
+            O = v.O;
+            o = (int64_t)jt.a * 32 + lane;
+            live = o < O;
+            const int64_t r0 = 8 * (int64_t)g;
+            if (live && r0 < R) {
+                const int sp1 = p.sp1[w];
+                const float* __restrict__ X = static_cast<const float*>(v.X);
+                const int nr = R - r0 < 8 ? (int)(R - r0) : 8;
+                float xv[8], ra[8], rb[8];
+                {
+                    const float* xp = X + r0 * v.xr + o * v.xo;
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
-                        const int64_t r = 8 * rc + i;
-                        if (r < R) {
-                            ra[i] += p.A[((int64_t)sp * R + r) * O + o];
-                            rb[i] += p.B[((int64_t)sp * R + r) * O + o];
-                        }
+                        xv[i] = i < nr ? *xp : 0.f;
+                        xp += v.xr;
+                        ra[i] = 0.f;
+                        rb[i] = 0.f;
+                    }
+                }
+                const float* Ap = p.A + r0 * O + o;
+                const float* Bp = p.B + r0 * O + o;
+                const int64_t ss = R * O - (int64_t)nr * O;
+                for (int sp = 0; sp < sp1; ++sp) {   // ascending split order
+                    float a0[8], b0[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        a0[i] = i < nr ? *Ap : 0.f;
+                        b0[i] = i < nr ? *Bp : 0.f;
+                        if (i < nr) { Ap += O; Bp += O; }
                     }
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const int64_t r = 8 * rc + i;
-                    if (r < R) xv[i] = X[r * v.xr + o * v.xo];
+                    for (int i = 0; i < 8; ++i) {
+                        ra[i] += a0[i];
+                        rb[i] += b0[i];
+                    }
+                    Ap += ss;
+                    Bp += ss;
                 }
-            }
-            float xm[8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int64_t r = 8 * rc + i;
-                xm[i] = 0.f;
-                xd[8 * rc + i] = 0.f;
-                if (live && r < R) {
+                for (int i = 0; i < 8; ++i) {
+                    const int64_t r = r0 + i;
+                    if (r >= R) continue;
                     const float cr = (float)p.c[r], ic = 1.0f / cr;
                     const float a = ra[i] * ic - 1.0f;   // eq. 7
                     const float b = rb[i] * ic;          // eq. 14
                     const float xr = xv[i];
                     xm[i] = xr * (ra[i] * ic);           // eq. 11
                     float d;
-                    if (a < 0.f) {                    // eq. 15, gain floored at eps
+                    if (a < 0.f) {                       // eq. 15, gain floored at eps
                         const float xb = xr * b;
                         const float gn = simt::dev_div(xb, xb - a);
                         d = xr * (gn > eps ? gn : eps);
-                    } else {                          // eq. 17, step capped at alpha x
+                    } else {                             // eq. 17, step capped at alpha x
                         const float stp = b > 0.f ? simt::dev_div(a, b) : 0.f;
                         const float cap = alpha * xr;
                         d = xr + (stp < cap ? stp : cap);
                     }
                     p.Xmu[r * O + o] = xm[i];
-                    xd[8 * rc + i] = d;
+                    xd[i] = d;
                     den += cr * d;
                 }
             }
-            *reinterpret_cast<uint4*>(Xmk + 8 * rc) =
-                make_uint4(glue::pack2(xm[0], xm[1]), glue::pack2(xm[2], xm[3]),
-                           glue::pack2(xm[4], xm[5]), glue::pack2(xm[6], xm[7]));
         }
-        // eq. 10: column scale s_o / sum_r c_r g_r (1 when that sum is not positive)
-        const float sc = live ? (den > 0.f ? (float)v.vsum[o] / den : 1.0f) : 0.f;
-#pragma unroll
-        for (int rc = 0; rc < 8; ++rc) {
-            float d[8];
+        red[wid][lane] = den;
+        stm[wid][lane] = make_uint4(glue::pack2(xm[0], xm[1]), glue::pack2(xm[2], xm[3]),
+                                    glue::pack2(xm[4], xm[5]), glue::pack2(xm[6], xm[7]));
+        __syncthreads();
+        if (jt.prob >= 0) {
+            // eq. 10: column scale s_o / sum_r c_r g_r (1 when that sum is not positive)
+            float tot = red[lead][lane];
+            for (int k = 1; k < ng; ++k) tot += red[lead + k][lane];
+            const GProb& p = P[jt.prob];
+            const float sc = live ? (tot > 0.f ? (float)p.v[w].vsum[o] / tot : 1.0f) : 0.f;
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-                const int64_t r = 8 * rc + i;
-                d[i] = xd[8 * rc + i] * sc;
-                if (live && r < R) p.Xdna[r * O + o] = d[i];
+                xd[i] *= sc;
+                const int64_t r = 8 * (int64_t)g + i;
+                if (live && r < R) p.Xdna[r * O + o] = xd[i];
             }
-            *reinterpret_cast<uint4*>(Xdk + 8 * rc) =
-                make_uint4(glue::pack2(d[0], d[1]), glue::pack2(d[2], d[3]),
-                           glue::pack2(d[4], d[5]), glue::pack2(d[6], d[7]));
         }
+        std_[wid][lane] = make_uint4(glue::pack2(xd[0], xd[1]), glue::pack2(xd[2], xd[3]),
+                                     glue::pack2(xd[4], xd[5]), glue::pack2(xd[6], xd[7]));
+        __syncthreads();
+        if (jt.prob >= 0) {
+            // the tile's rows: 32 x 8 chunks of 16 bytes per candidate, chunk k of row j from
+            // warp lead + k (zeros for k >= ng); warp g of the tile stores chunks g, g + ng, ..
+            const TcGView& tv = gv[2 * jt.prob + w];
+            uint4* Mk = reinterpret_cast<uint4*>(static_cast<glue::bf16*>(tv.Xmk)) + jt.a * 256;
+            uint4* Dk = reinterpret_cast<uint4*>(static_cast<glue::bf16*>(tv.Xdk)) + jt.a * 256;
+            for (int c = g * 32 + lane; c < 256; c += ng * 32) {
+                const int j = c >> 3, k = c & 7;
+                const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+                Mk[c] = k < ng ? stm[lead + k][j] : z;
+                Dk[c] = k < ng ? std_[lead + k][j] : z;
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -578,9 +615,27 @@ int build_tiles(dna_group* g) {
             t.slots2 = dna::TcBf16::pass2_split_slots(t.O_pad, S, (int)G);
             p.nslot[w] = t.slots2;
             for (int64_t me = 0; me < G; ++me) tq2[w].push_back({q, (int)me, (int)G, 0});
-            for (int64_t by = 0; by < t.O_pad / 32; ++by) tcb[w].push_back({q, (int)by, 0, 0});
+            // candidates: ng warps per 32-column tile (a power of two >= ceil(R / 8)), one
+            // for a tile wholly in the padding past O
+            int ng = 1;
+            while (8 * ng < p.v[w].R) ng *= 2;
+            for (int64_t by = 0; by < t.O_pad / 32; ++by)
+                tcb[w].push_back({q, (int)by, 0, by * 32 < p.v[w].O ? ng : 1});
             for (int64_t b = 0; b < t.O_pad / 64; ++b) ti[w].push_back({q, 0, (int)b, 0});
             for (int64_t b = 0; b < t.S_pad / 64; ++b) ti[w].push_back({q, 1, (int)b, 0});
+        }
+    if (g->tc)
+        for (int w = 0; w < 2; ++w) {
+            // candidate jobs: tiles by warps per tile, widest first, so that every tile's
+            // warps sit in one CTA of 8 at an offset that is a multiple of its width; then
+            // the tile's ng jobs (b = group of r) and empty jobs up to a whole CTA
+            std::stable_sort(tcb[w].begin(), tcb[w].end(),
+                             [](const GTile& a, const GTile& b) { return a.pad > b.pad; });
+            std::vector<GTile> jobs;
+            for (const GTile& x : tcb[w])
+                for (int k = 0; k < x.pad; ++k) jobs.push_back({x.prob, x.a, k, x.pad});
+            while (jobs.size() % 8) jobs.push_back({-1, 0, 0, 1});
+            tcb[w].swap(jobs);
         }
     if (g->tc)
         // longest tiles first (pass 1: rows of s in the tile; pass 2: units of the CTA), so
@@ -700,10 +755,10 @@ int g_half(dna_group* g, int w, bool mu_only, bool ops_ready = false, bool fuse_
         if (!e) e = dna::TcBf16::group_pass1(g->gv, g->tp1[w].d, g->tp1[w].n, w, true,
                                              g->num_sms, g->status, g->gs);
         if (!e && g->cand_bf[w].n) {
-            const int grid = std::max(1, std::min((g->cand_bf[w].n + 7) / 8, 8 * g->num_sms));
+            const int nblk = g->cand_bf[w].n / 8;
+            const int grid = std::max(1, std::min(nblk, 4 * g->num_sms));
             dna::grp::k_g_candidates_bf<<<grid, dim3(32, 8), 0, g->gs>>>(
-                g->dp, g->gv, g->cand_bf[w].d, g->cand_bf[w].n, w, (float)g->o.eps,
-                (float)g->o.alpha);
+                g->dp, g->gv, g->cand_bf[w].d, nblk, w, (float)g->o.eps, (float)g->o.alpha);
             e = after_launch();
         }
         if (!e) e = dna::TcBf16::group_pass2(g->gv, g->tp2[w].d, g->tp2[w].n, w, g->status, g->gs);

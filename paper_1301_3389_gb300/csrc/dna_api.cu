@@ -663,11 +663,11 @@ int step_core(dna_ctx* c, int w, bool mu_only, bool prepared, int stop) {
     }
     int slots = sp2;
     if (stop <= STOP_PASS2) {
-        // many split partials: one streaming pass sums them into split 0 first (the
-        // candidates kernel streams up to 4 itself when the rank allows its register form)
+        // split partials over many columns: one streaming pass sums them into split 0 first
+        // (in the candidates kernel each further split is another round of dependent loads;
+        // the sums are the same, ascending split order either way)
         const int parts = stop == STOP_PASS2 ? 1 : sp1;
-        const bool presum =
-            (int64_t)parts * v.O >= 32768 && (parts > 4 || !S::cand_in_registers(c->R));
+        const bool presum = (int64_t)parts * v.O >= 32768 && parts > 1;
         e = phase(c, DNA_PHASE_CANDIDATES, presum ? 2 : 1, [&] {
             if (presum)
                 if (int r = S::split_sum(A, B, c->R, v.O, parts, st)) return r;
@@ -701,17 +701,22 @@ int step_core(dna_ctx* c, int w, bool mu_only, bool prepared, int stop) {
 
 // Steps 16 / 29 after the new factor and its per-block sums (gpart) are written: f_r = sum
 // over o of the new x(r, o) + (rho | lambda), then the rescale, fused (next) with the
-// preparation of half-step 1 - w.
+// preparation of half-step 1 - w.  That half-step's eq. 7 / 14 denominators are the sums
+// of its Y (this step's X after the rescale) plus the same rho | lambda: sum_o x(r, o) / f_r
+// + reg, formed from f_r's own sum (equal to summing the rescaled factor up to rounding).
+// The sparse form sums the rescaled factor instead (its pass 2 reads the raw sums from
+// gpart).
 template <typename Tp>
 int finish_step(dna_ctx* c, int w, bool next) {
     using S = dna::Simt<Tp>;
     const View v = make_view(c, w == 1);
     cudaStream_t st = c->stream;
     int e = DNA_OK;
+    const bool derive = next && !c->sparse;   // the next denominators from f_r's sums
     // steps 16 / 29: f_r = sum over o of the new x(r, o) + (rho | lambda)
     e = phase(c, DNA_PHASE_SUMS, 1, [&] {
         return S::part_sums(c->gpart, S::glue_parts(v.O), c->R, w ? c->o.lambda : c->o.rho,
-                            c->sig, st);
+                            c->sig, st, derive ? c->c : nullptr);
     });
     if (e) return e;
     if (!next)
@@ -725,9 +730,9 @@ int finish_step(dna_ctx* c, int w, bool next) {
     const OpsOut o = ops_out(c, wn, true);
     e = phase(c, DNA_PHASE_SUMS, 1, [&] {
         return S::scale_ops(t, c->sig, true, o.Xk, o.Yk, o.Ytk, o.Y2tk, o.rp, o.O_pad, o.S_pad,
-                            o.plane, c->gpart, st);
+                            o.plane, derive ? nullptr : c->gpart, st);
     });
-    if (e) return e;
+    if (e || derive) return e;
     return phase(c, DNA_PHASE_SUMS, 1, [&] {
         return S::part_sums(c->gpart, S::glue_parts(t.S), c->R, wn ? c->o.rho : c->o.lambda, c->c,
                             st);

@@ -135,9 +135,10 @@ template <typename Tp> struct Simt {
     static int mu_fused(const View& v, const double* c, const Tp* Apart, int splits,
                         double* fpart, cudaStream_t st);
     // out[r] = sum over k < nparts of part[k * R + r] + reg (fixed order; an exact zero
-    // sum is replaced by 1)
+    // sum is replaced by 1); with `next`, next[r] = (that sum without reg) / out[r] + reg
+    // (guarded the same way)
     static int part_sums(const double* part, int64_t nparts, int64_t R, double reg, double* out,
-                         cudaStream_t st);
+                         cudaStream_t st, double* next = nullptr);
     // For the half-step `t`: when f is given, X(r, o) *= f_r and Y(s, r) /= f_r (xmul) or
     // X /= f_r and Y *= f_r (written back); when Xk is given (float only), the bf16
     // operands of `t` (Y2tk may be null); when cpart is given, cpart[glue_parts(S)][R] =

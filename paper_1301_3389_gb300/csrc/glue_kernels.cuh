@@ -177,10 +177,10 @@ __global__ void __launch_bounds__(1024) k_cand_fused(View v, const double* __res
 // x ceil(R / RS) <= 16 groups of RS consecutive r (threadIdx.y), every thread keeping its RS
 // candidates in registers, so the eq. 10 renormalisation needs one shared-memory
 // reduction and no second pass over r.  The split partials of pass 1 are summed in
-// ascending split order while they stream in (no separate pass over them); all loads of
-// a thread are issued before their results are used.  With BF the grid covers O_pad and
-// the bf16 operand rows [o][rp] are written with 16-byte stores (zeros in the padding).
-// The 32 columns of block bx (the kernel below; the grouped form runs it per problem).
+// ascending split order while they stream in (no separate pass over them).  With BF the grid covers O_pad and the bf16 operand rows
+// [o][rp] are written with zeros in the padding; at RS = 8 they go through shared memory,
+// so that the CTA's rows (32 rp contiguous values per plane) are stored 512 bytes per warp
+// instruction.  The 32 columns of block bx.
 template <typename Tp, bool BF, int RS>
 __device__ __forceinline__ void cand_reg_tile(const View& v, const double* __restrict__ c,
                                               const Tp* __restrict__ Apart,
@@ -190,32 +190,49 @@ __device__ __forceinline__ void cand_reg_tile(const View& v, const double* __res
                                               bf16* __restrict__ Xdk, int64_t rp, int64_t plane,
                                               int64_t bx) {
     static_assert(RS % 8 == 0, "operand rows are written 8 values at a time");
+    constexpr bool STAGE = BF && RS == 8;
     __shared__ Tp red[16][33];
     __shared__ Tp scl[32];
+    // staged bf16 rows: [plane: mu hi, dna hi, mu lo, dna lo][r group][o] (16 bytes each)
+    __shared__ uint4 stg[STAGE ? 4 : 1][STAGE ? 16 : 1][STAGE ? 33 : 1];
     const int64_t R = v.R, O = v.O;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int64_t o = bx * 32 + tx;
     const bool live = o < O;
     const int64_t r0 = (int64_t)ty * RS;
+    const int nr = live && r0 < R ? (int)(R - r0 < RS ? R - r0 : RS) : 0;
     const Tp* __restrict__ X = static_cast<const Tp*>(v.X);
 
     Tp ra[RS], rb[RS], x[RS];
 #pragma unroll
     for (int i = 0; i < RS; ++i) { ra[i] = Tp(0); rb[i] = Tp(0); x[i] = Tp(0); }
-    if (live) {
-#pragma unroll
-        for (int i = 0; i < RS; ++i)
-            if (r0 + i < R) x[i] = X[(r0 + i) * v.xr + o * v.xo];
-#pragma unroll 1
-        for (int sp = 0; sp < splits; ++sp) {
+    if (nr > 0) {
+        {
+            const Tp* xp = X + r0 * v.xr + o * v.xo;
 #pragma unroll
             for (int i = 0; i < RS; ++i) {
-                const int64_t r = r0 + i;
-                if (r < R) {
-                    ra[i] += Apart[((int64_t)sp * R + r) * O + o];
-                    rb[i] += Bpart[((int64_t)sp * R + r) * O + o];
-                }
+                if (i < nr) x[i] = *xp;
+                xp += v.xr;
             }
+        }
+        const Tp* ap = Apart + r0 * O + o;
+        const Tp* bp = Bpart + r0 * O + o;
+        const int64_t ss = R * O;
+#pragma unroll 1
+        for (int sp = 0; sp < splits; ++sp) {
+            Tp a0[RS], b0[RS];
+#pragma unroll
+            for (int i = 0; i < RS; ++i) {
+                a0[i] = i < nr ? ap[i * O] : Tp(0);
+                b0[i] = i < nr ? bp[i * O] : Tp(0);
+            }
+#pragma unroll
+            for (int i = 0; i < RS; ++i) {
+                ra[i] += a0[i];
+                rb[i] += b0[i];
+            }
+            ap += ss;
+            bp += ss;
         }
     }
     Tp den = Tp(0), xd[RS], xm[RS];
@@ -224,7 +241,7 @@ __device__ __forceinline__ void cand_reg_tile(const View& v, const double* __res
         const int64_t r = r0 + i;
         xd[i] = Tp(0);
         xm[i] = Tp(0);
-        if (!live || r >= R) continue;
+        if (i >= nr) continue;
         const Tp cr = (Tp)c[r], ic = Tp(1) / cr;
         const Tp a = ra[i] * ic - Tp(1);   // eq. 7
         const Tp b = rb[i] * ic;           // eq. 14
@@ -254,7 +271,7 @@ __device__ __forceinline__ void cand_reg_tile(const View& v, const double* __res
 #pragma unroll
     for (int i = 0; i < RS; ++i) {
         xd[i] *= sc;
-        if (live && r0 + i < R) Xdna[(r0 + i) * O + o] = xd[i];
+        if (i < nr) Xdna[(r0 + i) * O + o] = xd[i];
     }
     if constexpr (BF) {   // K-major bf16 rows [o][rp], o < O_pad, r < rp (zeros beyond)
         if (r0 < rp) {
@@ -270,12 +287,39 @@ __device__ __forceinline__ void cand_reg_tile(const View& v, const double* __res
                     ml[k] = pack2(m0 - lo_half(mh[k]), m1 - hi_half(mh[k]));   // x - bf16(x)
                     dl[k] = pack2(d0 - lo_half(dh[k]), d1 - hi_half(dh[k]));
                 }
-                const int64_t off = o * rp + r0 + q;
-                *reinterpret_cast<uint4*>(Xmk + off) = make_uint4(mh[0], mh[1], mh[2], mh[3]);
-                *reinterpret_cast<uint4*>(Xdk + off) = make_uint4(dh[0], dh[1], dh[2], dh[3]);
+                if constexpr (STAGE) {
+                    stg[0][ty][tx] = make_uint4(mh[0], mh[1], mh[2], mh[3]);
+                    stg[1][ty][tx] = make_uint4(dh[0], dh[1], dh[2], dh[3]);
+                    stg[2][ty][tx] = make_uint4(ml[0], ml[1], ml[2], ml[3]);
+                    stg[3][ty][tx] = make_uint4(dl[0], dl[1], dl[2], dl[3]);
+                } else {
+                    const int64_t off = o * rp + r0 + q;
+                    *reinterpret_cast<uint4*>(Xmk + off) = make_uint4(mh[0], mh[1], mh[2], mh[3]);
+                    *reinterpret_cast<uint4*>(Xdk + off) = make_uint4(dh[0], dh[1], dh[2], dh[3]);
+                    if (plane) {
+                        *reinterpret_cast<uint4*>(Xmk + plane + off) =
+                            make_uint4(ml[0], ml[1], ml[2], ml[3]);
+                        *reinterpret_cast<uint4*>(Xdk + plane + off) =
+                            make_uint4(dl[0], dl[1], dl[2], dl[3]);
+                    }
+                }
+            }
+        }
+        if constexpr (STAGE) {
+            // the CTA's rows o = 32 bx .. 32 bx + 31 are one run of 32 rp bf16 values per
+            // plane: chunk k (16 bytes) of the run is group k % (rp / 8) of row k / (rp / 8)
+            __syncthreads();
+            const int gpr = (int)(rp / 8), nch = 32 * gpr;
+            const int tid = ty * 32 + tx, nt = 32 * (int)blockDim.y;
+            uint4* M = reinterpret_cast<uint4*>(Xmk + bx * 32 * rp);
+            uint4* D = reinterpret_cast<uint4*>(Xdk + bx * 32 * rp);
+            for (int k = tid; k < nch; k += nt) {
+                const int j = k / gpr, g = k % gpr;
+                M[k] = stg[0][g][j];
+                D[k] = stg[1][g][j];
                 if (plane) {
-                    *reinterpret_cast<uint4*>(Xmk + plane + off) = make_uint4(ml[0], ml[1], ml[2], ml[3]);
-                    *reinterpret_cast<uint4*>(Xdk + plane + off) = make_uint4(dl[0], dl[1], dl[2], dl[3]);
+                    reinterpret_cast<uint4*>(Xmk + plane + bx * 32 * rp)[k] = stg[2][g][j];
+                    reinterpret_cast<uint4*>(Xdk + plane + bx * 32 * rp)[k] = stg[3][g][j];
                 }
             }
         }
@@ -541,69 +585,83 @@ struct OpsArgs {
     int64_t xtiles_o, tiles_r, xtiles;   // X tiles: xtiles_o x tiles_r; then the Y tiles
 };
 
-// Tiles of 32 x 32: blocks [0, xtiles) cover X as (o-tile, r-tile), the rest cover Y as
-// (s-tile, r-tile).  Extents are the padded ones when bf16 operands are written, so the
-// padding of the operand buffers is rewritten as zeros.
-template <typename Tp>
-__global__ void __launch_bounds__(256) k_scale_ops(OpsArgs a) {
-    __shared__ Tp tile[TO][TO + 1];
-    __shared__ Tp fr[TO];
+// Tiles of 32 values of i (o of X, s of Y) x RT values of r: blocks [0, xtiles) cover X as
+// (o-tile, r-tile), the rest cover Y as (s-tile, r-tile).  Every thread issues its RT / 8
+// loads before any store.  Extents are the padded ones when bf16 operands are written, so
+// the padding of the operand buffers is rewritten as zeros.
+template <typename Tp, int RT>
+__global__ void __launch_bounds__(256, 4) k_scale_ops(OpsArgs a) {
+    constexpr int NL = RT / 8;                 // elements per thread
+    __shared__ Tp tile[RT][TO + 1];            // [r][i]
+    __shared__ Tp fr[RT];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
     const bool isx = (int64_t)blockIdx.x < a.xtiles;
     const int64_t b = isx ? (int64_t)blockIdx.x : (int64_t)blockIdx.x - a.xtiles;
     const int64_t it = b / a.tiles_r, rt = b % a.tiles_r;
-    const int64_t r0 = rt * TO, i0 = it * TO;   // i = o (X tiles) or s (Y tiles)
+    const int64_t r0 = rt * RT, i0 = it * TO;   // i = o (X tiles) or s (Y tiles)
     const int64_t n = isx ? a.O : a.S;
-    if (tid < TO) {
-        const int64_t r = r0 + tid;
+    for (int k = tid; k < RT; k += 256) {
+        const int64_t r = r0 + k;
         Tp s = Tp(1);
         if (a.f && r < a.R) {
             const Tp f = (Tp)a.f[r];
             s = (isx == a.xmul) ? f : Tp(1) / f;
         }
-        fr[tid] = s;
+        fr[k] = s;
     }
     __syncthreads();
     Tp* M = static_cast<Tp*>(isx ? a.X : a.Y);
     // element (r, i): X[r * xr + i * xo] or Y[i * ys + r * yr]
     const int64_t sr = isx ? a.xr : a.yr, si = isx ? a.xo : a.ys;
-    if (si == 1) {   // contiguous along i: lanes walk i
-        for (int k = ty; k < TO; k += 8) {
-            const int64_t r = r0 + k, i = i0 + tx;
-            Tp x = Tp(0);
-            if (r < a.R && i < n) {
-                x = M[r * sr + i] * fr[k];
-                if (a.f) M[r * sr + i] = x;
-            }
-            tile[k][tx] = x;   // tile[r][i]
+    Tp x[NL];
+    if (si == 1) {   // contiguous along i: lanes walk i, thread rows walk r
+        const int64_t i = i0 + tx;
+#pragma unroll
+        for (int k = 0; k < NL; ++k) {
+            const int64_t r = r0 + ty + 8 * k;
+            x[k] = (r < a.R && i < n) ? M[r * sr + i] : Tp(0);
         }
-    } else {         // contiguous along r: lanes walk r
-        for (int k = ty; k < TO; k += 8) {
-            const int64_t i = i0 + k, r = r0 + tx;
-            Tp x = Tp(0);
-            if (r < a.R && i < n) {
-                x = M[i * si + r * sr] * fr[tx];
-                if (a.f) M[i * si + r * sr] = x;
-            }
-            tile[tx][k] = x;
+#pragma unroll
+        for (int k = 0; k < NL; ++k) {
+            const int rl = ty + 8 * k;
+            const int64_t r = r0 + rl, i = i0 + tx;
+            x[k] *= fr[rl];
+            if (a.f && r < a.R && i < n) M[r * sr + i] = x[k];
+            tile[rl][tx] = x[k];
+        }
+    } else {         // contiguous along r: lanes walk 32 values of r, thread rows walk i
+#pragma unroll
+        for (int k = 0; k < NL; ++k) {
+            const int il = ty + 8 * (k % 4), rl = tx + 32 * (k / 4);
+            const int64_t i = i0 + il, r = r0 + rl;
+            x[k] = (r < a.R && i < n) ? M[i * si + r * sr] : Tp(0);
+        }
+#pragma unroll
+        for (int k = 0; k < NL; ++k) {
+            const int il = ty + 8 * (k % 4), rl = tx + 32 * (k / 4);
+            const int64_t i = i0 + il, r = r0 + rl;
+            x[k] *= fr[rl];
+            if (a.f && r < a.R && i < n) M[i * si + r * sr] = x[k];
+            tile[rl][il] = x[k];
         }
     }
     __syncthreads();
-    if (!isx && a.cpart && tid < TO && r0 + tid < a.R && i0 < a.S) {
-        Tp s = Tp(0);
+    if (!isx && a.cpart && i0 < a.S)
+        for (int k = tid; k < RT; k += 256)
+            if (r0 + k < a.R) {
+                Tp s = Tp(0);
 #pragma unroll 8
-        for (int k = 0; k < TO; ++k) s += tile[tid][k];
-        a.cpart[it * a.R + r0 + tid] = (double)s;
-    }
+                for (int j = 0; j < TO; ++j) s += tile[k][j];
+                a.cpart[it * a.R + r0 + k] = (double)s;
+            }
     if (a.Xk == nullptr) return;
     if constexpr (sizeof(Tp) == 4) {
-        // bf16 pairs, one 32-bit store per thread (a warp stores two 64-byte runs); the
-        // tile reads tile[2 j][.] / tile[.][2 j] over the lanes are bank-conflict free
-        // rows [i][rp] with r contiguous (Xk of X tiles, Yk of Y tiles): pairs of r
+        // rows [i][rp] with r contiguous (Xk of X tiles, Yk of Y tiles): pairs of r, a warp
+        // storing one row's RT values of r (or two rows' when RT = 32)
         bf16* RM = isx ? a.Xk : a.Yk;
         const int64_t ipad = isx ? a.O_pad : a.S_pad;
-        for (int k = ty; k < TO / 2; k += 8) {
-            const int il = 2 * k + (tx >> 4), rl = 2 * (tx & 15);
+        for (int p = tid; p < TO * RT / 2; p += 256) {
+            const int il = p / (RT / 2), rl = 2 * (p % (RT / 2));
             const int64_t i = i0 + il, r = r0 + rl;
             if (i < ipad && r < a.rp) {   // rp is even, so r + 1 < rp too
                 const float y0 = tile[rl][il], y1 = tile[rl + 1][il];
@@ -616,8 +674,8 @@ __global__ void __launch_bounds__(256) k_scale_ops(OpsArgs a) {
         }
         if (isx) return;
         // Ytk, Y2tk [r][S_pad] with s contiguous: pairs of s (S_pad is a multiple of 64)
-        for (int k = ty; k < TO / 2; k += 8) {
-            const int rl = 2 * k + (tx >> 4), il = 2 * (tx & 15);
+        for (int p = tid; p < RT * TO / 2; p += 256) {
+            const int rl = p / (TO / 2), il = 2 * (p % (TO / 2));
             const int64_t r = r0 + rl, i = i0 + il;
             if (r < a.rp && i < a.S_pad) {
                 const float y0 = tile[rl][il], y1 = tile[rl][il + 1];

@@ -1015,16 +1015,17 @@ __global__ void k_colsum_part(const Tp* __restrict__ M, int64_t n, int64_t R, in
     }
 }
 
-// out[r] = sum over splits of part[split][r] + reg, zero sum guarded.  CTA = 32 values of
-// r (lanes, so loads coalesce) x 32 groups of splits: group g adds splits g, g + 32, ... in
-// order, then the 32 group sums are added in order.
 // out[r] = sum over k of part[k][r] + reg for a few r: one CTA per r, 256 partial sums
-// per thread stride, then a fixed tree (the part_sums of the glue, R small).  A template
+// per thread stride, then a fixed tree (the part_sums of the glue, R small).  With `next`,
+// also next[r] = d_r / out[r] + reg (d_r the sum without reg, an exact zero guarded): the
+// sum over the row of the factor that the step 16 / 29 normalisation divides by out[r],
+// plus reg, which is the eq. 7 / 14 denominator of the following half-step.  A template
 // only so that every translation unit including this header may define it.
 template <int UNUSED = 0>
 __global__ void __launch_bounds__(256) k_colsum_small(const double* __restrict__ part,
                                                       int nsplit, int64_t R, double reg,
-                                                      double* __restrict__ out, bool guard) {
+                                                      double* __restrict__ out, bool guard,
+                                                      double* __restrict__ next = nullptr) {
     __shared__ double red[256];
     const int64_t r = blockIdx.x;
     double t = 0.0;
@@ -1035,13 +1036,21 @@ __global__ void __launch_bounds__(256) k_colsum_small(const double* __restrict__
         if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
         __syncthreads();
     }
-    if (threadIdx.x == 0) out[r] = nonzero_sum(red[0] + reg, guard);
+    if (threadIdx.x == 0) {
+        const double f = nonzero_sum(red[0] + reg, guard);
+        out[r] = f;
+        if (next) next[r] = nonzero_sum(red[0] / f + reg, true);
+    }
 }
 
+// out[r] (and next[r]) as k_colsum_small for many r.  CTA = 32 values of r (lanes, so loads
+// coalesce) x 32 groups of splits: group g adds splits g, g + 32, ... in order, then the 32
+// group sums are added in order.
 template <int UNUSED = 0>
 __global__ void __launch_bounds__(1024) k_colsum_final(const double* __restrict__ part,
                                                        int nsplit, int64_t R, double reg,
-                                                       double* __restrict__ out, bool guard) {
+                                                       double* __restrict__ out, bool guard,
+                                                       double* __restrict__ next = nullptr) {
     __shared__ double red[32][33];
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int64_t r = (int64_t)blockIdx.x * 32 + tx;
@@ -1055,7 +1064,9 @@ __global__ void __launch_bounds__(1024) k_colsum_final(const double* __restrict_
     if (ty == 0 && r < R) {
         double tot = 0.0;
         for (int g = 0; g < 32; ++g) tot += red[g][tx];
-        out[r] = nonzero_sum(tot + reg, guard);
+        const double f = nonzero_sum(tot + reg, guard);
+        out[r] = f;
+        if (next) next[r] = nonzero_sum(tot / f + reg, true);
     }
 }
 

@@ -395,12 +395,13 @@ int Simt<Tp>::mu_fused(const View& v, const double* c, const Tp* A, int splits, 
 
 template <typename Tp>
 int Simt<Tp>::part_sums(const double* part, int64_t nparts, int64_t R, double reg, double* out,
-                        cudaStream_t st) {
+                        cudaStream_t st, double* next) {
     if (R <= 1024)   // a CTA per r: latency of one load round and a tree, not of nparts / 32
-        simt::k_colsum_small<0><<<(unsigned)R, 256, 0, st>>>(part, (int)nparts, R, reg, out, true);
+        simt::k_colsum_small<0><<<(unsigned)R, 256, 0, st>>>(part, (int)nparts, R, reg, out, true,
+                                                             next);
     else
         simt::k_colsum_final<<<(unsigned)((R + 31) / 32), dim3(32, 32), 0, st>>>(
-            part, (int)nparts, R, reg, out, true);
+            part, (int)nparts, R, reg, out, true, next);
     return simt::launch_status();
 }
 
@@ -419,14 +420,20 @@ int Simt<Tp>::scale_ops(const View& t, const double* f, bool xmul, void* Xk, voi
     a.Ytk = static_cast<glue::bf16*>(Ytk); a.Y2tk = static_cast<glue::bf16*>(Y2tk);
     a.rp = rp; a.O_pad = O_pad; a.S_pad = S_pad; a.plane = bf ? plane : 0; a.cpart = cpart;
     const int64_t rcov = bf ? rp : t.R, ocov = bf ? O_pad : t.O, scov = bf ? S_pad : t.S;
-    a.tiles_r = glue_parts(rcov);
+    const int rt = rcov <= 32 ? 32 : rcov <= 64 ? 64 : 128;   // values of r per tile
+    a.tiles_r = (rcov + rt - 1) / rt;
     // without scaling and operands the X tiles have nothing to do
     a.xtiles_o = (f || bf) ? glue_parts(ocov) : 0;
     a.xtiles = a.xtiles_o * a.tiles_r;
     const int64_t ytiles = (f || bf || cpart) ? glue_parts(scov) * a.tiles_r : 0;
     const int64_t blocks = a.xtiles + ytiles;
     if (blocks == 0) return DNA_OK;
-    glue::k_scale_ops<Tp><<<(unsigned)blocks, dim3(32, 8), 0, st>>>(a);
+    if (rt == 32)
+        glue::k_scale_ops<Tp, 32><<<(unsigned)blocks, dim3(32, 8), 0, st>>>(a);
+    else if (rt == 64)
+        glue::k_scale_ops<Tp, 64><<<(unsigned)blocks, dim3(32, 8), 0, st>>>(a);
+    else
+        glue::k_scale_ops<Tp, 128><<<(unsigned)blocks, dim3(32, 8), 0, st>>>(a);
     return simt::launch_status();
 }
 

@@ -61,7 +61,10 @@ def test_plain_small_mu_iterations(kind):
 @pytest.mark.parametrize("kind", ["f32", "f32t", "f64"])
 def test_mu_iterate_matches_oracle(kind):
     """mu_iterate (MU iterations with each half-step preparing the next) against the oracle's
-    MU (eq. 11 then steps 16 / 29), and bit-identical to the same iterations by mu_step."""
+    MU (eq. 11 then steps 16 / 29), and against the same iterations by mu_step.  Chained
+    half-steps take the next eq. 7 / 14 denominators from the step 16 / 29 sums (the sum of a
+    rescaled row is its old sum over the normaliser) instead of summing the rescaled factor
+    again, so the two agree to rounding: 1e-6 (FP32) or 1e-13 (FP64) relative."""
     p = workloads.custom(150, 333, 12, seed=31)
     V = p.V.astype(np.float64)
     W, H = o.normalize_w_columns(p.W, p.H)
@@ -81,8 +84,8 @@ def test_mu_iterate_matches_oracle(kind):
     Wg, Hg = outs[0]
     assert rel_fro(Wg, W) < TOL[kind] and rel_fro(Hg, H) < TOL[kind]
     assert rel_elem(Wg, W, "mu W") < ELEM_TOL[kind] and rel_elem(Hg, H, "mu H") < ELEM_TOL[kind]
-    np.testing.assert_array_equal(outs[0][0], outs[1][0])
-    np.testing.assert_array_equal(outs[0][1], outs[1][1])
+    same = 1e-13 if kind == "f64" else 1e-6
+    assert rel_fro(outs[0][0], outs[1][0]) < same and rel_fro(outs[0][1], outs[1][1]) < same
 
 
 @pytest.mark.parametrize("kind", ["f32", "f32t", "f64"])

@@ -233,7 +233,10 @@ void plan_all(dna_ctx* c) {
             // cost slots (one per column group of the epilogue warps)
             if (balanced_pass2(c))
                 c->tsp2[w] = dna::TcBf16::pass2_split_slots(c->pad_o[w], Sdim, c->num_sms);
-            else
+            else if (!c->split && c->rp == 512) {   // Y-resident pass 2: a slot per s-block
+                c->tsp2[w] = (int)((Sdim + SPLIT_CHUNK - 1) / SPLIT_CHUNK);
+                c->tper2[w] = SPLIT_CHUNK;
+            } else
                 c->tsp2[w] *= 4;
         }
     }

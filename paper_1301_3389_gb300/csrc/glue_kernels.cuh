@@ -21,7 +21,7 @@ namespace glue {
 using bf16 = __nv_bfloat16;
 constexpr int TO = 32;   // o (or s) per tile
 constexpr int TY = 32;   // r groups per CTA (threadIdx.y): 1024 threads
-constexpr int UNR = 4;   // r values per thread whose loads are issued together
+constexpr int UNR = 8;   // r values per thread whose loads are issued together
 static_assert(TY == TO, "k_cand_fused gives each r group one column of the tile");
 
 __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
@@ -71,12 +71,12 @@ __global__ void __launch_bounds__(1024) k_cand_fused(View v, const double* __res
         ics[r] = Tp(1) / (Tp)c[r];
     }
     if (v.xo == 1) {   // rows of X contiguous along o
-#pragma unroll 4
+#pragma unroll 8
         for (int64_t r = ty; r < R; r += TY) xs[r * (TO + 1) + tx] = live ? X[r * v.xr + o] : Tp(0);
     } else {           // columns of X contiguous along r: lanes walk r
         const int i = ty;   // TY == TO: one column per r group
         const int64_t oi = o0 + i;
-#pragma unroll 4
+#pragma unroll 8
         for (int64_t r = tx; r < R; r += 32)
             xs[r * (TO + 1) + i] = oi < O ? X[r * v.xr + oi * v.xo] : Tp(0);
     }
@@ -417,7 +417,8 @@ __global__ void __launch_bounds__(256) k_select_fused(View v, const Tp* __restri
         const int per = (splits + 7) / 8, sp0 = ty * per, sp1 = min(splits, sp0 + per);
         double dm = 0.0, dd = 0.0;
         if (live)
-            for (int sp = sp0; sp < sp1; ++sp) {
+#pragma unroll 8
+            for (int sp = sp0; sp < sp1; ++sp) {   // loads of eight slots in flight
                 dm += dpart[((int64_t)sp * 2 + 0) * O + o];
                 dd += dpart[((int64_t)sp * 2 + 1) * O + o];
             }

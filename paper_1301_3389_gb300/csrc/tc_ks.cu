@@ -1,5 +1,6 @@
-// tcgen05 pass 2 of the BF16 form at padded rank RP = 512 (Algorithm 1 steps 6-9 and
-// 12-14; pass 1 at these ranks is in tc_mat.cu), and the tile walk it shares.
+// tcgen05 pass 2 at padded rank RP = 512 (Algorithm 1 steps 6-9 and 12-14; pass 1 at these
+// ranks is in tc_mat.cu): the K-sliced kernel of the split FP32 form (RP 256, 512) and the
+// Y-resident kernel of the BF16 form, and the tile walk they share.
 #include <algorithm>
 #include <cfloat>
 #include <type_traits>
@@ -320,6 +321,265 @@ int launch_pass2_kt(const P2Args& a, const TcMaps& m, int64_t O_pad, int splits,
     return after_launch();
 }
 
+
+// ---------------------------------------------------------------- pass 2, BF16, RP = 512
+// Candidate costs with Y resident: a CTA walks units (s-block of 128 values of s, o-block),
+// s-block-major, holding the s-block's Y ([128 s][512 r], 128 KB in eight 64-wide K-slices)
+// in shared memory while the two candidates' K-slices ([128 o][64 r] each) stream through
+// a ring of three stages.  Per unit only the candidates come in (256 KB against 384 KB when
+// Y streams too), which is what bounds this pass: the copy rate into the SM.  Z_mu and
+// Z_dna of a unit take 256 tensor-memory columns; two units are in flight.  Each of the 16
+// epilogue warps sums d' = sum_s (z - v log z) (v > 0; z where v = 0) over 32 values of s
+// for its 32 columns o in float32; the four partials of a column meet in tensor memory
+// (each warp stores its pair into the first two Z columns it has read), and the warp with
+// the first 32 values of s adds them in order in float64, so each (s-block, column) cost
+// slot has one writer: dpart[sb][2][O].
+namespace ks {
+struct LayoutY {
+    static constexpr int KS = 8;                        // 64-wide K-slices of r
+    static constexpr int KST = 3;
+    static constexpr uint32_t X_SLICE = OBLK * 64 * 2;  // [128 o][64 r]
+    static constexpr uint32_t Y_SLICE = SC * 64 * 2;    // [128 s][64 r]
+    static constexpr uint32_t K_STAGE = 2 * X_SLICE;    // X_mu, X_dna
+    static constexpr uint32_t YR = 0;
+    static constexpr uint32_t XR = YR + KS * Y_SLICE;
+    static constexpr uint32_t BAR = XR + KST * K_STAGE;
+    static constexpr uint32_t TOTAL = BAR + 256;
+    static constexpr uint32_t NCOLS = 512;              // two (Z_mu, Z_dna) buffers
+    static_assert(K_STAGE % 1024 == 0 && XR % 1024 == 0, "alignment");
+    static_assert(TOTAL + 1024 <= 232448, "shared memory budget");
+};
+enum { Y_KFULL = 0, Y_KEMPTY = 3, Y_ZFULL = 6, Y_ZEMPTY = 8, Y_YFULL = 10, Y_YEMPTY = 11,
+       Y_DRAIN = 12, Y_COUNT = 13 };
+}  // namespace ks
+
+__global__ void __launch_bounds__(ks::P2K_THREADS, 1)
+    k_tc_pass2_yr(P2Args a, int nob, int nunits, const __grid_constant__ CUtensorMap tmXm,
+                  const __grid_constant__ CUtensorMap tmXd, const __grid_constant__ CUtensorMap tmY) {
+    using L = ks::LayoutY;
+    using namespace ks;
+    constexpr int KST = L::KST, KS = L::KS;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* sm = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const uint32_t sbase = smem_u32(sm);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + L::BAR);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L::BAR + Y_COUNT * 8);
+    volatile int* abort = reinterpret_cast<volatile int*>(sm + L::BAR + Y_COUNT * 8 + 8);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int u_begin = (int)((int64_t)blockIdx.x * nunits / gridDim.x);
+    const int u_end = (int)((int64_t)(blockIdx.x + 1) * nunits / gridDim.x);
+    const int nloc = u_end - u_begin;
+
+    if (warp == 0) { tmem_alloc(tslot, L::NCOLS); tmem_relinquish(); }
+    if (tid == W_PRODUCER * 32) {
+        for (int i = 0; i < KST; ++i) {
+            mbar_init(&bar[Y_KFULL + i], 1);
+            mbar_init(&bar[Y_KEMPTY + i], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&bar[Y_ZFULL + b], 1);
+            mbar_init(&bar[Y_ZEMPTY + b], W_EPI);
+        }
+        mbar_init(&bar[Y_YFULL], 1);
+        mbar_init(&bar[Y_YEMPTY], 1);
+        mbar_init(&bar[Y_DRAIN], 1);
+        *abort = 0;
+        fence_mbar_init();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    if (warp == W_PRODUCER) {
+        if (lane == 0 && nloc > 0) {
+            tma_prefetch_desc(&tmXm); tma_prefetch_desc(&tmXd); tma_prefetch_desc(&tmY);
+            bool ok = true;
+            int j = 0, yl = 0, prev = -1;
+            for (int m = 0; ok && m < nloc; ++m) {
+                const int u = u_begin + m, sb = u / nob, ob = u % nob;
+                if (sb != prev) {   // the s-block's Y, once every MMA on the previous one is done
+                    if (yl > 0 && !(ok = wait_phase(&bar[Y_YEMPTY], (yl - 1) & 1, abort))) break;
+                    mbar_arrive_expect_tx(&bar[Y_YFULL], KS * L::Y_SLICE);
+                    const int32_t s0 = 128 * sb;
+                    for (int k = 0; k < KS; ++k) {
+                        const uint32_t d = sbase + L::YR + k * L::Y_SLICE;
+                        tma_load_2d(d, &tmY, 64 * k, s0, &bar[Y_YFULL]);
+                        tma_load_2d(d + SCH * 128, &tmY, 64 * k, s0 + SCH, &bar[Y_YFULL]);
+                    }
+                    ++yl;
+                    prev = sb;
+                }
+                for (int k = 0; k < KS; ++k, ++j) {
+                    const int st = j % KST;
+                    if (!(ok = wait_phase(&bar[Y_KEMPTY + st], ((j / KST) & 1) ^ 1, abort))) break;
+                    const uint32_t d = sbase + L::XR + st * L::K_STAGE;
+                    mbar_arrive_expect_tx(&bar[Y_KFULL + st], L::K_STAGE);
+                    tma_load_2d(d, &tmXm, 64 * k, OBLK * ob, &bar[Y_KFULL + st]);
+                    tma_load_2d(d + L::X_SLICE, &tmXd, 64 * k, OBLK * ob, &bar[Y_KFULL + st]);
+                }
+            }
+            if (*abort) {   // let the copies already issued land before the CTA exits
+                for (int k = max(0, j - KST); k < j; ++k)
+                    drain_phase(&bar[Y_KFULL + k % KST], (k / KST) & 1);
+                if (yl > 0) drain_phase(&bar[Y_YFULL], (yl - 1) & 1);
+            }
+        }
+    } else if (warp == W_EPI + 1) {
+        // Z_mu(m), Z_dna(m) into buffer m & 1, K-slice by K-slice against the resident Y
+        if (lane == 0) {
+            bool ok = true;
+            int j = 0, yl = 0, prev = -1;
+            constexpr uint32_t idesc = idesc_bf16(OBLK, SC);
+            for (int m = 0; ok && m < nloc; ++m) {
+                const int sb = (u_begin + m) / nob, b = m & 1;
+                if (sb != prev) {
+                    if (!(ok = wait_phase(&bar[Y_YFULL], yl & 1, abort))) break;
+                    ++yl;
+                    prev = sb;
+                }
+                // the epilogue has read unit m - 2 out of this buffer
+                if (m >= 2 && !(ok = wait_phase(&bar[Y_ZEMPTY + b], ((m - 2) >> 1) & 1, abort)))
+                    break;
+                tc_fence_after();
+                const uint32_t zm = tmem + b * 2 * SC, zd = zm + SC;
+#pragma unroll 1
+                for (int k = 0; k < KS; ++k, ++j) {
+                    if (!(ok = wait_phase(&bar[Y_KFULL + j % KST], (j / KST) & 1, abort))) break;
+                    const uint32_t xs = sbase + L::XR + (j % KST) * L::K_STAGE;
+                    const uint32_t ys = sbase + L::YR + k * L::Y_SLICE;
+#pragma unroll
+                    for (int kq = 0; kq < 4; ++kq) {
+                        const uint64_t yd = desc_sw128(ys + 32u * kq);
+                        const uint32_t acc = (k > 0 || kq > 0) ? 1u : 0u;
+                        mma_bf16(zm, desc_sw128(xs + 32u * kq), yd, idesc, acc);
+                        mma_bf16(zd, desc_sw128(xs + L::X_SLICE + 32u * kq), yd, idesc, acc);
+                    }
+                    mma_commit(&bar[Y_KEMPTY + j % KST]);
+                }
+                if (!ok) break;
+                mma_commit(&bar[Y_ZFULL + b]);
+                const int nsb = m + 1 < nloc ? (u_begin + m + 1) / nob : -1;
+                if (nsb != sb) mma_commit(&bar[Y_YEMPTY]);   // Y free once these MMAs finish
+            }
+            if (!ok) {
+                mma_commit(&bar[Y_DRAIN]);
+                drain_phase(&bar[Y_DRAIN], 0);
+            }
+        }
+    } else if (warp < W_EPI) {
+        // epilogue warp: lanes o = o0 + 32 qd + lane, values s = 32 cg .. 32 cg + 31 of the
+        // unit's s-block, in two halves of 16
+        const int qd = warp & 3, cg = warp >> 2;
+        const int row = 32 * qd + lane;
+        const uint32_t lane_off = (uint32_t)(32 * qd) << 16;
+        auto v_src = [&](int m, int h, const float*& p, int& n) {
+            const int u = u_begin + m;
+            const int64_t o = (int64_t)(u % nob) * OBLK + row;
+            const int64_t s0 = (int64_t)(u / nob) * SC + 32 * cg + 16 * h;
+            const int64_t left = a.S - s0;
+            p = a.V + s0 * a.vs + o;
+            n = o < a.O ? (left < 16 ? (left > 0 ? (int)left : 0) : 16) : 0;
+        };
+        float vn[16];   // v of the half being processed, then of the next one
+        if (nloc > 0) {
+            const float* p;
+            int n;
+            v_src(0, 0, p, n);
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) vn[jj] = jj < n ? __ldg(p + jj * a.vs) : 0.f;
+        }
+        bool bad = false;
+        for (int m = 0; m < nloc; ++m) {
+            const int b = m & 1;
+            bool ok = wait_phase(&bar[Y_ZFULL + b], (m >> 1) & 1, abort);
+            ok = __all_sync(0xffffffffu, ok);   // keep the warp converged
+            tc_fence_after();
+            const uint32_t zbase = tmem + b * 2 * SC + lane_off;
+            float run_m = 0.f, run_d = 0.f;
+#pragma unroll 1
+            for (int h = 0; ok && h < 2; ++h) {
+                const uint32_t col = zbase + 32 * cg + 16 * h;
+                uint32_t zm[16], zd[16];
+                tmem_ld16(col, zm);
+                tmem_ld16(col + SC, zd);
+                const float* pn = a.V;   // the next half's v
+                int nn = 0;
+                if (h == 0)
+                    v_src(m, 1, pn, nn);
+                else if (m + 1 < nloc)
+                    v_src(m + 1, 0, pn, nn);
+                tmem_ld_wait();
+#pragma unroll
+                for (int jj = 0; jj < 16; ++jj) {
+                    const float v = vn[jj];
+                    vn[jj] = jj < nn ? __ldg(pn + jj * a.vs) : 0.f;
+                    const float z1 = __uint_as_float(zm[jj]), z2 = __uint_as_float(zd[jj]);
+                    const bool pos = v > 0.f;
+                    bad |= pos && !(z1 > 0.f && z2 > 0.f);
+                    run_m += pos ? z1 - v * __logf(z1) : z1;
+                    run_d += pos ? z2 - v * __logf(z2) : z2;
+                }
+            }
+            // the four partials of each column meet in the first two columns each warp read;
+            // every epilogue warp reaches the barrier of every unit, and all of them leave
+            // together if any one gave up waiting
+            if (ok) {
+                tmem_st2(zbase + 32 * cg, __float_as_uint(run_m), __float_as_uint(run_d));
+                tmem_st_wait();
+            }
+            tc_fence_before();
+            const bool fail = named_any(1, 32 * W_EPI, !ok);
+            tc_fence_after();
+            if (fail) break;
+            if (cg == 0) {
+                uint32_t pm[4], pd[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) tmem_ld2(zbase + 32 * k, pm[k], pd[k]);
+                tmem_ld_wait();
+                double acc_m = 0.0, acc_d = 0.0;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    acc_m += (double)__uint_as_float(pm[k]);
+                    acc_d += (double)__uint_as_float(pd[k]);
+                }
+                const int u = u_begin + m;
+                const int64_t o = (int64_t)(u % nob) * OBLK + row, sb = u / nob;
+                if (o < a.O) {
+                    a.dpart[(sb * 2 + 0) * a.O + o] = acc_m;
+                    a.dpart[(sb * 2 + 1) * a.O + o] = acc_d;
+                }
+            }
+            // the unit is read: buffer free for unit m + 2
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bar[Y_ZEMPTY + b]);
+        }
+        if (bad) atomicOr(a.status, STATUS_NONFINITE);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0 && *abort) atomicOr(a.status, STATUS_TIMEOUT);
+    if (warp == 0) tmem_dealloc(tmem, L::NCOLS);
+}
+
+int launch_pass2_yr(const P2Args& a, const TcMaps& m, int64_t O_pad, int ctas, cudaStream_t st) {
+    const uint32_t smem = ks::LayoutY::TOTAL + 1024;
+    if (cudaFuncSetAttribute(k_tc_pass2_yr, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return DNA_ERR_CUDA;
+    const int nob = (int)(O_pad / OBLK);
+    const int64_t nsb = (a.S + ks::SC - 1) / ks::SC;
+    const int64_t nunits = nsb * nob;
+    if (nunits == 0) return DNA_OK;
+    if (nunits > INT32_MAX) return DNA_ERR_ARG;
+    const int grid = (int)std::min<int64_t>(ctas > 0 ? ctas : nunits, nunits);
+    k_tc_pass2_yr<<<grid, ks::P2K_THREADS, smem, st>>>(a, nob, (int)nunits, m.xm, m.xd, m.y);
+    return after_launch();
+}
+
 }  // namespace tc
 
 int TcBf16::pass2_large(const TcOperands& op, const TcMaps& maps, double* dpart, int slots,
@@ -328,6 +588,11 @@ int TcBf16::pass2_large(const TcOperands& op, const TcMaps& maps, double* dpart,
     a.S = op.S; a.O = op.O; a.R = op.R; a.s_per = s_per;
     a.dpart = dpart; a.status = status;
     a.V = op.V; a.vs = op.vs; a.Xm = op.Xmk; a.Xd = op.Xdk; a.rp = rank_pad(op.R);
+    if (!op.plane && a.rp == 512) {   // BF16: Y resident, one cost slot per 128 values of s
+        if (s_per != tc::ks::SC || slots != (op.S + tc::ks::SC - 1) / tc::ks::SC)
+            return DNA_ERR_ARG;
+        return tc::launch_pass2_yr(a, maps, op.O_pad, op.ctas, st);
+    }
     if (s_per % tc::ks::SC != 0 || slots % 4 != 0) return DNA_ERR_ARG;
     const int splits = slots / 4;
     if (splits != (int)((op.S + s_per - 1) / s_per)) return DNA_ERR_ARG;
@@ -336,7 +601,6 @@ int TcBf16::pass2_large(const TcOperands& op, const TcMaps& maps, double* dpart,
         if (a.rp == 512) return tc::launch_pass2_kt<512, true>(a, maps, op.O_pad, splits, op.ctas, st);
         return DNA_ERR_UNSUPPORTED;
     }
-    if (a.rp == 512) return tc::launch_pass2_kt<512, false>(a, maps, op.O_pad, splits, op.ctas, st);
     return DNA_ERR_UNSUPPORTED;
 }
 

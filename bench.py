@@ -869,7 +869,8 @@ def measure_batched(dna, torch, probs, steps, warmup, peaks, bf16=False):
         torch.cuda.synchronize()
         ms = ev0.elapsed_time(ev1)
         kl1 = dna.dna_group_kl(g, len(probs))
-        launches = dna.dna_group_launches_per_iteration(g) * steps
+        # BF16: plus the first H half-step's operands, written once per dna_group_iterate call
+        launches = dna.dna_group_launches_per_iteration(g) * steps + (1 if bf16 else 0)
     finally:
         dna.dna_group_destroy(g)
     nt = sum(s[0] * s[1] for s in shapes)

@@ -307,7 +307,9 @@ int dna_group_step_H(dna_group* g);
 int dna_group_step_W(dna_group* g);
 
 /* iters DNA iterations of every problem; with dna_group_use_graph(g, 1) the first call
- * captures one iteration as a CUDA graph and every iteration replays it. */
+ * captures one iteration as a CUDA graph and every iteration replays it.  BF16 form: each
+ * half-step's rescale (steps 16 / 29) also writes the bf16 operands of the half-step after
+ * it, and each call first writes those of its first H half-step (one launch). */
 int dna_group_iterate(dna_group* g, int iters);
 int dna_group_use_graph(dna_group* g, int enable);
 
@@ -335,7 +337,7 @@ int dna_group_get_status(dna_group* g);
 int dna_group_get_choice(dna_group* g, int q, int which, uint8_t* out, int64_t len);
 
 /* Kernel launches of one grouped iteration (both half-steps, as dna_group_iterate runs
- * them). */
+ * them; in the BF16 form not counting the one operand launch per dna_group_iterate call). */
 int64_t dna_group_launches_per_iteration(dna_group* g);
 
 /* Release the group and its workspace. */

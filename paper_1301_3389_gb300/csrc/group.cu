@@ -793,6 +793,22 @@ int g_iteration(dna_group* g) {
     return e ? e : g_half(g, 1, false, true, false);
 }
 
+// One iteration of dna_group_iterate.  BF16 form: the H half-step's operands were written
+// by the previous iteration's W rescale (or by g_prepare_h before the first), and the W
+// rescale writes the next H half-step's; FP32: g_iteration.
+int g_iteration_chained(dna_group* g) {
+    if (!g->tc) return g_iteration(g);
+    int e = g_half(g, 0, false, true, true);
+    return e ? e : g_half(g, 1, false, true, true);
+}
+
+// The H half-step's bf16 operands from the current W and H (BF16 form).
+int g_prepare_h(dna_group* g) {
+    if (!g->tc || !g->ops_in[0].n) return DNA_OK;
+    return dna::TcBf16::group_operands(g->gv, g->ops_in[0].d, g->ops_in[0].n, 0,
+                                       8 * g->num_sms, g->gs);
+}
+
 struct Handoff {   // order the group's private stream after, and before, the caller's
     dna_group* g;
     int err = DNA_OK;
@@ -1053,9 +1069,11 @@ int dna_group_iterate(dna_group* g, int iters) {
     if (!g || !g->bound || iters < 0) return DNA_ERR_ARG;
     Handoff h(g);
     if (h.err) return h.err;
+    if (iters == 0) return DNA_OK;
+    if (int e = g_prepare_h(g)) return e;
     if (!g->use_graph) {
         for (int i = 0; i < iters; ++i)
-            if (int e = g_iteration(g)) return e;
+            if (int e = g_iteration_chained(g)) return e;
         return DNA_OK;
     }
     if (!g->gexec) {  // capture one iteration once; parameters are fixed after bind
@@ -1063,7 +1081,7 @@ int dna_group_iterate(dna_group* g, int iters) {
         if (cudaStreamBeginCapture(g->gs, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
             return DNA_ERR_CUDA;
         const int64_t before = dna::launch_count();
-        const int e = g_iteration(g);
+        const int e = g_iteration_chained(g);
         const cudaError_t ce = cudaStreamEndCapture(g->gs, &graph);
         if (e || ce != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);
@@ -1197,9 +1215,9 @@ int64_t dna_group_launches_per_iteration(dna_group* g) {
     int64_t n = 0;
     for (int w = 0; w < 2; ++w) {
         n += 5;  // sums, candidates, select, normaliser sums, rescale
-        if (g->tc)   // pass 1, pass 2 and, for the H half-step only, the operands (the W
-                     // half-step's come from the H half-step's rescale)
-            n += (w == 0 && g->ops_in[w].n > 0) + (g->tp1[w].n > 0) + (g->tp2[w].n > 0);
+        if (g->tc)   // pass 1 and pass 2 (each half-step's operands come from the other's
+                     // rescale; dna_group_iterate writes the first H operands once per call)
+            n += (g->tp1[w].n > 0) + (g->tp2[w].n > 0);
         else
             for (int k = 0; k < dna::grp::NCLASS; ++k)
                 n += (g->p1[w][k].n > 0) + (g->p2[w][k].n > 0);

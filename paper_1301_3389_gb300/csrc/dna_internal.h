@@ -201,6 +201,7 @@ struct TcOperands {
     void* Qbg;
     int64_t ldq;
     int64_t qplane;
+    int64_t ldt;   // row stride of Ytk, Y2tk in elements (0: S_pad)
 };
 
 // TMA descriptors of one half-step view (built once per bound problem).
@@ -235,6 +236,7 @@ struct alignas(64) TcGView {
     int64_t s_per1;                 // rows of s per pass-1 split (a multiple of 64)
     int64_t nch2, U2;               // pass 2: chunks of 128 per o-block, (o-block, chunk) units
     int slots2;                     // pass-2 cost slots per column
+    int64_t ldt;                    // row stride of Ytk, Y2tk (the same for both views)
 };
 
 struct TcBf16 {

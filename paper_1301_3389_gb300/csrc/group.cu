@@ -104,8 +104,9 @@ __global__ void __launch_bounds__(256)
 // 8 warps: the eq. 10 sum over r adds the groups' partials in ascending order through
 // shared memory (the order of the single-problem kernel), and the tile's bf16 rows, a
 // contiguous 4 KB per candidate with zeros past r = 8 ng, are staged in shared memory and
-// stored 512 bytes per warp instruction.  Tiles wholly past O (padding up to O_pad) are one
-// job writing zero rows.  Job lists are padded to whole CTAs with empty jobs (prob < 0).
+// stored 512 bytes per warp instruction (values r >= R stay as the zeros the buffers were
+// created with).  Tiles wholly past O (padding up to O_pad) are one job writing zero rows.
+// Job lists are padded to whole CTAs with empty jobs (prob < 0).
 __global__ void __launch_bounds__(256, 4)
     k_g_candidates_bf(const GProb* __restrict__ P, const TcGView* __restrict__ gv,
                       const GTile* __restrict__ jobs, int nblk, int w, float eps, float alpha) {
@@ -215,8 +216,10 @@ __global__ void __launch_bounds__(256, 4)
             const TcGView& tv = gv[2 * jt.prob + w];
             uint4* Mk = reinterpret_cast<uint4*>(static_cast<glue::bf16*>(tv.Xmk)) + jt.a * 256;
             uint4* Dk = reinterpret_cast<uint4*>(static_cast<glue::bf16*>(tv.Xdk)) + jt.a * 256;
+            const int nk = (int)((tv.R + 7) / 8);   // chunks past r = R stay zero
             for (int c = g * 32 + lane; c < 256; c += ng * 32) {
                 const int j = c >> 3, k = c & 7;
+                if (k >= nk) continue;
                 const uint4 z = make_uint4(0u, 0u, 0u, 0u);
                 Mk[c] = k < ng ? stm[lead + k][j] : z;
                 Dk[c] = k < ng ? std_[lead + k][j] : z;
@@ -420,23 +423,24 @@ __global__ void __launch_bounds__(256)
                 }
         }
         __syncthreads();
+        // values r >= R stay as the zeros the buffers were created with
         glue::bf16* RM = static_cast<glue::bf16*>(isx ? v.Xk : v.Yk);
         const int64_t ipad = isx ? v.O_pad : v.S_pad;
         for (int k = ty; k < 64; k += 8) {
             const int64_t i = i0 + k;
-            if (i < ipad)
+            if (i < ipad && 2 * lane < R)
                 *reinterpret_cast<uint32_t*>(RM + i * 64 + 2 * lane) =
                     glue::pack2(tile[2 * lane][k], tile[2 * lane + 1][k]);
         }
         if (!isx) {
             glue::bf16* Yt = static_cast<glue::bf16*>(v.Ytk);
             glue::bf16* Y2t = static_cast<glue::bf16*>(v.Y2tk);
-            for (int r = ty; r < 64; r += 8) {
+            for (int r = ty; r < R; r += 8) {
                 const int64_t i = i0 + 2 * lane;
                 if (i < v.S_pad) {
                     const float y0 = tile[r][2 * lane], y1 = tile[r][2 * lane + 1];
-                    *reinterpret_cast<uint32_t*>(Yt + r * v.S_pad + i) = glue::pack2(y0, y1);
-                    *reinterpret_cast<uint32_t*>(Y2t + r * v.S_pad + i) = glue::pack2(y0 * y0, y1 * y1);
+                    *reinterpret_cast<uint32_t*>(Yt + r * v.ldt + i) = glue::pack2(y0, y1);
+                    *reinterpret_cast<uint32_t*>(Y2t + r * v.ldt + i) = glue::pack2(y0 * y0, y1 * y1);
                 }
             }
         }
@@ -499,7 +503,7 @@ struct dna_group {
     int64_t p2_units = 8;       // pass-2 (o-block, chunk) units per CTA (autotuned)
     dna::TcGView* gv = nullptr; // device table [count][2]
     std::vector<dna::TcGView> hgv;
-    struct TcBufs { float* Vp; int64_t ldp; void *Xk, *Yk, *Ytk, *Y2tk, *Xmk, *Xdk; };
+    struct TcBufs { float* Vp; int64_t ldp, ldt; void *Xk, *Yk, *Ytk, *Y2tk, *Xmk, *Xdk; };
     std::vector<TcBufs> tcb;
     TileList ops_in[2], cand_bf[2], tp1[2], tp2[2];
     cudaGraphExec_t gexec = nullptr;
@@ -957,6 +961,16 @@ int dna_group_create(int count, const int64_t* N, const int64_t* T, const int64_
             tb.Yk = b; b += al(2 * 64 * spad);
             tb.Ytk = b; b += al(2 * 64 * spad);
             tb.Y2tk = b; b += al(2 * 64 * spad);
+            // Ytk, Y2tk rows of both views at the same stride, so rows r >= R stay zero
+            tb.ldt = spad;
+            // the operand buffers start as zeros; the kernels write only r < R of them
+            if (cudaMemsetAsync(tb.Xk, 0,
+                                static_cast<size_t>(b - static_cast<unsigned char*>(tb.Xk)),
+                                g->gs) != cudaSuccess) {
+                cudaGetLastError();
+                dna_group_destroy(g);
+                return DNA_ERR_CUDA;
+            }
             g->tcb.push_back(tb);
         }
         p.rclass = r <= 16 ? 0 : r <= 32 ? 1 : 2;
@@ -1016,12 +1030,12 @@ int dna_group_bind(dna_group* g, const void* const* V, const int64_t* ldv, void*
                 tv.X = static_cast<const float*>(v.X); tv.xr = v.xr; tv.xo = v.xo;
                 tv.Y = static_cast<const float*>(v.Y); tv.ys = v.ys; tv.yr = v.yr;
                 tv.Xk = tb.Xk; tv.Yk = tb.Yk; tv.Ytk = tb.Ytk; tv.Y2tk = tb.Y2tk;
-                tv.Xmk = tb.Xmk; tv.Xdk = tb.Xdk;
+                tv.Xmk = tb.Xmk; tv.Xdk = tb.Xdk; tv.ldt = tb.ldt;
                 tv.Xmu = p.Xmu; tv.Xdna = p.Xdna; tv.A = p.A; tv.B = p.B; tv.dpart = p.dpart;
                 dna::TcOperands op{};
                 op.S = v.S; op.O = v.O; op.R = v.R; op.S_pad = tv.S_pad; op.O_pad = tv.O_pad;
                 op.Xk = tb.Xk; op.Yk = tb.Yk; op.Ytk = tb.Ytk; op.Y2tk = tb.Y2tk;
-                op.Xmk = tb.Xmk; op.Xdk = tb.Xdk;
+                op.Xmk = tb.Xmk; op.Xdk = tb.Xdk; op.ldt = tb.ldt;
                 op.ctas = g->num_sms;
                 op.V = w ? static_cast<const float*>(v.V) : tb.Vp;
                 op.vs = w ? v.vs : tb.ldp;

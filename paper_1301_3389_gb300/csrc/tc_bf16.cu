@@ -765,24 +765,25 @@ __global__ void __launch_bounds__(256)
                 }
         }
         __syncthreads();
-        // rows [i][64] with r contiguous: Xk (X) or Yk (Y); lanes walk pairs of r
+        // rows [i][64] with r contiguous: Xk (X) or Yk (Y); lanes walk pairs of r (values
+        // r >= R stay as the zeros the buffers were created with)
         bf16* RM = static_cast<bf16*>(isx ? v.Xk : v.Yk);
         const int64_t ipad = isx ? v.O_pad : v.S_pad;
         for (int k = ty; k < 64; k += 8) {
             const int64_t i = i0 + k;
-            if (i < ipad)
+            if (i < ipad && 2 * lane < R)
                 *reinterpret_cast<uint32_t*>(RM + i * 64 + 2 * lane) =
                     pack_bf16x2(tile[2 * lane][k], tile[2 * lane + 1][k]);
         }
-        if (!isx) {   // Ytk, Y2tk [64][S_pad] with s contiguous; lanes walk pairs of s
+        if (!isx) {   // Ytk, Y2tk rows r < R, [64][ldt] with s contiguous; lanes walk pairs of s
             bf16* Yt = static_cast<bf16*>(v.Ytk);
             bf16* Y2t = static_cast<bf16*>(v.Y2tk);
-            for (int r = ty; r < 64; r += 8) {
+            for (int r = ty; r < R; r += 8) {
                 const int64_t i = i0 + 2 * lane;
                 if (i < v.S_pad) {
                     const float y0 = tile[r][2 * lane], y1 = tile[r][2 * lane + 1];
-                    *reinterpret_cast<uint32_t*>(Yt + r * v.S_pad + i) = pack_bf16x2(y0, y1);
-                    *reinterpret_cast<uint32_t*>(Y2t + r * v.S_pad + i) =
+                    *reinterpret_cast<uint32_t*>(Yt + r * v.ldt + i) = pack_bf16x2(y0, y1);
+                    *reinterpret_cast<uint32_t*>(Y2t + r * v.ldt + i) =
                         pack_bf16x2(y0 * y0, y1 * y1);
                 }
             }
@@ -851,8 +852,9 @@ int TcBf16::make_maps(TcMaps* m, const TcOperands& op, const float* V, int64_t v
     int e = make_map(&m->x, BF, op.Xk, rp, op.O_pad, rp * 2, 64, OBLK, SW);
     if (!e) e = make_map(&m->y, BF, op.Yk, rp, op.S_pad, rp * 2, 64, SCH, SW);
     const uint32_t ytbox = (uint32_t)(rp < 128 ? rp : 128);   // rows of one r-block
-    if (!e) e = make_map(&m->yt, BF, op.Ytk, op.S_pad, rp, op.S_pad * 2, SCH, ytbox, SW);
-    if (!e) e = make_map(&m->y2t, BF, op.Y2tk, op.S_pad, rp, op.S_pad * 2, SCH, ytbox, SW);
+    const uint64_t ldt = (uint64_t)(op.ldt ? op.ldt : op.S_pad);
+    if (!e) e = make_map(&m->yt, BF, op.Ytk, op.S_pad, rp, ldt * 2, SCH, ytbox, SW);
+    if (!e) e = make_map(&m->y2t, BF, op.Y2tk, op.S_pad, rp, ldt * 2, SCH, ytbox, SW);
     if (!e) e = make_map(&m->xm, BF, Xmk, rp, op.O_pad, rp * 2, 64, OBLK, SW);
     if (!e) e = make_map(&m->xd, BF, Xdk, rp, op.O_pad, rp * 2, 64, OBLK, SW);
     if (!e)

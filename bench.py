@@ -863,10 +863,13 @@ def measure_batched(dna, torch, probs, steps, warmup, peaks, bf16=False):
         torch.cuda.synchronize()
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
+        # the timed iterations form the profiler range (ncu --profile-from-start off)
+        torch.cuda.profiler.start()
         ev0.record(stream)
         dna.dna_group_iterate(g, steps)
         ev1.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
         ms = ev0.elapsed_time(ev1)
         kl1 = dna.dna_group_kl(g, len(probs))
         # BF16: plus the first H half-step's operands, written once per dna_group_iterate call

@@ -28,11 +28,22 @@ def big():
 
 @pytest.mark.parametrize("kind", ["f32", "f32t"])
 def test_plain_large_sampled(big, kind):
+    _sampled(big, kind, 1e-5 if kind == "f32" else 1e-4, 1e-4)
+
+
+def test_precision_large_split_sampled():
+    """N=8192 T=32768 R=512 in the FP32 form on the tensor cores (the form the bench's
+    time-to-target runs at this size): sampled columns and rows against the oracle, with
+    the tolerance derived for the split operands at R > 300 (tests/gpu_helpers.py)."""
+    from gpu_helpers import SPLIT_LARGE_R_TOL
+    _sampled(workloads.precision_large(0), "f32t", SPLIT_LARGE_R_TOL, SPLIT_LARGE_R_TOL)
+
+
+def _sampled(big, kind, ctol, tol):
     g = np.random.default_rng(0)
     N, T = big.V.shape
     cols = np.sort(g.choice(T, 48, replace=False))
     rows = np.sort(g.choice(N, 48, replace=False))
-    ctol = 1e-5 if kind == "f32" else 1e-4
     with GpuProblem(big.V, big.W, big.H, kind) as gp:
         gp.dna.dna_normalize(gp.ctx, 1)
         kl0 = gp.dna.dna_kl(gp.ctx)
@@ -51,7 +62,7 @@ def test_plain_large_sampled(big, kind):
         sigma = W1.sum(axis=0) / W0.sum(axis=0)          # step 16 factor per r
         eh = rel_fro(H1[:, cols], X / sigma[:, None])
         print(f"\n{kind}: H half-step error on sampled columns {eh:.2e}")
-        assert eh < 1e-4
+        assert eh < tol
         half = dataclasses.replace(half, choice=mask)
         assert step_elementwise(half, 0, W0, H0[:, cols], W1, H1[:, cols], kind, sig=sigma,
                                 check_y=False, label="H sampled") <= 1.0
@@ -66,7 +77,7 @@ def test_plain_large_sampled(big, kind):
         sigma = H2.sum(axis=1) / H1.sum(axis=1)          # step 29 factor per r
         ew = rel_fro(W2[rows, :], X / sigma[None, :])
         print(f"{kind}: W half-step error on sampled rows {ew:.2e}")
-        assert ew < 1e-4
+        assert ew < tol
         half = dataclasses.replace(half, choice=mask)
         assert step_elementwise(half, 1, W1[rows, :], H1, W2[rows, :], H2, kind, sig=sigma,
                                 check_y=False, label="W sampled") <= 1.0
@@ -76,4 +87,4 @@ def test_plain_large_sampled(big, kind):
         import torch
         Z = gp.W @ gp.H
         rs = Z.double().sum(dim=1).cpu().numpy()
-        np.testing.assert_allclose(rs, big.V.astype(np.float64).sum(axis=1), rtol=1e-4)
+        np.testing.assert_allclose(rs, big.V.astype(np.float64).sum(axis=1), rtol=tol)

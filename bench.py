@@ -5,6 +5,10 @@ A step is one DNA iteration (H half-step then W half-step, Algorithm 1 steps 4-2
 the workload N=4096 T=16384 R=128 (Gamma(0.3) truth scaled to mean count 2, Poisson
 counts; seeded synthetic data standing in for the paper's dense datasets) in the FP32
 form.  The inputs (V is 268 MB) are larger than L2, so no flush is needed between steps.
+The K timed iterations are one dna_iterate call with the iteration replayed as a CUDA
+graph (dna_use_graph); the dominant kernel's duration comes from event pairs around the
+passes over the same K iterations launched directly, right after (events recorded inside
+the graph would slow its replay), which the line also reports as direct_launches.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl dna|reference]
 
@@ -300,13 +304,14 @@ def main(argv=None):
         "roofline": res["roofline"],
         "clocks": res["clocks"],
         "kl_start": res["kl_start"], "kl_end": res["kl_end"],
+        "direct_launches": res["direct"],
     }
     if args.dtype == "f32" and not args.no_forms:
         # the other forms on the same workload, and seconds to the FP32 form's target d_KL
         bf = measure(dna, torch, dist, prob, "bf16", args, world, local, peaks, clocks=False)
         line["bf16_form"] = {"value": bf["value"], "unit": UNIT,
                              "ms_per_step": bf["ms_max"] / args.steps, "roofline": bf["roofline"],
-                             "gpu_launches": bf["launches"]}
+                             "gpu_launches": bf["launches"], "direct_launches": bf["direct"]}
         if args.engine == "tensor":
             sargs = argparse.Namespace(**vars(args))
             sargs.steps = max(3, min(args.steps, 20))
@@ -333,7 +338,7 @@ def main(argv=None):
             line["precision_form"] = {
                 "value": pr["value"], "unit": UNIT, "steps": pargs.steps,
                 "ms_per_step": pr["ms_max"] / pargs.steps, "roofline": pr["roofline"],
-                "gpu_launches": pr["launches"],
+                "gpu_launches": pr["launches"], "direct_launches": pr["direct"],
                 "config": {"workload": "precision_large", "desc": pspec["desc"],
                            "N": pspec["N"], "T": pspec["T"], "R": pspec["R"], "form": "BF16"}}
             if not args.no_c3_target:
@@ -436,31 +441,48 @@ def measure(dna, torch, dist, prob, dtype, args, world, local, peaks, clocks, en
     ctx, keep = _bind(dna, torch, prob, dtype, dev, engine)
     stream = torch.cuda.current_stream()
     kl_start = dna.dna_kl(ctx)
-    for _ in range(args.warmup):
-        dna.dna_iterate(ctx, 1)
-    torch.cuda.synchronize()
-    sampler = ClockSampler(local) if clocks else None
-    if sampler:
-        time.sleep(0.3)
-    # timed region: K iterations in one call; event pairs around the two passes only (the
-    # candidates for the dominant kernel), so the other phases run back to back
-    dna.dna_profile_phases(ctx, ["pass1", "pass2"])
-    dna.dna_phase_times(ctx)                     # reset counters
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    dna.dna_iterate(ctx, args.steps)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    ms = ev0.elapsed_time(ev1)
-    phases = dna.dna_phase_times(ctx)
-    clk = sampler.stop() if sampler else None
-    # phase shares from a separate, untimed pass with every phase bracketed
+    # timed region: K iterations in one dna_iterate call replayed as a CUDA graph of one
+    # iteration (dna_use_graph) on a stream of its own (a graph is not captured on the
+    # legacy default stream)
+    gstream = torch.cuda.Stream(device=dev)
+    dna.dna_set_stream(ctx, gstream)
+    dna.dna_use_graph(ctx, True)
+    with torch.cuda.stream(gstream):
+        for _ in range(args.warmup):
+            dna.dna_iterate(ctx, 1)              # the first call captures the graph
+        torch.cuda.synchronize()
+        sampler = ClockSampler(local) if clocks else None
+        if sampler:
+            time.sleep(0.3)
+        dna.dna_phase_times(ctx)                 # reset counters
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(gstream)
+        dna.dna_iterate(ctx, args.steps)
+        ev1.record(gstream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        ms = ev0.elapsed_time(ev1)
+        graph_phases = dna.dna_phase_times(ctx)  # launch counts of the timed region
+        # the dominant kernel's duration: the same K iterations launched directly with event
+        # pairs around the two passes only (events inside the graph would slow its replay)
+        dna.dna_use_graph(ctx, False)
+        dna.dna_profile_phases(ctx, ["pass1", "pass2"])
+        d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        d0.record(gstream)
+        dna.dna_iterate(ctx, args.steps)
+        d1.record(gstream)
+        torch.cuda.synchronize()
+        direct_ms = d0.elapsed_time(d1)
+        phases = dna.dna_phase_times(ctx)
+        dna.dna_profile_phases(ctx, [])
+        clk = sampler.stop() if sampler else None
+    dna.dna_set_stream(ctx, stream)
+    # phase shares from a separate, untimed pass with every phase bracketed (direct launches)
     dna.dna_profile(ctx, True)
     prof_iters = max(1, min(args.steps, 10))
     e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -544,14 +566,21 @@ def measure(dna, torch, dist, prob, dtype, args, world, local, peaks, clocks, en
     roof["algorithmic_flops_per_launch"] = flops
     roof["algorithmic_bytes_per_launch"] = alg_bytes
     roof["launch_ms"] = per_launch_s * 1e3
+    roof["launch_ms_source"] = ("CUDA events around each pass on the library's stream, over K "
+                                "directly launched iterations right after the timed region")
     roof["kernels_per_pass"] = dom_launches / instances
     roof["phase_share"] = {p: round(prof_phases[p][0] / prof_ms, 4)
                            for p in ("pass1", "candidates", "pass2", "select", "sums", "operands")}
     roof["phase_share_note"] = (f"separate pass of {prof_iters} iterations with every phase "
                                 f"bracketed by events ({prof_ms / prof_iters:.3f} ms/iteration)")
     return {"value": value, "ms_max": ms_max, "roofline": roof, "clocks": clk,
-            "launches": sum(v[1] for v in phases.values()), "kl_start": kl_start,
-            "kl_end": kl_end}
+            "launches": sum(v[1] for v in graph_phases.values()), "kl_start": kl_start,
+            "kl_end": kl_end,
+            "direct": {"value": args.steps / (direct_ms / 1e3), "unit": UNIT,
+                       "ms_per_step": direct_ms / args.steps,
+                       "note": "the same iterations with every kernel launched directly and "
+                               "event pairs around the two passes (the pass that gives "
+                               "roofline.launch_ms), right after the timed region"}}
 
 
 def run_logged(dna, torch, prob, dtype, engine, max_iters, target=None, algo="dna",

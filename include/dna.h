@@ -141,6 +141,16 @@ int dna_step_W(dna_ctx* ctx);
 /* iters DNA iterations: iters times (dna_step_H, dna_step_W).  Asynchronous. */
 int dna_iterate(dna_ctx* ctx, int iters);
 
+/* enable != 0: dna_iterate forms the first H half-step's operands and denominators from the
+ * current factors, then replays one captured iteration (a CUDA graph, captured on the first
+ * such call and kept until the next dna_bind, selection change or change of the profiled
+ * phases) iters times; W and H are bit-identical to the direct launches.  Profiled phases
+ * of the captured iteration are timed by events recorded inside the graph: dna_phase_times
+ * counts each replay with the times of the last one.  Used only with a stream set by
+ * dna_set_stream (not the legacy default stream) and dense V; otherwise dna_iterate
+ * launches directly.  Default: off. */
+int dna_use_graph(dna_ctx* ctx, int enable);
+
 /* Multiplicative update (eq. 11; Algorithm 1 "MU" steps).  which = 0: H <- H (W^t Q) /
  * (W^t 1 + lambda) then step 16; which = 1: W <- W (Q H^t) / (H 1 + rho) then step 29.
  * Asynchronous. */

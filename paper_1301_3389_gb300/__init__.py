@@ -15,4 +15,4 @@ from ._lib import (  # noqa: F401
     dna_group_launches_per_iteration, dna_group_destroy, dna_shard_rowsums,
     dna_shard_set_rowsums, dna_shard_H_begin, dna_shard_H_end, dna_shard_W_begin,
     dna_shard_W_pass1, dna_shard_W_pass2, dna_shard_W_end, DNA_SELECT_PAPER, DNA_SELECT_DESCENT,
-    dna_set_selection)
+    dna_set_selection, dna_use_graph)

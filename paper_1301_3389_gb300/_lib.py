@@ -55,6 +55,7 @@ def _load() -> ctypes.CDLL:
         "dna_step_H": (I, [P]),
         "dna_step_W": (I, [P]),
         "dna_iterate": (I, [P, I]),
+        "dna_use_graph": (I, [P, I]),
         "mu_step": (I, [P, I]),
         "mu_iterate": (I, [P, I]),
         "dna_create_sparse": (I, [I64, I64, I64, I64, ctypes.POINTER(dna_opts), ctypes.POINTER(P)]),
@@ -200,6 +201,10 @@ def dna_step_W(ctx: int) -> None:
 
 def dna_iterate(ctx: int, iters: int) -> None:
     _check(LIB.dna_iterate(ctx, iters), "dna_iterate")
+
+
+def dna_use_graph(ctx: int, enable: bool) -> None:
+    _check(LIB.dna_use_graph(ctx, int(bool(enable))), "dna_use_graph")
 
 
 def mu_step(ctx: int, which: int) -> None:

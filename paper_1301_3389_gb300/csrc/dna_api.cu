@@ -110,6 +110,19 @@ struct dna_ctx {
     double* wg_cpart = nullptr;
     int wsp = 0;
     int64_t wper = 0;
+    // dna_iterate replayed as a CUDA graph of one iteration (dna_use_graph): the
+    // instantiated graph and the kernel launches it holds, in all and per phase
+    bool use_graph = false;
+    bool capturing = false;
+    cudaGraphExec_t gexec = nullptr;
+    int64_t graph_launches = 0;
+    int64_t graph_phase_launches[DNA_NUM_PHASES] = {};
+    // phase events captured in the graph (their own events: every replay records them
+    // again), their (phase, index) pairs, and the replays since the last dna_phase_times
+    std::vector<cudaEvent_t> graph_ev;
+    size_t graph_ev_used = 0;
+    std::vector<std::pair<int, size_t>> graph_recs;
+    int64_t graph_replays = 0;
     // profiling: event pairs around phases, launch counts
     unsigned prof_mask = 0;          // phases whose instances get an event pair
     std::vector<cudaEvent_t> ev_pool;
@@ -254,6 +267,11 @@ void free_all(dna_ctx* c) {
         if (p) cudaFree(p);
     for (cudaEvent_t ev : c->ev_pool) cudaEventDestroy(ev);
     c->ev_pool.clear();
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+    for (cudaEvent_t ev : c->graph_ev) cudaEventDestroy(ev);
+    c->graph_ev.clear();
+    c->graph_recs.clear();
 }
 
 template <typename Tp>
@@ -895,18 +913,32 @@ int set_device(const dna_ctx* c) {
 // the kernels it launches are counted (nlaunch is the expected count, for reading only).
 template <class F>
 int phase(dna_ctx* c, int ph, int nlaunch, F&& f) {
-    size_t idx = SIZE_MAX;
-    if (((c->prof_mask >> ph) & 1u) && c->ev_used + 2 <= c->ev_pool.size()) {
-        idx = c->ev_used;
-        c->ev_used += 2;
-        if (cudaEventRecord(c->ev_pool[idx], c->stream) != cudaSuccess) return DNA_ERR_CUDA;
+    // events of a profiled phase: from the pool, or while a graph is being captured two
+    // events of the graph's own, recorded as graph nodes (cudaEventRecordExternal)
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if ((c->prof_mask >> ph) & 1u) {
+        if (c->capturing) {
+            if (c->graph_ev_used + 2 <= c->graph_ev.size()) {
+                e0 = c->graph_ev[c->graph_ev_used];
+                e1 = c->graph_ev[c->graph_ev_used + 1];
+                c->graph_recs.emplace_back(ph, c->graph_ev_used);
+                c->graph_ev_used += 2;
+            }
+        } else if (c->ev_used + 2 <= c->ev_pool.size()) {
+            e0 = c->ev_pool[c->ev_used];
+            e1 = c->ev_pool[c->ev_used + 1];
+            c->ev_recs.emplace_back(ph, c->ev_used);
+            c->ev_used += 2;
+        }
     }
+    auto record = [&](cudaEvent_t ev) {
+        return c->capturing ? cudaEventRecordWithFlags(ev, c->stream, cudaEventRecordExternal)
+                            : cudaEventRecord(ev, c->stream);
+    };
+    if (e0 && record(e0) != cudaSuccess) return DNA_ERR_CUDA;
     const int64_t before = dna::launch_count();
     const int e = f();
-    if (idx != SIZE_MAX) {
-        if (cudaEventRecord(c->ev_pool[idx + 1], c->stream) != cudaSuccess) return DNA_ERR_CUDA;
-        c->ev_recs.emplace_back(ph, idx);
-    }
+    if (e1 && record(e1) != cudaSuccess) return DNA_ERR_CUDA;
     c->phase_launches[ph] += dna::launch_count() - before;
     return e;
 }
@@ -980,6 +1012,77 @@ int shard_W_end(dna_ctx* c, const double* cost) {
     if (int e = d2d(c->dpart, cost, sizeof(double) * 2 * c->N, c->stream)) return e;
     if (int e = step_core<Tp>(c, 1, false, true, STOP_SELECT)) return e;
     return finish_step<Tp>(c, 1, false);
+}
+
+// dna_iterate as graph replays: the H half-step's operands and denominators are formed
+// from the current factors (as the first half-step of an eager call does), then each
+// iteration replays one captured iteration whose half-steps both leave the next one's
+// operands (the last one's are not used).  The factors match the eager path bit for bit.
+template <typename Tp>
+int iterate_graph(dna_ctx* c, int iters) {
+    if (int e = prep_step<Tp>(c, 0, true)) return e;
+    if (!c->gexec) {   // one iteration, captured once; pointers are fixed until the next bind
+        // events for the profiled phases of the captured iteration (created before capture)
+        c->graph_recs.clear();
+        c->graph_ev_used = 0;
+        if (c->prof_mask && c->graph_ev.empty()) {
+            c->graph_ev.resize(64, nullptr);
+            for (auto& ev : c->graph_ev)
+                if (cudaEventCreate(&ev) != cudaSuccess) return DNA_ERR_CUDA;
+        }
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            return DNA_ERR_CUDA;
+        int64_t ph0[DNA_NUM_PHASES];
+        std::copy(c->phase_launches, c->phase_launches + DNA_NUM_PHASES, ph0);
+        const int64_t before = dna::launch_count();
+        c->capturing = true;
+        int e = half_step<Tp>(c, 0, false, true, true);
+        if (!e) e = half_step<Tp>(c, 1, false, true, true);
+        c->capturing = false;
+        const cudaError_t ce = cudaStreamEndCapture(c->stream, &graph);
+        // the capture ran nothing: move its launch counts from the counters to the graph
+        c->graph_launches = dna::launch_count() - before;
+        dna::launch_count() = before;
+        for (int p = 0; p < DNA_NUM_PHASES; ++p) {
+            c->graph_phase_launches[p] = c->phase_launches[p] - ph0[p];
+            c->phase_launches[p] = ph0[p];
+        }
+        if (e || ce != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            c->graph_recs.clear();
+            return e ? e : DNA_ERR_CUDA;
+        }
+        const cudaError_t ie = cudaGraphInstantiate(&c->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) {
+            c->gexec = nullptr;
+            c->graph_recs.clear();
+            cudaGetLastError();
+            return DNA_ERR_CUDA;
+        }
+        c->graph_replays = 0;
+    }
+    for (int i = 0; i < iters; ++i) {
+        if (cudaGraphLaunch(c->gexec, c->stream) != cudaSuccess) return DNA_ERR_CUDA;
+        dna::launch_count() += c->graph_launches;
+        for (int p = 0; p < DNA_NUM_PHASES; ++p) c->phase_launches[p] += c->graph_phase_launches[p];
+    }
+    c->graph_replays += iters;
+    return DNA_OK;
+}
+
+void drop_graph(dna_ctx* c) {
+    if (c->gexec) {
+        cudaStreamSynchronize(c->stream);
+        cudaGraphExecDestroy(c->gexec);
+    }
+    c->gexec = nullptr;
+    for (cudaEvent_t ev : c->graph_ev) cudaEventDestroy(ev);
+    c->graph_ev.clear();
+    c->graph_recs.clear();
+    c->graph_replays = 0;
 }
 
 }  // namespace
@@ -1144,6 +1247,7 @@ int dna_bind(dna_ctx* c, const void* V, int64_t ldv, void* W, void* H) {
     if (set_device(c)) return DNA_ERR_CUDA;
     c->V = V; c->ldv = ldv; c->W = W; c->H = H;
     c->bound = true;
+    drop_graph(c);
     if (c->tc && (ldv % 4 != 0 || reinterpret_cast<uintptr_t>(V) % 16 != 0)) {
         // the tensor-core kernels copy V in 16-byte pieces: keep an aligned, padded copy
         c->ldvp = (c->T + 3) / 4 * 4;
@@ -1193,6 +1297,8 @@ int dna_iterate(dna_ctx* c, int iters) {
     if (int e = check_ready(c)) return e;
     if (iters < 0) return DNA_ERR_ARG;
     if (set_device(c)) return DNA_ERR_CUDA;
+    if (iters > 0 && c->use_graph && c->stream && !c->sparse)
+        return is_f64(c) ? iterate_graph<double>(c, iters) : iterate_graph<float>(c, iters);
     // each half-step leaves the operands and denominators of the next one
     for (int i = 0; i < iters; ++i) {
         const bool more = i + 1 < iters;
@@ -1237,7 +1343,14 @@ int dna_set_selection(dna_ctx* c, int mode) {
         if (dmalloc(&c->dcur, sizeof(double) * (size_t)sp * std::max(c->N, c->T)))
             return DNA_ERR_ALLOC;
     }
+    if (mode != c->selection) drop_graph(c);
     c->selection = mode;
+    return DNA_OK;
+}
+
+int dna_use_graph(dna_ctx* c, int enable) {
+    if (!c) return DNA_ERR_ARG;
+    c->use_graph = enable != 0;
     return DNA_OK;
 }
 
@@ -1433,7 +1546,9 @@ int dna_profile_phases(dna_ctx* c, unsigned mask) {
         for (auto& ev : c->ev_pool)
             if (cudaEventCreate(&ev) != cudaSuccess) return DNA_ERR_CUDA;
     }
-    c->prof_mask = mask & ((1u << DNA_NUM_PHASES) - 1u);
+    mask &= (1u << DNA_NUM_PHASES) - 1u;
+    if (mask != c->prof_mask) drop_graph(c);   // a captured graph holds the old mask's events
+    c->prof_mask = mask;
     return DNA_OK;
 }
 
@@ -1454,6 +1569,16 @@ int dna_phase_times(dna_ctx* c, double* ms, int64_t* launches, int n) {
     }
     c->ev_recs.clear();
     c->ev_used = 0;
+    // graph replays: the captured phases' times of the last replay, once per replay
+    if (c->graph_replays > 0)
+        for (const auto& rec : c->graph_recs) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, c->graph_ev[rec.second], c->graph_ev[rec.second + 1]) !=
+                cudaSuccess)
+                return DNA_ERR_CUDA;
+            c->phase_ms[rec.first] += (double)t * (double)c->graph_replays;
+        }
+    c->graph_replays = 0;
     for (int i = 0; i < n; ++i) {
         if (ms) ms[i] = c->phase_ms[i];
         if (launches) launches[i] = c->phase_launches[i];

@@ -251,3 +251,30 @@ def test_wait_timeout_reported_and_context_usable():
         gp.dna.dna_iterate(gp.ctx, 2)
         assert gp.dna.dna_get_status(gp.ctx) == dna.DNA_OK
     assert dna.LIB.dna_check_wait_timeout(0) == dna.DNA_ERR_ARG
+
+
+@pytest.mark.parametrize("kind", ["f32", "f32t", "f64", "bf16"])
+def test_iterate_graph_equals_direct(kind):
+    """dna_use_graph: dna_iterate replays one captured iteration (after forming the first
+    H half-step's operands from the current factors); W and H equal those of the direct
+    launches bit for bit, across calls (the second call replays the same graph) and after
+    a rebind (a new capture)."""
+    import torch
+    p = workloads.custom(150, 260, 20, seed=41)
+    outs = []
+    for graph in (False, True):
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            with GpuProblem(p.V, p.W, p.H, kind) as gp:
+                gp.dna.dna_set_stream(gp.ctx, stream)
+                gp.dna.dna_use_graph(gp.ctx, graph)
+                gp.dna.dna_normalize(gp.ctx, 1)
+                gp.dna.dna_iterate(gp.ctx, 2)
+                gp.dna.dna_iterate(gp.ctx, 1)
+                gp.dna.dna_bind(gp.ctx, gp.V, gp.W, gp.H)
+                gp.dna.dna_iterate(gp.ctx, 2)
+                stream.synchronize()
+                assert gp.dna.dna_get_status(gp.ctx) == 0
+                outs.append(gp.WH())
+    np.testing.assert_array_equal(outs[0][0], outs[1][0])
+    np.testing.assert_array_equal(outs[0][1], outs[1][1])

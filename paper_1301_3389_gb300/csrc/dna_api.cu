@@ -237,8 +237,11 @@ void plan_all(dna_ctx* c) {
             // the split form, and pass 1 at ranks above 128, stream s in chunks of 128
             const int sch = c->split ? (int)SPLIT_CHUNK : tch;
             const int sch1 = c->split || c->rp > 128 ? (int)SPLIT_CHUNK : tch;
+            // the split form's pass 1 at R <= 128 accumulates a whole split in tensor
+            // memory, so its splits are at most SPLIT_MAX_CHUNKS chunks; at R > 128 the
+            // contraction kernel cuts each split into such segments itself
             plan_split(Sdim, c->pad_o[w] / tob * rblocks, c->num_sms, sch1, &c->tsp1[w],
-                       &c->tper1[w], part, c->split ? SPLIT_MAX_CHUNKS : 0);
+                       &c->tper1[w], part, c->split && c->rp <= 128 ? SPLIT_MAX_CHUNKS : 0);
             plan_split(Sdim, c->pad_o[w] / tob, c->num_sms, c->rp > 256 ? (int)SPLIT_CHUNK : sch,
                        &c->tsp2[w], &c->tper2[w], 2.0 / (double)Sdim);
             // pass 2 of the split form at R <= 128 and of the BF16 form at R <= 256 balances

@@ -14,10 +14,14 @@
 //   contract  A[o, r] += sum_s Q[o, s] Yt[r, s] (CTAs of which = 0) and
 //             B[o, r] += sum_s Qbar[o, s] Y2t[r, s] (which = 1) over (o-block, 256-wide
 //             r-block, split of s) tiles, the three products per K-step into one 128 x 256
-//             accumulator (two, double-buffered across tiles), written per split
-//             ([split][R][O]).  The tensor pipe's float32 accumulation is not
-//             round-to-nearest, so a split covers at most 1024 values of s (the host plans
-//             it so), as in the split form's other pass-1 kernel.
+//             accumulator, written per split ([split][R][O]).  The tensor pipe's float32
+//             accumulation is not round-to-nearest, so one accumulation covers at most 1024
+//             values of s: a longer split runs as segments of 1024 into alternating
+//             accumulators (double-buffered), and the epilogue adds each segment to the
+//             split's float32 partial in order with round-to-nearest adds (the previous sums
+//             read back from L2).  The splits are then only as many as the load balance
+//             wants, and the host's sum over them reads a few partials instead of one per
+//             1024 values of s.
 //
 // Every barrier wait is bounded (wait_phase) and aborts the CTA; after an abort the
 // producer waits for its armed copies, each MMA-issuing thread for its MMAs, and the store
@@ -103,6 +107,10 @@ constexpr int B_EPI = 8;                      // epilogue warps of the contract 
 constexpr int W_PROD_B = B_EPI, W_MMA_B = B_EPI + 1;
 constexpr int B_THREADS = (B_EPI + 2) * 32;
 constexpr int RB = 256;                       // r per tile of the contract kernel
+// K-slices of 64 values of s that one accumulation in tensor memory takes at most (1024
+// values: the tensor pipe's float32 accumulation stays short); a longer tile adds its
+// segments into the float32 partial in order with round-to-nearest adds
+constexpr int SEG_SL = 16;
 
 struct LayoutB {
     static constexpr int KST = 2;
@@ -499,36 +507,42 @@ __global__ void __launch_bounds__(mats::B_THREADS, 1)
     } else if (warp == W_MMA_B) {
         if (lane == 0) {
             bool ok = true;
-            int j = 0, tt = 0;
+            int j = 0, sg = 0;
             constexpr uint32_t idesc = idesc_bf16(OBLK, RB);
-            for (int t = t_begin; ok && t < t_end; ++t, ++tt) {
+            for (int t = t_begin; ok && t < t_end; ++t) {
                 const int nsl = b_tile(t, nob, nrb, nsplit, a).nsl;
-                const int ab = tt & 1;
-                // the epilogue has copied tile tt - 2 out of this accumulator
-                if (tt >= 2 &&
-                    !(ok = wait_phase(&bar[C_ACCEMPTY + ab], ((tt - 2) >> 1) & 1, abort)))
-                    break;
-                tc_fence_after();
-                const uint32_t acc = tmem + (uint32_t)(ab * RB);
-#pragma unroll 1
-                for (int sl = 0; sl < nsl; ++sl, ++j) {
-                    if (!(ok = wait_phase(&bar[C_KFULL + j % KST], (j / KST) & 1, abort))) break;
+                // segments of at most SEG_SL K-slices, each into the next accumulator
+                for (int sl0 = 0; ok && sl0 < nsl; sl0 += SEG_SL, ++sg) {
+                    const int ab = sg & 1, sl1 = min(nsl, sl0 + SEG_SL);
+                    // the epilogue has copied segment sg - 2 out of this accumulator
+                    if (sg >= 2 &&
+                        !(ok = wait_phase(&bar[C_ACCEMPTY + ab], ((sg - 2) >> 1) & 1, abort)))
+                        break;
                     tc_fence_after();
-                    const uint32_t qh = sbase + (j % KST) * L::STAGE, ql = qh + L::Q_TILE;
-                    const uint32_t yh = qh + 2 * L::Q_TILE, yl = yh + L::Y_TILE;
+                    const uint32_t acc = tmem + (uint32_t)(ab * RB);
+#pragma unroll 1
+                    for (int sl = sl0; sl < sl1; ++sl, ++j) {
+                        if (!(ok = wait_phase(&bar[C_KFULL + j % KST], (j / KST) & 1, abort)))
+                            break;
+                        tc_fence_after();
+                        const uint32_t qh = sbase + (j % KST) * L::STAGE, ql = qh + L::Q_TILE;
+                        const uint32_t yh = qh + 2 * L::Q_TILE, yl = yh + L::Y_TILE;
 #pragma unroll
-                    for (int kq = 0; kq < 4; ++kq)   // Q hi Yt hi
-                        mma_bf16(acc, desc_sw128(qh + 32u * kq), desc_sw128(yh + 32u * kq), idesc,
-                                 (sl > 0 || kq > 0) ? 1u : 0u);
+                        for (int kq = 0; kq < 4; ++kq)   // Q hi Yt hi
+                            mma_bf16(acc, desc_sw128(qh + 32u * kq), desc_sw128(yh + 32u * kq),
+                                     idesc, (sl > sl0 || kq > 0) ? 1u : 0u);
 #pragma unroll
-                    for (int kq = 0; kq < 4; ++kq)   // Q hi Yt lo
-                        mma_bf16(acc, desc_sw128(qh + 32u * kq), desc_sw128(yl + 32u * kq), idesc, 1u);
+                        for (int kq = 0; kq < 4; ++kq)   // Q hi Yt lo
+                            mma_bf16(acc, desc_sw128(qh + 32u * kq), desc_sw128(yl + 32u * kq),
+                                     idesc, 1u);
 #pragma unroll
-                    for (int kq = 0; kq < 4; ++kq)   // Q lo Yt hi
-                        mma_bf16(acc, desc_sw128(ql + 32u * kq), desc_sw128(yh + 32u * kq), idesc, 1u);
-                    mma_commit(&bar[C_KEMPTY + j % KST]);
+                        for (int kq = 0; kq < 4; ++kq)   // Q lo Yt hi
+                            mma_bf16(acc, desc_sw128(ql + 32u * kq), desc_sw128(yh + 32u * kq),
+                                     idesc, 1u);
+                        mma_commit(&bar[C_KEMPTY + j % KST]);
+                    }
+                    if (ok) mma_commit(&bar[C_ACCFULL + ab]);
                 }
-                if (ok) mma_commit(&bar[C_ACCFULL + ab]);
             }
             if (!ok) {
                 mma_commit(&bar[C_DRAIN]);
@@ -540,31 +554,46 @@ __global__ void __launch_bounds__(mats::B_THREADS, 1)
         // rows o = o0 + 32 qd + lane
         const int qd = warp & 3, hf = warp >> 2;
         const uint32_t lane_off = (uint32_t)(32 * qd) << 16;
-        int tt = 0;
-        for (int t = t_begin; t < t_end; ++t, ++tt) {
+        int sg = 0;
+        bool live = true;
+        for (int t = t_begin; live && t < t_end; ++t) {
             const BTile x = b_tile(t, nob, nrb, nsplit, a);
-            const int ab = tt & 1;
-            bool ok = wait_phase(&bar[C_ACCFULL + ab], (tt >> 1) & 1, abort);
-            if (!__all_sync(0xffffffffu, ok)) break;
-            tc_fence_after();
             const int64_t o = x.o0 + 32 * qd + lane;
             float* dst = x.which ? a.Bpart : a.Apart;
             const int64_t base = (int64_t)x.split * a.R;
+            for (int sl0 = 0; sl0 < x.nsl; sl0 += SEG_SL, ++sg) {
+                const int ab = sg & 1;
+                bool ok = wait_phase(&bar[C_ACCFULL + ab], (sg >> 1) & 1, abort);
+                if (!__all_sync(0xffffffffu, ok)) {
+                    live = false;
+                    break;
+                }
+                tc_fence_after();
 #pragma unroll 1
-            for (int c = 0; c < 4; ++c) {
-                uint32_t r32[32];
-                tmem_ld32(tmem + (uint32_t)(ab * RB + 128 * hf + 32 * c) + lane_off, r32);
-                tmem_ld_wait();
-                if (o < a.O)
+                for (int c = 0; c < 4; ++c) {
+                    uint32_t r32[32];
+                    tmem_ld32(tmem + (uint32_t)(ab * RB + 128 * hf + 32 * c) + lane_off, r32);
+                    tmem_ld_wait();
+                    if (o < a.O) {
+                        // the tile's segments in order: the first writes, the later ones add
+                        // (the previous sums' loads all issued before any store)
+                        const int64_t r0 = (int64_t)RB * x.rb + 128 * hf + 32 * c;
+                        float* col = dst + (base + r0) * a.O + o;
+                        const int64_t left = a.R - r0;
+                        const int nr = left < 32 ? (int)left : 32;
+                        float prev[32];
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        const int64_t r = (int64_t)RB * x.rb + 128 * hf + 32 * c + i;
-                        if (r < a.R) dst[(base + r) * a.O + o] = __uint_as_float(r32[i]);
+                        for (int i = 0; i < 32; ++i)
+                            prev[i] = (sl0 > 0 && i < nr) ? col[(int64_t)i * a.O] : 0.f;
+#pragma unroll
+                        for (int i = 0; i < 32; ++i)
+                            if (i < nr) col[(int64_t)i * a.O] = prev[i] + __uint_as_float(r32[i]);
                     }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&bar[C_ACCEMPTY + ab]);
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&bar[C_ACCEMPTY + ab]);
         }
     }
     tc_fence_before();
@@ -625,7 +654,7 @@ int TcBf16::pass1_mats(const TcOperands& op, const TcMaps& maps, float* Apart, f
                        int splits, int64_t s_per, bool with_b, int* status, cudaStream_t st) {
     const int rp = rank_pad(op.R);
     if (!op.Qg || !op.Qbg || !op.plane || !op.qplane || op.ldq % tc::mats::SC != 0 ||
-        s_per % 64 != 0 || s_per > 1024)
+        s_per % 64 != 0)
         return DNA_ERR_ARG;
     if (splits != (int)((op.S + s_per - 1) / s_per)) return DNA_ERR_ARG;
     if (rp == 256)

@@ -247,8 +247,10 @@ int dna_get_status(dna_ctx* ctx);
 /* End-to-end call on HOST buffers: copy V (N x T, ldv = T), W and H from host memory
  * to library-owned device buffers (allocated on the first call and reused), run
  * iters DNA iterations, copy W and H back and write d_KL(V, WH) to *kl_out (may be
- * NULL).  Pinned host memory gives the fastest copies.  Synchronises.  A context used
- * this way must not also be bound with dna_bind. */
+ * NULL).  Pinned host memory gives the fastest copies: a V in pinned (device-mapped)
+ * memory is read across the host link by the kernel that forms V's transpose and sums,
+ * which writes the device copy in the same pass; other host memory is copied first.
+ * Synchronises.  A context used this way must not also be bound with dna_bind. */
 int dna_run_host(dna_ctx* ctx, const void* V, void* W, void* H, int iters, double* kl_out);
 
 /* Phases of a half-step, for dna_phase_times. */

@@ -477,11 +477,13 @@ int bind_csr(dna_ctx* c, const int64_t* rptr, const int32_t* cidx, const Tp* val
 }
 
 template <typename Tp>
-int prepare(dna_ctx* c) {
+int prepare(dna_ctx* c, const void* Vsrc = nullptr) {
+    // Vsrc: V in pinned host memory, read by the transpose kernel and copied into c->V
     return phase(c, DNA_PHASE_PREPARE, 3, [&] {
-        return dna::Simt<Tp>::prepare_v(static_cast<const Tp*>(c->V), c->N, c->T, c->ldv,
-                                        static_cast<Tp*>(c->Vt), c->ldvt, c->colsum_v,
-                                        c->rowsum_v, c->stream, c->vpart);
+        return dna::Simt<Tp>::prepare_v(
+            static_cast<const Tp*>(Vsrc ? Vsrc : c->V), c->N, c->T, Vsrc ? c->T : c->ldv,
+            static_cast<Tp*>(c->Vt), c->ldvt, c->colsum_v, c->rowsum_v, c->stream, c->vpart,
+            Vsrc ? static_cast<Tp*>(const_cast<void*>(c->V)) : nullptr);
     });
 }
 
@@ -1523,11 +1525,20 @@ int dna_run_host(dna_ctx* c, const void* V, void* W, void* H, int iters, double*
             if (int e2 = build_tc_maps(c)) return e2;
     }
     cudaStream_t st = c->stream;
-    if (cudaMemcpyAsync(c->own_V, V, bv, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+    // V in pinned (page-locked, device-mapped) host memory: the transpose-and-sums kernel
+    // reads it across the host link and writes the device copy in the same pass; other
+    // host memory: a copy first
+    const void* vsrc = nullptr;
+    cudaPointerAttributes pa{};
+    if (cudaPointerGetAttributes(&pa, V) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+        pa.devicePointer)
+        vsrc = pa.devicePointer;
+    cudaGetLastError();
+    if ((!vsrc && cudaMemcpyAsync(c->own_V, V, bv, cudaMemcpyHostToDevice, st) != cudaSuccess) ||
         cudaMemcpyAsync(c->own_W, W, bw, cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemcpyAsync(c->own_H, H, bh, cudaMemcpyHostToDevice, st) != cudaSuccess)
         return DNA_ERR_CUDA;
-    int e = is_f64(c) ? prepare<double>(c) : prepare<float>(c);
+    int e = is_f64(c) ? prepare<double>(c, vsrc) : prepare<float>(c, vsrc);
     if (e) return e;
     if ((e = dna_iterate(c, iters))) return e;
     double kl = 0.0;

@@ -165,10 +165,11 @@ template <typename Tp> struct Simt {
                      cudaStream_t st);
     // out (cols x rows) = in^t (rows x cols), both row-major
     static int transpose(const Tp* in, int64_t rows, int64_t cols, Tp* out, cudaStream_t st);
-    // one-time: row and column sums of V (float64) and the transposed copy
+    // one-time: row and column sums of V (float64) and the transposed copy; with Vc (needs
+    // part) also a copy of V into Vc [N][T] in the same pass (V may be pinned host memory)
     static int prepare_v(const Tp* V, int64_t N, int64_t T, int64_t ldv, Tp* Vt, int64_t ldvt,
                          double* colsum, double* rowsum, cudaStream_t st,
-                         double* part = nullptr);
+                         double* part = nullptr, Tp* Vc = nullptr);
     // how many CTAs of pass 1 / pass 2 fit on one SM
     static int pass1_blocks_per_sm(int64_t R);
     static int pass2_blocks_per_sm(int64_t R);

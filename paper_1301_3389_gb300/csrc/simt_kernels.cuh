@@ -1142,18 +1142,23 @@ __global__ void k_transpose(const Tp* __restrict__ V, int64_t N, int64_t T, int6
 
 // k_transpose fused with the column and row sums of V: per 32 x 32 tile the sums of its
 // 32 rows (colpart[n-tile][t]) and of its 32 columns (rowpart[t-tile][n]), in the element
-// type (exact for counts), for k_colsum_final to add up in float64.
+// type (exact for counts), for k_colsum_final to add up in float64.  With Vc, also a copy
+// of V into Vc (leading dimension T): V may then be pinned host memory that the kernel
+// reads across the host link (the copy in of dna_run_host).
 template <typename Tp>
 __global__ void __launch_bounds__(256) k_transpose_sums(const Tp* __restrict__ V, int64_t N,
                                                         int64_t T, int64_t ldv,
                                                         Tp* __restrict__ Vt, int64_t ldvt,
                                                         double* __restrict__ colpart,
-                                                        double* __restrict__ rowpart) {
+                                                        double* __restrict__ rowpart,
+                                                        Tp* __restrict__ Vc = nullptr) {
     __shared__ Tp tile[32][33];
     const int64_t n0 = (int64_t)blockIdx.y * 32, t0 = (int64_t)blockIdx.x * 32;
     for (int k = threadIdx.y; k < 32; k += 8) {
         const int64_t n = n0 + k, t = t0 + threadIdx.x;
-        tile[k][threadIdx.x] = (n < N && t < T) ? V[n * ldv + t] : Tp(0);
+        const Tp x = (n < N && t < T) ? V[n * ldv + t] : Tp(0);
+        tile[k][threadIdx.x] = x;
+        if (Vc && n < N && t < T) Vc[n * T + t] = x;
     }
     __syncthreads();
     for (int k = threadIdx.y; k < 32; k += 8) {

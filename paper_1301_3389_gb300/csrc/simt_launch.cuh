@@ -439,13 +439,15 @@ int Simt<Tp>::scale_ops(const View& t, const double* f, bool xmul, void* Xk, voi
 
 template <typename Tp>
 int Simt<Tp>::prepare_v(const Tp* V, int64_t N, int64_t T, int64_t ldv, Tp* Vt, int64_t ldvt,
-                        double* colsum, double* rowsum, cudaStream_t st, double* part) {
+                        double* colsum, double* rowsum, cudaStream_t st, double* part, Tp* Vc) {
     dim3 blk(32, 8);
     dim3 grid((unsigned)((T + 31) / 32), (unsigned)((N + 31) / 32));
+    if (Vc && !part) return DNA_ERR_ARG;
     if (part) {   // one pass over V: transpose and per-tile sums, then the float64 totals
         double* colpart = part;                                // [ceil(N / 32)][T]
         double* rowpart = part + (size_t)((N + 31) / 32) * T;  // [ceil(T / 32)][N]
-        simt::k_transpose_sums<Tp><<<grid, blk, 0, st>>>(V, N, T, ldv, Vt, ldvt, colpart, rowpart);
+        simt::k_transpose_sums<Tp><<<grid, blk, 0, st>>>(V, N, T, ldv, Vt, ldvt, colpart, rowpart,
+                                                         Vc);
         if (simt::launch_status()) return DNA_ERR_CUDA;
         simt::k_colsum_final<<<(unsigned)((T + 31) / 32), dim3(32, 32), 0, st>>>(
             colpart, (int)((N + 31) / 32), T, 0.0, colsum, false);

@@ -177,24 +177,37 @@ def test_nonfinite_reported(kind, fault):
         assert gp.dna.dna_get_status(gp.ctx) == dna.DNA_ERR_NONFINITE
 
 
-def test_run_host_matches_device_path():
-    """dna_run_host (host buffers, copies inside) equals the device-buffer path."""
+@pytest.mark.parametrize("kind", ["f32", "f32t"])
+def test_run_host_matches_device_path(kind):
+    """dna_run_host (host buffers, copies inside) equals the device-buffer path, with V in
+    pageable memory (copied in) and in pinned memory (read across the host link by the
+    transpose kernel, which writes the device copy), twice on one context."""
+    import torch
+
     import paper_1301_3389_gb300 as dna
     p = workloads.custom(120, 200, 9, seed=4)
-    with GpuProblem(p.V, p.W, p.H, "f32") as gp:
+    with GpuProblem(p.V, p.W, p.H, kind) as gp:
         gp.dna.dna_iterate(gp.ctx, 3)
         kl_dev = gp.dna.dna_kl(gp.ctx)
         Wd, Hd = gp.WH()
-    ctx = dna.dna_create(120, 200, 9, dna.make_opts(dtype=dna.DNA_F32))
+    eng = dna.DNA_ENGINE_TENSOR if kind == "f32t" else dna.DNA_ENGINE_AUTO
+    ctx = dna.dna_create(120, 200, 9, dna.make_opts(dtype=dna.DNA_F32, engine=eng))
     try:
-        W = p.W.copy()
-        H = p.H.copy()
-        kl = dna.dna_run_host(ctx, p.V, W, H, 3)
+        for pinned in (False, True, True):
+            if pinned:
+                V = torch.from_numpy(p.V).pin_memory()
+                W = torch.from_numpy(p.W.copy()).pin_memory()
+                H = torch.from_numpy(p.H.copy()).pin_memory()
+            else:
+                V, W, H = p.V, p.W.copy(), p.H.copy()
+            kl = dna.dna_run_host(ctx, V, W, H, 3)
+            Wn = W.numpy() if pinned else W
+            Hn = H.numpy() if pinned else H
+            assert kl == kl_dev, pinned
+            np.testing.assert_array_equal(Wn, Wd.astype(np.float32))
+            np.testing.assert_array_equal(Hn, Hd.astype(np.float32))
     finally:
         dna.dna_destroy(ctx)
-    assert kl == kl_dev
-    np.testing.assert_array_equal(W, Wd.astype(np.float32))
-    np.testing.assert_array_equal(H, Hd.astype(np.float32))
 
 
 def test_deterministic():

@@ -322,6 +322,23 @@ def main(argv=None):
                                       "roofline": sm["roofline"], "gpu_launches": sm["launches"]}
         line["time_to_target"] = time_to_target(dna, torch, prob, args.target_iters, args.engine,
                                                 args.workload)
+        if args.workload == "plain_large":
+            # the launch-bound size N=256 T=512 R=16 (FP32 form on the tensor cores): time
+            # per iteration under graph replay and with direct launches
+            sspec = WORKLOADS["plain_small"]
+            sprob = sspec["fn"](rank)
+            sm_args = argparse.Namespace(**vars(args))
+            sm_args.workload = "plain_small"
+            ss = measure(dna, torch, dist, sprob, "f32", sm_args, world, local, peaks,
+                         clocks=False, engine=args.engine)
+            line["small_form"] = {
+                "value": ss["value"], "unit": UNIT, "steps": sm_args.steps,
+                "us_per_step": 1e3 * ss["ms_max"] / sm_args.steps,
+                "direct_launches_us_per_step": 1e3 * ss["direct"]["ms_per_step"],
+                "gpu_launches": ss["launches"],
+                "config": {"workload": "plain_small", "desc": sspec["desc"], "N": sspec["N"],
+                           "T": sspec["T"], "R": sspec["R"], "form": "F32",
+                           "bound": "launch latency (each kernel has less than a wave of work)"}}
         if args.workload == "plain_large" and not args.no_mu_log:
             line["dna_vs_mu"] = convergence_log(dna, torch, prob, args.target_iters, args.engine,
                                                 args.log_file)

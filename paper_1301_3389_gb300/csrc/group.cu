@@ -401,26 +401,33 @@ __global__ void __launch_bounds__(256)
         const int64_t cnt = isx ? v.O : v.S;
         const int64_t si = isx ? v.xo : v.ys, sr = isx ? v.xr : v.yr;
         const int64_t R = v.R, i0 = (int64_t)tt.b * 64;
-        auto scaled = [&](int64_t r, int64_t at) {
-            const float f = (float)p.sig[r];
-            const float x = isx ? M[at] * f : M[at] * (1.0f / f);
-            M[at] = x;
-            return x;
-        };
-        if (si == 1) {
-            for (int r = ty; r < 64; r += 8)
+        // element e = 2 j + h of this thread: (r, i) = (ty + 8 j, i0 + 32 h + lane) when the
+        // matrix is contiguous along i, else (32 h + lane, i0 + ty + 8 j); all 16 loads are
+        // issued before the scaled values are stored back
+        const bool along_i = si == 1;
+        float val[16];
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int64_t i = i0 + 32 * h + lane;
-                    tile[r][32 * h + lane] = (r < R && i < cnt) ? scaled(r, r * sr + i) : 0.f;
-                }
-        } else {
-            for (int k = ty; k < 64; k += 8)
+        for (int e = 0; e < 16; ++e) {
+            const int j = e >> 1, h = e & 1;
+            const int64_t r = along_i ? ty + 8 * j : 32 * h + lane;
+            const int64_t i = along_i ? i0 + 32 * h + lane : i0 + ty + 8 * j;
+            val[e] = (r < R && i < cnt) ? M[r * sr + i * si] : 0.f;
+        }
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int64_t i = i0 + k, r = 32 * h + lane;
-                    tile[r][k] = (r < R && i < cnt) ? scaled(r, i * si + r * sr) : 0.f;
-                }
+        for (int e = 0; e < 16; ++e) {
+            const int j = e >> 1, h = e & 1;
+            const int64_t r = along_i ? ty + 8 * j : 32 * h + lane;
+            const int64_t i = along_i ? i0 + 32 * h + lane : i0 + ty + 8 * j;
+            float x = 0.f;
+            if (r < R && i < cnt) {
+                const float f = (float)p.sig[r];
+                x = isx ? val[e] * f : val[e] * (1.0f / f);
+                M[r * sr + i * si] = x;
+            }
+            if (along_i)
+                tile[r][32 * h + lane] = x;
+            else
+                tile[r][ty + 8 * j] = x;
         }
         __syncthreads();
         // values r >= R stay as the zeros the buffers were created with

@@ -122,9 +122,12 @@ struct BTile {
     int64_t o0, s_begin;       // o0: the first of the tile's two o-blocks
     int nsl, rb, split, which;
 };
-// tiles: which slowest, then the split, then the o-block pair, r-block fastest: a CTA
-// runs the r-blocks of one (pair, split) back to back, so the second reads the Q slices
-// from L2 (CTAs running together share the Yt slices of one split)
+// tiles: which slowest, then the split, then the o-block pair, r-block fastest.  CTA i of
+// G takes tiles i, i + G, i + 2 G, ..., so with G even the r-blocks of one (pair, split)
+// run at the same time on CTAs i and i + 1 and the second read of each Q slice comes from
+// L2 (CTAs running together also share the Yt slices of one split).  A contiguous range
+// of tiles per CTA ran the r-blocks back to back instead, and at 2 MB of Q per tile the
+// second read missed L2 behind the other CTAs' tiles.
 __device__ __forceinline__ BTile b_tile(int t, int nop, int nrb, int nsplit,
                                         const ContractArgs& a) {
     BTile x;
@@ -433,8 +436,8 @@ __global__ void __launch_bounds__(mat::B_THREADS, 1)
     volatile int* abort = reinterpret_cast<volatile int*>(sm + L::BAR + C_COUNT * 8 + 8);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int t_begin = (int)((int64_t)blockIdx.x * ntiles / gridDim.x);
-    const int t_end = (int)((int64_t)(blockIdx.x + 1) * ntiles / gridDim.x);
+    // tiles blockIdx.x, + gridDim.x, ... (see b_tile)
+    const int t_first = (int)blockIdx.x, t_step = (int)gridDim.x;
 
     if (warp == 0) { tmem_alloc(tslot, L::NCOLS); tmem_relinquish(); }
     if (tid == W_PROD_B * 32) {
@@ -454,12 +457,12 @@ __global__ void __launch_bounds__(mat::B_THREADS, 1)
     const uint32_t tmem = *tslot;
 
     if (warp == W_PROD_B) {
-        if (lane == 0 && t_begin < t_end) {
+        if (lane == 0 && t_first < ntiles) {
             tma_prefetch_desc(&tmQ); tma_prefetch_desc(&tmYt);
             if (WITH_B) { tma_prefetch_desc(&tmQb); tma_prefetch_desc(&tmY2t); }
             int kk = 0;
             bool ok = true;
-            for (int t = t_begin; ok && t < t_end; ++t) {
+            for (int t = t_first; ok && t < ntiles; t += t_step) {
                 const BTile x = b_tile(t, nop, nrb, nsplit, a);
                 const CUtensorMap* mq = x.which ? &tmQb : &tmQ;
                 const CUtensorMap* my = x.which ? &tmY2t : &tmYt;
@@ -488,7 +491,7 @@ __global__ void __launch_bounds__(mat::B_THREADS, 1)
             bool ok = true;
             int j = 0, tt = 0;
             constexpr uint32_t idesc = idesc_bf16(OBLK, RB);
-            for (int t = t_begin; ok && t < t_end; ++t, ++tt) {
+            for (int t = t_first; ok && t < ntiles; t += t_step, ++tt) {
                 const BTile x = b_tile(t, nop, nrb, nsplit, a);
                 const int nsl = x.nsl;
                 const bool two = x.o0 / OBLK + 1 < nob;
@@ -523,7 +526,7 @@ __global__ void __launch_bounds__(mat::B_THREADS, 1)
         const int qd = warp & 3, h = warp >> 2;
         const uint32_t lane_off = (uint32_t)(32 * qd) << 16;
         int tt = 0;
-        for (int t = t_begin; t < t_end; ++t, ++tt) {
+        for (int t = t_first; t < ntiles; t += t_step, ++tt) {
             const BTile x = b_tile(t, nop, nrb, nsplit, a);
             bool ok = wait_phase(&bar[C_ACCFULL], tt & 1, abort);
             if (!__all_sync(0xffffffffu, ok)) break;

@@ -136,9 +136,10 @@ struct BTile {
     int64_t o0, s_begin;
     int nsl, rb, split, which;
 };
-// tiles: which slowest, then the split, then the o-block, r-block fastest: a CTA runs the
-// r-blocks of one (o-block, split) back to back, so the second reads the Q planes from L2
-// (CTAs running together share the Yt slices of one split)
+// tiles: which slowest, then the split, then the o-block, r-block fastest.  CTA i of G
+// takes tiles i, i + G, i + 2 G, ..., so with G even the r-blocks of one (o-block, split)
+// run at the same time on CTAs i and i + 1 and the second read of the Q planes comes from
+// L2 (CTAs running together also share the Yt slices of one split).
 __device__ __forceinline__ BTile b_tile(int t, int nob, int nrb, int nsplit,
                                         const ContractArgs& a) {
     BTile x;
@@ -447,8 +448,8 @@ __global__ void __launch_bounds__(mats::B_THREADS, 1)
     volatile int* abort = reinterpret_cast<volatile int*>(sm + L::BAR + C_COUNT * 8 + 8);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int t_begin = (int)((int64_t)blockIdx.x * ntiles / gridDim.x);
-    const int t_end = (int)((int64_t)(blockIdx.x + 1) * ntiles / gridDim.x);
+    // tiles blockIdx.x, + gridDim.x, ... (see b_tile)
+    const int t_first = (int)blockIdx.x, t_step = (int)gridDim.x;
 
     if (warp == 0) { tmem_alloc(tslot, L::NCOLS); tmem_relinquish(); }
     if (tid == W_PROD_B * 32) {
@@ -470,7 +471,7 @@ __global__ void __launch_bounds__(mats::B_THREADS, 1)
     const uint32_t tmem = *tslot;
 
     if (warp == W_PROD_B) {
-        if (lane == 0 && t_begin < t_end) {
+        if (lane == 0 && t_first < ntiles) {
             tma_prefetch_desc(&tmQ); tma_prefetch_desc(&tmQl);
             tma_prefetch_desc(&tmYt); tma_prefetch_desc(&tmYtl);
             if (WITH_B) {
@@ -479,7 +480,7 @@ __global__ void __launch_bounds__(mats::B_THREADS, 1)
             }
             int kk = 0;
             bool ok = true;
-            for (int t = t_begin; ok && t < t_end; ++t) {
+            for (int t = t_first; ok && t < ntiles; t += t_step) {
                 const BTile x = b_tile(t, nob, nrb, nsplit, a);
                 const CUtensorMap* mq = x.which ? &tmQb : &tmQ;
                 const CUtensorMap* mql = x.which ? &tmQbl : &tmQl;
@@ -509,7 +510,7 @@ __global__ void __launch_bounds__(mats::B_THREADS, 1)
             bool ok = true;
             int j = 0, sg = 0;
             constexpr uint32_t idesc = idesc_bf16(OBLK, RB);
-            for (int t = t_begin; ok && t < t_end; ++t) {
+            for (int t = t_first; ok && t < ntiles; t += t_step) {
                 const int nsl = b_tile(t, nob, nrb, nsplit, a).nsl;
                 // segments of at most SEG_SL K-slices, each into the next accumulator
                 for (int sl0 = 0; ok && sl0 < nsl; sl0 += SEG_SL, ++sg) {
@@ -556,7 +557,7 @@ __global__ void __launch_bounds__(mats::B_THREADS, 1)
         const uint32_t lane_off = (uint32_t)(32 * qd) << 16;
         int sg = 0;
         bool live = true;
-        for (int t = t_begin; live && t < t_end; ++t) {
+        for (int t = t_first; live && t < ntiles; t += t_step) {
             const BTile x = b_tile(t, nob, nrb, nsplit, a);
             const int64_t o = x.o0 + 32 * qd + lane;
             float* dst = x.which ? a.Bpart : a.Apart;

@@ -275,10 +275,10 @@ __global__ void __launch_bounds__(ks::P2K_THREADS, 1)
                         const float z1 = __uint_as_float(zm[jj]), z2 = __uint_as_float(zd[jj]);
                         const bool pos = v > 0.f;
                         bad |= pos && !(z1 > 0.f && z2 > 0.f);
-                        // the hardware logarithm (absolute error near 2^-21 around 1,
-                        // relative 2^-21 elsewhere), far below the bf16 operand rounding
-                        run_m += pos ? z1 - v * __logf(z1) : z1;
-                        run_d += pos ? z2 - v * __logf(z2) : z2;
+                        // ln z = ln 2 log2 z with the hardware log2 (relative error
+                        // about 2^-22), far below the bf16 operand rounding
+                        run_m += pos ? z1 - v * (LN2F * lg2_ftz(z1)) : z1;
+                        run_d += pos ? z2 - v * (LN2F * lg2_ftz(z2)) : z2;
                     }
                 }
                 acc_m += (double)run_m;
@@ -519,8 +519,8 @@ __global__ void __launch_bounds__(ks::P2K_THREADS, 1)
                     const float z1 = __uint_as_float(zm[jj]), z2 = __uint_as_float(zd[jj]);
                     const bool pos = v > 0.f;
                     bad |= pos && !(z1 > 0.f && z2 > 0.f);
-                    run_m += pos ? z1 - v * __logf(z1) : z1;
-                    run_d += pos ? z2 - v * __logf(z2) : z2;
+                    run_m += pos ? z1 - v * (LN2F * lg2_ftz(z1)) : z1;
+                    run_d += pos ? z2 - v * (LN2F * lg2_ftz(z2)) : z2;
                 }
             }
             // the four partials of each column meet in the first two columns each warp read;

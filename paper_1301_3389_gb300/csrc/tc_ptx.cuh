@@ -307,5 +307,16 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
     return *reinterpret_cast<uint32_t*>(&v);
 }
 
+// The costs' logarithm on the multi-function unit: log2(x) by the PTX instruction
+// lg2.approx.ftz.f32 (relative error about 2^-22 on normal x), and ln x = ln 2 * log2 x.
+// Subnormal x is read as 0 (log2 = -inf, so the cost is infinite as for z = 0); without
+// .ftz the instruction needs extra steps for subnormal inputs on every call.
+__device__ __forceinline__ float lg2_ftz(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+constexpr float LN2F = 0.693147180559945309f;
+
 }  // namespace tc
 }  // namespace dna

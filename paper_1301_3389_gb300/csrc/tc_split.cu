@@ -762,11 +762,10 @@ __device__ __forceinline__ void pass2s_body(const P2Args& a, int64_t nch, int64_
                     if constexpr (FULL) {
                         run_m += pos ? z1 + v * logf(v / z1) - v : z1;
                     } else {
-                        // the hardware logarithm (absolute error near 2^-21 around 1,
-                        // relative 2^-21 elsewhere): well inside the split form's 1e-4
-                        // near-tie margin
-                        run_m += pos ? z1 - v * __logf(z1) : z1;
-                        run_d += pos ? z2 - v * __logf(z2) : z2;
+                        // ln z = ln 2 log2 z with the hardware log2 (relative error about
+                        // 2^-22): well inside the split form's 1e-4 near-tie margin
+                        run_m += pos ? z1 - v * (LN2F * lg2_ftz(z1)) : z1;
+                        run_d += pos ? z2 - v * (LN2F * lg2_ftz(z2)) : z2;
                     }
                 }
                 __syncwarp();

@@ -234,8 +234,9 @@ __device__ __forceinline__ void pass1_body(const P1Args& a, int64_t bx, int64_t 
             __syncwarp();
             if (lane == 0) mbar_arrive(&bar[B_XFULL]);
         }
-        // min over v > 0 of z: a non-positive z there is an infinite cost (a NaN z makes
-        // NaN candidates, which pass 2 reports)
+        // min over v > 0 of z: a z there below the smallest normal float (read as 0 by the
+        // reciprocal) is an infinite cost (a NaN z makes NaN candidates, which pass 2
+        // reports)
         float zmin = 1.f;
         bool ok = true;
         for (int k = 0; k < nch; ++k) {
@@ -264,7 +265,7 @@ __device__ __forceinline__ void pass1_body(const P1Args& a, int64_t bx, int64_t 
                 for (int t = 0; t < 2; ++t) {
                     const float v = vv[j + t];
                     const float z = __uint_as_float(zr[j + t]);
-                    const float rz = __fdividef(1.0f, z);
+                    const float rz = rcp_ftz(z);
                     const bool pos = v > 0.f;
                     zmin = fminf(zmin, pos ? z : 1.f);
                     q[t] = pos ? v * rz : 0.f;
@@ -288,7 +289,7 @@ __device__ __forceinline__ void pass1_body(const P1Args& a, int64_t bx, int64_t 
             __syncwarp();
             if (lane == 0) mbar_arrive(&bar[B_QFULL]);
         }
-        if (!(zmin > 0.f)) atomicOr(a.status, STATUS_NONFINITE);
+        if (!(zmin >= FLT_MIN_NORMAL)) atomicOr(a.status, STATUS_NONFINITE);
         if (ok && nch > 0) {   // GEMM2/3 of the last chunk done: A and B are final
             const int kl = nch - 1;
             ok = __all_sync(0xffffffffu,
@@ -589,7 +590,7 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
                     for (int t = 0; t < 2; ++t) {
                         const float v = vv[jj + t];
                         const float z = __uint_as_float(zr[jj + t]);
-                        const float rz = __fdividef(1.0f, z);
+                        const float rz = rcp_ftz(z);
                         const bool pos = v > 0.f;
                         zmin = fminf(zmin, pos ? z : 1.f);
                         q[t] = pos ? v * rz : 0.f;
@@ -651,7 +652,7 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
             __syncwarp();
             if (lane == 0) mbar_arrive(&bar[B_ACCEMPTY]);
         }
-        if (!(zmin > 0.f)) atomicOr(status, STATUS_NONFINITE);
+        if (!(zmin >= FLT_MIN_NORMAL)) atomicOr(status, STATUS_NONFINITE);
     }
     tc_fence_before();
     __syncthreads();

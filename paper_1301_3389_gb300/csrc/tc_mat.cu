@@ -372,7 +372,7 @@ __global__ void __launch_bounds__(mat::A_THREADS, 1)
                         for (int u = 0; u < 2; ++u) {
                             const float v = fmaxf(vh[(j + u) * OBLK], 0.f);
                             const float z = fmaxf(__uint_as_float(zr[j + u]), FLT_MIN);
-                            const float rz = __fdividef(1.0f, z);
+                            const float rz = rcp_ftz(z);
                             q[u] = v * rz;
                             qb[u] = q[u] * rz;
                             qbmax = fmaxf(qbmax, qb[u]);

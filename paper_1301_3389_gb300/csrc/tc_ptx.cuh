@@ -318,5 +318,15 @@ __device__ __forceinline__ float lg2_ftz(float x) {
 }
 constexpr float LN2F = 0.693147180559945309f;
 
+// 1 / x by the PTX instruction rcp.approx.ftz.f32 (relative error about 2^-23 on normal x);
+// subnormal x is read as 0 (1 / x = inf), so the ratio kernels treat z below the smallest
+// normal float like z = 0
+__device__ __forceinline__ float rcp_ftz(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+constexpr float FLT_MIN_NORMAL = 1.17549435e-38f;   // 2^-126
+
 }  // namespace tc
 }  // namespace dna

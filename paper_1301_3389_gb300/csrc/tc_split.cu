@@ -424,7 +424,7 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
                         for (int tt = 0; tt < 2; ++tt) {
                             const float v = vv[j + tt];
                             const float z = __uint_as_float(zr[j + tt]);
-                            const float rz = __fdividef(1.0f, z);
+                            const float rz = rcp_ftz(z);
                             const bool pos = v > 0.f;
                             zmin = fminf(zmin, pos ? z : 1.f);
                             const float q = v * rz;
@@ -478,7 +478,7 @@ __global__ void __launch_bounds__(P1_THREADS, 1)
             }
             tc_fence_before();
         }
-        if (!(zmin > 0.f)) atomicOr(a.status, STATUS_NONFINITE);
+        if (!(zmin >= FLT_MIN_NORMAL)) atomicOr(a.status, STATUS_NONFINITE);
     }
     tc_fence_before();
     __syncthreads();

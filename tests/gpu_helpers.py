@@ -34,7 +34,9 @@ SPLIT_LARGE_R_TOL = 2e-4
 # check).  ELEM_TOL per form; derivation in the module docstring of test_gpu_parity.py.
 ELEM_FLOOR = 1e-6
 # free-running trajectories (errors of earlier steps carried along): measured maxima over
-# the parity tests 1.4e-3 (f32), 8.6e-3 (f32t), 5e-12 (f64); about 3x margin
+# the parity tests 1.4e-3 (f32), 8.6e-3 (f32t at R <= 128), 5e-12 (f64), about 3x margin;
+# the split form at R = 300 and 512 reaches 7.7e-3 and 1.7e-2 (its operand representation
+# error grows with R, see SPLIT_LARGE_R_TOL), inside the same bound
 ELEM_TOL = {"f32": 5e-3, "f32t": 2e-2, "f64": 1e-9}
 
 
